@@ -1,0 +1,204 @@
+"""CPU FP64 oracle for P1 assembly (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use this
+package. It loads ``liboracle.so`` built from ``oracle.c`` with gcc (``-O2 -ffp-contract=off``,
+so no multiply-add contraction changes the rounding) and wraps it for numpy arrays. It shares
+nothing with the CUDA library; see ``oracle.c`` for what each routine follows in the paper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+MASS, WMASS, STIFF, ELAS = 0, 1, 2, 3
+_ERRORS = {1: "invalid argument", 2: "index out of range", 3: "repeated vertex in an element",
+           4: "element not counter-clockwise (D <= 0)", 5: "out of memory", 6: "capacity"}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"oracle {where}: {_ERRORS.get(code, code)}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to its source (plain C, gcc)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        D = ctypes.c_double
+        _lib.or_double_area.argtypes = [P, P]
+        _lib.or_double_area.restype = D
+        _lib.or_elem_mass.argtypes = [D, P]
+        _lib.or_elem_wmass.argtypes = [D, P, P]
+        _lib.or_elem_stiff.argtypes = [P, P, D, P]
+        _lib.or_elem_elas.argtypes = [P, P, D, D, D, P]
+        _lib.or_triplets.argtypes = [ctypes.c_int, I64, I64, P, P, P, D, D, P, P, P, P]
+        _lib.or_sparse.argtypes = [I64, I64, I64, P, P, P, P, P, P, I64, P]
+        _lib.or_assemble.argtypes = [ctypes.c_int, I64, I64, P, P, P, D, D, P, P, P, I64, P, P]
+        _lib.or_adjoint.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, P, P, P]
+        for f in ("or_triplets", "or_sparse", "or_assemble", "or_adjoint"):
+            getattr(_lib, f).restype = ctypes.c_int
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ------------------------------------------------------------------ element matrices
+
+def double_area(x, y) -> float:
+    return lib().or_double_area(_p(_f64(x)), _p(_f64(y)))
+
+
+def elem_mass(area: float) -> np.ndarray:
+    E = np.empty(9)
+    lib().or_elem_mass(area, _p(E))
+    return E.reshape(3, 3)
+
+
+def elem_wmass(area: float, w) -> np.ndarray:
+    E = np.empty(9)
+    lib().or_elem_wmass(area, _p(_f64(w)), _p(E))
+    return E.reshape(3, 3)
+
+
+def elem_stiff(x, y, area: float) -> np.ndarray:
+    E = np.empty(9)
+    lib().or_elem_stiff(_p(_f64(x)), _p(_f64(y)), area, _p(E))
+    return E.reshape(3, 3)
+
+
+def elem_elas(x, y, area: float, lam: float, mu: float) -> np.ndarray:
+    E = np.empty(36)
+    lib().or_elem_elas(_p(_f64(x)), _p(_f64(y)), area, lam, mu, _p(E))
+    return E.reshape(6, 6)
+
+
+# ------------------------------------------------------------------ assembly
+
+def triplets(kind: int, q, me, w=None, lam: float = 1.0, mu: float = 0.5):
+    """(Ig, Jg, Kg) with entry c = n*n*k + n*jl + il (element matrices stored column-wise)."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    n = 6 if kind == ELAS else 3
+    I = np.empty(n * n * nme, np.int32)
+    J = np.empty_like(I)
+    K = np.empty(n * n * nme)
+    w = _f64(w) if w is not None else np.zeros(max(nq, 1))
+    bad = ctypes.c_int64(-1)
+    st = lib().or_triplets(kind, nq, nme, _p(q), _p(me), _p(w), lam, mu, _p(I), _p(J), _p(K),
+                           ctypes.byref(bad))
+    if st:
+        raise OracleError(st, f"triplets (element {bad.value})")
+    return I, J, K
+
+
+def sparse(I, J, K, n_rows: int, n_cols: int):
+    """CSR (row_ptr, col_idx, val) of sparse(I, J, K, n_rows, n_cols), 0-based."""
+    I, J, K = _i32(I), _i32(J), _f64(K)
+    nt = I.shape[0]
+    row_ptr = np.empty(n_rows + 1, np.int32)
+    col_idx = np.empty(max(nt, 1), np.int32)
+    val = np.empty(max(nt, 1))
+    nnz = ctypes.c_int64(0)
+    st = lib().or_sparse(n_rows, n_cols, nt, _p(I), _p(J), _p(K), _p(row_ptr), _p(col_idx),
+                         _p(val), max(nt, 1), ctypes.byref(nnz))
+    if st:
+        raise OracleError(st, "sparse")
+    return row_ptr, col_idx[:nnz.value].copy(), val[:nnz.value].copy()
+
+
+def assemble(kind: int, q, me, w=None, lam: float = 1.0, mu: float = 0.5):
+    """Global CSR matrix (row_ptr, col_idx, val) of one kind: triplets then sparse()."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    n = 6 if kind == ELAS else 3
+    n_rows = 2 * nq if kind == ELAS else nq
+    cap = max(n * n * nme, 1)
+    row_ptr = np.empty(n_rows + 1, np.int32)
+    col_idx = np.empty(cap, np.int32)
+    val = np.empty(cap)
+    w = _f64(w) if w is not None else np.zeros(max(nq, 1))
+    nnz = ctypes.c_int64(0)
+    bad = ctypes.c_int64(-1)
+    st = lib().or_assemble(kind, nq, nme, _p(q), _p(me), _p(w), lam, mu, _p(row_ptr),
+                           _p(col_idx), _p(val), cap, ctypes.byref(nnz), ctypes.byref(bad))
+    if st:
+        raise OracleError(st, f"assemble (element {bad.value})")
+    return row_ptr, col_idx[:nnz.value].copy(), val[:nnz.value].copy()
+
+
+def adjoint(kind: int, q, me, row_ptr, col_idx, G, w=None, dq=None, dw=None):
+    """Accumulate dL/dq ([2, nq]) and dL/dw ([nq]) of L = sum(G * A.values) for one kind."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    if dq is None:
+        dq = np.zeros((2, nq))
+    if dw is None:
+        dw = np.zeros(nq)
+    w = _f64(w) if w is not None else np.zeros(max(nq, 1))
+    st = lib().or_adjoint(kind, nq, nme, _p(q), _p(me), _p(w), _p(_i32(row_ptr)),
+                          _p(_i32(col_idx)), _p(_f64(G)), _p(dq), _p(dw))
+    if st:
+        raise OracleError(st, "adjoint")
+    return dq, dw
+
+
+def csr_to_dense(row_ptr, col_idx, val, n_cols: int) -> np.ndarray:
+    n_rows = len(row_ptr) - 1
+    A = np.zeros((n_rows, n_cols))
+    for i in range(n_rows):
+        A[i, col_idx[row_ptr[i]:row_ptr[i + 1]]] = val[row_ptr[i]:row_ptr[i + 1]]
+    return A
+
+
+def csr_row_values(kind: int, q, me, rows, w=None, lam: float = 1.0, mu: float = 0.5):
+    """Oracle values of selected rows only, for meshes too large to assemble whole.
+
+    For each requested row r (vertex r, or dof r for ELAS) it finds the elements containing
+    the vertex, assembles just their triplets with the oracle, and applies sparse() to the
+    triplets whose row is r. Returns a list of (cols, vals) in ascending column order.
+    """
+    q, me = _f64(q), _i32(me)
+    out = []
+    for r in rows:
+        v = r // 2 if kind == ELAS else r
+        ks = np.nonzero((me == v).any(axis=0))[0]
+        sub = me[:, ks]
+        I, J, K = triplets(kind, q, sub, w, lam, mu)
+        sel = I == r
+        n_rows = 2 * q.shape[1] if kind == ELAS else q.shape[1]
+        rp, ci, va = sparse(I[sel], J[sel], K[sel], n_rows, n_rows)
+        out.append((ci[rp[r]:rp[r + 1]], va[rp[r]:rp[r + 1]]))
+    return out

@@ -1,0 +1,353 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU reference for P1 finite-element matrix assembly.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark may call this library. It shares no code, header, table or helper with the CUDA
+ * library; the two meet only through the seeded input arrays.
+ *
+ * What it computes (Cuvelier, Japhet, Scarella, "An efficient way to perform the assembly of
+ * finite element matrices in Matlab and Octave", INRIA RR-8305, 2013):
+ *   - element matrices straight from their closed forms: mass M^e (Eq. 1), weighted mass
+ *     M^{e,[w]} (Eq. 2), stiffness S^e (Eq. 3), and the plane-elasticity K^e = |T| B^T C B
+ *     with the gradients of Eq. (GradFoncBas) (Section 6);
+ *   - the triplet arrays Ig, Jg, Kg in the paper's order: element k's local matrix stored
+ *     column-wise, contribution index c = n^2*k + n*jl + il for an n x n element matrix
+ *     (Section 4, "Ke = E(:)"; Section 6.1 for n = 6);
+ *   - the sparse(I,J,K,m,n) semantics of Section 4: triplets with equal (row, col) are summed.
+ *     Result in CSR, columns ascending in each row. Reading kept here: the pattern is
+ *     structural, so a sum that happens to be exactly 0.0 is still stored.
+ *
+ * Conventions: indices are 0-based (the paper is 1-based). q is [2][nq] row-major (x row,
+ * then y row); me is [3][nme] row-major. The area |T| is not an input here: it is half the
+ * signed cross product D = v_x*w_y - w_x*v_y of the edge vectors v = q3-q1, w = q1-q2, taken
+ * from coordinate differences; D <= 0 is rejected (counter-clockwise triangles only).
+ * Elasticity dofs are interleaved: vertex i owns rows 2i (x) and 2i+1 (y).
+ *
+ * Summation: duplicates are summed left to right in ascending contribution index c, in
+ * round-to-nearest FP64 with no fused multiply-add (the build passes -ffp-contract=off).
+ *
+ * The adjoint (dL/dq, dL/dw for L = sum_p G[p]*A.values[p]) is not in the paper; it is the
+ * derivative of the element formulas above, written out term by term in or_adjoint().
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { OR_MASS = 0, OR_WMASS = 1, OR_STIFF = 2, OR_ELAS = 3 };
+enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_INDEX = 2, OR_ERR_DEGENERATE = 3, OR_ERR_ORIENT = 4,
+       OR_ERR_NOMEM = 5, OR_ERR_CAP = 6 };
+
+/* ---------------------------------------------------------------- element matrices ---- */
+
+/* Twice the signed area from the edge vectors v = p2 - p0 and w = p0 - p1 (0-based names of
+ * the paper's q^3 - q^1 and q^1 - q^2). */
+double or_double_area(const double x[3], const double y[3]) {
+    double vx = x[2] - x[0], vy = y[2] - y[0];
+    double wx = x[0] - x[1], wy = y[0] - y[1];
+    return vx * wy - wx * vy;
+}
+
+/* Eq. (1): M^e = |T|/12 * [[2,1,1],[1,2,1],[1,1,2]].  E is row-major E[3*a+b]. */
+void or_elem_mass(double area, double E[9]) {
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            E[3 * a + b] = (area / 12.0) * (a == b ? 2.0 : 1.0);
+}
+
+/* Eq. (2), entry by entry as printed: |T|/30 times
+ *   [3w1+w2+w3,    w1+w2+w3/2,  w1+w2/2+w3 ]
+ *   [w1+w2+w3/2,   w1+3w2+w3,   w1/2+w2+w3 ]
+ *   [w1+w2/2+w3,   w1/2+w2+w3,  w1+w2+3w3  ]                                             */
+void or_elem_wmass(double area, const double w[3], double E[9]) {
+    double c = area / 30.0;
+    E[0] = c * (3.0 * w[0] + w[1] + w[2]);
+    E[1] = c * (w[0] + w[1] + w[2] / 2.0);
+    E[2] = c * (w[0] + w[1] / 2.0 + w[2]);
+    E[3] = c * (w[0] + w[1] + w[2] / 2.0);
+    E[4] = c * (w[0] + 3.0 * w[1] + w[2]);
+    E[5] = c * (w[0] / 2.0 + w[1] + w[2]);
+    E[6] = c * (w[0] + w[1] / 2.0 + w[2]);
+    E[7] = c * (w[0] / 2.0 + w[1] + w[2]);
+    E[8] = c * (w[0] + w[1] + 3.0 * w[2]);
+}
+
+/* The three edge vectors of Eq. (3): u = q2-q3, v = q3-q1, w = q1-q2 (0-based p1-p2, p2-p0,
+ * p0-p1). ex[a], ey[a] are the components of the a-th of (u, v, w). */
+static void edges(const double x[3], const double y[3], double ex[3], double ey[3]) {
+    ex[0] = x[1] - x[2]; ey[0] = y[1] - y[2];
+    ex[1] = x[2] - x[0]; ey[1] = y[2] - y[0];
+    ex[2] = x[0] - x[1]; ey[2] = y[0] - y[1];
+}
+
+/* Eq. (3): S^e = 1/(4|T|) * Gram(u, v, w). */
+void or_elem_stiff(const double x[3], const double y[3], double area, double E[9]) {
+    double ex[3], ey[3];
+    edges(x, y, ex, ey);
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            E[3 * a + b] = (ex[a] * ex[b] + ey[a] * ey[b]) / (4.0 * area);
+}
+
+/* Section 6: K^e = |T| * B^T C B, 6x6 row-major. Gradients (Eq. GradFoncBas):
+ * grad(phi_a) = (e_a,y, -e_a,x) / (2|T|) with e = (u, v, w). Local dof 2a is the x-component
+ * of vertex a, 2a+1 the y-component; B has column 2a = (dphi_a/dx, 0, dphi_a/dy) and column
+ * 2a+1 = (0, dphi_a/dy, dphi_a/dx). C = [[l+2m, l, 0], [l, l+2m, 0], [0, 0, m]].            */
+void or_elem_elas(const double x[3], const double y[3], double area, double lam, double mu,
+                  double E[36]) {
+    double ex[3], ey[3];
+    edges(x, y, ex, ey);
+    double B[3][6];
+    memset(B, 0, sizeof B);
+    for (int a = 0; a < 3; a++) {
+        double gx = ey[a] / (2.0 * area);
+        double gy = -ex[a] / (2.0 * area);
+        B[0][2 * a] = gx;  B[2][2 * a] = gy;
+        B[1][2 * a + 1] = gy;  B[2][2 * a + 1] = gx;
+    }
+    double C[3][3] = {{lam + 2.0 * mu, lam, 0.0}, {lam, lam + 2.0 * mu, 0.0}, {0.0, 0.0, mu}};
+    double CB[3][6];
+    for (int r = 0; r < 3; r++)
+        for (int j = 0; j < 6; j++) {
+            double s = 0.0;
+            for (int t = 0; t < 3; t++) s += C[r][t] * B[t][j];
+            CB[r][j] = s;
+        }
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j < 6; j++) {
+            double s = 0.0;
+            for (int t = 0; t < 3; t++) s += B[t][i] * CB[t][j];
+            E[6 * i + j] = area * s;
+        }
+}
+
+/* ------------------------------------------------------------------------ triplets ---- */
+
+static int gather_element(int64_t nq, const double* q, int64_t nme, const int32_t* me, int64_t k,
+                          int32_t v[3], double x[3], double y[3]) {
+    for (int a = 0; a < 3; a++) {
+        v[a] = me[a * nme + k];
+        if (v[a] < 0 || v[a] >= nq) return OR_ERR_INDEX;
+        x[a] = q[v[a]];
+        y[a] = q[nq + v[a]];
+    }
+    if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2]) return OR_ERR_DEGENERATE;
+    return OR_OK;
+}
+
+/* The arrays Ig, Jg, Kg of Sections 4-6 for one matrix kind, 0-based. Element k writes
+ * entries c = n*n*k + n*jl + il (its matrix column-wise), n = 3 (or 6 for OR_ELAS).
+ * w: vertex values (OR_WMASS only). On error, *bad_element receives the element index. */
+int or_triplets(int kind, int64_t nq, int64_t nme, const double* q, const int32_t* me,
+                const double* w, double lam, double mu, int32_t* I, int32_t* J, double* K,
+                int64_t* bad_element) {
+    if (kind < OR_MASS || kind > OR_ELAS || nq < 0 || nme < 0) return OR_ERR_ARG;
+    int n = (kind == OR_ELAS) ? 6 : 3;
+    for (int64_t k = 0; k < nme; k++) {
+        int32_t v[3];
+        double x[3], y[3], E[36];
+        int st = gather_element(nq, q, nme, me, k, v, x, y);
+        if (st) { if (bad_element) *bad_element = k; return st; }
+        double D = or_double_area(x, y);
+        if (!(D > 0.0)) { if (bad_element) *bad_element = k; return OR_ERR_ORIENT; }
+        double area = D / 2.0;
+        if (kind == OR_MASS) {
+            or_elem_mass(area, E);
+        } else if (kind == OR_WMASS) {
+            double wl[3] = {w[v[0]], w[v[1]], w[v[2]]};
+            or_elem_wmass(area, wl, E);
+        } else if (kind == OR_STIFF) {
+            or_elem_stiff(x, y, area, E);
+        } else {
+            or_elem_elas(x, y, area, lam, mu, E);
+        }
+        for (int jl = 0; jl < n; jl++)
+            for (int il = 0; il < n; il++) {
+                int64_t c = (int64_t)n * n * k + (int64_t)n * jl + il;
+                int32_t gi, gj;
+                if (n == 3) { gi = v[il]; gj = v[jl]; }
+                else { gi = 2 * v[il / 2] + (il % 2); gj = 2 * v[jl / 2] + (jl % 2); }
+                I[c] = gi;
+                J[c] = gj;
+                K[c] = E[n * il + jl];
+            }
+    }
+    return OR_OK;
+}
+
+/* -------------------------------------------------------------- sparse(I, J, K) ---- */
+
+static const int32_t* g_I;
+static const int32_t* g_J;
+
+static int key_less(int64_t a, int64_t b) {
+    if (g_I[a] != g_I[b]) return g_I[a] < g_I[b];
+    return g_J[a] < g_J[b];
+}
+
+/* Stable bottom-up merge sort of the permutation idx by (I, J): equal keys keep their input
+ * order, so every run of duplicates stays in ascending contribution index. */
+static int stable_sort_by_key(int64_t n, int64_t* idx) {
+    int64_t* tmp = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!tmp) return OR_ERR_NOMEM;
+    int64_t* src = idx;
+    int64_t* dst = tmp;
+    for (int64_t width = 1; width < n; width *= 2) {
+        for (int64_t lo = 0; lo < n; lo += 2 * width) {
+            int64_t mid = lo + width < n ? lo + width : n;
+            int64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            int64_t i = lo, j = mid, o = lo;
+            while (i < mid && j < hi) {
+                if (key_less(src[j], src[i])) dst[o++] = src[j++];
+                else dst[o++] = src[i++];
+            }
+            while (i < mid) dst[o++] = src[i++];
+            while (j < hi) dst[o++] = src[j++];
+        }
+        int64_t* t = src; src = dst; dst = t;
+    }
+    if (src != idx) memcpy(idx, src, (size_t)n * sizeof(int64_t));
+    free(tmp);
+    return OR_OK;
+}
+
+/* sparse(I, J, K, n_rows, n_cols) into CSR: row_ptr[n_rows+1], col_idx[cap], val[cap].
+ * Duplicates are summed in ascending input position; exact zeros are kept. */
+int or_sparse(int64_t n_rows, int64_t n_cols, int64_t ntrip, const int32_t* I, const int32_t* J,
+              const double* K, int32_t* row_ptr, int32_t* col_idx, double* val, int64_t cap,
+              int64_t* nnz_out) {
+    for (int64_t t = 0; t < ntrip; t++)
+        if (I[t] < 0 || I[t] >= n_rows || J[t] < 0 || J[t] >= n_cols) return OR_ERR_INDEX;
+    int64_t* idx = (int64_t*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(int64_t));
+    if (!idx) return OR_ERR_NOMEM;
+    for (int64_t t = 0; t < ntrip; t++) idx[t] = t;
+    g_I = I;
+    g_J = J;
+    int st = stable_sort_by_key(ntrip, idx);
+    if (st) { free(idx); return st; }
+    for (int64_t r = 0; r <= n_rows; r++) row_ptr[r] = 0;
+    int64_t nnz = 0;
+    for (int64_t s = 0; s < ntrip; ) {
+        int64_t e = s + 1;
+        double sum = K[idx[s]];
+        while (e < ntrip && I[idx[e]] == I[idx[s]] && J[idx[e]] == J[idx[s]]) {
+            sum += K[idx[e]];
+            e++;
+        }
+        if (nnz >= cap) { free(idx); return OR_ERR_CAP; }
+        col_idx[nnz] = J[idx[s]];
+        val[nnz] = sum;
+        row_ptr[I[idx[s]] + 1]++;
+        nnz++;
+        s = e;
+    }
+    for (int64_t r = 0; r < n_rows; r++) row_ptr[r + 1] += row_ptr[r];
+    *nnz_out = nnz;
+    free(idx);
+    return OR_OK;
+}
+
+/* One full assembly: triplets of one kind, then sparse(). n_rows = nq (or 2nq for OR_ELAS).
+ * The caller provides row_ptr[n_rows+1] and col_idx/val with capacity cap (9*nme, or 36*nme,
+ * always suffices). */
+int or_assemble(int kind, int64_t nq, int64_t nme, const double* q, const int32_t* me,
+                const double* w, double lam, double mu, int32_t* row_ptr, int32_t* col_idx,
+                double* val, int64_t cap, int64_t* nnz_out, int64_t* bad_element) {
+    int n = (kind == OR_ELAS) ? 6 : 3;
+    int64_t ntrip = (int64_t)n * n * nme;
+    int32_t* I = (int32_t*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(int32_t));
+    int32_t* J = (int32_t*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(int32_t));
+    double* K = (double*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(double));
+    int st = (I && J && K) ? OR_OK : OR_ERR_NOMEM;
+    if (!st) st = or_triplets(kind, nq, nme, q, me, w, lam, mu, I, J, K, bad_element);
+    if (!st) st = or_sparse(n == 6 ? 2 * nq : nq, n == 6 ? 2 * nq : nq, ntrip, I, J, K,
+                            row_ptr, col_idx, val, cap, nnz_out);
+    free(I); free(J); free(K);
+    return st;
+}
+
+/* ------------------------------------------------------------------------- adjoint ---- */
+
+/* Position of column j in CSR row i (binary search over the ascending columns), -1 if absent. */
+static int64_t csr_find(const int32_t* row_ptr, const int32_t* col_idx, int32_t i, int32_t j) {
+    int64_t lo = row_ptr[i], hi = row_ptr[i + 1];
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (col_idx[mid] < j) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < row_ptr[i + 1] && col_idx[lo] == j) ? lo : -1;
+}
+
+/* Accumulates into dq ([2][nq]) and, for OR_WMASS, dw ([nq]) the gradient of
+ *   L = sum_p G[p] * A.values[p]
+ * where A is the scalar matrix of the given kind (OR_MASS, OR_WMASS or OR_STIFF) on the CSR
+ * pattern (row_ptr, col_idx). The caller zeroes dq and dw. Per element, with A = |T| = D/2,
+ * g_ab = G at the position of (me[a], me[b]) and e = (u, v, w) as in Eq. (3):
+ *   dA/dp_a = (e_a,y, -e_a,x) / 2                          (derivative of D/2)
+ *   mass:     dL/dA = sum_ab g_ab * M_ab / A               (M^e is linear in A)
+ *   wmass:    dL/dA = sum_ab g_ab * Mw_ab / A,  dL/dw_c = sum_ab g_ab * dMw_ab/dw_c
+ *   stiff:    dL/de_a = sum_b (g_ab + g_ba) e_b / (4A),  dL/dA = -sum_ab g_ab * S_ab / A
+ * and, since e_0 = p1-p2, e_1 = p2-p0, e_2 = p0-p1,
+ *   dL/dp_0 = dL/de_2 - dL/de_1,  dL/dp_1 = dL/de_0 - dL/de_2,  dL/dp_2 = dL/de_1 - dL/de_0,
+ * plus dL/dA * dA/dp_a. Vertex sums run in element order. */
+int or_adjoint(int kind, int64_t nq, int64_t nme, const double* q, const int32_t* me,
+               const double* w, const int32_t* row_ptr, const int32_t* col_idx, const double* G,
+               double* dq, double* dw) {
+    if (kind != OR_MASS && kind != OR_WMASS && kind != OR_STIFF) return OR_ERR_ARG;
+    for (int64_t k = 0; k < nme; k++) {
+        int32_t v[3];
+        double x[3], y[3], E[9], g[9];
+        int st = gather_element(nq, q, nme, me, k, v, x, y);
+        if (st) return st;
+        double D = or_double_area(x, y);
+        if (!(D > 0.0)) return OR_ERR_ORIENT;
+        double area = D / 2.0;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                int64_t p = csr_find(row_ptr, col_idx, v[a], v[b]);
+                if (p < 0) return OR_ERR_INDEX;
+                g[3 * a + b] = G[p];
+            }
+        double ex[3], ey[3];
+        edges(x, y, ex, ey);
+        double dex[3] = {0, 0, 0}, dey[3] = {0, 0, 0};
+        double dA = 0.0;
+        if (kind == OR_MASS) {
+            or_elem_mass(area, E);
+            for (int t = 0; t < 9; t++) dA += g[t] * E[t] / area;
+        } else if (kind == OR_WMASS) {
+            double wl[3] = {w[v[0]], w[v[1]], w[v[2]]};
+            or_elem_wmass(area, wl, E);
+            for (int t = 0; t < 9; t++) dA += g[t] * E[t] / area;
+            /* dMw/dw_c: Eq. (2) with w replaced by the c-th unit vector. */
+            for (int c = 0; c < 3; c++) {
+                double unit[3] = {0, 0, 0}, Ec[9];
+                unit[c] = 1.0;
+                or_elem_wmass(area, unit, Ec);
+                double s = 0.0;
+                for (int t = 0; t < 9; t++) s += g[t] * Ec[t];
+                dw[v[c]] += s;
+            }
+        } else {
+            or_elem_stiff(x, y, area, E);
+            for (int t = 0; t < 9; t++) dA -= g[t] * E[t] / area;
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) {
+                    double gs = (g[3 * a + b] + g[3 * b + a]) / (4.0 * area);
+                    dex[a] += gs * ex[b];
+                    dey[a] += gs * ey[b];
+                }
+        }
+        double dpx[3], dpy[3];
+        dpx[0] = dex[2] - dex[1]; dpy[0] = dey[2] - dey[1];
+        dpx[1] = dex[0] - dex[2]; dpy[1] = dey[0] - dey[2];
+        dpx[2] = dex[1] - dex[0]; dpy[2] = dey[1] - dey[0];
+        for (int a = 0; a < 3; a++) {
+            dpx[a] += dA * (ey[a] / 2.0);
+            dpy[a] += dA * (-ex[a] / 2.0);
+            dq[v[a]] += dpx[a];
+            dq[nq + v[a]] += dpy[a];
+        }
+    }
+    return OR_OK;
+}

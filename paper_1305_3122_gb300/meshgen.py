@@ -1,0 +1,165 @@
+"""Seeded synthetic inputs: jittered, node-permuted triangulations of the unit square.
+
+This module generates *inputs only* (vertex coordinates, connectivity, vertex weights,
+upstream gradients, sample indices). It holds none of the assembly arithmetic, so it can
+feed both the CUDA path and the CPU oracle with identical arrays.
+
+Layout follows the mesh description of Section 2 of the paper (the table of ``q``, ``me``):
+``q`` is ``[2, nq]`` float64 (row 0 = x, row 1 = y) and ``me`` is ``[3, nme]`` int32 with
+0-based vertex ids (the paper is 1-based), every triangle counter-clockwise.
+
+Random numbers come from one counter-based generator: the output sequence of splitmix64
+(Steele, Lea and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014),
+started at a key derived from ``(seed, stream)``. Value ``i`` of a stream is
+``mix(key + (i + 1) * 0x9E3779B97F4A7C15)`` with the splitmix64 finaliser ``mix``; a uniform
+double in [0, 1) is the top 53 bits times 2**-53. Because every value depends only on its
+counter, the arrays are identical on every machine and independent of numpy's own RNGs.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# stream ids (one per purpose, so that changing one draw never shifts another)
+S_JITTER_X, S_JITTER_Y, S_PERM, S_WNOISE, S_SIZES, S_GRAD_S, S_GRAD_M, S_SAMPLE = range(1, 9)
+
+# seeds of the five standard workloads: 13053122 + workload number
+SEED_BASE = 13053122
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def stream_u64(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
+    """Values ``offset .. offset+n-1`` of the splitmix64 sequence of ``(seed, stream)``."""
+    with np.errstate(over="ignore"):
+        key = _mix(np.array([(seed * 0x100000001B3 + stream * 0x632BE59BD9B4E019) & (2**64 - 1)],
+                            dtype=np.uint64))[0]
+        ctr = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        return _mix(key + ctr * _GAMMA)
+
+
+def stream_uniform(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
+    """Uniform float64 in [0, 1) with 53 random bits."""
+    return (stream_u64(seed, stream, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def stream_normal(seed: int, stream: int, n: int) -> np.ndarray:
+    """Standard normal float64 by the Box-Muller transform on pairs of uniforms."""
+    m = (n + 1) // 2
+    u = stream_uniform(seed, stream, 2 * m)
+    u1 = 1.0 - u[0::2]                      # in (0, 1]
+    u2 = u[1::2]
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.empty(2 * m)
+    z[0::2] = r * np.cos(2.0 * math.pi * u2)
+    z[1::2] = r * np.sin(2.0 * math.pi * u2)
+    return z[:n]
+
+
+def random_permutation(seed: int, stream: int, n: int) -> np.ndarray:
+    """A uniformly random permutation of ``0..n-1`` (ranks of 64-bit random keys, ties by index)."""
+    keys = stream_u64(seed, stream, n)
+    order = np.argsort(keys, kind="stable")
+    rank = np.empty(n, dtype=np.int64)
+    rank[order] = np.arange(n, dtype=np.int64)
+    return rank
+
+
+@dataclass
+class Mesh:
+    q: np.ndarray      # [2, nq] float64
+    me: np.ndarray     # [3, nme] int32, 0-based, counter-clockwise
+    N: int             # cells per side
+
+    @property
+    def nq(self) -> int:
+        return self.q.shape[1]
+
+    @property
+    def nme(self) -> int:
+        return self.me.shape[1]
+
+
+def square_mesh(N: int, seed: int, jitter: float = 0.2, permute: bool = True) -> Mesh:
+    """Unit square cut into N x N cells, each cell split into two triangles.
+
+    Node (i, j) has id ``j*(N+1)+i`` at ``(i/N, j/N)`` before the permutation. Cell (i, j) with
+    corners a=(i,j), b=(i+1,j), c=(i+1,j+1), d=(i,j+1) gives triangles (a,b,c) and (a,c,d), both
+    counter-clockwise, numbered ``2*(j*N+i)`` and ``2*(j*N+i)+1`` (cell-major element order).
+    Interior nodes move by independent offsets drawn uniformly from [-jitter*h, jitter*h) in x
+    and in y (h = 1/N); boundary nodes stay put, so the domain stays the unit square. With
+    jitter <= 0.2 no triangle can invert. Then the node ids are randomly permuted (element order
+    and the local vertex order of each triangle are kept).
+    """
+    if N < 1:
+        raise ValueError("N must be >= 1")
+    n1 = N + 1
+    h = 1.0 / N
+    nq = n1 * n1
+    ii = np.tile(np.arange(n1), n1)
+    jj = np.repeat(np.arange(n1), n1)
+    x = ii * h
+    y = jj * h
+    interior = (ii > 0) & (ii < N) & (jj > 0) & (jj < N)
+    if jitter != 0.0:
+        jx = (2.0 * stream_uniform(seed, S_JITTER_X, nq) - 1.0) * (jitter * h)
+        jy = (2.0 * stream_uniform(seed, S_JITTER_Y, nq) - 1.0) * (jitter * h)
+        x = np.where(interior, x + jx, x)
+        y = np.where(interior, y + jy, y)
+    ci = np.tile(np.arange(N), N)
+    cj = np.repeat(np.arange(N), N)
+    a = cj * n1 + ci
+    b = a + 1
+    c = a + n1 + 1
+    d = a + n1
+    me = np.empty((3, 2 * N * N), dtype=np.int64)
+    me[0, 0::2], me[1, 0::2], me[2, 0::2] = a, b, c
+    me[0, 1::2], me[1, 1::2], me[2, 1::2] = a, c, d
+    q = np.stack([x, y]).astype(np.float64)
+    if permute:
+        newid = random_permutation(seed, S_PERM, nq)
+        qp = np.empty_like(q)
+        qp[:, newid] = q
+        q = qp
+        me = newid[me]
+    return Mesh(q=np.ascontiguousarray(q), me=np.ascontiguousarray(me.astype(np.int32)), N=N)
+
+
+def vertex_weights(mesh: Mesh, seed: int) -> np.ndarray:
+    """w_i = 1 + 0.5*sin(2*pi*x_i)*cos(2*pi*y_i) + U(0, 0.1), sampled at the (jittered) vertices."""
+    x, y = mesh.q
+    noise = 0.1 * stream_uniform(seed, S_WNOISE, mesh.nq)
+    return 1.0 + 0.5 * np.sin(2.0 * math.pi * x) * np.cos(2.0 * math.pi * y) + noise
+
+
+def batch_sizes(seed: int, count: int = 256, lo: int = 16, hi: int = 512) -> np.ndarray:
+    """Cells per side of each mesh of a batch: round(exp(U(ln lo, ln hi)))."""
+    u = stream_uniform(seed, S_SIZES, count)
+    n = np.rint(np.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))).astype(np.int64)
+    return np.clip(n, lo, hi)
+
+
+def batch_meshes(seed: int, count: int = 256, lo: int = 16, hi: int = 512) -> list[Mesh]:
+    """``count`` independent jittered, permuted meshes; mesh m uses seed*1000003 + m."""
+    return [square_mesh(int(n), seed * 1000003 + m) for m, n in enumerate(batch_sizes(seed, count, lo, hi))]
+
+
+def upstream_gradients(seed: int, nnz: int) -> tuple[np.ndarray, np.ndarray]:
+    """G_S, G_M ~ N(0, 1), one value per stored non-zero of S and of M^[w]."""
+    return stream_normal(seed, S_GRAD_S, nnz), stream_normal(seed, S_GRAD_M, nnz)
+
+
+def sample_indices(seed: int, count: int, upper: int) -> np.ndarray:
+    """``count`` indices drawn uniformly from [0, upper) (with replacement)."""
+    u = stream_u64(seed, S_SAMPLE, count)
+    return (u % np.uint64(upper)).astype(np.int64)
