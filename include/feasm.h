@@ -1,0 +1,231 @@
+/*
+ * feasm.h -- C ABI of the GB300 (sm_103a) P1 finite-element assembly library (libfeasm.so).
+ *
+ * The library computes, for a triangulation given by vertex coordinates q and connectivity me
+ * (Section 2 of Cuvelier, Japhet, Scarella, "An efficient way to perform the assembly of finite
+ * element matrices in Matlab and Octave", INRIA RR-8305), the global sparse matrices
+ *   M   mass              (element matrix Eq. 1)
+ *   M^w weighted mass     (element matrix Eq. 2, w given at the vertices)
+ *   S   stiffness         (element matrix Eq. 3)
+ *   K   plane elasticity  (element matrix |T| B^T C B of Section 6, Lame lambda, mu)
+ * by summing every element's contributions into CSR storage, which is what the paper does with
+ * sparse(Ig, Jg, Kg, n, n) (Sections 4-6). It also provides the adjoint of S and M^w with respect
+ * to q and w, and a batched form for many meshes.
+ *
+ * Conventions shared by every call
+ *   - Indices are 0-based (the paper is 1-based). Vertex ids and CSR indices are int32.
+ *   - q is [2][nq] row-major FP64: q[i] is x_i, q[nq + i] is y_i (the paper's q(1,i), q(2,i)).
+ *   - me is [3][nme] row-major int32: me[a*nme + k] is local vertex a of triangle k. Triangles
+ *     must be counter-clockwise with three distinct vertices.
+ *   - The area |T| is computed from the coordinates (half the cross product of two edge
+ *     vectors); it is not an input. Signed area <= 0 is an orientation error.
+ *   - Elasticity (dofs_per_vertex = 2) numbers the unknowns interleaved: vertex i owns rows
+ *     2i (x-displacement) and 2i+1 (y-displacement); the paper's 2i-1, 2i in 1-based terms.
+ *   - CSR output: row_ptr[n_rows+1], col_idx[nnz] strictly ascending inside each row. The
+ *     pattern is structural: (i, j) is stored iff i and j share a triangle, so a value that
+ *     sums to exactly 0.0 is still stored. All four matrices are symmetric, so these CSR arrays
+ *     are also the CSC arrays the paper describes in Section 3.
+ *   - Every call that takes a stream is stream-ordered and asynchronous, except where noted
+ *     ("synchronises"). Device pointers must be device-resident (cudaMalloc / torch CUDA
+ *     tensors) on the current device; FE_PTR_HOST inputs may be pageable or pinned host memory.
+ *   - Errors are returned as fe_status; nothing traps on the device. fe_last_error() gives a
+ *     human-readable message for the last failing call on the calling host thread.
+ *   - Handles own the device memory they allocate; output value buffers belong to the caller.
+ *   - Limits: nq < 2^31; 9*nme < 2^31 (36*nme < 2^31 for elasticity); nnz < 2^31; at most
+ *     FE_MAX_VALENCE triangles around one vertex.
+ */
+#ifndef FEASM_H
+#define FEASM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FE_OK = 0,
+    FE_ERR_INVALID_ARG = 1,      /* null pointer, negative size, bad flag or kind, lambda+mu <= 0 */
+    FE_ERR_INDEX_RANGE = 2,      /* a vertex id outside [0, nq) */
+    FE_ERR_DEGENERATE = 3,       /* a triangle with a repeated vertex */
+    FE_ERR_ORIENTATION = 4,      /* a triangle with signed area <= 0 (clockwise or flat) */
+    FE_ERR_BUFFER_TOO_SMALL = 5, /* output capacity below the pattern's nnz */
+    FE_ERR_OOM = 6,              /* a device allocation failed */
+    FE_ERR_CUDA = 7,             /* a CUDA runtime call failed (message has the CUDA error) */
+    FE_ERR_TIMEOUT = 8,          /* a bounded device-side wait ran out (none in this version) */
+    FE_ERR_LIMIT = 9             /* a size limit above is exceeded */
+} fe_status;
+
+#define FE_MAX_VALENCE 4096
+
+/* CUDA stream handle; identical to cudaStream_t (pass torch.cuda.Stream.cuda_stream). */
+typedef struct CUstream_st* fe_stream;
+
+typedef struct fe_mesh_s* fe_mesh;        /* owns device copies of q and me */
+typedef struct fe_pattern_s* fe_pattern;  /* owns the CSR structure and element-to-nnz map */
+typedef struct fe_batch_s* fe_batch;      /* a set of (mesh, pattern) assembled together */
+
+enum { FE_PTR_HOST = 0, FE_PTR_DEVICE = 1 };
+
+/* Scatter variants of the assembly calls. */
+enum {
+    FE_VARIANT_ATOMIC = 0, /* element-parallel; FP64 atomicAdd into values (zeroed first).
+                              Rounding of each sum depends on the order atomics land. */
+    FE_VARIANT_GATHER = 1  /* deterministic: element matrices are staged in contribution order
+                              c, then one thread per non-zero sums its contributions in
+                              ascending c (the order of the paper's sparse() call).
+                              Bit-identical from run to run. Needs FE_PATTERN_GATHER. */
+};
+
+/* Pattern build flags. */
+enum {
+    FE_PATTERN_DEFAULT = 0,
+    FE_PATTERN_GATHER = 1  /* also build the per-non-zero contribution lists (seg_ptr, perm)
+                              and the vertex-to-triangle lists used by FE_VARIANT_GATHER and
+                              by the deterministic adjoint */
+};
+
+/* ----------------------------------------------------------------------------- meshes ---- */
+
+/* Creates a mesh from q ([2][nq] FP64) and me ([3][nme] int32), both host (FE_PTR_HOST) or
+ * device (FE_PTR_DEVICE) memory; the library copies them (the caller keeps ownership of its
+ * arrays). Validates every triangle: ids in [0, nq) (else FE_ERR_INDEX_RANGE), three distinct
+ * vertices (FE_ERR_DEGENERATE), signed area > 0 (FE_ERR_ORIENTATION). Synchronises the stream
+ * once to read the validation result. nme = 0 is allowed (an empty mesh). Paper: Section 2
+ * (mesh arrays q, me; areas derived, see the header comment). */
+fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, const int32_t* me,
+                         int ptr_kind, fe_stream stream, fe_mesh* out);
+
+/* Replaces the coordinates (same topology), e.g. for finite differences or moving meshes.
+ * Asynchronous; does not re-validate orientation (assembly calls report it, see
+ * fe_mesh_check). */
+fe_status fe_mesh_set_coords(fe_mesh mesh, const double* q, int ptr_kind, fe_stream stream);
+
+/* Reads and clears the mesh's device-side error word, set by an assembly call that met a
+ * triangle with signed area <= 0 after fe_mesh_set_coords. Synchronises the stream.
+ * Returns FE_OK or FE_ERR_ORIENTATION. */
+fe_status fe_mesh_check(fe_mesh mesh, fe_stream stream);
+
+fe_status fe_mesh_info(fe_mesh mesh, int32_t* nq, int32_t* nme);
+void fe_mesh_destroy(fe_mesh mesh);
+
+/* -------------------------------------------------------------------------- patterns ---- */
+
+/* Builds the CSR structure of the global matrix and the element-to-nnz map: for a scalar
+ * pattern (dofs_per_vertex = 1) map[9k + 3*jl + il] is the position in col_idx of
+ * (me[il][k], me[jl][k]) -- the paper's Ig/Jg arrays of Section 5 (Remark 5.1) resolved once
+ * into storage positions, with c = 9k + 3*jl + il the column-wise element order of Section 4.
+ * For dofs_per_vertex = 2 the pattern is the 2x2 block expansion of the scalar one
+ * (BuildIgJgP1VF, Section 6.2). The structural half of sparse(): a counting sort of the
+ * (row, col) keys on the row, then a sort of the columns inside each row, then unique.
+ * flags: FE_PATTERN_DEFAULT or FE_PATTERN_GATHER. Synchronises the stream once (to learn nnz). */
+fe_status fe_pattern_build(fe_mesh mesh, int dofs_per_vertex, int flags, fe_stream stream,
+                           fe_pattern* out);
+
+/* Borrowed device pointers, valid until fe_pattern_destroy. */
+fe_status fe_pattern_info(fe_pattern pattern, int64_t* n_rows, int64_t* nnz,
+                          const int32_t** row_ptr, const int32_t** col_idx);
+
+/* The scalar element-to-nnz map (device, 9*nme int32, layout above). For a dofs=2 pattern this
+ * is the map of the underlying scalar pattern. */
+fe_status fe_pattern_map(fe_pattern pattern, const int32_t** map, int64_t* len);
+
+void fe_pattern_destroy(fe_pattern pattern);
+
+/* -------------------------------------------------------------------------- assembly ---- */
+
+/* Each call writes the nnz values of one matrix into values[0 .. nnz) (device, FP64,
+ * capacity cap >= nnz, else FE_ERR_BUFFER_TOO_SMALL), in the order of the pattern's col_idx.
+ * mesh and pattern must belong together (same mesh topology; FE_ERR_INVALID_ARG otherwise). */
+
+/* M, Eq. (1): M^e = |T|/12 [[2,1,1],[1,2,1],[1,1,2]]. Scalar pattern. */
+fe_status fe_assemble_mass(fe_mesh mesh, fe_pattern pattern, int variant, double* values,
+                           int64_t cap, fe_stream stream);
+
+/* M^w, Eq. (2), with w[nq] (device FP64) the values of w at the vertices. Scalar pattern. */
+fe_status fe_assemble_wmass(fe_mesh mesh, fe_pattern pattern, const double* w, int variant,
+                            double* values, int64_t cap, fe_stream stream);
+
+/* S, Eq. (3): S^e = Gram(u, v, w) / (4|T|), u = q2-q3, v = q3-q1, w = q1-q2. Scalar pattern. */
+fe_status fe_assemble_stiff(fe_mesh mesh, fe_pattern pattern, int variant, double* values,
+                            int64_t cap, fe_stream stream);
+
+/* S and M^w together in one pass over the triangles (they share the scalar pattern). */
+fe_status fe_assemble_stiff_wmass(fe_mesh mesh, fe_pattern pattern, const double* w,
+                                  int variant, double* S_values, double* Mw_values, int64_t cap,
+                                  fe_stream stream);
+
+/* K, Section 6: K^e = |T| B^T C B with C = [[l+2m, l, 0], [l, l+2m, 0], [0, 0, m]].
+ * Needs a dofs_per_vertex = 2 pattern; lambda + mu > 0 (Section 6) else FE_ERR_INVALID_ARG. */
+fe_status fe_assemble_elas(fe_mesh mesh, fe_pattern pattern, double lambda, double mu,
+                           int variant, double* values, int64_t cap, fe_stream stream);
+
+/* --------------------------------------------------------------------------- adjoint ---- */
+
+/* Gradient of L = sum_p gS[p] * S.values[p] + sum_p gM[p] * Mw.values[p] with respect to the
+ * coordinates and the vertex weights (not in the paper: the derivative of Eqs. 2-3 with the
+ * area taken from the coordinates). gS, gM: device FP64 [nnz] on the scalar pattern (either
+ * may be NULL for zero). Writes dq ([2][nq], same layout as q) and dw ([nq]); both are
+ * overwritten, not accumulated. variant FE_VARIANT_ATOMIC scatters per-vertex sums with
+ * atomics; FE_VARIANT_GATHER stages per-element terms and sums each vertex's triangles in
+ * ascending triangle order (bit-identical run to run, needs FE_PATTERN_GATHER). */
+fe_status fe_adjoint_stiff_wmass(fe_mesh mesh, fe_pattern pattern, const double* w,
+                                 const double* gS, const double* gM, int variant, double* dq,
+                                 double* dw, fe_stream stream);
+
+/* --------------------------------------------------------------------------- batches ---- */
+
+/* A batch assembles S and M (the mass matrix of Eq. 1) for n independent meshes in one
+ * persistent kernel launch, replayed from a captured CUDA graph. meshes[m] / patterns[m] are
+ * borrowed (they must outlive the batch); patterns are scalar. The tile size and block size
+ * come from fe_batch_tune (or defaults). Not in the paper. */
+fe_status fe_batch_create(int32_t n, const fe_mesh* meshes, const fe_pattern* patterns,
+                          fe_batch* out);
+
+/* Times candidate launch shapes (block size x triangles per tile) on this batch with the
+ * given output buffers and keeps the fastest; writes the choice to *block and *tile if not
+ * NULL. Synchronises. */
+fe_status fe_batch_tune(fe_batch batch, double* const* S_values, double* const* M_values,
+                        fe_stream stream, int32_t* block, int32_t* tile);
+
+/* Sets the launch shape explicitly (block in {64..1024}, tile >= 1 triangles). */
+fe_status fe_batch_set_shape(fe_batch batch, int32_t block, int32_t tile);
+
+/* S_values[m], M_values[m]: device FP64 outputs of mesh m (capacity = that pattern's nnz).
+ * The first call with a given set of output pointers captures a CUDA graph (memsets + one
+ * persistent kernel); later calls with the same pointers replay it. */
+fe_status fe_batch_assemble_stiff_mass(fe_batch batch, double* const* S_values,
+                                       double* const* M_values, fe_stream stream);
+
+/* The same work as n separate plain launches (one memset pair + one kernel per mesh), for
+ * comparison with the batched launch. */
+fe_status fe_batch_assemble_stiff_mass_plain(fe_batch batch, double* const* S_values,
+                                             double* const* M_values, fe_stream stream);
+
+void fe_batch_destroy(fe_batch batch);
+
+/* --------------------------------------------------------------------- kernel timing ---- */
+
+/* Opt-in timing of the library's own kernels (measurement support; not in the paper). While
+ * on, every kernel launch is bracketed by two CUDA events recorded on its launch stream
+ * (skipped while that stream is being captured into a graph). fe_profile_read resolves the
+ * pending events (it waits for them) and returns per kernel name the summed device time in
+ * milliseconds and the number of launches: names is a caller array of max_entries x 64 chars,
+ * total_ms and launches have max_entries elements (any of the three may be NULL); *count gets
+ * the number of distinct kernels seen, which may exceed max_entries. fe_profile_reset drops
+ * all totals. Thread-safe; process-wide. */
+fe_status fe_profile_enable(int on);
+fe_status fe_profile_reset(void);
+fe_status fe_profile_read(int32_t max_entries, char* names, double* total_ms, int64_t* launches,
+                          int32_t* count);
+
+/* ---------------------------------------------------------------------------- status ---- */
+
+const char* fe_status_string(fe_status status);
+const char* fe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEASM_H */

@@ -1,0 +1,286 @@
+// batch.cu -- many independent meshes assembled in one persistent launch under a CUDA graph.
+//
+// Not in the paper. A batch concatenates the triangles of its meshes into a list of tiles
+// (mesh, first triangle, last triangle). One zeroing kernel clears every output and one
+// persistent kernel (grid = SMs x resident blocks) walks the tile list round-robin, computing
+// the stiffness S (Eq. 3) and mass M (Eq. 1) of each triangle and adding them into its mesh's
+// CSR values with FP64 atomics. The two kernels are captured once in a CUDA graph and replayed;
+// outputs are read from device pointer tables, so changing the output buffers only rewrites
+// the tables. fe_batch_tune times a small grid of (block size, tile size) shapes and keeps the
+// fastest.
+#include <string.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+struct MeshDesc {
+    const double2* q;
+    const int32_t* me;
+    const int32_t* map;
+    int32_t nme;
+    int32_t nnz;
+};
+
+struct Tile {
+    int32_t mesh, k0, k1;
+};
+
+struct fe_batch_s {
+    int32_t n = 0;
+    std::vector<fe_mesh> meshes;
+    std::vector<fe_pattern> patterns;
+    MeshDesc* d_desc = nullptr;
+    double** d_S = nullptr;   // [n] output pointers
+    double** d_M = nullptr;
+    double** h_ptrs = nullptr;   // pinned staging: S pointers then M pointers
+    std::vector<double*> cur_S, cur_M;
+    Tile* d_tiles = nullptr;
+    int32_t ntiles = 0;
+    int32_t block = 256, tile = 1024;
+    int64_t total_nnz = 0, total_nme = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cap_stream = nullptr;
+};
+
+// One warp per mesh-chunk: zero all outputs.
+__global__ void k_batch_zero(const MeshDesc* __restrict__ desc, int32_t n, double* const* __restrict__ S,
+                             double* const* __restrict__ M) {
+    for (int32_t m = blockIdx.x; m < n; m += gridDim.x) {
+        int32_t nnz = desc[m].nnz;
+        double* s = S[m];
+        double* mm = M[m];
+        for (int32_t i = threadIdx.x; i < nnz; i += blockDim.x) {
+            s[i] = 0.0;
+            mm[i] = 0.0;
+        }
+    }
+}
+
+__device__ __forceinline__ void tri_stiff_mass(const double2* __restrict__ q, const int32_t* __restrict__ me,
+                                               int32_t nme, int32_t k, const int32_t* __restrict__ mk,
+                                               double* __restrict__ S, double* __restrict__ M) {
+    int32_t v0 = me[k], v1 = me[nme + k], v2 = me[2 * nme + k];
+    double2 p0 = q[v0], p1 = q[v1], p2 = q[v2];
+    double ex[3] = {p1.x - p2.x, p2.x - p0.x, p0.x - p1.x};
+    double ey[3] = {p1.y - p2.y, p2.y - p0.y, p0.y - p1.y};
+    double D = ex[1] * ey[2] - ex[2] * ey[1];
+    double inv = 1.0 / (2.0 * D);
+    double dia = D / 12.0, off = D / 24.0;
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            int32_t p = mk[3 * b + a];
+            atomicAdd(&S[p], (ex[a] * ex[b] + ey[a] * ey[b]) * inv);
+            atomicAdd(&M[p], a == b ? dia : off);
+        }
+}
+
+__global__ void k_batch_asm(const MeshDesc* __restrict__ desc, const Tile* __restrict__ tiles, int32_t ntiles,
+                            double* const* __restrict__ S, double* const* __restrict__ M) {
+    for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        Tile tl = tiles[t];
+        MeshDesc d = desc[tl.mesh];
+        double* s = S[tl.mesh];
+        double* mm = M[tl.mesh];
+        for (int32_t k = tl.k0 + threadIdx.x; k < tl.k1; k += blockDim.x)
+            tri_stiff_mass(d.q, d.me, d.nme, k, d.map + 9 * (int64_t)k, s, mm);
+    }
+}
+
+// Plain form: one kernel per mesh.
+__global__ void k_mesh_asm(MeshDesc d, double* __restrict__ S, double* __restrict__ M) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < d.nme; k += gridDim.x * blockDim.x)
+        tri_stiff_mass(d.q, d.me, d.nme, k, d.map + 9 * (int64_t)k, S, M);
+}
+
+static void drop_graph(fe_batch b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+static int resident_blocks(int block) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_asm, block, 0);
+    return per_sm > 0 ? per_sm : 1;
+}
+
+static fe_status make_tiles(fe_batch b) {
+    std::vector<Tile> tiles;
+    for (int32_t m = 0; m < b->n; m++)
+        for (int32_t k = 0; k < b->meshes[m]->nme; k += b->tile) {
+            int32_t e = k + b->tile < b->meshes[m]->nme ? k + b->tile : b->meshes[m]->nme;
+            tiles.push_back({m, k, e});
+        }
+    fe_free(b->d_tiles);
+    b->d_tiles = nullptr;
+    b->ntiles = (int32_t)tiles.size();
+    fe_status st = fe_alloc_n(&b->d_tiles, tiles.size(), "batch tiles");
+    if (st) return st;
+    if (!tiles.empty()) FE_CUDA(cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    return FE_OK;
+}
+
+static void launch_batch(fe_batch b, cudaStream_t s) {
+    unsigned zgrid = (unsigned)(b->n < 4 * fe_sm_count() ? (b->n > 0 ? b->n : 1) : 4 * fe_sm_count());
+    { FE_PROF("k_batch_zero", s); k_batch_zero<<<zgrid, 256, 0, s>>>(b->d_desc, b->n, b->d_S, b->d_M); }
+    int64_t want = (int64_t)fe_sm_count() * resident_blocks(b->block);
+    unsigned grid = (unsigned)(b->ntiles < want ? (b->ntiles > 0 ? b->ntiles : 1) : want);
+    { FE_PROF("k_batch_asm", s); k_batch_asm<<<grid, b->block, 0, s>>>(b->d_desc, b->d_tiles, b->ntiles, b->d_S, b->d_M); }
+}
+
+static fe_status capture(fe_batch b) {
+    drop_graph(b);
+    FE_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    launch_batch(b, b->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &b->graph);
+    if (e != cudaSuccess) return fe_cuda_fail(e, "graph capture");
+    FE_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    return FE_OK;
+}
+
+// Copies the output pointer tables to the device if they changed (stream-ordered).
+static fe_status set_outputs(fe_batch b, double* const* S, double* const* M, cudaStream_t s) {
+    if (!S || !M) return fe_fail(FE_ERR_INVALID_ARG, "null output table");
+    for (int32_t m = 0; m < b->n; m++)
+        if ((!S[m] || !M[m]) && b->patterns[m]->nnz > 0) return fe_fail(FE_ERR_INVALID_ARG, "null output buffer in batch");
+    bool same = !b->cur_S.empty();
+    for (int32_t m = 0; same && m < b->n; m++) same = b->cur_S[m] == S[m] && b->cur_M[m] == M[m];
+    if (same) return FE_OK;
+    // the previous copy from the pinned staging area must be finished before it is rewritten
+    FE_CUDA(cudaStreamSynchronize(s));
+    b->cur_S.assign(S, S + b->n);
+    b->cur_M.assign(M, M + b->n);
+    memcpy(b->h_ptrs, S, sizeof(double*) * b->n);
+    memcpy(b->h_ptrs + b->n, M, sizeof(double*) * b->n);
+    FE_CUDA(cudaMemcpyAsync(b->d_S, b->h_ptrs, sizeof(double*) * 2 * b->n, cudaMemcpyHostToDevice, s));
+    return FE_OK;
+}
+
+extern "C" void fe_batch_destroy(fe_batch b) {
+    if (!b) return;
+    drop_graph(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    fe_free(b->d_desc);
+    fe_free(b->d_S);
+    fe_free(b->d_tiles);
+    if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
+    delete b;
+}
+
+extern "C" fe_status fe_batch_create(int32_t n, const fe_mesh* meshes, const fe_pattern* patterns, fe_batch* out) {
+    if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (n < 0 || (n > 0 && (!meshes || !patterns))) return fe_fail(FE_ERR_INVALID_ARG, "bad mesh list");
+    std::vector<MeshDesc> desc(n > 0 ? n : 1);
+    fe_batch b = new fe_batch_s();
+    b->n = n;
+    for (int32_t m = 0; m < n; m++) {
+        fe_status st = fe_check_pair(meshes[m], patterns[m], 1);
+        if (st) { fe_batch_destroy(b); return st; }
+        b->meshes.push_back(meshes[m]);
+        b->patterns.push_back(patterns[m]);
+        desc[m] = {meshes[m]->q, meshes[m]->me, patterns[m]->map, meshes[m]->nme, (int32_t)patterns[m]->nnz};
+        b->total_nnz += patterns[m]->nnz;
+        b->total_nme += meshes[m]->nme;
+    }
+    fe_status st = fe_alloc_n(&b->d_desc, desc.size(), "batch descriptors");
+    if (!st) st = fe_alloc_n(&b->d_S, 2 * (size_t)(n > 0 ? n : 1), "batch output tables");
+    if (st) { fe_batch_destroy(b); return st; }
+    b->d_M = b->d_S + n;
+    cudaError_t e = cudaMemcpy(b->d_desc, desc.data(), sizeof(MeshDesc) * desc.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_ptrs, sizeof(double*) * 2 * (n > 0 ? n : 1));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { fe_batch_destroy(b); return fe_cuda_fail(e, "batch setup"); }
+    st = make_tiles(b);
+    if (!st) st = capture(b);
+    if (st) { fe_batch_destroy(b); return st; }
+    *out = b;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_batch_set_shape(fe_batch b, int32_t block, int32_t tile) {
+    if (!b) return fe_fail(FE_ERR_INVALID_ARG, "null batch");
+    if (block < 64 || block > 1024 || block % 32 || tile < 1) return fe_fail(FE_ERR_INVALID_ARG, "bad batch shape");
+    if (block == b->block && tile == b->tile) return FE_OK;
+    FE_CUDA(cudaDeviceSynchronize());   // the graph may be in flight
+    b->block = block;
+    b->tile = tile;
+    fe_status st = make_tiles(b);
+    if (!st) st = capture(b);
+    return st;
+}
+
+extern "C" fe_status fe_batch_assemble_stiff_mass(fe_batch b, double* const* S, double* const* M, fe_stream stream) {
+    if (!b) return fe_fail(FE_ERR_INVALID_ARG, "null batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    fe_status st = set_outputs(b, S, M, s);
+    if (st) return st;
+    if (b->n == 0) return FE_OK;
+    FE_CUDA(cudaGraphLaunch(b->exec, s));
+    return FE_OK;
+}
+
+extern "C" fe_status fe_batch_assemble_stiff_mass_plain(fe_batch b, double* const* S, double* const* M, fe_stream stream) {
+    if (!b) return fe_fail(FE_ERR_INVALID_ARG, "null batch");
+    if (!S || !M) return fe_fail(FE_ERR_INVALID_ARG, "null output table");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int32_t m = 0; m < b->n; m++) {
+        fe_mesh me = b->meshes[m];
+        fe_pattern p = b->patterns[m];
+        if (p->nnz > 0) {
+            if (!S[m] || !M[m]) return fe_fail(FE_ERR_INVALID_ARG, "null output buffer in batch");
+            FE_CUDA(cudaMemsetAsync(S[m], 0, sizeof(double) * p->nnz, s));
+            FE_CUDA(cudaMemsetAsync(M[m], 0, sizeof(double) * p->nnz, s));
+        }
+        if (me->nme == 0) continue;
+        MeshDesc d = {me->q, me->me, p->map, me->nme, (int32_t)p->nnz};
+        { FE_PROF("k_mesh_asm", s); k_mesh_asm<<<fe_grid(me->nme, 256), 256, 0, s>>>(d, S[m], M[m]); }
+        FE_LAUNCHED("k_mesh_asm");
+    }
+    return FE_OK;
+}
+
+extern "C" fe_status fe_batch_tune(fe_batch b, double* const* S, double* const* M, fe_stream stream, int32_t* block_out,
+                                   int32_t* tile_out) {
+    if (!b) return fe_fail(FE_ERR_INVALID_ARG, "null batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    fe_status st = set_outputs(b, S, M, s);
+    if (st) return st;
+    const int blocks[] = {128, 256, 512};
+    const int tiles[] = {256, 1024, 4096};
+    cudaEvent_t e0, e1;
+    FE_CUDA(cudaEventCreate(&e0));
+    FE_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bb = b->block, bt = b->tile;
+    for (int blk : blocks)
+        for (int tl : tiles) {
+            b->block = blk;
+            b->tile = tl;
+            if ((st = make_tiles(b))) break;
+            for (int w = 0; w < 2; w++) launch_batch(b, s);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 5; r++) launch_batch(b, s);
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { st = fe_cuda_fail(e, "batch tuning"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; bb = blk; bt = tl; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    b->block = bb;
+    b->tile = bt;
+    if ((st = make_tiles(b))) return st;
+    if ((st = capture(b))) return st;
+    if (block_out) *block_out = bb;
+    if (tile_out) *tile_out = bt;
+    return FE_OK;
+}

@@ -1,0 +1,109 @@
+// internal.cuh -- shared declarations of the CUDA library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/feasm.h"
+
+// ------------------------------------------------------------------------ handles
+
+struct fe_mesh_s {
+    int32_t nq = 0, nme = 0;
+    double2* q = nullptr;       // [nq] (x, y) pairs: one 16-byte load per vertex gather
+    int32_t* me = nullptr;      // [3][nme], the caller's layout
+    int* err = nullptr;         // device error word: bit 0 = a triangle with signed area <= 0
+    uint64_t topology_id = 0;   // identifies the connectivity (patterns remember it)
+};
+
+struct fe_pattern_s {
+    int dofs = 1;
+    int flags = 0;
+    int32_t nq = 0, nme = 0;
+    uint64_t topology_id = 0;
+    int64_t n_rows = 0, nnz = 0;          // of the returned (possibly block-expanded) matrix
+    int64_t nnz_scalar = 0;
+    // scalar pattern (always)
+    int32_t* row_ptr = nullptr;           // [nq + 1]
+    int32_t* col_idx = nullptr;           // [nnz_scalar]
+    int32_t* map = nullptr;               // [9 nme]: map[9k + 3 jl + il] = position of (me[il][k], me[jl][k])
+    // block-expanded pattern (dofs == 2)
+    int32_t* row_ptr2 = nullptr;          // [2 nq + 1]
+    int32_t* col_idx2 = nullptr;          // [4 nnz_scalar]
+    // FE_PATTERN_GATHER
+    int32_t* seg_ptr = nullptr;           // [nnz_scalar + 1] into perm
+    int32_t* perm = nullptr;              // [9 nme] contribution ids c, grouped by non-zero, ascending c
+    int32_t* vptr = nullptr;              // [nq + 1] vertex -> triangle lists
+    int32_t* vel = nullptr;               // [3 nme] entries 3k + a (triangle k, local vertex a), ascending k
+    double* kg = nullptr;                 // staging of element values: 2 x 9 nme (dofs 1) or 36 nme (dofs 2)
+};
+
+struct fe_batch_s;   // batch.cu
+
+// ------------------------------------------------------------------------ errors
+
+fe_status fe_fail(fe_status st, const std::string& msg);
+fe_status fe_cuda_fail(cudaError_t e, const char* what);
+
+#define FE_CUDA(call)                                                     \
+    do {                                                                  \
+        cudaError_t fe_e_ = (call);                                       \
+        if (fe_e_ != cudaSuccess) return fe_cuda_fail(fe_e_, #call);      \
+    } while (0)
+
+#define FE_LAUNCHED(name)                                                 \
+    do {                                                                  \
+        cudaError_t fe_e_ = cudaGetLastError();                           \
+        if (fe_e_ != cudaSuccess) return fe_cuda_fail(fe_e_, name);       \
+    } while (0)
+
+// Device allocation helpers; return FE_ERR_OOM with a message on failure.
+fe_status fe_alloc(void** p, size_t bytes, const char* what);
+template <typename T>
+inline fe_status fe_alloc_n(T** p, size_t n, const char* what) {
+    return fe_alloc(reinterpret_cast<void**>(p), n * sizeof(T) + (n == 0 ? sizeof(T) : 0), what);
+}
+void fe_free(void* p);
+
+// ------------------------------------------------------------------------ launch shapes
+
+int fe_sm_count();
+inline unsigned fe_grid(int64_t n, int block, int per_sm = 8) {
+    int64_t need = (n + block - 1) / block;
+    int64_t cap = (int64_t)fe_sm_count() * per_sm;
+    if (need < 1) need = 1;
+    return (unsigned)(need < cap ? need : cap);
+}
+
+// ------------------------------------------------------------------------ scan
+
+// Exclusive prefix sum of in[0..n) into out[0..n], out[n] = total. int32 in, int32 out.
+// Returns FE_ERR_LIMIT if the total does not fit in int32. Synchronises only if total_out
+// is not null (it then reads the total back).
+fe_status fe_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s,
+                            int64_t* total_out);
+
+// ------------------------------------------------------------------------ checks shared by calls
+
+fe_status fe_check_pair(fe_mesh mesh, fe_pattern pat, int dofs);
+
+// ------------------------------------------------------------------------ kernel timing
+
+// Scope guard: records a CUDA event pair around the launches in its scope when profiling is
+// enabled (fe_profile_enable), attributed to `name` (a string literal).
+class FeProf {
+  public:
+    FeProf(const char* name, cudaStream_t s);
+    ~FeProf();
+    FeProf(const FeProf&) = delete;
+    FeProf& operator=(const FeProf&) = delete;
+
+  private:
+    const char* name_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr;
+};
+
+#define FE_PROF(name, stream) FeProf fe_prof_guard_(name, stream)

@@ -1,0 +1,152 @@
+// mesh.cu -- mesh handles: device copies of q and me, and validation of every triangle.
+//
+// Section 2 of the paper describes a mesh by q (vertex coordinates) and me (connectivity).
+// The library keeps q as (x, y) pairs so that a vertex gather is one 16-byte load, and me in
+// the caller's [3][nme] layout (coalesced per local vertex).
+#include <atomic>
+
+#include "internal.cuh"
+
+static std::atomic<uint64_t> g_topology_counter{1};
+
+// q [2][nq] (x row, y row) -> q2 [nq] (x, y)
+__global__ void k_pack_coords(const double* __restrict__ q, int32_t nq, double2* __restrict__ q2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x)
+        q2[i] = make_double2(q[i], q[nq + i]);
+}
+
+// Validation word layout: [0] = OR of error bits, [1] = first bad triangle (min), per kind.
+enum { BAD_RANGE = 1, BAD_REPEAT = 2, BAD_ORIENT = 4 };
+
+__global__ void k_validate(const double2* __restrict__ q, int32_t nq, const int32_t* __restrict__ me,
+                           int32_t nme, int* __restrict__ word) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v0 = me[k], v1 = me[nme + k], v2 = me[2 * (int64_t)nme + k];
+        int bad = 0;
+        if (v0 < 0 || v0 >= nq || v1 < 0 || v1 >= nq || v2 < 0 || v2 >= nq) {
+            bad = BAD_RANGE;
+        } else if (v0 == v1 || v1 == v2 || v0 == v2) {
+            bad = BAD_REPEAT;
+        } else {
+            double2 p0 = q[v0], p1 = q[v1], p2 = q[v2];
+            // twice the signed area from the edge vectors v = p2 - p0 and w = p0 - p1
+            double vx = p2.x - p0.x, vy = p2.y - p0.y, wx = p0.x - p1.x, wy = p0.y - p1.y;
+            double D = vx * wy - wx * vy;
+            if (!(D > 0.0)) bad = BAD_ORIENT;
+        }
+        if (bad) {
+            atomicOr(&word[0], bad);
+            int slot = bad == BAD_RANGE ? 1 : bad == BAD_REPEAT ? 2 : 3;
+            atomicMin(&word[slot], (int)k);
+        }
+    }
+}
+
+static fe_status copy_in(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_t s) {
+    if (bytes == 0) return FE_OK;
+    FE_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                            ptr_kind == FE_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    return FE_OK;
+}
+
+static fe_status set_coords(fe_mesh m, const double* q, int ptr_kind, cudaStream_t s) {
+    if (m->nq == 0) return FE_OK;
+    const double* qd = q;
+    double* tmp = nullptr;
+    if (ptr_kind == FE_PTR_HOST) {
+        fe_status st = fe_alloc_n(&tmp, 2 * (size_t)m->nq, "coordinate staging");
+        if (st) return st;
+        st = copy_in(tmp, q, 2 * (size_t)m->nq * sizeof(double), ptr_kind, s);
+        if (st) { fe_free(tmp); return st; }
+        qd = tmp;
+    }
+    { FE_PROF("k_pack_coords", s); k_pack_coords<<<fe_grid(m->nq, 256), 256, 0, s>>>(qd, m->nq, m->q); }
+    cudaError_t e = cudaGetLastError();
+    if (tmp) {
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        fe_free(tmp);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e != cudaSuccess) return fe_cuda_fail(e, "k_pack_coords");
+    return FE_OK;
+}
+
+extern "C" void fe_mesh_destroy(fe_mesh m) {
+    if (!m) return;
+    fe_free(m->q);
+    fe_free(m->me);
+    fe_free(m->err);
+    delete m;
+}
+
+extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, const int32_t* me,
+                                    int ptr_kind, fe_stream stream, fe_mesh* out) {
+    if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (nq < 0 || nme < 0) return fe_fail(FE_ERR_INVALID_ARG, "nq and nme must be >= 0");
+    if ((nq > 0 && !q) || (nme > 0 && !me)) return fe_fail(FE_ERR_INVALID_ARG, "q or me is null");
+    if (ptr_kind != FE_PTR_HOST && ptr_kind != FE_PTR_DEVICE) return fe_fail(FE_ERR_INVALID_ARG, "bad ptr_kind");
+    if ((int64_t)nme * 36 >= INT32_MAX && (int64_t)nme * 9 >= INT32_MAX)
+        return fe_fail(FE_ERR_LIMIT, "9*nme must be < 2^31");
+    cudaStream_t s = (cudaStream_t)stream;
+    fe_mesh m = new fe_mesh_s();
+    m->nq = nq;
+    m->nme = nme;
+    m->topology_id = g_topology_counter.fetch_add(1);
+    fe_status st = fe_alloc_n(&m->q, (size_t)nq, "mesh coordinates");
+    if (!st) st = fe_alloc_n(&m->me, 3 * (size_t)nme, "mesh connectivity");
+    if (!st) st = fe_alloc_n(&m->err, 4, "mesh error word");
+    if (!st) st = copy_in(m->me, me, 3 * (size_t)nme * sizeof(int32_t), ptr_kind, s);
+    if (!st) st = set_coords(m, q, ptr_kind, s);
+    if (st) { fe_mesh_destroy(m); return st; }
+    int init[4] = {0, INT32_MAX, INT32_MAX, INT32_MAX};
+    int word[4];
+    cudaError_t e = cudaMemcpyAsync(m->err, init, sizeof init, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nme > 0) {
+        { FE_PROF("k_validate", s); k_validate<<<fe_grid(nme, 256), 256, 0, s>>>(m->q, nq, m->me, nme, m->err); }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(word, m->err, sizeof word, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->err, 0, sizeof(int) * 4, s);
+    if (e != cudaSuccess) { fe_mesh_destroy(m); return fe_cuda_fail(e, "mesh validation"); }
+    if (word[0] & BAD_RANGE) {
+        fe_mesh_destroy(m);
+        return fe_fail(FE_ERR_INDEX_RANGE, "triangle " + std::to_string(word[1]) + " has a vertex id outside [0, nq)");
+    }
+    if (word[0] & BAD_REPEAT) {
+        fe_mesh_destroy(m);
+        return fe_fail(FE_ERR_DEGENERATE, "triangle " + std::to_string(word[2]) + " repeats a vertex");
+    }
+    if (word[0] & BAD_ORIENT) {
+        fe_mesh_destroy(m);
+        return fe_fail(FE_ERR_ORIENTATION, "triangle " + std::to_string(word[3]) +
+                                               " has signed area <= 0 (must be counter-clockwise)");
+    }
+    *out = m;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_mesh_set_coords(fe_mesh m, const double* q, int ptr_kind, fe_stream stream) {
+    if (!m || (m->nq > 0 && !q)) return fe_fail(FE_ERR_INVALID_ARG, "null mesh or q");
+    if (ptr_kind != FE_PTR_HOST && ptr_kind != FE_PTR_DEVICE) return fe_fail(FE_ERR_INVALID_ARG, "bad ptr_kind");
+    return set_coords(m, q, ptr_kind, (cudaStream_t)stream);
+}
+
+extern "C" fe_status fe_mesh_check(fe_mesh m, fe_stream stream) {
+    if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");
+    cudaStream_t s = (cudaStream_t)stream;
+    int word = 0;
+    FE_CUDA(cudaMemcpyAsync(&word, m->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    FE_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int), s));
+    if (word) return fe_fail(FE_ERR_ORIENTATION, "an assembly call met a triangle with signed area <= 0");
+    return FE_OK;
+}
+
+extern "C" fe_status fe_mesh_info(fe_mesh m, int32_t* nq, int32_t* nme) {
+    if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");
+    if (nq) *nq = m->nq;
+    if (nme) *nme = m->nme;
+    return FE_OK;
+}

@@ -1,0 +1,454 @@
+// pattern.cu -- the structural half of sparse(Ig, Jg, Kg): CSR structure + element-to-nnz map.
+//
+// The paper forms Ig = me([1 2 3 1 2 3 1 2 3], :) and Jg = me([1 1 1 2 2 2 3 3 3], :)
+// (Section 5, Remark 5.1) and lets sparse() sort the 9*nme (row, col) keys and merge equal
+// ones (Section 4). Here the keys are sorted by a two-level (most-significant-digit first)
+// radix sort that exploits their shape: the row digit is a counting sort (each triangle drops
+// its two other vertices into the bucket of each of its vertices), and the column digit is
+// sorted inside each row bucket, where a row holds only 2*valence+1 keys. Unique keys give
+// row_ptr / col_idx; each triangle then resolves its 9 keys to storage positions once (map),
+// so an assembly call never sorts.
+//
+// Row buckets with more than FAST_DEG triangles (rare: high-valence vertices) are handled by
+// one thread block per row in shared memory.
+#include <string>
+
+#include "internal.cuh"
+
+static constexpr int FAST_DEG = 32;
+static constexpr int BIG_BLOCK = 256;
+
+__global__ void k_count_deg(const int32_t* __restrict__ me, int64_t n3, int32_t* __restrict__ deg) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n3; t += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&deg[me[t]], 1);
+}
+
+// Bucket entry for vertex v of triangle k at local index a: the two other vertices, and
+// (optionally) the triangle/local id 3k + a.
+__global__ void k_fill_adj(const int32_t* __restrict__ me, int32_t nme, const int32_t* __restrict__ vptr,
+                           int32_t* __restrict__ cur, int2* __restrict__ adj, int32_t* __restrict__ vel) {
+    int64_t n3 = 3 * (int64_t)nme;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n3; t += (int64_t)gridDim.x * blockDim.x) {
+        int a = (int)(t / nme);
+        int32_t k = (int32_t)(t - (int64_t)a * nme);
+        int32_t v = me[t];
+        int a1 = a == 2 ? 0 : a + 1, a2 = a == 0 ? 2 : a - 1;
+        int32_t slot = vptr[v] + atomicAdd(&cur[v], 1);
+        adj[slot] = make_int2(me[(int64_t)a1 * nme + k], me[(int64_t)a2 * nme + k]);
+        if (vel) vel[slot] = 3 * k + a;
+    }
+}
+
+__device__ __forceinline__ void isort32(int32_t* x, int n) {
+    for (int i = 1; i < n; i++) {
+        int32_t v = x[i];
+        int j = i - 1;
+        while (j >= 0 && x[j] > v) { x[j + 1] = x[j]; j--; }
+        x[j + 1] = v;
+    }
+}
+
+__device__ __forceinline__ void isort64(long long* x, int n) {
+    for (int i = 1; i < n; i++) {
+        long long v = x[i];
+        int j = i - 1;
+        while (j >= 0 && x[j] > v) { x[j + 1] = x[j]; j--; }
+        x[j + 1] = v;
+    }
+}
+
+// Sorted unique columns of row i into cols; returns their number.
+__device__ __forceinline__ int row_columns(int32_t i, int32_t beg, int32_t d, const int2* __restrict__ adj,
+                                           int32_t* cols) {
+    if (d == 0) return 0;   // a vertex in no triangle has an empty row
+    int n = 0;
+    cols[n++] = i;
+    for (int32_t s = 0; s < d; s++) {
+        int2 p = adj[beg + s];
+        cols[n++] = p.x;
+        cols[n++] = p.y;
+    }
+    isort32(cols, n);
+    int u = 0;
+    for (int t = 0; t < n; t++)
+        if (t == 0 || cols[t] != cols[t - 1]) cols[u++] = cols[t];
+    return u;
+}
+
+__global__ void k_row_count(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t nq,
+                            int32_t* __restrict__ row_nnz, int32_t* __restrict__ big_list,
+                            int32_t* __restrict__ big_count, int* __restrict__ too_big) {
+    int32_t cols[2 * FAST_DEG + 1];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = (int32_t)r;
+        int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+        if (d > FAST_DEG) {
+            if (d > FE_MAX_VALENCE) { *too_big = 1; row_nnz[i] = 0; continue; }
+            big_list[atomicAdd(big_count, 1)] = i;
+            continue;
+        }
+        row_nnz[i] = row_columns(i, beg, d, adj, cols);
+    }
+}
+
+// One block per high-valence row: the 2d+1 columns go to shared memory; pass 1 flags the
+// first occurrence of each value, pass 2 places each first occurrence at its rank among the
+// distinct values (O(n^2) work per row, shared among the block's threads).
+__global__ void k_row_big(const int32_t* __restrict__ big_list, const int32_t* __restrict__ vptr,
+                          const int2* __restrict__ adj, const int32_t* __restrict__ row_ptr,
+                          int32_t* __restrict__ row_nnz, int32_t* __restrict__ col_idx) {
+    extern __shared__ int32_t sm[];
+    __shared__ int cnt;
+    int32_t i = big_list[blockIdx.x];
+    int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+    int n = 2 * d + 1;
+    unsigned char* first = reinterpret_cast<unsigned char*>(sm + n);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int32_t v;
+        if (t == 0) v = i;
+        else { int2 p = adj[beg + (t - 1) / 2]; v = ((t - 1) & 1) ? p.y : p.x; }
+        sm[t] = v;
+    }
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int32_t v = sm[t];
+        unsigned char f = 1;
+        for (int u = 0; u < t; u++) if (sm[u] == v) { f = 0; break; }
+        first[t] = f;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        if (!first[t]) continue;
+        int32_t v = sm[t];
+        int less = 0;
+        for (int u = 0; u < n; u++) less += (first[u] && sm[u] < v);
+        atomicAdd(&cnt, 1);
+        if (col_idx) col_idx[row_ptr[i] + less] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && row_nnz) row_nnz[i] = cnt;
+}
+
+// Contribution keys of row i: (col << 32 | c) for each of the 3 local columns of each triangle
+// containing i, where c = 9k + 3*b + a (a = local index of i, b = local index of the column).
+__device__ __forceinline__ void contrib_key(int32_t i, int2 p, int32_t e, long long out[3]) {
+    int32_t k = e / 3;
+    int a = e - 3 * k;
+    int a1 = a == 2 ? 0 : a + 1, a2 = a == 0 ? 2 : a - 1;
+    long long base = 9LL * k + a;
+    out[0] = ((long long)i << 32) | (base + 3 * a);
+    out[1] = ((long long)p.x << 32) | (base + 3 * a1);
+    out[2] = ((long long)p.y << 32) | (base + 3 * a2);
+}
+
+__global__ void k_row_fill(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t* __restrict__ vel,
+                           int32_t nq, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx,
+                           int32_t* __restrict__ seg_ptr, int32_t* __restrict__ perm) {
+    int32_t cols[2 * FAST_DEG + 1];
+    long long keys[3 * FAST_DEG];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = (int32_t)r;
+        int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+        if (d > FAST_DEG) continue;
+        int u = row_columns(i, beg, d, adj, cols);
+        int32_t o = row_ptr[i];
+        for (int t = 0; t < u; t++) col_idx[o + t] = cols[t];
+        if (!perm) continue;
+        int n = 0;
+        for (int32_t s = 0; s < d; s++) {
+            contrib_key(i, adj[beg + s], vel[beg + s], keys + n);
+            n += 3;
+        }
+        isort64(keys, n);
+        int32_t cbase = 3 * beg;   // this row's contributions occupy perm[3*vptr[i] .. 3*vptr[i+1])
+        int t = 0;
+        for (int s = 0; s < n; s++) {
+            if (s == 0 || (keys[s] >> 32) != (keys[s - 1] >> 32)) seg_ptr[o + t++] = cbase + s;
+            perm[cbase + s] = (int32_t)(keys[s] & 0xffffffffLL);
+        }
+        // the row's triangle list in ascending triangle order (used by deterministic gathers)
+        for (int32_t s = 1; s < d; s++) {
+            int32_t v = vel[beg + s];
+            int32_t j = s - 1;
+            while (j >= 0 && vel[beg + j] > v) { vel[beg + j + 1] = vel[beg + j]; j--; }
+            vel[beg + j + 1] = v;
+        }
+    }
+}
+
+// Contribution lists of a high-valence row, one block per row: 3d keys in shared memory
+// (distinct, since c is unique). Pass 1: each key's rank among all keys gives its perm slot,
+// and a key is the head of its column's segment if no smaller key has the same column.
+// Pass 2: each head's rank among the heads is its column's position in the row. The row's
+// triangle list is reordered by rank too (ascending triangle id).
+__global__ void k_row_big_perm(const int32_t* __restrict__ big_list, const int32_t* __restrict__ vptr,
+                               const int2* __restrict__ adj, int32_t* __restrict__ vel,
+                               const int32_t* __restrict__ row_ptr, int32_t* __restrict__ seg_ptr,
+                               int32_t* __restrict__ perm) {
+    extern __shared__ long long smk[];
+    int32_t i = big_list[blockIdx.x];
+    int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+    int n = 3 * d;
+    int32_t* rank = reinterpret_cast<int32_t*>(smk + n);
+    int32_t* vsort = rank + n;
+    unsigned char* head = reinterpret_cast<unsigned char*>(vsort + d);
+    for (int s = threadIdx.x; s < d; s += blockDim.x) {
+        long long k3[3];
+        contrib_key(i, adj[beg + s], vel[beg + s], k3);
+        smk[3 * s] = k3[0];
+        smk[3 * s + 1] = k3[1];
+        smk[3 * s + 2] = k3[2];
+    }
+    __syncthreads();
+    int32_t cbase = 3 * beg;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        long long v = smk[t];
+        int r = 0;
+        unsigned char h = 1;
+        for (int u = 0; u < n; u++) {
+            long long w = smk[u];
+            r += w < v;
+            if ((w >> 32) == (v >> 32) && w < v) h = 0;
+        }
+        rank[t] = r;
+        head[t] = h;
+        perm[cbase + r] = (int32_t)(v & 0xffffffffLL);
+    }
+    for (int s = threadIdx.x; s < d; s += blockDim.x) {
+        int32_t v = vel[beg + s];
+        int r = 0;
+        for (int u = 0; u < d; u++) r += vel[beg + u] < v;
+        vsort[r] = v;
+    }
+    __syncthreads();
+    int32_t o = row_ptr[i];
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        if (!head[t]) continue;
+        long long col = smk[t] >> 32;
+        int cr = 0;
+        for (int u = 0; u < n; u++) cr += (head[u] && (smk[u] >> 32) < col);
+        seg_ptr[o + cr] = cbase + rank[t];
+    }
+    for (int s = threadIdx.x; s < d; s += blockDim.x) vel[beg + s] = vsort[s];
+}
+
+// map[9k + 3b + a] = position of (me[a][k], me[b][k]); staged through shared memory so the
+// 9 entries of consecutive triangles leave as one contiguous, coalesced block.
+static constexpr int MAP_BLOCK = 256;
+
+__global__ void k_build_map(const int32_t* __restrict__ me, int32_t nme, const int32_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ col_idx, int32_t* __restrict__ map, int* __restrict__ missing) {
+    __shared__ int32_t tile[9 * MAP_BLOCK];
+    for (int64_t k0 = (int64_t)blockIdx.x * MAP_BLOCK; k0 < nme; k0 += (int64_t)gridDim.x * MAP_BLOCK) {
+        int64_t k = k0 + threadIdx.x;
+        if (k < nme) {
+            int32_t v[3] = {me[k], me[nme + k], me[2 * (int64_t)nme + k]};
+            for (int a = 0; a < 3; a++) {
+                int32_t lo0 = row_ptr[v[a]], hi0 = row_ptr[v[a] + 1];
+                for (int b = 0; b < 3; b++) {
+                    int32_t lo = lo0, hi = hi0;
+                    while (lo < hi) {
+                        int32_t mid = (lo + hi) >> 1;
+                        if (col_idx[mid] < v[b]) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo >= hi0 || col_idx[lo] != v[b]) { *missing = 1; lo = 0; }
+                    tile[9 * threadIdx.x + 3 * b + a] = lo;
+                }
+            }
+        }
+        __syncthreads();
+        int64_t n = nme - k0 < MAP_BLOCK ? nme - k0 : MAP_BLOCK;
+        for (int t = threadIdx.x; t < 9 * n; t += MAP_BLOCK) map[9 * k0 + t] = tile[t];
+        __syncthreads();
+    }
+}
+
+// 2x2 block expansion (elasticity): scalar row i with degree g gives rows 2i, 2i+1 with
+// row_ptr2[2i+a] = 4 row_ptr[i] + 2 a g and columns 2j, 2j+1 for each scalar column j.
+__global__ void k_expand(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t nq,
+                         int32_t* __restrict__ row_ptr2, int32_t* __restrict__ col_idx2) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t b = row_ptr[r], g = row_ptr[r + 1] - b;
+        for (int a = 0; a < 2; a++) {
+            int32_t o = 4 * b + 2 * a * g;
+            row_ptr2[2 * r + a] = o;
+            for (int32_t t = 0; t < g; t++) {
+                int32_t j = col_idx[b + t];
+                col_idx2[o + 2 * t] = 2 * j;
+                col_idx2[o + 2 * t + 1] = 2 * j + 1;
+            }
+        }
+        if (r == nq - 1) row_ptr2[2 * (int64_t)nq] = 4 * row_ptr[nq];
+    }
+}
+
+__global__ void k_set_last(int32_t* p, int32_t v) { *p = v; }
+
+extern "C" void fe_pattern_destroy(fe_pattern p) {
+    if (!p) return;
+    fe_free(p->row_ptr); fe_free(p->col_idx); fe_free(p->map);
+    fe_free(p->row_ptr2); fe_free(p->col_idx2);
+    fe_free(p->seg_ptr); fe_free(p->perm); fe_free(p->vptr); fe_free(p->vel); fe_free(p->kg);
+    delete p;
+}
+
+namespace {
+struct Temps {
+    int32_t *deg = nullptr, *cur = nullptr, *row_nnz = nullptr, *big_list = nullptr, *big_count = nullptr;
+    int* flag = nullptr;
+    int2* adj = nullptr;
+    ~Temps() {
+        fe_free(deg); fe_free(cur); fe_free(row_nnz); fe_free(big_list); fe_free(big_count); fe_free(flag); fe_free(adj);
+    }
+};
+}  // namespace
+
+static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_pattern p) {
+    const int32_t nq = m->nq, nme = m->nme;
+    const int64_t n3 = 3 * (int64_t)nme;
+    const bool gather = flags & FE_PATTERN_GATHER;
+    Temps t;
+    fe_status st;
+    if ((st = fe_alloc_n(&p->row_ptr, (size_t)nq + 1, "row_ptr"))) return st;
+    if ((st = fe_alloc_n(&p->vptr, (size_t)nq + 1, "vertex pointers"))) return st;
+    if ((st = fe_alloc_n(&t.deg, (size_t)nq + 1, "valences"))) return st;
+    if ((st = fe_alloc_n(&t.cur, (size_t)nq + 1, "bucket cursors"))) return st;
+    if ((st = fe_alloc_n(&t.row_nnz, (size_t)nq + 1, "row counts"))) return st;
+    if ((st = fe_alloc_n(&t.big_list, (size_t)nq + 1, "high-valence rows"))) return st;
+    if ((st = fe_alloc_n(&t.big_count, 1, "counter"))) return st;
+    if ((st = fe_alloc_n(&t.flag, 2, "flags"))) return st;
+    if ((st = fe_alloc_n(&t.adj, (size_t)n3, "row buckets"))) return st;
+    if (gather && (st = fe_alloc_n(&p->vel, (size_t)n3, "vertex-to-triangle lists"))) return st;
+    FE_CUDA(cudaMemsetAsync(t.deg, 0, sizeof(int32_t) * ((size_t)nq + 1), s));
+    FE_CUDA(cudaMemsetAsync(t.cur, 0, sizeof(int32_t) * ((size_t)nq + 1), s));
+    FE_CUDA(cudaMemsetAsync(t.row_nnz, 0, sizeof(int32_t) * ((size_t)nq + 1), s));
+    FE_CUDA(cudaMemsetAsync(t.big_count, 0, sizeof(int32_t), s));
+    FE_CUDA(cudaMemsetAsync(t.flag, 0, 2 * sizeof(int), s));
+
+    // row digit: counting sort of the 3 nme (vertex, triangle) incidences
+    if (n3 > 0) {
+        { FE_PROF("k_count_deg", s); k_count_deg<<<fe_grid(n3, 256), 256, 0, s>>>(m->me, n3, t.deg); }
+        FE_LAUNCHED("k_count_deg");
+    }
+    int64_t tot = 0;
+    if ((st = fe_exclusive_scan(t.deg, p->vptr, nq, s, nullptr))) return st;
+    if (n3 > 0) {
+        { FE_PROF("k_fill_adj", s); k_fill_adj<<<fe_grid(n3, 256), 256, 0, s>>>(m->me, nme, p->vptr, t.cur, t.adj, p->vel); }
+        FE_LAUNCHED("k_fill_adj");
+    }
+    // column digit inside each row, unique
+    if (nq > 0) {
+        { FE_PROF("k_row_count", s); k_row_count<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, t.adj, nq, t.row_nnz, t.big_list, t.big_count, t.flag); }
+        FE_LAUNCHED("k_row_count");
+    }
+    int host_flags[2] = {0, 0};
+    int32_t nbig = 0;
+    FE_CUDA(cudaMemcpyAsync(host_flags, t.flag, sizeof host_flags, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemcpyAsync(&nbig, t.big_count, sizeof nbig, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    if (host_flags[0])
+        return fe_fail(FE_ERR_LIMIT, "a vertex belongs to more than FE_MAX_VALENCE=" + std::to_string(FE_MAX_VALENCE) + " triangles");
+    size_t big_smem = (2 * (size_t)FE_MAX_VALENCE + 1) * (sizeof(int32_t) + 1);
+    if (nbig > 0) {
+        { FE_PROF("k_row_big", s); k_row_big<<<nbig, BIG_BLOCK, big_smem, s>>>(t.big_list, p->vptr, t.adj, nullptr, t.row_nnz, nullptr); }
+        FE_LAUNCHED("k_row_big (count)");
+    }
+    if ((st = fe_exclusive_scan(t.row_nnz, p->row_ptr, nq, s, &tot))) return st;
+    p->nnz_scalar = tot;
+    if ((st = fe_alloc_n(&p->col_idx, (size_t)tot, "col_idx"))) return st;
+    if ((st = fe_alloc_n(&p->map, 9 * (size_t)nme, "element-to-nnz map"))) return st;
+    if (gather) {
+        if ((st = fe_alloc_n(&p->seg_ptr, (size_t)tot + 1, "seg_ptr"))) return st;
+        if ((st = fe_alloc_n(&p->perm, 9 * (size_t)nme, "perm"))) return st;
+    }
+    if (nq > 0) {
+        { FE_PROF("k_row_fill", s); k_row_fill<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, t.adj, p->vel, nq, p->row_ptr, p->col_idx,
+                                                    p->seg_ptr, p->perm); }
+        FE_LAUNCHED("k_row_fill");
+    }
+    if (nbig > 0) {
+        { FE_PROF("k_row_big", s); k_row_big<<<nbig, BIG_BLOCK, big_smem, s>>>(t.big_list, p->vptr, t.adj, p->row_ptr, nullptr, p->col_idx); }
+        FE_LAUNCHED("k_row_big (fill)");
+        if (gather) {
+            size_t sm = 3 * (size_t)FE_MAX_VALENCE * (sizeof(long long) + sizeof(int32_t) + 1) +
+                        (size_t)FE_MAX_VALENCE * sizeof(int32_t);
+            FE_CUDA(cudaFuncSetAttribute(k_row_big_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            { FE_PROF("k_row_big_perm", s); k_row_big_perm<<<nbig, BIG_BLOCK, sm, s>>>(t.big_list, p->vptr, t.adj, p->vel, p->row_ptr, p->seg_ptr, p->perm); }
+            FE_LAUNCHED("k_row_big_perm");
+        }
+    }
+    if (gather) {
+        { FE_PROF("k_set_last", s); k_set_last<<<1, 1, 0, s>>>(p->seg_ptr + tot, (int32_t)(9 * (int64_t)nme)); }
+        FE_LAUNCHED("k_set_last");
+    }
+    if (nme > 0) {
+        { FE_PROF("k_build_map", s); k_build_map<<<fe_grid(nme, MAP_BLOCK), MAP_BLOCK, 0, s>>>(m->me, nme, p->row_ptr, p->col_idx, p->map, t.flag + 1); }
+        FE_LAUNCHED("k_build_map");
+    }
+    p->n_rows = nq;
+    p->nnz = tot;
+    if (dofs == 2) {
+        if (4 * tot >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "elasticity nnz exceeds int32");
+        if ((st = fe_alloc_n(&p->row_ptr2, 2 * (size_t)nq + 1, "row_ptr (dofs=2)"))) return st;
+        if ((st = fe_alloc_n(&p->col_idx2, 4 * (size_t)tot, "col_idx (dofs=2)"))) return st;
+        if (nq > 0) {
+            { FE_PROF("k_expand", s); k_expand<<<fe_grid(nq, 256), 256, 0, s>>>(p->row_ptr, p->col_idx, nq, p->row_ptr2, p->col_idx2); }
+            FE_LAUNCHED("k_expand");
+        } else {
+            FE_CUDA(cudaMemsetAsync(p->row_ptr2, 0, sizeof(int32_t), s));
+        }
+        p->n_rows = 2 * (int64_t)nq;
+        p->nnz = 4 * tot;
+    }
+    if (gather) {
+        size_t kg = dofs == 2 ? 36 * (size_t)nme : 18 * (size_t)nme;
+        if ((st = fe_alloc_n(&p->kg, kg, "element value staging"))) return st;
+    }
+    FE_CUDA(cudaMemcpyAsync(host_flags, t.flag, sizeof host_flags, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    if (host_flags[1]) return fe_fail(FE_ERR_CUDA, "internal error: a triangle key is missing from the pattern");
+    if (!gather) { fe_free(p->vptr); p->vptr = nullptr; }
+    return FE_OK;
+}
+
+extern "C" fe_status fe_pattern_build(fe_mesh m, int dofs, int flags, fe_stream stream, fe_pattern* out) {
+    if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");
+    if (dofs != 1 && dofs != 2) return fe_fail(FE_ERR_INVALID_ARG, "dofs_per_vertex must be 1 or 2");
+    if (flags & ~FE_PATTERN_GATHER) return fe_fail(FE_ERR_INVALID_ARG, "unknown pattern flag");
+    if (dofs == 2 && 36 * (int64_t)m->nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "36*nme must be < 2^31");
+    if (9 * (int64_t)m->nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "9*nme must be < 2^31");
+    fe_pattern p = new fe_pattern_s();
+    p->dofs = dofs;
+    p->flags = flags;
+    p->nq = m->nq;
+    p->nme = m->nme;
+    p->topology_id = m->topology_id;
+    fe_status st = build(m, dofs, flags, (cudaStream_t)stream, p);
+    if (st) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        fe_pattern_destroy(p);
+        return st;
+    }
+    *out = p;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_pattern_info(fe_pattern p, int64_t* n_rows, int64_t* nnz, const int32_t** row_ptr,
+                                     const int32_t** col_idx) {
+    if (!p) return fe_fail(FE_ERR_INVALID_ARG, "null pattern");
+    if (n_rows) *n_rows = p->n_rows;
+    if (nnz) *nnz = p->nnz;
+    if (row_ptr) *row_ptr = p->dofs == 2 ? p->row_ptr2 : p->row_ptr;
+    if (col_idx) *col_idx = p->dofs == 2 ? p->col_idx2 : p->col_idx;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_pattern_map(fe_pattern p, const int32_t** map, int64_t* len) {
+    if (!p) return fe_fail(FE_ERR_INVALID_ARG, "null pattern");
+    if (map) *map = p->map;
+    if (len) *len = 9 * (int64_t)p->nme;
+    return FE_OK;
+}

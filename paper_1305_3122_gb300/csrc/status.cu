@@ -1,0 +1,316 @@
+// status.cu -- error reporting, allocation helpers, device queries and the scan utility.
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "internal.cuh"
+
+static thread_local std::string g_last_error;
+
+fe_status fe_fail(fe_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+fe_status fe_cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA;
+}
+
+fe_status fe_alloc(void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fe_fail(e == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA,
+                       std::string("cudaMalloc(") + std::to_string(bytes) + " bytes) for " + what +
+                           ": " + cudaGetErrorString(e));
+    }
+    return FE_OK;
+}
+
+void fe_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+int fe_sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+extern "C" const char* fe_status_string(fe_status st) {
+    switch (st) {
+        case FE_OK: return "FE_OK";
+        case FE_ERR_INVALID_ARG: return "FE_ERR_INVALID_ARG";
+        case FE_ERR_INDEX_RANGE: return "FE_ERR_INDEX_RANGE";
+        case FE_ERR_DEGENERATE: return "FE_ERR_DEGENERATE";
+        case FE_ERR_ORIENTATION: return "FE_ERR_ORIENTATION";
+        case FE_ERR_BUFFER_TOO_SMALL: return "FE_ERR_BUFFER_TOO_SMALL";
+        case FE_ERR_OOM: return "FE_ERR_OOM";
+        case FE_ERR_CUDA: return "FE_ERR_CUDA";
+        case FE_ERR_TIMEOUT: return "FE_ERR_TIMEOUT";
+        case FE_ERR_LIMIT: return "FE_ERR_LIMIT";
+    }
+    return "FE_ERR_UNKNOWN";
+}
+
+extern "C" const char* fe_last_error(void) { return g_last_error.c_str(); }
+
+fe_status fe_check_pair(fe_mesh mesh, fe_pattern pat, int dofs) {
+    if (!mesh || !pat) return fe_fail(FE_ERR_INVALID_ARG, "null mesh or pattern");
+    if (pat->topology_id != mesh->topology_id || pat->nq != mesh->nq || pat->nme != mesh->nme)
+        return fe_fail(FE_ERR_INVALID_ARG, "pattern was built for another mesh topology");
+    if (dofs && pat->dofs != dofs)
+        return fe_fail(FE_ERR_INVALID_ARG, dofs == 2 ? "elasticity needs a dofs_per_vertex=2 pattern"
+                                                     : "scalar matrices need a dofs_per_vertex=1 pattern");
+    return FE_OK;
+}
+
+// ------------------------------------------------------------------------ scan
+//
+// Three passes: per-tile sums, an exclusive scan of the tile sums by one block, and a
+// per-tile scan that adds the tile's offset. Tiles are SCAN_TILE consecutive elements.
+
+static constexpr int SCAN_BLOCK = 512;
+static constexpr int SCAN_ITEMS = 8;
+static constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+__global__ void k_tile_sums(const int32_t* __restrict__ in, int64_t n, long long* __restrict__ sums) {
+    __shared__ long long red[SCAN_BLOCK / 32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    long long s = 0;
+    for (int t = threadIdx.x; t < SCAN_TILE; t += SCAN_BLOCK) {
+        int64_t i = base + t;
+        if (i < n) s += in[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < SCAN_BLOCK / 32 ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) sums[blockIdx.x] = s;
+    }
+}
+
+// One block of 1024 threads scans the tile sums in chunks of 1024 (exclusive), in place;
+// sums[ntiles] receives the total.
+__global__ void k_scan_sums(long long* sums, int64_t ntiles) {
+    __shared__ long long warp_tot[32];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < ntiles; base += 1024) {
+        int64_t i = base + threadIdx.x;
+        long long v = i < ntiles ? sums[i] : 0;
+        long long x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            long long t = warp_tot[threadIdx.x];
+            for (int o = 1; o < 32; o <<= 1) {
+                long long y = __shfl_up_sync(0xffffffffu, t, o);
+                if (threadIdx.x >= o) t += y;
+            }
+            warp_tot[threadIdx.x] = t;   // inclusive over warps
+        }
+        __syncthreads();
+        long long warp_off = (threadIdx.x >> 5) ? warp_tot[(threadIdx.x >> 5) - 1] : 0;
+        if (i < ntiles) sums[i] = carry + warp_off + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_tot[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[ntiles] = carry;
+}
+
+__global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n,
+                            const long long* __restrict__ offs, int* __restrict__ overflow) {
+    __shared__ long long warp_tot[SCAN_BLOCK / 32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    long long v[SCAN_ITEMS];
+    long long local = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        int64_t i = base + j;
+        v[j] = i < n ? in[i] : 0;
+        local += v[j];
+    }
+    long long x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        long long t = threadIdx.x < SCAN_BLOCK / 32 ? warp_tot[threadIdx.x] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (threadIdx.x >= o) t += y;
+        }
+        if (threadIdx.x < SCAN_BLOCK / 32) warp_tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+    long long run = offs[blockIdx.x] + ((threadIdx.x >> 5) ? warp_tot[(threadIdx.x >> 5) - 1] : 0) + x - local;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        int64_t i = base + j;
+        if (i < n) {
+            if (run > INT32_MAX) *overflow = 1;
+            out[i] = (int32_t)run;
+        }
+        run += v[j];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        long long tot = offs[gridDim.x];
+        if (tot > INT32_MAX) *overflow = 1;
+        out[n] = (int32_t)tot;
+    }
+}
+
+fe_status fe_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s,
+                            int64_t* total_out) {
+    int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (ntiles < 1) ntiles = 1;
+    long long* sums = nullptr;
+    int* ovf = nullptr;
+    fe_status st = fe_alloc_n(&sums, (size_t)ntiles + 1, "scan tile sums");
+    if (st) return st;
+    st = fe_alloc_n(&ovf, 1, "scan overflow flag");
+    if (st) { fe_free(sums); return st; }
+    cudaMemsetAsync(ovf, 0, sizeof(int), s);
+    { FE_PROF("k_tile_sums", s); k_tile_sums<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, sums); }
+    { FE_PROF("k_scan_sums", s); k_scan_sums<<<1, 1024, 0, s>>>(sums, ntiles); }
+    { FE_PROF("k_tile_scan", s); k_tile_scan<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, n, sums, ovf); }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { fe_free(sums); fe_free(ovf); return fe_cuda_fail(e, "scan kernels"); }
+    fe_status ret = FE_OK;
+    if (total_out) {
+        long long tot = 0;
+        int ov = 0;
+        e = cudaMemcpyAsync(&tot, sums + ntiles, sizeof(tot), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ov, ovf, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) ret = fe_cuda_fail(e, "scan total read-back");
+        else if (ov || tot > INT32_MAX) ret = fe_fail(FE_ERR_LIMIT, "prefix sum exceeds int32 (too many non-zeros)");
+        else *total_out = tot;
+    } else {
+        e = cudaStreamSynchronize(s);   // the temporaries are freed below
+        if (e != cudaSuccess) ret = fe_cuda_fail(e, "scan");
+    }
+    fe_free(sums);
+    fe_free(ovf);
+    return ret;
+}
+
+// ------------------------------------------------------------------------ kernel timing
+//
+// When enabled, every kernel launch of the library is bracketed by two CUDA events recorded
+// on its launch stream (skipped while the stream is being captured into a graph). Pending
+// event pairs are resolved into per-kernel totals by fe_profile_read.
+
+#include <map>
+#include <vector>
+
+namespace {
+struct Pending {
+    const char* name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_free_events;
+std::map<std::string, std::pair<double, long long>> g_totals;
+
+cudaEvent_t take_event() {
+    if (!g_free_events.empty()) {
+        cudaEvent_t e = g_free_events.back();
+        g_free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+}
+}  // namespace
+
+FeProf::FeProf(const char* name, cudaStream_t s) : name_(name), s_(s) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) { cudaGetLastError(); return; }
+    a_ = take_event();
+    if (a_ && cudaEventRecord(a_, s) != cudaSuccess) { cudaGetLastError(); g_free_events.push_back(a_); a_ = nullptr; }
+}
+
+FeProf::~FeProf() {
+    if (!a_) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t b = take_event();
+    if (!b || cudaEventRecord(b, s_) != cudaSuccess) {
+        cudaGetLastError();
+        g_free_events.push_back(a_);
+        if (b) g_free_events.push_back(b);
+        return;
+    }
+    g_pending.push_back({name_, a_, b});
+}
+
+extern "C" fe_status fe_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& p : g_pending) {
+        cudaEventSynchronize(p.b);
+        g_free_events.push_back(p.a);
+        g_free_events.push_back(p.b);
+    }
+    g_pending.clear();
+    g_totals.clear();
+    return FE_OK;
+}
+
+extern "C" fe_status fe_profile_read(int32_t max_entries, char* names, double* total_ms, int64_t* launches,
+                                     int32_t* count) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& p : g_pending) {
+        cudaError_t e = cudaEventSynchronize(p.b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e != cudaSuccess) { cudaGetLastError(); continue; }
+        auto& t = g_totals[p.name];
+        t.first += ms;
+        t.second += 1;
+        g_free_events.push_back(p.a);
+        g_free_events.push_back(p.b);
+    }
+    g_pending.clear();
+    int32_t n = 0;
+    for (auto& kv : g_totals) {
+        if (n < max_entries) {
+            if (names) {
+                strncpy(names + 64 * (size_t)n, kv.first.c_str(), 63);
+                names[64 * (size_t)n + 63] = 0;
+            }
+            if (total_ms) total_ms[n] = kv.second.first;
+            if (launches) launches[n] = kv.second.second;
+        }
+        n++;
+    }
+    if (count) *count = n;
+    return FE_OK;
+}

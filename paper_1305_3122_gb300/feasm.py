@@ -1,0 +1,377 @@
+"""Python binding of ``libfeasm.so`` (the C ABI declared in ``include/feasm.h``).
+
+Argument marshalling only: every step of the assembly runs in the CUDA library. PyTorch
+provides device memory (tensors) and streams (``torch.cuda.current_stream()``); the CSR
+structure owned by a pattern is exposed as zero-copy int32 CUDA tensors.
+
+If the library has not been built (``paper_1305_3122_gb300.build.build()``), or no GPU is
+present, the calls raise; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfeasm.so")
+
+FE_OK = 0
+PTR_HOST, PTR_DEVICE = 0, 1
+ATOMIC, GATHER = 0, 1
+PATTERN_DEFAULT, PATTERN_GATHER = 0, 1
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_INT = ctypes.c_int
+
+# name -> (restype, argtypes); mirrors include/feasm.h
+SIGNATURES = {
+    "fe_mesh_create": (_INT, [_I32, _I32, _P, _P, _INT, _P, ctypes.POINTER(_P)]),
+    "fe_mesh_set_coords": (_INT, [_P, _P, _INT, _P]),
+    "fe_mesh_check": (_INT, [_P, _P]),
+    "fe_mesh_info": (_INT, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "fe_mesh_destroy": (None, [_P]),
+    "fe_pattern_build": (_INT, [_P, _INT, _INT, _P, ctypes.POINTER(_P)]),
+    "fe_pattern_info": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "fe_pattern_map": (_INT, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
+    "fe_pattern_destroy": (None, [_P]),
+    "fe_assemble_mass": (_INT, [_P, _P, _INT, _P, _I64, _P]),
+    "fe_assemble_wmass": (_INT, [_P, _P, _P, _INT, _P, _I64, _P]),
+    "fe_assemble_stiff": (_INT, [_P, _P, _INT, _P, _I64, _P]),
+    "fe_assemble_stiff_wmass": (_INT, [_P, _P, _P, _INT, _P, _P, _I64, _P]),
+    "fe_assemble_elas": (_INT, [_P, _P, _D, _D, _INT, _P, _I64, _P]),
+    "fe_adjoint_stiff_wmass": (_INT, [_P, _P, _P, _P, _P, _INT, _P, _P, _P]),
+    "fe_batch_create": (_INT, [_I32, _P, _P, ctypes.POINTER(_P)]),
+    "fe_batch_tune": (_INT, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "fe_batch_set_shape": (_INT, [_P, _I32, _I32]),
+    "fe_batch_assemble_stiff_mass": (_INT, [_P, _P, _P, _P]),
+    "fe_batch_assemble_stiff_mass_plain": (_INT, [_P, _P, _P, _P]),
+    "fe_batch_destroy": (None, [_P]),
+    "fe_profile_enable": (_INT, [_INT]),
+    "fe_profile_reset": (_INT, []),
+    "fe_profile_read": (_INT, [_I32, _P, _P, _P, ctypes.POINTER(_I32)]),
+    "fe_status_string": (ctypes.c_char_p, [_INT]),
+    "fe_last_error": (ctypes.c_char_p, []),
+}
+
+
+class FeasmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(message)
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (raises if it is missing: build it first)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library with "
+                               "paper_1305_3122_gb300.build.build() (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != FE_OK:
+        L = lib()
+        raise FeasmError(status, f"{what}: {L.fe_status_string(status).decode()}: {L.fe_last_error().decode()}")
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dptr(t: torch.Tensor | None, dtype: torch.dtype, what: str) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous CUDA tensor of dtype {dtype}")
+    return t.data_ptr()
+
+
+class _DevView:
+    """Zero-copy view of library-owned device memory (keeps its owner alive)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, False),
+                                         "version": 3, "strides": None}
+        self.owner = owner
+
+
+def _view_i32(ptr: int, n: int, owner) -> torch.Tensor:
+    if n == 0:
+        return torch.empty(0, dtype=torch.int32, device="cuda")
+    return torch.as_tensor(_DevView(ptr, n, "<i4", owner), device="cuda")
+
+
+class Mesh:
+    """A triangulation: q [2, nq] float64 and me [3, nme] int32 (0-based, counter-clockwise).
+
+    q and me may be CUDA tensors, CPU tensors or numpy arrays; host inputs are copied by the
+    library (FE_PTR_HOST). Section 2 of the paper.
+    """
+
+    def __init__(self, q, me, stream=None):
+        L = lib()
+        self._h = None
+        if isinstance(q, torch.Tensor) and q.is_cuda:
+            qd = q.contiguous()
+            med = me.contiguous()
+            kind = PTR_DEVICE
+            qp = _dptr(qd, torch.float64, "q")
+            mp = _dptr(med, torch.int32, "me")
+        else:
+            qd = np.ascontiguousarray(q.cpu().numpy() if isinstance(q, torch.Tensor) else q, dtype=np.float64)
+            med = np.ascontiguousarray(me.cpu().numpy() if isinstance(me, torch.Tensor) else me, dtype=np.int32)
+            kind = PTR_HOST
+            qp = qd.ctypes.data
+            mp = med.ctypes.data
+        if qd.shape[0] != 2 or med.shape[0] != 3:
+            raise ValueError("q must be [2, nq] and me must be [3, nme]")
+        self.nq, self.nme = int(qd.shape[1]), int(med.shape[1])
+        h = _P()
+        _check(L.fe_mesh_create(self.nq, self.nme, qp, mp, kind, _stream(stream), ctypes.byref(h)), "fe_mesh_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_coords(self, q: torch.Tensor, stream=None):
+        if q.is_cuda:
+            _check(lib().fe_mesh_set_coords(self._h, _dptr(q.contiguous(), torch.float64, "q"), PTR_DEVICE,
+                                            _stream(stream)), "fe_mesh_set_coords")
+        else:
+            qh = np.ascontiguousarray(q.numpy(), dtype=np.float64)
+            _check(lib().fe_mesh_set_coords(self._h, qh.ctypes.data, PTR_HOST, _stream(stream)), "fe_mesh_set_coords")
+
+    def check(self, stream=None):
+        _check(lib().fe_mesh_check(self._h, _stream(stream)), "fe_mesh_check")
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fe_mesh_destroy(self._h)
+            self._h = None
+
+
+class Pattern:
+    """CSR structure and element-to-nnz map of a mesh (fe_pattern_build)."""
+
+    def __init__(self, mesh: Mesh, dofs: int = 1, gather: bool = False, stream=None):
+        h = _P()
+        _check(lib().fe_pattern_build(mesh.handle, dofs, PATTERN_GATHER if gather else PATTERN_DEFAULT,
+                                      _stream(stream), ctypes.byref(h)), "fe_pattern_build")
+        self._h = h
+        self.mesh = mesh
+        self.dofs = dofs
+        self.gather = gather
+        n_rows, nnz, rp, ci = _I64(), _I64(), _P(), _P()
+        _check(lib().fe_pattern_info(h, ctypes.byref(n_rows), ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci)),
+               "fe_pattern_info")
+        self.n_rows, self.nnz = n_rows.value, nnz.value
+        self.row_ptr = _view_i32(rp.value, self.n_rows + 1, self)
+        self.col_idx = _view_i32(ci.value, self.nnz, self)
+        mp, ml = _P(), _I64()
+        _check(lib().fe_pattern_map(h, ctypes.byref(mp), ctypes.byref(ml)), "fe_pattern_map")
+        self.map = _view_i32(mp.value, ml.value, self)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def new_values(self) -> torch.Tensor:
+        return torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+
+    def to_sparse_csr(self, values: torch.Tensor) -> torch.Tensor:
+        return torch.sparse_csr_tensor(self.row_ptr.long(), self.col_idx.long(), values,
+                                       size=(self.n_rows, self.n_rows))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fe_pattern_destroy(self._h)
+            self._h = None
+
+
+def _values(pattern: Pattern, out: torch.Tensor | None) -> torch.Tensor:
+    out = pattern.new_values() if out is None else out
+    _dptr(out, torch.float64, "values")
+    return out
+
+
+def assemble_mass(mesh: Mesh, pattern: Pattern, variant: int = ATOMIC, out=None, stream=None) -> torch.Tensor:
+    """Values of M (Eq. 1) on the pattern's CSR structure."""
+    out = _values(pattern, out)
+    _check(lib().fe_assemble_mass(mesh.handle, pattern.handle, variant, out.data_ptr(), out.numel(), _stream(stream)),
+           "fe_assemble_mass")
+    return out
+
+
+def assemble_wmass(mesh: Mesh, pattern: Pattern, w: torch.Tensor, variant: int = ATOMIC, out=None,
+                   stream=None) -> torch.Tensor:
+    """Values of M^[w] (Eq. 2), w = vertex values [nq] float64 on the GPU."""
+    out = _values(pattern, out)
+    _check(lib().fe_assemble_wmass(mesh.handle, pattern.handle, _dptr(w, torch.float64, "w"), variant, out.data_ptr(),
+                                   out.numel(), _stream(stream)), "fe_assemble_wmass")
+    return out
+
+
+def assemble_stiff(mesh: Mesh, pattern: Pattern, variant: int = ATOMIC, out=None, stream=None) -> torch.Tensor:
+    """Values of S (Eq. 3)."""
+    out = _values(pattern, out)
+    _check(lib().fe_assemble_stiff(mesh.handle, pattern.handle, variant, out.data_ptr(), out.numel(),
+                                   _stream(stream)), "fe_assemble_stiff")
+    return out
+
+
+def assemble_stiff_wmass(mesh: Mesh, pattern: Pattern, w: torch.Tensor, variant: int = ATOMIC, out_S=None,
+                         out_M=None, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+    """Values of S and M^[w] in one pass over the triangles."""
+    out_S = _values(pattern, out_S)
+    out_M = _values(pattern, out_M)
+    cap = min(out_S.numel(), out_M.numel())
+    _check(lib().fe_assemble_stiff_wmass(mesh.handle, pattern.handle, _dptr(w, torch.float64, "w"), variant,
+                                         out_S.data_ptr(), out_M.data_ptr(), cap, _stream(stream)),
+           "fe_assemble_stiff_wmass")
+    return out_S, out_M
+
+
+def assemble_elas(mesh: Mesh, pattern: Pattern, lam: float, mu: float, variant: int = ATOMIC, out=None,
+                  stream=None) -> torch.Tensor:
+    """Values of the plane-elasticity K (Section 6); pattern built with dofs=2."""
+    out = _values(pattern, out)
+    _check(lib().fe_assemble_elas(mesh.handle, pattern.handle, float(lam), float(mu), variant, out.data_ptr(),
+                                  out.numel(), _stream(stream)), "fe_assemble_elas")
+    return out
+
+
+def adjoint_stiff_wmass(mesh: Mesh, pattern: Pattern, w: torch.Tensor, gS: torch.Tensor | None,
+                        gM: torch.Tensor | None, variant: int = ATOMIC, stream=None):
+    """(dL/dq [2, nq], dL/dw [nq]) of L = sum(gS * S.values) + sum(gM * M^[w].values)."""
+    dq = torch.empty((2, mesh.nq), dtype=torch.float64, device="cuda")
+    dw = torch.empty(mesh.nq, dtype=torch.float64, device="cuda")
+    _check(lib().fe_adjoint_stiff_wmass(mesh.handle, pattern.handle, _dptr(w, torch.float64, "w"),
+                                        _dptr(gS, torch.float64, "gS"), _dptr(gM, torch.float64, "gM"), variant,
+                                        dq.data_ptr(), dw.data_ptr(), _stream(stream)), "fe_adjoint_stiff_wmass")
+    return dq, dw
+
+
+def profile_enable(on: bool = True):
+    """Turn the library's per-kernel event timing on or off (process-wide)."""
+    _check(lib().fe_profile_enable(1 if on else 0), "fe_profile_enable")
+
+
+def profile_reset():
+    _check(lib().fe_profile_reset(), "fe_profile_reset")
+
+
+def profile_read() -> dict[str, tuple[float, int]]:
+    """{kernel name: (total device ms, launches)} accumulated since the last reset."""
+    L = lib()
+    n = _I32()
+    _check(L.fe_profile_read(0, None, None, None, ctypes.byref(n)), "fe_profile_read")
+    cap = max(n.value, 1)
+    names = ctypes.create_string_buffer(64 * cap)
+    ms = (_D * cap)()
+    cnt = (_I64 * cap)()
+    _check(L.fe_profile_read(cap, names, ms, cnt, ctypes.byref(n)), "fe_profile_read")
+    out = {}
+    for i in range(min(n.value, cap)):
+        nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (ms[i], cnt[i])
+    return out
+
+
+class Batch:
+    """S and M of many meshes in one persistent, graph-replayed launch (fe_batch_*)."""
+
+    def __init__(self, meshes: list[Mesh], patterns: list[Pattern]):
+        n = len(meshes)
+        mh = (_P * max(n, 1))(*[m.handle for m in meshes])
+        ph = (_P * max(n, 1))(*[p.handle for p in patterns])
+        h = _P()
+        _check(lib().fe_batch_create(n, mh, ph, ctypes.byref(h)), "fe_batch_create")
+        self._h = h
+        self.meshes, self.patterns = meshes, patterns
+        self.n = n
+        self.S = [p.new_values() for p in patterns]
+        self.M = [p.new_values() for p in patterns]
+        self._tables = ((_P * max(n, 1))(*[t.data_ptr() for t in self.S]),
+                        (_P * max(n, 1))(*[t.data_ptr() for t in self.M]))
+
+    def tune(self, stream=None) -> tuple[int, int]:
+        b, t = _I32(), _I32()
+        _check(lib().fe_batch_tune(self._h, self._tables[0], self._tables[1], _stream(stream), ctypes.byref(b),
+                                   ctypes.byref(t)), "fe_batch_tune")
+        return b.value, t.value
+
+    def set_shape(self, block: int, tile: int):
+        _check(lib().fe_batch_set_shape(self._h, block, tile), "fe_batch_set_shape")
+
+    def assemble(self, stream=None):
+        _check(lib().fe_batch_assemble_stiff_mass(self._h, self._tables[0], self._tables[1], _stream(stream)),
+               "fe_batch_assemble_stiff_mass")
+        return self.S, self.M
+
+    def assemble_plain(self, stream=None):
+        _check(lib().fe_batch_assemble_stiff_mass_plain(self._h, self._tables[0], self._tables[1], _stream(stream)),
+               "fe_batch_assemble_stiff_mass_plain")
+        return self.S, self.M
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fe_batch_destroy(self._h)
+            self._h = None
+
+
+def assemble_host(kind: str, q: np.ndarray, me: np.ndarray, w: np.ndarray | None = None, lam: float = 1.0,
+                  mu: float = 0.5, variant: int = ATOMIC, pinned_out: dict | None = None, stream=None):
+    """One-shot assembly from host arrays to host CSR arrays (the end-to-end call).
+
+    kind in {"mass", "wmass", "stiff", "elas", "stiff_wmass"}. The mesh is created from host
+    memory (copied by the library), the pattern built, the values assembled, and row_ptr,
+    col_idx and values read back to (pinned, if given) host tensors. Returns a dict.
+    """
+    mesh = Mesh(q, me, stream=stream)
+    pat = Pattern(mesh, dofs=2 if kind == "elas" else 1, gather=(variant == GATHER), stream=stream)
+    vals = {}
+    if kind in ("wmass", "stiff_wmass"):
+        wd = torch.as_tensor(w).to("cuda", non_blocking=True)
+    if kind == "mass":
+        vals["values"] = assemble_mass(mesh, pat, variant, stream=stream)
+    elif kind == "wmass":
+        vals["values"] = assemble_wmass(mesh, pat, wd, variant, stream=stream)
+    elif kind == "stiff":
+        vals["values"] = assemble_stiff(mesh, pat, variant, stream=stream)
+    elif kind == "elas":
+        vals["values"] = assemble_elas(mesh, pat, lam, mu, variant, stream=stream)
+    elif kind == "stiff_wmass":
+        vals["S"], vals["Mw"] = assemble_stiff_wmass(mesh, pat, wd, variant, stream=stream)
+    else:
+        raise ValueError(kind)
+    out = {}
+    src = {"row_ptr": pat.row_ptr, "col_idx": pat.col_idx, **vals}
+    for name, t in src.items():
+        dst = (pinned_out or {}).get(name)
+        if dst is None or dst.numel() < t.numel():
+            dst = torch.empty(t.numel(), dtype=t.dtype, pin_memory=True)
+        dst = dst[: t.numel()]
+        dst.copy_(t, non_blocking=True)
+        out[name] = dst
+    (stream or torch.cuda.current_stream()).synchronize()
+    out["nnz"] = pat.nnz
+    return out

@@ -1,0 +1,206 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+row_ptr / col_idx / map are compared bit-exactly; values within 1e-13 of each row's largest
+|a_ij|; the deterministic variant must be bit-identical from run to run. Meshes span several
+thread blocks with ragged tails, plus the edge cases (empty mesh, one triangle, a vertex of
+high valence that takes the shared-memory path, the two-triangle square).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1305_3122_gb300 import feasm, meshgen
+from tests.gpu_common import assert_csr_equal, assert_values_close
+
+pytestmark = pytest.mark.gpu
+
+KINDS = {"mass": oracle.MASS, "wmass": oracle.WMASS, "stiff": oracle.STIFF}
+VARIANTS = [feasm.ATOMIC, feasm.GATHER]
+
+
+def fan_mesh(n_out: int, ring2: bool = True):
+    """A vertex of valence n_out (center 0 on a circle of n_out vertices), so the pattern build
+    takes its high-valence path; optionally a second ring to mix in ordinary rows."""
+    t = np.linspace(0, 2 * np.pi, n_out, endpoint=False)
+    pts = [(0.0, 0.0)] + [(np.cos(a), np.sin(a)) for a in t]
+    tris = [(0, 1 + i, 1 + (i + 1) % n_out) for i in range(n_out)]
+    if ring2:
+        base = len(pts)
+        pts += [(2 * np.cos(a + np.pi / n_out), 2 * np.sin(a + np.pi / n_out)) for a in t]
+        for i in range(n_out):
+            a, b = 1 + i, 1 + (i + 1) % n_out
+            c = base + i
+            tris.append((a, c, b))
+    q = np.array(pts).T.copy()
+    me = np.array(tris, dtype=np.int32).T.copy()
+    # make every triangle counter-clockwise
+    x, y = q
+    D = (x[me[2]] - x[me[0]]) * (y[me[0]] - y[me[1]]) - (x[me[0]] - x[me[1]]) * (y[me[2]] - y[me[0]])
+    flip = D < 0
+    me[1, flip], me[2, flip] = me[2, flip].copy(), me[1, flip].copy()
+    return q, me
+
+
+def _mesh_cases():
+    m64 = meshgen.square_mesh(64, meshgen.SEED_BASE + 1)
+    m37 = meshgen.square_mesh(37, 5)
+    qf, mef = fan_mesh(70)
+    q2 = np.array([[0.0, 1.0, 1.0, 0.0], [0.0, 0.0, 1.0, 1.0]])
+    me2 = np.array([[0, 0], [1, 2], [2, 3]], np.int32)
+    return {"square64": (m64.q, m64.me), "square37": (m37.q, m37.me), "fan70": (qf, mef), "two": (q2, me2),
+            "one": (q2, me2[:, :1].copy())}
+
+
+CASES = _mesh_cases()
+
+
+def _weights(q):
+    x, y = q
+    return 1.0 + 0.5 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) + 0.05 * np.cos(7 * x)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("gather", [False, True])
+def test_pattern_and_map(case, gather):
+    q, me = CASES[case]
+    mesh = feasm.Mesh(q, me)
+    pat = feasm.Pattern(mesh, gather=gather)
+    rp_o, ci_o, _ = oracle.assemble(oracle.MASS, q, me)
+    assert_csr_equal(pat.row_ptr.cpu(), pat.col_idx.cpu(), rp_o, ci_o)
+    # map[9k + 3 jl + il] is the stored position of (me[il][k], me[jl][k])
+    I, J, _ = oracle.triplets(oracle.MASS, q, me)
+    mp = pat.map.cpu().numpy()
+    rows = np.repeat(np.arange(len(rp_o) - 1), np.diff(rp_o))
+    np.testing.assert_array_equal(rows[mp], I)
+    np.testing.assert_array_equal(ci_o[mp], J)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("kind", sorted(KINDS))
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_scalar_values(case, kind, variant):
+    q, me = CASES[case]
+    w = _weights(q)
+    mesh = feasm.Mesh(q, me)
+    pat = feasm.Pattern(mesh, gather=True)
+    wd = torch.tensor(w, device="cuda")
+    if kind == "mass":
+        got = feasm.assemble_mass(mesh, pat, variant)
+    elif kind == "wmass":
+        got = feasm.assemble_wmass(mesh, pat, wd, variant)
+    else:
+        got = feasm.assemble_stiff(mesh, pat, variant)
+    rp, ci, va = oracle.assemble(KINDS[kind], q, me, w)
+    assert_values_close(rp, got.cpu().numpy(), va)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_stiff_wmass_fused(variant):
+    q, me = CASES["square64"]
+    w = _weights(q)
+    mesh = feasm.Mesh(q, me)
+    pat = feasm.Pattern(mesh, gather=True)
+    S, Mw = feasm.assemble_stiff_wmass(mesh, pat, torch.tensor(w, device="cuda"), variant)
+    rp, _, vs = oracle.assemble(oracle.STIFF, q, me)
+    _, _, vm = oracle.assemble(oracle.WMASS, q, me, w)
+    assert_values_close(rp, S.cpu().numpy(), vs)
+    assert_values_close(rp, Mw.cpu().numpy(), vm)
+
+
+@pytest.mark.parametrize("case", ["square37", "fan70", "two", "one"])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_elasticity(case, variant):
+    q, me = CASES[case]
+    mesh = feasm.Mesh(q, me)
+    pat = feasm.Pattern(mesh, dofs=2, gather=True)
+    rp, ci, va = oracle.assemble(oracle.ELAS, q, me, lam=1.0, mu=0.5)
+    assert_csr_equal(pat.row_ptr.cpu(), pat.col_idx.cpu(), rp, ci)
+    got = feasm.assemble_elas(mesh, pat, 1.0, 0.5, variant)
+    assert_values_close(rp, got.cpu().numpy(), va)
+
+
+def test_gather_bit_identical_runs():
+    q, me = CASES["square64"]
+    w = torch.tensor(_weights(q), device="cuda")
+    mesh = feasm.Mesh(q, me)
+    pat = feasm.Pattern(mesh, gather=True)
+    first = None
+    for _ in range(10):
+        S, Mw = feasm.assemble_stiff_wmass(mesh, pat, w, feasm.GATHER)
+        cur = torch.cat([S, Mw]).cpu().numpy().view(np.int64)
+        if first is None:
+            first = cur
+        np.testing.assert_array_equal(cur, first)
+
+
+def test_empty_mesh():
+    q = np.zeros((2, 5))
+    me = np.zeros((3, 0), np.int32)
+    mesh = feasm.Mesh(q, me)
+    pat = feasm.Pattern(mesh, gather=True)
+    assert pat.nnz == 0
+    np.testing.assert_array_equal(pat.row_ptr.cpu().numpy(), np.zeros(6, np.int32))
+    for v in VARIANTS:
+        assert feasm.assemble_stiff(mesh, pat, v).numel() == 0
+
+
+# ------------------------------------------------------------------ error paths
+
+def test_input_errors():
+    q = np.array([[0.0, 1.0, 1.0, 0.0], [0.0, 0.0, 1.0, 1.0]])
+    with pytest.raises(feasm.FeasmError) as e:
+        feasm.Mesh(q, np.array([[0], [1], [4]], np.int32))
+    assert e.value.status == 2
+    with pytest.raises(feasm.FeasmError) as e:
+        feasm.Mesh(q, np.array([[0], [1], [1]], np.int32))
+    assert e.value.status == 3
+    with pytest.raises(feasm.FeasmError) as e:
+        feasm.Mesh(q, np.array([[0], [2], [1]], np.int32))
+    assert e.value.status == 4
+    mesh = feasm.Mesh(q, np.array([[0, 0], [1, 2], [2, 3]], np.int32))
+    pat = feasm.Pattern(mesh)
+    with pytest.raises(feasm.FeasmError) as e:
+        feasm.assemble_mass(mesh, pat, out=torch.empty(5, dtype=torch.float64, device="cuda"))
+    assert e.value.status == 5
+    with pytest.raises(feasm.FeasmError) as e:
+        feasm.assemble_mass(mesh, pat, feasm.GATHER)      # pattern built without FE_PATTERN_GATHER
+    assert e.value.status == 1
+    other = feasm.Mesh(q, np.array([[0, 0], [1, 2], [2, 3]], np.int32))
+    with pytest.raises(feasm.FeasmError) as e:
+        feasm.assemble_mass(other, pat)                   # pattern of another mesh
+    assert e.value.status == 1
+    with pytest.raises(feasm.FeasmError) as e:
+        feasm.assemble_elas(mesh, pat, 1.0, 0.5)          # scalar pattern
+    assert e.value.status == 1
+    pat2 = feasm.Pattern(mesh, dofs=2)
+    with pytest.raises(feasm.FeasmError) as e:
+        feasm.assemble_elas(mesh, pat2, 1.0, -1.0)        # lambda + mu <= 0
+    assert e.value.status == 1
+
+
+def test_orientation_flag_after_set_coords():
+    q = np.array([[0.0, 1.0, 1.0, 0.0], [0.0, 0.0, 1.0, 1.0]])
+    mesh = feasm.Mesh(q, np.array([[0, 0], [1, 2], [2, 3]], np.int32))
+    pat = feasm.Pattern(mesh)
+    mesh.check()
+    bad = torch.tensor(q[:, [0, 3, 2, 1]], device="cuda")    # mirror: every triangle turns clockwise
+    mesh.set_coords(bad)
+    feasm.assemble_stiff(mesh, pat)
+    with pytest.raises(feasm.FeasmError) as e:
+        mesh.check()
+    assert e.value.status == 4
+    mesh.check()   # the word was cleared
+
+
+def test_host_one_shot_matches_device_path():
+    q, me = CASES["square37"]
+    w = _weights(q)
+    out = feasm.assemble_host("stiff_wmass", q, me, w)
+    rp, ci, vs = oracle.assemble(oracle.STIFF, q, me)
+    _, _, vm = oracle.assemble(oracle.WMASS, q, me, w)
+    assert_csr_equal(out["row_ptr"].numpy(), out["col_idx"].numpy(), rp, ci)
+    assert_values_close(rp, out["S"].numpy(), vs)
+    assert_values_close(rp, out["Mw"].numpy(), vm)
