@@ -1,0 +1,430 @@
+"""Benchmark: P1 stiffness S + weighted mass M^[w] assembly on one GB300 (per GPU for N > 1).
+
+Workload: the jittered, node-permuted unit-square mesh with 2048 x 2048 cells (nq = 4,198,401,
+nme = 8,388,608), w = 1 + 0.5 sin(2 pi x) cos(2 pi y) + U(0, 0.1), FP64 throughout. One step
+is one pass of the whole path over resident device inputs, as one sparse() call of the paper
+would do it: mesh validation (fe_mesh_create), the structural pattern (fe_pattern_build) and
+the values of S and M^[w] (fe_assemble_stiff_wmass). The value is triangles per second over
+the timed steps. Also reported:
+  - assemble_only: the values with the pattern built once beforehand (repeated assembly);
+  - batched: 256 uneven meshes (N log-uniform in [16, 512]) in one graph-replayed persistent
+    launch vs 256 plain launches;
+  - e2e: the same step from pinned host arrays to host CSR arrays through the public API;
+  - roofline of the dominant kernel, timed live with the library's own CUDA events;
+  - cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload.
+Between timed steps L2 is flushed by writing a 512 MB buffer (outside the timed intervals).
+
+Multi-GPU (torchrun): every rank assembles its own replica of the workload (no collective;
+weak scaling); value = all ranks' triangles / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "P1 assembly Melements/s and HBM GB/s (% peak), FP64, batched vs plain launches"
+UNIT = "Melem/s"
+N_CELLS = 2048
+SEED = 13053122 + 2
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ algorithmic bytes
+#
+# Bytes a kernel's role must move, per launch, for a mesh with nq vertices, nme triangles and
+# nnz stored entries per scalar matrix (int32 indices, FP64 values). The assembly figure is the
+# method's compulsory traffic (me, q, w read once; both value arrays written once).
+
+def algorithmic_bytes(name: str, nq: int, nme: int, nnz: int) -> int | None:
+    table = {
+        "k_scalar_atomic": 12 * nme + 16 * nq + 8 * nq + 16 * nnz,
+        "k_scalar_stage": 12 * nme + 16 * nq + 8 * nq + 2 * 72 * nme,
+        "k_seg_gather": 4 * (nnz + 1) + 36 * nme + 2 * 72 * nme + 16 * nnz,
+        "k_stiff_wmass_tiled": 12 * nme + 16 * nq + 8 * nq + 16 * nnz,
+        "k_validate": 12 * nme + 16 * nq,
+        "k_pack_coords": 32 * nq,
+        "k_count_deg": 12 * nme + 4 * nq,
+        "k_fill_adj": 12 * nme + 8 * nq + 24 * nme,
+        "k_row_count": 8 * nq + 24 * nme,
+        "k_row_fill": 12 * nq + 24 * nme + 4 * nnz,
+        "k_build_map": 12 * nme + 4 * nq + 4 * nnz + 36 * nme,
+        "k_tile_sums": 4 * nq,
+        "k_tile_scan": 8 * nq,
+    }
+    return table.get(name)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def cpu_oracle_sample(target_s: float = 10.0, n_cells: int = 512) -> dict:
+    """The oracle (single-threaded C, FP64) on a bounded sample: one 512 x 512-cell mesh of the
+    same recipe, S + M^[w] assembled repeatedly for about target_s seconds."""
+    import oracle
+    from paper_1305_3122_gb300 import meshgen
+
+    m = meshgen.square_mesh(n_cells, SEED)
+    w = meshgen.vertex_weights(m, SEED)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.assemble(oracle.STIFF, m.q, m.me)
+        oracle.assemble(oracle.WMASS, m.q, m.me, w)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= target_s:
+            break
+    return {"value": round(reps * m.nme / el / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x (S + M^[w]) on the {n_cells}x{n_cells}-cell mesh of the same recipe "
+                      f"(nme={m.nme}), {el:.1f} s, single-threaded C oracle"}
+
+
+def run_reference(args) -> int:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1305_3122_gb300 import meshgen
+
+    n_cells = 256
+    m = meshgen.square_mesh(n_cells, SEED)
+    w = meshgen.vertex_weights(m, SEED)
+
+    def step():
+        oracle.assemble(oracle.STIFF, m.q, m.me)
+        oracle.assemble(oracle.WMASS, m.q, m.me, w)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    value = args.steps * m.nme / el / 1e6
+    sample = (f"each step: S + M^[w] by the single-threaded FP64 C oracle (triplets + sparse) on the "
+              f"{n_cells}x{n_cells}-cell mesh of the same recipe (nme={m.nme}), a bounded sample of the "
+              f"2048x2048 workload")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(),
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(extra: dict | None = None) -> dict:
+    c = {"workload": f"P1 stiffness S + weighted mass M^[w], FP64, jittered node-permuted unit-square mesh "
+                     f"{N_CELLS}x{N_CELLS} cells (nq=4198401, nme=8388608, nnz=29372417 per matrix)",
+         "step": "mesh validation + pattern build + S and M^[w] values (one sparse()-equivalent call)",
+         "l2": "flushed between timed steps (512 MB write); inputs+outputs (~0.67 GB) exceed L2 too"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args) -> int:
+    import torch
+    import torch.distributed as dist
+
+    from paper_1305_3122_gb300 import feasm, meshgen
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    variant = {"atomic": feasm.ATOMIC, "gather": feasm.GATHER}[args.variant]
+
+    m = meshgen.square_mesh(N_CELLS, SEED + 1000 * rank)
+    w = meshgen.vertex_weights(m, SEED + 1000 * rank)
+    q_d = torch.tensor(m.q, device=dev)
+    me_d = torch.tensor(m.me, device=dev)
+    w_d = torch.tensor(w, device=dev)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    gather = variant == feasm.GATHER
+    mesh0 = feasm.Mesh(q_d, me_d)
+    pat0 = feasm.Pattern(mesh0, gather=gather)
+    nnz = pat0.nnz
+    S = pat0.new_values()
+    M = pat0.new_values()
+
+    def step():
+        # create, build, assemble and release: every allocation and free is inside the step
+        mesh = feasm.Mesh(q_d, me_d)
+        pat = feasm.Pattern(mesh, gather=gather)
+        feasm.assemble_stiff_wmass(mesh, pat, w_d, variant, S, M)
+        pat.close()
+        mesh.close()
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    feasm.profile_reset()
+    feasm.profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    feasm.profile_enable(False)
+    prof = feasm.profile_read()
+    if world > 1:
+        dist.barrier()
+    ms = sum(times) / len(times)
+    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms_max = float(tmax.item())
+    value = world * m.nme / (ms_max / 1e3) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    hbm, peak_kind = _peaks()
+    # dominant kernel of the step and its roofline
+    launches = sum(c for _, c in prof.values())
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    dom_bytes = algorithmic_bytes(dom, m.nq, m.nme, nnz)
+    roof = _roofline(dom, dom_bytes, dom_ms, hbm, peak_kind, args.traffic)
+
+    # assembly with a prebuilt pattern
+    asm = assemble_only(feasm, torch, mesh0, pat0, w_d, variant, S, M, flush, stream, args, m, nnz, hbm, peak_kind)
+    line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config({"variant": args.variant, "parallelism": f"replicas{world}" if world > 1 else "single"}),
+            "roofline": roof, "gpu_launches": int(launches), "clocks": clk,
+            "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 5), "launches": int(v[1]),
+                            "share": round(v[0] / sum(x[0] for x in prof.values()), 4)} for k, v in sorted(prof.items())},
+            "assemble_only": asm}
+    if not args.no_batched:
+        line["batched"] = batched(feasm, meshgen, torch, args)
+    if not args.no_e2e:
+        line["e2e"] = e2e(feasm, torch, m, w, args)
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_oracle_sample()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _roofline(name, nbytes, ms, hbm, peak_kind, traffic_path):
+    achieved = nbytes / (ms / 1e3) / 1e9 if nbytes else None
+    traffic = None
+    if traffic_path and os.path.exists(traffic_path):
+        with open(traffic_path) as f:
+            t = json.load(f)
+        traffic = t.get(name)
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
+            "traffic": traffic, "algorithmic_bytes": nbytes, "ms_per_launch": round(ms, 5),
+            "peak_source": f"{peak_kind} HBM copy bandwidth"}
+
+
+def assemble_only(feasm, torch, mesh, pat, w_d, variant, S, M, flush, stream, args, m, nnz, hbm, peak_kind):
+    for _ in range(3):
+        feasm.assemble_stiff_wmass(mesh, pat, w_d, variant, S, M)
+    feasm.profile_reset()
+    feasm.profile_enable(True)
+    times = []
+    reps = max(args.steps, 10)
+    for _ in range(reps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        feasm.assemble_stiff_wmass(mesh, pat, w_d, variant, S, M)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    feasm.profile_enable(False)
+    prof = feasm.profile_read()
+    ms = sum(times) / len(times)
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    roof = _roofline(dom, algorithmic_bytes(dom, m.nq, m.nme, nnz), dom_ms, hbm, peak_kind, args.traffic)
+    return {"value": round(m.nme / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms": round(ms, 4), "reps": reps,
+            "kernels": {k: round(v[0] / v[1], 5) for k, v in prof.items()}, "roofline": roof}
+
+
+def batched(feasm, meshgen, torch, args) -> dict:
+    seed = 13053122 + 4
+    meshes = meshgen.batch_meshes(seed)
+    fm = [feasm.Mesh(x.q, x.me) for x in meshes]
+    fp = [feasm.Pattern(x) for x in fm]
+    b = feasm.Batch(fm, fp)
+    block, tile = b.tune()
+    nme = sum(x.nme for x in meshes)
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_g = timed(b.assemble)
+    ms_p = timed(b.assemble_plain)
+    return {"meshes": len(meshes), "nme": nme, "graph_ms": round(ms_g, 4), "plain_ms": round(ms_p, 4),
+            "graph_melem_s": round(nme / ms_g / 1e3, 2), "plain_melem_s": round(nme / ms_p / 1e3, 2),
+            "speedup": round(ms_p / ms_g, 3), "shape": {"block": block, "tile": tile},
+            "what": "S + M (Eq. 1, Eq. 3) of 256 meshes, one graph-replayed persistent launch vs 256 plain launches"}
+
+
+def e2e(feasm, torch, m, w, args) -> dict:
+    """Same step from pinned host inputs to pinned host CSR outputs through feasm.assemble_host."""
+    q_h = torch.tensor(m.q).pin_memory()
+    me_h = torch.tensor(m.me).pin_memory()
+    w_h = torch.tensor(w).pin_memory()
+    pinned = {}
+    variant = {"atomic": feasm.ATOMIC, "gather": feasm.GATHER}[args.variant]
+
+    def step():
+        return feasm.assemble_host("stiff_wmass", q_h.numpy(), me_h.numpy(), w_h.numpy(), variant=variant,
+                                   pinned_out=pinned)
+
+    out = step()
+    pinned.update({k: v for k, v in out.items() if k != "nnz"})
+    for _ in range(max(args.warmup - 1, 1)):
+        step()
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out = step()
+        t.append(time.perf_counter() - t0)
+    el = sum(t) / len(t)
+    h2d = q_h.numel() * 8 + me_h.numel() * 4 + w_h.numel() * 8
+    d2h = sum(v.numel() * v.element_size() for k, v in out.items() if k != "nnz")
+    return {"value": round(m.nme / el / 1e6, 3), "unit": UNIT, "ms_per_step": round(el * 1e3, 3),
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "api": "feasm.assemble_host('stiff_wmass', ...) from pinned numpy arrays to pinned CSR arrays"}
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--variant", choices=["atomic", "gather"], default="atomic")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--traffic", default=os.path.join(ROOT, "profiles", "traffic.json"),
+                    help="per-kernel DRAM bytes per launch from an ncu capture (JSON)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)    # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -163,10 +163,14 @@ class Mesh:
     def check(self, stream=None):
         _check(lib().fe_mesh_check(self._h, _stream(stream)), "fe_mesh_check")
 
-    def __del__(self):
+    def close(self):
+        """Release the device copies now (also done on garbage collection)."""
         if getattr(self, "_h", None) and _lib is not None:
             _lib.fe_mesh_destroy(self._h)
-            self._h = None
+        self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 class Pattern:
@@ -201,10 +205,14 @@ class Pattern:
         return torch.sparse_csr_tensor(self.row_ptr.long(), self.col_idx.long(), values,
                                        size=(self.n_rows, self.n_rows))
 
-    def __del__(self):
+    def close(self):
+        """Release the pattern's device arrays now (views of them become invalid)."""
         if getattr(self, "_h", None) and _lib is not None:
             _lib.fe_pattern_destroy(self._h)
-            self._h = None
+        self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def _values(pattern: Pattern, out: torch.Tensor | None) -> torch.Tensor:
