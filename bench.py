@@ -59,7 +59,7 @@ def algorithmic_bytes(name: str, nq: int, nme: int, nnz: int) -> int | None:
         "k_scalar_atomic": 12 * nme + 16 * nq + 8 * nq + 16 * nnz,
         "k_scalar_stage": 12 * nme + 16 * nq + 8 * nq + 2 * 72 * nme,
         "k_seg_gather": 4 * (nnz + 1) + 36 * nme + 2 * 72 * nme + 16 * nnz,
-        "k_stiff_wmass_tiled": 12 * nme + 16 * nq + 8 * nq + 16 * nnz,
+        "k_row_scalar": 12 * nme + 16 * nq + 8 * nq + 16 * nnz,
         "k_validate": 12 * nme + 16 * nq,
         "k_pack_coords": 32 * nq,
         "k_count_deg": 12 * nme + 4 * nq,
@@ -213,7 +213,7 @@ def run_ours(args) -> int:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    variant = {"atomic": feasm.ATOMIC, "gather": feasm.GATHER}[args.variant]
+    variant = {"atomic": feasm.ATOMIC, "gather": feasm.GATHER, "row": feasm.ROW}[args.variant]
 
     m = meshgen.square_mesh(N_CELLS, SEED + 1000 * rank)
     w = meshgen.vertex_weights(m, SEED + 1000 * rank)
@@ -224,8 +224,9 @@ def run_ours(args) -> int:
     stream = torch.cuda.current_stream()
 
     gather = variant == feasm.GATHER
+    use_map = variant == feasm.ATOMIC
     mesh0 = feasm.Mesh(q_d, me_d)
-    pat0 = feasm.Pattern(mesh0, gather=gather)
+    pat0 = feasm.Pattern(mesh0, gather=gather, map=use_map)
     nnz = pat0.nnz
     S = pat0.new_values()
     M = pat0.new_values()
@@ -233,7 +234,7 @@ def run_ours(args) -> int:
     def step():
         # create, build, assemble and release: every allocation and free is inside the step
         mesh = feasm.Mesh(q_d, me_d)
-        pat = feasm.Pattern(mesh, gather=gather)
+        pat = feasm.Pattern(mesh, gather=gather, map=use_map)
         feasm.assemble_stiff_wmass(mesh, pat, w_d, variant, S, M)
         pat.close()
         mesh.close()
@@ -384,7 +385,7 @@ def e2e(feasm, torch, m, w, args) -> dict:
     me_h = torch.tensor(m.me).pin_memory()
     w_h = torch.tensor(w).pin_memory()
     pinned = {}
-    variant = {"atomic": feasm.ATOMIC, "gather": feasm.GATHER}[args.variant]
+    variant = {"atomic": feasm.ATOMIC, "gather": feasm.GATHER, "row": feasm.ROW}[args.variant]
 
     def step():
         return feasm.assemble_host("stiff_wmass", q_h.numpy(), me_h.numpy(), w_h.numpy(), variant=variant,
@@ -413,7 +414,7 @@ def main() -> int:
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--variant", choices=["atomic", "gather"], default="atomic")
+    ap.add_argument("--variant", choices=["atomic", "gather", "row"], default="row")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -72,18 +72,24 @@ enum { FE_PTR_HOST = 0, FE_PTR_DEVICE = 1 };
 enum {
     FE_VARIANT_ATOMIC = 0, /* element-parallel; FP64 atomicAdd into values (zeroed first).
                               Rounding of each sum depends on the order atomics land. */
-    FE_VARIANT_GATHER = 1  /* deterministic: element matrices are staged in contribution order
+    FE_VARIANT_GATHER = 1, /* deterministic: element matrices are staged in contribution order
                               c, then one thread per non-zero sums its contributions in
                               ascending c (the order of the paper's sparse() call).
                               Bit-identical from run to run. Needs FE_PATTERN_GATHER. */
+    FE_VARIANT_ROW = 2     /* deterministic and atomic-free (the fast path): one thread per CSR
+                              row walks the row's triangles in ascending order, computes the
+                              row's entries of each element matrix in double-float arithmetic
+                              (about 2^-45 of the row's largest entry from FP64) and writes each
+                              value once. Bit-identical from run to run. Any pattern. */
 };
 
 /* Pattern build flags. */
 enum {
-    FE_PATTERN_DEFAULT = 0,
-    FE_PATTERN_GATHER = 1  /* also build the per-non-zero contribution lists (seg_ptr, perm)
-                              and the vertex-to-triangle lists used by FE_VARIANT_GATHER and
-                              by the deterministic adjoint */
+    FE_PATTERN_DEFAULT = 0, /* CSR structure + the per-vertex triangle lists of FE_VARIANT_ROW */
+    FE_PATTERN_GATHER = 1,  /* also the element-to-nnz map, the per-non-zero contribution lists
+                               (seg_ptr, perm) and the staging buffer of FE_VARIANT_GATHER and
+                               of the deterministic adjoint */
+    FE_PATTERN_MAP = 2      /* also the element-to-nnz map (FE_VARIANT_ATOMIC, adjoint, batches) */
 };
 
 /* ----------------------------------------------------------------------------- meshes ---- */
@@ -103,8 +109,9 @@ fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, const int32_t
 fe_status fe_mesh_set_coords(fe_mesh mesh, const double* q, int ptr_kind, fe_stream stream);
 
 /* Reads and clears the mesh's device-side error word, set by an assembly call that met a
- * triangle with signed area <= 0 after fe_mesh_set_coords. Synchronises the stream.
- * Returns FE_OK or FE_ERR_ORIENTATION. */
+ * triangle with signed area <= 0 after fe_mesh_set_coords (FE_ERR_ORIENTATION), or, for
+ * FE_VARIANT_ROW, a nonzero edge-vector component or weight of magnitude outside
+ * [2^-74, 2^128) (FE_ERR_LIMIT; such values are then taken as zero). Synchronises the stream. */
 fe_status fe_mesh_check(fe_mesh mesh, fe_stream stream);
 
 fe_status fe_mesh_info(fe_mesh mesh, int32_t* nq, int32_t* nme);
@@ -119,7 +126,10 @@ void fe_mesh_destroy(fe_mesh mesh);
  * For dofs_per_vertex = 2 the pattern is the 2x2 block expansion of the scalar one
  * (BuildIgJgP1VF, Section 6.2). The structural half of sparse(): a counting sort of the
  * (row, col) keys on the row, then a sort of the columns inside each row, then unique.
- * flags: FE_PATTERN_DEFAULT or FE_PATTERN_GATHER. Synchronises the stream once (to learn nnz). */
+ * flags: FE_PATTERN_DEFAULT, FE_PATTERN_MAP, FE_PATTERN_GATHER (or-ed). Synchronises the
+ * stream twice (to learn the high-valence rows and nnz). Handles release their memory on the
+ * last stream they were used on (stream-ordered); work on other streams must be ordered by
+ * the caller before destroying them. */
 fe_status fe_pattern_build(fe_mesh mesh, int dofs_per_vertex, int flags, fe_stream stream,
                            fe_pattern* out);
 
@@ -128,7 +138,8 @@ fe_status fe_pattern_info(fe_pattern pattern, int64_t* n_rows, int64_t* nnz,
                           const int32_t** row_ptr, const int32_t** col_idx);
 
 /* The scalar element-to-nnz map (device, 9*nme int32, layout above). For a dofs=2 pattern this
- * is the map of the underlying scalar pattern. */
+ * is the map of the underlying scalar pattern. FE_ERR_INVALID_ARG if the pattern was built
+ * without FE_PATTERN_MAP or FE_PATTERN_GATHER. */
 fe_status fe_pattern_map(fe_pattern pattern, const int32_t** map, int64_t* len);
 
 void fe_pattern_destroy(fe_pattern pattern);
@@ -163,7 +174,8 @@ fe_status fe_assemble_elas(fe_mesh mesh, fe_pattern pattern, double lambda, doub
 
 /* --------------------------------------------------------------------------- adjoint ---- */
 
-/* Gradient of L = sum_p gS[p] * S.values[p] + sum_p gM[p] * Mw.values[p] with respect to the
+/* Needs a pattern with the element-to-nnz map (FE_PATTERN_MAP or FE_PATTERN_GATHER).
+ * Gradient of L = sum_p gS[p] * S.values[p] + sum_p gM[p] * Mw.values[p] with respect to the
  * coordinates and the vertex weights (not in the paper: the derivative of Eqs. 2-3 with the
  * area taken from the coordinates). gS, gM: device FP64 [nnz] on the scalar pattern (either
  * may be NULL for zero). Writes dq ([2][nq], same layout as q) and dw ([nq]); both are
@@ -178,7 +190,8 @@ fe_status fe_adjoint_stiff_wmass(fe_mesh mesh, fe_pattern pattern, const double*
 
 /* A batch assembles S and M (the mass matrix of Eq. 1) for n independent meshes in one
  * persistent kernel launch, replayed from a captured CUDA graph. meshes[m] / patterns[m] are
- * borrowed (they must outlive the batch); patterns are scalar. The tile size and block size
+ * borrowed (they must outlive the batch); patterns are scalar with the element-to-nnz map
+ * (FE_PATTERN_MAP). The tile size and block size
  * come from fe_batch_tune (or defaults). Not in the paper. */
 fe_status fe_batch_create(int32_t n, const fe_mesh* meshes, const fe_pattern* patterns,
                           fe_batch* out);

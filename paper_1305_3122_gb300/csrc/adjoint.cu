@@ -129,9 +129,11 @@ extern "C" fe_status fe_adjoint_stiff_wmass(fe_mesh m, fe_pattern p, const doubl
     if (variant != FE_VARIANT_ATOMIC && variant != FE_VARIANT_GATHER) return fe_fail(FE_ERR_INVALID_ARG, "unknown variant");
     if (variant == FE_VARIANT_GATHER && !(p->flags & FE_PATTERN_GATHER))
         return fe_fail(FE_ERR_INVALID_ARG, "FE_VARIANT_GATHER needs a pattern built with FE_PATTERN_GATHER");
+    if (!p->map) return fe_fail(FE_ERR_INVALID_ARG, "the adjoint needs a pattern built with FE_PATTERN_MAP");
     if (m->nq > 0 && (!dq || !dw)) return fe_fail(FE_ERR_INVALID_ARG, "dq or dw is null");
     if (gM && !w && m->nq > 0) return fe_fail(FE_ERR_INVALID_ARG, "w is null");
     cudaStream_t s = (cudaStream_t)stream;
+    m->last_stream = p->last_stream = s;
     const int32_t nq = m->nq, nme = m->nme;
     if (nq == 0) return FE_OK;
     if (variant == FE_VARIANT_ATOMIC || nme == 0) {

@@ -275,9 +275,12 @@ static fe_status check_out(fe_pattern p, const double* values, int64_t cap) {
 }
 
 static fe_status check_variant(fe_pattern p, int variant) {
-    if (variant != FE_VARIANT_ATOMIC && variant != FE_VARIANT_GATHER) return fe_fail(FE_ERR_INVALID_ARG, "unknown variant");
+    if (variant != FE_VARIANT_ATOMIC && variant != FE_VARIANT_GATHER && variant != FE_VARIANT_ROW)
+        return fe_fail(FE_ERR_INVALID_ARG, "unknown variant");
     if (variant == FE_VARIANT_GATHER && !(p->flags & FE_PATTERN_GATHER))
         return fe_fail(FE_ERR_INVALID_ARG, "FE_VARIANT_GATHER needs a pattern built with FE_PATTERN_GATHER");
+    if (variant == FE_VARIANT_ATOMIC && !p->map)
+        return fe_fail(FE_ERR_INVALID_ARG, "FE_VARIANT_ATOMIC needs a pattern built with FE_PATTERN_MAP");
     return FE_OK;
 }
 
@@ -290,6 +293,11 @@ static fe_status scalar(int kind, fe_mesh m, fe_pattern p, const double* w, int 
     if (kind == K_STIFF_WMASS && (st = check_out(p, out1, cap))) return st;
     if ((kind == K_WMASS || kind == K_STIFF_WMASS) && !w && m->nq > 0) return fe_fail(FE_ERR_INVALID_ARG, "w is null");
     const int32_t nme = m->nme;
+    m->last_stream = p->last_stream = s;
+    if (variant == FE_VARIANT_ROW) {
+        static const int bits[4] = {4, 2, 1, 3};   // K_MASS, K_WMASS, K_STIFF, K_STIFF_WMASS
+        return fe_row_scalar(bits[kind], m, p, w, out0, out1, s);
+    }
     if (variant == FE_VARIANT_ATOMIC) {
         if (p->nnz > 0) FE_CUDA(cudaMemsetAsync(out0, 0, sizeof(double) * p->nnz, s));
         if (kind == K_STIFF_WMASS && p->nnz > 0) FE_CUDA(cudaMemsetAsync(out1, 0, sizeof(double) * p->nnz, s));
@@ -350,6 +358,8 @@ extern "C" fe_status fe_assemble_elas(fe_mesh m, fe_pattern p, double lam, doubl
     if (!(lam + mu > 0.0)) return fe_fail(FE_ERR_INVALID_ARG, "Lame parameters need lambda + mu > 0");
     cudaStream_t s = (cudaStream_t)stream;
     const int32_t nme = m->nme;
+    m->last_stream = p->last_stream = s;
+    if (variant == FE_VARIANT_ROW) return fe_row_elas(m, p, lam, mu, values, s);
     if (variant == FE_VARIANT_ATOMIC) {
         if (p->nnz > 0) FE_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * p->nnz, s));
         if (nme == 0) return FE_OK;

@@ -163,6 +163,8 @@ static fe_status set_outputs(fe_batch b, double* const* S, double* const* M, cud
 
 extern "C" void fe_batch_destroy(fe_batch b) {
     if (!b) return;
+    cudaDeviceSynchronize();   // the graph may still be running on a caller's stream
+    FeStreamScope scope(nullptr);
     drop_graph(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     fe_free(b->d_desc);
@@ -177,10 +179,12 @@ extern "C" fe_status fe_batch_create(int32_t n, const fe_mesh* meshes, const fe_
     *out = nullptr;
     if (n < 0 || (n > 0 && (!meshes || !patterns))) return fe_fail(FE_ERR_INVALID_ARG, "bad mesh list");
     std::vector<MeshDesc> desc(n > 0 ? n : 1);
+    FeStreamScope scope(nullptr);
     fe_batch b = new fe_batch_s();
     b->n = n;
     for (int32_t m = 0; m < n; m++) {
         fe_status st = fe_check_pair(meshes[m], patterns[m], 1);
+        if (!st && !patterns[m]->map) st = fe_fail(FE_ERR_INVALID_ARG, "batched assembly needs patterns built with FE_PATTERN_MAP");
         if (st) { fe_batch_destroy(b); return st; }
         b->meshes.push_back(meshes[m]);
         b->patterns.push_back(patterns[m]);
@@ -208,6 +212,7 @@ extern "C" fe_status fe_batch_set_shape(fe_batch b, int32_t block, int32_t tile)
     if (block < 64 || block > 1024 || block % 32 || tile < 1) return fe_fail(FE_ERR_INVALID_ARG, "bad batch shape");
     if (block == b->block && tile == b->tile) return FE_OK;
     FE_CUDA(cudaDeviceSynchronize());   // the graph may be in flight
+    FeStreamScope scope(nullptr);
     b->block = block;
     b->tile = tile;
     fe_status st = make_tiles(b);
@@ -251,6 +256,8 @@ extern "C" fe_status fe_batch_tune(fe_batch b, double* const* S, double* const* 
     cudaStream_t s = (cudaStream_t)stream;
     fe_status st = set_outputs(b, S, M, s);
     if (st) return st;
+    FE_CUDA(cudaStreamSynchronize(s));
+    FeStreamScope scope(nullptr);
     const int blocks[] = {128, 256, 512};
     const int tiles[] = {256, 1024, 4096};
     cudaEvent_t e0, e1;

@@ -14,8 +14,11 @@ struct fe_mesh_s {
     int32_t nq = 0, nme = 0;
     double2* q = nullptr;       // [nq] (x, y) pairs: one 16-byte load per vertex gather
     int32_t* me = nullptr;      // [3][nme], the caller's layout
-    int* err = nullptr;         // device error word: bit 0 = a triangle with signed area <= 0
+    int32_t* deg = nullptr;     // [nq + 1] triangles per vertex (counted during validation)
+    int* err = nullptr;         // device error word: bit 0 = a triangle with signed area <= 0,
+                                // bit 1 = a value outside the double-float range (see ff.cuh)
     uint64_t topology_id = 0;   // identifies the connectivity (patterns remember it)
+    cudaStream_t last_stream = nullptr;   // frees are ordered on the last stream that used the handle
 };
 
 struct fe_pattern_s {
@@ -38,7 +41,23 @@ struct fe_pattern_s {
     int32_t* vptr = nullptr;              // [nq + 1] vertex -> triangle lists
     int32_t* vel = nullptr;               // [3 nme] entries 3k + a (triangle k, local vertex a), ascending k
     double* kg = nullptr;                 // staging of element values: 2 x 9 nme (dofs 1) or 36 nme (dofs 2)
+    // row-owner assembly (always)
+    int2* fan = nullptr;                  // [3 nme] per vertex: simple rows, neighbours in fan order
+                                          // (vertex, column position); general rows, sorted (j, l) pairs
+    int2* hdr = nullptr;                  // [nq] simple rows: (last neighbour, pos_self | pos_last << 14 |
+                                          // kind << 28), kind 0 closed / 1 open; kind 2 = general row
+    int32_t* gen_rows = nullptr;          // general rows (assembled one block per row)
+    int32_t n_gen = 0;
+    cudaStream_t last_stream = nullptr;
 };
+
+// longest triangle fan a simple row may have (rows with more go to the general path)
+constexpr int FE_FAN_MAX = 8;
+
+// row-owner assembly (rowasm.cu); kind bits: 1 = S, 2 = M^w, 4 = M
+fe_status fe_row_scalar(int kind_bits, fe_mesh m, fe_pattern p, const double* w, double* out0, double* out1,
+                        cudaStream_t s);
+fe_status fe_row_elas(fe_mesh m, fe_pattern p, double lam, double mu, double* out, cudaStream_t s);
 
 struct fe_batch_s;   // batch.cu
 
@@ -58,6 +77,15 @@ fe_status fe_cuda_fail(cudaError_t e, const char* what);
         cudaError_t fe_e_ = cudaGetLastError();                           \
         if (fe_e_ != cudaSuccess) return fe_cuda_fail(fe_e_, name);       \
     } while (0)
+
+// Device memory comes from a library-owned stream-ordered pool (cudaMallocFromPoolAsync) that
+// keeps freed blocks for reuse, so building and destroying handles does not synchronise the
+// device. Allocations and frees are ordered on the stream of the innermost FeStreamScope.
+struct FeStreamScope {
+    explicit FeStreamScope(cudaStream_t s);
+    ~FeStreamScope();
+    cudaStream_t prev;
+};
 
 // Device allocation helpers; return FE_ERR_OOM with a message on failure.
 fe_status fe_alloc(void** p, size_t bytes, const char* what);

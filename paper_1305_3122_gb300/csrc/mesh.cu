@@ -18,21 +18,55 @@ __global__ void k_pack_coords(const double* __restrict__ q, int32_t nq, double2*
 // Validation word layout: [0] = OR of error bits, [1] = first bad triangle (min), per kind.
 enum { BAD_RANGE = 1, BAD_REPEAT = 2, BAD_ORIENT = 4 };
 
+// High float (top 24 significant bits, truncated) of a double, by bit operations: no FP64
+// instruction. |result - x| < 2^-23 |x|; zero and subnormals give zero.
+__device__ __forceinline__ float trunc_float(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    int e = (int)((hi >> 20) & 0x7FF) - 1023;
+    if (e < -126) return 0.0f;
+    if (e > 127) return __uint_as_float((hi & 0x80000000u) | 0x7F800000u);   // +-inf: forces the exact path
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned)(e + 127) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
+// Every triangle: vertex ids in range, three distinct vertices, counter-clockwise. The sign of
+// D = (p1 - p0) x (p2 - p0) is first taken from truncated-float coordinates; the float result is
+// trusted when it exceeds a bound on its error (coordinate truncation 2^-23 |p|, float rounding of
+// the differences and products), otherwise D is recomputed in FP64 from edge vectors
+// v = p2 - p0, w = p0 - p1 as the oracle does. Also counts each vertex's triangles (the row digit
+// of the pattern build's counting sort), so a pattern build can skip that pass.
 __global__ void k_validate(const double2* __restrict__ q, int32_t nq, const int32_t* __restrict__ me,
-                           int32_t nme, int* __restrict__ word) {
+                           int32_t nme, int* __restrict__ word, int32_t* __restrict__ deg) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
         int32_t v0 = me[k], v1 = me[nme + k], v2 = me[2 * (int64_t)nme + k];
         int bad = 0;
         if (v0 < 0 || v0 >= nq || v1 < 0 || v1 >= nq || v2 < 0 || v2 >= nq) {
             bad = BAD_RANGE;
-        } else if (v0 == v1 || v1 == v2 || v0 == v2) {
-            bad = BAD_REPEAT;
         } else {
-            double2 p0 = q[v0], p1 = q[v1], p2 = q[v2];
-            // twice the signed area from the edge vectors v = p2 - p0 and w = p0 - p1
-            double vx = p2.x - p0.x, vy = p2.y - p0.y, wx = p0.x - p1.x, wy = p0.y - p1.y;
-            double D = vx * wy - wx * vy;
-            if (!(D > 0.0)) bad = BAD_ORIENT;
+            atomicAdd(&deg[v0], 1);
+            atomicAdd(&deg[v1], 1);
+            atomicAdd(&deg[v2], 1);
+            if (v0 == v1 || v1 == v2 || v0 == v2) {
+                bad = BAD_REPEAT;
+            } else {
+                double2 p0 = q[v0], p1 = q[v1], p2 = q[v2];
+                float x0 = trunc_float(p0.x), y0 = trunc_float(p0.y);
+                float ax = trunc_float(p1.x) - x0, ay = trunc_float(p1.y) - y0;
+                float bx = trunc_float(p2.x) - x0, by = trunc_float(p2.y) - y0;
+                float Df = ax * by - ay * bx;
+                float M = fmaxf(fmaxf(fmaxf(fabsf(x0), fabsf(y0)), fmaxf(fabsf(ax), fabsf(ay))),
+                                fmaxf(fabsf(bx), fabsf(by)));
+                float err = 3.0e-6f * M * (fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by));   // > 2^-19 bound
+                bool sure = fabsf(Df) > err && M < 1e18f && M > 1e-18f;
+                bool pos;
+                if (sure) {
+                    pos = Df > 0.0f;
+                } else {
+                    double vx = p2.x - p0.x, vy = p2.y - p0.y, wx = p0.x - p1.x, wy = p0.y - p1.y;
+                    pos = vx * wy - wx * vy > 0.0;
+                }
+                if (!pos) bad = BAD_ORIENT;
+            }
         }
         if (bad) {
             atomicOr(&word[0], bad);
@@ -73,9 +107,11 @@ static fe_status set_coords(fe_mesh m, const double* q, int ptr_kind, cudaStream
 
 extern "C" void fe_mesh_destroy(fe_mesh m) {
     if (!m) return;
+    FeStreamScope scope(m->last_stream);
     fe_free(m->q);
     fe_free(m->me);
     fe_free(m->err);
+    fe_free(m->deg);
     delete m;
 }
 
@@ -86,24 +122,28 @@ extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, co
     if (nq < 0 || nme < 0) return fe_fail(FE_ERR_INVALID_ARG, "nq and nme must be >= 0");
     if ((nq > 0 && !q) || (nme > 0 && !me)) return fe_fail(FE_ERR_INVALID_ARG, "q or me is null");
     if (ptr_kind != FE_PTR_HOST && ptr_kind != FE_PTR_DEVICE) return fe_fail(FE_ERR_INVALID_ARG, "bad ptr_kind");
-    if ((int64_t)nme * 36 >= INT32_MAX && (int64_t)nme * 9 >= INT32_MAX)
+    if ((int64_t)nme * 9 >= INT32_MAX)
         return fe_fail(FE_ERR_LIMIT, "9*nme must be < 2^31");
     cudaStream_t s = (cudaStream_t)stream;
+    FeStreamScope scope(s);
     fe_mesh m = new fe_mesh_s();
+    m->last_stream = s;
     m->nq = nq;
     m->nme = nme;
     m->topology_id = g_topology_counter.fetch_add(1);
     fe_status st = fe_alloc_n(&m->q, (size_t)nq, "mesh coordinates");
     if (!st) st = fe_alloc_n(&m->me, 3 * (size_t)nme, "mesh connectivity");
     if (!st) st = fe_alloc_n(&m->err, 4, "mesh error word");
+    if (!st) st = fe_alloc_n(&m->deg, (size_t)nq + 1, "vertex valences");
     if (!st) st = copy_in(m->me, me, 3 * (size_t)nme * sizeof(int32_t), ptr_kind, s);
     if (!st) st = set_coords(m, q, ptr_kind, s);
     if (st) { fe_mesh_destroy(m); return st; }
     int init[4] = {0, INT32_MAX, INT32_MAX, INT32_MAX};
     int word[4];
     cudaError_t e = cudaMemcpyAsync(m->err, init, sizeof init, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->deg, 0, sizeof(int32_t) * ((size_t)nq + 1), s);
     if (e == cudaSuccess && nme > 0) {
-        { FE_PROF("k_validate", s); k_validate<<<fe_grid(nme, 256), 256, 0, s>>>(m->q, nq, m->me, nme, m->err); }
+        { FE_PROF("k_validate", s); k_validate<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg); }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(word, m->err, sizeof word, cudaMemcpyDeviceToHost, s);
@@ -130,6 +170,8 @@ extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, co
 extern "C" fe_status fe_mesh_set_coords(fe_mesh m, const double* q, int ptr_kind, fe_stream stream) {
     if (!m || (m->nq > 0 && !q)) return fe_fail(FE_ERR_INVALID_ARG, "null mesh or q");
     if (ptr_kind != FE_PTR_HOST && ptr_kind != FE_PTR_DEVICE) return fe_fail(FE_ERR_INVALID_ARG, "bad ptr_kind");
+    FeStreamScope scope((cudaStream_t)stream);
+    m->last_stream = (cudaStream_t)stream;
     return set_coords(m, q, ptr_kind, (cudaStream_t)stream);
 }
 
@@ -140,7 +182,11 @@ extern "C" fe_status fe_mesh_check(fe_mesh m, fe_stream stream) {
     FE_CUDA(cudaMemcpyAsync(&word, m->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaStreamSynchronize(s));
     FE_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int), s));
-    if (word) return fe_fail(FE_ERR_ORIENTATION, "an assembly call met a triangle with signed area <= 0");
+    // a value out of the double-float range is reported first: it also makes areas look <= 0
+    if (word & 2)
+        return fe_fail(FE_ERR_LIMIT, "an edge-vector component or a weight is outside the double-float range "
+                                     "(nonzero magnitudes must lie in [2^-74, 2^128))");
+    if (word & 1) return fe_fail(FE_ERR_ORIENTATION, "an assembly call met a triangle with signed area <= 0");
     return FE_OK;
 }
 

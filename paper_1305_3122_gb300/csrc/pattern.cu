@@ -1,43 +1,68 @@
-// pattern.cu -- the structural half of sparse(Ig, Jg, Kg): CSR structure + element-to-nnz map.
+// pattern.cu -- the structural half of sparse(Ig, Jg, Kg): CSR structure, triangle fans, map.
 //
 // The paper forms Ig = me([1 2 3 1 2 3 1 2 3], :) and Jg = me([1 1 1 2 2 2 3 3 3], :)
 // (Section 5, Remark 5.1) and lets sparse() sort the 9*nme (row, col) keys and merge equal
 // ones (Section 4). Here the keys are sorted by a two-level (most-significant-digit first)
 // radix sort that exploits their shape: the row digit is a counting sort (each triangle drops
 // its two other vertices into the bucket of each of its vertices), and the column digit is
-// sorted inside each row bucket, where a row holds only 2*valence+1 keys. Unique keys give
-// row_ptr / col_idx; each triangle then resolves its 9 keys to storage positions once (map),
-// so an assembly call never sorts.
+// sorted inside each row bucket, which holds only 2*valence+1 keys. Unique keys give
+// row_ptr / col_idx.
 //
-// Row buckets with more than FAST_DEG triangles (rare: high-valence vertices) are handled by
-// one thread block per row in shared memory.
+// For the row-owner assembly (rowasm.cu) the build also orders each vertex's triangles around
+// it: triangle (i, j, l) is counter-clockwise, so in a manifold mesh the triangles around i form
+// one chain in which each triangle's l is the next one's j ("fan"; closed for interior vertices,
+// open on the boundary). A row whose triangles form one such chain with at most FAN_MAX
+// triangles is "simple": it stores its neighbours n_0 .. n_{d-1} in fan order with their column
+// positions, plus the last neighbour n_d (n_d = n_0 when closed). Any other row (higher valence,
+// several chains, an edge shared by more than two triangles) is "general": it stores its
+// (j, l) pairs sorted, and is assembled by a block-per-row kernel.
+//
+// On request the build also resolves every triangle's 9 keys to storage positions (the
+// element-to-nnz map, FE_PATTERN_MAP) and, for FE_PATTERN_GATHER, the per-non-zero lists of
+// contributions c = 9k + 3*jl + il in ascending order (seg_ptr, perm).
 #include <string>
 
 #include "internal.cuh"
 
-static constexpr int FAST_DEG = 32;
+static constexpr int FAST_DEG = 32;    // rows with more triangles are handled by one block each
 static constexpr int BIG_BLOCK = 256;
+static constexpr int FAN_MAX = FE_FAN_MAX;   // longest fan the simple-row path handles in registers
 
-__global__ void k_count_deg(const int32_t* __restrict__ me, int64_t n3, int32_t* __restrict__ deg) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n3; t += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&deg[me[t]], 1);
-}
+enum { KIND_CLOSED = 0, KIND_OPEN = 1, KIND_GENERAL = 2 };
 
-// Bucket entry for vertex v of triangle k at local index a: the two other vertices, and
-// (optionally) the triangle/local id 3k + a.
-__global__ void k_fill_adj(const int32_t* __restrict__ me, int32_t nme, const int32_t* __restrict__ vptr,
-                           int32_t* __restrict__ cur, int2* __restrict__ adj, int32_t* __restrict__ vel) {
-    int64_t n3 = 3 * (int64_t)nme;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n3; t += (int64_t)gridDim.x * blockDim.x) {
-        int a = (int)(t / nme);
-        int32_t k = (int32_t)(t - (int64_t)a * nme);
-        int32_t v = me[t];
-        int a1 = a == 2 ? 0 : a + 1, a2 = a == 0 ? 2 : a - 1;
-        int32_t slot = vptr[v] + atomicAdd(&cur[v], 1);
-        adj[slot] = make_int2(me[(int64_t)a1 * nme + k], me[(int64_t)a2 * nme + k]);
-        if (vel) vel[slot] = 3 * k + a;
+// ------------------------------------------------------------------ row digit (counting sort)
+
+__global__ void k_count_deg(const int32_t* __restrict__ me, int32_t nme, int32_t* __restrict__ deg) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
+        atomicAdd(&deg[me[k]], 1);
+        atomicAdd(&deg[me[nme + k]], 1);
+        atomicAdd(&deg[me[2 * (int64_t)nme + k]], 1);
     }
 }
+
+// Bucket entries of triangle k: for its vertex a, the two other vertices in counter-clockwise
+// order (and, for the staged gather, the triangle/local id 3k + a). One thread handles the three
+// vertices of a triangle, so the writes into a vertex's bucket come from nearby triangles and
+// merge in L2.
+__global__ void k_fill_adj(const int32_t* __restrict__ me, int32_t nme, const int32_t* __restrict__ vptr,
+                           int32_t* __restrict__ cur, int2* __restrict__ adj, int32_t* __restrict__ vel) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v[3] = {me[k], me[nme + k], me[2 * (int64_t)nme + k]};
+        int32_t slot[3];
+        // the three cursor bumps are independent: issue them (and the bucket starts) together
+#pragma unroll
+        for (int a = 0; a < 3; a++) slot[a] = atomicAdd(&cur[v[a]], 1);
+#pragma unroll
+        for (int a = 0; a < 3; a++) slot[a] += vptr[v[a]];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            adj[slot[a]] = make_int2(v[(a + 1) % 3], v[(a + 2) % 3]);
+            if (vel) vel[slot[a]] = 3 * (int32_t)k + a;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ column digit, general rows
 
 __device__ __forceinline__ void isort32(int32_t* x, int n) {
     for (int i = 1; i < n; i++) {
@@ -75,25 +100,171 @@ __device__ __forceinline__ int row_columns(int32_t i, int32_t beg, int32_t d, co
     return u;
 }
 
+// ------------------------------------------------------------------ fans (simple rows)
+
+struct Fan {
+    int32_t J[FAN_MAX], L[FAN_MAX];
+    int d;
+};
+
+__device__ __forceinline__ void load_fan(const int2* __restrict__ adj, int32_t beg, int d, Fan& f) {
+    f.d = d;
+#pragma unroll
+    for (int e = 0; e < FAN_MAX; e++) {
+        int2 p = e < d ? adj[beg + e] : make_int2(-1, -2);
+        f.J[e] = p.x;
+        f.L[e] = p.y;
+    }
+}
+
+// Analyses the fan: returns KIND_CLOSED / KIND_OPEN for one chain through all d triangles with
+// distinct j's and distinct l's, else KIND_GENERAL. start = first triangle of the chain (for a
+// closed fan, the one with the smallest j, so the order does not depend on the bucket order).
+__device__ __forceinline__ int fan_kind(const Fan& f, int& start) {
+    int nstart = 0, dup = 0, minj = INT32_MAX, minj_e = 0;
+    start = 0;
+#pragma unroll
+    for (int e = 0; e < FAN_MAX; e++) {
+        if (e >= f.d) continue;
+        bool is_l = false;
+#pragma unroll
+        for (int g = 0; g < FAN_MAX; g++) {
+            if (g >= f.d) continue;
+            is_l |= f.L[g] == f.J[e];
+            if (g > e) dup |= (f.J[g] == f.J[e]) | (f.L[g] == f.L[e]);
+        }
+        if (!is_l) { nstart++; start = e; }
+        if (f.J[e] < minj) { minj = f.J[e]; minj_e = e; }
+    }
+    if (dup || nstart > 1) return KIND_GENERAL;
+    if (nstart == 0) start = minj_e;
+    // follow the chain: it must visit every triangle once before closing (or ending)
+    int32_t jstart = 0, lcur = 0;
+#pragma unroll
+    for (int e = 0; e < FAN_MAX; e++)
+        if (e == start) { jstart = f.J[e]; lcur = f.L[e]; }
+    for (int s = 1; s < f.d; s++) {
+        bool found = false;
+        int32_t lnext = 0;
+#pragma unroll
+        for (int e = 0; e < FAN_MAX; e++)
+            if (e < f.d && f.J[e] == lcur) { found = true; lnext = f.L[e]; }
+        if (!found || lcur == jstart) return KIND_GENERAL;   // chain broken, or closed before the end
+        lcur = lnext;
+    }
+    if (nstart == 0) return lcur == jstart ? KIND_CLOSED : KIND_GENERAL;
+    return KIND_OPEN;
+}
+
+// Column position of vertex x in the row of vertex i with fan f (kind closed/open, last
+// neighbour lend): the number of row entries below x.
+__device__ __forceinline__ int fan_pos(const Fan& f, int32_t i, int kind, int32_t lend, int32_t x) {
+    int p = (i < x) + (kind == KIND_OPEN && lend < x);
+#pragma unroll
+    for (int e = 0; e < FAN_MAX; e++) p += (e < f.d && f.J[e] < x);
+    return p;
+}
+
+// Row counts: simple rows from the fan analysis (closed: d + 1 entries, open: d + 2); general
+// rows by sorting; rows with more than FAST_DEG triangles are listed for the block kernels.
 __global__ void k_row_count(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t nq,
-                            int32_t* __restrict__ row_nnz, int32_t* __restrict__ big_list,
-                            int32_t* __restrict__ big_count, int* __restrict__ too_big) {
-    int32_t cols[2 * FAST_DEG + 1];
+                            int32_t* __restrict__ row_nnz, unsigned char* __restrict__ kind_out,
+                            int32_t* __restrict__ big_list, int32_t* __restrict__ big_count, int* __restrict__ too_big) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = (int32_t)r;
         int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+        if (d == 0) { row_nnz[i] = 0; kind_out[i] = KIND_GENERAL; continue; }
+        if (d <= FAN_MAX) {
+            Fan f;
+            load_fan(adj, beg, d, f);
+            int start;
+            int kind = fan_kind(f, start);
+            if (kind != KIND_GENERAL) {
+                row_nnz[i] = d + 1 + (kind == KIND_OPEN);
+                kind_out[i] = (unsigned char)kind;
+                continue;
+            }
+        }
+        kind_out[i] = KIND_GENERAL;
         if (d > FAST_DEG) {
             if (d > FE_MAX_VALENCE) { *too_big = 1; row_nnz[i] = 0; continue; }
             big_list[atomicAdd(big_count, 1)] = i;
             continue;
         }
+        int32_t cols[2 * FAST_DEG + 1];
         row_nnz[i] = row_columns(i, beg, d, adj, cols);
     }
 }
 
-// One block per high-valence row: the 2d+1 columns go to shared memory; pass 1 flags the
-// first occurrence of each value, pass 2 places each first occurrence at its rank among the
-// distinct values (O(n^2) work per row, shared among the block's threads).
+// Row fill for rows with at most FAST_DEG triangles. Simple rows: fan-ordered neighbours with
+// their positions (fan[beg + e] = (n_e, pos(n_e))), header (n_d, pos_self | pos_nd << 14 |
+// kind << 28) and col_idx. General rows: sorted unique columns, their (j, l) pairs sorted
+// lexicographically (a deterministic order) and a place in the general-row list.
+__global__ void k_row_fill(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t nq,
+                           const unsigned char* __restrict__ kinds, const int32_t* __restrict__ row_ptr,
+                           int32_t* __restrict__ col_idx, int2* __restrict__ fan, int2* __restrict__ hdr,
+                           int32_t* __restrict__ gen_list, int32_t* __restrict__ gen_count) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = (int32_t)r;
+        int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+        int kind = kinds[i];
+        int32_t o = row_ptr[i];
+        if (kind != KIND_GENERAL) {
+            Fan f;
+            load_fan(adj, beg, d, f);
+            int start;
+            fan_kind(f, start);
+            int32_t jcur = 0, lcur = 0;
+#pragma unroll
+            for (int e = 0; e < FAN_MAX; e++)
+                if (e == start) { jcur = f.J[e]; lcur = f.L[e]; }
+            // the last neighbour: follow the chain to its end
+            int32_t lend = lcur;
+            for (int s = 1; s < d; s++) {
+                int32_t nl = lend;
+#pragma unroll
+                for (int e = 0; e < FAN_MAX; e++)
+                    if (e < d && f.J[e] == lend) nl = f.L[e];
+                lend = nl;
+            }
+            int pself = fan_pos(f, i, kind, lend, i);
+            int pend = fan_pos(f, i, kind, lend, lend);
+            col_idx[o + pself] = i;
+            if (kind == KIND_OPEN) col_idx[o + pend] = lend;
+            for (int s = 0; s < d; s++) {
+                int pj = fan_pos(f, i, kind, lend, jcur);
+                fan[beg + s] = make_int2(jcur, pj);
+                col_idx[o + pj] = jcur;
+                int32_t nl = lcur;
+#pragma unroll
+                for (int e = 0; e < FAN_MAX; e++)
+                    if (e < d && f.J[e] == lcur) nl = f.L[e];
+                jcur = lcur;
+                lcur = nl;
+            }
+            hdr[i] = make_int2(lend, pself | (pend << 14) | (kind << 28));
+            continue;
+        }
+        hdr[i] = make_int2(-1, KIND_GENERAL << 28);
+        if (d == 0 || d > FAST_DEG) continue;
+        int32_t cols[2 * FAST_DEG + 1];
+        int u = row_columns(i, beg, d, adj, cols);
+        for (int t = 0; t < u; t++) col_idx[o + t] = cols[t];
+        long long key[FAST_DEG];
+        for (int32_t s = 0; s < d; s++) {
+            int2 p = adj[beg + s];
+            key[s] = ((long long)p.x << 32) | (unsigned)p.y;
+        }
+        isort64(key, d);
+        for (int32_t s = 0; s < d; s++) fan[beg + s] = make_int2((int32_t)(key[s] >> 32), (int32_t)(key[s] & 0xffffffffLL));
+        gen_list[atomicAdd(gen_count, 1)] = i;
+    }
+}
+
+// ------------------------------------------------------------------ high-valence rows
+
+// One block per row: the 2d+1 columns go to shared memory; pass 1 flags the first occurrence
+// of each value, pass 2 places each first occurrence at its rank among the distinct values.
 __global__ void k_row_big(const int32_t* __restrict__ big_list, const int32_t* __restrict__ vptr,
                           const int2* __restrict__ adj, const int32_t* __restrict__ row_ptr,
                           int32_t* __restrict__ row_nnz, int32_t* __restrict__ col_idx) {
@@ -130,6 +301,32 @@ __global__ void k_row_big(const int32_t* __restrict__ big_list, const int32_t* _
     if (threadIdx.x == 0 && row_nnz) row_nnz[i] = cnt;
 }
 
+// (j, l) pairs of a high-valence row in lexicographic order (rank of each 64-bit key).
+__global__ void k_row_big_pairs(const int32_t* __restrict__ big_list, const int32_t* __restrict__ vptr,
+                                const int2* __restrict__ adj, int2* __restrict__ fan, int2* __restrict__ hdr,
+                                int32_t* __restrict__ gen_list, int32_t* __restrict__ gen_count) {
+    extern __shared__ long long sk[];
+    int32_t i = big_list[blockIdx.x];
+    int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+    for (int s = threadIdx.x; s < d; s += blockDim.x) {
+        int2 p = adj[beg + s];
+        sk[s] = ((long long)p.x << 32) | (unsigned)p.y;
+    }
+    if (threadIdx.x == 0) {
+        hdr[i] = make_int2(-1, KIND_GENERAL << 28);
+        gen_list[atomicAdd(gen_count, 1)] = i;
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < d; s += blockDim.x) {
+        long long v = sk[s];
+        int rank = 0;
+        for (int t = 0; t < d; t++) rank += sk[t] < v;
+        fan[beg + rank] = make_int2((int32_t)(v >> 32), (int32_t)(v & 0xffffffffLL));
+    }
+}
+
+// ------------------------------------------------------------------ staged-gather lists
+
 // Contribution keys of row i: (col << 32 | c) for each of the 3 local columns of each triangle
 // containing i, where c = 9k + 3*b + a (a = local index of i, b = local index of the column).
 __device__ __forceinline__ void contrib_key(int32_t i, int2 p, int32_t e, long long out[3]) {
@@ -142,46 +339,40 @@ __device__ __forceinline__ void contrib_key(int32_t i, int2 p, int32_t e, long l
     out[2] = ((long long)p.y << 32) | (base + 3 * a2);
 }
 
-__global__ void k_row_fill(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t* __restrict__ vel,
-                           int32_t nq, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx,
-                           int32_t* __restrict__ seg_ptr, int32_t* __restrict__ perm) {
-    int32_t cols[2 * FAST_DEG + 1];
+// Per non-zero, its contributions in ascending c (perm, grouped by seg_ptr), and the row's
+// triangle list sorted by triangle (vel), for rows with at most FAST_DEG triangles.
+__global__ void k_row_perm(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t* __restrict__ vel,
+                           int32_t nq, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ seg_ptr,
+                           int32_t* __restrict__ perm) {
     long long keys[3 * FAST_DEG];
+    int32_t ev[FAST_DEG];
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = (int32_t)r;
         int32_t beg = vptr[i], d = vptr[i + 1] - beg;
-        if (d > FAST_DEG) continue;
-        int u = row_columns(i, beg, d, adj, cols);
-        int32_t o = row_ptr[i];
-        for (int t = 0; t < u; t++) col_idx[o + t] = cols[t];
-        if (!perm) continue;
+        if (d == 0 || d > FAST_DEG) continue;
         int n = 0;
         for (int32_t s = 0; s < d; s++) {
-            contrib_key(i, adj[beg + s], vel[beg + s], keys + n);
+            ev[s] = vel[beg + s];
+            contrib_key(i, adj[beg + s], ev[s], keys + n);
             n += 3;
         }
         isort64(keys, n);
+        int32_t o = row_ptr[i];
         int32_t cbase = 3 * beg;   // this row's contributions occupy perm[3*vptr[i] .. 3*vptr[i+1])
         int t = 0;
         for (int s = 0; s < n; s++) {
             if (s == 0 || (keys[s] >> 32) != (keys[s - 1] >> 32)) seg_ptr[o + t++] = cbase + s;
             perm[cbase + s] = (int32_t)(keys[s] & 0xffffffffLL);
         }
-        // the row's triangle list in ascending triangle order (used by deterministic gathers)
-        for (int32_t s = 1; s < d; s++) {
-            int32_t v = vel[beg + s];
-            int32_t j = s - 1;
-            while (j >= 0 && vel[beg + j] > v) { vel[beg + j + 1] = vel[beg + j]; j--; }
-            vel[beg + j + 1] = v;
-        }
+        isort32(ev, d);
+        for (int32_t s = 0; s < d; s++) vel[beg + s] = ev[s];
     }
 }
 
-// Contribution lists of a high-valence row, one block per row: 3d keys in shared memory
-// (distinct, since c is unique). Pass 1: each key's rank among all keys gives its perm slot,
-// and a key is the head of its column's segment if no smaller key has the same column.
-// Pass 2: each head's rank among the heads is its column's position in the row. The row's
-// triangle list is reordered by rank too (ascending triangle id).
+// The same for a high-valence row, one block per row: 3d keys in shared memory (distinct, since
+// c is unique). Pass 1: each key's rank among all keys gives its perm slot, and a key heads its
+// column's segment if no smaller key has the same column. Pass 2: each head's rank among the
+// heads is its column's position in the row. The row's triangle list is reordered by rank too.
 __global__ void k_row_big_perm(const int32_t* __restrict__ big_list, const int32_t* __restrict__ vptr,
                                const int2* __restrict__ adj, int32_t* __restrict__ vel,
                                const int32_t* __restrict__ row_ptr, int32_t* __restrict__ seg_ptr,
@@ -232,6 +423,8 @@ __global__ void k_row_big_perm(const int32_t* __restrict__ big_list, const int32
     }
     for (int s = threadIdx.x; s < d; s += blockDim.x) vel[beg + s] = vsort[s];
 }
+
+// ------------------------------------------------------------------ element-to-nnz map
 
 // map[9k + 3b + a] = position of (me[a][k], me[b][k]); staged through shared memory so the
 // 9 entries of consecutive triangles leave as one contiguous, coalesced block.
@@ -285,21 +478,27 @@ __global__ void k_expand(const int32_t* __restrict__ row_ptr, const int32_t* __r
 
 __global__ void k_set_last(int32_t* p, int32_t v) { *p = v; }
 
+// ------------------------------------------------------------------ driver
+
 extern "C" void fe_pattern_destroy(fe_pattern p) {
     if (!p) return;
+    FeStreamScope scope(p->last_stream);
     fe_free(p->row_ptr); fe_free(p->col_idx); fe_free(p->map);
     fe_free(p->row_ptr2); fe_free(p->col_idx2);
     fe_free(p->seg_ptr); fe_free(p->perm); fe_free(p->vptr); fe_free(p->vel); fe_free(p->kg);
+    fe_free(p->fan); fe_free(p->hdr); fe_free(p->gen_rows);
     delete p;
 }
 
 namespace {
 struct Temps {
-    int32_t *deg = nullptr, *cur = nullptr, *row_nnz = nullptr, *big_list = nullptr, *big_count = nullptr;
+    int32_t *deg = nullptr, *cur = nullptr, *row_nnz = nullptr, *big_list = nullptr, *counters = nullptr;
     int* flag = nullptr;
     int2* adj = nullptr;
+    unsigned char* kinds = nullptr;
     ~Temps() {
-        fe_free(deg); fe_free(cur); fe_free(row_nnz); fe_free(big_list); fe_free(big_count); fe_free(flag); fe_free(adj);
+        fe_free(deg); fe_free(cur); fe_free(row_nnz); fe_free(big_list); fe_free(counters); fe_free(flag);
+        fe_free(adj); fe_free(kinds);
     }
 };
 }  // namespace
@@ -308,45 +507,55 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     const int32_t nq = m->nq, nme = m->nme;
     const int64_t n3 = 3 * (int64_t)nme;
     const bool gather = flags & FE_PATTERN_GATHER;
+    const bool want_map = gather || (flags & FE_PATTERN_MAP);
     Temps t;
     fe_status st;
     if ((st = fe_alloc_n(&p->row_ptr, (size_t)nq + 1, "row_ptr"))) return st;
     if ((st = fe_alloc_n(&p->vptr, (size_t)nq + 1, "vertex pointers"))) return st;
+    if ((st = fe_alloc_n(&p->fan, (size_t)n3, "row fans"))) return st;
+    if ((st = fe_alloc_n(&p->hdr, (size_t)nq, "row fan headers"))) return st;
+    if ((st = fe_alloc_n(&p->gen_rows, (size_t)nq + 1, "general-row list"))) return st;
     if ((st = fe_alloc_n(&t.deg, (size_t)nq + 1, "valences"))) return st;
     if ((st = fe_alloc_n(&t.cur, (size_t)nq + 1, "bucket cursors"))) return st;
     if ((st = fe_alloc_n(&t.row_nnz, (size_t)nq + 1, "row counts"))) return st;
+    if ((st = fe_alloc_n(&t.kinds, (size_t)nq + 1, "row kinds"))) return st;
     if ((st = fe_alloc_n(&t.big_list, (size_t)nq + 1, "high-valence rows"))) return st;
-    if ((st = fe_alloc_n(&t.big_count, 1, "counter"))) return st;
+    if ((st = fe_alloc_n(&t.counters, 2, "counters"))) return st;
     if ((st = fe_alloc_n(&t.flag, 2, "flags"))) return st;
     if ((st = fe_alloc_n(&t.adj, (size_t)n3, "row buckets"))) return st;
     if (gather && (st = fe_alloc_n(&p->vel, (size_t)n3, "vertex-to-triangle lists"))) return st;
     FE_CUDA(cudaMemsetAsync(t.deg, 0, sizeof(int32_t) * ((size_t)nq + 1), s));
     FE_CUDA(cudaMemsetAsync(t.cur, 0, sizeof(int32_t) * ((size_t)nq + 1), s));
-    FE_CUDA(cudaMemsetAsync(t.row_nnz, 0, sizeof(int32_t) * ((size_t)nq + 1), s));
-    FE_CUDA(cudaMemsetAsync(t.big_count, 0, sizeof(int32_t), s));
+    FE_CUDA(cudaMemsetAsync(t.counters, 0, 2 * sizeof(int32_t), s));
     FE_CUDA(cudaMemsetAsync(t.flag, 0, 2 * sizeof(int), s));
 
-    // row digit: counting sort of the 3 nme (vertex, triangle) incidences
-    if (n3 > 0) {
-        { FE_PROF("k_count_deg", s); k_count_deg<<<fe_grid(n3, 256), 256, 0, s>>>(m->me, n3, t.deg); }
-        FE_LAUNCHED("k_count_deg");
+    // row digit: counting sort of the 3 nme (vertex, triangle) incidences; the counts come with
+    // the mesh (its validation counted them)
+    const int32_t* deg = m->deg;
+    if (!deg) {
+        if (nme > 0) {
+            { FE_PROF("k_count_deg", s); k_count_deg<<<fe_grid(nme, 256), 256, 0, s>>>(m->me, nme, t.deg); }
+            FE_LAUNCHED("k_count_deg");
+        }
+        deg = t.deg;
     }
     int64_t tot = 0;
-    if ((st = fe_exclusive_scan(t.deg, p->vptr, nq, s, nullptr))) return st;
-    if (n3 > 0) {
-        { FE_PROF("k_fill_adj", s); k_fill_adj<<<fe_grid(n3, 256), 256, 0, s>>>(m->me, nme, p->vptr, t.cur, t.adj, p->vel); }
+    if ((st = fe_exclusive_scan(deg, p->vptr, nq, s, nullptr))) return st;
+    if (nme > 0) {
+        { FE_PROF("k_fill_adj", s); k_fill_adj<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->me, nme, p->vptr, t.cur, t.adj, p->vel); }
         FE_LAUNCHED("k_fill_adj");
     }
     // column digit inside each row, unique
     if (nq > 0) {
-        { FE_PROF("k_row_count", s); k_row_count<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, t.adj, nq, t.row_nnz, t.big_list, t.big_count, t.flag); }
+        { FE_PROF("k_row_count", s); k_row_count<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, t.adj, nq, t.row_nnz, t.kinds, t.big_list, t.counters, t.flag); }
         FE_LAUNCHED("k_row_count");
     }
     int host_flags[2] = {0, 0};
-    int32_t nbig = 0;
+    int32_t host_counts[2] = {0, 0};
     FE_CUDA(cudaMemcpyAsync(host_flags, t.flag, sizeof host_flags, cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaMemcpyAsync(&nbig, t.big_count, sizeof nbig, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemcpyAsync(host_counts, t.counters, sizeof host_counts, cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaStreamSynchronize(s));
+    const int32_t nbig = host_counts[0];
     if (host_flags[0])
         return fe_fail(FE_ERR_LIMIT, "a vertex belongs to more than FE_MAX_VALENCE=" + std::to_string(FE_MAX_VALENCE) + " triangles");
     size_t big_smem = (2 * (size_t)FE_MAX_VALENCE + 1) * (sizeof(int32_t) + 1);
@@ -357,19 +566,27 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     if ((st = fe_exclusive_scan(t.row_nnz, p->row_ptr, nq, s, &tot))) return st;
     p->nnz_scalar = tot;
     if ((st = fe_alloc_n(&p->col_idx, (size_t)tot, "col_idx"))) return st;
-    if ((st = fe_alloc_n(&p->map, 9 * (size_t)nme, "element-to-nnz map"))) return st;
+    if (want_map && (st = fe_alloc_n(&p->map, 9 * (size_t)nme, "element-to-nnz map"))) return st;
     if (gather) {
         if ((st = fe_alloc_n(&p->seg_ptr, (size_t)tot + 1, "seg_ptr"))) return st;
         if ((st = fe_alloc_n(&p->perm, 9 * (size_t)nme, "perm"))) return st;
     }
     if (nq > 0) {
-        { FE_PROF("k_row_fill", s); k_row_fill<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, t.adj, p->vel, nq, p->row_ptr, p->col_idx,
-                                                    p->seg_ptr, p->perm); }
+        { FE_PROF("k_row_fill", s); k_row_fill<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, t.adj, nq, t.kinds, p->row_ptr, p->col_idx, p->fan,
+                                                                                   p->hdr, p->gen_rows, t.counters + 1); }
         FE_LAUNCHED("k_row_fill");
+        if (gather) {
+            { FE_PROF("k_row_perm", s); k_row_perm<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, t.adj, p->vel, nq, p->row_ptr, p->seg_ptr, p->perm); }
+            FE_LAUNCHED("k_row_perm");
+        }
     }
     if (nbig > 0) {
         { FE_PROF("k_row_big", s); k_row_big<<<nbig, BIG_BLOCK, big_smem, s>>>(t.big_list, p->vptr, t.adj, p->row_ptr, nullptr, p->col_idx); }
         FE_LAUNCHED("k_row_big (fill)");
+        size_t pair_smem = (size_t)FE_MAX_VALENCE * sizeof(long long);
+        { FE_PROF("k_row_big_pairs", s); k_row_big_pairs<<<nbig, BIG_BLOCK, pair_smem, s>>>(t.big_list, p->vptr, t.adj, p->fan, p->hdr,
+                                                                                               p->gen_rows, t.counters + 1); }
+        FE_LAUNCHED("k_row_big_pairs");
         if (gather) {
             size_t sm = 3 * (size_t)FE_MAX_VALENCE * (sizeof(long long) + sizeof(int32_t) + 1) +
                         (size_t)FE_MAX_VALENCE * sizeof(int32_t);
@@ -382,7 +599,7 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
         { FE_PROF("k_set_last", s); k_set_last<<<1, 1, 0, s>>>(p->seg_ptr + tot, (int32_t)(9 * (int64_t)nme)); }
         FE_LAUNCHED("k_set_last");
     }
-    if (nme > 0) {
+    if (want_map && nme > 0) {
         { FE_PROF("k_build_map", s); k_build_map<<<fe_grid(nme, MAP_BLOCK), MAP_BLOCK, 0, s>>>(m->me, nme, p->row_ptr, p->col_idx, p->map, t.flag + 1); }
         FE_LAUNCHED("k_build_map");
     }
@@ -406,9 +623,10 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
         if ((st = fe_alloc_n(&p->kg, kg, "element value staging"))) return st;
     }
     FE_CUDA(cudaMemcpyAsync(host_flags, t.flag, sizeof host_flags, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemcpyAsync(host_counts, t.counters, sizeof host_counts, cudaMemcpyDeviceToHost, s));
     FE_CUDA(cudaStreamSynchronize(s));
     if (host_flags[1]) return fe_fail(FE_ERR_CUDA, "internal error: a triangle key is missing from the pattern");
-    if (!gather) { fe_free(p->vptr); p->vptr = nullptr; }
+    p->n_gen = host_counts[1];
     return FE_OK;
 }
 
@@ -417,7 +635,7 @@ extern "C" fe_status fe_pattern_build(fe_mesh m, int dofs, int flags, fe_stream 
     *out = nullptr;
     if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");
     if (dofs != 1 && dofs != 2) return fe_fail(FE_ERR_INVALID_ARG, "dofs_per_vertex must be 1 or 2");
-    if (flags & ~FE_PATTERN_GATHER) return fe_fail(FE_ERR_INVALID_ARG, "unknown pattern flag");
+    if (flags & ~(FE_PATTERN_GATHER | FE_PATTERN_MAP)) return fe_fail(FE_ERR_INVALID_ARG, "unknown pattern flag");
     if (dofs == 2 && 36 * (int64_t)m->nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "36*nme must be < 2^31");
     if (9 * (int64_t)m->nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "9*nme must be < 2^31");
     fe_pattern p = new fe_pattern_s();
@@ -426,6 +644,8 @@ extern "C" fe_status fe_pattern_build(fe_mesh m, int dofs, int flags, fe_stream 
     p->nq = m->nq;
     p->nme = m->nme;
     p->topology_id = m->topology_id;
+    p->last_stream = (cudaStream_t)stream;
+    FeStreamScope scope((cudaStream_t)stream);
     fe_status st = build(m, dofs, flags, (cudaStream_t)stream, p);
     if (st) {
         cudaStreamSynchronize((cudaStream_t)stream);
@@ -448,6 +668,7 @@ extern "C" fe_status fe_pattern_info(fe_pattern p, int64_t* n_rows, int64_t* nnz
 
 extern "C" fe_status fe_pattern_map(fe_pattern p, const int32_t** map, int64_t* len) {
     if (!p) return fe_fail(FE_ERR_INVALID_ARG, "null pattern");
+    if (!p->map) return fe_fail(FE_ERR_INVALID_ARG, "pattern built without FE_PATTERN_MAP");
     if (map) *map = p->map;
     if (len) *len = 9 * (int64_t)p->nme;
     return FE_OK;

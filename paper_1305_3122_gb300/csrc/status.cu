@@ -18,21 +18,53 @@ fe_status fe_cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA;
 }
 
+static thread_local cudaStream_t t_stream = nullptr;
+
+FeStreamScope::FeStreamScope(cudaStream_t s) : prev(t_stream) { t_stream = s; }
+FeStreamScope::~FeStreamScope() { t_stream = prev; }
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64];
+
+static cudaError_t pool_for_device(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~0ULL;   // keep freed blocks for reuse
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
 fe_status fe_alloc(void** p, size_t bytes, const char* what) {
     *p = nullptr;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaMemPool_t pool;
+    cudaError_t e = pool_for_device(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, t_stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return fe_fail(e == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA,
-                       std::string("cudaMalloc(") + std::to_string(bytes) + " bytes) for " + what +
+                       std::string("device allocation of ") + std::to_string(bytes) + " bytes for " + what +
                            ": " + cudaGetErrorString(e));
     }
     return FE_OK;
 }
 
 void fe_free(void* p) {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, t_stream);
 }
 
 int fe_sm_count() {
@@ -203,9 +235,6 @@ fe_status fe_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStre
         if (e != cudaSuccess) ret = fe_cuda_fail(e, "scan total read-back");
         else if (ov || tot > INT32_MAX) ret = fe_fail(FE_ERR_LIMIT, "prefix sum exceeds int32 (too many non-zeros)");
         else *total_out = tot;
-    } else {
-        e = cudaStreamSynchronize(s);   // the temporaries are freed below
-        if (e != cudaSuccess) ret = fe_cuda_fail(e, "scan");
     }
     fe_free(sums);
     fe_free(ovf);

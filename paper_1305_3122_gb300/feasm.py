@@ -20,8 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libfeasm.so")
 
 FE_OK = 0
 PTR_HOST, PTR_DEVICE = 0, 1
-ATOMIC, GATHER = 0, 1
-PATTERN_DEFAULT, PATTERN_GATHER = 0, 1
+ATOMIC, GATHER, ROW = 0, 1, 2
+PATTERN_DEFAULT, PATTERN_GATHER, PATTERN_MAP = 0, 1, 2
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -176,10 +176,12 @@ class Mesh:
 class Pattern:
     """CSR structure and element-to-nnz map of a mesh (fe_pattern_build)."""
 
-    def __init__(self, mesh: Mesh, dofs: int = 1, gather: bool = False, stream=None):
+    def __init__(self, mesh: Mesh, dofs: int = 1, gather: bool = False, map: bool = True, stream=None):
+        """gather: also build what FE_VARIANT_GATHER needs; map: also the element-to-nnz map
+        (FE_VARIANT_ATOMIC, the adjoint, batches). FE_VARIANT_ROW works with any pattern."""
         h = _P()
-        _check(lib().fe_pattern_build(mesh.handle, dofs, PATTERN_GATHER if gather else PATTERN_DEFAULT,
-                                      _stream(stream), ctypes.byref(h)), "fe_pattern_build")
+        flags = (PATTERN_GATHER if gather else 0) | (PATTERN_MAP if map else 0)
+        _check(lib().fe_pattern_build(mesh.handle, dofs, flags, _stream(stream), ctypes.byref(h)), "fe_pattern_build")
         self._h = h
         self.mesh = mesh
         self.dofs = dofs
@@ -190,9 +192,11 @@ class Pattern:
         self.n_rows, self.nnz = n_rows.value, nnz.value
         self.row_ptr = _view_i32(rp.value, self.n_rows + 1, self)
         self.col_idx = _view_i32(ci.value, self.nnz, self)
-        mp, ml = _P(), _I64()
-        _check(lib().fe_pattern_map(h, ctypes.byref(mp), ctypes.byref(ml)), "fe_pattern_map")
-        self.map = _view_i32(mp.value, ml.value, self)
+        self.map = None
+        if map or gather:
+            mp, ml = _P(), _I64()
+            _check(lib().fe_pattern_map(h, ctypes.byref(mp), ctypes.byref(ml)), "fe_pattern_map")
+            self.map = _view_i32(mp.value, ml.value, self)
 
     @property
     def handle(self):
@@ -347,7 +351,7 @@ class Batch:
 
 
 def assemble_host(kind: str, q: np.ndarray, me: np.ndarray, w: np.ndarray | None = None, lam: float = 1.0,
-                  mu: float = 0.5, variant: int = ATOMIC, pinned_out: dict | None = None, stream=None):
+                  mu: float = 0.5, variant: int = ROW, pinned_out: dict | None = None, stream=None):
     """One-shot assembly from host arrays to host CSR arrays (the end-to-end call).
 
     kind in {"mass", "wmass", "stiff", "elas", "stiff_wmass"}. The mesh is created from host
@@ -355,7 +359,8 @@ def assemble_host(kind: str, q: np.ndarray, me: np.ndarray, w: np.ndarray | None
     col_idx and values read back to (pinned, if given) host tensors. Returns a dict.
     """
     mesh = Mesh(q, me, stream=stream)
-    pat = Pattern(mesh, dofs=2 if kind == "elas" else 1, gather=(variant == GATHER), stream=stream)
+    pat = Pattern(mesh, dofs=2 if kind == "elas" else 1, gather=(variant == GATHER), map=(variant == ATOMIC),
+                  stream=stream)
     vals = {}
     if kind in ("wmass", "stiff_wmass"):
         wd = torch.as_tensor(w).to("cuda", non_blocking=True)

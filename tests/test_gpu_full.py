@@ -49,7 +49,7 @@ def config2():
     return m, w
 
 
-@pytest.mark.parametrize("variant", [feasm.ATOMIC, feasm.GATHER])
+@pytest.mark.parametrize("variant", [feasm.ATOMIC, feasm.GATHER, feasm.ROW])
 def test_config2_stiff_wmass_full_size(config2, variant):
     m, w = config2
     mesh = feasm.Mesh(m.q, m.me)
@@ -87,13 +87,13 @@ def test_config1_mass_full_oracle():
     rp, ci, va = oracle.assemble(oracle.MASS, m.q, m.me)
     assert len(ci) == _structured_nnz(64) == 29_057
     assert_csr_equal(pat.row_ptr.cpu(), pat.col_idx.cpu(), rp, ci)
-    for v in (feasm.ATOMIC, feasm.GATHER):
+    for v in (feasm.ATOMIC, feasm.GATHER, feasm.ROW):
         got = feasm.assemble_mass(mesh, pat, v).cpu().numpy()
         assert_values_close(rp, got, va)
         assert got.sum() == pytest.approx(1.0, rel=1e-13)
 
 
-@pytest.mark.parametrize("variant", [feasm.ATOMIC, feasm.GATHER])
+@pytest.mark.parametrize("variant", [feasm.ATOMIC, feasm.GATHER, feasm.ROW])
 def test_config3_elasticity_full_size(variant):
     m = meshgen.square_mesh(1024, meshgen.SEED_BASE + 3)
     mesh = feasm.Mesh(m.q, m.me)

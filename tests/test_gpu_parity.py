@@ -18,7 +18,7 @@ from tests.gpu_common import assert_csr_equal, assert_values_close
 pytestmark = pytest.mark.gpu
 
 KINDS = {"mass": oracle.MASS, "wmass": oracle.WMASS, "stiff": oracle.STIFF}
-VARIANTS = [feasm.ATOMIC, feasm.GATHER]
+VARIANTS = [feasm.ATOMIC, feasm.GATHER, feasm.ROW]
 
 
 def fan_mesh(n_out: int, ring2: bool = True):
@@ -48,9 +48,11 @@ def _mesh_cases():
     m64 = meshgen.square_mesh(64, meshgen.SEED_BASE + 1)
     m37 = meshgen.square_mesh(37, 5)
     qf, mef = fan_mesh(70)
+    q12, me12 = fan_mesh(12)
     q2 = np.array([[0.0, 1.0, 1.0, 0.0], [0.0, 0.0, 1.0, 1.0]])
     me2 = np.array([[0, 0], [1, 2], [2, 3]], np.int32)
-    return {"square64": (m64.q, m64.me), "square37": (m37.q, m37.me), "fan70": (qf, mef), "two": (q2, me2),
+    return {"square64": (m64.q, m64.me), "square37": (m37.q, m37.me), "fan70": (qf, mef), "fan12": (q12, me12),
+            "two": (q2, me2),
             "one": (q2, me2[:, :1].copy())}
 
 
@@ -110,7 +112,7 @@ def test_stiff_wmass_fused(variant):
     assert_values_close(rp, Mw.cpu().numpy(), vm)
 
 
-@pytest.mark.parametrize("case", ["square37", "fan70", "two", "one"])
+@pytest.mark.parametrize("case", ["square37", "fan70", "fan12", "two", "one"])
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_elasticity(case, variant):
     q, me = CASES[case]
@@ -122,14 +124,15 @@ def test_elasticity(case, variant):
     assert_values_close(rp, got.cpu().numpy(), va)
 
 
-def test_gather_bit_identical_runs():
+@pytest.mark.parametrize("variant", [feasm.GATHER, feasm.ROW])
+def test_deterministic_bit_identical_runs(variant):
     q, me = CASES["square64"]
     w = torch.tensor(_weights(q), device="cuda")
     mesh = feasm.Mesh(q, me)
     pat = feasm.Pattern(mesh, gather=True)
     first = None
     for _ in range(10):
-        S, Mw = feasm.assemble_stiff_wmass(mesh, pat, w, feasm.GATHER)
+        S, Mw = feasm.assemble_stiff_wmass(mesh, pat, w, variant)
         cur = torch.cat([S, Mw]).cpu().numpy().view(np.int64)
         if first is None:
             first = cur
@@ -204,3 +207,44 @@ def test_host_one_shot_matches_device_path():
     assert_csr_equal(out["row_ptr"].numpy(), out["col_idx"].numpy(), rp, ci)
     assert_values_close(rp, out["S"].numpy(), vs)
     assert_values_close(rp, out["Mw"].numpy(), vm)
+
+
+def test_row_variant_needs_no_map():
+    q, me = CASES["square37"]
+    mesh = feasm.Mesh(q, me)
+    pat = feasm.Pattern(mesh, map=False)
+    assert pat.map is None
+    rp, ci, va = oracle.assemble(oracle.STIFF, q, me)
+    assert_values_close(rp, feasm.assemble_stiff(mesh, pat, feasm.ROW).cpu().numpy(), va)
+    with pytest.raises(feasm.FeasmError) as e:
+        feasm.assemble_stiff(mesh, pat, feasm.ATOMIC)
+    assert e.value.status == 1
+    pat2 = feasm.Pattern(mesh, dofs=2, map=False)
+    rp, ci, va = oracle.assemble(oracle.ELAS, q, me, lam=2.0, mu=0.25)
+    assert_values_close(rp, feasm.assemble_elas(mesh, pat2, 2.0, 0.25, feasm.ROW).cpu().numpy(), va)
+
+
+def test_row_variant_scale_invariance():
+    """Coordinates scaled by 2^40 and 2^-30: S is unchanged, M scales with the area; the
+    double-float range covers both (edge components stay within [2^-74, 2^128))."""
+    m = meshgen.square_mesh(12, 3)
+    for sc in (2.0 ** 40, 2.0 ** -30):
+        q = m.q * sc
+        mesh = feasm.Mesh(q, m.me)
+        pat = feasm.Pattern(mesh, map=False)
+        for kind, fn in ((oracle.STIFF, lambda: feasm.assemble_stiff(mesh, pat, feasm.ROW)),
+                         (oracle.MASS, lambda: feasm.assemble_mass(mesh, pat, feasm.ROW))):
+            rp, ci, va = oracle.assemble(kind, q, m.me)
+            assert_values_close(rp, fn().cpu().numpy(), va)
+        mesh.check()
+
+
+def test_row_variant_flags_out_of_range():
+    m = meshgen.square_mesh(4, 3)
+    q = m.q * 2.0 ** -80                     # edge components below 2^-74
+    mesh = feasm.Mesh(q, m.me)
+    pat = feasm.Pattern(mesh, map=False)
+    feasm.assemble_stiff(mesh, pat, feasm.ROW)
+    with pytest.raises(feasm.FeasmError) as e:
+        mesh.check()
+    assert e.value.status == 9
