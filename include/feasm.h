@@ -172,6 +172,24 @@ fe_status fe_assemble_stiff_wmass(fe_mesh mesh, fe_pattern pattern, const double
 fe_status fe_assemble_elas(fe_mesh mesh, fe_pattern pattern, double lambda, double mu,
                            int variant, double* values, int64_t cap, fe_stream stream);
 
+/* S and M^w as fe_assemble_stiff_wmass with FE_VARIANT_GATHER, for callers that must not have
+ * device memory allocated during the call (work being captured into a CUDA graph, frameworks
+ * that own all device memory through their own pool, loops with hard latency budgets). The
+ * element values are staged in a fixed device array built into the library (18 MiB, resident on
+ * every GPU that loads the library until the process exits) instead of the pattern's buffer;
+ * the call performs no allocation of any kind. The paper has no counterpart.
+ *   - nme <= FE_NOALLOC_MAX_TRIANGLES, else FE_ERR_LIMIT (nothing is launched).
+ *   - The pattern must be built with FE_PATTERN_GATHER (FE_ERR_INVALID_ARG otherwise).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU (other streams, other
+ *     host threads) race and give wrong values; order them on one stream. Each call overwrites
+ *     every staged entry it reads, so nothing carries over from the previous call. */
+#define FE_NOALLOC_MAX_TRIANGLES 131072
+fe_status fe_assemble_stiff_wmass_noalloc(fe_mesh mesh, fe_pattern pattern, const double* w,
+                                          double* S_values, double* Mw_values, int64_t cap,
+                                          fe_stream stream);
+
 /* --------------------------------------------------------------------------- adjoint ---- */
 
 /* Needs a pattern with the element-to-nnz map (FE_PATTERN_MAP or FE_PATTERN_GATHER).

@@ -374,3 +374,65 @@ extern "C" fe_status fe_assemble_elas(fe_mesh m, fe_pattern p, double lam, doubl
     FE_LAUNCHED("k_elas_gather");
     return FE_OK;
 }
+
+// ---------------------------------------------------------------- allocation-free entry point
+//
+// fe_assemble_stiff_wmass_noalloc runs the staged-gather assembly of S and M^w with its staging
+// buffer in a fixed, file-scope device array instead of memory from an allocator. It serves
+// callers that must not allocate device memory during the call: code that is being recorded
+// into a CUDA graph (allocations are not allowed there), a host framework that owns all device
+// memory through its own pool and forbids hidden allocations, or a loop with a hard latency
+// budget where an allocation could stall. The array is FE_NOALLOC_MAX_TRIANGLES * 18 doubles
+// (18 MiB) and stays resident on every GPU that loads the library until the process exits.
+
+#include <mutex>
+
+static __device__ __align__(256) double g_noalloc_scratch[(size_t)FE_NOALLOC_MAX_TRIANGLES * 18];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_addr[64];   // device address of the array, per device
+
+// The host-side name of g_noalloc_scratch is a stand-in, not a device address; the address is
+// looked up once per device, with that device current.
+static fe_status noalloc_scratch(double** out) {
+    int dev = 0;
+    FE_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fe_fail(FE_ERR_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return fe_cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return FE_OK;
+}
+
+extern "C" fe_status fe_assemble_stiff_wmass_noalloc(fe_mesh m, fe_pattern p, const double* w, double* S, double* Mw,
+                                                     int64_t cap, fe_stream stream) {
+    fe_status st;
+    if ((st = fe_check_pair(m, p, 1))) return st;
+    if (!(p->flags & FE_PATTERN_GATHER))
+        return fe_fail(FE_ERR_INVALID_ARG, "fe_assemble_stiff_wmass_noalloc needs a pattern built with FE_PATTERN_GATHER");
+    if ((st = check_out(p, S, cap))) return st;
+    if ((st = check_out(p, Mw, cap))) return st;
+    if (!w && m->nq > 0) return fe_fail(FE_ERR_INVALID_ARG, "w is null");
+    if (m->nme > FE_NOALLOC_MAX_TRIANGLES)
+        return fe_fail(FE_ERR_LIMIT, "fe_assemble_stiff_wmass_noalloc takes at most FE_NOALLOC_MAX_TRIANGLES=" +
+                                         std::to_string(FE_NOALLOC_MAX_TRIANGLES) + " triangles; this mesh has " +
+                                         std::to_string(m->nme));
+    double* scratch = nullptr;
+    if ((st = noalloc_scratch(&scratch))) return st;
+    const int32_t nme = m->nme;
+    if (nme == 0) return FE_OK;   // then nnz == 0 as well
+    cudaStream_t s = (cudaStream_t)stream;
+    // every staged entry is written before it is read, so nothing needs zeroing between calls
+    double* kg0 = scratch;
+    double* kg1 = scratch + 9 * (size_t)nme;
+    k_scalar_stage<K_STIFF_WMASS><<<fe_grid(nme, STAGE_BLOCK), STAGE_BLOCK, 0, s>>>(m->q, m->me, nme, w, kg0, kg1, m->err);
+    FE_LAUNCHED("k_scalar_stage (no-alloc)");
+    k_seg_gather<true><<<fe_grid(p->nnz, 256), 256, 0, s>>>(p->seg_ptr, p->perm, p->nnz, kg0, kg1, S, Mw);
+    FE_LAUNCHED("k_seg_gather (no-alloc)");
+    return FE_OK;
+}

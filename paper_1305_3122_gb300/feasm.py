@@ -45,6 +45,7 @@ SIGNATURES = {
     "fe_assemble_stiff": (_INT, [_P, _P, _INT, _P, _I64, _P]),
     "fe_assemble_stiff_wmass": (_INT, [_P, _P, _P, _INT, _P, _P, _I64, _P]),
     "fe_assemble_elas": (_INT, [_P, _P, _D, _D, _INT, _P, _I64, _P]),
+    "fe_assemble_stiff_wmass_noalloc": (_INT, [_P, _P, _P, _P, _P, _I64, _P]),
     "fe_adjoint_stiff_wmass": (_INT, [_P, _P, _P, _P, _P, _INT, _P, _P, _P]),
     "fe_batch_create": (_INT, [_I32, _P, _P, ctypes.POINTER(_P)]),
     "fe_batch_tune": (_INT, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
