@@ -59,7 +59,7 @@ def algorithmic_bytes(name: str, nq: int, nme: int, nnz: int) -> int | None:
         "k_scalar_atomic": 12 * nme + 16 * nq + 8 * nq + 16 * nnz,
         "k_scalar_stage": 12 * nme + 16 * nq + 8 * nq + 2 * 72 * nme,
         "k_seg_gather": 4 * (nnz + 1) + 36 * nme + 2 * 72 * nme + 16 * nnz,
-        "k_row_scalar": 12 * nme + 16 * nq + 8 * nq + 16 * nnz,
+        "k_fan_scalar": 12 * nme + 16 * nq + 8 * nq + 16 * nnz,
         "k_validate": 12 * nme + 16 * nq,
         "k_pack_coords": 32 * nq,
         "k_count_deg": 12 * nme + 4 * nq,
@@ -99,9 +99,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self) -> dict:
+    def stop(self, t0: float | None = None, t1: float | None = None) -> dict:
+        """Median SM clock etc. over the samples taken between host times t0 and t1 (the timed
+        region; a 0.25 s margin on each side covers the sampler's own period)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -113,7 +115,9 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if t0 is not None and not (t0 - 0.25 <= ts <= t1 + 0.25):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -187,9 +191,10 @@ def run_reference(args) -> int:
     return 0
 
 
-def _config(extra: dict | None = None) -> dict:
+def _config(extra: dict | None = None, cells: int = N_CELLS, nq: int = 4198401, nme: int = 8388608,
+            nnz: int = 29372417) -> dict:
     c = {"workload": f"P1 stiffness S + weighted mass M^[w], FP64, jittered node-permuted unit-square mesh "
-                     f"{N_CELLS}x{N_CELLS} cells (nq=4198401, nme=8388608, nnz=29372417 per matrix)",
+                     f"{cells}x{cells} cells (nq={nq}, nme={nme}, nnz={nnz} per matrix)",
          "step": "mesh validation + pattern build + S and M^[w] values (one sparse()-equivalent call)",
          "l2": "flushed between timed steps (512 MB write); inputs+outputs (~0.67 GB) exceed L2 too"}
     if extra:
@@ -215,7 +220,7 @@ def run_ours(args) -> int:
     torch.cuda.set_device(dev)
     variant = {"atomic": feasm.ATOMIC, "gather": feasm.GATHER, "row": feasm.ROW}[args.variant]
 
-    m = meshgen.square_mesh(N_CELLS, SEED + 1000 * rank)
+    m = meshgen.square_mesh(args.cells, SEED + 1000 * rank)
     w = meshgen.vertex_weights(m, SEED + 1000 * rank)
     q_d = torch.tensor(m.q, device=dev)
     me_d = torch.tensor(m.me, device=dev)
@@ -250,7 +255,9 @@ def run_ours(args) -> int:
     feasm.profile_enable(True)
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(0.3)                      # let the sampler start before the timed region
     times = []
+    t_begin = time.time()
     for _ in range(args.steps):
         flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -261,7 +268,8 @@ def run_ours(args) -> int:
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    t_end = time.time()
+    clk = clocks.stop(t_begin, t_end)
     feasm.profile_enable(False)
     prof = feasm.profile_read()
     if world > 1:
@@ -292,7 +300,8 @@ def run_ours(args) -> int:
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config({"variant": args.variant, "parallelism": f"replicas{world}" if world > 1 else "single"}),
+            "config": _config({"variant": args.variant, "parallelism": f"replicas{world}" if world > 1 else "single"},
+                              cells=args.cells, nq=m.nq, nme=m.nme, nnz=nnz),
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk,
             "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 5), "launches": int(v[1]),
                             "share": round(v[0] / sum(x[0] for x in prof.values()), 4)} for k, v in sorted(prof.items())},
@@ -411,10 +420,12 @@ def e2e(feasm, torch, m, w, args) -> dict:
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--variant", choices=["atomic", "gather", "row"], default="row")
+    ap.add_argument("--cells", type=int, default=N_CELLS,
+                    help="cells per side of the mesh (the workload is 2048; smaller values are for profiling)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

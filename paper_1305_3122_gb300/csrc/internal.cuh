@@ -110,8 +110,9 @@ inline unsigned fe_grid(int64_t n, int block, int per_sm = 8) {
 // Exclusive prefix sum of in[0..n) into out[0..n], out[n] = total. int32 in, int32 out.
 // Returns FE_ERR_LIMIT if the total does not fit in int32. Synchronises only if total_out
 // is not null (it then reads the total back).
+// With round > 1 (a power of two) each input is first rounded up to a multiple of round.
 fe_status fe_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s,
-                            int64_t* total_out);
+                            int64_t* total_out, int round = 1);
 
 // ------------------------------------------------------------------------ checks shared by calls
 

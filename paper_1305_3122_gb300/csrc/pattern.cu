@@ -32,28 +32,18 @@ enum { KIND_CLOSED = 0, KIND_OPEN = 1, KIND_GENERAL = 2 };
 
 // ------------------------------------------------------------------ row digit (counting sort)
 
-__global__ void k_count_deg(const int32_t* __restrict__ me, int32_t nme, int32_t* __restrict__ deg) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
-        atomicAdd(&deg[me[k]], 1);
-        atomicAdd(&deg[me[nme + k]], 1);
-        atomicAdd(&deg[me[2 * (int64_t)nme + k]], 1);
-    }
-}
-
 // Bucket entries of triangle k: for its vertex a, the two other vertices in counter-clockwise
-// order (and, for the staged gather, the triangle/local id 3k + a). One thread handles the three
-// vertices of a triangle, so the writes into a vertex's bucket come from nearby triangles and
-// merge in L2.
-__global__ void k_fill_adj(const int32_t* __restrict__ me, int32_t nme, const int32_t* __restrict__ vptr,
-                           int32_t* __restrict__ cur, int2* __restrict__ adj, int32_t* __restrict__ vel) {
+// order (and, for the staged gather, the triangle/local id 3k + a). The cursors start at the
+// bucket starts, so each atomic returns the entry's final slot. One thread handles the three
+// vertices of a triangle; its three atomics are independent and issued together. (This pass is
+// bound by random L2 transactions: one atomic and one store per incidence.)
+__global__ void k_fill_adj(const int32_t* __restrict__ me, int32_t nme, int32_t* __restrict__ cur,
+                           int2* __restrict__ adj, int32_t* __restrict__ vel) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
         int32_t v[3] = {me[k], me[nme + k], me[2 * (int64_t)nme + k]};
         int32_t slot[3];
-        // the three cursor bumps are independent: issue them (and the bucket starts) together
 #pragma unroll
         for (int a = 0; a < 3; a++) slot[a] = atomicAdd(&cur[v[a]], 1);
-#pragma unroll
-        for (int a = 0; a < 3; a++) slot[a] += vptr[v[a]];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             adj[slot[a]] = make_int2(v[(a + 1) % 3], v[(a + 2) % 3]);
@@ -167,12 +157,14 @@ __device__ __forceinline__ int fan_pos(const Fan& f, int32_t i, int kind, int32_
 
 // Row counts: simple rows from the fan analysis (closed: d + 1 entries, open: d + 2); general
 // rows by sorting; rows with more than FAST_DEG triangles are listed for the block kernels.
-__global__ void k_row_count(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t nq,
+// abase: start of each vertex's bucket in adj (the same offsets as vptr).
+__global__ void k_row_count(const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase,
+                            const int2* __restrict__ adj, int32_t nq,
                             int32_t* __restrict__ row_nnz, unsigned char* __restrict__ kind_out,
                             int32_t* __restrict__ big_list, int32_t* __restrict__ big_count, int* __restrict__ too_big) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = (int32_t)r;
-        int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+        int32_t beg = abase[i], d = vptr[i + 1] - vptr[i];
         if (d == 0) { row_nnz[i] = 0; kind_out[i] = KIND_GENERAL; continue; }
         if (d <= FAN_MAX) {
             Fan f;
@@ -200,18 +192,19 @@ __global__ void k_row_count(const int32_t* __restrict__ vptr, const int2* __rest
 // their positions (fan[beg + e] = (n_e, pos(n_e))), header (n_d, pos_self | pos_nd << 14 |
 // kind << 28) and col_idx. General rows: sorted unique columns, their (j, l) pairs sorted
 // lexicographically (a deterministic order) and a place in the general-row list.
-__global__ void k_row_fill(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t nq,
+__global__ void k_row_fill(const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase,
+                           const int2* __restrict__ adj, int32_t nq,
                            const unsigned char* __restrict__ kinds, const int32_t* __restrict__ row_ptr,
                            int32_t* __restrict__ col_idx, int2* __restrict__ fan, int2* __restrict__ hdr,
                            int32_t* __restrict__ gen_list, int32_t* __restrict__ gen_count) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = (int32_t)r;
-        int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+        int32_t abeg = abase[i], beg = vptr[i], d = vptr[i + 1] - beg;
         int kind = kinds[i];
         int32_t o = row_ptr[i];
         if (kind != KIND_GENERAL) {
             Fan f;
-            load_fan(adj, beg, d, f);
+            load_fan(adj, abeg, d, f);
             int start;
             fan_kind(f, start);
             int32_t jcur = 0, lcur = 0;
@@ -248,11 +241,11 @@ __global__ void k_row_fill(const int32_t* __restrict__ vptr, const int2* __restr
         hdr[i] = make_int2(-1, KIND_GENERAL << 28);
         if (d == 0 || d > FAST_DEG) continue;
         int32_t cols[2 * FAST_DEG + 1];
-        int u = row_columns(i, beg, d, adj, cols);
+        int u = row_columns(i, abeg, d, adj, cols);
         for (int t = 0; t < u; t++) col_idx[o + t] = cols[t];
         long long key[FAST_DEG];
         for (int32_t s = 0; s < d; s++) {
-            int2 p = adj[beg + s];
+            int2 p = adj[abeg + s];
             key[s] = ((long long)p.x << 32) | (unsigned)p.y;
         }
         isort64(key, d);
@@ -265,13 +258,16 @@ __global__ void k_row_fill(const int32_t* __restrict__ vptr, const int2* __restr
 
 // One block per row: the 2d+1 columns go to shared memory; pass 1 flags the first occurrence
 // of each value, pass 2 places each first occurrence at its rank among the distinct values.
-__global__ void k_row_big(const int32_t* __restrict__ big_list, const int32_t* __restrict__ vptr,
-                          const int2* __restrict__ adj, const int32_t* __restrict__ row_ptr,
-                          int32_t* __restrict__ row_nnz, int32_t* __restrict__ col_idx) {
+__global__ void k_row_big(const int32_t* __restrict__ big_list, const int32_t* __restrict__ nbig,
+                          const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase, const int2* __restrict__ adj,
+                          const int32_t* __restrict__ row_ptr, int32_t* __restrict__ row_nnz,
+                          int32_t* __restrict__ col_idx) {
     extern __shared__ int32_t sm[];
     __shared__ int cnt;
-    int32_t i = big_list[blockIdx.x];
-    int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+  for (int32_t b = blockIdx.x; b < *nbig; b += gridDim.x) {
+    __syncthreads();
+    int32_t i = big_list[b];
+    int32_t beg = abase[i], d = vptr[i + 1] - vptr[i];
     int n = 2 * d + 1;
     unsigned char* first = reinterpret_cast<unsigned char*>(sm + n);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -299,17 +295,21 @@ __global__ void k_row_big(const int32_t* __restrict__ big_list, const int32_t* _
     }
     __syncthreads();
     if (threadIdx.x == 0 && row_nnz) row_nnz[i] = cnt;
+  }
 }
 
 // (j, l) pairs of a high-valence row in lexicographic order (rank of each 64-bit key).
-__global__ void k_row_big_pairs(const int32_t* __restrict__ big_list, const int32_t* __restrict__ vptr,
-                                const int2* __restrict__ adj, int2* __restrict__ fan, int2* __restrict__ hdr,
-                                int32_t* __restrict__ gen_list, int32_t* __restrict__ gen_count) {
+__global__ void k_row_big_pairs(const int32_t* __restrict__ big_list, const int32_t* __restrict__ nbig,
+                                const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase, const int2* __restrict__ adj,
+                                int2* __restrict__ fan, int2* __restrict__ hdr, int32_t* __restrict__ gen_list,
+                                int32_t* __restrict__ gen_count) {
     extern __shared__ long long sk[];
-    int32_t i = big_list[blockIdx.x];
-    int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+  for (int32_t b = blockIdx.x; b < *nbig; b += gridDim.x) {
+    __syncthreads();
+    int32_t i = big_list[b];
+    int32_t beg = vptr[i], d = vptr[i + 1] - beg, abeg = abase[i];
     for (int s = threadIdx.x; s < d; s += blockDim.x) {
-        int2 p = adj[beg + s];
+        int2 p = adj[abeg + s];
         sk[s] = ((long long)p.x << 32) | (unsigned)p.y;
     }
     if (threadIdx.x == 0) {
@@ -323,6 +323,7 @@ __global__ void k_row_big_pairs(const int32_t* __restrict__ big_list, const int3
         for (int t = 0; t < d; t++) rank += sk[t] < v;
         fan[beg + rank] = make_int2((int32_t)(v >> 32), (int32_t)(v & 0xffffffffLL));
     }
+  }
 }
 
 // ------------------------------------------------------------------ staged-gather lists
@@ -341,7 +342,8 @@ __device__ __forceinline__ void contrib_key(int32_t i, int2 p, int32_t e, long l
 
 // Per non-zero, its contributions in ascending c (perm, grouped by seg_ptr), and the row's
 // triangle list sorted by triangle (vel), for rows with at most FAST_DEG triangles.
-__global__ void k_row_perm(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t* __restrict__ vel,
+__global__ void k_row_perm(const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase, const int2* __restrict__ adj,
+                           int32_t* __restrict__ vel,
                            int32_t nq, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ seg_ptr,
                            int32_t* __restrict__ perm) {
     long long keys[3 * FAST_DEG];
@@ -353,7 +355,7 @@ __global__ void k_row_perm(const int32_t* __restrict__ vptr, const int2* __restr
         int n = 0;
         for (int32_t s = 0; s < d; s++) {
             ev[s] = vel[beg + s];
-            contrib_key(i, adj[beg + s], ev[s], keys + n);
+            contrib_key(i, adj[abase[i] + s], ev[s], keys + n);
             n += 3;
         }
         isort64(keys, n);
@@ -373,12 +375,14 @@ __global__ void k_row_perm(const int32_t* __restrict__ vptr, const int2* __restr
 // c is unique). Pass 1: each key's rank among all keys gives its perm slot, and a key heads its
 // column's segment if no smaller key has the same column. Pass 2: each head's rank among the
 // heads is its column's position in the row. The row's triangle list is reordered by rank too.
-__global__ void k_row_big_perm(const int32_t* __restrict__ big_list, const int32_t* __restrict__ vptr,
-                               const int2* __restrict__ adj, int32_t* __restrict__ vel,
-                               const int32_t* __restrict__ row_ptr, int32_t* __restrict__ seg_ptr,
-                               int32_t* __restrict__ perm) {
+__global__ void k_row_big_perm(const int32_t* __restrict__ big_list, const int32_t* __restrict__ nbig,
+                               const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase, const int2* __restrict__ adj,
+                               int32_t* __restrict__ vel, const int32_t* __restrict__ row_ptr,
+                               int32_t* __restrict__ seg_ptr, int32_t* __restrict__ perm) {
     extern __shared__ long long smk[];
-    int32_t i = big_list[blockIdx.x];
+  for (int32_t b = blockIdx.x; b < *nbig; b += gridDim.x) {
+    __syncthreads();
+    int32_t i = big_list[b];
     int32_t beg = vptr[i], d = vptr[i + 1] - beg;
     int n = 3 * d;
     int32_t* rank = reinterpret_cast<int32_t*>(smk + n);
@@ -386,7 +390,7 @@ __global__ void k_row_big_perm(const int32_t* __restrict__ big_list, const int32
     unsigned char* head = reinterpret_cast<unsigned char*>(vsort + d);
     for (int s = threadIdx.x; s < d; s += blockDim.x) {
         long long k3[3];
-        contrib_key(i, adj[beg + s], vel[beg + s], k3);
+        contrib_key(i, adj[abase[i] + s], vel[beg + s], k3);
         smk[3 * s] = k3[0];
         smk[3 * s + 1] = k3[1];
         smk[3 * s + 2] = k3[2];
@@ -422,6 +426,7 @@ __global__ void k_row_big_perm(const int32_t* __restrict__ big_list, const int32
         seg_ptr[o + cr] = cbase + rank[t];
     }
     for (int s = threadIdx.x; s < d; s += blockDim.x) vel[beg + s] = vsort[s];
+  }
 }
 
 // ------------------------------------------------------------------ element-to-nnz map
@@ -476,7 +481,8 @@ __global__ void k_expand(const int32_t* __restrict__ row_ptr, const int32_t* __r
     }
 }
 
-__global__ void k_set_last(int32_t* p, int32_t v) { *p = v; }
+// seg_ptr[nnz] = 9 nme, with nnz read on the device (row_ptr[nq])
+__global__ void k_set_last(int32_t* seg_ptr, const int32_t* row_ptr, int32_t nq, int32_t v) { seg_ptr[row_ptr[nq]] = v; }
 
 // ------------------------------------------------------------------ driver
 
@@ -492,22 +498,29 @@ extern "C" void fe_pattern_destroy(fe_pattern p) {
 
 namespace {
 struct Temps {
-    int32_t *deg = nullptr, *cur = nullptr, *row_nnz = nullptr, *big_list = nullptr, *counters = nullptr;
+    int32_t *row_nnz = nullptr, *big_list = nullptr, *counters = nullptr, *cur = nullptr;
     int* flag = nullptr;
     int2* adj = nullptr;
     unsigned char* kinds = nullptr;
     ~Temps() {
-        fe_free(deg); fe_free(cur); fe_free(row_nnz); fe_free(big_list); fe_free(counters); fe_free(flag);
-        fe_free(adj); fe_free(kinds);
+        fe_free(row_nnz); fe_free(big_list); fe_free(counters); fe_free(flag); fe_free(adj); fe_free(kinds);
+        fe_free(cur);
     }
 };
 }  // namespace
 
+static constexpr int BIG_GRID = 152;   // blocks of the high-valence kernels (they loop over the list)
+
+// One host synchronisation: after the last kernel that can raise a flag, to read nnz and the
+// flags. The row counts, the high-valence list and nnz stay on the device until then; col_idx is
+// allocated at its upper bound (each row has at most 2 d + 1 entries: 6 nme + nq in all).
 static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_pattern p) {
     const int32_t nq = m->nq, nme = m->nme;
     const int64_t n3 = 3 * (int64_t)nme;
     const bool gather = flags & FE_PATTERN_GATHER;
     const bool want_map = gather || (flags & FE_PATTERN_MAP);
+    const int64_t cap = 6 * (int64_t)nme + nq;
+    if (cap >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "6*nme + nq must be < 2^31");
     Temps t;
     fe_status st;
     if ((st = fe_alloc_n(&p->row_ptr, (size_t)nq + 1, "row_ptr"))) return st;
@@ -515,94 +528,81 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     if ((st = fe_alloc_n(&p->fan, (size_t)n3, "row fans"))) return st;
     if ((st = fe_alloc_n(&p->hdr, (size_t)nq, "row fan headers"))) return st;
     if ((st = fe_alloc_n(&p->gen_rows, (size_t)nq + 1, "general-row list"))) return st;
-    if ((st = fe_alloc_n(&t.deg, (size_t)nq + 1, "valences"))) return st;
-    if ((st = fe_alloc_n(&t.cur, (size_t)nq + 1, "bucket cursors"))) return st;
+    if ((st = fe_alloc_n(&p->col_idx, (size_t)cap, "col_idx"))) return st;
     if ((st = fe_alloc_n(&t.row_nnz, (size_t)nq + 1, "row counts"))) return st;
     if ((st = fe_alloc_n(&t.kinds, (size_t)nq + 1, "row kinds"))) return st;
     if ((st = fe_alloc_n(&t.big_list, (size_t)nq + 1, "high-valence rows"))) return st;
     if ((st = fe_alloc_n(&t.counters, 2, "counters"))) return st;
     if ((st = fe_alloc_n(&t.flag, 2, "flags"))) return st;
     if ((st = fe_alloc_n(&t.adj, (size_t)n3, "row buckets"))) return st;
-    if (gather && (st = fe_alloc_n(&p->vel, (size_t)n3, "vertex-to-triangle lists"))) return st;
-    FE_CUDA(cudaMemsetAsync(t.deg, 0, sizeof(int32_t) * ((size_t)nq + 1), s));
-    FE_CUDA(cudaMemsetAsync(t.cur, 0, sizeof(int32_t) * ((size_t)nq + 1), s));
+    if ((st = fe_alloc_n(&t.cur, (size_t)nq + 1, "bucket cursors"))) return st;
+    if (gather) {
+        if ((st = fe_alloc_n(&p->vel, (size_t)n3, "vertex-to-triangle lists"))) return st;
+        if ((st = fe_alloc_n(&p->seg_ptr, (size_t)cap + 1, "seg_ptr"))) return st;
+        if ((st = fe_alloc_n(&p->perm, 9 * (size_t)nme, "perm"))) return st;
+    }
+    if (want_map && (st = fe_alloc_n(&p->map, 9 * (size_t)nme, "element-to-nnz map"))) return st;
     FE_CUDA(cudaMemsetAsync(t.counters, 0, 2 * sizeof(int32_t), s));
     FE_CUDA(cudaMemsetAsync(t.flag, 0, 2 * sizeof(int), s));
 
-    // row digit: counting sort of the 3 nme (vertex, triangle) incidences; the counts come with
-    // the mesh (its validation counted them)
-    const int32_t* deg = m->deg;
-    if (!deg) {
-        if (nme > 0) {
-            { FE_PROF("k_count_deg", s); k_count_deg<<<fe_grid(nme, 256), 256, 0, s>>>(m->me, nme, t.deg); }
-            FE_LAUNCHED("k_count_deg");
-        }
-        deg = t.deg;
-    }
-    int64_t tot = 0;
-    if ((st = fe_exclusive_scan(deg, p->vptr, nq, s, nullptr))) return st;
+    // row digit: counting sort of the 3 nme incidences (the counts come with the mesh: its
+    // validation took them)
+    if ((st = fe_exclusive_scan(m->deg, p->vptr, nq, s, nullptr))) return st;
+    FE_CUDA(cudaMemcpyAsync(t.cur, p->vptr, sizeof(int32_t) * ((size_t)nq + 1), cudaMemcpyDeviceToDevice, s));
     if (nme > 0) {
-        { FE_PROF("k_fill_adj", s); k_fill_adj<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->me, nme, p->vptr, t.cur, t.adj, p->vel); }
+        { FE_PROF("k_fill_adj", s); k_fill_adj<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->me, nme, t.cur, t.adj, p->vel); }
         FE_LAUNCHED("k_fill_adj");
     }
     // column digit inside each row, unique
-    if (nq > 0) {
-        { FE_PROF("k_row_count", s); k_row_count<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, t.adj, nq, t.row_nnz, t.kinds, t.big_list, t.counters, t.flag); }
-        FE_LAUNCHED("k_row_count");
-    }
-    int host_flags[2] = {0, 0};
-    int32_t host_counts[2] = {0, 0};
-    FE_CUDA(cudaMemcpyAsync(host_flags, t.flag, sizeof host_flags, cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaMemcpyAsync(host_counts, t.counters, sizeof host_counts, cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaStreamSynchronize(s));
-    const int32_t nbig = host_counts[0];
-    if (host_flags[0])
-        return fe_fail(FE_ERR_LIMIT, "a vertex belongs to more than FE_MAX_VALENCE=" + std::to_string(FE_MAX_VALENCE) + " triangles");
     size_t big_smem = (2 * (size_t)FE_MAX_VALENCE + 1) * (sizeof(int32_t) + 1);
-    if (nbig > 0) {
-        { FE_PROF("k_row_big", s); k_row_big<<<nbig, BIG_BLOCK, big_smem, s>>>(t.big_list, p->vptr, t.adj, nullptr, t.row_nnz, nullptr); }
+    if (nq > 0) {
+        { FE_PROF("k_row_count", s); k_row_count<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.row_nnz, t.kinds, t.big_list, t.counters, t.flag); }
+        FE_LAUNCHED("k_row_count");
+        { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, nullptr, t.row_nnz, nullptr); }
         FE_LAUNCHED("k_row_big (count)");
     }
-    if ((st = fe_exclusive_scan(t.row_nnz, p->row_ptr, nq, s, &tot))) return st;
-    p->nnz_scalar = tot;
-    if ((st = fe_alloc_n(&p->col_idx, (size_t)tot, "col_idx"))) return st;
-    if (want_map && (st = fe_alloc_n(&p->map, 9 * (size_t)nme, "element-to-nnz map"))) return st;
-    if (gather) {
-        if ((st = fe_alloc_n(&p->seg_ptr, (size_t)tot + 1, "seg_ptr"))) return st;
-        if ((st = fe_alloc_n(&p->perm, 9 * (size_t)nme, "perm"))) return st;
-    }
+    if ((st = fe_exclusive_scan(t.row_nnz, p->row_ptr, nq, s, nullptr))) return st;
     if (nq > 0) {
-        { FE_PROF("k_row_fill", s); k_row_fill<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, t.adj, nq, t.kinds, p->row_ptr, p->col_idx, p->fan,
+        { FE_PROF("k_row_fill", s); k_row_fill<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.kinds, p->row_ptr, p->col_idx, p->fan,
                                                                                    p->hdr, p->gen_rows, t.counters + 1); }
         FE_LAUNCHED("k_row_fill");
-        if (gather) {
-            { FE_PROF("k_row_perm", s); k_row_perm<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, t.adj, p->vel, nq, p->row_ptr, p->seg_ptr, p->perm); }
-            FE_LAUNCHED("k_row_perm");
-        }
-    }
-    if (nbig > 0) {
-        { FE_PROF("k_row_big", s); k_row_big<<<nbig, BIG_BLOCK, big_smem, s>>>(t.big_list, p->vptr, t.adj, p->row_ptr, nullptr, p->col_idx); }
+        { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->row_ptr, nullptr, p->col_idx); }
         FE_LAUNCHED("k_row_big (fill)");
         size_t pair_smem = (size_t)FE_MAX_VALENCE * sizeof(long long);
-        { FE_PROF("k_row_big_pairs", s); k_row_big_pairs<<<nbig, BIG_BLOCK, pair_smem, s>>>(t.big_list, p->vptr, t.adj, p->fan, p->hdr,
-                                                                                               p->gen_rows, t.counters + 1); }
+        { FE_PROF("k_row_big_pairs", s); k_row_big_pairs<<<BIG_GRID, BIG_BLOCK, pair_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->fan, p->hdr,
+                                                                                                   p->gen_rows, t.counters + 1); }
         FE_LAUNCHED("k_row_big_pairs");
         if (gather) {
+            { FE_PROF("k_row_perm", s); k_row_perm<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, p->vptr, t.adj, p->vel, nq, p->row_ptr, p->seg_ptr, p->perm); }
+            FE_LAUNCHED("k_row_perm");
             size_t sm = 3 * (size_t)FE_MAX_VALENCE * (sizeof(long long) + sizeof(int32_t) + 1) +
                         (size_t)FE_MAX_VALENCE * sizeof(int32_t);
             FE_CUDA(cudaFuncSetAttribute(k_row_big_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            { FE_PROF("k_row_big_perm", s); k_row_big_perm<<<nbig, BIG_BLOCK, sm, s>>>(t.big_list, p->vptr, t.adj, p->vel, p->row_ptr, p->seg_ptr, p->perm); }
+            { FE_PROF("k_row_big_perm", s); k_row_big_perm<<<BIG_GRID, BIG_BLOCK, sm, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->vel, p->row_ptr, p->seg_ptr, p->perm); }
             FE_LAUNCHED("k_row_big_perm");
         }
     }
     if (gather) {
-        { FE_PROF("k_set_last", s); k_set_last<<<1, 1, 0, s>>>(p->seg_ptr + tot, (int32_t)(9 * (int64_t)nme)); }
+        { FE_PROF("k_set_last", s); k_set_last<<<1, 1, 0, s>>>(p->seg_ptr, p->row_ptr, nq, (int32_t)(9 * (int64_t)nme)); }
         FE_LAUNCHED("k_set_last");
     }
     if (want_map && nme > 0) {
         { FE_PROF("k_build_map", s); k_build_map<<<fe_grid(nme, MAP_BLOCK), MAP_BLOCK, 0, s>>>(m->me, nme, p->row_ptr, p->col_idx, p->map, t.flag + 1); }
         FE_LAUNCHED("k_build_map");
     }
+    int host_flags[2] = {0, 0};
+    int32_t host_counts[2] = {0, 0};
+    int32_t tot32 = 0;
+    FE_CUDA(cudaMemcpyAsync(host_flags, t.flag, sizeof host_flags, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemcpyAsync(host_counts, t.counters, sizeof host_counts, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaMemcpyAsync(&tot32, p->row_ptr + nq, sizeof tot32, cudaMemcpyDeviceToHost, s));
+    FE_CUDA(cudaStreamSynchronize(s));
+    if (host_flags[0])
+        return fe_fail(FE_ERR_LIMIT, "a vertex belongs to more than FE_MAX_VALENCE=" + std::to_string(FE_MAX_VALENCE) + " triangles");
+    if (host_flags[1]) return fe_fail(FE_ERR_CUDA, "internal error: a triangle key is missing from the pattern");
+    const int64_t tot = tot32;
+    p->nnz_scalar = tot;
+    p->n_gen = host_counts[1];
     p->n_rows = nq;
     p->nnz = tot;
     if (dofs == 2) {
@@ -622,11 +622,6 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
         size_t kg = dofs == 2 ? 36 * (size_t)nme : 18 * (size_t)nme;
         if ((st = fe_alloc_n(&p->kg, kg, "element value staging"))) return st;
     }
-    FE_CUDA(cudaMemcpyAsync(host_flags, t.flag, sizeof host_flags, cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaMemcpyAsync(host_counts, t.counters, sizeof host_counts, cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaStreamSynchronize(s));
-    if (host_flags[1]) return fe_fail(FE_ERR_CUDA, "internal error: a triangle key is missing from the pattern");
-    p->n_gen = host_counts[1];
     return FE_OK;
 }
 

@@ -111,13 +111,19 @@ static constexpr int SCAN_BLOCK = 512;
 static constexpr int SCAN_ITEMS = 8;
 static constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 
-__global__ void k_tile_sums(const int32_t* __restrict__ in, int64_t n, long long* __restrict__ sums) {
+// round: each input is rounded up to a multiple of `round` (a power of two) before summing.
+__device__ __forceinline__ long long scan_in(const int32_t* __restrict__ in, int64_t i, int round) {
+    int32_t v = in[i];
+    return round > 1 ? (long long)((v + round - 1) & ~(round - 1)) : (long long)v;
+}
+
+__global__ void k_tile_sums(const int32_t* __restrict__ in, int64_t n, long long* __restrict__ sums, int round) {
     __shared__ long long red[SCAN_BLOCK / 32];
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     long long s = 0;
     for (int t = threadIdx.x; t < SCAN_TILE; t += SCAN_BLOCK) {
         int64_t i = base + t;
-        if (i < n) s += in[i];
+        if (i < n) s += scan_in(in, i, round);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -165,7 +171,7 @@ __global__ void k_scan_sums(long long* sums, int64_t ntiles) {
 }
 
 __global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n,
-                            const long long* __restrict__ offs, int* __restrict__ overflow) {
+                            const long long* __restrict__ offs, int* __restrict__ overflow, int round) {
     __shared__ long long warp_tot[SCAN_BLOCK / 32];
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     long long v[SCAN_ITEMS];
@@ -173,7 +179,7 @@ __global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict_
 #pragma unroll
     for (int j = 0; j < SCAN_ITEMS; j++) {
         int64_t i = base + j;
-        v[j] = i < n ? in[i] : 0;
+        v[j] = i < n ? scan_in(in, i, round) : 0;
         local += v[j];
     }
     long long x = local;
@@ -210,7 +216,7 @@ __global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict_
 }
 
 fe_status fe_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s,
-                            int64_t* total_out) {
+                            int64_t* total_out, int round) {
     int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (ntiles < 1) ntiles = 1;
     long long* sums = nullptr;
@@ -220,9 +226,9 @@ fe_status fe_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStre
     st = fe_alloc_n(&ovf, 1, "scan overflow flag");
     if (st) { fe_free(sums); return st; }
     cudaMemsetAsync(ovf, 0, sizeof(int), s);
-    { FE_PROF("k_tile_sums", s); k_tile_sums<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, sums); }
+    { FE_PROF("k_tile_sums", s); k_tile_sums<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, sums, round); }
     { FE_PROF("k_scan_sums", s); k_scan_sums<<<1, 1024, 0, s>>>(sums, ntiles); }
-    { FE_PROF("k_tile_scan", s); k_tile_scan<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, n, sums, ovf); }
+    { FE_PROF("k_tile_scan", s); k_tile_scan<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, n, sums, ovf, round); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { fe_free(sums); fe_free(ovf); return fe_cuda_fail(e, "scan kernels"); }
     fe_status ret = FE_OK;
