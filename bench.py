@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -163,7 +164,11 @@ def run_reference(args) -> int:
     import oracle
     from paper_1305_3122_gb300 import meshgen
 
-    n_cells = 256
+    # each step is a bounded sample of the workload: a mesh of the same recipe sized so that the
+    # whole warm-up + timed run takes about a minute at the oracle's ~0.85 Melem/s
+    per_step_s = 60.0 / max(args.steps + args.warmup, 1)
+    n_cells = int(math.sqrt(0.85e6 * per_step_s / 2.0)) // 16 * 16
+    n_cells = max(32, min(512, n_cells))
     m = meshgen.square_mesh(n_cells, SEED)
     w = meshgen.vertex_weights(m, SEED)
 
@@ -420,7 +425,7 @@ def e2e(feasm, torch, m, w, args) -> dict:
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--variant", choices=["atomic", "gather", "row"], default="row")

@@ -7,9 +7,9 @@
  *   M   mass              (element matrix Eq. 1)
  *   M^w weighted mass     (element matrix Eq. 2, w given at the vertices)
  *   S   stiffness         (element matrix Eq. 3)
- *   K   plane elasticity  (element matrix |T| B^T C B of Section 6, Lame lambda, mu)
+ *   K   plane elasticity  (element matrix |T| B^T C B of Section 7, Lame lambda, mu)
  * by summing every element's contributions into CSR storage, which is what the paper does with
- * sparse(Ig, Jg, Kg, n, n) (Sections 4-6). It also provides the adjoint of S and M^w with respect
+ * sparse(Ig, Jg, Kg, n, n) (Sections 5-7). It also provides the adjoint of S and M^w with respect
  * to q and w, and a batched form for many meshes.
  *
  * Conventions shared by every call
@@ -24,7 +24,7 @@
  *   - CSR output: row_ptr[n_rows+1], col_idx[nnz] strictly ascending inside each row. The
  *     pattern is structural: (i, j) is stored iff i and j share a triangle, so a value that
  *     sums to exactly 0.0 is still stored. All four matrices are symmetric, so these CSR arrays
- *     are also the CSC arrays the paper describes in Section 3.
+ *     are also the CSC arrays the paper describes in Section 4.
  *   - Every call that takes a stream is stream-ordered and asynchronous, except where noted
  *     ("synchronises"). Device pointers must be device-resident (cudaMalloc / torch CUDA
  *     tensors) on the current device; FE_PTR_HOST inputs may be pageable or pinned host memory.
@@ -121,13 +121,14 @@ void fe_mesh_destroy(fe_mesh mesh);
 
 /* Builds the CSR structure of the global matrix and the element-to-nnz map: for a scalar
  * pattern (dofs_per_vertex = 1) map[9k + 3*jl + il] is the position in col_idx of
- * (me[il][k], me[jl][k]) -- the paper's Ig/Jg arrays of Section 5 (Remark 5.1) resolved once
- * into storage positions, with c = 9k + 3*jl + il the column-wise element order of Section 4.
+ * (me[il][k], me[jl][k]) -- the paper's Ig/Jg arrays (Section 6, the remark on forming Ig and Jg from me)
+ * resolved once into storage positions, with c = 9k + 3*jl + il the column-wise element order
+ * of Section 5.
  * For dofs_per_vertex = 2 the pattern is the 2x2 block expansion of the scalar one
- * (BuildIgJgP1VF, Section 6.2). The structural half of sparse(): a counting sort of the
+ * (the 6 x nme index array of Section 7.2). The structural half of sparse(): a counting sort of the
  * (row, col) keys on the row, then a sort of the columns inside each row, then unique.
  * flags: FE_PATTERN_DEFAULT, FE_PATTERN_MAP, FE_PATTERN_GATHER (or-ed). Synchronises the
- * stream twice (to learn the high-valence rows and nnz). Handles release their memory on the
+ * stream once (to learn nnz). Handles release their memory on the
  * last stream they were used on (stream-ordered); work on other streams must be ordered by
  * the caller before destroying them. */
 fe_status fe_pattern_build(fe_mesh mesh, int dofs_per_vertex, int flags, fe_stream stream,
@@ -167,8 +168,8 @@ fe_status fe_assemble_stiff_wmass(fe_mesh mesh, fe_pattern pattern, const double
                                   int variant, double* S_values, double* Mw_values, int64_t cap,
                                   fe_stream stream);
 
-/* K, Section 6: K^e = |T| B^T C B with C = [[l+2m, l, 0], [l, l+2m, 0], [0, 0, m]].
- * Needs a dofs_per_vertex = 2 pattern; lambda + mu > 0 (Section 6) else FE_ERR_INVALID_ARG. */
+/* K, Section 7: K^e = |T| B^T C B with C = [[l+2m, l, 0], [l, l+2m, 0], [0, 0, m]].
+ * Needs a dofs_per_vertex = 2 pattern; lambda + mu > 0 (Section 7) else FE_ERR_INVALID_ARG. */
 fe_status fe_assemble_elas(fe_mesh mesh, fe_pattern pattern, double lambda, double mu,
                            int variant, double* values, int64_t cap, fe_stream stream);
 

@@ -9,11 +9,11 @@
  * finite element matrices in Matlab and Octave", INRIA RR-8305, 2013):
  *   - element matrices straight from their closed forms: mass M^e (Eq. 1), weighted mass
  *     M^{e,[w]} (Eq. 2), stiffness S^e (Eq. 3), and the plane-elasticity K^e = |T| B^T C B
- *     with the gradients of Eq. (GradFoncBas) (Section 6);
+ *     with the basis-function gradients of Eq. (4) (Section 7);
  *   - the triplet arrays Ig, Jg, Kg in the paper's order: element k's local matrix stored
  *     column-wise, contribution index c = n^2*k + n*jl + il for an n x n element matrix
- *     (Section 4, "Ke = E(:)"; Section 6.1 for n = 6);
- *   - the sparse(I,J,K,m,n) semantics of Section 4: triplets with equal (row, col) are summed.
+ *     (Section 5, "Ke = E(:)"; Section 7.1 for n = 6);
+ *   - the sparse(I,J,K,m,n) semantics of Section 5: triplets with equal (row, col) are summed.
  *     Result in CSR, columns ascending in each row. Reading kept here: the pattern is
  *     structural, so a sum that happens to be exactly 0.0 is still stored.
  *
@@ -88,7 +88,7 @@ void or_elem_stiff(const double x[3], const double y[3], double area, double E[9
             E[3 * a + b] = (ex[a] * ex[b] + ey[a] * ey[b]) / (4.0 * area);
 }
 
-/* Section 6: K^e = |T| * B^T C B, 6x6 row-major. Gradients (Eq. GradFoncBas):
+/* Section 7: K^e = |T| * B^T C B, 6x6 row-major. Gradients (Eq. 4):
  * grad(phi_a) = (e_a,y, -e_a,x) / (2|T|) with e = (u, v, w). Local dof 2a is the x-component
  * of vertex a, 2a+1 the y-component; B has column 2a = (dphi_a/dx, 0, dphi_a/dy) and column
  * 2a+1 = (0, dphi_a/dy, dphi_a/dx). C = [[l+2m, l, 0], [l, l+2m, 0], [0, 0, m]].            */

@@ -6,8 +6,8 @@
 //   weighted     Eq. (2):  Mw_ab = |T|/30 (w_a + w_b + w_c/2)  for a != b (c the third vertex),
 //                          Mw_aa = |T|/30 (3 w_a + w_b + w_c)
 //   stiffness    Eq. (3):  S_ab  = (e_a . e_b) / (4|T|)
-//   elasticity   Sec. 6:   K = |T| B^T C B with grad(phi_a) = (e_a,y, -e_a,x) / (2|T|)
-// Scatter stage (Section 4, sparse() sums duplicates): element k's entry (il, jl) is
+//   elasticity   Sec. 7:   K = |T| B^T C B with grad(phi_a) = (e_a,y, -e_a,x) / (2|T|)
+// Scatter stage (Section 5, sparse() sums duplicates): element k's entry (il, jl) is
 // contribution c = n*n*k + n*jl + il and lands on non-zero map[...].
 //   FE_VARIANT_ATOMIC: one thread per triangle adds its entries with FP64 atomicAdd.
 //   FE_VARIANT_GATHER: one thread per triangle writes Kg[c] (staged through shared memory so the

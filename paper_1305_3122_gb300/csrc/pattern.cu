@@ -1,8 +1,8 @@
 // pattern.cu -- the structural half of sparse(Ig, Jg, Kg): CSR structure, triangle fans, map.
 //
 // The paper forms Ig = me([1 2 3 1 2 3 1 2 3], :) and Jg = me([1 1 1 2 2 2 3 3 3], :)
-// (Section 5, Remark 5.1) and lets sparse() sort the 9*nme (row, col) keys and merge equal
-// ones (Section 4). Here the keys are sorted by a two-level (most-significant-digit first)
+// (Section 6, the remark on forming them from me) and lets sparse() sort the 9*nme (row, col)
+// keys and merge equal ones (Section 5). Here the keys are sorted by a two-level (most-significant-digit first)
 // radix sort that exploits their shape: the row digit is a counting sort (each triangle drops
 // its two other vertices into the bucket of each of its vertices), and the column digit is
 // sorted inside each row bucket, which holds only 2*valence+1 keys. Unique keys give

@@ -1,6 +1,6 @@
 // rowasm.cu -- FE_VARIANT_ROW: atomic-free, deterministic assembly by row owners.
 //
-// The paper sums the 9*nme contributions with sparse() (Section 4). Here each CSR row i (vertex
+// The paper sums the 9*nme contributions with sparse() (Section 5). Here each CSR row i (vertex
 // i) is summed by its owner, which computes just the entries of each element matrix that land in
 // row i. For a triangle (i, j, l), counter-clockwise with i at local position a, and relative
 // coordinates r_t = p_t - p_i:
@@ -9,7 +9,7 @@
 //   M^w (Eq. 2): with s = w_i + w_j + w_l:
 //                Mw_ii += D/60 (s + 2 w_i), Mw_ij += D/60 (s - w_l/2), Mw_il += D/60 (s - w_j/2)
 //   M   (Eq. 1): M_ii += D/12, M_ij += D/24, M_il += D/24
-//   K   (Sec. 6): the 2 x 2 blocks of rows 2i, 2i+1 of K^e = |T| B^T C B (elas_terms below).
+//   K   (Sec. 7): the 2 x 2 blocks of rows 2i, 2i+1 of K^e = |T| B^T C B (elas_terms below).
 // Every value is written exactly once: no atomics, no zeroing, no staged element matrices.
 //
 // Simple rows (pattern.cu) list their neighbours n_0, n_1, ... in counter-clockwise fan order,

@@ -265,7 +265,7 @@ def assemble_stiff_wmass(mesh: Mesh, pattern: Pattern, w: torch.Tensor, variant:
 
 def assemble_elas(mesh: Mesh, pattern: Pattern, lam: float, mu: float, variant: int = ATOMIC, out=None,
                   stream=None) -> torch.Tensor:
-    """Values of the plane-elasticity K (Section 6); pattern built with dofs=2."""
+    """Values of the plane-elasticity K (Section 7); pattern built with dofs=2."""
     out = _values(pattern, out)
     _check(lib().fe_assemble_elas(mesh.handle, pattern.handle, float(lam), float(mu), variant, out.data_ptr(),
                                   out.numel(), _stream(stream)), "fe_assemble_elas")

@@ -1,7 +1,7 @@
 """Exact rational P1 element matrices, derived independently of both implementations.
 
 The oracle and the CUDA kernels use the paper's closed forms (Eqs. 1-3 and the B^T C B form
-of Section 6, built from edge vectors). This helper starts from the definitions instead:
+of Section 7, built from edge vectors). This helper starts from the definitions instead:
   - the barycentric coordinates lambda_a(x, y) = alpha_a + beta_a x + gamma_a y are found by
     solving lambda_a(p_b) = delta_ab with exact Gaussian elimination on Fractions;
   - integrals of products of barycentric coordinates use the exact monomial formula

@@ -3,8 +3,8 @@
 Each test is chosen so that a plausible mistake in the oracle (a dropped term, a wrong sign or
 index, a transposed operand, a wrong summation order) fails at least one of them:
   - element matrices vs an independent exact-rational derivation (tests/exact_fe.py);
-  - the worked CSC example of Section 3 (non-symmetric, so a transposition shows);
-  - the triplet layout of Sections 4-6 (Ig = me([1 2 3 1 2 3 1 2 3],:), Jg = me([1 1 1 2 2 2 ...]));
+  - the worked CSC example of Section 4 (non-symmetric, so a transposition shows);
+  - the triplet layout of Sections 5-7 (Ig = me([1 2 3 1 2 3 1 2 3],:), Jg = me([1 1 1 2 2 2 ...]));
   - exact rational values on a two-triangle square, brute-force dense assembly on small meshes;
   - integral identities that hold for any mesh of the unit square.
 """
@@ -110,7 +110,7 @@ def _load_golden_csc():
 
 @pytest.mark.parametrize("which", ["", "2"])
 def test_paper_csc_example(which):
-    """Section 3's 3x4 example. CSC of A equals CSR of A^T, so sparse() is called with the
+    """Section 4's 3x4 example. CSC of A equals CSR of A^T, so sparse() is called with the
     roles of rows and columns exchanged; the triplets are fed in a scrambled order with one
     entry split in two, and aa / ia / ja must come out exactly as printed."""
     g = _load_golden_csc()
