@@ -207,6 +207,29 @@ def _config(extra: dict | None = None, cells: int = N_CELLS, nq: int = 4198401, 
     return c
 
 
+# ------------------------------------------------------------------ whole-job aggregation
+
+def rank_seed(rank: int) -> int:
+    """Each rank assembles its own mesh of the same recipe (replicas, weak scaling)."""
+    return SEED + 1000 * rank
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The slowest rank's figure: the whole job ends when its last rank does."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput in millions of units per second: all ranks' units over the max time."""
+    return world * units_per_rank / (ms_max / 1e3) / 1e6
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_ours(args) -> int:
@@ -225,8 +248,8 @@ def run_ours(args) -> int:
     torch.cuda.set_device(dev)
     variant = {"atomic": feasm.ATOMIC, "gather": feasm.GATHER, "row": feasm.ROW}[args.variant]
 
-    m = meshgen.square_mesh(args.cells, SEED + 1000 * rank)
-    w = meshgen.vertex_weights(m, SEED + 1000 * rank)
+    m = meshgen.square_mesh(args.cells, rank_seed(rank))
+    w = meshgen.vertex_weights(m, rank_seed(rank))
     q_d = torch.tensor(m.q, device=dev)
     me_d = torch.tensor(m.me, device=dev)
     w_d = torch.tensor(w, device=dev)
@@ -280,11 +303,8 @@ def run_ours(args) -> int:
     if world > 1:
         dist.barrier()
     ms = sum(times) / len(times)
-    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_max = float(tmax.item())
-    value = world * m.nme / (ms_max / 1e3) / 1e6
+    ms_max = max_over_ranks(ms, dev)
+    value = job_value(m.nme, world, ms_max)
 
     if rank != 0:
         if world > 1:
