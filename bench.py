@@ -20,6 +20,7 @@ weak scaling); value = all ranks' triangles / the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -61,6 +62,7 @@ def algorithmic_bytes(name: str, nq: int, nme: int, nnz: int) -> int | None:
         "k_scalar_stage": 12 * nme + 16 * nq + 8 * nq + 2 * 72 * nme,
         "k_seg_gather": 4 * (nnz + 1) + 36 * nme + 2 * 72 * nme + 16 * nnz,
         "k_fan_scalar": 12 * nme + 16 * nq + 8 * nq + 16 * nnz,
+        "k_pack_vrec": 16 * nq + 8 * nq + 32 * nq,
         "k_validate": 12 * nme + 16 * nq,
         "k_pack_coords": 32 * nq,
         "k_count_deg": 12 * nme + 4 * nq,
@@ -318,7 +320,7 @@ def run_ours(args) -> int:
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
     dom_bytes = algorithmic_bytes(dom, m.nq, m.nme, nnz)
-    roof = _roofline(dom, dom_bytes, dom_ms, hbm, peak_kind, args.traffic)
+    roof = _roofline(dom, dom_bytes, dom_ms, hbm, peak_kind, args.traffic, args.cells)
 
     # assembly with a prebuilt pattern
     asm = assemble_only(feasm, torch, mesh0, pat0, w_d, variant, S, M, flush, stream, args, m, nnz, hbm, peak_kind)
@@ -344,13 +346,36 @@ def run_ours(args) -> int:
     return 0
 
 
-def _roofline(name, nbytes, ms, hbm, peak_kind, traffic_path):
+# Source files whose change invalidates a recorded DRAM-traffic figure of a kernel.
+KERNEL_SOURCES = {"k_fan_scalar": ["rowasm.cu", "ff.cuh"]}
+
+
+def kernel_source_hash(name: str) -> str | None:
+    files = KERNEL_SOURCES.get(name)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1305_3122_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(name: str, cells: int, traffic_path: str | None):
+    """DRAM bytes per launch from an ncu capture of this kernel on this mesh size, or None when
+    none was recorded or the kernel's source changed since."""
+    if not traffic_path or not os.path.exists(traffic_path):
+        return None
+    with open(traffic_path) as f:
+        rec = json.load(f).get(name)
+    if not isinstance(rec, dict) or rec.get("cells") != cells or rec.get("source") != kernel_source_hash(name):
+        return None
+    return rec.get("bytes")
+
+
+def _roofline(name, nbytes, ms, hbm, peak_kind, traffic_path, cells=N_CELLS):
     achieved = nbytes / (ms / 1e3) / 1e9 if nbytes else None
-    traffic = None
-    if traffic_path and os.path.exists(traffic_path):
-        with open(traffic_path) as f:
-            t = json.load(f)
-        traffic = t.get(name)
+    traffic = recorded_traffic(name, cells, traffic_path)
     return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
             "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
             "traffic": traffic, "algorithmic_bytes": nbytes, "ms_per_launch": round(ms, 5),
@@ -378,7 +403,7 @@ def assemble_only(feasm, torch, mesh, pat, w_d, variant, S, M, flush, stream, ar
     ms = sum(times) / len(times)
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
-    roof = _roofline(dom, algorithmic_bytes(dom, m.nq, m.nme, nnz), dom_ms, hbm, peak_kind, args.traffic)
+    roof = _roofline(dom, algorithmic_bytes(dom, m.nq, m.nme, nnz), dom_ms, hbm, peak_kind, args.traffic, args.cells)
     return {"value": round(m.nme / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms": round(ms, 4), "reps": reps,
             "kernels": {k: round(v[0] / v[1], 5) for k, v in prof.items()}, "roofline": roof}
 

@@ -9,11 +9,11 @@
 // errs by a few units of 2^-48 relative to the magnitude of its operands (not of its result), so
 // assembled values agree with FP64 to about 2^-45 of each row's largest entry.
 //
-// The conversions never touch the FP64 pipe:
+// The conversions use the FP64 pipe at most once:
 //   ff_from_double  splits the 53-bit significand: hi keeps the top 24 bits (truncated), lo the
-//                   next 29 bits rounded down to 24; |d - (hi + lo)| < 2^-47 |d|.
-//   ff_to_double    builds the FP64 bit pattern of hi + lo directly (lo's bits below the 53-bit
-//                   window are truncated, error < 2^-52 relative).
+//                   remaining 29 bits rounded to 24; |d - (hi + lo)| <= 2^-48 |d|.
+//   ff_to_double    builds hi and lo as FP64 numbers bit by bit and adds them with one FP64
+//                   addition (correctly rounded).
 // Range: nonzero inputs need 2^-74 <= |d| < 2^128 (the lo part must stay a normal float);
 // outside it `bad` is set and the value is treated as zero.
 #pragma once
@@ -25,30 +25,27 @@ struct ff {
 };
 
 __device__ __forceinline__ ff ff_make(float h) { return ff{h, 0.f}; }
+__device__ __forceinline__ ff z_ff() { return ff{0.f, 0.f}; }
 
 __device__ __forceinline__ ff ff_from_double(double d, int& bad) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+    unsigned hi32 = (unsigned)__double2hiint(d), lo32 = (unsigned)__double2loint(d);
+    unsigned E = (hi32 >> 20) & 0x7FFu;                  // biased FP64 exponent, e = E - 1023
     unsigned sgn = hi32 & 0x80000000u;
-    int e = (int)((hi32 >> 20) & 0x7FF) - 1023;
-    if (e == -1023) {                                    // zero or subnormal
-        if ((hi32 & 0xFFFFFu) | lo32) bad = 1;
-        return ff{0.f, 0.f};
-    }
-    if (e > 127 || e < -74) {
-        bad = 1;
-        return ff{0.f, 0.f};
-    }
-    float h = __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29));
-    unsigned r = lo32 & 0x1FFFFFFFu;                      // remaining 29 bits, weight 2^(e-52)
-    float l = 0.f;
-    if (r) {
-        int p = 31 - __clz(r);                           // leading bit, 0..28
-        unsigned m = p >= 23 ? (r >> (p - 23)) : (r << (23 - p));
-        int le = p + e - 52;                             // exponent of lo, >= -126 for e >= -74
-        l = __uint_as_float(sgn | ((unsigned)(le + 127) << 23) | (m & 0x7FFFFFu));
-    }
-    return ff{h, l};
+    // hi: sign, float exponent e + 127 (= E - 896), the top 23 stored significand bits
+    float h = __uint_as_float(__funnelshift_l(lo32, (hi32 & 0x7FFFFFFFu) - (896u << 20), 3) | sgn);
+    // lo: the remaining 29 bits as an integer, rounded to a float and scaled by +-2^(e-52)
+    float l = __uint2float_rn(lo32 & 0x1FFFFFFFu) * __uint_as_float(((E - 948u) << 23) | sgn);
+    bool ok = E - 949u <= 201u;                          // -74 <= e <= 127
+    if (!ok && E != 0u) bad = 1;                         // zero is exact; anything else out of range
+    return ok ? ff{h, l} : ff{0.f, 0.f};
+}
+
+// The same for a computed value whose magnitude, when tiny, is a rounding residue: values below
+// 2^-74 become zero without raising the range flag (only overflow does).
+__device__ __forceinline__ ff ff_from_value(double d, int& bad) {
+    unsigned E = ((unsigned)__double2hiint(d) >> 20) & 0x7FFu;
+    if (E < 949u) return ff{0.f, 0.f};
+    return ff_from_double(d, bad);
 }
 
 // The error-free transforms below must not be altered by the compiler's multiply-add
@@ -79,19 +76,23 @@ __device__ __forceinline__ ff fast_two_sum(float a, float b) {
     return ff{s, FSUB(b, FSUB(s, a))};
 }
 
+// a + b: exact two-sum of the high words, low words added, one Fast2Sum to renormalise (the
+// "sloppy" double-word sum of Joldes-Muller-Popescu). Error at most a few units of 2^-48 of
+// |a| + |b| (not of |a + b|: cancellation is not compensated, and need not be here, because every
+// sum's error is measured against the row's largest entry).
 __device__ __forceinline__ ff ff_add(ff a, ff b) {
     float s, e;
     two_sum(a.h, b.h, s, e);
     e = FADD(e, FADD(a.l, b.l));
-    return ff_norm(s, e);
+    return fast_two_sum(s, e);
 }
 
 __device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.h, -a.l}; }
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
 
 // Running sum acc += x, renormalised at every step so that each addition errs by at most a few
-// units of 2^-48 of the running sum (carrying the low word unnormalised lets its own rounding
-// grow with the number of terms).
+// units of 2^-48 of the running sum and the term (carrying the low word unnormalised lets its
+// own rounding grow with the number of terms).
 __device__ __forceinline__ void ff_acc(ff& acc, ff x) { acc = ff_add(acc, x); }
 
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
@@ -110,7 +111,7 @@ __device__ __forceinline__ ff ff_mulf(ff a, float b) {
     return fast_two_sum(p, e);
 }
 
-// a.x * b.x + a.y * b.y with one normalisation: error <= ~3 * 2^-48 (|ax bx| + |ay by|).
+// a.x * b.x + a.y * b.y with one normalisation: error <= ~4 * 2^-48 (|ax bx| + |ay by|).
 __device__ __forceinline__ ff ff_dot2(ff ax, ff ay, ff bx, ff by) {
     float p1 = FMUL(ax.h, bx.h);
     float e1 = fmaf(ax.h, bx.h, -p1);
@@ -122,7 +123,20 @@ __device__ __forceinline__ ff ff_dot2(ff ax, ff ay, ff bx, ff by) {
     e2 = fmaf(ay.l, by.h, e2);
     float s, e;
     two_sum(p1, p2, s, e);
-    return ff_norm(s, FADD(e, FADD(e1, e2)));
+    return fast_two_sum(s, FADD(e, FADD(e1, e2)));
+}
+
+// |a|^2 = a.x^2 + a.y^2 (both terms non-negative: no cancellation, so the high words are summed
+// with a Fast2Sum ordered by magnitude).
+__device__ __forceinline__ ff ff_norm2(ff ax, ff ay) {
+    float p1 = FMUL(ax.h, ax.h);
+    float e1 = fmaf(ax.h, ax.h, -p1);
+    e1 = fmaf(FADD(ax.h, ax.h), ax.l, e1);
+    float p2 = FMUL(ay.h, ay.h);
+    float e2 = fmaf(ay.h, ay.h, -p2);
+    e2 = fmaf(FADD(ay.h, ay.h), ay.l, e2);
+    ff s = fast_two_sum(fmaxf(p1, p2), fminf(p1, p2));
+    return fast_two_sum(s.h, FADD(s.l, FADD(e1, e2)));
 }
 
 // 1 / a: correctly rounded float reciprocal of the high part, then one Newton step in ff.
@@ -130,30 +144,18 @@ __device__ __forceinline__ ff ff_rcp(ff a) {
     float y = __frcp_rn(a.h);
     float r = fmaf(-a.h, y, 1.0f);
     r = fmaf(-a.l, y, r);
-    return ff_norm(y, FMUL(y, r));
+    return fast_two_sum(y, FMUL(y, r));
 }
 
-// FP64 value of h + l for a normalised pair (|l| <= ulp(h)/2, as every operation above returns),
-// built bit by bit (no FP64 instruction).
-__device__ __forceinline__ double ff_to_double(ff a) {
-    float s = a.h, t = a.l;
-    unsigned hb = __float_as_uint(s);
-    int eh = (int)((hb >> 23) & 0xFF);
-    if (eh == 0) return 0.0;                            // zero (float subnormals flush to zero)
-    unsigned sg = hb >> 31;
-    long long M = (long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;   // units of 2^(Eh - 52)
-    unsigned lb = __float_as_uint(t);
-    int el = (int)((lb >> 23) & 0xFF);
-    if (el != 0) {
-        long long Ml = (long long)((lb & 0x7FFFFFu) | 0x800000u);
-        int sh = el - eh + 29;                          // <= 5 since |t| <= ulp(s)/2
-        long long v = sh >= 0 ? (Ml << sh) : (sh > -40 ? (Ml >> -sh) : 0LL);
-        M = ((lb >> 31) == sg) ? M + v : M - v;
-    }
-    int E = eh - 127;
-    if (M >= (1LL << 53)) { M >>= 1; E += 1; }
-    else if (M < (1LL << 52)) { M <<= 1; E -= 1; }
-    unsigned long long bits = ((unsigned long long)sg << 63) | ((unsigned long long)(E + 1023) << 52) |
-                              ((unsigned long long)M & ((1ULL << 52) - 1));
-    return __longlong_as_double((long long)bits);
+// FP64 value of a float, built bit by bit (no conversion instruction): sign, exponent rebiased
+// from 127 to 1023, significand shifted into place. Zero (and flushed subnormals) give 0.
+__device__ __forceinline__ double f2d_bits(float f) {
+    unsigned b = __float_as_uint(f);
+    unsigned hi = (((b & 0x7FFFFFFFu) >> 3) + (896u << 20)) | (b & 0x80000000u);
+    hi = (b & 0x7F800000u) ? hi : 0u;
+    return __hiloint2double((int)hi, (int)(b << 29));
 }
+
+// FP64 value of h + l: both words are exact in FP64, so one FP64 addition gives h + l correctly
+// rounded (the only FP64 instruction of the conversion).
+__device__ __forceinline__ double ff_to_double(ff a) { return f2d_bits(a.h) + f2d_bits(a.l); }

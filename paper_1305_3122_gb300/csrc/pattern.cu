@@ -157,6 +157,7 @@ __device__ __forceinline__ int fan_pos(const Fan& f, int32_t i, int kind, int32_
 
 // Row counts: simple rows from the fan analysis (closed: d + 1 entries, open: d + 2); general
 // rows by sorting; rows with more than FAST_DEG triangles are listed for the block kernels.
+// kind_out keeps the row kind in bits 0-1 and, for a simple row, its chain start in bits 2-4.
 // abase: start of each vertex's bucket in adj (the same offsets as vptr).
 __global__ void k_row_count(const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase,
                             const int2* __restrict__ adj, int32_t nq,
@@ -173,7 +174,7 @@ __global__ void k_row_count(const int32_t* __restrict__ vptr, const int32_t* __r
             int kind = fan_kind(f, start);
             if (kind != KIND_GENERAL) {
                 row_nnz[i] = d + 1 + (kind == KIND_OPEN);
-                kind_out[i] = (unsigned char)kind;
+                kind_out[i] = (unsigned char)(kind | (start << 2));    // the fill pass reuses the chain start
                 continue;
             }
         }
@@ -200,13 +201,11 @@ __global__ void k_row_fill(const int32_t* __restrict__ vptr, const int32_t* __re
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = (int32_t)r;
         int32_t abeg = abase[i], beg = vptr[i], d = vptr[i + 1] - beg;
-        int kind = kinds[i];
+        int kind = kinds[i] & 3, start = kinds[i] >> 2;
         int32_t o = row_ptr[i];
         if (kind != KIND_GENERAL) {
             Fan f;
             load_fan(adj, abeg, d, f);
-            int start;
-            fan_kind(f, start);
             int32_t jcur = 0, lcur = 0;
 #pragma unroll
             for (int e = 0; e < FAN_MAX; e++)

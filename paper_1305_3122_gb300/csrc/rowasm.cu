@@ -29,17 +29,17 @@ namespace {
 enum { W_S = 1, W_W = 2, W_M = 4 };
 
 struct Consts {
-    ff c60, c12, c24;           // 1/60, 1/12, 1/24 as double-floats
+    ff c60, c12, c24, c120;     // 1/60, 1/12, 1/24, 1/120 as double-floats
     ff l2m, lam, mu;            // lambda + 2 mu, lambda, mu (elasticity)
     double d60, d12, d24;       // the same in FP64 (general rows)
     double dl2m, dlam, dmu;     // elasticity constants in FP64 (badly shaped triangles)
 };
 
 // A neighbour of the row's vertex: relative coordinates r = p - p_i and weight as double-floats,
-// exact squared length |r|^2 (stiffness only), its approximate float value (for the conditioning
-// test), vertex id and column position.
+// the approximate float value of |r|^2 (for the conditioning test), vertex id and column
+// position.
 struct Nb {
-    ff x, y, w, nn;
+    ff x, y, w;
     float n;
     int32_t id;
     int pos;
@@ -66,19 +66,19 @@ __device__ __noinline__ RowTerms row_terms_fp64(const double2* __restrict__ q, c
     double e1x = pl.x - pi.x, e1y = pl.y - pi.y;      // e_{a+1} = r_l
     double e2x = pi.x - pj.x, e2y = pi.y - pj.y;      // e_{a+2} = -r_j
     double D = e1x * e2y - e2x * e1y;
-    t.d = ff_from_double(D, bad);
+    t.d = ff_from_value(D, bad);
     if (KIND & W_S) {
         double inv = 1.0 / (2.0 * D);
-        t.s[0] = ff_from_double((eax * eax + eay * eay) * inv, bad);
-        t.s[1] = ff_from_double((eax * e1x + eay * e1y) * inv, bad);
-        t.s[2] = ff_from_double((eax * e2x + eay * e2y) * inv, bad);
+        t.s[0] = ff_from_value((eax * eax + eay * eay) * inv, bad);
+        t.s[1] = ff_from_value((eax * e1x + eay * e1y) * inv, bad);
+        t.s[2] = ff_from_value((eax * e2x + eay * e2y) * inv, bad);
     }
     if (KIND & W_W) {
         double wi = w[i], wj = w[j], wl = w[l];
         double s = wi + wj + wl;
-        t.w[0] = ff_from_double(D * (s + 2.0 * wi), bad);
-        t.w[1] = ff_from_double(D * (s - 0.5 * wl), bad);
-        t.w[2] = ff_from_double(D * (s - 0.5 * wj), bad);
+        t.w[0] = ff_from_value(D * (s + 2.0 * wi), bad);
+        t.w[1] = ff_from_value(D * (s - 0.5 * wl), bad);
+        t.w[2] = ff_from_value(D * (s - 0.5 * wj), bad);
     }
     return t;
 }
@@ -89,7 +89,7 @@ __device__ __forceinline__ ff ff_rcp_fast(ff a) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a.h));
     float r = fmaf(-a.h, y, 1.0f);
     r = fmaf(-a.l, y, r);
-    return ff_norm(y, FMUL(y, r));
+    return fast_two_sum(y, FMUL(y, r));
 }
 
 // Shape test: sin^2 of each angle is D^2 over the product of the two adjacent squared edges;
@@ -109,9 +109,9 @@ __device__ __forceinline__ RowTerms row_terms(const double2* __restrict__ q, con
     if (!well_shaped(j, l, t.d.h)) return row_terms_fp64<KIND>(q, w, i, j.id, l.id, bad);
     if (KIND & W_S) {
         ff inv = ff_mulf(ff_rcp_fast(t.d), 0.5f);              // 1 / 2D
-        ff njl = ff_dot2(j.x, j.y, l.x, l.y);
-        t.s[1] = ff_mul(ff_sub(njl, l.nn), inv);                // (r_j - r_l) . r_l
-        t.s[2] = ff_mul(ff_sub(njl, j.nn), inv);                // (r_j - r_l) . (-r_j)
+        ff ax = ff_sub(j.x, l.x), ay = ff_sub(j.y, l.y);        // e_a = r_j - r_l
+        t.s[1] = ff_mul(ff_dot2(ax, ay, l.x, l.y), inv);        // e_a . r_l
+        t.s[2] = ff_neg(ff_mul(ff_dot2(ax, ay, j.x, j.y), inv)); // e_a . (-r_j)
     }
     if (KIND & W_W) {
         ff s = ff_add(ff_add(wi, j.w), l.w);
@@ -146,7 +146,6 @@ __device__ __forceinline__ Nb make_nb(const Raw& r, double2 pi, int& bad) {
     b.x = ff_from_double(r.p.x - pi.x, bad);
     b.y = ff_from_double(r.p.y - pi.y, bad);
     b.n = b.x.h * b.x.h + b.y.h * b.y.h;
-    b.nn = (KIND & W_S) ? ff_dot2(b.x, b.y, b.x, b.y) : ff_make(0.f);
     b.w = (KIND & W_W) ? ff_from_double(r.w, bad) : ff_make(0.f);
     b.id = r.id;
     b.pos = r.pos;
@@ -181,14 +180,134 @@ __device__ __forceinline__ void pick(const RowTerms& t, int which, ff& v0, ff& v
 
 }  // namespace
 
+// ---------------------------------------------------------------- scalar fan kernel
+//
+// Triangle e of a simple row's fan is (i, c, n) with c = n_e, n = n_{e+1} (counter-clockwise),
+// D_e = r_c x r_n = 2|T_e| and e_a = r_c - r_n its edge opposite i. Its contributions to row i:
+//   S   (Eq. 3):  column c: e_a . r_n / 2D          column n: -e_a . r_c / 2D
+//                 (e_a formed first: the Gram form r_c . r_n - |r_n|^2 cancels badly when the
+//                 edges at i are long against e_a)
+//   M^w (Eq. 2):  column c: (D u_c + B_e) / 120     column n: (D u_n + A_e) / 120
+//                 diagonal: (3 w_i D + A_e + B_e) / 60
+//                 with A_e = D w_c, B_e = D w_n and u_k = 2 (w_i + w_k) per neighbour
+//   M   (Eq. 1):  columns D / 24, diagonal D / 12.
+// Column n_e collects triangles e-1 and e; their D's are summed first, so the M^w entry is
+// ((D_{e-1} + D_e) u + A_{e-1} + B_e) / 120 with one product by u. The S diagonal is minus the
+// sum of the row's off-diagonal S entries (S 1 = 0).
+
+namespace {
+
+// Vertex record of the weighted kinds: coordinates (FP64) and the weight already split into a
+// double-float, 32 bytes, so a neighbour's data is one sector (one DRAM access on a miss)
+// instead of a 16-byte and an 8-byte gather from two arrays.
+struct __align__(16) VRec {
+    double x, y;
+    float wh, wl, pad0, pad1;
+};
+
+__global__ void k_pack_vrec(const double2* __restrict__ q, const double* __restrict__ w, int32_t nq,
+                            VRec* __restrict__ vr, int* __restrict__ err) {
+    int bad = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)nq; i += gridDim.x * blockDim.x) {
+        ff wf = ff_from_double(w[i], bad);
+        VRec r;
+        double2 p = q[i];
+        r.x = p.x;
+        r.y = p.y;
+        r.wh = wf.h;
+        r.wl = wf.l;
+        r.pad0 = r.pad1 = 0.f;
+        vr[i] = r;
+    }
+    if (bad) atomicOr(err, 2);
+}
+
+// Coordinates, weight and fan record of one neighbour, loaded one triangle ahead of its use.
+struct FanRaw {
+    double2 p;
+    ff w;
+    int32_t id;
+    int pos;
+};
+
 template <int KIND>
-__global__ void __launch_bounds__(256, 3) k_fan_scalar(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ vptr,
+__device__ __forceinline__ FanRaw fan_load(const double2* __restrict__ q, const VRec* __restrict__ vr, int2 rec) {
+    FanRaw r;
+    if (KIND & W_W) {
+        const double2* a2 = reinterpret_cast<const double2*>(vr + rec.x);
+        r.p = a2[0];
+        float4 t = *reinterpret_cast<const float4*>(a2 + 1);
+        r.w = ff{t.x, t.y};
+    } else {
+        r.p = q[rec.x];
+        r.w = z_ff();
+    }
+    r.id = rec.x;
+    r.pos = rec.y;
+    return r;
+}
+
+// A neighbour of the row's vertex in the scalar fan kernel.
+struct FanNb {
+    ff x, y;      // r = p - p_i
+    float n;      // |r|^2 from the high words (shape test)
+    ff w;         // w at the neighbour      (M^w)
+    int32_t id;
+    int pos;
+};
+
+// 2 (w_i + w_k) of a neighbour k (M^w)
+__device__ __forceinline__ ff fan_u(ff wi2, const FanNb& k) { return ff_add(wi2, ff{FADD(k.w.h, k.w.h), FADD(k.w.l, k.w.l)}); }
+
+template <int KIND>
+__device__ __forceinline__ FanNb fan_nb(const FanRaw& r, double2 pi, int& bad) {
+    FanNb b;
+    b.x = ff_from_double(r.p.x - pi.x, bad);              // exact FP64 differences, then split
+    b.y = ff_from_double(r.p.y - pi.y, bad);
+    b.n = b.x.h * b.x.h + b.y.h * b.y.h;
+    b.w = r.w;
+    b.id = r.id;
+    b.pos = r.pos;
+    return b;
+}
+
+// Shape test on the float parts (sin^2 of every angle at least 1/16), as for row_terms; ex, ey
+// are the high words of e_a.
+__device__ __forceinline__ bool fan_well_shaped(const FanNb& c, const FanNb& n, float ex, float ey, float dh) {
+    float eaa = ex * ex + ey * ey;
+    float d2 = 16.0f * dh * dh;
+    return d2 >= c.n * n.n && d2 >= eaa * n.n && d2 >= eaa * c.n;
+}
+
+// FP64 stiffness terms of a badly shaped triangle (i, c, n): D and the two half-cotangent terms.
+__device__ __noinline__ void fan_terms_fp64(const double2* __restrict__ q, int32_t i, int32_t c, int32_t n, ff& D,
+                                            ff& sc, ff& sn, int& bad) {
+    double2 pi = q[i], pc = q[c], pn = q[n];
+    double cx = pc.x - pi.x, cy = pc.y - pi.y, nx = pn.x - pi.x, ny = pn.y - pi.y;
+    double ax = pc.x - pn.x, ay = pc.y - pn.y;           // e_a
+    double d = cx * ny - cy * nx;
+    double inv = 0.5 / d;
+    D = ff_from_value(d, bad);
+    sc = ff_from_value((ax * nx + ay * ny) * inv, bad);
+    sn = ff_from_value(-(ax * cx + ay * cy) * inv, bad);
+}
+
+// FP64 value of a row entry.
+__device__ __forceinline__ void put(double* __restrict__ out, int32_t at, ff v) { out[at] = ff_to_double(v); }
+
+}  // namespace
+
+template <int KIND>
+__global__ void __launch_bounds__(128, 5) k_fan_scalar(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ vptr,
                                                        const int2* __restrict__ fan, const int2* __restrict__ hdr,
-                                                       const double2* __restrict__ q, const double* __restrict__ w, int32_t nq,
+                                                       const double2* __restrict__ q, const VRec* __restrict__ vr, int32_t nq,
                                                        Consts cs, double* __restrict__ out0, double* __restrict__ out1,
                                                        int* __restrict__ err) {
+    constexpr bool DS = (KIND & W_S) != 0, DW = (KIND & W_W) != 0, DM = KIND == W_M;
+    // outputs: S -> out0; M^w -> out1 with S, else out0; M -> out0
+    double* __restrict__ outW = DS ? out1 : out0;
     int bad = 0, orient = 0;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < (uint32_t)nq; r += gridDim.x * blockDim.x) {
         int32_t i = (int32_t)r;
         int2 h = hdr[i];
         int kind = h.y >> 28;
@@ -197,48 +316,91 @@ __global__ void __launch_bounds__(256, 3) k_fan_scalar(const int32_t* __restrict
         int pself = h.y & 0x3FFF;
         // neighbour k of the fan: k < d from the fan records; k == d is the last neighbour of an
         // open fan (from the header) or n_0 again for a closed fan
-        const int2 last = kind == 1 ? make_int2(h.x, (h.y >> 14) & 0x3FFF) : fan[b0];
-        double2 pi = q[i];
-        ff wi = (KIND & W_W) ? ff_from_double(w[i], bad) : ff_make(0.f);
-        Raw rn = load_raw<KIND>(q, w, fan[b0]);
-        Raw rp = load_raw<KIND>(q, w, d > 1 ? fan[b0 + 1] : last);
-        Nb cur = make_nb<KIND>(rn, pi, bad);
+        const int2 rec0 = fan[b0];
+        const int2 last = kind == 1 ? make_int2(h.x, (h.y >> 14) & 0x3FFF) : rec0;
+        FanRaw self = fan_load<KIND>(q, vr, make_int2(i, 0));
+        double2 pi = self.p;
+        ff wi2 = ff{FADD(self.w.h, self.w.h), FADD(self.w.l, self.w.l)};   // 2 w_i (M^w)
+        FanRaw rn = fan_load<KIND>(q, vr, rec0);
+        FanRaw rp = fan_load<KIND>(q, vr, d > 1 ? fan[b0 + 1] : last);
+        FanNb cur = fan_nb<KIND>(rn, pi, bad);
         const int first_pos = cur.pos;
-        const ff z = ff_make(0.f);
-        ff dg0 = z, dg1 = z, fs0 = z, fs1 = z, ca0 = z, ca1 = z;
+        const ff first_u = DW ? fan_u(wi2, cur) : z_ff();
+        ff caS = z_ff(), fsS = z_ff(), dgS = z_ff();                      // S
+        ff Dp = z_ff(), Ap = z_ff(), fsD = z_ff(), fsM = z_ff();          // M^w / M carries
+        ff sD = z_ff(), sAB = z_ff();                                     // diagonal sums
         for (int32_t e = 0; e < d; e++) {
             rn = rp;                                             // neighbour e + 1 (already loaded)
-            if (e + 2 <= d) rp = load_raw<KIND>(q, w, e + 2 < d ? fan[b0 + e + 2] : last);
-            Nb nxt = make_nb<KIND>(rn, pi, bad);
-            RowTerms t = row_terms<KIND>(q, w, i, cur, nxt, wi, bad);
-            orient |= !(t.d.h > 0.f);
-            ff j0, j1, l0, l1;
-            pick<KIND>(t, 1, j0, j1);
-            pick<KIND>(t, 2, l0, l1);
-            if (KIND == W_W || KIND == (W_S | W_W)) ff_acc(KIND == W_W ? dg0 : dg1, t.w[0]);
-            if (KIND == W_M) ff_acc(dg0, t.d);
-            if (e == 0) {
-                fs0 = j0;
-                fs1 = j1;
+            if (e + 2 <= d) rp = fan_load<KIND>(q, vr, e + 2 < d ? fan[b0 + e + 2] : last);
+            FanNb nxt = fan_nb<KIND>(rn, pi, bad);
+            ff D = ff_dot2(cur.x, nxt.x, nxt.y, ff_neg(cur.y));          // r_c x r_n
+            ff ax = ff_sub(cur.x, nxt.x), ay = ff_sub(cur.y, nxt.y);      // e_a
+            ff sc = z_ff(), sn = z_ff();
+            if (fan_well_shaped(cur, nxt, ax.h, ay.h, D.h)) {
+                if (DS) {
+                    ff inv = ff_rcp_fast(D);
+                    inv = ff{0.5f * inv.h, 0.5f * inv.l};               // 1 / 2D
+                    sc = ff_mul(ff_dot2(ax, ay, nxt.x, nxt.y), inv);
+                    sn = ff_neg(ff_mul(ff_dot2(ax, ay, cur.x, cur.y), inv));
+                }
             } else {
-                ff v0 = ff_add(ca0, j0);
-                if (KIND & W_S) ff_acc(dg0, ff_neg(v0));
-                emit<KIND>(out0, out1, rb + cur.pos, v0, ff_add(ca1, j1), false, cs);
+                fan_terms_fp64(q, i, cur.id, nxt.id, D, sc, sn, bad);
             }
-            ca0 = l0;
-            ca1 = l1;
+            orient |= !(D.h > 0.f);
+            ff A = z_ff(), B = z_ff();
+            if (DW) {
+                A = ff_mul(D, cur.w);
+                B = ff_mul(D, nxt.w);
+                ff_acc(sAB, ff_add(A, B));
+            }
+            ff_acc(sD, D);
+            if (e == 0) {
+                fsS = sc;
+                fsD = D;
+                if (DW) fsM = ff_add(ff_mul(D, first_u), B);             // n_0's share of triangle 0
+            } else {
+                // column n_e is complete: triangles e - 1 and e
+                ff sig = ff_add(Dp, D);
+                if (DS) {
+                    ff v = ff_add(caS, sc);
+                    ff_acc(dgS, ff_neg(v));
+                    put(out0, rb + cur.pos, v);
+                }
+                if (DW) put(outW, rb + cur.pos, ff_mul(ff_add(ff_add(ff_mul(sig, fan_u(wi2, cur)), Ap), B), cs.c120));
+                if (DM) put(out0, rb + cur.pos, ff_mul(sig, cs.c24));
+            }
+            caS = sn;
+            Dp = D;
+            Ap = A;
             cur = nxt;
         }
-        if (kind == 0) {
-            ff v0 = ff_add(fs0, ca0);
-            if (KIND & W_S) ff_acc(dg0, ff_neg(v0));
-            emit<KIND>(out0, out1, rb + first_pos, v0, ff_add(fs1, ca1), false, cs);
-        } else {
-            if (KIND & W_S) { ff_acc(dg0, ff_neg(fs0)); ff_acc(dg0, ff_neg(ca0)); }
-            emit<KIND>(out0, out1, rb + first_pos, fs0, fs1, false, cs);
-            emit<KIND>(out0, out1, rb + cur.pos, ca0, ca1, false, cs);
+        if (kind == 0) {                                         // closed: n_0 meets triangle d - 1
+            if (DS) {
+                ff v = ff_add(caS, fsS);
+                ff_acc(dgS, ff_neg(v));
+                put(out0, rb + first_pos, v);
+            }
+            if (DW) put(outW, rb + first_pos, ff_mul(ff_add(ff_add(ff_mul(Dp, first_u), Ap), fsM), cs.c120));
+            if (DM) put(out0, rb + first_pos, ff_mul(ff_add(Dp, fsD), cs.c24));
+        } else {                                                 // open: n_0 and n_d have one triangle each
+            if (DS) {
+                ff_acc(dgS, ff_neg(fsS));
+                ff_acc(dgS, ff_neg(caS));
+                put(out0, rb + first_pos, fsS);
+                put(out0, rb + cur.pos, caS);
+            }
+            if (DW) {
+                put(outW, rb + first_pos, ff_mul(fsM, cs.c120));
+                put(outW, rb + cur.pos, ff_mul(ff_add(ff_mul(Dp, fan_u(wi2, cur)), Ap), cs.c120));
+            }
+            if (DM) {
+                put(out0, rb + first_pos, ff_mul(fsD, cs.c24));
+                put(out0, rb + cur.pos, ff_mul(Dp, cs.c24));
+            }
         }
-        emit<KIND>(out0, out1, rb + pself, dg0, dg1, true, cs);
+        if (DS) put(out0, rb + pself, dgS);
+        if (DW) put(outW, rb + pself, ff_mul(ff_add(ff_mul(ff_mulf(wi2, 1.5f), sD), sAB), cs.c60));
+        if (DM) put(out0, rb + pself, ff_mul(sD, cs.c12));
     }
     if (bad) atomicOr(err, 2);
     if (orient) atomicOr(err, 1);
@@ -330,12 +492,12 @@ __device__ __noinline__ ff elas_terms_fp64(const double2* __restrict__ q, int32_
     double bx[3] = {eax, e1x, e2x}, by[3] = {eay, e1y, e2y};
     double l2m = cs.dl2m, lam = cs.dlam, mu = cs.dmu;
     for (int b = 0; b < 3; b++) {
-        out[b].k00 = ff_from_double(l2m * ay * by[b] + mu * ax * bx[b], bad);
-        out[b].k01 = ff_from_double(-(lam * ay * bx[b] + mu * ax * by[b]), bad);
-        out[b].k10 = ff_from_double(-(lam * ax * by[b] + mu * ay * bx[b]), bad);
-        out[b].k11 = ff_from_double(l2m * ax * bx[b] + mu * ay * by[b], bad);
+        out[b].k00 = ff_from_value(l2m * ay * by[b] + mu * ax * bx[b], bad);
+        out[b].k01 = ff_from_value(-(lam * ay * bx[b] + mu * ax * by[b]), bad);
+        out[b].k10 = ff_from_value(-(lam * ax * by[b] + mu * ay * bx[b]), bad);
+        out[b].k11 = ff_from_value(l2m * ax * bx[b] + mu * ay * by[b], bad);
     }
-    return ff_from_double(D, bad);
+    return ff_from_value(D, bad);
 }
 
 __device__ __forceinline__ ff elas_terms(const double2* __restrict__ q, int32_t i, const Nb& j, const Nb& l,
@@ -460,6 +622,7 @@ static Consts make_consts(double lam, double mu) {
     c.c60 = host_ff(1.0 / 60.0);
     c.c12 = host_ff(1.0 / 12.0);
     c.c24 = host_ff(1.0 / 24.0);
+    c.c120 = host_ff(1.0 / 120.0);
     c.l2m = host_ff(lam + 2.0 * mu);
     c.lam = host_ff(lam);
     c.mu = host_ff(mu);
@@ -473,13 +636,28 @@ static Consts make_consts(double lam, double mu) {
 }
 
 static constexpr int FAN_BLOCK = 256;
+static constexpr int FAN_SCALAR_BLOCK = 128;   // 5 blocks of 128 per SM at up to 96 registers
 static constexpr int GEN_BLOCK = 64;
 
 template <int KIND>
 static fe_status launch_scalar(fe_mesh m, fe_pattern p, const double* w, double* out0, double* out1, cudaStream_t s) {
     Consts cs = make_consts(0.0, 0.0);
-    { FE_PROF("k_fan_scalar", s); k_fan_scalar<KIND><<<fe_grid(m->nq, FAN_BLOCK, 8), FAN_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, w, m->nq, cs, out0, out1, m->err); }
-    FE_LAUNCHED("k_fan_scalar");
+    VRec* vr = nullptr;
+    FeStreamScope scope(s);
+    if (KIND & W_W) {
+        fe_status st = fe_alloc_n(&vr, (size_t)m->nq, "vertex records");
+        if (st) return st;
+        { FE_PROF("k_pack_vrec", s); k_pack_vrec<<<fe_grid(m->nq, 256), 256, 0, s>>>(m->q, w, m->nq, vr, m->err); }
+        cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) {
+            fe_free(vr);
+            return fe_cuda_fail(e0, "k_pack_vrec");
+        }
+    }
+    { FE_PROF("k_fan_scalar", s); k_fan_scalar<KIND><<<fe_grid(m->nq, FAN_SCALAR_BLOCK, 5), FAN_SCALAR_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, m->nq, cs, out0, out1, m->err); }
+    cudaError_t e = cudaGetLastError();
+    fe_free(vr);
+    if (e != cudaSuccess) return fe_cuda_fail(e, "k_fan_scalar");
     if (p->n_gen > 0) {
         { FE_PROF("k_general_scalar", s); k_general_scalar<KIND><<<p->n_gen, GEN_BLOCK, 0, s>>>(p->gen_rows, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q, w, cs, out0, out1, m->err); }
         FE_LAUNCHED("k_general_scalar");

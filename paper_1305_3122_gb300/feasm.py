@@ -388,4 +388,8 @@ def assemble_host(kind: str, q: np.ndarray, me: np.ndarray, w: np.ndarray | None
         out[name] = dst
     (stream or torch.cuda.current_stream()).synchronize()
     out["nnz"] = pat.nnz
+    # release the device arrays now: the pattern's index views refer back to the pattern, so
+    # without an explicit close they would wait for Python's cycle collector
+    pat.close()
+    mesh.close()
     return out
