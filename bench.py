@@ -414,7 +414,8 @@ def batched(feasm, meshgen, torch, args) -> dict:
     fm = [feasm.Mesh(x.q, x.me) for x in meshes]
     fp = [feasm.Pattern(x) for x in fm]
     b = feasm.Batch(fm, fp)
-    block, tile = b.tune()
+    b.tune()
+    variant, block, tile = b.config()
     nme = sum(x.nme for x in meshes)
 
     def timed(fn, reps=10):
@@ -434,8 +435,12 @@ def batched(feasm, meshgen, torch, args) -> dict:
     ms_p = timed(b.assemble_plain)
     return {"meshes": len(meshes), "nme": nme, "graph_ms": round(ms_g, 4), "plain_ms": round(ms_p, 4),
             "graph_melem_s": round(nme / ms_g / 1e3, 2), "plain_melem_s": round(nme / ms_p / 1e3, 2),
-            "speedup": round(ms_p / ms_g, 3), "shape": {"block": block, "tile": tile},
-            "what": "S + M (Eq. 1, Eq. 3) of 256 meshes, one graph-replayed persistent launch vs 256 plain launches"}
+            "speedup": round(ms_p / ms_g, 3),
+            "tuned": {"variant": {feasm.ROW: "row", feasm.ATOMIC: "atomic"}[variant], "block": block, "tile": tile,
+                      "units_per_thread": tile / block,
+                      "unit": "rows" if variant == feasm.ROW else "triangles"},
+            "what": "S + M (Eq. 1, Eq. 3) of 256 meshes, one graph-replayed persistent launch vs 256 plain "
+                    "launches of the same scheme; scheme, block and tile picked by fe_batch_tune"}
 
 
 def e2e(feasm, torch, m, w, args) -> dict:

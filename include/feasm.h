@@ -89,7 +89,7 @@ enum {
     FE_PATTERN_GATHER = 1,  /* also the element-to-nnz map, the per-non-zero contribution lists
                                (seg_ptr, perm) and the staging buffer of FE_VARIANT_GATHER and
                                of the deterministic adjoint */
-    FE_PATTERN_MAP = 2      /* also the element-to-nnz map (FE_VARIANT_ATOMIC, adjoint, batches) */
+    FE_PATTERN_MAP = 2      /* also the element-to-nnz map (FE_VARIANT_ATOMIC, adjoint, atomic batches) */
 };
 
 /* ----------------------------------------------------------------------------- meshes ---- */
@@ -209,29 +209,40 @@ fe_status fe_adjoint_stiff_wmass(fe_mesh mesh, fe_pattern pattern, const double*
 
 /* A batch assembles S and M (the mass matrix of Eq. 1) for n independent meshes in one
  * persistent kernel launch, replayed from a captured CUDA graph. meshes[m] / patterns[m] are
- * borrowed (they must outlive the batch); patterns are scalar with the element-to-nnz map
- * (FE_PATTERN_MAP). The tile size and block size
- * come from fe_batch_tune (or defaults). Not in the paper. */
+ * borrowed (they must outlive the batch); patterns are scalar. Two schemes:
+ *   FE_VARIANT_ROW     row owners walk tiles of rows (tile = rows per tile); any pattern;
+ *   FE_VARIANT_ATOMIC  threads walk tiles of triangles (tile = triangles per tile) and add with
+ *                      FP64 atomics; needs every pattern built with FE_PATTERN_MAP.
+ * The scheme, block size and tile size come from fe_batch_tune, fe_batch_configure, or the
+ * defaults (FE_VARIANT_ROW, 256, 1024). Not in the paper. */
 fe_status fe_batch_create(int32_t n, const fe_mesh* meshes, const fe_pattern* patterns,
                           fe_batch* out);
 
-/* Times candidate launch shapes (block size x triangles per tile) on this batch with the
- * given output buffers and keeps the fastest; writes the choice to *block and *tile if not
- * NULL. Synchronises. */
+/* Times every candidate (scheme x block size x tile size) on this batch with the given
+ * output buffers, keeps the fastest and recaptures the graph; writes the chosen block and tile
+ * to *block and *tile if not NULL (the scheme: fe_batch_get_config). Synchronises. */
 fe_status fe_batch_tune(fe_batch batch, double* const* S_values, double* const* M_values,
                         fe_stream stream, int32_t* block, int32_t* tile);
 
-/* Sets the launch shape explicitly (block in {64..1024}, tile >= 1 triangles). */
+/* Sets the scheme and launch shape explicitly: variant FE_VARIANT_ROW (block 64..256) or
+ * FE_VARIANT_ATOMIC (block 64..1024), block a multiple of 32, tile >= 1. Synchronises the
+ * device (the graph may be in flight) and recaptures the graph. */
+fe_status fe_batch_configure(fe_batch batch, int32_t variant, int32_t block, int32_t tile);
+
+/* fe_batch_configure with the current scheme. */
 fe_status fe_batch_set_shape(fe_batch batch, int32_t block, int32_t tile);
 
+/* The current scheme, block size and tile size (any pointer may be NULL). */
+fe_status fe_batch_get_config(fe_batch batch, int32_t* variant, int32_t* block, int32_t* tile);
+
 /* S_values[m], M_values[m]: device FP64 outputs of mesh m (capacity = that pattern's nnz).
- * The first call with a given set of output pointers captures a CUDA graph (memsets + one
- * persistent kernel); later calls with the same pointers replay it. */
+ * Replays the batch's graph; a new set of output pointers is copied into the batch's device
+ * pointer tables first (stream-ordered). */
 fe_status fe_batch_assemble_stiff_mass(fe_batch batch, double* const* S_values,
                                        double* const* M_values, fe_stream stream);
 
-/* The same work as n separate plain launches (one memset pair + one kernel per mesh), for
- * comparison with the batched launch. */
+/* The same work as n separate plain launches of the batch's scheme (per mesh: the row-owner
+ * kernels, or one memset pair and one atomic kernel), for comparison with the batched launch. */
 fe_status fe_batch_assemble_stiff_mass_plain(fe_batch batch, double* const* S_values,
                                              double* const* M_values, fe_stream stream);
 

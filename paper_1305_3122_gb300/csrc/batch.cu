@@ -1,13 +1,17 @@
 // batch.cu -- many independent meshes assembled in one persistent launch under a CUDA graph.
 //
-// Not in the paper. A batch concatenates the triangles of its meshes into a list of tiles
-// (mesh, first triangle, last triangle). One zeroing kernel clears every output and one
-// persistent kernel (grid = SMs x resident blocks) walks the tile list round-robin, computing
-// the stiffness S (Eq. 3) and mass M (Eq. 1) of each triangle and adding them into its mesh's
-// CSR values with FP64 atomics. The two kernels are captured once in a CUDA graph and replayed;
-// outputs are read from device pointer tables, so changing the output buffers only rewrites
-// the tables. fe_batch_tune times a small grid of (block size, tile size) shapes and keeps the
-// fastest.
+// Not in the paper. A batch assembles the stiffness S (Eq. 3) and mass M (Eq. 1) of each of its
+// meshes with one of two schemes:
+//   FE_VARIANT_ROW     the row-owner fan computation (rowasm.cu) over a list of row tiles
+//                      (mesh, first row, end row): every value written once, no zeroing, no map;
+//                      general rows of all meshes are a second list, one block each;
+//   FE_VARIANT_ATOMIC  a list of triangle tiles (mesh, first triangle, end triangle): a zeroing
+//                      kernel, then each triangle's entries added with FP64 atomics through the
+//                      element-to-nnz map.
+// One persistent kernel (grid = SMs x resident blocks) walks its tile list round-robin. The
+// launches are captured once in a CUDA graph and replayed; outputs are read from device pointer
+// tables, so changing the output buffers only rewrites the tables. fe_batch_tune times every
+// (scheme, block size, tile size) in a small grid and keeps the fastest.
 #include <string.h>
 
 #include <vector>
@@ -28,6 +32,11 @@ struct Tile {
 
 struct fe_batch_s {
     int32_t n = 0;
+    int variant = FE_VARIANT_ROW;
+    bool has_map = true;                 // every pattern carries the element-to-nnz map
+    fe_row_mesh* d_rdesc = nullptr;
+    int2* d_gen = nullptr;               // general rows (mesh, row)
+    int32_t ngen = 0;
     std::vector<fe_mesh> meshes;
     std::vector<fe_pattern> patterns;
     MeshDesc* d_desc = nullptr;
@@ -109,13 +118,16 @@ static int resident_blocks(int block) {
     return per_sm > 0 ? per_sm : 1;
 }
 
+// Tiles of triangles (FE_VARIANT_ATOMIC) or of rows (FE_VARIANT_ROW), b->tile units each.
 static fe_status make_tiles(fe_batch b) {
     std::vector<Tile> tiles;
-    for (int32_t m = 0; m < b->n; m++)
-        for (int32_t k = 0; k < b->meshes[m]->nme; k += b->tile) {
-            int32_t e = k + b->tile < b->meshes[m]->nme ? k + b->tile : b->meshes[m]->nme;
+    for (int32_t m = 0; m < b->n; m++) {
+        int32_t units = b->variant == FE_VARIANT_ROW ? b->meshes[m]->nq : b->meshes[m]->nme;
+        for (int32_t k = 0; k < units; k += b->tile) {
+            int32_t e = k + b->tile < units ? k + b->tile : units;
             tiles.push_back({m, k, e});
         }
+    }
     fe_free(b->d_tiles);
     b->d_tiles = nullptr;
     b->ntiles = (int32_t)tiles.size();
@@ -126,6 +138,12 @@ static fe_status make_tiles(fe_batch b) {
 }
 
 static void launch_batch(fe_batch b, cudaStream_t s) {
+    if (b->variant == FE_VARIANT_ROW) {
+        static_assert(sizeof(Tile) == sizeof(fe_row_tile), "tile layouts must agree");
+        fe_row_batch_launch(b->d_rdesc, reinterpret_cast<const fe_row_tile*>(b->d_tiles), b->ntiles, b->d_gen, b->ngen,
+                            b->d_S, b->d_M, b->block, s);
+        return;
+    }
     unsigned zgrid = (unsigned)(b->n < 4 * fe_sm_count() ? (b->n > 0 ? b->n : 1) : 4 * fe_sm_count());
     { FE_PROF("k_batch_zero", s); k_batch_zero<<<zgrid, 256, 0, s>>>(b->d_desc, b->n, b->d_S, b->d_M); }
     int64_t want = (int64_t)fe_sm_count() * resident_blocks(b->block);
@@ -168,6 +186,8 @@ extern "C" void fe_batch_destroy(fe_batch b) {
     drop_graph(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     fe_free(b->d_desc);
+    fe_free(b->d_rdesc);
+    fe_free(b->d_gen);
     fe_free(b->d_S);
     fe_free(b->d_tiles);
     if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
@@ -179,24 +199,41 @@ extern "C" fe_status fe_batch_create(int32_t n, const fe_mesh* meshes, const fe_
     *out = nullptr;
     if (n < 0 || (n > 0 && (!meshes || !patterns))) return fe_fail(FE_ERR_INVALID_ARG, "bad mesh list");
     std::vector<MeshDesc> desc(n > 0 ? n : 1);
+    std::vector<fe_row_mesh> rdesc(n > 0 ? n : 1);
+    std::vector<int2> gen;
     FeStreamScope scope(nullptr);
     fe_batch b = new fe_batch_s();
     b->n = n;
     for (int32_t m = 0; m < n; m++) {
         fe_status st = fe_check_pair(meshes[m], patterns[m], 1);
-        if (!st && !patterns[m]->map) st = fe_fail(FE_ERR_INVALID_ARG, "batched assembly needs patterns built with FE_PATTERN_MAP");
         if (st) { fe_batch_destroy(b); return st; }
-        b->meshes.push_back(meshes[m]);
-        b->patterns.push_back(patterns[m]);
-        desc[m] = {meshes[m]->q, meshes[m]->me, patterns[m]->map, meshes[m]->nme, (int32_t)patterns[m]->nnz};
-        b->total_nnz += patterns[m]->nnz;
-        b->total_nme += meshes[m]->nme;
+        fe_mesh me = meshes[m];
+        fe_pattern p = patterns[m];
+        b->meshes.push_back(me);
+        b->patterns.push_back(p);
+        b->has_map = b->has_map && p->map != nullptr;
+        desc[m] = {me->q, me->me, p->map, me->nme, (int32_t)p->nnz};
+        rdesc[m] = {p->row_ptr, p->col_idx, p->vptr, p->fan, p->hdr, me->q, me->err, me->nq};
+        if (p->n_gen > 0) {
+            std::vector<int32_t> rows(p->n_gen);
+            cudaError_t e = cudaMemcpy(rows.data(), p->gen_rows, sizeof(int32_t) * p->n_gen, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) { fe_batch_destroy(b); return fe_cuda_fail(e, "batch general rows"); }
+            for (int32_t r : rows) gen.push_back(make_int2(m, r));
+        }
+        b->total_nnz += p->nnz;
+        b->total_nme += me->nme;
     }
+    if (!b->has_map) b->variant = FE_VARIANT_ROW;
+    b->ngen = (int32_t)gen.size();
     fe_status st = fe_alloc_n(&b->d_desc, desc.size(), "batch descriptors");
+    if (!st) st = fe_alloc_n(&b->d_rdesc, rdesc.size(), "batch row descriptors");
+    if (!st) st = fe_alloc_n(&b->d_gen, gen.size(), "batch general rows");
     if (!st) st = fe_alloc_n(&b->d_S, 2 * (size_t)(n > 0 ? n : 1), "batch output tables");
     if (st) { fe_batch_destroy(b); return st; }
     b->d_M = b->d_S + n;
     cudaError_t e = cudaMemcpy(b->d_desc, desc.data(), sizeof(MeshDesc) * desc.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_rdesc, rdesc.data(), sizeof(fe_row_mesh) * rdesc.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !gen.empty()) e = cudaMemcpy(b->d_gen, gen.data(), sizeof(int2) * gen.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_ptrs, sizeof(double*) * 2 * (n > 0 ? n : 1));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { fe_batch_destroy(b); return fe_cuda_fail(e, "batch setup"); }
@@ -207,17 +244,37 @@ extern "C" fe_status fe_batch_create(int32_t n, const fe_mesh* meshes, const fe_
     return FE_OK;
 }
 
-extern "C" fe_status fe_batch_set_shape(fe_batch b, int32_t block, int32_t tile) {
+static int max_block(int variant) { return variant == FE_VARIANT_ROW ? 256 : 1024; }
+
+extern "C" fe_status fe_batch_configure(fe_batch b, int32_t variant, int32_t block, int32_t tile) {
     if (!b) return fe_fail(FE_ERR_INVALID_ARG, "null batch");
-    if (block < 64 || block > 1024 || block % 32 || tile < 1) return fe_fail(FE_ERR_INVALID_ARG, "bad batch shape");
-    if (block == b->block && tile == b->tile) return FE_OK;
+    if (variant != FE_VARIANT_ROW && variant != FE_VARIANT_ATOMIC)
+        return fe_fail(FE_ERR_INVALID_ARG, "batches support FE_VARIANT_ROW and FE_VARIANT_ATOMIC");
+    if (variant == FE_VARIANT_ATOMIC && !b->has_map)
+        return fe_fail(FE_ERR_INVALID_ARG, "FE_VARIANT_ATOMIC needs every pattern built with FE_PATTERN_MAP");
+    if (block < 64 || block > max_block(variant) || block % 32 || tile < 1) return fe_fail(FE_ERR_INVALID_ARG, "bad batch shape");
+    if (variant == b->variant && block == b->block && tile == b->tile) return FE_OK;
     FE_CUDA(cudaDeviceSynchronize());   // the graph may be in flight
     FeStreamScope scope(nullptr);
+    b->variant = variant;
     b->block = block;
     b->tile = tile;
     fe_status st = make_tiles(b);
     if (!st) st = capture(b);
     return st;
+}
+
+extern "C" fe_status fe_batch_set_shape(fe_batch b, int32_t block, int32_t tile) {
+    if (!b) return fe_fail(FE_ERR_INVALID_ARG, "null batch");
+    return fe_batch_configure(b, b->variant, block, tile);
+}
+
+extern "C" fe_status fe_batch_get_config(fe_batch b, int32_t* variant, int32_t* block, int32_t* tile) {
+    if (!b) return fe_fail(FE_ERR_INVALID_ARG, "null batch");
+    if (variant) *variant = b->variant;
+    if (block) *block = b->block;
+    if (tile) *tile = b->tile;
+    return FE_OK;
 }
 
 extern "C" fe_status fe_batch_assemble_stiff_mass(fe_batch b, double* const* S, double* const* M, fe_stream stream) {
@@ -237,6 +294,12 @@ extern "C" fe_status fe_batch_assemble_stiff_mass_plain(fe_batch b, double* cons
     for (int32_t m = 0; m < b->n; m++) {
         fe_mesh me = b->meshes[m];
         fe_pattern p = b->patterns[m];
+        if (b->variant == FE_VARIANT_ROW) {
+            if (p->nnz > 0 && (!S[m] || !M[m])) return fe_fail(FE_ERR_INVALID_ARG, "null output buffer in batch");
+            fe_status st = fe_row_scalar(1 | 4, me, p, nullptr, S[m], M[m], s);   // W_S | W_M
+            if (st) return st;
+            continue;
+        }
         if (p->nnz > 0) {
             if (!S[m] || !M[m]) return fe_fail(FE_ERR_INVALID_ARG, "null output buffer in batch");
             FE_CUDA(cudaMemsetAsync(S[m], 0, sizeof(double) * p->nnz, s));
@@ -258,15 +321,20 @@ extern "C" fe_status fe_batch_tune(fe_batch b, double* const* S, double* const* 
     if (st) return st;
     FE_CUDA(cudaStreamSynchronize(s));
     FeStreamScope scope(nullptr);
+    const int variants[] = {FE_VARIANT_ROW, FE_VARIANT_ATOMIC};
     const int blocks[] = {128, 256, 512};
     const int tiles[] = {256, 1024, 4096};
     cudaEvent_t e0, e1;
     FE_CUDA(cudaEventCreate(&e0));
     FE_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bb = b->block, bt = b->tile;
+    int bv = b->variant, bb = b->block, bt = b->tile;
+    for (int var : variants)
     for (int blk : blocks)
         for (int tl : tiles) {
+            if (var == FE_VARIANT_ATOMIC && !b->has_map) continue;
+            if (blk > max_block(var)) continue;
+            b->variant = var;
             b->block = blk;
             b->tile = tl;
             if ((st = make_tiles(b))) break;
@@ -278,11 +346,12 @@ extern "C" fe_status fe_batch_tune(fe_batch b, double* const* S, double* const* 
             if (e != cudaSuccess) { st = fe_cuda_fail(e, "batch tuning"); break; }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; bb = blk; bt = tl; }
+            if (ms < best) { best = ms; bv = var; bb = blk; bt = tl; }
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) return st;
+    b->variant = bv;
     b->block = bb;
     b->tile = bt;
     if ((st = make_tiles(b))) return st;

@@ -54,6 +54,26 @@ struct fe_pattern_s {
 // longest triangle fan a simple row may have (rows with more go to the general path)
 constexpr int FE_FAN_MAX = 8;
 
+
+// Row-owner assembly of S and M for batches of meshes (rowasm.cu): per-mesh arrays, tiles of
+// rows, and the list of general rows as (mesh, row).
+struct fe_row_mesh {
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    const int32_t* vptr;
+    const int2* fan;
+    const int2* hdr;
+    const double2* q;
+    int* err;
+    int32_t nq;
+};
+struct fe_row_tile {
+    int32_t mesh, r0, r1;
+};
+int fe_row_batch_resident(int block);
+void fe_row_batch_launch(const fe_row_mesh* desc, const fe_row_tile* tiles, int32_t ntiles, const int2* general,
+                         int32_t ngeneral, double* const* S, double* const* M, int block, cudaStream_t s);
+
 // row-owner assembly (rowasm.cu); kind bits: 1 = S, 2 = M^w, 4 = M
 fe_status fe_row_scalar(int kind_bits, fe_mesh m, fe_pattern p, const double* w, double* out0, double* out1,
                         cudaStream_t s);

@@ -555,14 +555,14 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     // column digit inside each row, unique
     size_t big_smem = (2 * (size_t)FE_MAX_VALENCE + 1) * (sizeof(int32_t) + 1);
     if (nq > 0) {
-        { FE_PROF("k_row_count", s); k_row_count<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.row_nnz, t.kinds, t.big_list, t.counters, t.flag); }
+        { FE_PROF("k_row_count", s); k_row_count<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.row_nnz, t.kinds, t.big_list, t.counters, t.flag); }
         FE_LAUNCHED("k_row_count");
         { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, nullptr, t.row_nnz, nullptr); }
         FE_LAUNCHED("k_row_big (count)");
     }
     if ((st = fe_exclusive_scan(t.row_nnz, p->row_ptr, nq, s, nullptr))) return st;
     if (nq > 0) {
-        { FE_PROF("k_row_fill", s); k_row_fill<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.kinds, p->row_ptr, p->col_idx, p->fan,
+        { FE_PROF("k_row_fill", s); k_row_fill<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.kinds, p->row_ptr, p->col_idx, p->fan,
                                                                                    p->hdr, p->gen_rows, t.counters + 1); }
         FE_LAUNCHED("k_row_fill");
         { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->row_ptr, nullptr, p->col_idx); }

@@ -159,23 +159,14 @@ __device__ __forceinline__ Nb load_nb(const double2* __restrict__ q, const doubl
     return make_nb<KIND>(load_raw<KIND>(q, w, make_int2(c, pos)), pi, bad);
 }
 
-// Value (or pair of values) of one row entry, scaled and converted to FP64.
-template <int KIND>
-__device__ __forceinline__ void emit(double* __restrict__ out0, double* __restrict__ out1, int32_t at, ff a0, ff a1,
-                                     bool diag, const Consts& cs) {
-    if (KIND == W_M) a0 = ff_mul(a0, diag ? cs.c12 : cs.c24);
-    if (KIND == W_W) a0 = ff_mul(a0, cs.c60);
-    out0[at] = ff_to_double(a0);
-    if (KIND == (W_S | W_W)) out1[at] = ff_to_double(ff_mul(a1, cs.c60));
-}
-
-// per-contribution values of the two outputs (out0: S, else M^w, else M; out1: M^w with S)
+// per-contribution values of the two outputs (out0: S, else M^w, else M; out1: M^w or M with S),
+// unscaled (M^w by 1/60, M by 1/12 or 1/24 at the end)
 template <int KIND>
 __device__ __forceinline__ void pick(const RowTerms& t, int which, ff& v0, ff& v1) {
     if (KIND & W_S) v0 = t.s[which];
     else if (KIND & W_W) v0 = t.w[which];
     else v0 = t.d;
-    v1 = (KIND == (W_S | W_W)) ? t.w[which] : ff_make(0.f);
+    v1 = !(KIND & W_S) ? ff_make(0.f) : (KIND & W_W) ? t.w[which] : (KIND & W_M) ? t.d : ff_make(0.f);
 }
 
 }  // namespace
@@ -297,111 +288,121 @@ __device__ __forceinline__ void put(double* __restrict__ out, int32_t at, ff v) 
 
 }  // namespace
 
+// One simple row of the scalar kinds (S, M^w, M, or two of them): see the header of this section.
+// KIND bits: W_S stiffness, W_W weighted mass, W_M mass. The first matrix goes to out0, a second
+// one (with W_S) to out1.
+template <int KIND>
+__device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ vptr,
+                                        const int2* __restrict__ fan, const int2* __restrict__ hdr,
+                                        const double2* __restrict__ q, const VRec* __restrict__ vr, const Consts& cs,
+                                        double* __restrict__ out0, double* __restrict__ out1, int& bad, int& orient) {
+    constexpr bool DS = (KIND & W_S) != 0, DW = (KIND & W_W) != 0, DM = (KIND & W_M) != 0;
+    double* __restrict__ outX = DS ? out1 : out0;            // M^w or M
+    int2 h = hdr[i];
+    int kind = h.y >> 28;
+    if (kind > 1) return;                                    // general row (or no triangle)
+    int32_t rb = row_ptr[i], b0 = vptr[i], d = vptr[i + 1] - b0;
+    int pself = h.y & 0x3FFF;
+    // neighbour k of the fan: k < d from the fan records; k == d is the last neighbour of an
+    // open fan (from the header) or n_0 again for a closed fan
+    const int2 rec0 = fan[b0];
+    const int2 last = kind == 1 ? make_int2(h.x, (h.y >> 14) & 0x3FFF) : rec0;
+    FanRaw self = fan_load<KIND>(q, vr, make_int2(i, 0));
+    double2 pi = self.p;
+    ff wi2 = ff{FADD(self.w.h, self.w.h), FADD(self.w.l, self.w.l)};   // 2 w_i (M^w)
+    // neighbours are loaded one triangle ahead of their use (N_k = fan[b0 + k] for k < d,
+    // N_d = last); loading two ahead costs more in occupancy than it gains
+    FanRaw rn = fan_load<KIND>(q, vr, rec0);
+    FanRaw rp = fan_load<KIND>(q, vr, d > 1 ? fan[b0 + 1] : last);
+    FanNb cur = fan_nb<KIND>(rn, pi, bad);
+    const int first_pos = cur.pos;
+    const ff first_u = DW ? fan_u(wi2, cur) : z_ff();
+    ff caS = z_ff(), fsS = z_ff(), dgS = z_ff();                      // S
+    ff Dp = z_ff(), Ap = z_ff(), fsD = z_ff(), fsM = z_ff();          // M^w / M carries
+    ff sD = z_ff(), sAB = z_ff();                                     // diagonal sums
+    for (int32_t e = 0; e < d; e++) {
+        rn = rp;                                             // neighbour e + 1 (already loaded)
+        if (e + 2 <= d) rp = fan_load<KIND>(q, vr, e + 2 < d ? fan[b0 + e + 2] : last);
+        FanNb nxt = fan_nb<KIND>(rn, pi, bad);
+        ff D = ff_dot2(cur.x, nxt.x, nxt.y, ff_neg(cur.y));          // r_c x r_n
+        ff ax = ff_sub(cur.x, nxt.x), ay = ff_sub(cur.y, nxt.y);      // e_a
+        ff sc = z_ff(), sn = z_ff();
+        if (fan_well_shaped(cur, nxt, ax.h, ay.h, D.h)) {
+            if (DS) {
+                ff inv = ff_rcp_fast(D);
+                inv = ff{0.5f * inv.h, 0.5f * inv.l};               // 1 / 2D
+                sc = ff_mul(ff_dot2(ax, ay, nxt.x, nxt.y), inv);
+                sn = ff_neg(ff_mul(ff_dot2(ax, ay, cur.x, cur.y), inv));
+            }
+        } else {
+            fan_terms_fp64(q, i, cur.id, nxt.id, D, sc, sn, bad);
+        }
+        orient |= !(D.h > 0.f);
+        ff A = z_ff(), B = z_ff();
+        if (DW) {
+            A = ff_mul(D, cur.w);
+            B = ff_mul(D, nxt.w);
+            ff_acc(sAB, ff_add(A, B));
+        }
+        ff_acc(sD, D);
+        if (e == 0) {
+            fsS = sc;
+            fsD = D;
+            if (DW) fsM = ff_add(ff_mul(D, first_u), B);             // n_0's share of triangle 0
+        } else {
+            // column n_e is complete: triangles e - 1 and e
+            ff sig = ff_add(Dp, D);
+            if (DS) {
+                ff v = ff_add(caS, sc);
+                ff_acc(dgS, ff_neg(v));
+                put(out0, rb + cur.pos, v);
+            }
+            if (DW) put(outX, rb + cur.pos, ff_mul(ff_add(ff_add(ff_mul(sig, fan_u(wi2, cur)), Ap), B), cs.c120));
+            if (DM) put(outX, rb + cur.pos, ff_mul(sig, cs.c24));
+        }
+        caS = sn;
+        Dp = D;
+        Ap = A;
+        cur = nxt;
+    }
+    if (kind == 0) {                                         // closed: n_0 meets triangle d - 1
+        if (DS) {
+            ff v = ff_add(caS, fsS);
+            ff_acc(dgS, ff_neg(v));
+            put(out0, rb + first_pos, v);
+        }
+        if (DW) put(outX, rb + first_pos, ff_mul(ff_add(ff_add(ff_mul(Dp, first_u), Ap), fsM), cs.c120));
+        if (DM) put(outX, rb + first_pos, ff_mul(ff_add(Dp, fsD), cs.c24));
+    } else {                                                 // open: n_0 and n_d have one triangle each
+        if (DS) {
+            ff_acc(dgS, ff_neg(fsS));
+            ff_acc(dgS, ff_neg(caS));
+            put(out0, rb + first_pos, fsS);
+            put(out0, rb + cur.pos, caS);
+        }
+        if (DW) {
+            put(outX, rb + first_pos, ff_mul(fsM, cs.c120));
+            put(outX, rb + cur.pos, ff_mul(ff_add(ff_mul(Dp, fan_u(wi2, cur)), Ap), cs.c120));
+        }
+        if (DM) {
+            put(outX, rb + first_pos, ff_mul(fsD, cs.c24));
+            put(outX, rb + cur.pos, ff_mul(Dp, cs.c24));
+        }
+    }
+    if (DS) put(out0, rb + pself, dgS);
+    if (DW) put(outX, rb + pself, ff_mul(ff_add(ff_mul(ff_mulf(wi2, 1.5f), sD), sAB), cs.c60));
+    if (DM) put(outX, rb + pself, ff_mul(sD, cs.c12));
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(128, 5) k_fan_scalar(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ vptr,
                                                        const int2* __restrict__ fan, const int2* __restrict__ hdr,
                                                        const double2* __restrict__ q, const VRec* __restrict__ vr, int32_t nq,
                                                        Consts cs, double* __restrict__ out0, double* __restrict__ out1,
                                                        int* __restrict__ err) {
-    constexpr bool DS = (KIND & W_S) != 0, DW = (KIND & W_W) != 0, DM = KIND == W_M;
-    // outputs: S -> out0; M^w -> out1 with S, else out0; M -> out0
-    double* __restrict__ outW = DS ? out1 : out0;
     int bad = 0, orient = 0;
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < (uint32_t)nq; r += gridDim.x * blockDim.x) {
-        int32_t i = (int32_t)r;
-        int2 h = hdr[i];
-        int kind = h.y >> 28;
-        if (kind > 1) continue;                                  // general row (or no triangle)
-        int32_t rb = row_ptr[i], b0 = vptr[i], d = vptr[i + 1] - b0;
-        int pself = h.y & 0x3FFF;
-        // neighbour k of the fan: k < d from the fan records; k == d is the last neighbour of an
-        // open fan (from the header) or n_0 again for a closed fan
-        const int2 rec0 = fan[b0];
-        const int2 last = kind == 1 ? make_int2(h.x, (h.y >> 14) & 0x3FFF) : rec0;
-        FanRaw self = fan_load<KIND>(q, vr, make_int2(i, 0));
-        double2 pi = self.p;
-        ff wi2 = ff{FADD(self.w.h, self.w.h), FADD(self.w.l, self.w.l)};   // 2 w_i (M^w)
-        FanRaw rn = fan_load<KIND>(q, vr, rec0);
-        FanRaw rp = fan_load<KIND>(q, vr, d > 1 ? fan[b0 + 1] : last);
-        FanNb cur = fan_nb<KIND>(rn, pi, bad);
-        const int first_pos = cur.pos;
-        const ff first_u = DW ? fan_u(wi2, cur) : z_ff();
-        ff caS = z_ff(), fsS = z_ff(), dgS = z_ff();                      // S
-        ff Dp = z_ff(), Ap = z_ff(), fsD = z_ff(), fsM = z_ff();          // M^w / M carries
-        ff sD = z_ff(), sAB = z_ff();                                     // diagonal sums
-        for (int32_t e = 0; e < d; e++) {
-            rn = rp;                                             // neighbour e + 1 (already loaded)
-            if (e + 2 <= d) rp = fan_load<KIND>(q, vr, e + 2 < d ? fan[b0 + e + 2] : last);
-            FanNb nxt = fan_nb<KIND>(rn, pi, bad);
-            ff D = ff_dot2(cur.x, nxt.x, nxt.y, ff_neg(cur.y));          // r_c x r_n
-            ff ax = ff_sub(cur.x, nxt.x), ay = ff_sub(cur.y, nxt.y);      // e_a
-            ff sc = z_ff(), sn = z_ff();
-            if (fan_well_shaped(cur, nxt, ax.h, ay.h, D.h)) {
-                if (DS) {
-                    ff inv = ff_rcp_fast(D);
-                    inv = ff{0.5f * inv.h, 0.5f * inv.l};               // 1 / 2D
-                    sc = ff_mul(ff_dot2(ax, ay, nxt.x, nxt.y), inv);
-                    sn = ff_neg(ff_mul(ff_dot2(ax, ay, cur.x, cur.y), inv));
-                }
-            } else {
-                fan_terms_fp64(q, i, cur.id, nxt.id, D, sc, sn, bad);
-            }
-            orient |= !(D.h > 0.f);
-            ff A = z_ff(), B = z_ff();
-            if (DW) {
-                A = ff_mul(D, cur.w);
-                B = ff_mul(D, nxt.w);
-                ff_acc(sAB, ff_add(A, B));
-            }
-            ff_acc(sD, D);
-            if (e == 0) {
-                fsS = sc;
-                fsD = D;
-                if (DW) fsM = ff_add(ff_mul(D, first_u), B);             // n_0's share of triangle 0
-            } else {
-                // column n_e is complete: triangles e - 1 and e
-                ff sig = ff_add(Dp, D);
-                if (DS) {
-                    ff v = ff_add(caS, sc);
-                    ff_acc(dgS, ff_neg(v));
-                    put(out0, rb + cur.pos, v);
-                }
-                if (DW) put(outW, rb + cur.pos, ff_mul(ff_add(ff_add(ff_mul(sig, fan_u(wi2, cur)), Ap), B), cs.c120));
-                if (DM) put(out0, rb + cur.pos, ff_mul(sig, cs.c24));
-            }
-            caS = sn;
-            Dp = D;
-            Ap = A;
-            cur = nxt;
-        }
-        if (kind == 0) {                                         // closed: n_0 meets triangle d - 1
-            if (DS) {
-                ff v = ff_add(caS, fsS);
-                ff_acc(dgS, ff_neg(v));
-                put(out0, rb + first_pos, v);
-            }
-            if (DW) put(outW, rb + first_pos, ff_mul(ff_add(ff_add(ff_mul(Dp, first_u), Ap), fsM), cs.c120));
-            if (DM) put(out0, rb + first_pos, ff_mul(ff_add(Dp, fsD), cs.c24));
-        } else {                                                 // open: n_0 and n_d have one triangle each
-            if (DS) {
-                ff_acc(dgS, ff_neg(fsS));
-                ff_acc(dgS, ff_neg(caS));
-                put(out0, rb + first_pos, fsS);
-                put(out0, rb + cur.pos, caS);
-            }
-            if (DW) {
-                put(outW, rb + first_pos, ff_mul(fsM, cs.c120));
-                put(outW, rb + cur.pos, ff_mul(ff_add(ff_mul(Dp, fan_u(wi2, cur)), Ap), cs.c120));
-            }
-            if (DM) {
-                put(out0, rb + first_pos, ff_mul(fsD, cs.c24));
-                put(out0, rb + cur.pos, ff_mul(Dp, cs.c24));
-            }
-        }
-        if (DS) put(out0, rb + pself, dgS);
-        if (DW) put(outW, rb + pself, ff_mul(ff_add(ff_mul(ff_mulf(wi2, 1.5f), sD), sAB), cs.c60));
-        if (DM) put(out0, rb + pself, ff_mul(sD, cs.c12));
-    }
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < (uint32_t)nq; r += gridDim.x * blockDim.x)
+        fan_row<KIND>((int32_t)r, row_ptr, vptr, fan, hdr, q, vr, cs, out0, out1, bad, orient);
     if (bad) atomicOr(err, 2);
     if (orient) atomicOr(err, 1);
 }
@@ -412,17 +413,17 @@ __device__ __forceinline__ void neumaier(double& sum, double& c, double v) {
     sum = t;
 }
 
+// One general row, by one block: thread t owns column t of the row.
 template <int KIND>
-__global__ void k_general_scalar(const int32_t* __restrict__ gen, const int32_t* __restrict__ row_ptr,
-                                 const int32_t* __restrict__ col_idx, const int32_t* __restrict__ vptr,
-                                 const int2* __restrict__ fan, const double2* __restrict__ q,
-                                 const double* __restrict__ w, Consts cs, double* __restrict__ out0,
-                                 double* __restrict__ out1, int* __restrict__ err) {
-    int32_t i = gen[blockIdx.x];
+__device__ __forceinline__ void general_row(int32_t i, const int32_t* __restrict__ row_ptr,
+                                            const int32_t* __restrict__ col_idx, const int32_t* __restrict__ vptr,
+                                            const int2* __restrict__ fan, const double2* __restrict__ q,
+                                            const double* __restrict__ w, const Consts& cs, double* __restrict__ out0,
+                                            double* __restrict__ out1, int& bad, int& orient) {
+    constexpr bool TWO = (KIND & W_S) && (KIND & (W_W | W_M));   // a second matrix in out1
     int32_t rb = row_ptr[i], u = row_ptr[i + 1] - rb;
     int32_t b0 = vptr[i], d = vptr[i + 1] - b0;
     double2 pi = q[i];
-    int bad = 0, orient = 0;
     ff wi = (KIND & W_W) ? ff_from_double(w[i], bad) : ff_make(0.f);
     for (int t = threadIdx.x; t < u; t += blockDim.x) {
         int32_t col = col_idx[rb + t];
@@ -440,16 +441,60 @@ __global__ void k_general_scalar(const int32_t* __restrict__ gen, const int32_t*
             ff v0, v1;
             pick<KIND>(rt, which, v0, v1);
             neumaier(s0, c0, ff_to_double(v0));
-            if (KIND == (W_S | W_W)) neumaier(s1, c1, ff_to_double(v1));
+            if (TWO) neumaier(s1, c1, ff_to_double(v1));
         }
         double v = s0 + c0;
         if (KIND == W_M) v *= self ? cs.d12 : cs.d24;
         if (KIND == W_W) v *= cs.d60;
+        const double scale1 = (KIND & W_W) ? cs.d60 : (self ? cs.d12 : cs.d24);
         out0[rb + t] = v;
-        if (KIND == (W_S | W_W)) out1[rb + t] = (s1 + c1) * cs.d60;
+        if (TWO) out1[rb + t] = (s1 + c1) * scale1;
     }
+}
+
+template <int KIND>
+__global__ void k_general_scalar(const int32_t* __restrict__ gen, const int32_t* __restrict__ row_ptr,
+                                 const int32_t* __restrict__ col_idx, const int32_t* __restrict__ vptr,
+                                 const int2* __restrict__ fan, const double2* __restrict__ q,
+                                 const double* __restrict__ w, Consts cs, double* __restrict__ out0,
+                                 double* __restrict__ out1, int* __restrict__ err) {
+    int bad = 0, orient = 0;
+    general_row<KIND>(gen[blockIdx.x], row_ptr, col_idx, vptr, fan, q, w, cs, out0, out1, bad, orient);
     if (bad) atomicOr(err, 2);
     if (orient) atomicOr(err, 1);
+}
+
+// ---------------------------------------------------------------- batches of meshes
+//
+// S and M (W_S | W_M) of many meshes by row owners: one persistent launch walks a list of row
+// tiles (mesh, first row, end row); general rows of all meshes are a second list, one block
+// each. Output pointers come from device tables, so new output buffers need no new launch.
+
+__global__ void __launch_bounds__(256) k_batch_rows(const fe_row_mesh* __restrict__ desc,
+                                                    const fe_row_tile* __restrict__ tiles, int32_t ntiles,
+                                                    double* const* __restrict__ S, double* const* __restrict__ M,
+                                                    Consts cs) {
+    for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        fe_row_tile tl = tiles[t];
+        fe_row_mesh d = desc[tl.mesh];
+        double* s = S[tl.mesh];
+        double* m = M[tl.mesh];
+        int bad = 0, orient = 0;
+        for (int32_t i = tl.r0 + threadIdx.x; i < tl.r1; i += blockDim.x)
+            fan_row<W_S | W_M>(i, d.row_ptr, d.vptr, d.fan, d.hdr, d.q, nullptr, cs, s, m, bad, orient);
+        if (bad) atomicOr(d.err, 2);
+        if (orient) atomicOr(d.err, 1);
+    }
+}
+
+__global__ void k_batch_general(const fe_row_mesh* __restrict__ desc, const int2* __restrict__ list,
+                                double* const* __restrict__ S, double* const* __restrict__ M, Consts cs) {
+    int2 e = list[blockIdx.x];                                   // (mesh, row)
+    fe_row_mesh d = desc[e.x];
+    int bad = 0, orient = 0;
+    general_row<W_S | W_M>(e.y, d.row_ptr, d.col_idx, d.vptr, d.fan, d.q, nullptr, cs, S[e.x], M[e.x], bad, orient);
+    if (bad) atomicOr(d.err, 2);
+    if (orient) atomicOr(d.err, 1);
 }
 
 // ---------------------------------------------------------------- elasticity
@@ -673,6 +718,7 @@ fe_status fe_row_scalar(int kind_bits, fe_mesh m, fe_pattern p, const double* w,
         case W_W: return launch_scalar<W_W>(m, p, w, out0, out1, s);
         case W_M: return launch_scalar<W_M>(m, p, w, out0, out1, s);
         case W_S | W_W: return launch_scalar<W_S | W_W>(m, p, w, out0, out1, s);
+        case W_S | W_M: return launch_scalar<W_S | W_M>(m, p, w, out0, out1, s);
     }
     return fe_fail(FE_ERR_INVALID_ARG, "internal: bad row kind");
 }
@@ -687,4 +733,23 @@ fe_status fe_row_elas(fe_mesh m, fe_pattern p, double lam, double mu, double* ou
         FE_LAUNCHED("k_general_elas");
     }
     return FE_OK;
+}
+
+int fe_row_batch_resident(int block) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_rows, block, 0);
+    return per_sm > 0 ? per_sm : 1;
+}
+
+void fe_row_batch_launch(const fe_row_mesh* desc, const fe_row_tile* tiles, int32_t ntiles, const int2* general,
+                         int32_t ngeneral, double* const* S, double* const* M, int block, cudaStream_t s) {
+    Consts cs = make_consts(0.0, 0.0);
+    if (ntiles > 0) {
+        int64_t want = (int64_t)fe_sm_count() * fe_row_batch_resident(block);
+        unsigned grid = (unsigned)(ntiles < want ? ntiles : want);
+        { FE_PROF("k_batch_rows", s); k_batch_rows<<<grid, block, 0, s>>>(desc, tiles, ntiles, S, M, cs); }
+    }
+    if (ngeneral > 0) {
+        { FE_PROF("k_batch_general", s); k_batch_general<<<ngeneral, GEN_BLOCK, 0, s>>>(desc, general, S, M, cs); }
+    }
 }

@@ -50,6 +50,8 @@ SIGNATURES = {
     "fe_batch_create": (_INT, [_I32, _P, _P, ctypes.POINTER(_P)]),
     "fe_batch_tune": (_INT, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "fe_batch_set_shape": (_INT, [_P, _I32, _I32]),
+    "fe_batch_configure": (_INT, [_P, _I32, _I32, _I32]),
+    "fe_batch_get_config": (_INT, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "fe_batch_assemble_stiff_mass": (_INT, [_P, _P, _P, _P]),
     "fe_batch_assemble_stiff_mass_plain": (_INT, [_P, _P, _P, _P]),
     "fe_batch_destroy": (None, [_P]),
@@ -334,6 +336,17 @@ class Batch:
 
     def set_shape(self, block: int, tile: int):
         _check(lib().fe_batch_set_shape(self._h, block, tile), "fe_batch_set_shape")
+
+    def configure(self, variant: int, block: int, tile: int):
+        """Scheme (ROW or ATOMIC), block size and tile size; recaptures the graph."""
+        _check(lib().fe_batch_configure(self._h, variant, block, tile), "fe_batch_configure")
+
+    def config(self) -> tuple[int, int, int]:
+        """(variant, block, tile) currently captured."""
+        v, b, t = _I32(), _I32(), _I32()
+        _check(lib().fe_batch_get_config(self._h, ctypes.byref(v), ctypes.byref(b), ctypes.byref(t)),
+               "fe_batch_get_config")
+        return v.value, b.value, t.value
 
     def assemble(self, stream=None):
         _check(lib().fe_batch_assemble_stiff_mass(self._h, self._tables[0], self._tables[1], _stream(stream)),

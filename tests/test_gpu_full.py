@@ -193,10 +193,13 @@ def batch4():
     return meshes, fm, fp
 
 
-def test_batch_matches_plain_and_oracle(batch4):
+@pytest.mark.parametrize("variant", [feasm.ROW, feasm.ATOMIC])
+def test_batch_matches_plain_and_oracle(batch4, variant):
     meshes, fm, fp = batch4
     assert len(meshes) == 256
     b = feasm.Batch(fm, fp)
+    b.configure(variant, 256, 1024)
+    assert b.config() == (variant, 256, 1024)
     S, M = b.assemble()
     S = [t.clone() for t in S]
     M = [t.clone() for t in M]
@@ -205,7 +208,7 @@ def test_batch_matches_plain_and_oracle(batch4):
         rp = p.row_ptr.cpu().numpy()
         assert_values_close(rp, s0.cpu().numpy(), s1.cpu().numpy())
         assert_values_close(rp, m0.cpu().numpy(), m1.cpu().numpy())
-    for idx in (int(np.argmin([mm.nme for mm in meshes])), 7):
+    for idx in (int(np.argmin([mm.nme for mm in meshes])), 7, int(np.argmax([mm.nme for mm in meshes]))):
         m = meshes[idx]
         rp, ci, vs = oracle.assemble(oracle.STIFF, m.q, m.me)
         _, _, vm = oracle.assemble(oracle.MASS, m.q, m.me)
@@ -214,12 +217,41 @@ def test_batch_matches_plain_and_oracle(batch4):
         assert_values_close(rp, M[idx].cpu().numpy(), vm)
 
 
+def test_batch_row_variant_is_deterministic(batch4):
+    meshes, fm, fp = batch4
+    b = feasm.Batch(fm[:16], fp[:16])
+    b.configure(feasm.ROW, 128, 256)
+    ref = [t.clone() for t in b.assemble()[0]]
+    for _ in range(3):
+        for x, y in zip(ref, b.assemble()[0]):
+            assert torch.equal(x, y)
+
+
 def test_batch_tune_and_replay(batch4):
     meshes, fm, fp = batch4
     b = feasm.Batch(fm[:32], fp[:32])
     block, tile = b.tune()
+    variant, block2, tile2 = b.config()
+    assert (block2, tile2) == (block, tile)
+    assert variant in (feasm.ROW, feasm.ATOMIC)
     assert block in (128, 256, 512) and tile in (256, 1024, 4096)
     S1 = [t.clone() for t in b.assemble()[0]]
     S2 = b.assemble()[0]
     for p, x, y in zip(fp[:32], S1, S2):
         assert_values_close(p.row_ptr.cpu().numpy(), y.cpu().numpy(), x.cpu().numpy())
+
+
+def test_batch_without_map_uses_row_owners():
+    ms = [meshgen.square_mesh(n, 40 + n) for n in (3, 17, 40)]
+    fm = [feasm.Mesh(m.q, m.me) for m in ms]
+    fp = [feasm.Pattern(x, map=False) for x in fm]
+    b = feasm.Batch(fm, fp)
+    assert b.config()[0] == feasm.ROW
+    with pytest.raises(feasm.FeasmError):
+        b.configure(feasm.ATOMIC, 256, 1024)
+    S, M = b.assemble()
+    for m, s, mm, p in zip(ms, S, M, fp):
+        rp, _, vs = oracle.assemble(oracle.STIFF, m.q, m.me)
+        _, _, vm = oracle.assemble(oracle.MASS, m.q, m.me)
+        assert_values_close(rp, s.cpu().numpy(), vs)
+        assert_values_close(rp, mm.cpu().numpy(), vm)
