@@ -310,10 +310,12 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
     FanRaw self = fan_load<KIND>(q, vr, make_int2(i, 0));
     double2 pi = self.p;
     ff wi2 = ff{FADD(self.w.h, self.w.h), FADD(self.w.l, self.w.l)};   // 2 w_i (M^w)
-    // neighbours are loaded one triangle ahead of their use (N_k = fan[b0 + k] for k < d,
-    // N_d = last); loading two ahead costs more in occupancy than it gains
+    // neighbour data are loaded one triangle ahead of their use and fan records two ahead, so a
+    // gather never waits for its own record (N_k = fan[b0 + k] for k < d, N_d = last); loading
+    // the data two ahead costs more in occupancy than it gains
     FanRaw rn = fan_load<KIND>(q, vr, rec0);
     FanRaw rp = fan_load<KIND>(q, vr, d > 1 ? fan[b0 + 1] : last);
+    int2 recn = d > 2 ? fan[b0 + 2] : last;                  // N_2
     FanNb cur = fan_nb<KIND>(rn, pi, bad);
     const int first_pos = cur.pos;
     const ff first_u = DW ? fan_u(wi2, cur) : z_ff();
@@ -322,7 +324,10 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
     ff sD = z_ff(), sAB = z_ff();                                     // diagonal sums
     for (int32_t e = 0; e < d; e++) {
         rn = rp;                                             // neighbour e + 1 (already loaded)
-        if (e + 2 <= d) rp = fan_load<KIND>(q, vr, e + 2 < d ? fan[b0 + e + 2] : last);
+        if (e + 2 <= d) {
+            rp = fan_load<KIND>(q, vr, recn);                // N_{e+2}
+            recn = e + 3 < d ? fan[b0 + e + 3] : last;       // N_{e+3}
+        }
         FanNb nxt = fan_nb<KIND>(rn, pi, bad);
         ff D = ff_dot2(cur.x, nxt.x, nxt.y, ff_neg(cur.y));          // r_c x r_n
         ff ax = ff_sub(cur.x, nxt.x), ay = ff_sub(cur.y, nxt.y);      // e_a

@@ -255,3 +255,27 @@ def test_batch_without_map_uses_row_owners():
         _, _, vm = oracle.assemble(oracle.MASS, m.q, m.me)
         assert_values_close(rp, s.cpu().numpy(), vs)
         assert_values_close(rp, mm.cpu().numpy(), vm)
+
+
+def test_batch_general_rows_match_oracle():
+    """A batch whose meshes contain general rows (a vertex of valence 70, and a vertex shared by
+    two separate fans): the row-owner scheme routes them through its general-row list."""
+    from tests.test_gpu_parity import fan_mesh
+    qf, mef = fan_mesh(70)
+    q2 = np.array([[0.0, 1.0, 0.0, -1.0, 0.0], [0.0, 0.0, 1.0, 0.0, -1.0]])
+    me2 = np.array([[0, 0], [1, 3], [2, 4]], np.int32)          # two triangles touching at vertex 0 only
+    sq = meshgen.square_mesh(9, 77)
+    cases = [(qf, mef), (sq.q, sq.me), (q2, me2)]
+    fm = [feasm.Mesh(q, me) for q, me in cases]
+    fp = [feasm.Pattern(x, map=False) for x in fm]
+    b = feasm.Batch(fm, fp)
+    for variant_shape in [(128, 256), (256, 4096)]:
+        b.configure(feasm.ROW, *variant_shape)
+        S, M = b.assemble()
+        for (q, me), s, mm in zip(cases, S, M):
+            rp, _, vs = oracle.assemble(oracle.STIFF, q, me)
+            _, _, vm = oracle.assemble(oracle.MASS, q, me)
+            assert_values_close(rp, s.cpu().numpy(), vs)
+            assert_values_close(rp, mm.cpu().numpy(), vm)
+    for x in fm:
+        x.check()
