@@ -66,7 +66,10 @@ typedef struct fe_mesh_s* fe_mesh;        /* owns device copies of q and me */
 typedef struct fe_pattern_s* fe_pattern;  /* owns the CSR structure and element-to-nnz map */
 typedef struct fe_batch_s* fe_batch;      /* a set of (mesh, pattern) assembled together */
 
-enum { FE_PTR_HOST = 0, FE_PTR_DEVICE = 1 };
+/* Where the arrays passed to fe_mesh_create live. FE_PTR_DEVICE_BORROW: device memory, and the
+ * mesh uses the caller's me in place instead of copying it (q is always packed into the mesh's
+ * own array); the caller keeps me valid and unchanged until fe_mesh_destroy. */
+enum { FE_PTR_HOST = 0, FE_PTR_DEVICE = 1, FE_PTR_DEVICE_BORROW = 2 };
 
 /* Scatter variants of the assembly calls. */
 enum {
@@ -96,7 +99,7 @@ enum {
 
 /* Creates a mesh from q ([2][nq] FP64) and me ([3][nme] int32), both host (FE_PTR_HOST) or
  * device (FE_PTR_DEVICE) memory; the library copies them (the caller keeps ownership of its
- * arrays). Validates every triangle: ids in [0, nq) (else FE_ERR_INDEX_RANGE), three distinct
+ * arrays), except me under FE_PTR_DEVICE_BORROW, which is used in place. Validates every triangle: ids in [0, nq) (else FE_ERR_INDEX_RANGE), three distinct
  * vertices (FE_ERR_DEGENERATE), signed area > 0 (FE_ERR_ORIENTATION). Synchronises the stream
  * once to read the validation result. nme = 0 is allowed (an empty mesh). Paper: Section 2
  * (mesh arrays q, me; areas derived, see the header comment). */
@@ -107,6 +110,7 @@ fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, const int32_t
  * Asynchronous; does not re-validate orientation (assembly calls report it, see
  * fe_mesh_check). */
 fe_status fe_mesh_set_coords(fe_mesh mesh, const double* q, int ptr_kind, fe_stream stream);
+/* (ptr_kind: FE_PTR_HOST or FE_PTR_DEVICE; FE_PTR_DEVICE_BORROW is taken as FE_PTR_DEVICE.) */
 
 /* Reads and clears the mesh's device-side error word, set by an assembly call that met a
  * triangle with signed area <= 0 after fe_mesh_set_coords (FE_ERR_ORIENTATION), or, for
@@ -172,6 +176,20 @@ fe_status fe_assemble_stiff_wmass(fe_mesh mesh, fe_pattern pattern, const double
  * Needs a dofs_per_vertex = 2 pattern; lambda + mu > 0 (Section 7) else FE_ERR_INVALID_ARG. */
 fe_status fe_assemble_elas(fe_mesh mesh, fe_pattern pattern, double lambda, double mu,
                            int variant, double* values, int64_t cap, fe_stream stream);
+
+/* End to end: S and M^w (FE_VARIANT_ROW) from host arrays q [2][nq], me [3][nme], w [nq] to host
+ * CSR arrays row_ptr [nq + 1], col_idx, S, Mw [cap]. Creates and validates the mesh, builds the
+ * pattern, assembles, and copies back, overlapping the copies with the work where the data allow
+ * (the weight upload with mesh validation; the col_idx download and the value download of each
+ * of 8 row blocks with the assembly of the later blocks). Output buffers should be pinned host
+ * memory for the copies to overlap (pageable memory works, without overlap). *nnz gets the
+ * number of stored entries; if cap < nnz the call returns FE_ERR_BUFFER_TOO_SMALL with *nnz set
+ * and row_ptr unspecified (6 nme + nq always suffices). Errors of the mesh as for fe_mesh_create,
+ * and of the values as for fe_mesh_check. Synchronises. Not in the paper (its Matlab call has no
+ * device memory). */
+fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const double* q, const int32_t* me,
+                                       const double* w, int32_t* row_ptr, int32_t* col_idx, double* S,
+                                       double* Mw, int64_t cap, int64_t* nnz, fe_stream stream);
 
 /* S and M^w as fe_assemble_stiff_wmass with FE_VARIANT_GATHER, for callers that must not have
  * device memory allocated during the call (work being captured into a CUDA graph, frameworks

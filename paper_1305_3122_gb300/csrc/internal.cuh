@@ -14,6 +14,7 @@ struct fe_mesh_s {
     int32_t nq = 0, nme = 0;
     double2* q = nullptr;       // [nq] (x, y) pairs: one 16-byte load per vertex gather
     int32_t* me = nullptr;      // [3][nme], the caller's layout
+    bool me_owned = true;       // false: the caller's device array, used in place
     int32_t* deg = nullptr;     // [nq + 1] triangles per vertex (counted during validation)
     int* err = nullptr;         // device error word: bit 0 = a triangle with signed area <= 0,
                                 // bit 1 = a value outside the double-float range (see ff.cuh)
@@ -132,7 +133,7 @@ inline unsigned fe_grid(int64_t n, int block, int per_sm = 8) {
 // is not null (it then reads the total back).
 // With round > 1 (a power of two) each input is first rounded up to a multiple of round.
 fe_status fe_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s,
-                            int64_t* total_out, int round = 1);
+                            int64_t* total_out, int round = 1, int32_t* out2 = nullptr);
 
 // ------------------------------------------------------------------------ checks shared by calls
 

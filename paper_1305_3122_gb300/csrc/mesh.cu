@@ -109,7 +109,7 @@ extern "C" void fe_mesh_destroy(fe_mesh m) {
     if (!m) return;
     FeStreamScope scope(m->last_stream);
     fe_free(m->q);
-    fe_free(m->me);
+    if (m->me_owned) fe_free(m->me);
     fe_free(m->err);
     fe_free(m->deg);
     delete m;
@@ -121,7 +121,10 @@ extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, co
     *out = nullptr;
     if (nq < 0 || nme < 0) return fe_fail(FE_ERR_INVALID_ARG, "nq and nme must be >= 0");
     if ((nq > 0 && !q) || (nme > 0 && !me)) return fe_fail(FE_ERR_INVALID_ARG, "q or me is null");
-    if (ptr_kind != FE_PTR_HOST && ptr_kind != FE_PTR_DEVICE) return fe_fail(FE_ERR_INVALID_ARG, "bad ptr_kind");
+    if (ptr_kind != FE_PTR_HOST && ptr_kind != FE_PTR_DEVICE && ptr_kind != FE_PTR_DEVICE_BORROW)
+        return fe_fail(FE_ERR_INVALID_ARG, "bad ptr_kind");
+    const bool borrow = ptr_kind == FE_PTR_DEVICE_BORROW;
+    if (borrow) ptr_kind = FE_PTR_DEVICE;
     if ((int64_t)nme * 9 >= INT32_MAX)
         return fe_fail(FE_ERR_LIMIT, "9*nme must be < 2^31");
     cudaStream_t s = (cudaStream_t)stream;
@@ -132,15 +135,21 @@ extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, co
     m->nme = nme;
     m->topology_id = g_topology_counter.fetch_add(1);
     fe_status st = fe_alloc_n(&m->q, (size_t)nq, "mesh coordinates");
-    if (!st) st = fe_alloc_n(&m->me, 3 * (size_t)nme, "mesh connectivity");
+    if (borrow) {
+        m->me = const_cast<int32_t*>(me);
+        m->me_owned = false;
+    } else {
+        if (!st) st = fe_alloc_n(&m->me, 3 * (size_t)nme, "mesh connectivity");
+        if (!st) st = copy_in(m->me, me, 3 * (size_t)nme * sizeof(int32_t), ptr_kind, s);
+    }
     if (!st) st = fe_alloc_n(&m->err, 4, "mesh error word");
     if (!st) st = fe_alloc_n(&m->deg, (size_t)nq + 1, "vertex valences");
-    if (!st) st = copy_in(m->me, me, 3 * (size_t)nme * sizeof(int32_t), ptr_kind, s);
     if (!st) st = set_coords(m, q, ptr_kind, s);
     if (st) { fe_mesh_destroy(m); return st; }
-    int init[4] = {0, INT32_MAX, INT32_MAX, INT32_MAX};
+    // error word: [0] = 0, [1..3] = 0x7F7F7F7F (above any triangle index: "none yet" for atomicMin)
     int word[4];
-    cudaError_t e = cudaMemcpyAsync(m->err, init, sizeof init, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaMemsetAsync(m->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->err + 1, 0x7F, 3 * sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->deg, 0, sizeof(int32_t) * ((size_t)nq + 1), s);
     if (e == cudaSuccess && nme > 0) {
         { FE_PROF("k_validate", s); k_validate<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg); }
@@ -169,6 +178,7 @@ extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, co
 
 extern "C" fe_status fe_mesh_set_coords(fe_mesh m, const double* q, int ptr_kind, fe_stream stream) {
     if (!m || (m->nq > 0 && !q)) return fe_fail(FE_ERR_INVALID_ARG, "null mesh or q");
+    if (ptr_kind == FE_PTR_DEVICE_BORROW) ptr_kind = FE_PTR_DEVICE;
     if (ptr_kind != FE_PTR_HOST && ptr_kind != FE_PTR_DEVICE) return fe_fail(FE_ERR_INVALID_ARG, "bad ptr_kind");
     FeStreamScope scope((cudaStream_t)stream);
     m->last_stream = (cudaStream_t)stream;

@@ -498,11 +498,11 @@ extern "C" void fe_pattern_destroy(fe_pattern p) {
 namespace {
 struct Temps {
     int32_t *row_nnz = nullptr, *big_list = nullptr, *counters = nullptr, *cur = nullptr;
-    int* flag = nullptr;
+    int* flag = nullptr;                 // points into counters (counters[0..1], flags[2..3])
     int2* adj = nullptr;
     unsigned char* kinds = nullptr;
     ~Temps() {
-        fe_free(row_nnz); fe_free(big_list); fe_free(counters); fe_free(flag); fe_free(adj); fe_free(kinds);
+        fe_free(row_nnz); fe_free(big_list); fe_free(counters); fe_free(adj); fe_free(kinds);
         fe_free(cur);
     }
 };
@@ -522,37 +522,26 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     if (cap >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "6*nme + nq must be < 2^31");
     Temps t;
     fe_status st;
-    if ((st = fe_alloc_n(&p->row_ptr, (size_t)nq + 1, "row_ptr"))) return st;
+    // Arrays are allocated just before their first use, so that the host-side allocation calls
+    // overlap the kernels already queued instead of delaying the first one.
     if ((st = fe_alloc_n(&p->vptr, (size_t)nq + 1, "vertex pointers"))) return st;
-    if ((st = fe_alloc_n(&p->fan, (size_t)n3, "row fans"))) return st;
-    if ((st = fe_alloc_n(&p->hdr, (size_t)nq, "row fan headers"))) return st;
-    if ((st = fe_alloc_n(&p->gen_rows, (size_t)nq + 1, "general-row list"))) return st;
-    if ((st = fe_alloc_n(&p->col_idx, (size_t)cap, "col_idx"))) return st;
-    if ((st = fe_alloc_n(&t.row_nnz, (size_t)nq + 1, "row counts"))) return st;
-    if ((st = fe_alloc_n(&t.kinds, (size_t)nq + 1, "row kinds"))) return st;
-    if ((st = fe_alloc_n(&t.big_list, (size_t)nq + 1, "high-valence rows"))) return st;
-    if ((st = fe_alloc_n(&t.counters, 2, "counters"))) return st;
-    if ((st = fe_alloc_n(&t.flag, 2, "flags"))) return st;
-    if ((st = fe_alloc_n(&t.adj, (size_t)n3, "row buckets"))) return st;
     if ((st = fe_alloc_n(&t.cur, (size_t)nq + 1, "bucket cursors"))) return st;
-    if (gather) {
-        if ((st = fe_alloc_n(&p->vel, (size_t)n3, "vertex-to-triangle lists"))) return st;
-        if ((st = fe_alloc_n(&p->seg_ptr, (size_t)cap + 1, "seg_ptr"))) return st;
-        if ((st = fe_alloc_n(&p->perm, 9 * (size_t)nme, "perm"))) return st;
-    }
-    if (want_map && (st = fe_alloc_n(&p->map, 9 * (size_t)nme, "element-to-nnz map"))) return st;
-    FE_CUDA(cudaMemsetAsync(t.counters, 0, 2 * sizeof(int32_t), s));
-    FE_CUDA(cudaMemsetAsync(t.flag, 0, 2 * sizeof(int), s));
-
     // row digit: counting sort of the 3 nme incidences (the counts come with the mesh: its
     // validation took them)
-    if ((st = fe_exclusive_scan(m->deg, p->vptr, nq, s, nullptr))) return st;
-    FE_CUDA(cudaMemcpyAsync(t.cur, p->vptr, sizeof(int32_t) * ((size_t)nq + 1), cudaMemcpyDeviceToDevice, s));
+    if ((st = fe_exclusive_scan(m->deg, p->vptr, nq, s, nullptr, 1, t.cur))) return st;   // cursors start at the bucket starts
+    if ((st = fe_alloc_n(&t.adj, (size_t)n3, "row buckets"))) return st;
+    if (gather && (st = fe_alloc_n(&p->vel, (size_t)n3, "vertex-to-triangle lists"))) return st;
     if (nme > 0) {
         { FE_PROF("k_fill_adj", s); k_fill_adj<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->me, nme, t.cur, t.adj, p->vel); }
         FE_LAUNCHED("k_fill_adj");
     }
     // column digit inside each row, unique
+    if ((st = fe_alloc_n(&t.row_nnz, (size_t)nq + 1, "row counts"))) return st;
+    if ((st = fe_alloc_n(&t.kinds, (size_t)nq + 1, "row kinds"))) return st;
+    if ((st = fe_alloc_n(&t.big_list, (size_t)nq + 1, "high-valence rows"))) return st;
+    if ((st = fe_alloc_n(&t.counters, 4, "counters and flags"))) return st;
+    t.flag = t.counters + 2;
+    FE_CUDA(cudaMemsetAsync(t.counters, 0, 4 * sizeof(int32_t), s));
     size_t big_smem = (2 * (size_t)FE_MAX_VALENCE + 1) * (sizeof(int32_t) + 1);
     if (nq > 0) {
         { FE_PROF("k_row_count", s); k_row_count<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.row_nnz, t.kinds, t.big_list, t.counters, t.flag); }
@@ -560,7 +549,17 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
         { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, nullptr, t.row_nnz, nullptr); }
         FE_LAUNCHED("k_row_big (count)");
     }
+    if ((st = fe_alloc_n(&p->row_ptr, (size_t)nq + 1, "row_ptr"))) return st;
     if ((st = fe_exclusive_scan(t.row_nnz, p->row_ptr, nq, s, nullptr))) return st;
+    if ((st = fe_alloc_n(&p->col_idx, (size_t)cap, "col_idx"))) return st;
+    if ((st = fe_alloc_n(&p->fan, (size_t)n3, "row fans"))) return st;
+    if ((st = fe_alloc_n(&p->hdr, (size_t)nq, "row fan headers"))) return st;
+    if ((st = fe_alloc_n(&p->gen_rows, (size_t)nq + 1, "general-row list"))) return st;
+    if (gather) {
+        if ((st = fe_alloc_n(&p->seg_ptr, (size_t)cap + 1, "seg_ptr"))) return st;
+        if ((st = fe_alloc_n(&p->perm, 9 * (size_t)nme, "perm"))) return st;
+    }
+    if (want_map && (st = fe_alloc_n(&p->map, 9 * (size_t)nme, "element-to-nnz map"))) return st;
     if (nq > 0) {
         { FE_PROF("k_row_fill", s); k_row_fill<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.kinds, p->row_ptr, p->col_idx, p->fan,
                                                                                    p->hdr, p->gen_rows, t.counters + 1); }

@@ -402,11 +402,11 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
 template <int KIND>
 __global__ void __launch_bounds__(128, 5) k_fan_scalar(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ vptr,
                                                        const int2* __restrict__ fan, const int2* __restrict__ hdr,
-                                                       const double2* __restrict__ q, const VRec* __restrict__ vr, int32_t nq,
-                                                       Consts cs, double* __restrict__ out0, double* __restrict__ out1,
+                                                       const double2* __restrict__ q, const VRec* __restrict__ vr, int32_t r0,
+                                                       int32_t r1, Consts cs, double* __restrict__ out0, double* __restrict__ out1,
                                                        int* __restrict__ err) {
     int bad = 0, orient = 0;
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < (uint32_t)nq; r += gridDim.x * blockDim.x)
+    for (uint32_t r = r0 + blockIdx.x * blockDim.x + threadIdx.x; r < (uint32_t)r1; r += gridDim.x * blockDim.x)
         fan_row<KIND>((int32_t)r, row_ptr, vptr, fan, hdr, q, vr, cs, out0, out1, bad, orient);
     if (bad) atomicOr(err, 2);
     if (orient) atomicOr(err, 1);
@@ -704,7 +704,7 @@ static fe_status launch_scalar(fe_mesh m, fe_pattern p, const double* w, double*
             return fe_cuda_fail(e0, "k_pack_vrec");
         }
     }
-    { FE_PROF("k_fan_scalar", s); k_fan_scalar<KIND><<<fe_grid(m->nq, FAN_SCALAR_BLOCK, 5), FAN_SCALAR_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, m->nq, cs, out0, out1, m->err); }
+    { FE_PROF("k_fan_scalar", s); k_fan_scalar<KIND><<<fe_grid(m->nq, FAN_SCALAR_BLOCK, 5), FAN_SCALAR_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, 0, m->nq, cs, out0, out1, m->err); }
     cudaError_t e = cudaGetLastError();
     fe_free(vr);
     if (e != cudaSuccess) return fe_cuda_fail(e, "k_fan_scalar");
@@ -757,4 +757,118 @@ void fe_row_batch_launch(const fe_row_mesh* desc, const fe_row_tile* tiles, int3
     if (ngeneral > 0) {
         { FE_PROF("k_batch_general", s); k_batch_general<<<ngeneral, GEN_BLOCK, 0, s>>>(desc, general, S, M, cs); }
     }
+}
+
+// ---------------------------------------------------------------- end-to-end call
+//
+// Host arrays in, host CSR arrays out, with the copies overlapped where the data allow it:
+//   side stream:  w upload (while the mesh is uploaded and validated) | col_idx download | value
+//                 downloads of row block k as soon as block k is assembled
+//   main stream:  mesh upload + validation | pattern build | row_ptr download (its entries split
+//                 the values into row blocks) | vertex records, general rows, row blocks 0..K-1
+// The host link (about 0.2 TB/s each way) is the bound: the value downloads dominate.
+
+namespace {
+constexpr int E2E_BLOCKS = 8;
+
+cudaStream_t side_stream() {
+    static thread_local int dev = -1;
+    static thread_local cudaStream_t st = nullptr;
+    int d = 0;
+    cudaGetDevice(&d);
+    if (!st || d != dev) {
+        st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
+        dev = d;
+    }
+    return st;
+}
+}  // namespace
+
+extern "C" fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const double* q, const int32_t* me,
+                                                  const double* w, int32_t* row_ptr, int32_t* col_idx, double* S,
+                                                  double* Mw, int64_t cap, int64_t* nnz_out, fe_stream stream) {
+    if (!nnz_out || !row_ptr) return fe_fail(FE_ERR_INVALID_ARG, "row_ptr or nnz_out is null");
+    *nnz_out = 0;
+    if (nq < 0 || nme < 0) return fe_fail(FE_ERR_INVALID_ARG, "nq and nme must be >= 0");
+    if (nq > 0 && (!q || !w)) return fe_fail(FE_ERR_INVALID_ARG, "q or w is null");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t s2 = side_stream();
+    if (!s2) return fe_fail(FE_ERR_CUDA, "could not create the copy stream");
+    FeStreamScope scope(s);
+    fe_mesh m = nullptr;
+    fe_pattern p = nullptr;
+    double *wd = nullptr, *Sd = nullptr, *Md = nullptr;
+    VRec* vr = nullptr;
+    cudaEvent_t ev[E2E_BLOCKS + 1] = {};
+    fe_status st = FE_OK;
+    auto done = [&](fe_status ret) {
+        cudaStreamSynchronize(s2);
+        cudaStreamSynchronize(s);
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        fe_free(vr);
+        fe_free(Sd);
+        fe_free(Md);
+        fe_free(wd);
+        if (p) fe_pattern_destroy(p);
+        if (m) fe_mesh_destroy(m);
+        return ret;
+    };
+    for (auto& e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return done(fe_fail(FE_ERR_CUDA, "event creation"));
+    // 1. w goes up on the side stream while the mesh is uploaded and validated
+    if ((st = fe_alloc_n(&wd, (size_t)nq, "vertex weights"))) return done(st);
+    cudaEventRecord(ev[0], s);                                   // wd's allocation is ordered on s
+    cudaStreamWaitEvent(s2, ev[0]);
+    if (nq > 0 && cudaMemcpyAsync(wd, w, sizeof(double) * nq, cudaMemcpyHostToDevice, s2) != cudaSuccess)
+        return done(fe_fail(FE_ERR_CUDA, "weight upload"));
+    cudaEventRecord(ev[0], s2);
+    // 2. mesh and pattern (each synchronises the main stream)
+    if ((st = fe_mesh_create(nq, nme, q, me, FE_PTR_HOST, stream, &m))) return done(st);
+    if ((st = fe_pattern_build(m, 1, FE_PATTERN_DEFAULT, stream, &p))) return done(st);
+    const int64_t nnz = p->nnz;
+    *nnz_out = nnz;
+    if (cap < nnz)
+        return done(fe_fail(FE_ERR_BUFFER_TOO_SMALL, "capacity " + std::to_string(cap) + " < nnz " + std::to_string(nnz)));
+    if (nnz > 0 && (!col_idx || !S || !Mw)) return done(fe_fail(FE_ERR_INVALID_ARG, "col_idx, S or Mw is null"));
+    // 3. row_ptr first: its entries split the value downloads into row blocks
+    if (cudaMemcpyAsync(row_ptr, p->row_ptr, sizeof(int32_t) * ((size_t)nq + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return done(fe_fail(FE_ERR_CUDA, "row_ptr download"));
+    if (nnz == 0) return done(FE_OK);
+    // 4. the column indices go down while the values are computed
+    if (cudaMemcpyAsync(col_idx, p->col_idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s2) != cudaSuccess)
+        return done(fe_fail(FE_ERR_CUDA, "col_idx download"));
+    // 5. values: vertex records, general rows, then the row blocks, each downloaded when done
+    if ((st = fe_alloc_n(&Sd, (size_t)nnz, "S values")) || (st = fe_alloc_n(&Md, (size_t)nnz, "Mw values")) ||
+        (st = fe_alloc_n(&vr, (size_t)nq, "vertex records")))
+        return done(st);
+    cudaStreamWaitEvent(s, ev[0]);                               // w is on the device
+    Consts cs = make_consts(0.0, 0.0);
+    { FE_PROF("k_pack_vrec", s); k_pack_vrec<<<fe_grid(nq, 256), 256, 0, s>>>(m->q, wd, nq, vr, m->err); }
+    if (p->n_gen > 0) {
+        FE_PROF("k_general_scalar", s);
+        k_general_scalar<W_S | W_W><<<p->n_gen, GEN_BLOCK, 0, s>>>(p->gen_rows, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q,
+                                                                   wd, cs, Sd, Md, m->err);
+    }
+    for (int k = 0; k < E2E_BLOCKS; k++) {
+        int32_t r0 = (int32_t)((int64_t)nq * k / E2E_BLOCKS), r1 = (int32_t)((int64_t)nq * (k + 1) / E2E_BLOCKS);
+        if (r1 > r0) {
+            FE_PROF("k_fan_scalar", s);
+            k_fan_scalar<W_S | W_W><<<fe_grid(r1 - r0, FAN_SCALAR_BLOCK, 5), FAN_SCALAR_BLOCK, 0, s>>>(
+                p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, r0, r1, cs, Sd, Md, m->err);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return done(fe_cuda_fail(e, "k_fan_scalar"));
+        cudaEventRecord(ev[k + 1], s);
+        cudaStreamWaitEvent(s2, ev[k + 1]);
+        int64_t v0 = row_ptr[r0], v1 = row_ptr[r1];
+        if (v1 > v0 && (cudaMemcpyAsync(S + v0, Sd + v0, sizeof(double) * (v1 - v0), cudaMemcpyDeviceToHost, s2) != cudaSuccess ||
+                        cudaMemcpyAsync(Mw + v0, Md + v0, sizeof(double) * (v1 - v0), cudaMemcpyDeviceToHost, s2) != cudaSuccess))
+            return done(fe_fail(FE_ERR_CUDA, "value download"));
+    }
+    if (cudaStreamSynchronize(s2) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return done(fe_fail(FE_ERR_CUDA, "end-to-end call"));
+    return done(fe_mesh_check(m, stream));
 }

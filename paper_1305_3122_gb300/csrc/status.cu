@@ -170,8 +170,8 @@ __global__ void k_scan_sums(long long* sums, int64_t ntiles) {
     if (threadIdx.x == 0) sums[ntiles] = carry;
 }
 
-__global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n,
-                            const long long* __restrict__ offs, int* __restrict__ overflow, int round) {
+__global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict__ out, int32_t* __restrict__ out2,
+                            int64_t n, const long long* __restrict__ offs, int* __restrict__ overflow, int round) {
     __shared__ long long warp_tot[SCAN_BLOCK / 32];
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     long long v[SCAN_ITEMS];
@@ -205,6 +205,7 @@ __global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict_
         if (i < n) {
             if (run > INT32_MAX) *overflow = 1;
             out[i] = (int32_t)run;
+            if (out2) out2[i] = (int32_t)run;
         }
         run += v[j];
     }
@@ -212,11 +213,12 @@ __global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict_
         long long tot = offs[gridDim.x];
         if (tot > INT32_MAX) *overflow = 1;
         out[n] = (int32_t)tot;
+        if (out2) out2[n] = (int32_t)tot;
     }
 }
 
 fe_status fe_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s,
-                            int64_t* total_out, int round) {
+                            int64_t* total_out, int round, int32_t* out2) {
     int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (ntiles < 1) ntiles = 1;
     long long* sums = nullptr;
@@ -228,7 +230,7 @@ fe_status fe_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStre
     cudaMemsetAsync(ovf, 0, sizeof(int), s);
     { FE_PROF("k_tile_sums", s); k_tile_sums<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, sums, round); }
     { FE_PROF("k_scan_sums", s); k_scan_sums<<<1, 1024, 0, s>>>(sums, ntiles); }
-    { FE_PROF("k_tile_scan", s); k_tile_scan<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, n, sums, ovf, round); }
+    { FE_PROF("k_tile_scan", s); k_tile_scan<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, out2, n, sums, ovf, round); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { fe_free(sums); fe_free(ovf); return fe_cuda_fail(e, "scan kernels"); }
     fe_status ret = FE_OK;

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfeasm.so")
 
 FE_OK = 0
-PTR_HOST, PTR_DEVICE = 0, 1
+PTR_HOST, PTR_DEVICE, PTR_DEVICE_BORROW = 0, 1, 2
 ATOMIC, GATHER, ROW = 0, 1, 2
 PATTERN_DEFAULT, PATTERN_GATHER, PATTERN_MAP = 0, 1, 2
 
@@ -47,6 +47,7 @@ SIGNATURES = {
     "fe_assemble_elas": (_INT, [_P, _P, _D, _D, _INT, _P, _I64, _P]),
     "fe_assemble_stiff_wmass_noalloc": (_INT, [_P, _P, _P, _P, _P, _I64, _P]),
     "fe_adjoint_stiff_wmass": (_INT, [_P, _P, _P, _P, _P, _INT, _P, _P, _P]),
+    "fe_assemble_stiff_wmass_host": (_INT, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "fe_batch_create": (_INT, [_I32, _P, _P, ctypes.POINTER(_P)]),
     "fe_batch_tune": (_INT, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "fe_batch_set_shape": (_INT, [_P, _I32, _I32]),
@@ -129,13 +130,18 @@ class Mesh:
     library (FE_PTR_HOST). Section 2 of the paper.
     """
 
-    def __init__(self, q, me, stream=None):
+    def __init__(self, q, me, stream=None, borrow: bool = False):
+        """borrow: with CUDA tensors, use me in place (FE_PTR_DEVICE_BORROW) instead of copying
+        it; the mesh keeps a reference to the tensor, which must not be modified meanwhile."""
         L = lib()
         self._h = None
+        self._me_ref = None
         if isinstance(q, torch.Tensor) and q.is_cuda:
             qd = q.contiguous()
             med = me.contiguous()
-            kind = PTR_DEVICE
+            kind = PTR_DEVICE_BORROW if borrow else PTR_DEVICE
+            if borrow:
+                self._me_ref = med
             qp = _dptr(qd, torch.float64, "q")
             mp = _dptr(med, torch.int32, "me")
         else:
@@ -171,6 +177,7 @@ class Mesh:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.fe_mesh_destroy(self._h)
         self._h = None
+        self._me_ref = None
 
     def __del__(self):
         self.close()
@@ -364,6 +371,39 @@ class Batch:
             self._h = None
 
 
+def _host_f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a.numpy() if isinstance(a, torch.Tensor) else a, dtype=np.float64)
+
+
+def assemble_stiff_wmass_host(q, me, w, pinned_out: dict | None = None, stream=None) -> dict:
+    """S and M^[w] from host arrays to host CSR arrays in one pipelined library call
+    (fe_assemble_stiff_wmass_host). pinned_out may hold reusable pinned torch tensors "row_ptr",
+    "col_idx", "S", "Mw" (int32 / float64); missing or too small ones are allocated (pinned)."""
+    qh = _host_f64(q)
+    meh = np.ascontiguousarray(me.numpy() if isinstance(me, torch.Tensor) else me, dtype=np.int32)
+    wh = _host_f64(w)
+    nq, nme = int(qh.shape[1]), int(meh.shape[1])
+    cap = 6 * nme + nq
+    outs = dict(pinned_out or {})
+    want = {"row_ptr": (nq + 1, torch.int32), "col_idx": (cap, torch.int32), "S": (cap, torch.float64),
+            "Mw": (cap, torch.float64)}
+    for name, (n, dt) in want.items():
+        t = outs.get(name)
+        if t is None or t.numel() < n or t.dtype != dt:
+            outs[name] = torch.empty(n, dtype=dt, pin_memory=True)
+    nnz = _I64()
+    _check(lib().fe_assemble_stiff_wmass_host(nq, nme, qh.ctypes.data, meh.ctypes.data, wh.ctypes.data,
+                                              outs["row_ptr"].data_ptr(), outs["col_idx"].data_ptr(),
+                                              outs["S"].data_ptr(), outs["Mw"].data_ptr(), cap,
+                                              ctypes.byref(nnz), _stream(stream)), "fe_assemble_stiff_wmass_host")
+    n = nnz.value
+    res = {"row_ptr": outs["row_ptr"][: nq + 1], "col_idx": outs["col_idx"][:n], "S": outs["S"][:n],
+           "Mw": outs["Mw"][:n], "nnz": n}
+    if pinned_out is not None:
+        pinned_out.update({k: outs[k] for k in want})
+    return res
+
+
 def assemble_host(kind: str, q: np.ndarray, me: np.ndarray, w: np.ndarray | None = None, lam: float = 1.0,
                   mu: float = 0.5, variant: int = ROW, pinned_out: dict | None = None, stream=None):
     """One-shot assembly from host arrays to host CSR arrays (the end-to-end call).
@@ -371,7 +411,10 @@ def assemble_host(kind: str, q: np.ndarray, me: np.ndarray, w: np.ndarray | None
     kind in {"mass", "wmass", "stiff", "elas", "stiff_wmass"}. The mesh is created from host
     memory (copied by the library), the pattern built, the values assembled, and row_ptr,
     col_idx and values read back to (pinned, if given) host tensors. Returns a dict.
+    "stiff_wmass" with FE_VARIANT_ROW is one pipelined library call (assemble_stiff_wmass_host).
     """
+    if kind == "stiff_wmass" and variant == ROW:
+        return assemble_stiff_wmass_host(q, me, w, pinned_out, stream)
     mesh = Mesh(q, me, stream=stream)
     pat = Pattern(mesh, dofs=2 if kind == "elas" else 1, gather=(variant == GATHER), map=(variant == ATOMIC),
                   stream=stream)
@@ -394,8 +437,10 @@ def assemble_host(kind: str, q: np.ndarray, me: np.ndarray, w: np.ndarray | None
     src = {"row_ptr": pat.row_ptr, "col_idx": pat.col_idx, **vals}
     for name, t in src.items():
         dst = (pinned_out or {}).get(name)
-        if dst is None or dst.numel() < t.numel():
+        if dst is None or dst.numel() < t.numel() or dst.dtype != t.dtype:
             dst = torch.empty(t.numel(), dtype=t.dtype, pin_memory=True)
+            if pinned_out is not None:
+                pinned_out[name] = dst
         dst = dst[: t.numel()]
         dst.copy_(t, non_blocking=True)
         out[name] = dst

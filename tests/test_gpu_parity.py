@@ -248,3 +248,83 @@ def test_row_variant_flags_out_of_range():
     with pytest.raises(feasm.FeasmError) as e:
         mesh.check()
     assert e.value.status == 9
+
+
+def test_borrowed_connectivity_matches_copied():
+    """FE_PTR_DEVICE_BORROW: the mesh reads the caller's me in place; results equal the copying
+    mesh's, and the caller's array is left unchanged."""
+    m = meshgen.square_mesh(37, 5)
+    w = torch.tensor(_weights(m.q), device="cuda")
+    q_d, me_d = torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda")
+    me_before = me_d.clone()
+    ref = feasm.Mesh(q_d, me_d)
+    bor = feasm.Mesh(q_d, me_d, borrow=True)
+    pr, pb = feasm.Pattern(ref, gather=True), feasm.Pattern(bor, gather=True)
+    assert torch.equal(pr.row_ptr, pb.row_ptr) and torch.equal(pr.col_idx, pb.col_idx)
+    for variant in VARIANTS:
+        Sr, Mr = feasm.assemble_stiff_wmass(ref, pr, w, variant)
+        Sb, Mb = feasm.assemble_stiff_wmass(bor, pb, w, variant)
+        rp = pr.row_ptr.cpu().numpy()
+        assert_values_close(rp, Sb.cpu().numpy(), Sr.cpu().numpy())
+        assert_values_close(rp, Mb.cpu().numpy(), Mr.cpu().numpy())
+    bor.close()
+    assert torch.equal(me_d, me_before)
+
+
+def test_end_to_end_host_call():
+    """fe_assemble_stiff_wmass_host: host arrays in, host CSR out, pipelined over row blocks; equal
+    (bit for bit) to the device-resident row-owner call, and within tolerance of the oracle."""
+    m = meshgen.square_mesh(61, 8)
+    w = _weights(m.q)
+    out = feasm.assemble_stiff_wmass_host(m.q, m.me, w)
+    rp, ci, vs = oracle.assemble(oracle.STIFF, m.q, m.me)
+    _, _, vm = oracle.assemble(oracle.WMASS, m.q, m.me, w)
+    assert out["nnz"] == len(ci)
+    assert_csr_equal(out["row_ptr"], out["col_idx"], rp, ci)
+    assert_values_close(rp, out["S"].numpy(), vs)
+    assert_values_close(rp, out["Mw"].numpy(), vm)
+    mesh = feasm.Mesh(m.q, m.me)
+    pat = feasm.Pattern(mesh)
+    S, Mw = feasm.assemble_stiff_wmass(mesh, pat, torch.tensor(w, device="cuda"), feasm.ROW)
+    assert torch.equal(S.cpu(), out["S"]) and torch.equal(Mw.cpu(), out["Mw"])
+    # reusing the pinned buffers on a second, smaller mesh
+    buf = {}
+    feasm.assemble_stiff_wmass_host(m.q, m.me, w, pinned_out=buf)
+    m2 = meshgen.square_mesh(13, 9)
+    out2 = feasm.assemble_stiff_wmass_host(m2.q, m2.me, _weights(m2.q), pinned_out=buf)
+    rp2, ci2, vs2 = oracle.assemble(oracle.STIFF, m2.q, m2.me)
+    assert_csr_equal(out2["row_ptr"], out2["col_idx"], rp2, ci2)
+    assert_values_close(rp2, out2["S"].numpy(), vs2)
+
+
+def test_end_to_end_host_call_errors():
+    import ctypes
+    m = meshgen.square_mesh(9, 3)
+    q = np.ascontiguousarray(m.q)
+    me = np.ascontiguousarray(m.me)
+    w = np.ones(m.nq)
+    rp = np.zeros(m.nq + 1, np.int32)
+    ci = np.zeros(8, np.int32)
+    S = np.zeros(8)
+    M = np.zeros(8)
+    nnz = ctypes.c_int64()
+    L = feasm.lib()
+    st = L.fe_assemble_stiff_wmass_host(m.nq, m.nme, q.ctypes.data, me.ctypes.data, w.ctypes.data, rp.ctypes.data,
+                                        ci.ctypes.data, S.ctypes.data, M.ctypes.data, 8, ctypes.byref(nnz), None)
+    assert st == 5 and nnz.value == (m.nq + 2 * (3 * 81 + 18))       # FE_ERR_BUFFER_TOO_SMALL, nnz reported
+    # pageable outputs of the right size work (without overlap)
+    n = nnz.value
+    ci, S, M = np.zeros(n, np.int32), np.zeros(n), np.zeros(n)
+    st = L.fe_assemble_stiff_wmass_host(m.nq, m.nme, q.ctypes.data, me.ctypes.data, w.ctypes.data, rp.ctypes.data,
+                                        ci.ctypes.data, S.ctypes.data, M.ctypes.data, n, ctypes.byref(nnz), None)
+    assert st == 0
+    rpo, cio, vso = oracle.assemble(oracle.STIFF, m.q, m.me)
+    np.testing.assert_array_equal(rp, rpo)
+    np.testing.assert_array_equal(ci, cio)
+    assert_values_close(rpo, S, vso)
+    # a clockwise triangle is an orientation error
+    bad = me.copy()
+    bad[1, 0], bad[2, 0] = bad[2, 0], bad[1, 0]
+    st = L.fe_assemble_stiff_wmass_host(m.nq, m.nme, q.ctypes.data, bad.ctypes.data, w.ctypes.data, rp.ctypes.data,
+                                        ci.ctypes.data, S.ctypes.data, M.ctypes.data, n, ctypes.byref(nnz), None)
+    assert st == 4                                                      # FE_ERR_ORIENTATION
