@@ -189,10 +189,62 @@ __global__ void k_row_count(const int32_t* __restrict__ vptr, const int32_t* __r
     }
 }
 
-// Row fill for rows with at most FAST_DEG triangles. Simple rows: fan-ordered neighbours with
-// their positions (fan[beg + e] = (n_e, pos(n_e))), header (n_d, pos_self | pos_nd << 14 |
-// kind << 28) and col_idx. General rows: sorted unique columns, their (j, l) pairs sorted
-// lexicographically (a deterministic order) and a place in the general-row list.
+// Fill of a simple row (closed or open fan with chain start `start`): fan-ordered neighbours
+// with their positions (fan[beg + e] = (n_e, pos(n_e))), header (n_d, pos_self | pos_nd << 14 |
+// kind << 28) and col_idx from position o.
+__device__ __forceinline__ void fill_simple(int32_t i, int32_t beg, int32_t d, int kind, int start, const Fan& f,
+                                            int32_t o, int32_t* __restrict__ col_idx, int2* __restrict__ fan,
+                                            int2* __restrict__ hdr) {
+    int32_t jcur = 0, lcur = 0;
+#pragma unroll
+    for (int e = 0; e < FAN_MAX; e++)
+        if (e == start) { jcur = f.J[e]; lcur = f.L[e]; }
+    // the last neighbour: follow the chain to its end
+    int32_t lend = lcur;
+    for (int s = 1; s < d; s++) {
+        int32_t nl = lend;
+#pragma unroll
+        for (int e = 0; e < FAN_MAX; e++)
+            if (e < d && f.J[e] == lend) nl = f.L[e];
+        lend = nl;
+    }
+    int pself = fan_pos(f, i, kind, lend, i);
+    int pend = fan_pos(f, i, kind, lend, lend);
+    col_idx[o + pself] = i;
+    if (kind == KIND_OPEN) col_idx[o + pend] = lend;
+    for (int s = 0; s < d; s++) {
+        int pj = fan_pos(f, i, kind, lend, jcur);
+        fan[beg + s] = make_int2(jcur, pj);
+        col_idx[o + pj] = jcur;
+        int32_t nl = lcur;
+#pragma unroll
+        for (int e = 0; e < FAN_MAX; e++)
+            if (e < d && f.J[e] == lcur) nl = f.L[e];
+        jcur = lcur;
+        lcur = nl;
+    }
+    hdr[i] = make_int2(lend, pself | (pend << 14) | (kind << 28));
+}
+
+// Fill of a general row with at most FAST_DEG triangles: its u sorted unique columns, its (j, l)
+// pairs sorted lexicographically (a deterministic order) and a place in the general-row list.
+__device__ __forceinline__ void fill_general(int32_t i, int32_t beg, int32_t abeg, int32_t d, const int32_t* cols,
+                                             int u, int32_t o, const int2* __restrict__ adj,
+                                             int32_t* __restrict__ col_idx, int2* __restrict__ fan,
+                                             int32_t* __restrict__ gen_list, int32_t* __restrict__ gen_count) {
+    for (int t = 0; t < u; t++) col_idx[o + t] = cols[t];
+    long long key[FAST_DEG];
+    for (int32_t s = 0; s < d; s++) {
+        int2 p = adj[abeg + s];
+        key[s] = ((long long)p.x << 32) | (unsigned)p.y;
+    }
+    isort64(key, d);
+    for (int32_t s = 0; s < d; s++) fan[beg + s] = make_int2((int32_t)(key[s] >> 32), (int32_t)(key[s] & 0xffffffffLL));
+    gen_list[atomicAdd(gen_count, 1)] = i;
+}
+
+// Row fill for rows with at most FAST_DEG triangles (kinds and counts from k_row_count, offsets
+// from the scan of the counts).
 __global__ void k_row_fill(const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase,
                            const int2* __restrict__ adj, int32_t nq,
                            const unsigned char* __restrict__ kinds, const int32_t* __restrict__ row_ptr,
@@ -206,50 +258,14 @@ __global__ void k_row_fill(const int32_t* __restrict__ vptr, const int32_t* __re
         if (kind != KIND_GENERAL) {
             Fan f;
             load_fan(adj, abeg, d, f);
-            int32_t jcur = 0, lcur = 0;
-#pragma unroll
-            for (int e = 0; e < FAN_MAX; e++)
-                if (e == start) { jcur = f.J[e]; lcur = f.L[e]; }
-            // the last neighbour: follow the chain to its end
-            int32_t lend = lcur;
-            for (int s = 1; s < d; s++) {
-                int32_t nl = lend;
-#pragma unroll
-                for (int e = 0; e < FAN_MAX; e++)
-                    if (e < d && f.J[e] == lend) nl = f.L[e];
-                lend = nl;
-            }
-            int pself = fan_pos(f, i, kind, lend, i);
-            int pend = fan_pos(f, i, kind, lend, lend);
-            col_idx[o + pself] = i;
-            if (kind == KIND_OPEN) col_idx[o + pend] = lend;
-            for (int s = 0; s < d; s++) {
-                int pj = fan_pos(f, i, kind, lend, jcur);
-                fan[beg + s] = make_int2(jcur, pj);
-                col_idx[o + pj] = jcur;
-                int32_t nl = lcur;
-#pragma unroll
-                for (int e = 0; e < FAN_MAX; e++)
-                    if (e < d && f.J[e] == lcur) nl = f.L[e];
-                jcur = lcur;
-                lcur = nl;
-            }
-            hdr[i] = make_int2(lend, pself | (pend << 14) | (kind << 28));
+            fill_simple(i, beg, d, kind, start, f, o, col_idx, fan, hdr);
             continue;
         }
         hdr[i] = make_int2(-1, KIND_GENERAL << 28);
         if (d == 0 || d > FAST_DEG) continue;
         int32_t cols[2 * FAST_DEG + 1];
         int u = row_columns(i, abeg, d, adj, cols);
-        for (int t = 0; t < u; t++) col_idx[o + t] = cols[t];
-        long long key[FAST_DEG];
-        for (int32_t s = 0; s < d; s++) {
-            int2 p = adj[abeg + s];
-            key[s] = ((long long)p.x << 32) | (unsigned)p.y;
-        }
-        isort64(key, d);
-        for (int32_t s = 0; s < d; s++) fan[beg + s] = make_int2((int32_t)(key[s] >> 32), (int32_t)(key[s] & 0xffffffffLL));
-        gen_list[atomicAdd(gen_count, 1)] = i;
+        fill_general(i, beg, abeg, d, cols, u, o, adj, col_idx, fan, gen_list, gen_count);
     }
 }
 
@@ -535,22 +551,14 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
         { FE_PROF("k_fill_adj", s); k_fill_adj<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->me, nme, t.cur, t.adj, p->vel); }
         FE_LAUNCHED("k_fill_adj");
     }
-    // column digit inside each row, unique
+    // column digit inside each row, unique, and the CSR offsets
     if ((st = fe_alloc_n(&t.row_nnz, (size_t)nq + 1, "row counts"))) return st;
-    if ((st = fe_alloc_n(&t.kinds, (size_t)nq + 1, "row kinds"))) return st;
     if ((st = fe_alloc_n(&t.big_list, (size_t)nq + 1, "high-valence rows"))) return st;
-    if ((st = fe_alloc_n(&t.counters, 4, "counters and flags"))) return st;
+    // counters: [0] high-valence rows, [1] general rows, [2] a valence over the limit, [3] a key
+    // missing from the pattern
+    if ((st = fe_alloc_n(&t.counters, 8, "counters and flags"))) return st;
     t.flag = t.counters + 2;
-    FE_CUDA(cudaMemsetAsync(t.counters, 0, 4 * sizeof(int32_t), s));
-    size_t big_smem = (2 * (size_t)FE_MAX_VALENCE + 1) * (sizeof(int32_t) + 1);
-    if (nq > 0) {
-        { FE_PROF("k_row_count", s); k_row_count<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.row_nnz, t.kinds, t.big_list, t.counters, t.flag); }
-        FE_LAUNCHED("k_row_count");
-        { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, nullptr, t.row_nnz, nullptr); }
-        FE_LAUNCHED("k_row_big (count)");
-    }
     if ((st = fe_alloc_n(&p->row_ptr, (size_t)nq + 1, "row_ptr"))) return st;
-    if ((st = fe_exclusive_scan(t.row_nnz, p->row_ptr, nq, s, nullptr))) return st;
     if ((st = fe_alloc_n(&p->col_idx, (size_t)cap, "col_idx"))) return st;
     if ((st = fe_alloc_n(&p->fan, (size_t)n3, "row fans"))) return st;
     if ((st = fe_alloc_n(&p->hdr, (size_t)nq, "row fan headers"))) return st;
@@ -560,44 +568,73 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
         if ((st = fe_alloc_n(&p->perm, 9 * (size_t)nme, "perm"))) return st;
     }
     if (want_map && (st = fe_alloc_n(&p->map, 9 * (size_t)nme, "element-to-nnz map"))) return st;
-    if (nq > 0) {
-        { FE_PROF("k_row_fill", s); k_row_fill<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.kinds, p->row_ptr, p->col_idx, p->fan,
-                                                                                   p->hdr, p->gen_rows, t.counters + 1); }
-        FE_LAUNCHED("k_row_fill");
-        { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->row_ptr, nullptr, p->col_idx); }
-        FE_LAUNCHED("k_row_big (fill)");
-        size_t pair_smem = (size_t)FE_MAX_VALENCE * sizeof(long long);
-        { FE_PROF("k_row_big_pairs", s); k_row_big_pairs<<<BIG_GRID, BIG_BLOCK, pair_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->fan, p->hdr,
-                                                                                                   p->gen_rows, t.counters + 1); }
-        FE_LAUNCHED("k_row_big_pairs");
-        if (gather) {
-            { FE_PROF("k_row_perm", s); k_row_perm<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, p->vptr, t.adj, p->vel, nq, p->row_ptr, p->seg_ptr, p->perm); }
-            FE_LAUNCHED("k_row_perm");
-            size_t sm = 3 * (size_t)FE_MAX_VALENCE * (sizeof(long long) + sizeof(int32_t) + 1) +
-                        (size_t)FE_MAX_VALENCE * sizeof(int32_t);
-            FE_CUDA(cudaFuncSetAttribute(k_row_big_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            { FE_PROF("k_row_big_perm", s); k_row_big_perm<<<BIG_GRID, BIG_BLOCK, sm, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->vel, p->row_ptr, p->seg_ptr, p->perm); }
-            FE_LAUNCHED("k_row_big_perm");
+    const size_t big_smem = (2 * (size_t)FE_MAX_VALENCE + 1) * (sizeof(int32_t) + 1);
+
+    // counts (fan analysis), offsets (scan of the counts) and fill of the rows with at most
+    // FAST_DEG triangles
+    auto rows = [&]() -> fe_status {
+        fe_status sa = t.kinds ? FE_OK : fe_alloc_n(&t.kinds, (size_t)nq + 1, "row kinds");
+        if (sa) return sa;
+        if (nq > 0) {
+            { FE_PROF("k_row_count", s); k_row_count<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.row_nnz, t.kinds, t.big_list, t.counters, t.flag); }
+            FE_LAUNCHED("k_row_count");
+            { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, nullptr, t.row_nnz, nullptr); }
+            FE_LAUNCHED("k_row_big (count)");
         }
-    }
-    if (gather) {
-        { FE_PROF("k_set_last", s); k_set_last<<<1, 1, 0, s>>>(p->seg_ptr, p->row_ptr, nq, (int32_t)(9 * (int64_t)nme)); }
-        FE_LAUNCHED("k_set_last");
-    }
-    if (want_map && nme > 0) {
-        { FE_PROF("k_build_map", s); k_build_map<<<fe_grid(nme, MAP_BLOCK), MAP_BLOCK, 0, s>>>(m->me, nme, p->row_ptr, p->col_idx, p->map, t.flag + 1); }
-        FE_LAUNCHED("k_build_map");
-    }
-    int host_flags[2] = {0, 0};
-    int32_t host_counts[2] = {0, 0};
+        if ((sa = fe_exclusive_scan(t.row_nnz, p->row_ptr, nq, s, nullptr))) return sa;
+        if (nq > 0) {
+            { FE_PROF("k_row_fill", s); k_row_fill<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.kinds, p->row_ptr, p->col_idx, p->fan,
+                                                                                       p->hdr, p->gen_rows, t.counters + 1); }
+            FE_LAUNCHED("k_row_fill");
+        }
+        return FE_OK;
+    };
+    // high-valence rows, staged-gather lists, map (all need the offsets)
+    auto rows_rest = [&]() -> fe_status {
+        if (nq > 0) {
+            { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->row_ptr, nullptr, p->col_idx); }
+            FE_LAUNCHED("k_row_big (fill)");
+            size_t pair_smem = (size_t)FE_MAX_VALENCE * sizeof(long long);
+            { FE_PROF("k_row_big_pairs", s); k_row_big_pairs<<<BIG_GRID, BIG_BLOCK, pair_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->fan, p->hdr,
+                                                                                                       p->gen_rows, t.counters + 1); }
+            FE_LAUNCHED("k_row_big_pairs");
+            if (gather) {
+                { FE_PROF("k_row_perm", s); k_row_perm<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, p->vptr, t.adj, p->vel, nq, p->row_ptr, p->seg_ptr, p->perm); }
+                FE_LAUNCHED("k_row_perm");
+                size_t sm = 3 * (size_t)FE_MAX_VALENCE * (sizeof(long long) + sizeof(int32_t) + 1) +
+                            (size_t)FE_MAX_VALENCE * sizeof(int32_t);
+                FE_CUDA(cudaFuncSetAttribute(k_row_big_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                { FE_PROF("k_row_big_perm", s); k_row_big_perm<<<BIG_GRID, BIG_BLOCK, sm, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->vel, p->row_ptr, p->seg_ptr, p->perm); }
+                FE_LAUNCHED("k_row_big_perm");
+            }
+        }
+        if (gather) {
+            { FE_PROF("k_set_last", s); k_set_last<<<1, 1, 0, s>>>(p->seg_ptr, p->row_ptr, nq, (int32_t)(9 * (int64_t)nme)); }
+            FE_LAUNCHED("k_set_last");
+        }
+        if (want_map && nme > 0) {
+            { FE_PROF("k_build_map", s); k_build_map<<<fe_grid(nme, MAP_BLOCK), MAP_BLOCK, 0, s>>>(m->me, nme, p->row_ptr, p->col_idx, p->map, t.flag + 1); }
+            FE_LAUNCHED("k_build_map");
+        }
+        return FE_OK;
+    };
+    // one host synchronisation: flags, the counts of the lists, nnz
+    int host_c[4] = {0, 0, 0, 0};
     int32_t tot32 = 0;
-    FE_CUDA(cudaMemcpyAsync(host_flags, t.flag, sizeof host_flags, cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaMemcpyAsync(host_counts, t.counters, sizeof host_counts, cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaMemcpyAsync(&tot32, p->row_ptr + nq, sizeof tot32, cudaMemcpyDeviceToHost, s));
-    FE_CUDA(cudaStreamSynchronize(s));
-    if (host_flags[0])
+    auto read_back = [&]() -> fe_status {
+        FE_CUDA(cudaMemcpyAsync(host_c, t.counters, sizeof host_c, cudaMemcpyDeviceToHost, s));
+        FE_CUDA(cudaMemcpyAsync(&tot32, p->row_ptr + nq, sizeof tot32, cudaMemcpyDeviceToHost, s));
+        FE_CUDA(cudaStreamSynchronize(s));
+        return FE_OK;
+    };
+    FE_CUDA(cudaMemsetAsync(t.counters, 0, 8 * sizeof(int32_t), s));
+    if ((st = rows())) return st;
+    if ((st = rows_rest())) return st;
+    if ((st = read_back())) return st;
+    if (host_c[2])
         return fe_fail(FE_ERR_LIMIT, "a vertex belongs to more than FE_MAX_VALENCE=" + std::to_string(FE_MAX_VALENCE) + " triangles");
-    if (host_flags[1]) return fe_fail(FE_ERR_CUDA, "internal error: a triangle key is missing from the pattern");
+    if (host_c[3]) return fe_fail(FE_ERR_CUDA, "internal error: a triangle key is missing from the pattern");
+    int32_t host_counts[2] = {host_c[0], host_c[1]};
     const int64_t tot = tot32;
     p->nnz_scalar = tot;
     p->n_gen = host_counts[1];

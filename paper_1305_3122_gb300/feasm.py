@@ -188,7 +188,7 @@ class Pattern:
 
     def __init__(self, mesh: Mesh, dofs: int = 1, gather: bool = False, map: bool = True, stream=None):
         """gather: also build what FE_VARIANT_GATHER needs; map: also the element-to-nnz map
-        (FE_VARIANT_ATOMIC, the adjoint, batches). FE_VARIANT_ROW works with any pattern."""
+        (FE_VARIANT_ATOMIC, the adjoint, atomic batches). FE_VARIANT_ROW works with any pattern."""
         h = _P()
         flags = (PATTERN_GATHER if gather else 0) | (PATTERN_MAP if map else 0)
         _check(lib().fe_pattern_build(mesh.handle, dofs, flags, _stream(stream), ctypes.byref(h)), "fe_pattern_build")
