@@ -345,6 +345,9 @@ def run_ours(args) -> int:
             "assemble_only": asm}
     if not args.no_batched:
         line["batched"] = batched(feasm, meshgen, torch, args)
+    if not args.no_other:
+        line["elasticity"] = elasticity(feasm, meshgen, torch, flush, hbm, peak_kind)
+        line["adjoint"] = adjoint(feasm, meshgen, torch, flush)
     if not args.no_e2e:
         line["e2e"] = e2e(feasm, torch, m, w, args)
     if not args.no_cpu and world == 1:
@@ -416,6 +419,61 @@ def assemble_only(feasm, torch, mesh, pat, w_d, variant, S, M, flush, stream, ar
     roof = _roofline(dom, algorithmic_bytes(dom, m.nq, m.nme, nnz), dom_ms, hbm, peak_kind, args.traffic, args.cells)
     return {"value": round(m.nme / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms": round(ms, 4), "reps": reps,
             "kernels": {k: round(v[0] / v[1], 5) for k, v in prof.items()}, "roofline": roof}
+
+
+def _time_calls(torch, fn, flush, reps=20):
+    """Median device time (ms) of fn() between L2 flushes, CUDA events on the current stream."""
+    for _ in range(3):
+        fn()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def elasticity(feasm, meshgen, torch, flush, hbm, peak_kind) -> dict:
+    """Plane-elasticity K (Section 7) on the 1024 x 1024-cell mesh, lambda = 1, mu = 0.5, row owners,
+    pattern prebuilt (2 dofs per vertex)."""
+    m = meshgen.square_mesh(1024, 13053122 + 3)
+    mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))
+    pat = feasm.Pattern(mesh, dofs=2, map=False)
+    K = pat.new_values()
+    feasm.profile_reset()
+    feasm.profile_enable(True)
+    ms = _time_calls(torch, lambda: feasm.assemble_elas(mesh, pat, 1.0, 0.5, feasm.ROW, K), flush)
+    feasm.profile_enable(False)
+    prof = feasm.profile_read()
+    k_ms = prof["k_fan_elas"][0] / prof["k_fan_elas"][1]
+    nbytes = 12 * m.nme + 16 * m.nq + 8 * pat.nnz            # me, q, K values
+    return {"workload": f"K, 1024x1024-cell mesh (nq={m.nq}, nme={m.nme}, nnz={pat.nnz})", "ms": round(ms, 4),
+            "melem_s": round(m.nme / ms / 1e3, 2), "k_fan_elas_ms": round(k_ms, 4),
+            "roofline": {"kernel": "k_fan_elas", "bound": "hbm", "algorithmic_bytes": nbytes,
+                         "achieved": round(nbytes / k_ms / 1e6, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(nbytes / k_ms / 1e6 / hbm, 4), "peak_source": f"{peak_kind} HBM copy bandwidth"}}
+
+
+def adjoint(feasm, meshgen, torch, flush) -> dict:
+    """dL/dq, dL/dw of L = <G_S, S> + <G_M, M^[w]> on the 1024 x 1024-cell mesh (deterministic gather)."""
+    seed = 13053122 + 5
+    m = meshgen.square_mesh(1024, seed)
+    w = torch.tensor(meshgen.vertex_weights(m, seed), device="cuda")
+    mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))
+    pat = feasm.Pattern(mesh, gather=True)
+    GS, GM = (torch.tensor(g, device="cuda") for g in meshgen.upstream_gradients(seed, pat.nnz))
+    ms_g = _time_calls(torch, lambda: feasm.adjoint_stiff_wmass(mesh, pat, w, GS, GM, feasm.GATHER), flush)
+    ms_a = _time_calls(torch, lambda: feasm.adjoint_stiff_wmass(mesh, pat, w, GS, GM, feasm.ATOMIC), flush)
+    ms_f = _time_calls(torch, lambda: feasm.assemble_stiff_wmass(mesh, pat, w, feasm.ROW), flush)
+    return {"workload": f"S + M^[w] and adjoint, 1024x1024-cell mesh (nq={m.nq}, nme={m.nme}, nnz={pat.nnz})",
+            "forward_ms": round(ms_f, 4), "adjoint_gather_ms": round(ms_g, 4), "adjoint_atomic_ms": round(ms_a, 4),
+            "adjoint_melem_s": round(m.nme / min(ms_g, ms_a) / 1e3, 2)}
 
 
 def batched(feasm, meshgen, torch, args) -> dict:
@@ -497,6 +555,7 @@ def main() -> int:
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-other", action="store_true", help="skip the elasticity and adjoint legs")
     ap.add_argument("--traffic", default=os.path.join(ROOT, "profiles", "traffic.json"),
                     help="per-kernel DRAM bytes per launch from an ncu capture (JSON)")
     args = ap.parse_args()

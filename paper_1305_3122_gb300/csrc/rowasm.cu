@@ -550,6 +550,10 @@ __device__ __noinline__ ff elas_terms_fp64(const double2* __restrict__ q, int32_
     return ff_from_value(D, bad);
 }
 
+// The three 2 x 2 blocks of triangle (i, j, l) in row i: out[0] (column i), out[1] (column j),
+// out[2] (column l). (Row owners of simple rows compute only the last two: K annihilates the
+// translations, since the gradients of a triangle's basis functions sum to zero, so each 2 x 2
+// diagonal block of the assembled K is minus the sum of its row's off-diagonal blocks.)
 __device__ __forceinline__ ff elas_terms(const double2* __restrict__ q, int32_t i, const Nb& j, const Nb& l,
                                          const Consts& cs, Block2 out[3], int& bad) {
     ff D = ff_dot2(j.x, l.x, l.y, ff_neg(j.y));
@@ -577,6 +581,8 @@ __device__ __forceinline__ void write_block(double* __restrict__ out, int32_t rb
 
 }  // namespace
 
+__device__ __forceinline__ Block2 bneg(const Block2& a) { return Block2{ff_neg(a.k00), ff_neg(a.k01), ff_neg(a.k10), ff_neg(a.k11)}; }
+
 __global__ void __launch_bounds__(256, 2) k_fan_elas(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ vptr,
                                                      const int2* __restrict__ fan, const int2* __restrict__ hdr,
                                                      const double2* __restrict__ q, int32_t nq, Consts cs,
@@ -589,34 +595,61 @@ __global__ void __launch_bounds__(256, 2) k_fan_elas(const int32_t* __restrict__
         if (kind > 1) continue;
         int32_t rb = row_ptr[i], u = row_ptr[i + 1] - rb, b0 = vptr[i], d = vptr[i + 1] - b0;
         int pself = h.y & 0x3FFF;
-        const int2 last = kind == 1 ? make_int2(h.x, (h.y >> 14) & 0x3FFF) : fan[b0];
+        const int2 rec0 = fan[b0];
+        const int2 last = kind == 1 ? make_int2(h.x, (h.y >> 14) & 0x3FFF) : rec0;
         double2 pi = q[i];
-        Raw rn = load_raw<0>(q, nullptr, fan[b0]);
+        // neighbour data one triangle ahead of use, fan records two ahead (as in the scalar kernel)
+        Raw rn = load_raw<0>(q, nullptr, rec0);
         Raw rp = load_raw<0>(q, nullptr, d > 1 ? fan[b0 + 1] : last);
+        int2 recn = d > 2 ? fan[b0 + 2] : last;
         Nb cur = make_nb<0>(rn, pi, bad);
         const int first_pos = cur.pos;
         const ff z = ff_make(0.f);
-        Block2 dg = {z, z, z, z}, fs = dg, ca = dg;
+        Block2 ndg = {z, z, z, z}, fs = ndg, ca = ndg;           // ndg: sum of the off-diagonal blocks
         for (int32_t e = 0; e < d; e++) {
             rn = rp;
-            if (e + 2 <= d) rp = load_raw<0>(q, nullptr, e + 2 < d ? fan[b0 + e + 2] : last);
+            if (e + 2 <= d) {
+                rp = load_raw<0>(q, nullptr, recn);
+                recn = e + 3 < d ? fan[b0 + e + 3] : last;
+            }
             Nb nxt = make_nb<0>(rn, pi, bad);
-            Block2 k[3];
-            ff D = elas_terms(q, i, cur, nxt, cs, k, bad);
+            // the blocks of columns n_e and n_{e+1}; the FP64 path (badly shaped triangles) fills a
+            // stack array, the fast path stays in registers
+            Block2 kc, kn;
+            ff D = ff_dot2(cur.x, nxt.x, nxt.y, ff_neg(cur.y));
+            if (well_shaped(cur, nxt, D.h)) {
+                ff rr = ff_mulf(ff_rcp_fast(D), 0.5f);
+                ff eax = ff_sub(cur.x, nxt.x), eay = ff_sub(cur.y, nxt.y);
+                ff sax = ff_mul(eax, rr), say = ff_mul(eay, rr);
+                kc = elas_block(sax, say, nxt.x, nxt.y, cs);
+                kn = elas_block(sax, say, ff_neg(cur.x), ff_neg(cur.y), cs);
+            } else {
+                Block2 k[3];
+                D = elas_terms_fp64(q, i, cur.id, nxt.id, cs, k, bad);
+                kc = k[1];
+                kn = k[2];
+            }
             orient |= !(D.h > 0.f);
-            dg = badd(dg, k[0]);
-            if (e == 0) fs = k[1];
-            else write_block(out, rb, u, cur.pos, badd(ca, k[1]));
-            ca = k[2];
+            if (e == 0) {
+                fs = kc;
+            } else {
+                Block2 v = badd(ca, kc);
+                ndg = badd(ndg, v);
+                write_block(out, rb, u, cur.pos, v);
+            }
+            ca = kn;
             cur = nxt;
         }
         if (kind == 0) {
-            write_block(out, rb, u, first_pos, badd(fs, ca));
+            Block2 v = badd(fs, ca);
+            ndg = badd(ndg, v);
+            write_block(out, rb, u, first_pos, v);
         } else {
+            ndg = badd(badd(ndg, fs), ca);
             write_block(out, rb, u, first_pos, fs);
             write_block(out, rb, u, cur.pos, ca);
         }
-        write_block(out, rb, u, pself, dg);
+        write_block(out, rb, u, pself, bneg(ndg));
     }
     if (bad) atomicOr(err, 2);
     if (orient) atomicOr(err, 1);
