@@ -48,6 +48,33 @@ __device__ __forceinline__ ff ff_from_value(double d, int& bad) {
     return ff_from_double(d, bad);
 }
 
+// Scaling by powers of two (exact): a group of FP64 inputs that enters a computation linearly
+// (upstream gradients, say) is brought to magnitude about 1 by a common 2^k before the split,
+// so that its range does not matter, and the results are scaled back by 2^-k in the conversion.
+// Values below 2^-74 of the group's largest one become zero: they are negligible against it.
+
+// k such that the largest |v| of the group times 2^k lies in [1, 2), from the biased FP64
+// exponent emax of the largest value (0 for an all-zero group); clamped so that every
+// conversion stays within the FP64 and float exponent ranges.
+__device__ __forceinline__ int ff_group_scale(unsigned emax) {
+    int k = emax ? 1023 - (int)emax : 0;
+    return k < -100 ? -100 : (k > 800 ? 800 : k);
+}
+
+__device__ __forceinline__ unsigned fp64_biased_exponent(double d) { return ((unsigned)__double2hiint(d) >> 20) & 0x7FFu; }
+
+// d * 2^k as a double-float (|d| 2^k <= 2^1 for the group's values).
+__device__ __forceinline__ ff ff_from_double_scaled(double d, int k) {
+    unsigned hi32 = (unsigned)__double2hiint(d), lo32 = (unsigned)__double2loint(d);
+    int E = (int)((hi32 >> 20) & 0x7FFu);
+    int Es = E + k;
+    if (E == 0 || Es < 949 || Es > 1150) return ff{0.f, 0.f};
+    unsigned sgn = hi32 & 0x80000000u;
+    float h = __uint_as_float(sgn | ((unsigned)(Es - 896) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29));
+    float l = __uint2float_rn(lo32 & 0x1FFFFFFFu) * __uint_as_float(((unsigned)(Es - 948) << 23) | sgn);
+    return ff{h, l};
+}
+
 // The error-free transforms below must not be altered by the compiler's multiply-add
 // contraction (fusing p + e with the product that made p, say, breaks their exactness), so each
 // rounding step is written with the _rn intrinsics, which are never contracted; fmaf is used only
@@ -147,6 +174,15 @@ __device__ __forceinline__ ff ff_rcp(ff a) {
     return fast_two_sum(y, FMUL(y, r));
 }
 
+// 1/a from the approximate float reciprocal and one Newton step in double-float (about 46 bits).
+__device__ __forceinline__ ff ff_rcp_fast(ff a) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a.h));
+    float r = fmaf(-a.h, y, 1.0f);
+    r = fmaf(-a.l, y, r);
+    return fast_two_sum(y, FMUL(y, r));
+}
+
 // FP64 value of a float, built bit by bit (no conversion instruction): sign, exponent rebiased
 // from 127 to 1023, significand shifted into place. Zero (and flushed subnormals) give 0.
 __device__ __forceinline__ double f2d_bits(float f) {
@@ -159,3 +195,14 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // FP64 value of h + l: both words are exact in FP64, so one FP64 addition gives h + l correctly
 // rounded (the only FP64 instruction of the conversion).
 __device__ __forceinline__ double ff_to_double(ff a) { return f2d_bits(a.h) + f2d_bits(a.l); }
+
+// f * 2^-k as FP64, built bit by bit (k as from ff_group_scale, so the result stays normal).
+__device__ __forceinline__ double f2d_bits_scaled(float f, int k) {
+    unsigned b = __float_as_uint(f);
+    unsigned hi = (((b & 0x7FFFFFFFu) >> 3) + ((unsigned)(896 - k) << 20)) | (b & 0x80000000u);
+    hi = (b & 0x7F800000u) ? hi : 0u;
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// (h + l) * 2^-k as FP64 (one FP64 addition).
+__device__ __forceinline__ double ff_to_double_scaled(ff a, int k) { return f2d_bits_scaled(a.h, k) + f2d_bits_scaled(a.l, k); }

@@ -83,14 +83,6 @@ __device__ __noinline__ RowTerms row_terms_fp64(const double2* __restrict__ q, c
     return t;
 }
 
-// 1/a from the approximate float reciprocal and one Newton step in double-float (about 46 bits).
-__device__ __forceinline__ ff ff_rcp_fast(ff a) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a.h));
-    float r = fmaf(-a.h, y, 1.0f);
-    r = fmaf(-a.l, y, r);
-    return fast_two_sum(y, FMUL(y, r));
-}
 
 // Shape test: sin^2 of each angle is D^2 over the product of the two adjacent squared edges;
 // all three must be at least 1/16 (angles of at least about 14.5 degrees) for the fast path.
