@@ -43,15 +43,15 @@ def _check_map_sampled(m, rp, ci, mp, seed=4, count=4096):
 
 
 @pytest.fixture(scope="module")
-def config2():
+def mesh_2048():
     m = meshgen.square_mesh(2048, meshgen.SEED_BASE + 2)
     w = meshgen.vertex_weights(m, meshgen.SEED_BASE + 2)
     return m, w
 
 
 @pytest.mark.parametrize("variant", [feasm.ATOMIC, feasm.GATHER, feasm.ROW])
-def test_config2_stiff_wmass_full_size(config2, variant):
-    m, w = config2
+def test_stiff_wmass_2048_full_size(mesh_2048, variant):
+    m, w = mesh_2048
     mesh = feasm.Mesh(m.q, m.me)
     pat = feasm.Pattern(mesh, gather=(variant == feasm.GATHER))
     assert pat.nnz == _structured_nnz(2048) == 29_372_417
@@ -80,7 +80,7 @@ def test_config2_stiff_wmass_full_size(config2, variant):
     assert vm.sum() == pytest.approx(np.sum(D / 2 * (w[me[0]] + w[me[1]] + w[me[2]]) / 3), rel=1e-12)
 
 
-def test_config1_mass_full_oracle():
+def test_mass_64_full_oracle():
     m = meshgen.square_mesh(64, meshgen.SEED_BASE + 1)
     mesh = feasm.Mesh(m.q, m.me)
     pat = feasm.Pattern(mesh, gather=True)
@@ -94,7 +94,7 @@ def test_config1_mass_full_oracle():
 
 
 @pytest.mark.parametrize("variant", [feasm.ATOMIC, feasm.GATHER, feasm.ROW])
-def test_config3_elasticity_full_size(variant):
+def test_elasticity_1024_full_size(variant):
     m = meshgen.square_mesh(1024, meshgen.SEED_BASE + 3)
     mesh = feasm.Mesh(m.q, m.me)
     pat = feasm.Pattern(mesh, dofs=2, gather=(variant == feasm.GATHER))
@@ -146,7 +146,7 @@ def test_adjoint_gather_bit_identical():
         np.testing.assert_array_equal(cur, ref)
 
 
-def test_config5_adjoint_finite_differences():
+def test_adjoint_1024_finite_differences():
     """Central differences (h = 1e-6) of L = sum(G_S S.values) + sum(G_M M^[w].values) on 64
     sampled coordinates of the 1024 x 1024 mesh. The forward uses the deterministic variant,
     so values of the non-zeros a move does not touch are bit-identical and drop out exactly."""
