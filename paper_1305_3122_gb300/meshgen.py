@@ -29,7 +29,9 @@ _M2 = np.uint64(0x94D049BB133111EB)
 # stream ids (one per purpose, so that changing one draw never shifts another)
 S_JITTER_X, S_JITTER_Y, S_PERM, S_WNOISE, S_SIZES, S_GRAD_S, S_GRAD_M, S_SAMPLE = range(1, 9)
 
-# seeds of the five standard workloads: 13053122 + workload number
+# seeds of the standard workloads: SEED_BASE + 1 mass on 64 x 64 cells, + 2 stiffness and weighted
+# mass on 2048 x 2048, + 3 elasticity on 1024 x 1024, + 4 the batch of 256 meshes, + 5 the
+# differentiated assembly on 1024 x 1024
 SEED_BASE = 13053122
 
 
