@@ -155,46 +155,12 @@ __device__ __forceinline__ int fan_pos(const Fan& f, int32_t i, int kind, int32_
     return p;
 }
 
-// Row counts: simple rows from the fan analysis (closed: d + 1 entries, open: d + 2); general
-// rows by sorting; rows with more than FAST_DEG triangles are listed for the block kernels.
-// kind_out keeps the row kind in bits 0-1 and, for a simple row, its chain start in bits 2-4.
-// abase: start of each vertex's bucket in adj (the same offsets as vptr).
-__global__ void k_row_count(const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase,
-                            const int2* __restrict__ adj, int32_t nq,
-                            int32_t* __restrict__ row_nnz, unsigned char* __restrict__ kind_out,
-                            int32_t* __restrict__ big_list, int32_t* __restrict__ big_count, int* __restrict__ too_big) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
-        int32_t i = (int32_t)r;
-        int32_t beg = abase[i], d = vptr[i + 1] - vptr[i];
-        if (d == 0) { row_nnz[i] = 0; kind_out[i] = KIND_GENERAL; continue; }
-        if (d <= FAN_MAX) {
-            Fan f;
-            load_fan(adj, beg, d, f);
-            int start;
-            int kind = fan_kind(f, start);
-            if (kind != KIND_GENERAL) {
-                row_nnz[i] = d + 1 + (kind == KIND_OPEN);
-                kind_out[i] = (unsigned char)(kind | (start << 2));    // the fill pass reuses the chain start
-                continue;
-            }
-        }
-        kind_out[i] = KIND_GENERAL;
-        if (d > FAST_DEG) {
-            if (d > FE_MAX_VALENCE) { *too_big = 1; row_nnz[i] = 0; continue; }
-            big_list[atomicAdd(big_count, 1)] = i;
-            continue;
-        }
-        int32_t cols[2 * FAST_DEG + 1];
-        row_nnz[i] = row_columns(i, beg, d, adj, cols);
-    }
-}
-
-// Fill of a simple row (closed or open fan with chain start `start`): fan-ordered neighbours
-// with their positions (fan[beg + e] = (n_e, pos(n_e))), header (n_d, pos_self | pos_nd << 14 |
-// kind << 28) and col_idx from position o.
-__device__ __forceinline__ void fill_simple(int32_t i, int32_t beg, int32_t d, int kind, int start, const Fan& f,
-                                            int32_t o, int32_t* __restrict__ col_idx, int2* __restrict__ fan,
-                                            int2* __restrict__ hdr) {
+// Fan records and header of a simple row (closed or open fan with chain start `start`):
+// fan-ordered neighbours with their column positions inside the row (fan[beg + e] = (n_e,
+// pos(n_e))) and the header (n_d, pos_self | pos_nd << 14 | kind << 28). None of it depends on
+// the row's CSR offset.
+__device__ __forceinline__ void simple_row_records(int32_t i, int32_t beg, int32_t d, int kind, int start, const Fan& f,
+                                                   int2* __restrict__ fan, int2* __restrict__ hdr) {
     int32_t jcur = 0, lcur = 0;
 #pragma unroll
     for (int e = 0; e < FAN_MAX; e++)
@@ -210,12 +176,8 @@ __device__ __forceinline__ void fill_simple(int32_t i, int32_t beg, int32_t d, i
     }
     int pself = fan_pos(f, i, kind, lend, i);
     int pend = fan_pos(f, i, kind, lend, lend);
-    col_idx[o + pself] = i;
-    if (kind == KIND_OPEN) col_idx[o + pend] = lend;
     for (int s = 0; s < d; s++) {
-        int pj = fan_pos(f, i, kind, lend, jcur);
-        fan[beg + s] = make_int2(jcur, pj);
-        col_idx[o + pj] = jcur;
+        fan[beg + s] = make_int2(jcur, fan_pos(f, i, kind, lend, jcur));
         int32_t nl = lcur;
 #pragma unroll
         for (int e = 0; e < FAN_MAX; e++)
@@ -226,46 +188,74 @@ __device__ __forceinline__ void fill_simple(int32_t i, int32_t beg, int32_t d, i
     hdr[i] = make_int2(lend, pself | (pend << 14) | (kind << 28));
 }
 
-// Fill of a general row with at most FAST_DEG triangles: its u sorted unique columns, its (j, l)
-// pairs sorted lexicographically (a deterministic order) and a place in the general-row list.
-__device__ __forceinline__ void fill_general(int32_t i, int32_t beg, int32_t abeg, int32_t d, const int32_t* cols,
-                                             int u, int32_t o, const int2* __restrict__ adj,
-                                             int32_t* __restrict__ col_idx, int2* __restrict__ fan,
-                                             int32_t* __restrict__ gen_list, int32_t* __restrict__ gen_count) {
-    for (int t = 0; t < u; t++) col_idx[o + t] = cols[t];
-    long long key[FAST_DEG];
-    for (int32_t s = 0; s < d; s++) {
-        int2 p = adj[abeg + s];
-        key[s] = ((long long)p.x << 32) | (unsigned)p.y;
-    }
-    isort64(key, d);
-    for (int32_t s = 0; s < d; s++) fan[beg + s] = make_int2((int32_t)(key[s] >> 32), (int32_t)(key[s] & 0xffffffffLL));
-    gen_list[atomicAdd(gen_count, 1)] = i;
-}
-
-// Row fill for rows with at most FAST_DEG triangles (kinds and counts from k_row_count, offsets
-// from the scan of the counts).
-__global__ void k_row_fill(const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase,
-                           const int2* __restrict__ adj, int32_t nq,
-                           const unsigned char* __restrict__ kinds, const int32_t* __restrict__ row_ptr,
-                           int32_t* __restrict__ col_idx, int2* __restrict__ fan, int2* __restrict__ hdr,
-                           int32_t* __restrict__ gen_list, int32_t* __restrict__ gen_count) {
+// Row analysis, once per row: the column count, and everything of the row that does not depend
+// on its CSR offset. Simple rows (one fan of at most FAN_MAX triangles): d + 1 entries (closed) or
+// d + 2 (open), fan records and header. General rows with at most FAST_DEG triangles: the count
+// of their sorted unique columns, their (j, l) pairs sorted lexicographically (a deterministic
+// order) and a place in the general-row list. Rows with more triangles are listed for the block
+// kernels. bucket: start of each vertex's bucket in adj (the same offsets as vptr).
+__global__ void k_row_analyse(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t nq,
+                              int32_t* __restrict__ row_nnz, int2* __restrict__ fan, int2* __restrict__ hdr,
+                              int32_t* __restrict__ big_list, int32_t* __restrict__ big_count,
+                              int32_t* __restrict__ gen_list, int32_t* __restrict__ gen_count, int* __restrict__ too_big) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = (int32_t)r;
-        int32_t abeg = abase[i], beg = vptr[i], d = vptr[i + 1] - beg;
-        int kind = kinds[i] & 3, start = kinds[i] >> 2;
-        int32_t o = row_ptr[i];
-        if (kind != KIND_GENERAL) {
+        int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+        if (d == 0) { row_nnz[i] = 0; hdr[i] = make_int2(-1, KIND_GENERAL << 28); continue; }
+        if (d <= FAN_MAX) {
             Fan f;
-            load_fan(adj, abeg, d, f);
-            fill_simple(i, beg, d, kind, start, f, o, col_idx, fan, hdr);
-            continue;
+            load_fan(adj, beg, d, f);
+            int start;
+            int kind = fan_kind(f, start);
+            if (kind != KIND_GENERAL) {
+                row_nnz[i] = d + 1 + (kind == KIND_OPEN);
+                simple_row_records(i, beg, d, kind, start, f, fan, hdr);
+                continue;
+            }
         }
         hdr[i] = make_int2(-1, KIND_GENERAL << 28);
+        if (d > FAST_DEG) {
+            if (d > FE_MAX_VALENCE) { *too_big = 1; row_nnz[i] = 0; continue; }
+            big_list[atomicAdd(big_count, 1)] = i;
+            continue;
+        }
+        int32_t cols[2 * FAST_DEG + 1];
+        row_nnz[i] = row_columns(i, beg, d, adj, cols);
+        long long key[FAST_DEG];
+        for (int32_t s = 0; s < d; s++) {
+            int2 p = adj[beg + s];
+            key[s] = ((long long)p.x << 32) | (unsigned)p.y;
+        }
+        isort64(key, d);
+        for (int32_t s = 0; s < d; s++) fan[beg + s] = make_int2((int32_t)(key[s] >> 32), (int32_t)(key[s] & 0xffffffffLL));
+        gen_list[atomicAdd(gen_count, 1)] = i;
+    }
+}
+
+// col_idx of the rows with at most FAST_DEG triangles, once the offsets are known: simple rows
+// from their fan records and header, general rows by sorting their columns again (they are
+// rare).
+__global__ void k_col_fill(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t nq,
+                           const int32_t* __restrict__ row_ptr, const int2* __restrict__ fan,
+                           const int2* __restrict__ hdr, int32_t* __restrict__ col_idx) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = (int32_t)r;
+        int2 h = hdr[i];
+        int kind = h.y >> 28;
+        int32_t o = row_ptr[i], beg = vptr[i], d = vptr[i + 1] - beg;
+        if (kind != KIND_GENERAL) {
+            col_idx[o + (h.y & 0x3FFF)] = i;
+            if (kind == KIND_OPEN) col_idx[o + ((h.y >> 14) & 0x3FFF)] = h.x;
+            for (int32_t s = 0; s < d; s++) {
+                int2 e = fan[beg + s];
+                col_idx[o + e.y] = e.x;
+            }
+            continue;
+        }
         if (d == 0 || d > FAST_DEG) continue;
         int32_t cols[2 * FAST_DEG + 1];
-        int u = row_columns(i, abeg, d, adj, cols);
-        fill_general(i, beg, abeg, d, cols, u, o, adj, col_idx, fan, gen_list, gen_count);
+        int u = row_columns(i, beg, d, adj, cols);
+        for (int t = 0; t < u; t++) col_idx[o + t] = cols[t];
     }
 }
 
@@ -516,9 +506,8 @@ struct Temps {
     int32_t *row_nnz = nullptr, *big_list = nullptr, *counters = nullptr, *cur = nullptr;
     int* flag = nullptr;                 // points into counters (counters[0..1], flags[2..3])
     int2* adj = nullptr;
-    unsigned char* kinds = nullptr;
     ~Temps() {
-        fe_free(row_nnz); fe_free(big_list); fe_free(counters); fe_free(adj); fe_free(kinds);
+        fe_free(row_nnz); fe_free(big_list); fe_free(counters); fe_free(adj);
         fe_free(cur);
     }
 };
@@ -570,22 +559,21 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     if (want_map && (st = fe_alloc_n(&p->map, 9 * (size_t)nme, "element-to-nnz map"))) return st;
     const size_t big_smem = (2 * (size_t)FE_MAX_VALENCE + 1) * (sizeof(int32_t) + 1);
 
-    // counts (fan analysis), offsets (scan of the counts) and fill of the rows with at most
-    // FAST_DEG triangles
+    // counts and offset-free records (one fan analysis per row), offsets (scan of the counts),
+    // then col_idx of the rows with at most FAST_DEG triangles
     auto rows = [&]() -> fe_status {
-        fe_status sa = t.kinds ? FE_OK : fe_alloc_n(&t.kinds, (size_t)nq + 1, "row kinds");
-        if (sa) return sa;
+        fe_status sa;
         if (nq > 0) {
-            { FE_PROF("k_row_count", s); k_row_count<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.row_nnz, t.kinds, t.big_list, t.counters, t.flag); }
-            FE_LAUNCHED("k_row_count");
+            { FE_PROF("k_row_analyse", s); k_row_analyse<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, t.adj, nq, t.row_nnz, p->fan, p->hdr, t.big_list,
+                                                                                             t.counters, p->gen_rows, t.counters + 1, t.flag); }
+            FE_LAUNCHED("k_row_analyse");
             { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, nullptr, t.row_nnz, nullptr); }
             FE_LAUNCHED("k_row_big (count)");
         }
         if ((sa = fe_exclusive_scan(t.row_nnz, p->row_ptr, nq, s, nullptr))) return sa;
         if (nq > 0) {
-            { FE_PROF("k_row_fill", s); k_row_fill<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, p->vptr, t.adj, nq, t.kinds, p->row_ptr, p->col_idx, p->fan,
-                                                                                       p->hdr, p->gen_rows, t.counters + 1); }
-            FE_LAUNCHED("k_row_fill");
+            { FE_PROF("k_col_fill", s); k_col_fill<<<fe_grid(nq, 256, 16), 256, 0, s>>>(p->vptr, t.adj, nq, p->row_ptr, p->fan, p->hdr, p->col_idx); }
+            FE_LAUNCHED("k_col_fill");
         }
         return FE_OK;
     };
