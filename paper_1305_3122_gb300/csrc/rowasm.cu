@@ -391,8 +391,15 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
     if (DM) put(outX, rb + pself, ff_mul(sD, cs.c12));
 }
 
+// Resident blocks of 128 threads per SM for each kind: as many as fit without register spills
+// (measured at 2048 x 2048 cells: S and M run fastest at 7, the weighted kinds at 5).
 template <int KIND>
-__global__ void __launch_bounds__(128, 5) k_fan_scalar(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ vptr,
+struct FanOcc {
+    static constexpr int blocks = (KIND == W_S || KIND == W_M) ? 7 : (KIND == (W_S | W_M) ? 6 : 5);
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(128, FanOcc<KIND>::blocks) k_fan_scalar(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ vptr,
                                                        const int2* __restrict__ fan, const int2* __restrict__ hdr,
                                                        const double2* __restrict__ q, const VRec* __restrict__ vr, int32_t r0,
                                                        int32_t r1, Consts cs, double* __restrict__ out0, double* __restrict__ out1,
@@ -711,7 +718,7 @@ static Consts make_consts(double lam, double mu) {
 }
 
 static constexpr int FAN_BLOCK = 256;
-static constexpr int FAN_SCALAR_BLOCK = 128;   // 5 blocks of 128 per SM at up to 96 registers
+static constexpr int FAN_SCALAR_BLOCK = 128;
 static constexpr int GEN_BLOCK = 64;
 
 template <int KIND>
@@ -729,7 +736,7 @@ static fe_status launch_scalar(fe_mesh m, fe_pattern p, const double* w, double*
             return fe_cuda_fail(e0, "k_pack_vrec");
         }
     }
-    { FE_PROF("k_fan_scalar", s); k_fan_scalar<KIND><<<fe_grid(m->nq, FAN_SCALAR_BLOCK, 5), FAN_SCALAR_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, 0, m->nq, cs, out0, out1, m->err); }
+    { FE_PROF("k_fan_scalar", s); k_fan_scalar<KIND><<<fe_grid(m->nq, FAN_SCALAR_BLOCK, FanOcc<KIND>::blocks), FAN_SCALAR_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, 0, m->nq, cs, out0, out1, m->err); }
     cudaError_t e = cudaGetLastError();
     fe_free(vr);
     if (e != cudaSuccess) return fe_cuda_fail(e, "k_fan_scalar");
@@ -881,7 +888,7 @@ extern "C" fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const
         int32_t r0 = (int32_t)((int64_t)nq * k / E2E_BLOCKS), r1 = (int32_t)((int64_t)nq * (k + 1) / E2E_BLOCKS);
         if (r1 > r0) {
             FE_PROF("k_fan_scalar", s);
-            k_fan_scalar<W_S | W_W><<<fe_grid(r1 - r0, FAN_SCALAR_BLOCK, 5), FAN_SCALAR_BLOCK, 0, s>>>(
+            k_fan_scalar<W_S | W_W><<<fe_grid(r1 - r0, FAN_SCALAR_BLOCK, FanOcc<W_S | W_W>::blocks), FAN_SCALAR_BLOCK, 0, s>>>(
                 p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, r0, r1, cs, Sd, Md, m->err);
         }
         cudaError_t e = cudaGetLastError();
