@@ -92,34 +92,36 @@ __device__ __forceinline__ int row_columns(int32_t i, int32_t beg, int32_t d, co
 
 // ------------------------------------------------------------------ fans (simple rows)
 
+// A row's fan with exactly D triangles (D <= FAN_MAX): triangle e is (i, J[e], L[e]),
+// counter-clockwise. The analysis is written for a compile-time D (the caller dispatches on the
+// row's valence), so no loop runs over unused slots.
+template <int D>
 struct Fan {
-    int32_t J[FAN_MAX], L[FAN_MAX];
-    int d;
+    int32_t J[D], L[D];
 };
 
-__device__ __forceinline__ void load_fan(const int2* __restrict__ adj, int32_t beg, int d, Fan& f) {
-    f.d = d;
+template <int D>
+__device__ __forceinline__ void load_fan(const int2* __restrict__ adj, int32_t beg, Fan<D>& f) {
 #pragma unroll
-    for (int e = 0; e < FAN_MAX; e++) {
-        int2 p = e < d ? adj[beg + e] : make_int2(-1, -2);
+    for (int e = 0; e < D; e++) {
+        int2 p = adj[beg + e];
         f.J[e] = p.x;
         f.L[e] = p.y;
     }
 }
 
-// Analyses the fan: returns KIND_CLOSED / KIND_OPEN for one chain through all d triangles with
+// Analyses the fan: returns KIND_CLOSED / KIND_OPEN for one chain through all D triangles with
 // distinct j's and distinct l's, else KIND_GENERAL. start = first triangle of the chain (for a
 // closed fan, the one with the smallest j, so the order does not depend on the bucket order).
-__device__ __forceinline__ int fan_kind(const Fan& f, int& start) {
+template <int D>
+__device__ __forceinline__ int fan_kind(const Fan<D>& f, int& start) {
     int nstart = 0, dup = 0, minj = INT32_MAX, minj_e = 0;
     start = 0;
 #pragma unroll
-    for (int e = 0; e < FAN_MAX; e++) {
-        if (e >= f.d) continue;
+    for (int e = 0; e < D; e++) {
         bool is_l = false;
 #pragma unroll
-        for (int g = 0; g < FAN_MAX; g++) {
-            if (g >= f.d) continue;
+        for (int g = 0; g < D; g++) {
             is_l |= f.L[g] == f.J[e];
             if (g > e) dup |= (f.J[g] == f.J[e]) | (f.L[g] == f.L[e]);
         }
@@ -131,14 +133,15 @@ __device__ __forceinline__ int fan_kind(const Fan& f, int& start) {
     // follow the chain: it must visit every triangle once before closing (or ending)
     int32_t jstart = 0, lcur = 0;
 #pragma unroll
-    for (int e = 0; e < FAN_MAX; e++)
+    for (int e = 0; e < D; e++)
         if (e == start) { jstart = f.J[e]; lcur = f.L[e]; }
-    for (int s = 1; s < f.d; s++) {
+#pragma unroll
+    for (int s = 1; s < D; s++) {
         bool found = false;
         int32_t lnext = 0;
 #pragma unroll
-        for (int e = 0; e < FAN_MAX; e++)
-            if (e < f.d && f.J[e] == lcur) { found = true; lnext = f.L[e]; }
+        for (int e = 0; e < D; e++)
+            if (f.J[e] == lcur) { found = true; lnext = f.L[e]; }
         if (!found || lcur == jstart) return KIND_GENERAL;   // chain broken, or closed before the end
         lcur = lnext;
     }
@@ -148,10 +151,11 @@ __device__ __forceinline__ int fan_kind(const Fan& f, int& start) {
 
 // Column position of vertex x in the row of vertex i with fan f (kind closed/open, last
 // neighbour lend): the number of row entries below x.
-__device__ __forceinline__ int fan_pos(const Fan& f, int32_t i, int kind, int32_t lend, int32_t x) {
+template <int D>
+__device__ __forceinline__ int fan_pos(const Fan<D>& f, int32_t i, int kind, int32_t lend, int32_t x) {
     int p = (i < x) + (kind == KIND_OPEN && lend < x);
 #pragma unroll
-    for (int e = 0; e < FAN_MAX; e++) p += (e < f.d && f.J[e] < x);
+    for (int e = 0; e < D; e++) p += f.J[e] < x;
     return p;
 }
 
@@ -159,33 +163,50 @@ __device__ __forceinline__ int fan_pos(const Fan& f, int32_t i, int kind, int32_
 // fan-ordered neighbours with their column positions inside the row (fan[beg + e] = (n_e,
 // pos(n_e))) and the header (n_d, pos_self | pos_nd << 14 | kind << 28). None of it depends on
 // the row's CSR offset.
-__device__ __forceinline__ void simple_row_records(int32_t i, int32_t beg, int32_t d, int kind, int start, const Fan& f,
+template <int D>
+__device__ __forceinline__ void simple_row_records(int32_t i, int32_t beg, int kind, int start, const Fan<D>& f,
                                                    int2* __restrict__ fan, int2* __restrict__ hdr) {
     int32_t jcur = 0, lcur = 0;
 #pragma unroll
-    for (int e = 0; e < FAN_MAX; e++)
+    for (int e = 0; e < D; e++)
         if (e == start) { jcur = f.J[e]; lcur = f.L[e]; }
     // the last neighbour: follow the chain to its end
     int32_t lend = lcur;
-    for (int s = 1; s < d; s++) {
+#pragma unroll
+    for (int s = 1; s < D; s++) {
         int32_t nl = lend;
 #pragma unroll
-        for (int e = 0; e < FAN_MAX; e++)
-            if (e < d && f.J[e] == lend) nl = f.L[e];
+        for (int e = 0; e < D; e++)
+            if (f.J[e] == lend) nl = f.L[e];
         lend = nl;
     }
     int pself = fan_pos(f, i, kind, lend, i);
     int pend = fan_pos(f, i, kind, lend, lend);
-    for (int s = 0; s < d; s++) {
+#pragma unroll
+    for (int s = 0; s < D; s++) {
         fan[beg + s] = make_int2(jcur, fan_pos(f, i, kind, lend, jcur));
         int32_t nl = lcur;
 #pragma unroll
-        for (int e = 0; e < FAN_MAX; e++)
-            if (e < d && f.J[e] == lcur) nl = f.L[e];
+        for (int e = 0; e < D; e++)
+            if (f.J[e] == lcur) nl = f.L[e];
         jcur = lcur;
         lcur = nl;
     }
     hdr[i] = make_int2(lend, pself | (pend << 14) | (kind << 28));
+}
+
+// A simple row of valence D: returns its column count, or 0 if the fan is not simple (then
+// nothing is written).
+template <int D>
+__device__ __forceinline__ int32_t simple_row(int32_t i, int32_t beg, const int2* __restrict__ adj,
+                                              int2* __restrict__ fan, int2* __restrict__ hdr) {
+    Fan<D> f;
+    load_fan<D>(adj, beg, f);
+    int start;
+    int kind = fan_kind<D>(f, start);
+    if (kind == KIND_GENERAL) return 0;
+    simple_row_records<D>(i, beg, kind, start, f, fan, hdr);
+    return D + 1 + (kind == KIND_OPEN);
 }
 
 // Row analysis, once per row: the column count, and everything of the row that does not depend
@@ -203,13 +224,20 @@ __global__ void k_row_analyse(const int32_t* __restrict__ vptr, const int2* __re
         int32_t beg = vptr[i], d = vptr[i + 1] - beg;
         if (d == 0) { row_nnz[i] = 0; hdr[i] = make_int2(-1, KIND_GENERAL << 28); continue; }
         if (d <= FAN_MAX) {
-            Fan f;
-            load_fan(adj, beg, d, f);
-            int start;
-            int kind = fan_kind(f, start);
-            if (kind != KIND_GENERAL) {
-                row_nnz[i] = d + 1 + (kind == KIND_OPEN);
-                simple_row_records(i, beg, d, kind, start, f, fan, hdr);
+            int32_t cnt = 0;
+            switch (d) {
+                case 1: cnt = simple_row<1>(i, beg, adj, fan, hdr); break;
+                case 2: cnt = simple_row<2>(i, beg, adj, fan, hdr); break;
+                case 3: cnt = simple_row<3>(i, beg, adj, fan, hdr); break;
+                case 4: cnt = simple_row<4>(i, beg, adj, fan, hdr); break;
+                case 5: cnt = simple_row<5>(i, beg, adj, fan, hdr); break;
+                case 6: cnt = simple_row<6>(i, beg, adj, fan, hdr); break;
+                case 7: cnt = simple_row<7>(i, beg, adj, fan, hdr); break;
+                default: cnt = simple_row<8>(i, beg, adj, fan, hdr); break;
+            }
+            static_assert(FAN_MAX == 8, "the valence dispatch covers 1..8");
+            if (cnt > 0) {
+                row_nnz[i] = cnt;
                 continue;
             }
         }
