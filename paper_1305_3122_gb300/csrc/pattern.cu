@@ -262,28 +262,66 @@ __global__ void k_row_analyse(const int32_t* __restrict__ vptr, const int2* __re
 
 // col_idx of the rows with at most FAST_DEG triangles, once the offsets are known: simple rows
 // from their fan records and header, general rows by sorting their columns again (they are
-// rare).
-__global__ void k_col_fill(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t nq,
-                           const int32_t* __restrict__ row_ptr, const int2* __restrict__ fan,
-                           const int2* __restrict__ hdr, int32_t* __restrict__ col_idx) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
-        int32_t i = (int32_t)r;
-        int2 h = hdr[i];
-        int kind = h.y >> 28;
-        int32_t o = row_ptr[i], beg = vptr[i], d = vptr[i + 1] - beg;
-        if (kind != KIND_GENERAL) {
-            col_idx[o + (h.y & 0x3FFF)] = i;
-            if (kind == KIND_OPEN) col_idx[o + ((h.y >> 14) & 0x3FFF)] = h.x;
-            for (int32_t s = 0; s < d; s++) {
-                int2 e = fan[beg + s];
-                col_idx[o + e.y] = e.x;
-            }
-            continue;
+// rare). The 32 rows of a warp own one contiguous range of col_idx: a warp of simple rows places
+// its entries in shared memory first and writes the range with coalesced stores (scattered
+// 4-byte stores made this pass L1-bound); a warp with a general row, or a range too long for
+// the staging area, writes directly.
+constexpr int CF_BLOCK = 256;
+constexpr int CF_STAGE = 32 * (FAN_MAX + 2);                    // entries per warp (simple rows)
+
+__global__ void __launch_bounds__(CF_BLOCK) k_col_fill(const int32_t* __restrict__ vptr, const int2* __restrict__ adj,
+                                                       int32_t nq, const int32_t* __restrict__ row_ptr,
+                                                       const int2* __restrict__ fan, const int2* __restrict__ hdr,
+                                                       int32_t* __restrict__ col_idx) {
+    __shared__ int32_t stage[CF_BLOCK / 32][CF_STAGE];
+    const int lane = threadIdx.x & 31;
+    int32_t* st = stage[threadIdx.x >> 5];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // every lane of a warp runs the same number of iterations (the loop bound is rounded up to a
+    // multiple of 32 rows), so the warp-wide operations below see all 32 lanes
+    const int64_t nq32 = ((int64_t)nq + 31) / 32 * 32;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq32; r += stride) {
+        const bool act = r < nq;
+        const int32_t i = (int32_t)r;
+        int2 h = act ? hdr[i] : make_int2(0, 0);
+        const int kind = act ? (h.y >> 28) : KIND_CLOSED;
+        int32_t o = 0, e = 0, beg = 0, d = 0;
+        if (act) {
+            o = row_ptr[i];
+            e = row_ptr[i + 1];
+            beg = vptr[i];
+            d = vptr[i + 1] - beg;
         }
-        if (d == 0 || d > FAST_DEG) continue;
-        int32_t cols[2 * FAST_DEG + 1];
-        int u = row_columns(i, beg, d, adj, cols);
-        for (int t = 0; t < u; t++) col_idx[o + t] = cols[t];
+        const bool general = act && kind == KIND_GENERAL;
+        const unsigned any_general = __ballot_sync(0xffffffffu, general);
+        // the warp's range [lo, hi): rows are consecutive, so it starts at lane 0's offset and ends
+        // at the last active lane's end
+        const unsigned active = __ballot_sync(0xffffffffu, act);
+        const int last = active ? 31 - __clz(active) : 0;
+        const int32_t lo = __shfl_sync(0xffffffffu, o, 0);
+        const int32_t hi = __shfl_sync(0xffffffffu, e, last);
+        const bool staged = active && !any_general && hi - lo <= CF_STAGE;   // warp-uniform
+        auto put = [&](int32_t at, int32_t v) {
+            if (staged) st[at - lo] = v;
+            else col_idx[at] = v;
+        };
+        if (act && !general) {
+            put(o + (h.y & 0x3FFF), i);
+            if (kind == KIND_OPEN) put(o + ((h.y >> 14) & 0x3FFF), h.x);
+            for (int32_t s = 0; s < d; s++) {
+                int2 f = fan[beg + s];
+                put(o + f.y, f.x);
+            }
+        } else if (general && d > 0 && d <= FAST_DEG) {
+            int32_t cols[2 * FAST_DEG + 1];
+            int u = row_columns(i, beg, d, adj, cols);
+            for (int t = 0; t < u; t++) col_idx[o + t] = cols[t];
+        }
+        if (staged) {
+            __syncwarp();
+            for (int32_t p = lane; p < hi - lo; p += 32) col_idx[lo + p] = st[p];
+            __syncwarp();
+        }
     }
 }
 
@@ -600,7 +638,7 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
         }
         if ((sa = fe_exclusive_scan(t.row_nnz, p->row_ptr, nq, s, nullptr))) return sa;
         if (nq > 0) {
-            { FE_PROF("k_col_fill", s); k_col_fill<<<fe_grid(nq, 256, 16), 256, 0, s>>>(p->vptr, t.adj, nq, p->row_ptr, p->fan, p->hdr, p->col_idx); }
+            { FE_PROF("k_col_fill", s); k_col_fill<<<fe_grid(nq, CF_BLOCK, 8), CF_BLOCK, 0, s>>>(p->vptr, t.adj, nq, p->row_ptr, p->fan, p->hdr, p->col_idx); }
             FE_LAUNCHED("k_col_fill");
         }
         return FE_OK;
