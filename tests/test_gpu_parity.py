@@ -44,6 +44,21 @@ def fan_mesh(n_out: int, ring2: bool = True):
     return q, me
 
 
+def fans_mesh(n_fans: int, n_out: int):
+    """n_fans disjoint fans of valence n_out whose centres are vertices 0 .. n_fans - 1: one vertex
+    block of the pattern build's two-level placement then holds more incidences than its
+    shared-memory staging area, so that block is placed directly in global memory."""
+    pts, tris = [], []
+    for c in range(n_fans):
+        pts.append((3.0 * c, 0.0))
+    t = np.linspace(0, 2 * np.pi, n_out, endpoint=False)
+    for c in range(n_fans):
+        base = n_fans + c * n_out
+        pts += [(3.0 * c + np.cos(a), np.sin(a)) for a in t]
+        tris += [(c, base + i, base + (i + 1) % n_out) for i in range(n_out)]
+    return np.array(pts).T.copy(), np.array(tris, dtype=np.int32).T.copy()
+
+
 def _mesh_cases():
     m64 = meshgen.square_mesh(64, meshgen.SEED_BASE + 1)
     m37 = meshgen.square_mesh(37, 5)
@@ -51,7 +66,9 @@ def _mesh_cases():
     q12, me12 = fan_mesh(12)
     q2 = np.array([[0.0, 1.0, 1.0, 0.0], [0.0, 0.0, 1.0, 1.0]])
     me2 = np.array([[0, 0], [1, 2], [2, 3]], np.int32)
+    qb, meb = fans_mesh(5, 4000)
     return {"square64": (m64.q, m64.me), "square37": (m37.q, m37.me), "fan70": (qf, mef), "fan12": (q12, me12),
+            "fans5x4000": (qb, meb),
             "two": (q2, me2),
             "one": (q2, me2[:, :1].copy())}
 
