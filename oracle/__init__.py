@@ -58,6 +58,8 @@ def lib() -> ctypes.CDLL:
         _lib.or_sparse.argtypes = [I64, I64, I64, P, P, P, P, P, P, I64, P]
         _lib.or_assemble.argtypes = [ctypes.c_int, I64, I64, P, P, P, D, D, P, P, P, I64, P, P]
         _lib.or_adjoint.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, P, P, P]
+        _lib.or_drop_zeros.argtypes = [I64, P, P, P, P, P, P]
+        _lib.or_drop_zeros.restype = I64
         for f in ("or_triplets", "or_sparse", "or_assemble", "or_adjoint"):
             getattr(_lib, f).restype = ctypes.c_int
     return _lib
@@ -137,6 +139,18 @@ def sparse(I, J, K, n_rows: int, n_cols: int):
     if st:
         raise OracleError(st, "sparse")
     return row_ptr, col_idx[:nnz.value].copy(), val[:nnz.value].copy()
+
+
+def drop_zeros(row_ptr, col_idx, val):
+    """CSR without the entries equal to 0.0 (Matlab's sparse() stores no zero), order kept."""
+    row_ptr, col_idx, val = _i32(row_ptr), _i32(col_idx), _f64(val)
+    n_rows = row_ptr.shape[0] - 1
+    nnz = int(row_ptr[-1]) if n_rows >= 0 else 0
+    rp = np.empty(n_rows + 1, np.int32)
+    ci = np.empty(max(nnz, 1), np.int32)
+    va = np.empty(max(nnz, 1))
+    n = lib().or_drop_zeros(n_rows, _p(row_ptr), _p(col_idx), _p(val), _p(rp), _p(ci), _p(va))
+    return rp, ci[:n].copy(), va[:n].copy()
 
 
 def assemble(kind: int, q, me, w=None, lam: float = 1.0, mu: float = 0.5):

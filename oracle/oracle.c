@@ -15,7 +15,8 @@
  *     (Section 5, "Ke = E(:)"; Section 7.1 for n = 6);
  *   - the sparse(I,J,K,m,n) semantics of Section 5: triplets with equal (row, col) are summed.
  *     Result in CSR, columns ascending in each row. Reading kept here: the pattern is
- *     structural, so a sum that happens to be exactly 0.0 is still stored.
+ *     structural, so a sum that happens to be exactly 0.0 is still stored; or_drop_zeros then
+ *     gives Matlab's value-dependent result (no zero stored).
  *
  * Conventions: indices are 0-based (the paper is 1-based). q is [2][nq] row-major (x row,
  * then y row); me is [3][nme] row-major. The area |T| is not an input here: it is half the
@@ -244,6 +245,29 @@ int or_sparse(int64_t n_rows, int64_t n_cols, int64_t ntrip, const int32_t* I, c
     *nnz_out = nnz;
     free(idx);
     return OR_OK;
+}
+
+/* Matlab's sparse() stores no zero: an entry of K that is zero adds nothing, and a position whose
+ * sum is zero is not stored (Section 5). or_sparse keeps those positions (the structural
+ * reading); this removes every entry that compares equal to 0.0 (+0 and -0) from a CSR matrix,
+ * keeping the others in order (NaN compares unequal to 0 and stays). The outputs may not alias
+ * the inputs; col_idx_out and val_out need room for row_ptr[n_rows] entries. Returns the number
+ * of entries kept. */
+int64_t or_drop_zeros(int64_t n_rows, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                      int32_t* row_ptr_out, int32_t* col_idx_out, double* val_out) {
+    int64_t n = 0;
+    row_ptr_out[0] = 0;
+    for (int64_t i = 0; i < n_rows; i++) {
+        for (int64_t s = row_ptr[i]; s < row_ptr[i + 1]; s++) {
+            if (val[s] != 0.0) {
+                col_idx_out[n] = col_idx[s];
+                val_out[n] = val[s];
+                n++;
+            }
+        }
+        row_ptr_out[i + 1] = (int32_t)n;
+    }
+    return n;
 }
 
 /* One full assembly: triplets of one kind, then sparse(). n_rows = nq (or 2nq for OR_ELAS).

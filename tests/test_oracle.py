@@ -139,6 +139,76 @@ def test_sparse_sums_in_ascending_input_order_and_keeps_zeros():
     assert va[0] == 0.0 and va[2] == 0.0     # exact zeros are stored, not dropped
 
 
+@pytest.mark.parametrize("which", ["", "2"])
+def test_paper_csc_example_drop_zeros(which):
+    """Section 4's example with every entry of the dense A fed as a triplet, zeros included, and
+    one zero position fed as x and -x: sparse() keeps those positions (structural reading), and
+    dropping the zeros must give the printed aa / ia / ja, which store no zero."""
+    g = _load_golden_csc()
+    A = g["A" + which]
+    J, I = np.meshgrid(np.arange(A.shape[1]), np.arange(A.shape[0]))
+    I, J = I.ravel(), J.ravel()
+    K = A[I, J]
+    z = int(np.nonzero(K == 0)[0][0])
+    I = np.append(I, I[z]); J = np.append(J, J[z]); K = np.append(K, 3.5); K[z] = -3.5
+    order = np.random.default_rng(1).permutation(len(K))
+    rp, ci, va = oracle.sparse(J[order], I[order], K[order], A.shape[1], A.shape[0])
+    assert len(va) == A.size                         # structural: zeros stored
+    rp, ci, va = oracle.drop_zeros(rp, ci, va)
+    np.testing.assert_array_equal(va, g["aa" + which])
+    np.testing.assert_array_equal(ci + 1, g["ia" + which])
+    np.testing.assert_array_equal(rp + 1, g["ja" + which])
+
+
+def test_drop_zeros_cell_diagonals_of_unjittered_mesh():
+    """On the unjittered N x N mesh with N a power of two (exact coordinates) every cell's diagonal
+    is opposite a right angle in both of its triangles, so S is exactly 0 there (cot 90 = 0,
+    Eq. 3): dropping the zeros removes exactly those 2 N^2 entries, node ids differing by N + 2
+    in the unpermuted numbering. M has no zero."""
+    N = 8
+    m = meshgen.square_mesh(N, 3, jitter=0.0, permute=False)
+    rp, ci, va = oracle.assemble(oracle.STIFF, m.q, m.me)
+    rp2, ci2, va2 = oracle.drop_zeros(rp, ci, va)
+    assert len(ci) - len(ci2) == 2 * N * N
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    gone = va == 0.0
+    assert np.all(np.abs(rows[gone] - ci[gone]) == N + 2)
+    np.testing.assert_array_equal(va2, va[~gone])
+    np.testing.assert_array_equal(ci2, ci[~gone])
+    rpm, cim, vam = oracle.assemble(oracle.MASS, m.q, m.me)
+    rpm2, cim2, vam2 = oracle.drop_zeros(rpm, cim, vam)
+    np.testing.assert_array_equal(rpm2, rpm)
+
+
+def test_drop_zeros_special_values():
+    """+0 and -0 go; NaN, subnormals and negative values stay, in order; empty rows stay empty."""
+    rp = np.array([0, 3, 3, 7, 8], np.int32)
+    ci = np.array([0, 2, 3, 0, 1, 2, 3, 1], np.int32)
+    va = np.array([0.0, np.nan, -0.0, 5e-324, -2.0, 0.0, 1.0, 0.0])
+    rp2, ci2, va2 = oracle.drop_zeros(rp, ci, va)
+    np.testing.assert_array_equal(rp2, [0, 1, 1, 4, 4])
+    np.testing.assert_array_equal(ci2, [2, 0, 1, 3])
+    assert np.isnan(va2[0]) and va2[1] == 5e-324 and va2[2] == -2.0 and va2[3] == 1.0
+
+
+def test_drop_zeros_brute_force():
+    """Random CSR with about a third of the values zero, against a boolean mask and per-row
+    counts."""
+    rng = np.random.default_rng(5)
+    for n_rows in (0, 1, 17, 300):
+        lens = rng.integers(0, 12, n_rows)
+        rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+        nnz = int(rp[-1])
+        ci = rng.integers(0, 50, nnz).astype(np.int32)
+        va = rng.standard_normal(nnz) * (rng.random(nnz) > 0.35)
+        rp2, ci2, va2 = oracle.drop_zeros(rp, ci, va)
+        keep = va != 0
+        np.testing.assert_array_equal(ci2, ci[keep])
+        np.testing.assert_array_equal(va2, va[keep])
+        per_row = np.array([keep[rp[i]:rp[i + 1]].sum() for i in range(n_rows)], dtype=np.int64)
+        np.testing.assert_array_equal(np.diff(rp2), per_row)
+
+
 def test_sparse_rejects_out_of_range():
     with pytest.raises(oracle.OracleError):
         oracle.sparse(np.array([0, 3]), np.array([0, 0]), np.array([1.0, 2.0]), 3, 3)
