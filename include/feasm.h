@@ -209,6 +209,26 @@ fe_status fe_assemble_stiff_wmass_noalloc(fe_mesh mesh, fe_pattern pattern, cons
                                           double* S_values, double* Mw_values, int64_t cap,
                                           fe_stream stream);
 
+/* -------------------------------------------------------------------- zero dropping ---- */
+
+/* Matlab's sparse() stores no zero (Section 5): an entry of K that is zero adds nothing and a
+ * position whose sum is zero is not stored. The assembly calls keep every structural position
+ * (one pattern then serves every matrix and every q); this call gives the value-dependent
+ * result. It removes from a CSR matrix every entry whose value compares equal to 0.0 (+0 and -0)
+ * and keeps the others in their order (NaN compares unequal to 0 and stays). For the symmetric
+ * M, M^w, S and K the CSR arrays are also Matlab's CSC arrays.
+ *   row_ptr [n_rows + 1], col_idx [row_ptr[n_rows]], values [row_ptr[n_rows]]: the input, device,
+ *     for example a pattern's arrays (fe_pattern_info) and an assembled value array;
+ *   row_ptr_out [n_rows + 1], col_idx_out [cap], values_out [cap]: device, caller-owned; they
+ *     must not overlap the inputs (FE_ERR_INVALID_ARG if they start at the same address);
+ *   *nnz_out (host): the number of entries kept.
+ * 0 <= n_rows < 2^31. Synchronises once, to read the count. If cap is below the count the call
+ * returns FE_ERR_BUFFER_TOO_SMALL with *nnz_out set and row_ptr_out written, and col_idx_out /
+ * values_out untouched. */
+fe_status fe_csr_drop_zeros(int64_t n_rows, const int32_t* row_ptr, const int32_t* col_idx,
+                            const double* values, int32_t* row_ptr_out, int32_t* col_idx_out,
+                            double* values_out, int64_t cap, int64_t* nnz_out, fe_stream stream);
+
 /* --------------------------------------------------------------------------- adjoint ---- */
 
 /* Needs a pattern with the element-to-nnz map (FE_PATTERN_MAP or FE_PATTERN_GATHER).

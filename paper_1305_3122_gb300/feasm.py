@@ -47,6 +47,7 @@ SIGNATURES = {
     "fe_assemble_elas": (_INT, [_P, _P, _D, _D, _INT, _P, _I64, _P]),
     "fe_assemble_stiff_wmass_noalloc": (_INT, [_P, _P, _P, _P, _P, _I64, _P]),
     "fe_adjoint_stiff_wmass": (_INT, [_P, _P, _P, _P, _P, _INT, _P, _P, _P]),
+    "fe_csr_drop_zeros": (_INT, [_I64, _P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "fe_assemble_stiff_wmass_host": (_INT, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "fe_batch_create": (_INT, [_I32, _P, _P, ctypes.POINTER(_P)]),
     "fe_batch_tune": (_INT, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
@@ -233,6 +234,26 @@ def _values(pattern: Pattern, out: torch.Tensor | None) -> torch.Tensor:
     out = pattern.new_values() if out is None else out
     _dptr(out, torch.float64, "values")
     return out
+
+
+def drop_zeros(row_ptr: torch.Tensor, col_idx: torch.Tensor, values: torch.Tensor, stream=None):
+    """CSR (row_ptr, col_idx, values) without the entries equal to 0.0, as Matlab's sparse()
+    stores them (fe_csr_drop_zeros): int32 / int32 / float64 CUDA tensors in, new ones out."""
+    n_rows = row_ptr.numel() - 1
+    if n_rows < 0 or col_idx.numel() != values.numel():
+        raise ValueError("row_ptr must have n_rows + 1 entries and col_idx / values the same length")
+    rp = torch.empty(n_rows + 1, dtype=torch.int32, device="cuda")
+    cap = values.numel()
+    ci = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
+    va = torch.empty(max(cap, 1), dtype=torch.float64, device="cuda")
+    kept = _I64(0)
+    if cap == 0:   # no entry: pass one-element buffers rather than null pointers
+        col_idx = torch.zeros(1, dtype=torch.int32, device="cuda")
+        values = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _check(lib().fe_csr_drop_zeros(n_rows, _dptr(row_ptr, torch.int32, "row_ptr"), _dptr(col_idx, torch.int32, "col_idx"),
+                                   _dptr(values, torch.float64, "values"), rp.data_ptr(), ci.data_ptr(), va.data_ptr(),
+                                   cap, ctypes.byref(kept), _stream(stream)), "fe_csr_drop_zeros")
+    return rp, ci[:kept.value], va[:kept.value]
 
 
 def assemble_mass(mesh: Mesh, pattern: Pattern, variant: int = ATOMIC, out=None, stream=None) -> torch.Tensor:
