@@ -60,6 +60,15 @@ def lib() -> ctypes.CDLL:
         _lib.or_adjoint.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, P, P, P]
         _lib.or_drop_zeros.argtypes = [I64, P, P, P, P, P, P]
         _lib.or_drop_zeros.restype = I64
+        _lib.or_tet_volume6.argtypes = [P, P, P]
+        _lib.or_tet_volume6.restype = D
+        _lib.or_tet_elem_mass.argtypes = [D, P]
+        _lib.or_tet_elem_wmass.argtypes = [D, P, P]
+        _lib.or_tet_elem_stiff.argtypes = [P, P, P, D, P]
+        _lib.or_tet_triplets.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, P, P]
+        _lib.or_tet_assemble.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, P, I64, P, P]
+        for f in ("or_tet_triplets", "or_tet_assemble"):
+            getattr(_lib, f).restype = ctypes.c_int
         for f in ("or_triplets", "or_sparse", "or_assemble", "or_adjoint"):
             getattr(_lib, f).restype = ctypes.c_int
     return _lib
@@ -216,3 +225,61 @@ def csr_row_values(kind: int, q, me, rows, w=None, lam: float = 1.0, mu: float =
         rp, ci, va = sparse(I[sel], J[sel], K[sel], n_rows, n_rows)
         out.append((ci[rp[r]:rp[r + 1]], va[rp[r]:rp[r + 1]]))
     return out
+
+
+# ------------------------------------------------------------------ tetrahedra (3-D P1)
+
+def tet_volume6(x, y, z) -> float:
+    """det [p1-p0 | p2-p0 | p3-p0] = 6 |K| (signed)."""
+    return lib().or_tet_volume6(_p(_f64(x)), _p(_f64(y)), _p(_f64(z)))
+
+
+def tet_elem_mass(vol: float) -> np.ndarray:
+    E = np.empty(16)
+    lib().or_tet_elem_mass(vol, _p(E))
+    return E.reshape(4, 4)
+
+
+def tet_elem_wmass(vol: float, w) -> np.ndarray:
+    E = np.empty(16)
+    lib().or_tet_elem_wmass(vol, _p(_f64(w)), _p(E))
+    return E.reshape(4, 4)
+
+
+def tet_elem_stiff(x, y, z, vol: float) -> np.ndarray:
+    E = np.empty(16)
+    lib().or_tet_elem_stiff(_p(_f64(x)), _p(_f64(y)), _p(_f64(z)), vol, _p(E))
+    return E.reshape(4, 4)
+
+
+def tet_triplets(kind: int, q, me, w=None):
+    """(Ig, Jg, Kg) of a tetrahedral mesh, entry c = 16k + 4*jl + il."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    I = np.empty(16 * nme, np.int32)
+    J = np.empty_like(I)
+    K = np.empty(16 * nme)
+    w = _f64(w) if w is not None else np.zeros(max(nq, 1))
+    bad = ctypes.c_int64(-1)
+    st = lib().or_tet_triplets(kind, nq, nme, _p(q), _p(me), _p(w), _p(I), _p(J), _p(K), ctypes.byref(bad))
+    if st:
+        raise OracleError(st, f"tet_triplets (element {bad.value})")
+    return I, J, K
+
+
+def tet_assemble(kind: int, q, me, w=None):
+    """Global CSR (row_ptr, col_idx, val) of a tetrahedral mesh: triplets then sparse()."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    cap = max(16 * nme, 1)
+    row_ptr = np.empty(nq + 1, np.int32)
+    col_idx = np.empty(cap, np.int32)
+    val = np.empty(cap)
+    w = _f64(w) if w is not None else np.zeros(max(nq, 1))
+    nnz = ctypes.c_int64(0)
+    bad = ctypes.c_int64(-1)
+    st = lib().or_tet_assemble(kind, nq, nme, _p(q), _p(me), _p(w), _p(row_ptr), _p(col_idx), _p(val), cap,
+                               ctypes.byref(nnz), ctypes.byref(bad))
+    if st:
+        raise OracleError(st, f"tet_assemble (element {bad.value})")
+    return row_ptr, col_idx[:nnz.value].copy(), val[:nnz.value].copy()

@@ -375,3 +375,135 @@ int or_adjoint(int kind, int64_t nq, int64_t nme, const double* q, const int32_t
     }
     return OR_OK;
 }
+
+/* --------------------------------------------------------- tetrahedra (3-D P1) ---- */
+
+/* The paper states that the method extends to three dimensions and gives no formulas (its
+ * conclusion); these are the P1 element matrices on a tetrahedron K with vertices p0..p3,
+ * written from the standard integrals:
+ *   phi_a affine, phi_a(p_b) = delta_ab; grad(phi_1), grad(phi_2), grad(phi_3) are the rows of
+ *   J^{-1} with J = [p1-p0 | p2-p0 | p3-p0] (columns), and grad(phi_0) = -(their sum);
+ *   integral over K of phi_0^a0 phi_1^a1 phi_2^a2 phi_3^a3 = 6|K| a0! a1! a2! a3! / (a0+a1+a2+a3+3)!
+ * so that
+ *   mass            M^e_ab   = |K|/20 (1 + delta_ab)
+ *   weighted mass   M^{e,[w]}_ab = |K|/120 sum_c kappa_abc w_c, kappa = 6 if a = b = c, 2 if exactly
+ *                   two of a, b, c are equal, 1 if all three differ (w_h = sum_c w_c phi_c)
+ *   stiffness       S^e_ab   = |K| grad(phi_a) . grad(phi_b)
+ * q is [3][nq] (x, y, z rows), me is [4][nme]; element k writes c = 16k + 4*jl + il. The signed
+ * volume 6|K| = det J must be > 0. */
+
+/* det [p1-p0 | p2-p0 | p3-p0] = 6 |K| (signed) */
+double or_tet_volume6(const double x[4], const double y[4], const double z[4]) {
+    double ax = x[1] - x[0], ay = y[1] - y[0], az = z[1] - z[0];
+    double bx = x[2] - x[0], by = y[2] - y[0], bz = z[2] - z[0];
+    double cx = x[3] - x[0], cy = y[3] - y[0], cz = z[3] - z[0];
+    return ax * (by * cz - bz * cy) - bx * (ay * cz - az * cy) + cx * (ay * bz - az * by);
+}
+
+void or_tet_elem_mass(double vol, double E[16]) {
+    for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++)
+            E[4 * a + b] = (vol / 20.0) * (a == b ? 2.0 : 1.0);
+}
+
+void or_tet_elem_wmass(double vol, const double w[4], double E[16]) {
+    for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++) {
+            double s = 0.0;
+            for (int c = 0; c < 4; c++) {
+                int eq = (a == b) + (a == c) + (b == c);     /* 3: all equal, 1: one pair, 0: distinct */
+                double kappa = eq == 3 ? 6.0 : (eq == 1 ? 2.0 : 1.0);
+                s += kappa * w[c];
+            }
+            E[4 * a + b] = (vol / 120.0) * s;
+        }
+}
+
+/* grad(phi_a), a = 0..3, as g[a][0..2] */
+static void tet_gradients(const double x[4], const double y[4], const double z[4], double g[4][3]) {
+    double J[3][3] = {{x[1] - x[0], x[2] - x[0], x[3] - x[0]},
+                      {y[1] - y[0], y[2] - y[0], y[3] - y[0]},
+                      {z[1] - z[0], z[2] - z[0], z[3] - z[0]}};
+    double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1])
+               - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0])
+               + J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    /* J^{-1} = adj(J) / det; row r of J^{-1} is grad(phi_{r+1}) */
+    double inv[3][3];
+    inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    for (int d = 0; d < 3; d++) {
+        g[1][d] = inv[0][d];
+        g[2][d] = inv[1][d];
+        g[3][d] = inv[2][d];
+        g[0][d] = -(inv[0][d] + inv[1][d] + inv[2][d]);
+    }
+}
+
+void or_tet_elem_stiff(const double x[4], const double y[4], const double z[4], double vol, double E[16]) {
+    double g[4][3];
+    tet_gradients(x, y, z, g);
+    for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++)
+            E[4 * a + b] = vol * (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]);
+}
+
+/* Ig, Jg, Kg of a tetrahedral mesh for OR_MASS, OR_WMASS or OR_STIFF (c = 16k + 4*jl + il). */
+int or_tet_triplets(int kind, int64_t nq, int64_t nme, const double* q, const int32_t* me,
+                    const double* w, int32_t* I, int32_t* J, double* K, int64_t* bad_element) {
+    if (kind < OR_MASS || kind > OR_STIFF || nq < 0 || nme < 0) return OR_ERR_ARG;
+    for (int64_t k = 0; k < nme; k++) {
+        int32_t v[4];
+        double x[4], y[4], z[4], E[16];
+        for (int a = 0; a < 4; a++) {
+            v[a] = me[a * nme + k];
+            if (v[a] < 0 || v[a] >= nq) { if (bad_element) *bad_element = k; return OR_ERR_INDEX; }
+            x[a] = q[v[a]];
+            y[a] = q[nq + v[a]];
+            z[a] = q[2 * nq + v[a]];
+        }
+        for (int a = 0; a < 4; a++)
+            for (int b = a + 1; b < 4; b++)
+                if (v[a] == v[b]) { if (bad_element) *bad_element = k; return OR_ERR_DEGENERATE; }
+        double D = or_tet_volume6(x, y, z);
+        if (!(D > 0.0)) { if (bad_element) *bad_element = k; return OR_ERR_ORIENT; }
+        double vol = D / 6.0;
+        if (kind == OR_MASS) {
+            or_tet_elem_mass(vol, E);
+        } else if (kind == OR_WMASS) {
+            double wl[4] = {w[v[0]], w[v[1]], w[v[2]], w[v[3]]};
+            or_tet_elem_wmass(vol, wl, E);
+        } else {
+            or_tet_elem_stiff(x, y, z, vol, E);
+        }
+        for (int jl = 0; jl < 4; jl++)
+            for (int il = 0; il < 4; il++) {
+                int64_t c = 16 * k + 4 * jl + il;
+                I[c] = v[il];
+                J[c] = v[jl];
+                K[c] = E[4 * il + jl];
+            }
+    }
+    return OR_OK;
+}
+
+/* One full tetrahedral assembly: triplets, then sparse() (cap >= 16 nme always suffices). */
+int or_tet_assemble(int kind, int64_t nq, int64_t nme, const double* q, const int32_t* me,
+                    const double* w, int32_t* row_ptr, int32_t* col_idx, double* val, int64_t cap,
+                    int64_t* nnz_out, int64_t* bad_element) {
+    int64_t ntrip = 16 * nme;
+    int32_t* I = (int32_t*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(int32_t));
+    int32_t* J = (int32_t*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(int32_t));
+    double* K = (double*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(double));
+    int st = (I && J && K) ? OR_OK : OR_ERR_NOMEM;
+    if (!st) st = or_tet_triplets(kind, nq, nme, q, me, w, I, J, K, bad_element);
+    if (!st) st = or_sparse(nq, nq, ntrip, I, J, K, row_ptr, col_idx, val, cap, nnz_out);
+    free(I); free(J); free(K);
+    return st;
+}

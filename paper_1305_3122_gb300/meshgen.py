@@ -1,4 +1,5 @@
-"""Seeded synthetic inputs: jittered, node-permuted triangulations of the unit square.
+"""Seeded synthetic inputs: jittered, node-permuted triangulations of the unit square (and
+tetrahedralisations of the unit cube).
 
 This module generates *inputs only* (vertex coordinates, connectivity, vertex weights,
 upstream gradients, sample indices). It holds none of the assembly arithmetic, so it can
@@ -27,7 +28,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 # stream ids (one per purpose, so that changing one draw never shifts another)
-S_JITTER_X, S_JITTER_Y, S_PERM, S_WNOISE, S_SIZES, S_GRAD_S, S_GRAD_M, S_SAMPLE = range(1, 9)
+S_JITTER_X, S_JITTER_Y, S_PERM, S_WNOISE, S_SIZES, S_GRAD_S, S_GRAD_M, S_SAMPLE, S_JITTER_Z = range(1, 10)
 
 # seeds of the standard workloads: SEED_BASE + 1 mass on 64 x 64 cells, + 2 stiffness and weighted
 # mass on 2048 x 2048, + 3 elasticity on 1024 x 1024, + 4 the batch of 256 meshes, + 5 the
@@ -135,6 +136,63 @@ def square_mesh(N: int, seed: int, jitter: float = 0.2, permute: bool = True) ->
         q = qp
         me = newid[me]
     return Mesh(q=np.ascontiguousarray(q), me=np.ascontiguousarray(me.astype(np.int32)), N=N)
+
+
+def cube_mesh(N: int, seed: int, jitter: float = 0.05, permute: bool = True) -> Mesh:
+    """Unit cube cut into N^3 cells, each cell split into six tetrahedra around its main diagonal.
+
+    Node (i, j, k) has id ``(k*(N+1)+j)*(N+1)+i`` at ``(i/N, j/N, k/N)`` before the permutation.
+    Cell (i, j, k) with corner v0 = (i, j, k) gives, for each order (d1, d2, d3) of the three
+    axes, the tetrahedron (v0, v0+e_d1, v0+e_d1+e_d2, v0+e_d1+e_d2+e_d3), its last two vertices
+    exchanged when the order is odd so that every one has positive signed volume
+    det[p1-p0 | p2-p0 | p3-p0]; elements are cell-major, six per cell. Interior nodes move by
+    independent offsets drawn uniformly from [-jitter*h, jitter*h) per coordinate; boundary nodes
+    stay put. Then the node ids are randomly permuted, as for ``square_mesh``. ``q`` is [3, nq]
+    float64 and ``me`` [4, nme] int32."""
+    if N < 1:
+        raise ValueError("N must be >= 1")
+    n1 = N + 1
+    h = 1.0 / N
+    nq = n1 ** 3
+    ii = np.tile(np.arange(n1), n1 * n1)
+    jj = np.tile(np.repeat(np.arange(n1), n1), n1)
+    kk = np.repeat(np.arange(n1), n1 * n1)
+    x, y, z = ii * h, jj * h, kk * h
+    interior = (ii > 0) & (ii < N) & (jj > 0) & (jj < N) & (kk > 0) & (kk < N)
+    if jitter != 0.0:
+        x = np.where(interior, x + (2.0 * stream_uniform(seed, S_JITTER_X, nq) - 1.0) * (jitter * h), x)
+        y = np.where(interior, y + (2.0 * stream_uniform(seed, S_JITTER_Y, nq) - 1.0) * (jitter * h), y)
+        z = np.where(interior, z + (2.0 * stream_uniform(seed, S_JITTER_Z, nq) - 1.0) * (jitter * h), z)
+    ci = np.tile(np.arange(N), N * N)
+    cj = np.tile(np.repeat(np.arange(N), N), N)
+    ck = np.repeat(np.arange(N), N * N)
+    v0 = (ck * n1 + cj) * n1 + ci
+    step = (1, n1, n1 * n1)                      # id offset of a unit move along x, y, z
+    orders = ((0, 1, 2), (1, 2, 0), (2, 0, 1), (0, 2, 1), (2, 1, 0), (1, 0, 2))   # three even, three odd
+    me = np.empty((4, 6 * N ** 3), dtype=np.int64)
+    for t, (d1, d2, d3) in enumerate(orders):
+        p1 = v0 + step[d1]
+        p2 = p1 + step[d2]
+        p3 = p2 + step[d3]
+        if t >= 3:
+            p2, p3 = p3, p2
+        me[0, t::6], me[1, t::6], me[2, t::6], me[3, t::6] = v0, p1, p2, p3
+    q = np.stack([x, y, z]).astype(np.float64)
+    if permute:
+        newid = random_permutation(seed, S_PERM, nq)
+        qp = np.empty_like(q)
+        qp[:, newid] = q
+        q = qp
+        me = newid[me]
+    return Mesh(q=np.ascontiguousarray(q), me=np.ascontiguousarray(me.astype(np.int32)), N=N)
+
+
+def vertex_weights3(mesh: Mesh, seed: int) -> np.ndarray:
+    """w_i = 1 + 0.5*sin(2*pi*x_i)*cos(2*pi*y_i)*cos(2*pi*z_i) + U(0, 0.1) at the vertices of a
+    tetrahedral mesh."""
+    x, y, z = mesh.q
+    noise = 0.1 * stream_uniform(seed, S_WNOISE, mesh.nq)
+    return 1.0 + 0.5 * np.sin(2.0 * math.pi * x) * np.cos(2.0 * math.pi * y) * np.cos(2.0 * math.pi * z) + noise
 
 
 def vertex_weights(mesh: Mesh, seed: int) -> np.ndarray:

@@ -130,3 +130,93 @@ def assemble_dense(kind, pts_all, me, w=None, lam=1, mu=Fraction(1, 2)):
             for j in range(m):
                 G[dof[i]][dof[j]] += E[i][j]
     return G
+
+
+# ------------------------------------------------------------------ tetrahedra
+
+def _solve(A, rhs):
+    """Exact solution of an n x n linear system (Gaussian elimination with pivot search)."""
+    n = len(A)
+    M = [list(A[r]) + [rhs[r]] for r in range(n)]
+    for c in range(n):
+        p = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[p] = M[p], M[c]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c] / M[c][c]
+                M[r] = [M[r][t] - f * M[c][t] for t in range(n + 1)]
+    return [M[r][n] / M[r][r] for r in range(n)]
+
+
+def barycentric3(pts):
+    """[(alpha, beta_x, beta_y, beta_z)] of the four barycentric coordinates of tetrahedron pts."""
+    A = [[Fraction(1), Fraction(x), Fraction(y), Fraction(z)] for (x, y, z) in pts]
+    return [tuple(_solve(A, [Fraction(int(a == b)) for b in range(4)])) for a in range(4)]
+
+
+def volume3(pts):
+    """|K| from the barycentric gradients: the coordinate l_0 = 1 - l_1 - l_2 - l_3 has the
+    constant gradient; |K| = 1 / (6 |det of the three gradients of l_1, l_2, l_3|)."""
+    b = barycentric3(pts)
+    G = [[b[a][1], b[a][2], b[a][3]] for a in (1, 2, 3)]
+    det = (G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) - G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0])
+           + G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]))
+    return 1 / (6 * abs(det))
+
+
+def mono3(vol, e):
+    """int_K l0^e0 l1^e1 l2^e2 l3^e3 = 6|K| e0! e1! e2! e3! / (e0+e1+e2+e3+3)!"""
+    num = 6 * vol
+    for v in e:
+        num *= factorial(v)
+    return num / factorial(sum(e) + 3)
+
+
+def tet_mass(pts):
+    vol = volume3(pts)
+    E = [[Fraction(0)] * 4 for _ in range(4)]
+    for a in range(4):
+        for b in range(4):
+            e = [0] * 4
+            e[a] += 1
+            e[b] += 1
+            E[a][b] = mono3(vol, e)
+    return E
+
+
+def tet_wmass(pts, w):
+    vol = volume3(pts)
+    E = [[Fraction(0)] * 4 for _ in range(4)]
+    for a in range(4):
+        for b in range(4):
+            for c in range(4):
+                e = [0] * 4
+                e[a] += 1
+                e[b] += 1
+                e[c] += 1
+                E[a][b] += Fraction(w[c]) * mono3(vol, e)
+    return E
+
+
+def tet_stiff(pts):
+    vol = volume3(pts)
+    g = [b[1:] for b in barycentric3(pts)]
+    return [[vol * sum(g[a][d] * g[b][d] for d in range(3)) for b in range(4)] for a in range(4)]
+
+
+def tet_assemble_dense(kind, pts_all, me, w=None):
+    """Dense global matrix of a tetrahedral mesh, exact (kind in mass, wmass, stiff)."""
+    n = len(pts_all)
+    G = [[Fraction(0)] * n for _ in range(n)]
+    for t in me:
+        pts = [pts_all[v] for v in t]
+        if kind == "mass":
+            E = tet_mass(pts)
+        elif kind == "wmass":
+            E = tet_wmass(pts, [w[v] for v in t])
+        else:
+            E = tet_stiff(pts)
+        for a in range(4):
+            for b in range(4):
+                G[t[a]][t[b]] += E[a][b]
+    return G
