@@ -349,6 +349,7 @@ def run_ours(args) -> int:
         line["elasticity"] = elasticity(feasm, meshgen, torch, flush, hbm, peak_kind)
         line["adjoint"] = adjoint(feasm, meshgen, torch, flush)
         line["drop_zeros"] = drop_zeros(feasm, torch, pat0, S, flush, hbm, peak_kind)
+        line["tetrahedra"] = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind)
     if not args.no_e2e:
         line["e2e"] = e2e(feasm, torch, m, w, args)
     if not args.no_cpu and world == 1:
@@ -484,6 +485,50 @@ def drop_zeros(feasm, torch, pat, S, flush, hbm, peak_kind) -> dict:
                          "frac": round(kbytes / k_ms / 1e6 / hbm, 4), "peak_source": f"{peak_kind} HBM copy bandwidth"}}
 
 
+# FP64 instructions of one stiffness element in k_tet_atomic / k_tet_stage: 9 edge differences,
+# 3 cross products (18), the determinant (3), g_0 (6), 1/(6 det) (about 9 with the division's
+# iteration), 10 dot products (30) and their scaling (10).
+TET_STIFF_FP64_OPS = 85
+# FP64 issue rate of GB300: 2 instructions per SM per clock (measured about 0.6 T DFMA/s).
+FP64_PEAK_G = 152 * 2 * 2.07
+
+
+def tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind) -> dict:
+    """P1 tetrahedra (the 3-D extension), 128^3-cell cube (jittered, node-permuted): mesh, pattern,
+    and S / M^w / M values by FP64 atomics and by the deterministic gather."""
+    seed = 13053122 + 6
+    m = meshgen.cube_mesh(128, seed)
+    w = torch.tensor(meshgen.vertex_weights3(m, seed), device="cuda")
+    q = torch.tensor(m.q, device="cuda")
+    me = torch.tensor(m.me, device="cuda")
+    ms_mesh = _time_calls(torch, lambda: feasm.TetMesh(q, me, borrow=True).close(), flush, reps=5)
+    mesh = feasm.TetMesh(q, me, borrow=True)
+    ms_pat = _time_calls(torch, lambda: feasm.TetPattern(mesh).close(), flush, reps=5)
+    ms_pat_g = _time_calls(torch, lambda: feasm.TetPattern(mesh, gather=True).close(), flush, reps=5)
+    pat = feasm.TetPattern(mesh, gather=True)
+    out = pat.new_values()
+    res = {}
+    for kn, k in (("S", feasm.TET_STIFF), ("Mw", feasm.TET_WMASS), ("M", feasm.TET_MASS)):
+        for vn, v in (("atomic", feasm.ATOMIC), ("gather", feasm.GATHER)):
+            res[f"{kn}_{vn}_ms"] = round(_time_calls(torch, lambda: feasm.tet_assemble(mesh, pat, k, w, v, out), flush), 4)
+    feasm.profile_reset()
+    feasm.profile_enable(True)
+    _time_calls(torch, lambda: feasm.tet_assemble(mesh, pat, feasm.TET_STIFF, None, feasm.ATOMIC, out), flush)
+    feasm.profile_enable(False)
+    prof = feasm.profile_read()
+    k_ms = prof["k_tet_atomic"][0] / prof["k_tet_atomic"][1]
+    ops = TET_STIFF_FP64_OPS * m.nme
+    nbytes = 16 * m.nme + 32 * m.nq + 64 * m.nme + 8 * pat.nnz     # me, vertex records, map, values
+    return {"workload": f"S, M^w, M of the 128^3-cell cube (nq={m.nq}, nme={m.nme} tetrahedra, nnz={pat.nnz})",
+            "mesh_ms": round(ms_mesh, 4), "pattern_ms": round(ms_pat, 4), "pattern_gather_ms": round(ms_pat_g, 4),
+            **res, "S_atomic_melem_s": round(m.nme / res["S_atomic_ms"] / 1e3, 1),
+            "roofline": {"kernel": "k_tet_atomic<S>", "bound": "fp64", "algorithmic_ops": ops,
+                         "achieved": round(ops / k_ms / 1e6, 1), "peak": round(FP64_PEAK_G, 1),
+                         "unit": "G FP64 instr/s", "frac": round(ops / k_ms / 1e6 / FP64_PEAK_G, 4),
+                         "peak_source": "2 FP64 instructions per SM per clock x 152 SMs x 2.07 GHz",
+                         "hbm_frac": round(nbytes / k_ms / 1e6 / hbm, 4), "hbm_peak_source": f"{peak_kind} HBM copy bandwidth"}}
+
+
 def adjoint(feasm, meshgen, torch, flush) -> dict:
     """dL/dq, dL/dw of L = <G_S, S> + <G_M, M^[w]> on the 1024 x 1024-cell mesh (deterministic gather)."""
     seed = 13053122 + 5
@@ -579,7 +624,7 @@ def main() -> int:
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-other", action="store_true", help="skip the elasticity, adjoint and zero-dropping legs")
+    ap.add_argument("--no-other", action="store_true", help="skip the elasticity, adjoint, zero-dropping and tetrahedra legs")
     ap.add_argument("--traffic", default=os.path.join(ROOT, "profiles", "traffic.json"),
                     help="per-kernel DRAM bytes per launch from an ncu capture (JSON)")
     args = ap.parse_args()

@@ -65,6 +65,8 @@ typedef struct CUstream_st* fe_stream;
 typedef struct fe_mesh_s* fe_mesh;        /* owns device copies of q and me */
 typedef struct fe_pattern_s* fe_pattern;  /* owns the CSR structure and element-to-nnz map */
 typedef struct fe_batch_s* fe_batch;      /* a set of (mesh, pattern) assembled together */
+typedef struct fe_tet_mesh_s* fe_tet_mesh;       /* tetrahedral mesh: device q [3][nq], me [4][nme] */
+typedef struct fe_tet_pattern_s* fe_tet_pattern; /* CSR structure and map of a tetrahedral mesh */
 
 /* Where the arrays passed to fe_mesh_create live. FE_PTR_DEVICE_BORROW: device memory, and the
  * mesh uses the caller's me in place instead of copying it (q is always packed into the mesh's
@@ -208,6 +210,51 @@ fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const double* q,
 fe_status fe_assemble_stiff_wmass_noalloc(fe_mesh mesh, fe_pattern pattern, const double* w,
                                           double* S_values, double* Mw_values, int64_t cap,
                                           fe_stream stream);
+
+/* ---------------------------------------------------------- tetrahedra (3-D P1) ---- */
+
+/* The paper states that its method extends to three dimensions without giving the formulas. These
+ * calls assemble the P1 matrices of a tetrahedral mesh from the standard integrals on a
+ * tetrahedron K with vertices p0..p3 (0-based local indices a, b, c):
+ *   mass           M^e_ab = |K|/20 (1 + delta_ab)
+ *   weighted mass  M^{e,[w]}_ab = |K|/120 sum_c kappa_abc w_c, kappa = 6 when a = b = c, 2 when
+ *                  exactly two of a, b, c are equal, 1 when all differ (w at the vertices)
+ *   stiffness      S^e_ab = |K| grad(phi_a) . grad(phi_b)
+ * with |K| = det[p1-p0 | p2-p0 | p3-p0] / 6, which must be > 0. The global matrix is the
+ * structural sum of the element matrices, as for triangles (every pair of vertices sharing a
+ * tetrahedron is stored, zeros included; fe_csr_drop_zeros removes them). */
+enum { FE_TET_MASS = 0, FE_TET_WMASS = 1, FE_TET_STIFF = 2 };
+
+/* Most tetrahedra around one vertex (fe_tet_pattern_build returns FE_ERR_LIMIT above it). */
+#define FE_TET_MAX_VALENCE 1024
+
+/* Creates a tetrahedral mesh from q ([3][nq] FP64: x row, y row, z row) and me ([4][nme] int32,
+ * 0-based), host or device memory as for fe_mesh_create (FE_PTR_DEVICE_BORROW uses me in place).
+ * Validates every tetrahedron: ids in [0, nq) (FE_ERR_INDEX_RANGE), four distinct vertices
+ * (FE_ERR_DEGENERATE), det[p1-p0 | p2-p0 | p3-p0] > 0 (FE_ERR_ORIENTATION). Synchronises once.
+ * 16 nme must be < 2^31. */
+fe_status fe_tet_mesh_create(int32_t nq, int32_t nme, const double* q, const int32_t* me, int ptr_kind,
+                             fe_stream stream, fe_tet_mesh* out);
+void fe_tet_mesh_destroy(fe_tet_mesh mesh);
+
+/* CSR structure (columns ascending in each row) and the element-to-nnz map of a tetrahedral mesh.
+ * flags: FE_PATTERN_GATHER adds the per-non-zero contribution lists and the staging buffer of
+ * FE_VARIANT_GATHER (other bits are ignored; the map is always built). Synchronises once (nnz). */
+fe_status fe_tet_pattern_build(fe_tet_mesh mesh, int flags, fe_stream stream, fe_tet_pattern* out);
+fe_status fe_tet_pattern_info(fe_tet_pattern pattern, int64_t* n_rows, int64_t* nnz, const int32_t** row_ptr,
+                              const int32_t** col_idx);
+/* The map (device, 16 nme int32): map[16k + 4 il + jl] = position of (me[il][k], me[jl][k]). Note
+ * the order: row-major per element (il before jl), unlike the column-wise scalar triangle map. */
+fe_status fe_tet_pattern_map(fe_tet_pattern pattern, const int32_t** map, int64_t* len);
+void fe_tet_pattern_destroy(fe_tet_pattern pattern);
+
+/* Values of one matrix kind (FE_TET_MASS, FE_TET_WMASS with w[nq] device FP64, FE_TET_STIFF) on
+ * the pattern's structure, into values[0 .. nnz) (device, capacity cap). variant: FE_VARIANT_ATOMIC
+ * (FP64 atomicAdd after zeroing) or FE_VARIANT_GATHER (element values staged, then each non-zero
+ * sums its contributions in ascending element order: bit-identical from run to run; needs a
+ * pattern built with FE_PATTERN_GATHER). Element arithmetic in FP64. */
+fe_status fe_tet_assemble(fe_tet_mesh mesh, fe_tet_pattern pattern, int kind, const double* w, int variant,
+                          double* values, int64_t cap, fe_stream stream);
 
 /* -------------------------------------------------------------------- zero dropping ---- */
 

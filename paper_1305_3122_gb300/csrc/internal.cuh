@@ -55,6 +55,46 @@ struct fe_pattern_s {
 // longest triangle fan a simple row may have (rows with more go to the general path)
 constexpr int FE_FAN_MAX = 8;
 
+// Tetrahedral (3-D P1) meshes and patterns (tet.cu).
+struct fe_tet_mesh_s {
+    int32_t nq = 0, nme = 0;
+    double4_32a* q = nullptr;   // [nq] (x, y, z, 0): one 32-byte record per vertex gather
+    int32_t* me = nullptr;      // [4][nme], the caller's layout
+    bool me_owned = true;
+    int32_t* deg = nullptr;     // [nq + 1] tetrahedra per vertex (counted during validation)
+    int* err = nullptr;         // [4] validation word
+    uint64_t topology_id = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+struct fe_tet_pattern_s {
+    int flags = 0;
+    int32_t nq = 0, nme = 0;
+    uint64_t topology_id = 0;
+    int64_t nnz = 0;
+    int32_t* row_ptr = nullptr;           // [nq + 1]
+    int32_t* col_idx = nullptr;           // [nnz]
+    int32_t* map = nullptr;               // [16 nme]: map[16k + 4 il + jl] = position of (me[il][k], me[jl][k])
+    int32_t* seg_ptr = nullptr;           // [nnz + 1] into perm (FE_PATTERN_GATHER)
+    int32_t* perm = nullptr;              // [16 nme] staging indices 16k + 4 il + jl, by non-zero, ascending k
+    double* kg = nullptr;                 // [16 nme] staged element values (FE_PATTERN_GATHER)
+    cudaStream_t last_stream = nullptr;
+};
+
+uint64_t fe_next_topology_id();
+
+// High float (top 24 significant bits, truncated) of a double, by bit operations: no FP64
+// instruction. |result - x| < 2^-23 |x|; zero and subnormals give zero, magnitudes above the
+// float range give +-inf.
+__device__ __forceinline__ float fe_trunc_float(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    int e = (int)((hi >> 20) & 0x7FF) - 1023;
+    if (e < -126) return 0.0f;
+    if (e > 127) return __uint_as_float((hi & 0x80000000u) | 0x7F800000u);
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned)(e + 127) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
 
 // Row-owner assembly of S and M for batches of meshes (rowasm.cu): per-mesh arrays, tiles of
 // rows, and the list of general rows as (mesh, row).

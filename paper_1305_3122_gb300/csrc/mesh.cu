@@ -9,6 +9,8 @@
 
 static std::atomic<uint64_t> g_topology_counter{1};
 
+uint64_t fe_next_topology_id() { return g_topology_counter.fetch_add(1); }
+
 // q [2][nq] (x row, y row) -> q2 [nq] (x, y)
 __global__ void k_pack_coords(const double* __restrict__ q, int32_t nq, double2* __restrict__ q2) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x)
@@ -17,17 +19,6 @@ __global__ void k_pack_coords(const double* __restrict__ q, int32_t nq, double2*
 
 // Validation word layout: [0] = OR of error bits, [1] = first bad triangle (min), per kind.
 enum { BAD_RANGE = 1, BAD_REPEAT = 2, BAD_ORIENT = 4 };
-
-// High float (top 24 significant bits, truncated) of a double, by bit operations: no FP64
-// instruction. |result - x| < 2^-23 |x|; zero and subnormals give zero.
-__device__ __forceinline__ float trunc_float(double x) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-    int e = (int)((hi >> 20) & 0x7FF) - 1023;
-    if (e < -126) return 0.0f;
-    if (e > 127) return __uint_as_float((hi & 0x80000000u) | 0x7F800000u);   // +-inf: forces the exact path
-    return __uint_as_float((hi & 0x80000000u) | ((unsigned)(e + 127) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
-}
 
 // Every triangle: vertex ids in range, three distinct vertices, counter-clockwise. The sign of
 // D = (p1 - p0) x (p2 - p0) is first taken from truncated-float coordinates; the float result is
@@ -50,9 +41,9 @@ __global__ void k_validate(const double2* __restrict__ q, int32_t nq, const int3
                 bad = BAD_REPEAT;
             } else {
                 double2 p0 = q[v0], p1 = q[v1], p2 = q[v2];
-                float x0 = trunc_float(p0.x), y0 = trunc_float(p0.y);
-                float ax = trunc_float(p1.x) - x0, ay = trunc_float(p1.y) - y0;
-                float bx = trunc_float(p2.x) - x0, by = trunc_float(p2.y) - y0;
+                float x0 = fe_trunc_float(p0.x), y0 = fe_trunc_float(p0.y);
+                float ax = fe_trunc_float(p1.x) - x0, ay = fe_trunc_float(p1.y) - y0;
+                float bx = fe_trunc_float(p2.x) - x0, by = fe_trunc_float(p2.y) - y0;
                 float Df = ax * by - ay * bx;
                 float M = fmaxf(fmaxf(fmaxf(fabsf(x0), fabsf(y0)), fmaxf(fabsf(ax), fabsf(ay))),
                                 fmaxf(fabsf(bx), fabsf(by)));
@@ -133,7 +124,7 @@ extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, co
     m->last_stream = s;
     m->nq = nq;
     m->nme = nme;
-    m->topology_id = g_topology_counter.fetch_add(1);
+    m->topology_id = fe_next_topology_id();
     fe_status st = fe_alloc_n(&m->q, (size_t)nq, "mesh coordinates");
     if (borrow) {
         m->me = const_cast<int32_t*>(me);

@@ -1,0 +1,712 @@
+// tet.cu -- P1 tetrahedra (3-D): mesh handles, pattern build and the assembly of M, M^w and S.
+//
+// The paper states that its method extends to three dimensions and gives no formulas. The
+// element matrices follow the standard P1 integrals on a tetrahedron K with vertices p0..p3:
+// with edge vectors a = p1 - p0, b = p2 - p0, c = p3 - p0 and det = a . (b x c) = 6|K|, the
+// barycentric gradients are grad(phi_1) = (b x c)/det, grad(phi_2) = (c x a)/det,
+// grad(phi_3) = (a x b)/det, grad(phi_0) = -(their sum), and
+//   M^e_ab   = |K|/20 (1 + delta_ab)
+//   M^w_ab   = |K|/120 (2 W + 4 w_a) on the diagonal, |K|/120 (W + w_a + w_b) off it (W = sum w)
+//   S^e_ab   = |K| grad(phi_a) . grad(phi_b) = (g_a . g_b) / (6 det), g = the unnormalised gradients.
+//
+// Pattern (the structural half of sparse()): a counting sort by vertex drops, for each
+// tetrahedron k and each of its vertices a, the record (its three other vertices, 4k + a) into the
+// bucket of vertex me[a][k]. One warp per row then inserts the row's neighbour ids into a
+// shared-memory hash table (repeats merge; each slot counts its multiplicity), ranks the distinct
+// ids (their rank is the column's position in the sorted row), and writes, for every incidence,
+// the in-row positions of its four columns: the element-to-nnz map, row-major per element
+// (map[16k + 4 il + jl]), relative to the row start until the offsets are known. For the
+// deterministic gather variant the warp also writes each non-zero's contributions in ascending
+// element order: row i has exactly 4 * (its valence) contributions, so its part of the list starts
+// at 4 * vptr[i] before any offset is known.
+#include "internal.cuh"
+
+namespace {
+
+constexpr int TET_BLOCK = 256;
+constexpr int ROW_WARPS = 4;                 // warps per block in the row pass (fast rows)
+constexpr int FAST_TS = 256;                 // hash-table slots per warp, fast rows
+constexpr int FAST_EMAX = 64;                // fast rows: at most 64 tetrahedra (3 * 64 + 1 ids < 256)
+constexpr int BIG_TS = 4096;                 // one warp per block for rows up to FE_TET_MAX_VALENCE
+constexpr int BIG_EMAX = FE_TET_MAX_VALENCE;
+static_assert(3 * BIG_EMAX + 1 < BIG_TS, "the big-row table must hold every distinct id");
+static_assert(3 * FAST_EMAX + 1 < FAST_TS, "the fast-row table must hold every distinct id");
+
+enum { BAD_RANGE = 1, BAD_REPEAT = 2, BAD_ORIENT = 4 };
+
+__global__ void k_tet_pack(const double* __restrict__ q, int32_t nq, double4_32a* __restrict__ q4) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x)
+        q4[i] = make_double4_32a(q[i], q[nq + i], q[2 * (int64_t)nq + i], 0.0);
+}
+
+// Sign of det[p1-p0 | p2-p0 | p3-p0] > 0, first from truncated-float coordinates: each float
+// edge component is within delta = 2^-22 M + 2^-24 E of the exact one (M = largest |coordinate|,
+// E = largest |edge component|), which moves the determinant by at most 16 delta (E + delta)^2
+// (Hadamard's bound for each perturbed column), and the float evaluation errs by at most
+// 4 * 2^-24 times the sum of the six |products| <= 6 E^3. When |det_f| exceeds both the sign is
+// certain; otherwise (or out of the float range) the determinant is recomputed in FP64.
+__device__ __forceinline__ bool tet_positive(double4_32a p0, double4_32a p1, double4_32a p2, double4_32a p3) {
+    const float x0 = fe_trunc_float(p0.x), y0 = fe_trunc_float(p0.y), z0 = fe_trunc_float(p0.z);
+    const float x1 = fe_trunc_float(p1.x), y1 = fe_trunc_float(p1.y), z1 = fe_trunc_float(p1.z);
+    const float x2 = fe_trunc_float(p2.x), y2 = fe_trunc_float(p2.y), z2 = fe_trunc_float(p2.z);
+    const float x3 = fe_trunc_float(p3.x), y3 = fe_trunc_float(p3.y), z3 = fe_trunc_float(p3.z);
+    const float ax = x1 - x0, ay = y1 - y0, az = z1 - z0;
+    const float bx = x2 - x0, by = y2 - y0, bz = z2 - z0;
+    const float cx = x3 - x0, cy = y3 - y0, cz = z3 - z0;
+    const float det = ax * (by * cz - bz * cy) - ay * (bx * cz - bz * cx) + az * (bx * cy - by * cx);
+    float M = fmaxf(fmaxf(fmaxf(fabsf(x0), fabsf(y0)), fmaxf(fabsf(z0), fabsf(x1))),
+                    fmaxf(fmaxf(fabsf(y1), fabsf(z1)), fmaxf(fabsf(x2), fabsf(y2))));
+    M = fmaxf(M, fmaxf(fmaxf(fabsf(z2), fabsf(x3)), fmaxf(fabsf(y3), fabsf(z3))));
+    float E = fmaxf(fmaxf(fmaxf(fabsf(ax), fabsf(ay)), fmaxf(fabsf(az), fabsf(bx))),
+                    fmaxf(fmaxf(fabsf(by), fabsf(bz)), fmaxf(fabsf(cx), fabsf(cy))));
+    E = fmaxf(E, fabsf(cz));
+    const float delta = 2.4e-7f * M + 6.0e-8f * E;
+    const float err = 2.9e-6f * E * E * E + 16.0f * delta * (E + delta) * (E + delta);
+    if (fabsf(det) > err && E < 1e12f && E > 1e-10f && M < 1e30f) return det > 0.0f;
+    const double dax = p1.x - p0.x, day = p1.y - p0.y, daz = p1.z - p0.z;
+    const double dbx = p2.x - p0.x, dby = p2.y - p0.y, dbz = p2.z - p0.z;
+    const double dcx = p3.x - p0.x, dcy = p3.y - p0.y, dcz = p3.z - p0.z;
+    return dax * (dby * dcz - dbz * dcy) - day * (dbx * dcz - dbz * dcx) + daz * (dbx * dcy - dby * dcx) > 0.0;
+}
+
+// Range, repeats and orientation of every tetrahedron; counts each vertex's tetrahedra.
+__global__ void k_tet_validate(const double4_32a* __restrict__ q, int32_t nq, const int32_t* __restrict__ me,
+                               int32_t nme, int* __restrict__ word, int32_t* __restrict__ deg) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v[4];
+#pragma unroll
+        for (int a = 0; a < 4; a++) v[a] = me[a * (int64_t)nme + k];
+        int bad = 0;
+        bool in = true;
+#pragma unroll
+        for (int a = 0; a < 4; a++) in &= v[a] >= 0 && v[a] < nq;
+        if (!in) {
+            bad = BAD_RANGE;
+        } else {
+#pragma unroll
+            for (int a = 0; a < 4; a++) atomicAdd(&deg[v[a]], 1);
+            if (v[0] == v[1] || v[0] == v[2] || v[0] == v[3] || v[1] == v[2] || v[1] == v[3] || v[2] == v[3])
+                bad = BAD_REPEAT;
+            else if (!tet_positive(q[v[0]], q[v[1]], q[v[2]], q[v[3]]))
+                bad = BAD_ORIENT;
+        }
+        if (bad) {
+            atomicOr(&word[0], bad);
+            atomicMin(&word[bad == BAD_RANGE ? 1 : bad == BAD_REPEAT ? 2 : 3], (int)k);
+        }
+    }
+}
+
+// Bucket records: for tetrahedron k and vertex a, (v[a+1], v[a+2], v[a+3], 4k + a) (indices mod 4)
+// into the bucket of v[a]; the cursors start at the bucket starts.
+__global__ void k_tet_fill(const int32_t* __restrict__ me, int32_t nme, int32_t* __restrict__ cur,
+                           int4* __restrict__ adj) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v[4];
+#pragma unroll
+        for (int a = 0; a < 4; a++) v[a] = me[a * (int64_t)nme + k];
+        int32_t slot[4];
+#pragma unroll
+        for (int a = 0; a < 4; a++) slot[a] = atomicAdd(&cur[v[a]], 1);
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+            adj[slot[a]] = make_int4(v[(a + 1) & 3], v[(a + 2) & 3], v[(a + 3) & 3], 4 * (int32_t)k + a);
+    }
+}
+
+// Per-warp shared memory of the row pass for a table of TS slots and at most EMAX incidences.
+template <int TS, int EMAX>
+struct RowSmem {
+    int32_t tab[TS];     // ids (-1: empty)
+    int32_t mult[TS];    // multiplicity of each id (incidences that touch the column), then a running count
+    int32_t rnk[TS];     // rank (column position) of each slot's id
+    int32_t uid[TS];     // the distinct ids, in insertion order
+    int32_t uslot[TS];   // their slots
+    int32_t cum[TS];     // by rank: multiplicities, then their exclusive prefix (gather lists)
+    int4 e[EMAX];        // the row's bucket records
+    int32_t ord[EMAX];   // incidences in ascending element order
+    int32_t ucount;
+};
+
+__device__ __forceinline__ uint32_t tet_hash(int32_t id) { return (uint32_t)id * 0x9E3779B1u; }
+
+// Slot of id (inserted if absent); *fresh tells whether this call inserted it. The table always
+// has a free slot (TS > the row's distinct ids), so the probe ends within TS steps.
+template <int TS>
+__device__ __forceinline__ int tab_insert(int32_t* tab, int32_t id, bool* fresh) {
+    constexpr int SH = 32 - (TS == 256 ? 8 : 12);
+    static_assert(TS == 256 || TS == 4096, "table sizes");
+    int s = (int)(tet_hash(id) >> SH);
+    for (int step = 0; step < TS; step++) {
+        int32_t old = atomicCAS(&tab[s], -1, id);
+        if (old == -1) { *fresh = true; return s; }
+        if (old == id) { *fresh = false; return s; }
+        s = (s + 1) & (TS - 1);
+    }
+    *fresh = false;
+    return 0;    // not reached: the table is never full
+}
+
+template <int TS>
+__device__ __forceinline__ int tab_find(const int32_t* tab, int32_t id) {
+    constexpr int SH = 32 - (TS == 256 ? 8 : 12);
+    int s = (int)(tet_hash(id) >> SH);
+    for (int step = 0; step < TS; step++) {
+        if (tab[s] == id) return s;
+        s = (s + 1) & (TS - 1);
+    }
+    return 0;    // not reached: every id looked up was inserted
+}
+
+// One row by one warp: distinct columns (sorted, into tmp at 3 vptr[i] + i), their count, the
+// relative map of every incidence, and (GATHER) the within-row segment starts (into tmp2) and the
+// contribution lists (into perm at 4 vptr[i]).
+template <int TS, int EMAX, bool GATHER>
+__device__ void tet_row(int32_t i, int32_t beg, int32_t d, const int4* __restrict__ adj, RowSmem<TS, EMAX>& sm,
+                        int32_t* __restrict__ tmp, int32_t* __restrict__ tmp2, int32_t* __restrict__ cnt,
+                        int32_t* __restrict__ map, int32_t* __restrict__ perm) {
+    const int lane = threadIdx.x & 31;
+    for (int s = lane; s < TS; s += 32) {
+        sm.tab[s] = -1;
+        sm.mult[s] = 0;
+    }
+    if (lane == 0) sm.ucount = 0;
+    for (int t = lane; t < d; t += 32) sm.e[t] = adj[beg + t];
+    __syncwarp();
+    // every incidence contributes the row's own vertex and its three other vertices
+    for (int x = lane; x < 4 * d; x += 32) {
+        const int4 r = sm.e[x >> 2];
+        const int q = x & 3;
+        const int32_t id = q == 0 ? i : q == 1 ? r.x : q == 2 ? r.y : r.z;
+        bool fresh;
+        const int s = tab_insert<TS>(sm.tab, id, &fresh);
+        atomicAdd(&sm.mult[s], 1);
+        if (fresh) {
+            const int p = atomicAdd(&sm.ucount, 1);
+            sm.uid[p] = id;
+            sm.uslot[p] = s;
+        }
+    }
+    __syncwarp();
+    const int u = sm.ucount;
+    const int64_t tb = 3 * (int64_t)beg + i;
+    for (int p = lane; p < u; p += 32) {
+        const int32_t id = sm.uid[p];
+        int r = 0;
+        for (int qq = 0; qq < u; qq++) r += sm.uid[qq] < id;
+        sm.rnk[sm.uslot[p]] = r;
+        tmp[tb + r] = id;
+        if (GATHER) sm.cum[r] = sm.mult[sm.uslot[p]];
+    }
+    __syncwarp();
+    // relative map: the four column positions of each incidence, one 16-byte store
+    for (int t = lane; t < d; t += 32) {
+        const int4 r = sm.e[t];
+        const int a = r.w & 3;
+        const int32_t k = r.w >> 2;
+        const int ri = sm.rnk[tab_find<TS>(sm.tab, i)];
+        const int rx = sm.rnk[tab_find<TS>(sm.tab, r.x)];
+        const int ry = sm.rnk[tab_find<TS>(sm.tab, r.y)];
+        const int rz = sm.rnk[tab_find<TS>(sm.tab, r.z)];
+        int o[4];
+#pragma unroll
+        for (int jl = 0; jl < 4; jl++) {
+            const int off = (jl - a) & 3;     // 0: the row's vertex, 1..3: the record's x, y, z
+            o[jl] = off == 0 ? ri : off == 1 ? rx : off == 2 ? ry : rz;
+        }
+        *reinterpret_cast<int4*>(map + 16 * (int64_t)k + 4 * a) = make_int4(o[0], o[1], o[2], o[3]);
+    }
+    if (GATHER) {
+        // exclusive prefix of the multiplicities by rank: the start of each column's list
+        int32_t run = 0;
+        for (int base = 0; base < u; base += 32) {
+            const int r = base + lane;
+            const int32_t v = r < u ? sm.cum[r] : 0;
+            int32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (r < u) {
+                sm.cum[r] = run + incl - v;
+                tmp2[tb + r] = run + incl - v;
+            }
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        // incidences in ascending element order (the keys 4k + a are distinct within a row)
+        for (int t = lane; t < d; t += 32) {
+            const int32_t key = sm.e[t].w;
+            int r = 0;
+            for (int tt = 0; tt < d; tt++) r += sm.e[tt].w < key;
+            sm.ord[r] = t;
+        }
+        for (int s = lane; s < TS; s += 32) sm.mult[s] = 0;
+        __syncwarp();
+        // walk them in that order; lanes 0..3 place the incidence's four contributions (distinct
+        // columns, so no two lanes share a counter)
+        for (int s = 0; s < d; s++) {
+            if (lane < 4) {
+                const int4 r = sm.e[sm.ord[s]];
+                const int a = r.w & 3;
+                const int32_t k = r.w >> 2;
+                const int32_t id = lane == 0 ? i : lane == 1 ? r.x : lane == 2 ? r.y : r.z;
+                const int slot = tab_find<TS>(sm.tab, id);
+                const int pos = sm.cum[sm.rnk[slot]] + sm.mult[slot];
+                sm.mult[slot] += 1;
+                const int jl = (a + lane) & 3;
+                perm[4 * (int64_t)beg + pos] = 16 * k + 4 * a + jl;
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0) cnt[i] = u;
+    __syncwarp();
+}
+
+// Rows with at most FAST_EMAX tetrahedra, one warp each; longer rows are listed for k_tet_rows_big.
+template <bool GATHER>
+__global__ void __launch_bounds__(ROW_WARPS * 32) k_tet_rows(const int32_t* __restrict__ vptr, const int4* __restrict__ adj,
+                                                            int32_t nq, int32_t* __restrict__ tmp, int32_t* __restrict__ tmp2,
+                                                            int32_t* __restrict__ cnt, int32_t* __restrict__ map,
+                                                            int32_t* __restrict__ perm, int32_t* __restrict__ big_list,
+                                                            int32_t* __restrict__ big_count) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RowSmem<FAST_TS, FAST_EMAX>& sm = reinterpret_cast<RowSmem<FAST_TS, FAST_EMAX>*>(smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * ROW_WARPS;
+    for (int64_t r = (int64_t)blockIdx.x * ROW_WARPS + (threadIdx.x >> 5); r < nq; r += nwarps) {
+        const int32_t i = (int32_t)r;
+        const int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+        if (d == 0) {
+            if (lane == 0) cnt[i] = 0;
+            continue;
+        }
+        if (d > FAST_EMAX) {
+            if (lane == 0) big_list[atomicAdd(big_count, 1)] = i;
+            continue;
+        }
+        tet_row<FAST_TS, FAST_EMAX, GATHER>(i, beg, d, adj, sm, tmp, tmp2, cnt, map, perm);
+    }
+}
+
+template <bool GATHER>
+__global__ void __launch_bounds__(32) k_tet_rows_big(const int32_t* __restrict__ vptr, const int4* __restrict__ adj,
+                                                     const int32_t* __restrict__ big_list,
+                                                     const int32_t* __restrict__ big_count, int32_t* __restrict__ tmp,
+                                                     int32_t* __restrict__ tmp2, int32_t* __restrict__ cnt,
+                                                     int32_t* __restrict__ map, int32_t* __restrict__ perm,
+                                                     int* __restrict__ too_big) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RowSmem<BIG_TS, BIG_EMAX>& sm = *reinterpret_cast<RowSmem<BIG_TS, BIG_EMAX>*>(smem_raw);
+    const int32_t n = *big_count;
+    for (int32_t b = blockIdx.x; b < n; b += gridDim.x) {
+        const int32_t i = big_list[b];
+        const int32_t beg = vptr[i], d = vptr[i + 1] - beg;
+        if (d > BIG_EMAX) {
+            if (threadIdx.x == 0) {
+                *too_big = 1;
+                cnt[i] = 0;
+            }
+            continue;
+        }
+        tet_row<BIG_TS, BIG_EMAX, GATHER>(i, beg, d, adj, sm, tmp, tmp2, cnt, map, perm);
+    }
+}
+
+// Columns (and segment starts) into their final places, one warp per row.
+template <bool GATHER>
+__global__ void __launch_bounds__(TET_BLOCK) k_tet_cols(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
+                                                        int32_t nq, const int32_t* __restrict__ tmp,
+                                                        const int32_t* __restrict__ tmp2, int32_t* __restrict__ col_idx,
+                                                        int32_t* __restrict__ seg_ptr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (TET_BLOCK / 32);
+    for (int64_t r = (int64_t)blockIdx.x * (TET_BLOCK / 32) + (threadIdx.x >> 5); r < nq; r += nwarps) {
+        const int32_t i = (int32_t)r;
+        const int32_t rb = row_ptr[i], u = row_ptr[i + 1] - rb;
+        const int32_t beg = vptr[i];
+        const int64_t tb = 3 * (int64_t)beg + i;
+        for (int c = lane; c < u; c += 32) {
+            col_idx[rb + c] = tmp[tb + c];
+            if (GATHER) seg_ptr[rb + c] = 4 * beg + tmp2[tb + c];
+        }
+    }
+}
+
+// map[16k + 4 il + jl] += row_ptr[me[il][k]]: relative positions become absolute.
+__global__ void k_tet_map_base(const int32_t* __restrict__ me, int32_t nme, const int32_t* __restrict__ row_ptr,
+                               int32_t* __restrict__ map) {
+    const int64_t n = 16 * (int64_t)nme;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = c >> 4;
+        const int il = (int)(c >> 2) & 3;
+        map[c] += row_ptr[me[il * (int64_t)nme + k]];
+    }
+}
+
+__global__ void k_tet_set_last(int32_t* seg_ptr, int64_t nnz, int32_t v) { seg_ptr[nnz] = v; }
+
+// ------------------------------------------------------------------ element matrices
+
+template <int KIND>
+__device__ __forceinline__ void tet_elem(const double4_32a p[4], const double w[4], double E[4][4]) {
+    const double ax = p[1].x - p[0].x, ay = p[1].y - p[0].y, az = p[1].z - p[0].z;
+    const double bx = p[2].x - p[0].x, by = p[2].y - p[0].y, bz = p[2].z - p[0].z;
+    const double cx = p[3].x - p[0].x, cy = p[3].y - p[0].y, cz = p[3].z - p[0].z;
+    // unnormalised gradients g_1 = b x c, g_2 = c x a, g_3 = a x b
+    double g[4][3];
+    g[1][0] = by * cz - bz * cy; g[1][1] = bz * cx - bx * cz; g[1][2] = bx * cy - by * cx;
+    g[2][0] = cy * az - cz * ay; g[2][1] = cz * ax - cx * az; g[2][2] = cx * ay - cy * ax;
+    g[3][0] = ay * bz - az * by; g[3][1] = az * bx - ax * bz; g[3][2] = ax * by - ay * bx;
+    const double det = ax * g[1][0] + ay * g[1][1] + az * g[1][2];   // a . (b x c) = 6|K|
+    if (KIND == FE_TET_STIFF) {
+#pragma unroll
+        for (int t = 0; t < 3; t++) g[0][t] = -(g[1][t] + g[2][t] + g[3][t]);
+        const double s = 1.0 / (6.0 * det);
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = a; b < 4; b++) {
+                const double v = (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]) * s;
+                E[a][b] = v;
+                E[b][a] = v;
+            }
+    } else if (KIND == FE_TET_MASS) {
+        const double m = det / 120.0;                 // |K| / 20
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) E[a][b] = a == b ? 2.0 * m : m;
+    } else {
+        const double m = det / 720.0;                 // |K| / 120
+        const double W = w[0] + w[1] + w[2] + w[3];
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) E[a][b] = a == b ? m * (2.0 * W + 4.0 * w[a]) : m * (W + w[a] + w[b]);
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ void tet_load(const int32_t* __restrict__ me, int32_t nme, int64_t k, const double4_32a* __restrict__ q,
+                                         const double* __restrict__ w, double4_32a p[4], double wl[4]) {
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+        const int32_t v = me[a * (int64_t)nme + k];
+        p[a] = q[v];
+        wl[a] = KIND == FE_TET_WMASS ? w[v] : 0.0;
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(TET_BLOCK) k_tet_atomic(const int32_t* __restrict__ me, int32_t nme, const double4_32a* __restrict__ q,
+                                                          const double* __restrict__ w, const int32_t* __restrict__ map,
+                                                          double* __restrict__ val) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
+        double4_32a p[4];
+        double wl[4], E[4][4];
+        tet_load<KIND>(me, nme, k, q, w, p, wl);
+        tet_elem<KIND>(p, wl, E);
+        const int4* m4 = reinterpret_cast<const int4*>(map + 16 * k);
+#pragma unroll
+        for (int il = 0; il < 4; il++) {
+            const int4 m = m4[il];
+            atomicAdd(&val[m.x], E[il][0]);
+            atomicAdd(&val[m.y], E[il][1]);
+            atomicAdd(&val[m.z], E[il][2]);
+            atomicAdd(&val[m.w], E[il][3]);
+        }
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(TET_BLOCK) k_tet_stage(const int32_t* __restrict__ me, int32_t nme, const double4_32a* __restrict__ q,
+                                                         const double* __restrict__ w, double* __restrict__ kg) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
+        double4_32a p[4];
+        double wl[4], E[4][4];
+        tet_load<KIND>(me, nme, k, q, w, p, wl);
+        tet_elem<KIND>(p, wl, E);
+        double2* o = reinterpret_cast<double2*>(kg + 16 * k);
+#pragma unroll
+        for (int il = 0; il < 4; il++) {
+            o[2 * il] = make_double2(E[il][0], E[il][1]);
+            o[2 * il + 1] = make_double2(E[il][2], E[il][3]);
+        }
+    }
+}
+
+// Each non-zero sums its staged contributions in ascending element order.
+__global__ void __launch_bounds__(TET_BLOCK) k_tet_gather(const int32_t* __restrict__ seg_ptr, const int32_t* __restrict__ perm,
+                                                          const double* __restrict__ kg, int64_t nnz,
+                                                          double* __restrict__ val) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int32_t t = seg_ptr[p]; t < seg_ptr[p + 1]; t++) s += kg[perm[t]];
+        val[p] = s;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handles
+
+extern "C" void fe_tet_mesh_destroy(fe_tet_mesh m) {
+    if (!m) return;
+    FeStreamScope scope(m->last_stream);
+    fe_free(m->q);
+    if (m->me_owned) fe_free(m->me);
+    fe_free(m->err);
+    fe_free(m->deg);
+    delete m;
+}
+
+extern "C" fe_status fe_tet_mesh_create(int32_t nq, int32_t nme, const double* q, const int32_t* me, int ptr_kind,
+                                        fe_stream stream, fe_tet_mesh* out) {
+    if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (nq < 0 || nme < 0) return fe_fail(FE_ERR_INVALID_ARG, "nq and nme must be >= 0");
+    if ((nq > 0 && !q) || (nme > 0 && !me)) return fe_fail(FE_ERR_INVALID_ARG, "q or me is null");
+    if (ptr_kind != FE_PTR_HOST && ptr_kind != FE_PTR_DEVICE && ptr_kind != FE_PTR_DEVICE_BORROW)
+        return fe_fail(FE_ERR_INVALID_ARG, "bad ptr_kind");
+    if (16 * (int64_t)nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "16*nme must be < 2^31");
+    const bool borrow = ptr_kind == FE_PTR_DEVICE_BORROW;
+    const cudaMemcpyKind dir = ptr_kind == FE_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaStream_t s = (cudaStream_t)stream;
+    FeStreamScope scope(s);
+    fe_tet_mesh m = new fe_tet_mesh_s();
+    m->last_stream = s;
+    m->nq = nq;
+    m->nme = nme;
+    m->topology_id = fe_next_topology_id();
+    double* qtmp = nullptr;
+    fe_status st = fe_alloc_n(&m->q, (size_t)nq, "tetrahedral mesh coordinates");
+    if (!st) st = fe_alloc_n(&m->err, 4, "mesh error word");
+    if (!st) st = fe_alloc_n(&m->deg, (size_t)nq + 1, "vertex valences");
+    if (!st && borrow) {
+        m->me = const_cast<int32_t*>(me);
+        m->me_owned = false;
+    } else if (!st) {
+        st = fe_alloc_n(&m->me, 4 * (size_t)nme, "tetrahedral mesh connectivity");
+        if (!st && nme > 0 && cudaMemcpyAsync(m->me, me, 16 * (size_t)nme, dir, s) != cudaSuccess)
+            st = fe_fail(FE_ERR_CUDA, "copy of me");
+    }
+    const double* qd = q;
+    if (!st && nq > 0 && ptr_kind == FE_PTR_HOST) {
+        st = fe_alloc_n(&qtmp, 3 * (size_t)nq, "coordinate staging");
+        if (!st && cudaMemcpyAsync(qtmp, q, 24 * (size_t)nq, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            st = fe_fail(FE_ERR_CUDA, "copy of q");
+        qd = qtmp;
+    }
+    if (st) { fe_free(qtmp); fe_tet_mesh_destroy(m); return st; }
+    int word[4];
+    cudaError_t e = cudaSuccess;
+    if (nq > 0) {
+        { FE_PROF("k_tet_pack", s); k_tet_pack<<<fe_grid(nq, TET_BLOCK), TET_BLOCK, 0, s>>>(qd, nq, m->q); }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->err + 1, 0x7F, 3 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->deg, 0, sizeof(int32_t) * ((size_t)nq + 1), s);
+    if (e == cudaSuccess && nme > 0) {
+        { FE_PROF("k_tet_validate", s); k_tet_validate<<<fe_grid(nme, TET_BLOCK, 16), TET_BLOCK, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg); }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(word, m->err, sizeof word, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    fe_free(qtmp);
+    if (e != cudaSuccess) { fe_tet_mesh_destroy(m); return fe_cuda_fail(e, "tetrahedral mesh validation"); }
+    if (word[0] & BAD_RANGE) {
+        fe_tet_mesh_destroy(m);
+        return fe_fail(FE_ERR_INDEX_RANGE, "tetrahedron " + std::to_string(word[1]) + " has a vertex id outside [0, nq)");
+    }
+    if (word[0] & BAD_REPEAT) {
+        fe_tet_mesh_destroy(m);
+        return fe_fail(FE_ERR_DEGENERATE, "tetrahedron " + std::to_string(word[2]) + " repeats a vertex");
+    }
+    if (word[0] & BAD_ORIENT) {
+        fe_tet_mesh_destroy(m);
+        return fe_fail(FE_ERR_ORIENTATION, "tetrahedron " + std::to_string(word[3]) +
+                                               " has det[p1-p0 | p2-p0 | p3-p0] <= 0");
+    }
+    *out = m;
+    return FE_OK;
+}
+
+extern "C" void fe_tet_pattern_destroy(fe_tet_pattern p) {
+    if (!p) return;
+    FeStreamScope scope(p->last_stream);
+    fe_free(p->row_ptr); fe_free(p->col_idx); fe_free(p->map);
+    fe_free(p->seg_ptr); fe_free(p->perm); fe_free(p->kg);
+    delete p;
+}
+
+namespace {
+struct TetTemps {
+    int32_t *vptr = nullptr, *cur = nullptr, *cnt = nullptr, *tmp = nullptr, *tmp2 = nullptr;
+    int32_t *big = nullptr, *counters = nullptr;
+    int4* adj = nullptr;
+    ~TetTemps() {
+        fe_free(vptr); fe_free(cur); fe_free(cnt); fe_free(tmp); fe_free(tmp2);
+        fe_free(big); fe_free(counters); fe_free(adj);
+    }
+};
+
+template <bool GATHER>
+fe_status tet_rows(const TetTemps& t, int32_t nq, fe_tet_pattern p, cudaStream_t s) {
+    const size_t fast_smem = ROW_WARPS * sizeof(RowSmem<FAST_TS, FAST_EMAX>);
+    const size_t big_smem = sizeof(RowSmem<BIG_TS, BIG_EMAX>);
+    FE_CUDA(cudaFuncSetAttribute(k_tet_rows<GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast_smem));
+    FE_CUDA(cudaFuncSetAttribute(k_tet_rows_big<GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem));
+    { FE_PROF("k_tet_rows", s); k_tet_rows<GATHER><<<fe_grid(((int64_t)nq + ROW_WARPS - 1) / ROW_WARPS, 1, 8), ROW_WARPS * 32, fast_smem, s>>>(
+          t.vptr, t.adj, nq, t.tmp, t.tmp2, t.cnt, p->map, p->perm, t.big, t.counters); }
+    FE_LAUNCHED("k_tet_rows");
+    { FE_PROF("k_tet_rows_big", s); k_tet_rows_big<GATHER><<<fe_sm_count(), 32, big_smem, s>>>(
+          t.vptr, t.adj, t.big, t.counters, t.tmp, t.tmp2, t.cnt, p->map, p->perm, t.counters + 1); }
+    FE_LAUNCHED("k_tet_rows_big");
+    return FE_OK;
+}
+}  // namespace
+
+extern "C" fe_status fe_tet_pattern_build(fe_tet_mesh m, int flags, fe_stream stream, fe_tet_pattern* out) {
+    if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");
+    const bool gather = (flags & FE_PATTERN_GATHER) != 0;
+    const int32_t nq = m->nq, nme = m->nme;
+    const int64_t n4 = 4 * (int64_t)nme;
+    cudaStream_t s = (cudaStream_t)stream;
+    FeStreamScope scope(s);
+    fe_tet_pattern p = new fe_tet_pattern_s();
+    p->flags = gather ? FE_PATTERN_GATHER : 0;
+    p->nq = nq;
+    p->nme = nme;
+    p->topology_id = m->topology_id;
+    p->last_stream = s;
+    m->last_stream = s;
+    TetTemps t;
+    auto fail = [&](fe_status st) {
+        cudaStreamSynchronize(s);
+        fe_tet_pattern_destroy(p);
+        return st;
+    };
+    fe_status st;
+    const int64_t tcap = 3 * n4 + nq;            // sum over rows of 3 d + 1
+    if ((st = fe_alloc_n(&t.vptr, (size_t)nq + 1, "vertex pointers"))) return fail(st);
+    if ((st = fe_alloc_n(&t.cur, (size_t)nq + 1, "bucket cursors"))) return fail(st);
+    if ((st = fe_exclusive_scan(m->deg, t.vptr, nq, s, nullptr, 1, t.cur))) return fail(st);
+    if ((st = fe_alloc_n(&t.adj, (size_t)n4, "row buckets"))) return fail(st);
+    if (nme > 0) {
+        { FE_PROF("k_tet_fill", s); k_tet_fill<<<fe_grid(nme, TET_BLOCK, 16), TET_BLOCK, 0, s>>>(m->me, nme, t.cur, t.adj); }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(fe_cuda_fail(e, "k_tet_fill"));
+    }
+    if ((st = fe_alloc_n(&t.cnt, (size_t)nq + 1, "row counts"))) return fail(st);
+    if ((st = fe_alloc_n(&t.tmp, (size_t)tcap, "row columns"))) return fail(st);
+    if (gather && (st = fe_alloc_n(&t.tmp2, (size_t)tcap, "row segment starts"))) return fail(st);
+    if ((st = fe_alloc_n(&t.big, (size_t)nq + 1, "long rows"))) return fail(st);
+    if ((st = fe_alloc_n(&t.counters, 4, "counters"))) return fail(st);
+    if ((st = fe_alloc_n(&p->map, 16 * (size_t)nme, "element-to-nnz map"))) return fail(st);
+    if (gather && (st = fe_alloc_n(&p->perm, 16 * (size_t)nme, "contribution lists"))) return fail(st);
+    if (cudaMemsetAsync(t.counters, 0, 4 * sizeof(int32_t), s) != cudaSuccess) return fail(fe_fail(FE_ERR_CUDA, "memset"));
+    if (nq > 0) {
+        st = gather ? tet_rows<true>(t, nq, p, s) : tet_rows<false>(t, nq, p, s);
+        if (st) return fail(st);
+    }
+    if ((st = fe_alloc_n(&p->row_ptr, (size_t)nq + 1, "row_ptr"))) return fail(st);
+    int64_t nnz = 0;
+    if ((st = fe_exclusive_scan(t.cnt, p->row_ptr, nq, s, &nnz))) return fail(st);   // synchronises
+    int too_big = 0;
+    if (cudaMemcpyAsync(&too_big, t.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(fe_fail(FE_ERR_CUDA, "flag read-back"));
+    if (too_big)
+        return fail(fe_fail(FE_ERR_LIMIT, "a vertex belongs to more than FE_TET_MAX_VALENCE=" +
+                                              std::to_string(FE_TET_MAX_VALENCE) + " tetrahedra"));
+    p->nnz = nnz;
+    if ((st = fe_alloc_n(&p->col_idx, (size_t)nnz, "col_idx"))) return fail(st);
+    if (gather && (st = fe_alloc_n(&p->seg_ptr, (size_t)nnz + 1, "seg_ptr"))) return fail(st);
+    if (gather && (st = fe_alloc_n(&p->kg, 16 * (size_t)nme, "element value staging"))) return fail(st);
+    if (nq > 0) {
+        const unsigned g = fe_grid(((int64_t)nq + 7) / 8, 1, 8);
+        if (gather) {
+            { FE_PROF("k_tet_cols", s); k_tet_cols<true><<<g, TET_BLOCK, 0, s>>>(t.vptr, p->row_ptr, nq, t.tmp, t.tmp2, p->col_idx, p->seg_ptr); }
+        } else {
+            { FE_PROF("k_tet_cols", s); k_tet_cols<false><<<g, TET_BLOCK, 0, s>>>(t.vptr, p->row_ptr, nq, t.tmp, nullptr, p->col_idx, nullptr); }
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(fe_cuda_fail(e, "k_tet_cols"));
+    }
+    if (nme > 0) {
+        { FE_PROF("k_tet_map_base", s); k_tet_map_base<<<fe_grid(16 * (int64_t)nme, TET_BLOCK), TET_BLOCK, 0, s>>>(m->me, nme, p->row_ptr, p->map); }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(fe_cuda_fail(e, "k_tet_map_base"));
+    }
+    if (gather) {
+        { FE_PROF("k_tet_set_last", s); k_tet_set_last<<<1, 1, 0, s>>>(p->seg_ptr, nnz, 16 * nme); }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(fe_cuda_fail(e, "k_tet_set_last"));
+    }
+    *out = p;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_tet_pattern_info(fe_tet_pattern p, int64_t* n_rows, int64_t* nnz, const int32_t** row_ptr,
+                                         const int32_t** col_idx) {
+    if (!p) return fe_fail(FE_ERR_INVALID_ARG, "null pattern");
+    if (n_rows) *n_rows = p->nq;
+    if (nnz) *nnz = p->nnz;
+    if (row_ptr) *row_ptr = p->row_ptr;
+    if (col_idx) *col_idx = p->col_idx;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_tet_pattern_map(fe_tet_pattern p, const int32_t** map, int64_t* len) {
+    if (!p) return fe_fail(FE_ERR_INVALID_ARG, "null pattern");
+    if (map) *map = p->map;
+    if (len) *len = 16 * (int64_t)p->nme;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_tet_assemble(fe_tet_mesh m, fe_tet_pattern p, int kind, const double* w, int variant,
+                                     double* values, int64_t cap, fe_stream stream) {
+    if (!m || !p) return fe_fail(FE_ERR_INVALID_ARG, "null mesh or pattern");
+    if (m->topology_id != p->topology_id) return fe_fail(FE_ERR_INVALID_ARG, "the pattern was built for another mesh");
+    if (kind != FE_TET_MASS && kind != FE_TET_WMASS && kind != FE_TET_STIFF) return fe_fail(FE_ERR_INVALID_ARG, "unknown kind");
+    if (kind == FE_TET_WMASS && !w && m->nq > 0) return fe_fail(FE_ERR_INVALID_ARG, "w is null");
+    if (variant != FE_VARIANT_ATOMIC && variant != FE_VARIANT_GATHER)
+        return fe_fail(FE_ERR_INVALID_ARG, "tetrahedra take FE_VARIANT_ATOMIC or FE_VARIANT_GATHER");
+    if (variant == FE_VARIANT_GATHER && !(p->flags & FE_PATTERN_GATHER))
+        return fe_fail(FE_ERR_INVALID_ARG, "FE_VARIANT_GATHER needs a pattern built with FE_PATTERN_GATHER");
+    if (cap < p->nnz) return fe_fail(FE_ERR_BUFFER_TOO_SMALL, "cap is below nnz");
+    if (!values && p->nnz > 0) return fe_fail(FE_ERR_INVALID_ARG, "values is null");
+    cudaStream_t s = (cudaStream_t)stream;
+    FeStreamScope scope(s);
+    m->last_stream = s;
+    p->last_stream = s;
+    const int32_t nme = m->nme;
+    if (p->nnz == 0) return FE_OK;
+    const unsigned g = fe_grid(nme, TET_BLOCK, 8);
+    if (variant == FE_VARIANT_ATOMIC) {
+        FE_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * (size_t)p->nnz, s));
+        if (nme > 0) {
+            FE_PROF("k_tet_atomic", s);
+            if (kind == FE_TET_MASS) k_tet_atomic<FE_TET_MASS><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->map, values);
+            else if (kind == FE_TET_WMASS) k_tet_atomic<FE_TET_WMASS><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->map, values);
+            else k_tet_atomic<FE_TET_STIFF><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->map, values);
+        }
+        FE_LAUNCHED("k_tet_atomic");
+        return FE_OK;
+    }
+    if (nme > 0) {
+        FE_PROF("k_tet_stage", s);
+        if (kind == FE_TET_MASS) k_tet_stage<FE_TET_MASS><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->kg);
+        else if (kind == FE_TET_WMASS) k_tet_stage<FE_TET_WMASS><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->kg);
+        else k_tet_stage<FE_TET_STIFF><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->kg);
+    }
+    FE_LAUNCHED("k_tet_stage");
+    { FE_PROF("k_tet_gather", s); k_tet_gather<<<fe_grid(p->nnz, TET_BLOCK, 8), TET_BLOCK, 0, s>>>(p->seg_ptr, p->perm, p->kg, p->nnz, values); }
+    FE_LAUNCHED("k_tet_gather");
+    return FE_OK;
+}

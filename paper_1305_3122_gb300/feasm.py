@@ -48,6 +48,13 @@ SIGNATURES = {
     "fe_assemble_stiff_wmass_noalloc": (_INT, [_P, _P, _P, _P, _P, _I64, _P]),
     "fe_adjoint_stiff_wmass": (_INT, [_P, _P, _P, _P, _P, _INT, _P, _P, _P]),
     "fe_csr_drop_zeros": (_INT, [_I64, _P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
+    "fe_tet_mesh_create": (_INT, [_I32, _I32, _P, _P, _INT, _P, ctypes.POINTER(_P)]),
+    "fe_tet_mesh_destroy": (None, [_P]),
+    "fe_tet_pattern_build": (_INT, [_P, _INT, _P, ctypes.POINTER(_P)]),
+    "fe_tet_pattern_info": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "fe_tet_pattern_map": (_INT, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
+    "fe_tet_pattern_destroy": (None, [_P]),
+    "fe_tet_assemble": (_INT, [_P, _P, _INT, _P, _INT, _P, _I64, _P]),
     "fe_assemble_stiff_wmass_host": (_INT, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "fe_batch_create": (_INT, [_I32, _P, _P, ctypes.POINTER(_P)]),
     "fe_batch_tune": (_INT, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
@@ -233,6 +240,98 @@ class Pattern:
 def _values(pattern: Pattern, out: torch.Tensor | None) -> torch.Tensor:
     out = pattern.new_values() if out is None else out
     _dptr(out, torch.float64, "values")
+    return out
+
+
+TET_MASS, TET_WMASS, TET_STIFF = 0, 1, 2
+
+
+class TetMesh:
+    """A tetrahedral mesh: q [3, nq] float64 and me [4, nme] int32 (0-based, positive volume
+    det[p1-p0 | p2-p0 | p3-p0] > 0). Inputs as for Mesh (CUDA tensors, CPU tensors or numpy)."""
+
+    def __init__(self, q, me, stream=None, borrow: bool = False):
+        L = lib()
+        self._h = None
+        self._me_ref = None
+        if isinstance(q, torch.Tensor) and q.is_cuda:
+            qd, med = q.contiguous(), me.contiguous()
+            kind = PTR_DEVICE_BORROW if borrow else PTR_DEVICE
+            if borrow:
+                self._me_ref = med
+            qp, mp = _dptr(qd, torch.float64, "q"), _dptr(med, torch.int32, "me")
+        else:
+            qd = np.ascontiguousarray(q.cpu().numpy() if isinstance(q, torch.Tensor) else q, dtype=np.float64)
+            med = np.ascontiguousarray(me.cpu().numpy() if isinstance(me, torch.Tensor) else me, dtype=np.int32)
+            kind = PTR_HOST
+            qp, mp = qd.ctypes.data, med.ctypes.data
+        if qd.shape[0] != 3 or med.shape[0] != 4:
+            raise ValueError("q must be [3, nq] and me must be [4, nme]")
+        self.nq, self.nme = int(qd.shape[1]), int(med.shape[1])
+        h = _P()
+        _check(L.fe_tet_mesh_create(self.nq, self.nme, qp, mp, kind, _stream(stream), ctypes.byref(h)),
+               "fe_tet_mesh_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fe_tet_mesh_destroy(self._h)
+        self._h = None
+        self._me_ref = None
+
+    def __del__(self):
+        self.close()
+
+
+class TetPattern:
+    """CSR structure and element-to-nnz map (map[16k + 4 il + jl]) of a tetrahedral mesh."""
+
+    def __init__(self, mesh: TetMesh, gather: bool = False, stream=None):
+        h = _P()
+        _check(lib().fe_tet_pattern_build(mesh.handle, PATTERN_GATHER if gather else 0, _stream(stream), ctypes.byref(h)),
+               "fe_tet_pattern_build")
+        self._h = h
+        self.mesh = mesh
+        self.gather = gather
+        n_rows, nnz, rp, ci = _I64(), _I64(), _P(), _P()
+        _check(lib().fe_tet_pattern_info(h, ctypes.byref(n_rows), ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci)),
+               "fe_tet_pattern_info")
+        self.n_rows, self.nnz = n_rows.value, nnz.value
+        self.row_ptr = _view_i32(rp.value, self.n_rows + 1, self)
+        self.col_idx = _view_i32(ci.value, self.nnz, self)
+        mp, ml = _P(), _I64()
+        _check(lib().fe_tet_pattern_map(h, ctypes.byref(mp), ctypes.byref(ml)), "fe_tet_pattern_map")
+        self.map = _view_i32(mp.value, ml.value, self)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def new_values(self) -> torch.Tensor:
+        return torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fe_tet_pattern_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def tet_assemble(mesh: TetMesh, pattern: TetPattern, kind: int, w: torch.Tensor | None = None, variant: int = ATOMIC,
+                 out=None, stream=None) -> torch.Tensor:
+    """Values of M (TET_MASS), M^w (TET_WMASS, w [nq] float64 CUDA) or S (TET_STIFF) of a
+    tetrahedral mesh on the pattern's CSR structure (fe_tet_assemble)."""
+    out = pattern.new_values() if out is None else out
+    if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 CUDA tensor")
+    _check(lib().fe_tet_assemble(mesh.handle, pattern.handle, kind, _dptr(w, torch.float64, "w"), variant,
+                                 out.data_ptr(), out.numel(), _stream(stream)), "fe_tet_assemble")
     return out
 
 
