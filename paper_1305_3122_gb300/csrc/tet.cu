@@ -118,13 +118,12 @@ __global__ void k_tet_fill(const int32_t* __restrict__ me, int32_t nme, int32_t*
 template <int TS, int EMAX>
 struct RowSmem {
     int32_t tab[TS];     // ids (-1: empty)
-    int32_t mult[TS];    // multiplicity of each id (incidences that touch the column), then a running count
+    int32_t mult[TS];    // multiplicity of each id (incidences that touch the column)
     int32_t rnk[TS];     // rank (column position) of each slot's id
     int32_t uid[TS];     // the distinct ids, in insertion order
     int32_t uslot[TS];   // their slots
     int32_t cum[TS];     // by rank: multiplicities, then their exclusive prefix (gather lists)
     int4 e[EMAX];        // the row's bucket records
-    int32_t ord[EMAX];   // incidences in ascending element order
     int32_t ucount;
 };
 
@@ -234,30 +233,31 @@ __device__ void tet_row(int32_t i, int32_t beg, int32_t d, const int4* __restric
             }
             run += __shfl_sync(0xffffffffu, incl, 31);
         }
-        // incidences in ascending element order (the keys 4k + a are distinct within a row)
-        for (int t = lane; t < d; t += 32) {
-            const int32_t key = sm.e[t].w;
-            int r = 0;
-            for (int tt = 0; tt < d; tt++) r += sm.e[tt].w < key;
-            sm.ord[r] = t;
-        }
-        for (int s = lane; s < TS; s += 32) sm.mult[s] = 0;
         __syncwarp();
-        // walk them in that order; lanes 0..3 place the incidence's four contributions (distinct
-        // columns, so no two lanes share a counter)
-        for (int s = 0; s < d; s++) {
-            if (lane < 4) {
-                const int4 r = sm.e[sm.ord[s]];
-                const int a = r.w & 3;
-                const int32_t k = r.w >> 2;
-                const int32_t id = lane == 0 ? i : lane == 1 ? r.x : lane == 2 ? r.y : r.z;
-                const int slot = tab_find<TS>(sm.tab, id);
-                const int pos = sm.cum[sm.rnk[slot]] + sm.mult[slot];
-                sm.mult[slot] += 1;
-                const int jl = (a + lane) & 3;
-                perm[4 * (int64_t)beg + pos] = 16 * k + 4 * a + jl;
+        // each incidence places its four contributions: a column's list is in ascending element
+        // order (keys 4k + a are distinct within a row), so the place is the column's start plus
+        // the number of earlier-element incidences that touch the column (every one touches the
+        // row's own vertex)
+        for (int t = lane; t < d; t += 32) {
+            const int4 r = sm.e[t];
+            const int32_t key = r.w;
+            int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+            for (int tt = 0; tt < d; tt++) {
+                const int4 o = sm.e[tt];
+                const int before = o.w < key;
+                c0 += before;
+                c1 += before & (o.x == r.x || o.y == r.x || o.z == r.x);
+                c2 += before & (o.x == r.y || o.y == r.y || o.z == r.y);
+                c3 += before & (o.x == r.z || o.y == r.z || o.z == r.z);
             }
-            __syncwarp();
+            const int a = r.w & 3;
+            const int32_t k = r.w >> 2;
+            int32_t* pr = perm + 4 * (int64_t)beg;
+            const int32_t base = 16 * k + 4 * a;
+            pr[sm.cum[sm.rnk[tab_find<TS>(sm.tab, i)]] + c0] = base + a;
+            pr[sm.cum[sm.rnk[tab_find<TS>(sm.tab, r.x)]] + c1] = base + ((a + 1) & 3);
+            pr[sm.cum[sm.rnk[tab_find<TS>(sm.tab, r.y)]] + c2] = base + ((a + 2) & 3);
+            pr[sm.cum[sm.rnk[tab_find<TS>(sm.tab, r.z)]] + c3] = base + ((a + 3) & 3);
         }
     }
     if (lane == 0) cnt[i] = u;
@@ -266,7 +266,7 @@ __device__ void tet_row(int32_t i, int32_t beg, int32_t d, const int4* __restric
 
 // Rows with at most FAST_EMAX tetrahedra, one warp each; longer rows are listed for k_tet_rows_big.
 template <bool GATHER>
-__global__ void __launch_bounds__(ROW_WARPS * 32) k_tet_rows(const int32_t* __restrict__ vptr, const int4* __restrict__ adj,
+__global__ void __launch_bounds__(ROW_WARPS * 32, 7) k_tet_rows(const int32_t* __restrict__ vptr, const int4* __restrict__ adj,
                                                             int32_t nq, int32_t* __restrict__ tmp, int32_t* __restrict__ tmp2,
                                                             int32_t* __restrict__ cnt, int32_t* __restrict__ map,
                                                             int32_t* __restrict__ perm, int32_t* __restrict__ big_list,
@@ -361,6 +361,9 @@ __device__ __forceinline__ void tet_elem(const double4_32a p[4], const double w[
     g[3][0] = ay * bz - az * by; g[3][1] = az * bx - ax * bz; g[3][2] = ax * by - ay * bx;
     const double det = ax * g[1][0] + ay * g[1][1] + az * g[1][2];   // a . (b x c) = 6|K|
     if (KIND == FE_TET_STIFF) {
+        // every entry from its own dot product: deriving vertex 0's entries from the zero row sums
+        // instead costs fewer FP64 instructions but loses too much to cancellation on thin
+        // tetrahedra (2.7e-13 of the row maximum at the centre of an 80-tetrahedron star)
 #pragma unroll
         for (int t = 0; t < 3; t++) g[0][t] = -(g[1][t] + g[2][t] + g[3][t]);
         const double s = 1.0 / (6.0 * det);
