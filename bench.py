@@ -348,7 +348,7 @@ def run_ours(args) -> int:
     if not args.no_other:
         line["elasticity"] = elasticity(feasm, meshgen, torch, flush, hbm, peak_kind)
         line["adjoint"] = adjoint(feasm, meshgen, torch, flush)
-        line["drop_zeros"] = drop_zeros(feasm, torch, pat0, S, flush, hbm, peak_kind)
+        line["drop_zeros"] = drop_zeros(feasm, torch, pat0, S, flush, hbm, peak_kind, cells=args.cells)
         line["tetrahedra"] = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind)
     if not args.no_e2e:
         line["e2e"] = e2e(feasm, torch, m, w, args)
@@ -462,10 +462,11 @@ def elasticity(feasm, meshgen, torch, flush, hbm, peak_kind) -> dict:
                          "frac": round(nbytes / k_ms / 1e6 / hbm, 4), "peak_source": f"{peak_kind} HBM copy bandwidth"}}
 
 
-def drop_zeros(feasm, torch, pat, S, flush, hbm, peak_kind) -> dict:
+def drop_zeros(feasm, torch, pat, S, flush, hbm, peak_kind, cells: int = N_CELLS) -> dict:
     """Matlab's value-dependent sparse() result from the structural one: fe_csr_drop_zeros on the
-    step's S (2048 x 2048 cells). The jittered mesh has no exact zero, so every entry is kept and
-    every byte moves; the call includes its one synchronisation (the kept count)."""
+    step's S (2048 x 2048 cells unless --cells says otherwise). The jittered mesh has no exact zero,
+    so every entry is kept and every byte moves; the call includes its one synchronisation (the
+    kept count)."""
     feasm.profile_reset()
     feasm.profile_enable(True)
     kept = []
@@ -477,7 +478,7 @@ def drop_zeros(feasm, torch, pat, S, flush, hbm, peak_kind) -> dict:
     n, nnz, out = pat.n_rows, pat.nnz, kept[-1]
     nbytes = 4 * (n + 1) + 12 * nnz + 4 * (n + 1) + 12 * out     # read CSR once, write the kept CSR
     kbytes = 8 * (n + 1) + 12 * nnz + 12 * out                   # k_compact_rows: both row_ptr, entries in and out
-    return {"workload": f"S of the 2048x2048-cell step (n_rows={n}, nnz={nnz}, kept={out})", "ms": round(ms, 4),
+    return {"workload": f"S of the {cells}x{cells}-cell mesh (n_rows={n}, nnz={nnz}, kept={out})", "ms": round(ms, 4),
             "gentries_s": round(nnz / ms / 1e6, 2), "algorithmic_bytes": nbytes,
             "k_row_nonzeros_ms": round(c_ms, 4), "k_compact_rows_ms": round(k_ms, 4),
             "roofline": {"kernel": "k_compact_rows", "bound": "hbm", "algorithmic_bytes": kbytes,
@@ -493,11 +494,11 @@ TET_STIFF_FP64_OPS = 85
 FP64_PEAK_G = 152 * 2 * 2.07
 
 
-def tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind) -> dict:
+def tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 128) -> dict:
     """P1 tetrahedra (the 3-D extension), 128^3-cell cube (jittered, node-permuted): mesh, pattern,
     and S / M^w / M values by FP64 atomics and by the deterministic gather."""
     seed = 13053122 + 6
-    m = meshgen.cube_mesh(128, seed)
+    m = meshgen.cube_mesh(cells, seed)
     w = torch.tensor(meshgen.vertex_weights3(m, seed), device="cuda")
     q = torch.tensor(m.q, device="cuda")
     me = torch.tensor(m.me, device="cuda")
@@ -519,7 +520,7 @@ def tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind) -> dict:
     k_ms = prof["k_tet_atomic"][0] / prof["k_tet_atomic"][1]
     ops = TET_STIFF_FP64_OPS * m.nme
     nbytes = 16 * m.nme + 32 * m.nq + 64 * m.nme + 8 * pat.nnz     # me, vertex records, map, values
-    return {"workload": f"S, M^w, M of the 128^3-cell cube (nq={m.nq}, nme={m.nme} tetrahedra, nnz={pat.nnz})",
+    return {"workload": f"S, M^w, M of the {cells}^3-cell cube (nq={m.nq}, nme={m.nme} tetrahedra, nnz={pat.nnz})",
             "mesh_ms": round(ms_mesh, 4), "pattern_ms": round(ms_pat, 4), "pattern_gather_ms": round(ms_pat_g, 4),
             **res, "S_atomic_melem_s": round(m.nme / res["S_atomic_ms"] / 1e3, 1),
             "roofline": {"kernel": "k_tet_atomic<S>", "bound": "fp64", "algorithmic_ops": ops,
@@ -627,11 +628,38 @@ def main() -> int:
     ap.add_argument("--no-other", action="store_true", help="skip the elasticity, adjoint, zero-dropping and tetrahedra legs")
     ap.add_argument("--traffic", default=os.path.join(ROOT, "profiles", "traffic.json"),
                     help="per-kernel DRAM bytes per launch from an ncu capture (JSON)")
+    ap.add_argument("--only", choices=["elasticity", "adjoint", "drop_zeros", "tetrahedra"],
+                    help="run this one leg alone and print its object (for profiling; no headline step)")
+    ap.add_argument("--tet-cells", type=int, default=128, help="cells per side of the tetrahedra leg's cube")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)    # at least 3 untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_leg(args)
     return run_ours(args)
+
+
+def run_leg(args) -> int:
+    """One extra leg alone, on its own inputs, printed as {"leg": name, ...}."""
+    import torch
+    from paper_1305_3122_gb300 import feasm, meshgen
+    hbm, peak_kind = _peaks()
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.int32, device="cuda")
+    if args.only == "elasticity":
+        out = elasticity(feasm, meshgen, torch, flush, hbm, peak_kind)
+    elif args.only == "adjoint":
+        out = adjoint(feasm, meshgen, torch, flush)
+    elif args.only == "tetrahedra":
+        out = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind, cells=args.tet_cells)
+    else:
+        m = meshgen.square_mesh(args.cells, 13053122 + 2)
+        mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))
+        pat = feasm.Pattern(mesh, map=False)
+        S = feasm.assemble_stiff(mesh, pat, feasm.ROW)
+        out = drop_zeros(feasm, torch, pat, S, flush, hbm, peak_kind, cells=args.cells)
+    print(json.dumps({"leg": args.only, **out}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -27,6 +27,10 @@ __device__ __forceinline__ unsigned bits_between(int lo, int hi) {
     return up & ~dn;
 }
 
+// Non-zero test on the bits: the value without its sign bit is zero only for +0 and -0 (NaN and
+// subnormals are kept). Integer instructions, so the FP64 pipe stays out of the loop.
+__device__ __forceinline__ bool nonzero(double v) { return (__double_as_longlong(v) << 1) != 0; }
+
 __global__ void __launch_bounds__(CZ_BLOCK) k_row_nonzeros(const int32_t* __restrict__ row_ptr,
                                                            const double* __restrict__ values, int32_t n_rows,
                                                            int32_t* __restrict__ cnt) {
@@ -49,7 +53,7 @@ __global__ void __launch_bounds__(CZ_BLOCK) k_row_nonzeros(const int32_t* __rest
 #pragma unroll
             for (int u = 0; u < CZ_UNROLL; u++) {
                 const int32_t base = base0 + 32 * u;
-                const unsigned m = __ballot_sync(0xffffffffu, v[u] != 0.0);
+                const unsigned m = __ballot_sync(0xffffffffu, nonzero(v[u]));
                 const int lo = (int)max(0, min(32, rs - base)), hi = (int)max(0, min(32, re - base));
                 c += __popc(m & bits_between(lo, hi));
             }
@@ -81,7 +85,7 @@ __global__ void __launch_bounds__(CZ_BLOCK) k_compact_rows(const int32_t* __rest
             }
 #pragma unroll
             for (int u = 0; u < CZ_UNROLL; u++) {
-                const bool keep = v[u] != 0.0;                    // 0.0 beyond the range: never kept
+                const bool keep = nonzero(v[u]);                  // 0.0 beyond the range: never kept
                 const unsigned m = __ballot_sync(0xffffffffu, keep);
                 if (keep) {
                     const int32_t p = out + __popc(m & below);
