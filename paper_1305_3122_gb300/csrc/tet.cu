@@ -19,6 +19,7 @@
 // deterministic gather variant the warp also writes each non-zero's contributions in ascending
 // element order: row i has exactly 4 * (its valence) contributions, so its part of the list starts
 // at 4 * vptr[i] before any offset is known.
+#include "ff.cuh"
 #include "internal.cuh"
 
 namespace {
@@ -361,33 +362,77 @@ __device__ __forceinline__ void tet_elem(const double4_32a p[4], const double w[
     g[3][0] = ay * bz - az * by; g[3][1] = az * bx - ax * bz; g[3][2] = ax * by - ay * bx;
     const double det = ax * g[1][0] + ay * g[1][1] + az * g[1][2];   // a . (b x c) = 6|K|
     if (KIND == FE_TET_STIFF) {
-        // every entry from its own dot product: deriving vertex 0's entries from the zero row sums
-        // instead costs fewer FP64 instructions but loses too much to cancellation on thin
-        // tetrahedra (2.7e-13 of the row maximum at the centre of an 80-tetrahedron star)
+        // The gradients, det and 1/(6 det) stay in FP64 (exact to 2^-53, so no cancellation in a
+        // cross product or in det is amplified); the ten dot products and their scaling run in
+        // double-float on the FP32 pipes (ff.cuh), erring by a few units of 2^-48 of
+        // |g_a| |g_b| / (6 det) each. That halves the FP64 instructions of an element (85 -> 55,
+        // counting the ten conversions back). The twelve gradient components are scaled by a
+        // common power of two 2^k that brings the largest to [1, 2) (their products then stay
+        // far inside the float range whatever the mesh's size), and 2^-2k goes into 1/(6 det).
+        // Every entry keeps its own dot product: deriving vertex 0's entries from the zero row
+        // sums loses too much to cancellation on thin tetrahedra (2.7e-13 of the row maximum at
+        // the centre of an 80-tetrahedron star).
 #pragma unroll
         for (int t = 0; t < 3; t++) g[0][t] = -(g[1][t] + g[2][t] + g[3][t]);
-        const double s = 1.0 / (6.0 * det);
+        const double sd = 1.0 / (6.0 * det);
+        unsigned emax = 0;
 #pragma unroll
         for (int a = 0; a < 4; a++)
 #pragma unroll
-            for (int b = a; b < 4; b++) {
-                const double v = (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]) * s;
+            for (int t = 0; t < 3; t++) emax = max(emax, fp64_biased_exponent(g[a][t]));
+        const int k = ff_group_scale(emax);
+        ff G[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int t = 0; t < 3; t++) G[a][t] = ff_from_double_scaled(g[a][t], k);
+        int bad = 0;
+        const ff sf = ff_from_double(ldexp(sd, -2 * k), bad);
+        if (!bad) {
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = a; b < 4; b++) {
+                    const ff d = ff_add(ff_dot2(G[a][0], G[a][1], G[b][0], G[b][1]), ff_mul(G[a][2], G[b][2]));
+                    const double v = ff_to_double(ff_mul(d, sf));
+                    E[a][b] = v;
+                    E[b][a] = v;
+                }
+        } else {                                      // 1/(6 det) 2^-2k outside the double-float range: all FP64
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = a; b < 4; b++) {
+                    const double v = (g[a][0] * g[b][0] + g[a][1] * g[b][1] + g[a][2] * g[b][2]) * sd;
+                    E[a][b] = v;
+                    E[b][a] = v;
+                }
+        }
+    } else if (KIND == FE_TET_MASS) {
+        const double m = det / 120.0;                 // |K| / 20
+        const double m2 = 2.0 * m;
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) E[a][b] = a == b ? m2 : m;
+    } else {
+        // the ten distinct entries: m (2W + 4 w_a) on the diagonal, m (W + w_a + w_b) off it
+        const double m = det / 720.0;                 // |K| / 120
+        const double mW = m * (w[0] + w[1] + w[2] + w[3]);
+        double u[4];
+#pragma unroll
+        for (int a = 0; a < 4; a++) u[a] = m * w[a];
+        const double mW2 = 2.0 * mW;
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            E[a][a] = fma(4.0, u[a], mW2);
+#pragma unroll
+            for (int b = a + 1; b < 4; b++) {
+                const double v = mW + u[a] + u[b];
                 E[a][b] = v;
                 E[b][a] = v;
             }
-    } else if (KIND == FE_TET_MASS) {
-        const double m = det / 120.0;                 // |K| / 20
-#pragma unroll
-        for (int a = 0; a < 4; a++)
-#pragma unroll
-            for (int b = 0; b < 4; b++) E[a][b] = a == b ? 2.0 * m : m;
-    } else {
-        const double m = det / 720.0;                 // |K| / 120
-        const double W = w[0] + w[1] + w[2] + w[3];
-#pragma unroll
-        for (int a = 0; a < 4; a++)
-#pragma unroll
-            for (int b = 0; b < 4; b++) E[a][b] = a == b ? m * (2.0 * W + 4.0 * w[a]) : m * (W + w[a] + w[b]);
+        }
     }
 }
 

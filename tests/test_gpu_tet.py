@@ -86,6 +86,22 @@ def test_tet_values(case, kind, variant):
     assert_values_close(rp, got.cpu().numpy(), va)
 
 
+@pytest.mark.parametrize("scale,offset", [(1e-9, 0.0), (1e9, 0.0), (1.0, 1000.0)])
+def test_tet_scale_and_offset(scale, offset):
+    """The double-float dot products work on gradients scaled by a power of two, so a cube shrunk
+    to 1e-9, blown up to 1e9 or moved far from the origin still matches the oracle."""
+    m = meshgen.cube_mesh(5, 8)
+    q = m.q * scale + offset
+    w = _weights(m.q)
+    mesh = feasm.TetMesh(q, m.me)
+    pat = feasm.TetPattern(mesh, gather=True)
+    for kg, ko in KINDS.values():
+        rp, ci, va = oracle.tet_assemble(ko, q, m.me, w)
+        for variant in (feasm.ATOMIC, feasm.GATHER):
+            got = feasm.tet_assemble(mesh, pat, kg, torch.tensor(w, device="cuda"), variant)
+            assert_values_close(rp, got.cpu().numpy(), va)
+
+
 def test_tet_gather_bit_identical_runs():
     q, me = CASES["cube12"]
     mesh = feasm.TetMesh(q, me)
