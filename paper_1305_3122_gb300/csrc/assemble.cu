@@ -160,14 +160,28 @@ __global__ void k_seg_gather(const int32_t* __restrict__ seg_ptr, const int32_t*
                              const double* __restrict__ kg0, const double* __restrict__ kg1,
                              double* __restrict__ out0, double* __restrict__ out1) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
-        int32_t s0 = seg_ptr[p], s1 = seg_ptr[p + 1];
-        int32_t c = perm[s0];
-        double a0 = kg0[c];
-        double a1 = TWO ? kg1[c] : 0.0;
-        for (int32_t s = s0 + 1; s < s1; s++) {
-            c = perm[s];
-            a0 += kg0[c];
-            if (TWO) a1 += kg1[c];
+        const int32_t s0 = seg_ptr[p], s1 = seg_ptr[p + 1];
+        double a0 = 0.0, a1 = 0.0;
+        // four contributions per step: their ids, then their values, are loaded together (more
+        // loads in flight); they are still added one by one in ascending order, the first one
+        // taken as the start of the sum, so the result is that of the plain loop
+        for (int32_t b = s0; b < s1; b += 4) {
+            int32_t c[4];
+            double v0[4], v1[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) c[u] = b + u < s1 ? perm[b + u] : 0;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                v0[u] = b + u < s1 ? kg0[c[u]] : 0.0;
+                v1[u] = TWO && b + u < s1 ? kg1[c[u]] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (b + u < s1) {
+                    a0 = b + u == s0 ? v0[u] : a0 + v0[u];
+                    if (TWO) a1 = b + u == s0 ? v1[u] : a1 + v1[u];
+                }
+            }
         }
         out0[p] = a0;
         if (TWO) out1[p] = a1;

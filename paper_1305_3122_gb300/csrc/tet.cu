@@ -490,8 +490,20 @@ __global__ void __launch_bounds__(TET_BLOCK) k_tet_gather(const int32_t* __restr
                                                           const double* __restrict__ kg, int64_t nnz,
                                                           double* __restrict__ val) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s0 = seg_ptr[p], s1 = seg_ptr[p + 1];
         double s = 0.0;
-        for (int32_t t = seg_ptr[p]; t < seg_ptr[p + 1]; t++) s += kg[perm[t]];
+        // four contributions per step, loaded together and added one by one in ascending order
+        for (int32_t b = s0; b < s1; b += 4) {
+            int32_t c[4];
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) c[u] = b + u < s1 ? perm[b + u] : 0;
+#pragma unroll
+            for (int u = 0; u < 4; u++) v[u] = b + u < s1 ? kg[c[u]] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (b + u < s1) s = b + u == s0 ? v[u] : s + v[u];
+        }
         val[p] = s;
     }
 }
