@@ -155,13 +155,31 @@ __global__ void k_adjoint_gather(const int32_t* __restrict__ vptr, const int32_t
                                  double* __restrict__ dw) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
         double sx = 0.0, sy = 0.0, sw = 0.0;
-        for (int32_t s = vptr[i]; s < vptr[i + 1]; s++) {
-            int32_t e = vel[s];
-            int32_t k = e / 3, a = e - 3 * k;
-            const double* o = stage + 9 * (int64_t)k;
-            sx += o[a];
-            sy += o[3 + a];
-            sw += o[6 + a];
+        const int32_t s0 = vptr[i], s1 = vptr[i + 1];
+        // four triangles per step: their ids, then their staged values, are loaded together;
+        // the sums still take them one by one in ascending order
+        for (int32_t b = s0; b < s1; b += 4) {
+            int32_t e[4];
+            double vx[4], vy[4], vw[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) e[u] = b + u < s1 ? vel[b + u] : 0;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int32_t k = e[u] / 3, a = e[u] - 3 * k;
+                const double* o = stage + 9 * (int64_t)k;
+                const bool in = b + u < s1;
+                vx[u] = in ? o[a] : 0.0;
+                vy[u] = in ? o[3 + a] : 0.0;
+                vw[u] = in && want_w ? o[6 + a] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (b + u < s1) {
+                    sx += vx[u];
+                    sy += vy[u];
+                    sw += vw[u];
+                }
+            }
         }
         dq[i] = sx;
         dq[nq + i] = sy;
