@@ -487,10 +487,9 @@ def drop_zeros(feasm, torch, pat, S, flush, hbm, peak_kind, cells: int = N_CELLS
 
 
 # FP64 instructions of one stiffness element in k_tet_atomic / k_tet_stage: 9 edge differences,
-# 3 cross products (18), the determinant (3), g_0 (6), 1/(6 det) (about 9 with the division's
-# iteration) and the 10 additions that convert the double-float entries back; the 10 dot products
-# and their scaling run on the FP32 pipes.
-TET_STIFF_FP64_OPS = 55
+# 3 cross products (18), the determinant (3), g_0 (6) and the 10 additions that convert the
+# double-float entries back; 1/(6 det), the 10 dot products and their scaling run on the FP32 pipes.
+TET_STIFF_FP64_OPS = 46
 # FP64 issue rate of GB300: 2 instructions per SM per clock (measured about 0.6 T DFMA/s).
 FP64_PEAK_G = 152 * 2 * 2.07
 

@@ -26,8 +26,8 @@ namespace {
 
 constexpr int TET_BLOCK = 256;
 constexpr int ROW_WARPS = 4;                 // warps per block in the row pass (fast rows)
-constexpr int FAST_TS = 256;                 // hash-table slots per warp, fast rows
-constexpr int FAST_EMAX = 64;                // fast rows: at most 64 tetrahedra (3 * 64 + 1 ids < 256)
+constexpr int FAST_TS = 128;                 // hash-table slots per warp, fast rows (small, for occupancy)
+constexpr int FAST_EMAX = 42;                // fast rows: at most 42 tetrahedra (3 * 42 + 1 ids < 128)
 constexpr int BIG_TS = 4096;                 // one warp per block for rows up to FE_TET_MAX_VALENCE
 constexpr int BIG_EMAX = FE_TET_MAX_VALENCE;
 static_assert(3 * BIG_EMAX + 1 < BIG_TS, "the big-row table must hold every distinct id");
@@ -134,8 +134,8 @@ __device__ __forceinline__ uint32_t tet_hash(int32_t id) { return (uint32_t)id *
 // has a free slot (TS > the row's distinct ids), so the probe ends within TS steps.
 template <int TS>
 __device__ __forceinline__ int tab_insert(int32_t* tab, int32_t id, bool* fresh) {
-    constexpr int SH = 32 - (TS == 256 ? 8 : 12);
-    static_assert(TS == 256 || TS == 4096, "table sizes");
+    constexpr int SH = 32 - (TS == 128 ? 7 : 12);
+    static_assert(TS == 128 || TS == 4096, "table sizes");
     int s = (int)(tet_hash(id) >> SH);
     for (int step = 0; step < TS; step++) {
         int32_t old = atomicCAS(&tab[s], -1, id);
@@ -149,7 +149,7 @@ __device__ __forceinline__ int tab_insert(int32_t* tab, int32_t id, bool* fresh)
 
 template <int TS>
 __device__ __forceinline__ int tab_find(const int32_t* tab, int32_t id) {
-    constexpr int SH = 32 - (TS == 256 ? 8 : 12);
+    constexpr int SH = 32 - (TS == 128 ? 7 : 12);
     int s = (int)(tet_hash(id) >> SH);
     for (int step = 0; step < TS; step++) {
         if (tab[s] == id) return s;
@@ -267,7 +267,7 @@ __device__ void tet_row(int32_t i, int32_t beg, int32_t d, const int4* __restric
 
 // Rows with at most FAST_EMAX tetrahedra, one warp each; longer rows are listed for k_tet_rows_big.
 template <bool GATHER>
-__global__ void __launch_bounds__(ROW_WARPS * 32, 7) k_tet_rows(const int32_t* __restrict__ vptr, const int4* __restrict__ adj,
+__global__ void __launch_bounds__(ROW_WARPS * 32, 12) k_tet_rows(const int32_t* __restrict__ vptr, const int4* __restrict__ adj,
                                                             int32_t nq, int32_t* __restrict__ tmp, int32_t* __restrict__ tmp2,
                                                             int32_t* __restrict__ cnt, int32_t* __restrict__ map,
                                                             int32_t* __restrict__ perm, int32_t* __restrict__ big_list,
@@ -362,10 +362,10 @@ __device__ __forceinline__ void tet_elem(const double4_32a p[4], const double w[
     g[3][0] = ay * bz - az * by; g[3][1] = az * bx - ax * bz; g[3][2] = ax * by - ay * bx;
     const double det = ax * g[1][0] + ay * g[1][1] + az * g[1][2];   // a . (b x c) = 6|K|
     if (KIND == FE_TET_STIFF) {
-        // The gradients, det and 1/(6 det) stay in FP64 (exact to 2^-53, so no cancellation in a
-        // cross product or in det is amplified); the ten dot products and their scaling run in
-        // double-float on the FP32 pipes (ff.cuh), erring by a few units of 2^-48 of
-        // |g_a| |g_b| / (6 det) each. That halves the FP64 instructions of an element (85 -> 55,
+        // The gradients and det stay in FP64 (exact to 2^-53, so no cancellation in a cross
+        // product or in det is amplified); 1/(6 det), the ten dot products and their scaling run
+        // in double-float on the FP32 pipes (ff.cuh), erring by a few units of 2^-48 of
+        // |g_a| |g_b| / (6 det) each. That halves the FP64 instructions of an element (85 -> 46,
         // counting the ten conversions back). The twelve gradient components are scaled by a
         // common power of two 2^k that brings the largest to [1, 2) (their products then stay
         // far inside the float range whatever the mesh's size), and 2^-2k goes into 1/(6 det).
@@ -374,7 +374,6 @@ __device__ __forceinline__ void tet_elem(const double4_32a p[4], const double w[
         // the centre of an 80-tetrahedron star).
 #pragma unroll
         for (int t = 0; t < 3; t++) g[0][t] = -(g[1][t] + g[2][t] + g[3][t]);
-        const double sd = 1.0 / (6.0 * det);
         unsigned emax = 0;
 #pragma unroll
         for (int a = 0; a < 4; a++)
@@ -386,9 +385,12 @@ __device__ __forceinline__ void tet_elem(const double4_32a p[4], const double w[
         for (int a = 0; a < 4; a++)
 #pragma unroll
             for (int t = 0; t < 3; t++) G[a][t] = ff_from_double_scaled(g[a][t], k);
-        int bad = 0;
-        const ff sf = ff_from_double(ldexp(sd, -2 * k), bad);
-        if (!bad) {
+        // 2^-2k / (6 det): det scaled by 2^2k in the conversion (exact), the reciprocal in
+        // double-float (about 46 bits)
+        const ff D = ff_from_double_scaled(det, 2 * k);
+        const bool ok = D.h != 0.0f;                  // zero: 2^2k det outside the double-float range
+        const ff sf = ff_rcp_fast(ff_mulf(D, 6.0f));
+        if (ok) {
 #pragma unroll
             for (int a = 0; a < 4; a++)
 #pragma unroll
@@ -398,7 +400,8 @@ __device__ __forceinline__ void tet_elem(const double4_32a p[4], const double w[
                     E[a][b] = v;
                     E[b][a] = v;
                 }
-        } else {                                      // 1/(6 det) 2^-2k outside the double-float range: all FP64
+        } else {                                      // outside the double-float range: all FP64
+            const double sd = 1.0 / (6.0 * det);
 #pragma unroll
             for (int a = 0; a < 4; a++)
 #pragma unroll
