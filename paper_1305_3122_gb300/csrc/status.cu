@@ -112,19 +112,40 @@ static constexpr int SCAN_ITEMS = 8;
 static constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 
 // round: each input is rounded up to a multiple of `round` (a power of two) before summing.
-__device__ __forceinline__ long long scan_in(const int32_t* __restrict__ in, int64_t i, int round) {
-    int32_t v = in[i];
+__device__ __forceinline__ long long scan_round(int32_t v, int round) {
     return round > 1 ? (long long)((v + round - 1) & ~(round - 1)) : (long long)v;
 }
+__device__ __forceinline__ long long scan_in(const int32_t* __restrict__ in, int64_t i, int round) {
+    return scan_round(in[i], round);
+}
 
-__global__ void k_tile_sums(const int32_t* __restrict__ in, int64_t n, long long* __restrict__ sums, int round) {
-    __shared__ long long red[SCAN_BLOCK / 32];
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    long long s = 0;
-    for (int t = threadIdx.x; t < SCAN_TILE; t += SCAN_BLOCK) {
-        int64_t i = base + t;
-        if (i < n) s += scan_in(in, i, round);
+// The SCAN_ITEMS = 8 consecutive inputs of one thread: two 16-byte loads when the arrays are
+// 16-byte aligned (vec) and all eight lie below n, else eight scalar loads (zeros past n).
+__device__ __forceinline__ void scan_load8(const int32_t* __restrict__ in, int64_t i0, int64_t n, bool vec, int round,
+                                           long long v[SCAN_ITEMS]) {
+    static_assert(SCAN_ITEMS == 8, "two 16-byte vectors per thread");
+    if (vec && i0 + SCAN_ITEMS <= n) {
+        const int4 a = *reinterpret_cast<const int4*>(in + i0);
+        const int4 b = *reinterpret_cast<const int4*>(in + i0 + 4);
+        v[0] = scan_round(a.x, round); v[1] = scan_round(a.y, round);
+        v[2] = scan_round(a.z, round); v[3] = scan_round(a.w, round);
+        v[4] = scan_round(b.x, round); v[5] = scan_round(b.y, round);
+        v[6] = scan_round(b.z, round); v[7] = scan_round(b.w, round);
+    } else {
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; j++) v[j] = i0 + j < n ? scan_in(in, i0 + j, round) : 0;
     }
+}
+
+// Tiles are read in the same thread-to-element order as k_tile_scan (eight consecutive elements
+// per thread), so each warp reads 1 KB of consecutive memory per pair of vector loads.
+__global__ void k_tile_sums(const int32_t* __restrict__ in, int64_t n, long long* __restrict__ sums, int round, bool vec) {
+    __shared__ long long red[SCAN_BLOCK / 32];
+    long long v[SCAN_ITEMS];
+    scan_load8(in, (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS, n, vec, round, v);
+    long long s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) s += v[j];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -171,17 +192,14 @@ __global__ void k_scan_sums(long long* sums, int64_t ntiles) {
 }
 
 __global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict__ out, int32_t* __restrict__ out2,
-                            int64_t n, const long long* __restrict__ offs, int* __restrict__ overflow, int round) {
+                            int64_t n, const long long* __restrict__ offs, int* __restrict__ overflow, int round, bool vec) {
     __shared__ long long warp_tot[SCAN_BLOCK / 32];
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     long long v[SCAN_ITEMS];
+    scan_load8(in, base, n, vec, round, v);
     long long local = 0;
 #pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; j++) {
-        int64_t i = base + j;
-        v[j] = i < n ? scan_in(in, i, round) : 0;
-        local += v[j];
-    }
+    for (int j = 0; j < SCAN_ITEMS; j++) local += v[j];
     long long x = local;
     for (int o = 1; o < 32; o <<= 1) {
         long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -199,15 +217,32 @@ __global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict_
     }
     __syncthreads();
     long long run = offs[blockIdx.x] + ((threadIdx.x >> 5) ? warp_tot[(threadIdx.x >> 5) - 1] : 0) + x - local;
+    if (vec && base + SCAN_ITEMS <= n) {
+        int32_t r[SCAN_ITEMS];
 #pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; j++) {
-        int64_t i = base + j;
-        if (i < n) {
+        for (int j = 0; j < SCAN_ITEMS; j++) {
             if (run > INT32_MAX) *overflow = 1;
-            out[i] = (int32_t)run;
-            if (out2) out2[i] = (int32_t)run;
+            r[j] = (int32_t)run;
+            run += v[j];
         }
-        run += v[j];
+        const int4 a = make_int4(r[0], r[1], r[2], r[3]), b = make_int4(r[4], r[5], r[6], r[7]);
+        *reinterpret_cast<int4*>(out + base) = a;
+        *reinterpret_cast<int4*>(out + base + 4) = b;
+        if (out2) {
+            *reinterpret_cast<int4*>(out2 + base) = a;
+            *reinterpret_cast<int4*>(out2 + base + 4) = b;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; j++) {
+            int64_t i = base + j;
+            if (i < n) {
+                if (run > INT32_MAX) *overflow = 1;
+                out[i] = (int32_t)run;
+                if (out2) out2[i] = (int32_t)run;
+            }
+            run += v[j];
+        }
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
         long long tot = offs[gridDim.x];
@@ -228,9 +263,11 @@ fe_status fe_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStre
     st = fe_alloc_n(&ovf, 1, "scan overflow flag");
     if (st) { fe_free(sums); return st; }
     cudaMemsetAsync(ovf, 0, sizeof(int), s);
-    { FE_PROF("k_tile_sums", s); k_tile_sums<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, sums, round); }
+    const bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) |
+                       reinterpret_cast<uintptr_t>(out2)) & 15u) == 0;
+    { FE_PROF("k_tile_sums", s); k_tile_sums<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, sums, round, vec); }
     { FE_PROF("k_scan_sums", s); k_scan_sums<<<1, 1024, 0, s>>>(sums, ntiles); }
-    { FE_PROF("k_tile_scan", s); k_tile_scan<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, out2, n, sums, ovf, round); }
+    { FE_PROF("k_tile_scan", s); k_tile_scan<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, out2, n, sums, ovf, round, vec); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { fe_free(sums); fe_free(ovf); return fe_cuda_fail(e, "scan kernels"); }
     fe_status ret = FE_OK;
