@@ -182,8 +182,10 @@ fe_status fe_assemble_elas(fe_mesh mesh, fe_pattern pattern, double lambda, doub
 /* End to end: S and M^w (FE_VARIANT_ROW) from host arrays q [2][nq], me [3][nme], w [nq] to host
  * CSR arrays row_ptr [nq + 1], col_idx, S, Mw [cap]. Creates and validates the mesh, builds the
  * pattern, assembles, and copies back, overlapping the copies with the work where the data allow
- * (the weight upload with mesh validation; the col_idx download and the value download of each
- * of 8 row blocks with the assembly of the later blocks). Output buffers should be pinned host
+ * (me goes up first and is checked for range and repeats while q and w follow, and the pattern is
+ * built during their upload; the orientation check follows; the col_idx download and the value
+ * download of each of 8 row blocks overlap the assembly of the later blocks). Inputs should be
+ * pinned host memory for the uploads to overlap the work, and output buffers pinned host
  * memory for the copies to overlap (pageable memory works, without overlap). *nnz gets the
  * number of stored entries; if cap < nnz the call returns FE_ERR_BUFFER_TOO_SMALL with *nnz set
  * and row_ptr unspecified (6 nme + nq always suffices). Errors of the mesh as for fe_mesh_create,

@@ -83,6 +83,15 @@ struct fe_tet_pattern_s {
 
 uint64_t fe_next_topology_id();
 
+// Staged mesh creation for the one-shot host call (mesh.cu): the connectivity (device array,
+// owned by the mesh afterwards) is checked for range, repeats and valences with one
+// synchronisation; fe_mesh_attach_coords packs device coordinates [2][nq] and queues the
+// orientation check (no synchronisation); fe_mesh_orientation_status interprets the error word
+// read back afterwards (4 ints).
+fe_status fe_mesh_create_topology(int32_t nq, int32_t nme, int32_t* me_dev, cudaStream_t s, fe_mesh* out);
+fe_status fe_mesh_attach_coords(fe_mesh m, const double* q_dev, cudaStream_t s);
+fe_status fe_mesh_orientation_status(const int word[4]);
+
 // High float (top 24 significant bits, truncated) of a double, by bit operations: no FP64
 // instruction. |result - x| < 2^-23 |x|; zero and subnormals give zero, magnitudes above the
 // float range give +-inf.

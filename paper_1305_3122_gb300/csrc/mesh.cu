@@ -20,6 +20,10 @@ __global__ void k_pack_coords(const double* __restrict__ q, int32_t nq, double2*
 // Validation word layout: [0] = OR of error bits, [1] = first bad triangle (min), per kind.
 enum { BAD_RANGE = 1, BAD_REPEAT = 2, BAD_ORIENT = 4 };
 
+// Validation passes (mode bits): the connectivity alone, and the orientation (which needs the
+// coordinates; its pass assumes ids already checked).
+enum { VAL_TOPOLOGY = 1, VAL_ORIENT = 2 };
+
 // Every triangle: vertex ids in range, three distinct vertices, counter-clockwise. The sign of
 // D = (p1 - p0) x (p2 - p0) is first taken from truncated-float coordinates; the float result is
 // trusted when it exceeds a bound on its error (coordinate truncation 2^-23 |p|, float rounding of
@@ -27,19 +31,21 @@ enum { BAD_RANGE = 1, BAD_REPEAT = 2, BAD_ORIENT = 4 };
 // v = p2 - p0, w = p0 - p1 as the oracle does. Also counts each vertex's triangles (the row digit
 // of the pattern build's counting sort), so a pattern build can skip that pass.
 __global__ void k_validate(const double2* __restrict__ q, int32_t nq, const int32_t* __restrict__ me,
-                           int32_t nme, int* __restrict__ word, int32_t* __restrict__ deg) {
+                           int32_t nme, int* __restrict__ word, int32_t* __restrict__ deg, int mode) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
         int32_t v0 = me[k], v1 = me[nme + k], v2 = me[2 * (int64_t)nme + k];
         int bad = 0;
         if (v0 < 0 || v0 >= nq || v1 < 0 || v1 >= nq || v2 < 0 || v2 >= nq) {
-            bad = BAD_RANGE;
+            if (mode & VAL_TOPOLOGY) bad = BAD_RANGE;
         } else {
-            atomicAdd(&deg[v0], 1);
-            atomicAdd(&deg[v1], 1);
-            atomicAdd(&deg[v2], 1);
+            if (mode & VAL_TOPOLOGY) {
+                atomicAdd(&deg[v0], 1);
+                atomicAdd(&deg[v1], 1);
+                atomicAdd(&deg[v2], 1);
+            }
             if (v0 == v1 || v1 == v2 || v0 == v2) {
-                bad = BAD_REPEAT;
-            } else {
+                if (mode & VAL_TOPOLOGY) bad = BAD_REPEAT;
+            } else if (mode & VAL_ORIENT) {
                 double2 p0 = q[v0], p1 = q[v1], p2 = q[v2];
                 float x0 = fe_trunc_float(p0.x), y0 = fe_trunc_float(p0.y);
                 float ax = fe_trunc_float(p1.x) - x0, ay = fe_trunc_float(p1.y) - y0;
@@ -143,7 +149,7 @@ extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, co
     if (e == cudaSuccess) e = cudaMemsetAsync(m->err + 1, 0x7F, 3 * sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->deg, 0, sizeof(int32_t) * ((size_t)nq + 1), s);
     if (e == cudaSuccess && nme > 0) {
-        { FE_PROF("k_validate", s); k_validate<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg); }
+        { FE_PROF("k_validate", s); k_validate<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg, VAL_TOPOLOGY | VAL_ORIENT); }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(word, m->err, sizeof word, cudaMemcpyDeviceToHost, s);
@@ -164,6 +170,71 @@ extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, co
                                                " has signed area <= 0 (must be counter-clockwise)");
     }
     *out = m;
+    return FE_OK;
+}
+
+// ------------------------------------------------------------------ staged creation
+//
+// The one-shot host call (fe_assemble_stiff_wmass_host) uploads the connectivity first and builds
+// the pattern while the coordinates are still on their way: the mesh is created from device
+// connectivity (ownership passes to the mesh) and checked for range, repeats and valences, which
+// is all the pattern build needs; fe_mesh_attach_coords then packs the coordinates and queues the
+// orientation check, whose result fe_mesh_orientation_status reads from the validation word.
+
+fe_status fe_mesh_create_topology(int32_t nq, int32_t nme, int32_t* me_dev, cudaStream_t s, fe_mesh* out) {
+    *out = nullptr;
+    fe_mesh m = new fe_mesh_s();
+    m->last_stream = s;
+    m->nq = nq;
+    m->nme = nme;
+    m->topology_id = fe_next_topology_id();
+    m->me = me_dev;
+    m->me_owned = true;
+    fe_status st = fe_alloc_n(&m->q, (size_t)nq, "mesh coordinates");
+    if (!st) st = fe_alloc_n(&m->err, 4, "mesh error word");
+    if (!st) st = fe_alloc_n(&m->deg, (size_t)nq + 1, "vertex valences");
+    if (st) { fe_mesh_destroy(m); return st; }
+    int word[4];
+    cudaError_t e = cudaMemsetAsync(m->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->err + 1, 0x7F, 3 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->deg, 0, sizeof(int32_t) * ((size_t)nq + 1), s);
+    if (e == cudaSuccess && nme > 0) {
+        { FE_PROF("k_validate", s); k_validate<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg, VAL_TOPOLOGY); }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(word, m->err, sizeof word, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { fe_mesh_destroy(m); return fe_cuda_fail(e, "mesh validation"); }
+    if (word[0] & BAD_RANGE) {
+        fe_mesh_destroy(m);
+        return fe_fail(FE_ERR_INDEX_RANGE, "triangle " + std::to_string(word[1]) + " has a vertex id outside [0, nq)");
+    }
+    if (word[0] & BAD_REPEAT) {
+        fe_mesh_destroy(m);
+        return fe_fail(FE_ERR_DEGENERATE, "triangle " + std::to_string(word[2]) + " repeats a vertex");
+    }
+    *out = m;
+    return FE_OK;
+}
+
+fe_status fe_mesh_attach_coords(fe_mesh m, const double* q_dev, cudaStream_t s) {
+    const int32_t nq = m->nq, nme = m->nme;
+    if (nq > 0) { FE_PROF("k_pack_coords", s); k_pack_coords<<<fe_grid(nq, 256), 256, 0, s>>>(q_dev, nq, m->q); }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->err + 1, 0x7F, 3 * sizeof(int), s);
+    if (e == cudaSuccess && nme > 0) {
+        { FE_PROF("k_validate", s); k_validate<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg, VAL_ORIENT); }
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return fe_cuda_fail(e, "orientation check");
+    return FE_OK;
+}
+
+fe_status fe_mesh_orientation_status(const int word[4]) {
+    if (word[0] & BAD_ORIENT)
+        return fe_fail(FE_ERR_ORIENTATION, "triangle " + std::to_string(word[3]) +
+                                               " has signed area <= 0 (must be counter-clockwise)");
     return FE_OK;
 }
 

@@ -828,9 +828,12 @@ extern "C" fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const
     cudaStream_t s2 = side_stream();
     if (!s2) return fe_fail(FE_ERR_CUDA, "could not create the copy stream");
     FeStreamScope scope(s);
+    if (nme > 0 && !me) return fe_fail(FE_ERR_INVALID_ARG, "me is null");
+    if ((int64_t)nme * 9 >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "9*nme must be < 2^31");
     fe_mesh m = nullptr;
     fe_pattern p = nullptr;
-    double *wd = nullptr, *Sd = nullptr, *Md = nullptr;
+    int32_t* med = nullptr;
+    double *qd = nullptr, *wd = nullptr, *Sd = nullptr, *Md = nullptr;
     VRec* vr = nullptr;
     cudaEvent_t ev[E2E_BLOCKS + 1] = {};
     fe_status st = FE_OK;
@@ -843,36 +846,62 @@ extern "C" fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const
         fe_free(Sd);
         fe_free(Md);
         fe_free(wd);
+        fe_free(qd);
+        fe_free(med);
         if (p) fe_pattern_destroy(p);
         if (m) fe_mesh_destroy(m);
         return ret;
     };
     for (auto& e : ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return done(fe_fail(FE_ERR_CUDA, "event creation"));
-    // 1. w goes up on the side stream while the mesh is uploaded and validated
+    // 1. the connectivity goes up first on the main stream; the coordinates and the weights follow
+    //    on the side stream and arrive while the pattern is built (the pattern needs only me)
+    if ((st = fe_alloc_n(&med, 3 * (size_t)nme, "mesh connectivity"))) return done(st);
+    if ((st = fe_alloc_n(&qd, 2 * (size_t)nq, "coordinate staging"))) return done(st);
     if ((st = fe_alloc_n(&wd, (size_t)nq, "vertex weights"))) return done(st);
-    cudaEventRecord(ev[0], s);                                   // wd's allocation is ordered on s
+    if (nme > 0 && cudaMemcpyAsync(med, me, 3 * sizeof(int32_t) * nme, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return done(fe_fail(FE_ERR_CUDA, "connectivity upload"));
+    cudaEventRecord(ev[0], s);                                   // allocations and the me upload come first
     cudaStreamWaitEvent(s2, ev[0]);
-    if (nq > 0 && cudaMemcpyAsync(wd, w, sizeof(double) * nq, cudaMemcpyHostToDevice, s2) != cudaSuccess)
-        return done(fe_fail(FE_ERR_CUDA, "weight upload"));
-    cudaEventRecord(ev[0], s2);
-    // 2. mesh and pattern (each synchronises the main stream)
-    if ((st = fe_mesh_create(nq, nme, q, me, FE_PTR_HOST, stream, &m))) return done(st);
+    if (nq > 0 && (cudaMemcpyAsync(qd, q, 2 * sizeof(double) * nq, cudaMemcpyHostToDevice, s2) != cudaSuccess ||
+                   cudaMemcpyAsync(wd, w, sizeof(double) * nq, cudaMemcpyHostToDevice, s2) != cudaSuccess))
+        return done(fe_fail(FE_ERR_CUDA, "coordinate or weight upload"));
+    cudaEventRecord(ev[0], s2);                                  // q and w are up
+    // 2. mesh (range, repeats, valences) and pattern, each synchronising the main stream; the mesh
+    //    owns the connectivity from here on (also when it fails)
+    st = fe_mesh_create_topology(nq, nme, med, s, &m);
+    med = nullptr;
+    if (st) return done(st);
     if ((st = fe_pattern_build(m, 1, FE_PATTERN_DEFAULT, stream, &p))) return done(st);
+    // 3. the coordinates: packed, and every triangle's orientation checked
+    cudaStreamWaitEvent(s, ev[0]);
+    if ((st = fe_mesh_attach_coords(m, qd, s))) return done(st);
     const int64_t nnz = p->nnz;
     *nnz_out = nnz;
-    if (cap < nnz)
+    int word[4] = {0, 0, 0, 0};
+    auto read_word = [&]() -> fe_status {
+        if (cudaMemcpyAsync(word, m->err, sizeof word, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fe_fail(FE_ERR_CUDA, "validation word read-back");
+        return fe_mesh_orientation_status(word);
+    };
+    if (cap < nnz) {                                             // mesh errors come before buffer errors
+        if ((st = read_word())) return done(st);
         return done(fe_fail(FE_ERR_BUFFER_TOO_SMALL, "capacity " + std::to_string(cap) + " < nnz " + std::to_string(nnz)));
+    }
     if (nnz > 0 && (!col_idx || !S || !Mw)) return done(fe_fail(FE_ERR_INVALID_ARG, "col_idx, S or Mw is null"));
-    // 3. row_ptr first: its entries split the value downloads into row blocks
-    if (cudaMemcpyAsync(row_ptr, p->row_ptr, sizeof(int32_t) * ((size_t)nq + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return done(fe_fail(FE_ERR_CUDA, "row_ptr download"));
-    if (nnz == 0) return done(FE_OK);
-    // 4. the column indices go down while the values are computed
-    if (cudaMemcpyAsync(col_idx, p->col_idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s2) != cudaSuccess)
+    // 4. the column indices go down at once (the pattern is complete) while the coordinates are
+    //    packed and checked and the values computed
+    if (nnz > 0 && cudaMemcpyAsync(col_idx, p->col_idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s2) != cudaSuccess)
         return done(fe_fail(FE_ERR_CUDA, "col_idx download"));
-    // 5. values: vertex records, general rows, then the row blocks, each downloaded when done
+    // 5. row_ptr (its entries split the value downloads into row blocks) with the orientation
+    //    result; then the error word is cleared for the assembly's own flags
+    if (cudaMemcpyAsync(row_ptr, p->row_ptr, sizeof(int32_t) * ((size_t)nq + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return done(fe_fail(FE_ERR_CUDA, "row_ptr download"));
+    if ((st = read_word())) return done(st);
+    if (cudaMemsetAsync(m->err, 0, 4 * sizeof(int), s) != cudaSuccess) return done(fe_fail(FE_ERR_CUDA, "memset"));
+    if (nnz == 0) return done(FE_OK);
+    // 6. values: vertex records, general rows, then the row blocks, each downloaded when done
     if ((st = fe_alloc_n(&Sd, (size_t)nnz, "S values")) || (st = fe_alloc_n(&Md, (size_t)nnz, "Mw values")) ||
         (st = fe_alloc_n(&vr, (size_t)nq, "vertex records")))
         return done(st);
