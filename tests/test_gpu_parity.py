@@ -345,3 +345,20 @@ def test_end_to_end_host_call_errors():
     st = L.fe_assemble_stiff_wmass_host(m.nq, m.nme, q.ctypes.data, bad.ctypes.data, w.ctypes.data, rp.ctypes.data,
                                         ci.ctypes.data, S.ctypes.data, M.ctypes.data, n, ctypes.byref(nnz), None)
     assert st == 4                                                      # FE_ERR_ORIENTATION
+    # the connectivity is checked before the coordinates arrive: range and repeats
+    bad = me.copy()
+    bad[2, 5] = m.nq
+    st = L.fe_assemble_stiff_wmass_host(m.nq, m.nme, q.ctypes.data, bad.ctypes.data, w.ctypes.data, rp.ctypes.data,
+                                        ci.ctypes.data, S.ctypes.data, M.ctypes.data, n, ctypes.byref(nnz), None)
+    assert st == 2 and b"triangle 5" in L.fe_last_error()              # FE_ERR_INDEX_RANGE
+    bad = me.copy()
+    bad[1, 7] = bad[0, 7]
+    st = L.fe_assemble_stiff_wmass_host(m.nq, m.nme, q.ctypes.data, bad.ctypes.data, w.ctypes.data, rp.ctypes.data,
+                                        ci.ctypes.data, S.ctypes.data, M.ctypes.data, n, ctypes.byref(nnz), None)
+    assert st == 3 and b"triangle 7" in L.fe_last_error()              # FE_ERR_DEGENERATE
+    # an orientation error takes precedence over a buffer that is too small
+    bad = me.copy()
+    bad[1, 3], bad[2, 3] = bad[2, 3], bad[1, 3]
+    st = L.fe_assemble_stiff_wmass_host(m.nq, m.nme, q.ctypes.data, bad.ctypes.data, w.ctypes.data, rp.ctypes.data,
+                                        ci.ctypes.data, S.ctypes.data, M.ctypes.data, 8, ctypes.byref(nnz), None)
+    assert st == 4 and b"triangle 3" in L.fe_last_error()
