@@ -69,6 +69,12 @@ def lib() -> ctypes.CDLL:
         _lib.or_tet_assemble.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, P, I64, P, P]
         for f in ("or_tet_triplets", "or_tet_assemble"):
             getattr(_lib, f).restype = ctypes.c_int
+        _lib.or_p2_elem_mass.argtypes = [D, P]
+        _lib.or_p2_elem_stiff.argtypes = [P, P, D, P]
+        _lib.or_p2_triplets.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, P, P]
+        _lib.or_p2_assemble.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, I64, P, P, P]
+        for f in ("or_p2_triplets", "or_p2_assemble"):
+            getattr(_lib, f).restype = ctypes.c_int
         for f in ("or_triplets", "or_sparse", "or_assemble", "or_adjoint"):
             getattr(_lib, f).restype = ctypes.c_int
     return _lib
@@ -283,3 +289,61 @@ def tet_assemble(kind: int, q, me, w=None):
     if st:
         raise OracleError(st, f"tet_assemble (element {bad.value})")
     return row_ptr, col_idx[:nnz.value].copy(), val[:nnz.value].copy()
+
+
+# ------------------------------------------------------------------ P2 triangles
+
+def p2_elem_mass(area: float) -> np.ndarray:
+    E = np.empty(36)
+    lib().or_p2_elem_mass(area, _p(E))
+    return E.reshape(6, 6)
+
+
+def p2_elem_stiff(x, y, area: float) -> np.ndarray:
+    E = np.empty(36)
+    lib().or_p2_elem_stiff(_p(_f64(x)), _p(_f64(y)), area, _p(E))
+    return E.reshape(6, 6)
+
+
+def p2_triplets(kind: int, q, me):
+    """(Ig, Jg, Kg, ndof) of the P2 matrices, entry c = 36k + 6*jl + il; dofs: vertices, then edges
+    in ascending (smaller id, larger id) order."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    I = np.empty(36 * nme, np.int32)
+    J = np.empty_like(I)
+    K = np.empty(36 * nme)
+    ndof = ctypes.c_int64(0)
+    bad = ctypes.c_int64(-1)
+    st = lib().or_p2_triplets(kind, nq, nme, _p(q), _p(me), _p(I), _p(J), _p(K), ctypes.byref(ndof), ctypes.byref(bad))
+    if st:
+        raise OracleError(st, f"p2_triplets (element {bad.value})")
+    return I, J, K, ndof.value
+
+
+def p2_assemble(kind: int, q, me):
+    """Global P2 CSR (row_ptr, col_idx, val) of a triangle mesh (kind MASS or STIFF)."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    cap = max(36 * nme, 1)
+    row_ptr = np.empty(nq + 3 * nme + 1, np.int32)
+    col_idx = np.empty(cap, np.int32)
+    val = np.empty(cap)
+    nnz, ndof, bad = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(-1)
+    st = lib().or_p2_assemble(kind, nq, nme, _p(q), _p(me), _p(row_ptr), _p(col_idx), _p(val), cap,
+                              ctypes.byref(nnz), ctypes.byref(ndof), ctypes.byref(bad))
+    if st:
+        raise OracleError(st, f"p2_assemble (element {bad.value})")
+    return row_ptr[:ndof.value + 1].copy(), col_idx[:nnz.value].copy(), val[:nnz.value].copy()
+
+
+def p2_dof_values(q, me, f):
+    """f at the P2 dofs of a triangle mesh: the vertices, then the edge midpoints in the oracle's
+    edge order (for interpolating test functions)."""
+    q, me = _f64(q), _i32(me)
+    nq = q.shape[1]
+    e = np.sort(np.concatenate([me[[0, 1]], me[[1, 2]], me[[2, 0]]], axis=1), axis=0)
+    keys = np.unique((e[0].astype(np.int64) << 32) | e[1])
+    lo, hi = keys >> 32, keys & 0xFFFFFFFF
+    mid = 0.5 * (q[:, lo] + q[:, hi])
+    return np.concatenate([f(q[0], q[1]), f(mid[0], mid[1])])

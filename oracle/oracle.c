@@ -507,3 +507,199 @@ int or_tet_assemble(int kind, int64_t nq, int64_t nme, const double* q, const in
     free(I); free(J); free(K);
     return st;
 }
+
+/* ----------------------------------------------- P2 triangles (quadratic, 6 dofs) ---- */
+
+/* The paper states that the method extends to P_k elements and gives no formulas. These are the P2
+ * (quadratic) matrices on a triangle T with vertices p0, p1, p2, written from the definitions:
+ *   barycentric coordinates l0, l1, l2 (the P1 functions of Eq. (1)-(3); grad l_a as in Eq. (4));
+ *   local dofs 0, 1, 2: the vertex functions phi_a = l_a (2 l_a - 1);
+ *   local dofs 3, 4, 5: the edge functions 4 l0 l1, 4 l1 l2, 4 l2 l0 (midpoints of the edges
+ *   (0,1), (1,2), (2,0));
+ *   mass       M^e_ij = int_T phi_i phi_j
+ *   stiffness  S^e_ij = int_T grad phi_i . grad phi_j, grad phi = sum_k (d phi / d l_k) grad l_k
+ * with every polynomial in l0, l1, l2 integrated exactly:
+ *   int_T l0^a l1^b l2^c = 2|T| a! b! c! / (a + b + c + 2)!.
+ * Global dofs: vertex i is dof i; the edges follow, numbered in ascending order of their
+ * (smaller vertex id, larger vertex id). Element k writes c = 36k + 6*jl + il (column-wise). */
+
+#define P2_DEG 5      /* exponents 0..4 per barycentric coordinate */
+typedef struct { double c[P2_DEG][P2_DEG][P2_DEG]; } p2_poly;
+
+static void p2_zero(p2_poly* p) { memset(p, 0, sizeof *p); }
+
+static void p2_mul(const p2_poly* a, const p2_poly* b, p2_poly* out) {
+    p2_zero(out);
+    for (int i = 0; i < P2_DEG; i++)
+        for (int j = 0; j < P2_DEG - i; j++)
+            for (int k = 0; k < P2_DEG - i - j; k++) {
+                double x = a->c[i][j][k];
+                if (x == 0.0) continue;
+                for (int u = 0; u < P2_DEG - i; u++)
+                    for (int v = 0; v < P2_DEG - j; v++)
+                        for (int w = 0; w < P2_DEG - k; w++) {
+                            double y = b->c[u][v][w];
+                            if (y != 0.0 && i + u + j + v + k + w < P2_DEG) out->c[i + u][j + v][k + w] += x * y;
+                        }
+            }
+}
+
+/* d/d l_var */
+static void p2_diff(const p2_poly* a, int var, p2_poly* out) {
+    p2_zero(out);
+    for (int i = 0; i < P2_DEG; i++)
+        for (int j = 0; j < P2_DEG; j++)
+            for (int k = 0; k < P2_DEG; k++) {
+                double x = a->c[i][j][k];
+                if (x == 0.0) continue;
+                if (var == 0 && i > 0) out->c[i - 1][j][k] += i * x;
+                if (var == 1 && j > 0) out->c[i][j - 1][k] += j * x;
+                if (var == 2 && k > 0) out->c[i][j][k - 1] += k * x;
+            }
+}
+
+static double p2_fact(int n) { double f = 1.0; for (int i = 2; i <= n; i++) f *= i; return f; }
+
+static double p2_integrate(const p2_poly* a, double area) {
+    double s = 0.0;
+    for (int i = 0; i < P2_DEG; i++)
+        for (int j = 0; j < P2_DEG; j++)
+            for (int k = 0; k < P2_DEG; k++)
+                if (a->c[i][j][k] != 0.0)
+                    s += a->c[i][j][k] * 2.0 * area * p2_fact(i) * p2_fact(j) * p2_fact(k) / p2_fact(i + j + k + 2);
+    return s;
+}
+
+/* the six basis functions as polynomials in (l0, l1, l2) */
+static void p2_basis(p2_poly phi[6]) {
+    for (int a = 0; a < 6; a++) p2_zero(&phi[a]);
+    for (int a = 0; a < 3; a++) {
+        int e[3] = {0, 0, 0};
+        e[a] = 2;
+        phi[a].c[e[0]][e[1]][e[2]] += 2.0;           /* 2 l_a^2 */
+        e[a] = 1;
+        phi[a].c[e[0]][e[1]][e[2]] -= 1.0;           /* - l_a */
+    }
+    phi[3].c[1][1][0] = 4.0;                          /* 4 l0 l1 */
+    phi[4].c[0][1][1] = 4.0;                          /* 4 l1 l2 */
+    phi[5].c[1][0][1] = 4.0;                          /* 4 l2 l0 */
+}
+
+void or_p2_elem_mass(double area, double E[36]) {
+    p2_poly phi[6], prod;
+    p2_basis(phi);
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j < 6; j++) {
+            p2_mul(&phi[i], &phi[j], &prod);
+            E[6 * i + j] = p2_integrate(&prod, area);
+        }
+}
+
+void or_p2_elem_stiff(const double x[3], const double y[3], double area, double E[36]) {
+    double ex[3], ey[3];
+    edges(x, y, ex, ey);
+    double g[3][2];                                   /* grad l_a = (e_a,y, -e_a,x) / (2|T|), Eq. (4) */
+    for (int a = 0; a < 3; a++) {
+        g[a][0] = ey[a] / (2.0 * area);
+        g[a][1] = -ex[a] / (2.0 * area);
+    }
+    p2_poly phi[6], d[6][3], prod;
+    p2_basis(phi);
+    for (int i = 0; i < 6; i++)
+        for (int k = 0; k < 3; k++) p2_diff(&phi[i], k, &d[i][k]);
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j < 6; j++) {
+            double s = 0.0;
+            for (int k = 0; k < 3; k++)
+                for (int l = 0; l < 3; l++) {
+                    p2_mul(&d[i][k], &d[j][l], &prod);
+                    s += (g[k][0] * g[l][0] + g[k][1] * g[l][1]) * p2_integrate(&prod, area);
+                }
+            E[6 * i + j] = s;
+        }
+}
+
+static int cmp_i64(const void* a, const void* b) {
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return x < y ? -1 : x > y;
+}
+
+/* Edge keys (smaller id << 32 | larger id) of a triangle mesh, sorted and unique; returns their
+ * number (the caller frees *keys). */
+int64_t or_p2_edges(int64_t nq, int64_t nme, const int32_t* me, int64_t** keys_out) {
+    int64_t* keys = (int64_t*)malloc((size_t)(3 * nme > 0 ? 3 * nme : 1) * sizeof(int64_t));
+    if (!keys) return -1;
+    for (int64_t k = 0; k < nme; k++)
+        for (int a = 0; a < 3; a++) {
+            int64_t u = me[a * nme + k], v = me[((a + 1) % 3) * nme + k];
+            int64_t lo = u < v ? u : v, hi = u < v ? v : u;
+            keys[3 * k + a] = (lo << 32) | hi;
+        }
+    qsort(keys, (size_t)(3 * nme), sizeof(int64_t), cmp_i64);
+    int64_t n = 0;
+    for (int64_t t = 0; t < 3 * nme; t++)
+        if (n == 0 || keys[t] != keys[n - 1]) keys[n++] = keys[t];
+    (void)nq;
+    *keys_out = keys;
+    return n;
+}
+
+static int64_t p2_edge_id(const int64_t* keys, int64_t ne, int64_t u, int64_t v) {
+    int64_t key = ((u < v ? u : v) << 32) | (u < v ? v : u);
+    int64_t lo = 0, hi = ne - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (keys[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+/* Ig, Jg, Kg of the P2 matrices (OR_MASS or OR_STIFF) of a triangle mesh; *ndof = nq + edges. */
+int or_p2_triplets(int kind, int64_t nq, int64_t nme, const double* q, const int32_t* me, int32_t* I, int32_t* J,
+                   double* K, int64_t* ndof, int64_t* bad_element) {
+    if ((kind != OR_MASS && kind != OR_STIFF) || nq < 0 || nme < 0) return OR_ERR_ARG;
+    int64_t* keys = NULL;
+    int64_t ne = or_p2_edges(nq, nme, me, &keys);
+    if (ne < 0) return OR_ERR_NOMEM;
+    *ndof = nq + ne;
+    for (int64_t k = 0; k < nme; k++) {
+        int32_t v[3];
+        double x[3], y[3], E[36];
+        int st = gather_element(nq, q, nme, me, k, v, x, y);
+        if (st) { if (bad_element) *bad_element = k; free(keys); return st; }
+        double D = or_double_area(x, y);
+        if (!(D > 0.0)) { if (bad_element) *bad_element = k; free(keys); return OR_ERR_ORIENT; }
+        double area = D / 2.0;
+        if (kind == OR_MASS) or_p2_elem_mass(area, E);
+        else or_p2_elem_stiff(x, y, area, E);
+        int32_t dof[6] = {v[0], v[1], v[2], (int32_t)(nq + p2_edge_id(keys, ne, v[0], v[1])),
+                          (int32_t)(nq + p2_edge_id(keys, ne, v[1], v[2])), (int32_t)(nq + p2_edge_id(keys, ne, v[2], v[0]))};
+        for (int jl = 0; jl < 6; jl++)
+            for (int il = 0; il < 6; il++) {
+                int64_t c = 36 * k + 6 * jl + il;
+                I[c] = dof[il];
+                J[c] = dof[jl];
+                K[c] = E[6 * il + jl];
+            }
+    }
+    free(keys);
+    return OR_OK;
+}
+
+/* One full P2 assembly: triplets, then sparse(). row_ptr needs nq + 3 nme + 1 entries (an upper
+ * bound on ndof + 1); cap >= 36 nme always suffices. */
+int or_p2_assemble(int kind, int64_t nq, int64_t nme, const double* q, const int32_t* me, int32_t* row_ptr,
+                   int32_t* col_idx, double* val, int64_t cap, int64_t* nnz_out, int64_t* ndof_out,
+                   int64_t* bad_element) {
+    int64_t ntrip = 36 * nme;
+    int32_t* I = (int32_t*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(int32_t));
+    int32_t* J = (int32_t*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(int32_t));
+    double* K = (double*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(double));
+    int st = (I && J && K) ? OR_OK : OR_ERR_NOMEM;
+    int64_t ndof = nq;
+    if (!st) st = or_p2_triplets(kind, nq, nme, q, me, I, J, K, &ndof, bad_element);
+    if (!st) st = or_sparse(ndof, ndof, ntrip, I, J, K, row_ptr, col_idx, val, cap, nnz_out);
+    *ndof_out = ndof;
+    free(I); free(J); free(K);
+    return st;
+}
