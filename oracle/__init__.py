@@ -347,3 +347,43 @@ def p2_dof_values(q, me, f):
     lo, hi = keys >> 32, keys & 0xFFFFFFFF
     mid = 0.5 * (q[:, lo] + q[:, hi])
     return np.concatenate([f(q[0], q[1]), f(mid[0], mid[1])])
+
+
+def _p2_edge_keys(me):
+    """Sorted unique edge keys (smaller id << 32 | larger id): the edge numbering of the P2 dofs."""
+    e = np.sort(np.concatenate([me[[0, 1]], me[[1, 2]], me[[2, 0]]], axis=1), axis=0)
+    return np.unique((e[0].astype(np.int64) << 32) | e[1])
+
+
+def p2_row_values(kind: int, q, me, rows):
+    """Oracle values of selected P2 rows only, for meshes too large to assemble whole: the element
+    matrices of the triangles containing each row's dof (vertex, or both ends of the edge), summed
+    per column in ascending element order (the order of sparse() over c = 36k + 6 jl + il).
+    Returns a list of (cols, vals) in ascending column order."""
+    q, me = _f64(q), _i32(me)
+    nq = q.shape[1]
+    keys = _p2_edge_keys(me)
+    out = []
+    for r in rows:
+        r = int(r)
+        if r < nq:
+            ks = np.nonzero((me == r).any(axis=0))[0]
+        else:
+            lo, hi = int(keys[r - nq] >> 32), int(keys[r - nq] & 0xFFFFFFFF)
+            ks = np.nonzero((me == lo).any(axis=0) & (me == hi).any(axis=0))[0]
+        acc = {}
+        for k in ks:
+            v = [int(t) for t in me[:, k]]
+            x, y = q[0, v], q[1, v]
+            area = double_area(x, y) / 2
+            E = p2_elem_mass(area) if kind == MASS else p2_elem_stiff(x, y, area)
+            ek = [(min(v[a], v[(a + 1) % 3]) << 32) | max(v[a], v[(a + 1) % 3]) for a in range(3)]
+            dof = v + [nq + int(np.searchsorted(keys, key)) for key in ek]
+            for il in range(6):
+                if dof[il] != r:
+                    continue
+                for jl in range(6):
+                    acc[dof[jl]] = acc.get(dof[jl], 0.0) + E[il, jl]
+        cols = np.array(sorted(acc), dtype=np.int64)
+        out.append((cols, np.array([acc[c] for c in cols])))
+    return out

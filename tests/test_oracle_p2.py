@@ -116,3 +116,13 @@ def test_stiffness_identities(sq):
     w = oracle.p2_dof_values(m.q, m.me, lambda x, y: 2 * x - 3 * y)
     assert w @ S @ w == pytest.approx(13.0, rel=1e-12)                 # int |(2, -3)|^2
     np.testing.assert_allclose(S, S.T, rtol=0, atol=1e-12)
+
+
+def test_row_sampler_matches_full_assembly():
+    m = meshgen.square_mesh(7, 5)
+    for kind in (oracle.MASS, oracle.STIFF):
+        rp, ci, va = oracle.p2_assemble(kind, m.q, m.me)
+        rows = [0, 5, m.nq - 1, m.nq, m.nq + 17, len(rp) - 2]
+        for r, (cols, vals) in zip(rows, oracle.p2_row_values(kind, m.q, m.me, rows)):
+            np.testing.assert_array_equal(cols, ci[rp[r]:rp[r + 1]])
+            np.testing.assert_array_equal(vals, va[rp[r]:rp[r + 1]])
