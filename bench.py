@@ -350,6 +350,7 @@ def run_ours(args) -> int:
         line["adjoint"] = adjoint(feasm, meshgen, torch, flush)
         line["drop_zeros"] = drop_zeros(feasm, torch, pat0, S, flush, hbm, peak_kind, cells=args.cells)
         line["tetrahedra"] = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind)
+        line["p2"] = p2(feasm, meshgen, torch, flush, hbm, peak_kind)
     if not args.no_e2e:
         line["e2e"] = e2e(feasm, torch, m, w, args)
     if not args.no_cpu and world == 1:
@@ -530,6 +531,35 @@ def tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 128) -
                          "hbm_frac": round(nbytes / k_ms / 1e6 / hbm, 4), "hbm_peak_source": f"{peak_kind} HBM copy bandwidth"}}
 
 
+def p2(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 1024) -> dict:
+    """P2 (quadratic) triangles on the 1024 x 1024-cell square (jittered, node-permuted): the P2
+    pattern from the scalar one, and the mass and stiffness by FP64 atomics."""
+    seed = 13053122 + 7
+    m = meshgen.square_mesh(cells, seed)
+    mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))
+    pat = feasm.Pattern(mesh, map=False)
+    ms_pat = _time_calls(torch, lambda: feasm.P2Pattern(mesh, pat).close(), flush, reps=5)
+    p2p = feasm.P2Pattern(mesh, pat)
+    out = p2p.new_values()
+    ms_m = _time_calls(torch, lambda: feasm.p2_assemble(mesh, p2p, feasm.P2_MASS, out), flush)
+    ms_s = _time_calls(torch, lambda: feasm.p2_assemble(mesh, p2p, feasm.P2_STIFF, out), flush)
+    feasm.profile_reset()
+    feasm.profile_enable(True)
+    _time_calls(torch, lambda: feasm.p2_assemble(mesh, p2p, feasm.P2_STIFF, out), flush)
+    feasm.profile_enable(False)
+    prof = feasm.profile_read()
+    k_ms = prof["k_p2_atomic"][0] / prof["k_p2_atomic"][1]
+    nbytes = 12 * m.nme + 16 * m.nq + 144 * m.nme + 8 * p2p.nnz          # me, q, map, values
+    return {"workload": f"P2 M and S of the {cells}x{cells}-cell square (nq={m.nq}, edges={p2p.n_edges}, "
+                        f"dofs={p2p.n_rows}, nme={m.nme}, nnz={p2p.nnz})",
+            "pattern_ms": round(ms_pat, 4), "M_ms": round(ms_m, 4), "S_ms": round(ms_s, 4),
+            "S_melem_s": round(m.nme / ms_s / 1e3, 1), "k_p2_atomic_S_ms": round(k_ms, 4),
+            "roofline": {"kernel": "k_p2_atomic<S>", "bound": "hbm", "algorithmic_bytes": nbytes,
+                         "achieved": round(nbytes / k_ms / 1e6, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(nbytes / k_ms / 1e6 / hbm, 4), "peak_source": f"{peak_kind} HBM copy bandwidth",
+                         "note": "36 FP64 atomics per element into values zeroed first; the atomics, not DRAM, set the time"}}
+
+
 def adjoint(feasm, meshgen, torch, flush) -> dict:
     """dL/dq, dL/dw of L = <G_S, S> + <G_M, M^[w]> on the 1024 x 1024-cell mesh (deterministic gather)."""
     seed = 13053122 + 5
@@ -625,10 +655,10 @@ def main() -> int:
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-other", action="store_true", help="skip the elasticity, adjoint, zero-dropping and tetrahedra legs")
+    ap.add_argument("--no-other", action="store_true", help="skip the elasticity, adjoint, zero-dropping, tetrahedra and P2 legs")
     ap.add_argument("--traffic", default=os.path.join(ROOT, "profiles", "traffic.json"),
                     help="per-kernel DRAM bytes per launch from an ncu capture (JSON)")
-    ap.add_argument("--only", choices=["elasticity", "adjoint", "drop_zeros", "tetrahedra"],
+    ap.add_argument("--only", choices=["elasticity", "adjoint", "drop_zeros", "tetrahedra", "p2"],
                     help="run this one leg alone and print its object (for profiling; no headline step)")
     ap.add_argument("--tet-cells", type=int, default=128, help="cells per side of the tetrahedra leg's cube")
     args = ap.parse_args()
@@ -652,6 +682,8 @@ def run_leg(args) -> int:
         out = adjoint(feasm, meshgen, torch, flush)
     elif args.only == "tetrahedra":
         out = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind, cells=args.tet_cells)
+    elif args.only == "p2":
+        out = p2(feasm, meshgen, torch, flush, hbm, peak_kind)
     else:
         m = meshgen.square_mesh(args.cells, 13053122 + 2)
         mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))

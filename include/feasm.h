@@ -67,6 +67,7 @@ typedef struct fe_pattern_s* fe_pattern;  /* owns the CSR structure and element-
 typedef struct fe_batch_s* fe_batch;      /* a set of (mesh, pattern) assembled together */
 typedef struct fe_tet_mesh_s* fe_tet_mesh;       /* tetrahedral mesh: device q [3][nq], me [4][nme] */
 typedef struct fe_tet_pattern_s* fe_tet_pattern; /* CSR structure and map of a tetrahedral mesh */
+typedef struct fe_p2_pattern_s* fe_p2_pattern;   /* P2 dofs, CSR structure and map of a triangle mesh */
 
 /* Where the arrays passed to fe_mesh_create live. FE_PTR_DEVICE_BORROW: device memory, and the
  * mesh uses the caller's me in place instead of copying it (q is always packed into the mesh's
@@ -257,6 +258,35 @@ void fe_tet_pattern_destroy(fe_tet_pattern pattern);
  * pattern built with FE_PATTERN_GATHER). Element arithmetic in FP64. */
 fe_status fe_tet_assemble(fe_tet_mesh mesh, fe_tet_pattern pattern, int kind, const double* w, int variant,
                           double* values, int64_t cap, fe_stream stream);
+
+/* ------------------------------------------------------- P2 triangles (quadratic) ---- */
+
+/* The paper states that its method extends to P_k elements without giving the formulas. These
+ * calls assemble the P2 mass and stiffness of a triangle mesh from the definitions: with the
+ * barycentric coordinates l0, l1, l2 of a triangle (the P1 functions; grad l_a as in Eq. 4), the
+ * local dofs are the vertex functions l_a (2 l_a - 1) (a = 0, 1, 2) and the edge functions
+ * 4 l0 l1, 4 l1 l2, 4 l2 l0 (local dofs 3, 4, 5: the midpoints of edges (0,1), (1,2), (2,0));
+ * M^e_ij = int_T phi_i phi_j and S^e_ij = int_T grad phi_i . grad phi_j.
+ * Global dofs: vertex i is dof i; the nE edges are dofs nq .. nq + nE - 1, numbered in ascending
+ * order of (smaller vertex id, larger vertex id). The structure is the structural sum, as for
+ * P1. Assembly by FP64 element matrices and FP64 atomics (values zeroed first). */
+enum { FE_P2_MASS = 0, FE_P2_STIFF = 1 };
+
+/* Most triangles around one vertex for a P2 pattern (FE_ERR_LIMIT above it). */
+#define FE_P2_MAX_VALENCE 680
+
+/* Dofs, CSR structure and element-to-nnz map from a mesh and its scalar (dofs = 1) pattern, whose
+ * structure numbers the edges. Synchronises (the edge count, nnz). */
+fe_status fe_p2_pattern_build(fe_mesh mesh, fe_pattern scalar_pattern, fe_stream stream, fe_p2_pattern* out);
+fe_status fe_p2_pattern_info(fe_p2_pattern pattern, int64_t* n_dofs, int64_t* nnz, const int32_t** row_ptr,
+                             const int32_t** col_idx);
+/* edof (device, [nme][6] int32): each triangle's dofs in local order; map (device, 36 nme):
+ * map[36k + 6 il + jl] = position of (edof[k][il], edof[k][jl]); *n_edges = nE. */
+fe_status fe_p2_pattern_dofs(fe_p2_pattern pattern, const int32_t** edof, const int32_t** map, int64_t* n_edges);
+void fe_p2_pattern_destroy(fe_p2_pattern pattern);
+
+/* Values of FE_P2_MASS or FE_P2_STIFF into values[0 .. nnz) (device, capacity cap). */
+fe_status fe_p2_assemble(fe_mesh mesh, fe_p2_pattern pattern, int kind, double* values, int64_t cap, fe_stream stream);
 
 /* -------------------------------------------------------------------- zero dropping ---- */
 

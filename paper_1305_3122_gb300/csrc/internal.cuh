@@ -81,6 +81,20 @@ struct fe_tet_pattern_s {
     cudaStream_t last_stream = nullptr;
 };
 
+// P2 (quadratic) triangle patterns (p2.cu).
+struct fe_p2_pattern_s {
+    int32_t nq = 0, nme = 0;
+    int64_t ne = 0;                       // edges (dofs nq .. nq + ne - 1)
+    int32_t ndof = 0;
+    uint64_t topology_id = 0;
+    int64_t nnz = 0;
+    int32_t* row_ptr = nullptr;           // [ndof + 1]
+    int32_t* col_idx = nullptr;           // [nnz]
+    int32_t* edof = nullptr;              // [nme][6] element dofs (vertices, then edges (0,1), (1,2), (2,0))
+    int32_t* map = nullptr;               // [36 nme] map[36k + 6 il + jl] = position of (edof[k][il], edof[k][jl])
+    cudaStream_t last_stream = nullptr;
+};
+
 uint64_t fe_next_topology_id();
 
 // Staged mesh creation for the one-shot host call (mesh.cu): the connectivity (device array,

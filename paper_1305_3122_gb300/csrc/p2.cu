@@ -1,0 +1,434 @@
+// p2.cu -- P2 (quadratic) triangles: dof numbering, CSR structure and the mass and stiffness.
+//
+// The paper states that its method extends to P_k elements and gives no formulas. The P2 element
+// has the three vertex functions phi_a = l_a (2 l_a - 1) (local dofs 0, 1, 2) and the three edge
+// functions 4 l0 l1, 4 l1 l2, 4 l2 l0 (local dofs 3, 4, 5: the midpoints of the edges (0,1), (1,2),
+// (2,0)), with l_a the barycentric coordinates (the P1 functions) and G_kl = grad l_k . grad l_l
+// (grad l_a as in Eq. (4)). Integrating the products with int_T l_i l_j = |T| (1 + delta_ij) / 12
+// and friends gives, for vertices a != b, c the third vertex, and edges (a,b), (c,d):
+//   M^e = |T|/180 [[6 -1 -1 0 -4 0] [-1 6 -1 0 0 -4] [-1 -1 6 -4 0 0]
+//                  [0 0 -4 32 16 16] [-4 0 0 16 32 16] [0 -4 0 16 16 32]]
+//   S_aa = |T| G_aa,  S_ab = -|T| G_ab / 3,
+//   S(vertex a, edge (a,c)) = 4/3 |T| G_ac,  S(vertex a, the opposite edge) = 0,
+//   S(edge (a,b), edge (c,d)) = 16 (G_ac I_bd + G_ad I_bc + G_bc I_ad + G_bd I_ac),  I_ij = |T| (1 + delta_ij) / 12.
+//
+// Dofs: vertex i is dof i; the edges follow, numbered in ascending order of (smaller vertex id,
+// larger vertex id). Those are the entries above the diagonal of the scalar (P1) pattern in CSR
+// order, so an edge's id is its rank among them: per row the number of entries right of the
+// diagonal, a scan, and a binary search of the other vertex in the smaller vertex's row.
+//
+// Pattern: every element couples its six dofs. The incidences (element k, local dof a) are bucketed
+// by dof with a counting sort; one warp per row merges the dofs of the row's elements in a
+// shared-memory hash table (rowhash.cuh), ranks them (the sorted columns) and writes each
+// incidence's six in-row positions: the element-to-nnz map, row-major per element
+// (map[36k + 6 il + jl]), made absolute once the offsets are known. Assembly: one thread per
+// element, FP64, 36 FP64 atomics.
+#include "internal.cuh"
+#include "rowhash.cuh"
+
+namespace {
+
+constexpr int P2_BLOCK = 256;
+constexpr int P2_WARPS = 4;
+constexpr int FAST_TS = 128, FAST_EMAX = 21;             // 6 * 21 ids < 128
+constexpr int BIG_TS = 4096, BIG_EMAX = FE_P2_MAX_VALENCE;
+static_assert(6 * FAST_EMAX < FAST_TS && 6 * BIG_EMAX < BIG_TS, "tables hold every id");
+
+// Entries right of the diagonal in each scalar row (0 for an empty row), and the diagonal's place.
+__global__ void k_p2_upper(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t nq,
+                           int32_t* __restrict__ ucnt, int32_t* __restrict__ dpos) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = (int32_t)r, b = row_ptr[i], n = row_ptr[i + 1] - b;
+        int lo = 0, hi = n;                                   // first column >= i
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (col_idx[b + mid] < i) lo = mid + 1;
+            else hi = mid;
+        }
+        dpos[i] = lo;
+        ucnt[i] = n > 0 ? n - lo - 1 : 0;
+    }
+}
+
+__device__ __forceinline__ int32_t p2_edge(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                                           const int32_t* __restrict__ eoff, const int32_t* __restrict__ dpos,
+                                           int32_t u, int32_t v) {
+    const int32_t a = min(u, v), c = max(u, v);
+    const int32_t b = row_ptr[a];
+    int lo = dpos[a] + 1, hi = row_ptr[a + 1] - b - 1;        // c lies right of the diagonal
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (col_idx[b + mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return eoff[a] + (lo - dpos[a] - 1);
+}
+
+// edof[6k .. 6k+5]: the element's dofs; also counts each dof's elements.
+__global__ void k_p2_edof(const int32_t* __restrict__ me, int32_t nme, int32_t nq, const int32_t* __restrict__ row_ptr,
+                          const int32_t* __restrict__ col_idx, const int32_t* __restrict__ eoff,
+                          const int32_t* __restrict__ dpos, int32_t* __restrict__ edof, int32_t* __restrict__ deg) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v0 = me[k], v1 = me[nme + k], v2 = me[2 * (int64_t)nme + k];
+        int32_t d[6] = {v0, v1, v2, nq + p2_edge(row_ptr, col_idx, eoff, dpos, v0, v1),
+                        nq + p2_edge(row_ptr, col_idx, eoff, dpos, v1, v2), nq + p2_edge(row_ptr, col_idx, eoff, dpos, v2, v0)};
+        int2* o = reinterpret_cast<int2*>(edof + 6 * k);
+        o[0] = make_int2(d[0], d[1]);
+        o[1] = make_int2(d[2], d[3]);
+        o[2] = make_int2(d[4], d[5]);
+#pragma unroll
+        for (int a = 0; a < 6; a++) atomicAdd(&deg[d[a]], 1);
+    }
+}
+
+__global__ void k_p2_fill(const int32_t* __restrict__ edof, int32_t nme, int32_t* __restrict__ cur,
+                          int32_t* __restrict__ inc) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 6; a++) inc[atomicAdd(&cur[edof[6 * k + a]], 1)] = 6 * (int32_t)k + a;
+    }
+}
+
+template <int TS, int EMAX>
+struct P2Smem {
+    int32_t tab[TS];
+    int32_t rnk[TS];
+    int32_t uid[TS];
+    int32_t uslot[TS];
+    int32_t key[EMAX];
+    int32_t ucount;
+};
+
+// One row by one warp: sorted distinct columns into tmp at 6 vptr[r] (each incidence brings at
+// most six), their count, and the six relative positions of every incidence in map.
+template <int TS, int EMAX>
+__device__ void p2_row(int32_t r, int32_t beg, int32_t d, const int32_t* __restrict__ inc, const int32_t* __restrict__ edof,
+                       P2Smem<TS, EMAX>& sm, int32_t* __restrict__ tmp, int32_t* __restrict__ cnt,
+                       int32_t* __restrict__ map) {
+    const int lane = threadIdx.x & 31;
+    for (int s = lane; s < TS; s += 32) sm.tab[s] = -1;
+    if (lane == 0) sm.ucount = 0;
+    for (int t = lane; t < d; t += 32) sm.key[t] = inc[beg + t];
+    __syncwarp();
+    for (int x = lane; x < 6 * d; x += 32) {
+        const int32_t id = edof[6 * (int64_t)(sm.key[x / 6] / 6) + x % 6];
+        bool fresh;
+        const int s = tab_insert<TS>(sm.tab, id, &fresh);
+        if (fresh) {
+            const int p = atomicAdd(&sm.ucount, 1);
+            sm.uid[p] = id;
+            sm.uslot[p] = s;
+        }
+    }
+    __syncwarp();
+    const int u = sm.ucount;
+    const int64_t tb = 6 * (int64_t)beg;
+    for (int p = lane; p < u; p += 32) {
+        const int32_t id = sm.uid[p];
+        int rk = 0;
+        for (int qq = 0; qq < u; qq++) rk += sm.uid[qq] < id;
+        sm.rnk[sm.uslot[p]] = rk;
+        tmp[tb + rk] = id;
+    }
+    __syncwarp();
+    for (int t = lane; t < d; t += 32) {
+        const int32_t kk = sm.key[t] / 6, a = sm.key[t] - 6 * (sm.key[t] / 6);
+        const int32_t* e = edof + 6 * (int64_t)kk;
+        int32_t* o = map + 36 * (int64_t)kk + 6 * a;
+#pragma unroll
+        for (int jl = 0; jl < 6; jl++) o[jl] = sm.rnk[tab_find<TS>(sm.tab, e[jl])];
+    }
+    if (lane == 0) cnt[r] = u;
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(P2_WARPS * 32) k_p2_rows(const int32_t* __restrict__ vptr, const int32_t* __restrict__ inc,
+                                                           const int32_t* __restrict__ edof, int32_t ndof,
+                                                           int32_t* __restrict__ tmp, int32_t* __restrict__ cnt,
+                                                           int32_t* __restrict__ map, int32_t* __restrict__ big_list,
+                                                           int32_t* __restrict__ big_count) {
+    __shared__ P2Smem<FAST_TS, FAST_EMAX> sm_all[P2_WARPS];
+    P2Smem<FAST_TS, FAST_EMAX>& sm = sm_all[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    for (int64_t rr = (int64_t)blockIdx.x * P2_WARPS + (threadIdx.x >> 5); rr < ndof; rr += (int64_t)gridDim.x * P2_WARPS) {
+        const int32_t r = (int32_t)rr, beg = vptr[r], d = vptr[r + 1] - beg;
+        if (d == 0) {
+            if (lane == 0) cnt[r] = 0;
+            continue;
+        }
+        if (d > FAST_EMAX) {
+            if (lane == 0) big_list[atomicAdd(big_count, 1)] = r;
+            continue;
+        }
+        p2_row<FAST_TS, FAST_EMAX>(r, beg, d, inc, edof, sm, tmp, cnt, map);
+    }
+}
+
+__global__ void __launch_bounds__(32) k_p2_rows_big(const int32_t* __restrict__ vptr, const int32_t* __restrict__ inc,
+                                                    const int32_t* __restrict__ edof, const int32_t* __restrict__ big_list,
+                                                    const int32_t* __restrict__ big_count, int32_t* __restrict__ tmp,
+                                                    int32_t* __restrict__ cnt, int32_t* __restrict__ map,
+                                                    int* __restrict__ too_big) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    P2Smem<BIG_TS, BIG_EMAX>& sm = *reinterpret_cast<P2Smem<BIG_TS, BIG_EMAX>*>(smem_raw);
+    const int32_t n = *big_count;
+    for (int32_t b = blockIdx.x; b < n; b += gridDim.x) {
+        const int32_t r = big_list[b], beg = vptr[r], d = vptr[r + 1] - beg;
+        if (d > BIG_EMAX) {
+            if (threadIdx.x == 0) {
+                *too_big = 1;
+                cnt[r] = 0;
+            }
+            continue;
+        }
+        p2_row<BIG_TS, BIG_EMAX>(r, beg, d, inc, edof, sm, tmp, cnt, map);
+    }
+}
+
+__global__ void __launch_bounds__(P2_BLOCK) k_p2_cols(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
+                                                      int32_t ndof, const int32_t* __restrict__ tmp, int32_t* __restrict__ col_idx) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (P2_BLOCK / 32);
+    for (int64_t rr = (int64_t)blockIdx.x * (P2_BLOCK / 32) + (threadIdx.x >> 5); rr < ndof; rr += nwarps) {
+        const int32_t r = (int32_t)rr, rb = row_ptr[r], u = row_ptr[r + 1] - rb;
+        const int64_t tb = 6 * (int64_t)vptr[r];
+        for (int c = lane; c < u; c += 32) col_idx[rb + c] = tmp[tb + c];
+    }
+}
+
+__global__ void k_p2_map_base(const int32_t* __restrict__ edof, int32_t nme, const int32_t* __restrict__ row_ptr,
+                              int32_t* __restrict__ map) {
+    const int64_t n = 36 * (int64_t)nme;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = c / 36;
+        const int il = (int)((c - 36 * k) / 6);
+        map[c] += row_ptr[edof[6 * k + il]];
+    }
+}
+
+// ------------------------------------------------------------------ element matrices
+
+template <int KIND>
+__device__ __forceinline__ void p2_elem(double2 p0, double2 p1, double2 p2, double E[6][6]) {
+    // e_a = the edge opposite vertex a (Eq. 3's u, v, w); D = 2|T|; grad l_a = (e_a,y, -e_a,x) / D
+    const double ex[3] = {p1.x - p2.x, p2.x - p0.x, p0.x - p1.x};
+    const double ey[3] = {p1.y - p2.y, p2.y - p0.y, p0.y - p1.y};
+    const double D = ex[1] * ey[2] - ex[2] * ey[1];
+    const double T = 0.5 * D;
+    if (KIND == FE_P2_MASS) {
+        const double m = T / 180.0;
+        const double a = 6.0 * m, b = -m, c = -4.0 * m, d = 32.0 * m, e = 16.0 * m;
+        const double tbl[6][6] = {{a, b, b, 0.0, c, 0.0}, {b, a, b, 0.0, 0.0, c}, {b, b, a, c, 0.0, 0.0},
+                                  {0.0, 0.0, c, d, e, e}, {c, 0.0, 0.0, e, d, e}, {0.0, c, 0.0, e, e, d}};
+#pragma unroll
+        for (int i = 0; i < 6; i++)
+#pragma unroll
+            for (int j = 0; j < 6; j++) E[i][j] = tbl[i][j];
+        return;
+    }
+    // T G_kl = T (e_k . e_l) / D^2 = (e_k . e_l) / (2 D)
+    const double s = 0.5 / D;
+    double G[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int l = k; l < 3; l++) {
+            G[k][l] = (ex[k] * ex[l] + ey[k] * ey[l]) * s;
+            G[l][k] = G[k][l];
+        }
+    const int ea[3] = {0, 1, 2}, eb[3] = {1, 2, 0};            // edge dof 3 + t joins vertices ea[t], eb[t]
+    // vertices
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) E[a][b] = a == b ? G[a][a] : -G[a][b] / 3.0;
+    // vertex - edge: 4/3 T G_ac for the edge (a, c), 0 for the opposite edge
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int t = 0; t < 3; t++) {
+            double v = 0.0;
+            if (ea[t] == a) v = 4.0 / 3.0 * G[a][eb[t]];
+            else if (eb[t] == a) v = 4.0 / 3.0 * G[a][ea[t]];
+            E[a][3 + t] = v;
+            E[3 + t][a] = v;
+        }
+    // edge - edge: 16 (G_ac I_bd + G_ad I_bc + G_bc I_ad + G_bd I_ac), T I_ij = T (1 + delta_ij) / 12
+#pragma unroll
+    for (int t = 0; t < 3; t++)
+#pragma unroll
+        for (int u = t; u < 3; u++) {
+            const int a = ea[t], b = eb[t], c = ea[u], d = eb[u];
+            const double Ibd = (b == d ? 2.0 : 1.0) / 12.0, Ibc = (b == c ? 2.0 : 1.0) / 12.0;
+            const double Iad = (a == d ? 2.0 : 1.0) / 12.0, Iac = (a == c ? 2.0 : 1.0) / 12.0;
+            const double v = 16.0 * (G[a][c] * Ibd + G[a][d] * Ibc + G[b][c] * Iad + G[b][d] * Iac);
+            E[3 + t][3 + u] = v;
+            E[3 + u][3 + t] = v;
+        }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(P2_BLOCK) k_p2_atomic(const int32_t* __restrict__ me, int32_t nme, const double2* __restrict__ q,
+                                                        const int32_t* __restrict__ map, double* __restrict__ val) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
+        double E[6][6];
+        p2_elem<KIND>(q[me[k]], q[me[nme + k]], q[me[2 * (int64_t)nme + k]], E);
+        const int32_t* mk = map + 36 * k;
+#pragma unroll
+        for (int il = 0; il < 6; il++)
+#pragma unroll
+            for (int jl = 0; jl < 6; jl++) atomicAdd(&val[mk[6 * il + jl]], E[il][jl]);
+    }
+}
+
+}  // namespace
+
+extern "C" void fe_p2_pattern_destroy(fe_p2_pattern p) {
+    if (!p) return;
+    FeStreamScope scope(p->last_stream);
+    fe_free(p->row_ptr); fe_free(p->col_idx); fe_free(p->map); fe_free(p->edof);
+    delete p;
+}
+
+namespace {
+struct P2Temps {
+    int32_t *ucnt = nullptr, *dpos = nullptr, *eoff = nullptr, *deg = nullptr, *vptr = nullptr, *cur = nullptr;
+    int32_t *inc = nullptr, *cnt = nullptr, *tmp = nullptr, *big = nullptr, *counters = nullptr;
+    ~P2Temps() {
+        fe_free(ucnt); fe_free(dpos); fe_free(eoff); fe_free(deg); fe_free(vptr); fe_free(cur);
+        fe_free(inc); fe_free(cnt); fe_free(tmp); fe_free(big); fe_free(counters);
+    }
+};
+}  // namespace
+
+extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, fe_stream stream, fe_p2_pattern* out) {
+    if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    fe_status st;
+    if ((st = fe_check_pair(m, p1, 1))) return st;
+    const int32_t nq = m->nq, nme = m->nme;
+    if (36 * (int64_t)nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "36*nme must be < 2^31");
+    cudaStream_t s = (cudaStream_t)stream;
+    FeStreamScope scope(s);
+    fe_p2_pattern p = new fe_p2_pattern_s();
+    p->nq = nq;
+    p->nme = nme;
+    p->topology_id = m->topology_id;
+    p->last_stream = s;
+    P2Temps t;
+    auto fail = [&](fe_status e) {
+        cudaStreamSynchronize(s);
+        fe_p2_pattern_destroy(p);
+        return e;
+    };
+    // edges: rank of each entry right of the diagonal of the scalar pattern
+    if ((st = fe_alloc_n(&t.ucnt, (size_t)nq + 1, "upper counts"))) return fail(st);
+    if ((st = fe_alloc_n(&t.dpos, (size_t)nq + 1, "diagonal places"))) return fail(st);
+    if ((st = fe_alloc_n(&t.eoff, (size_t)nq + 1, "edge offsets"))) return fail(st);
+    if (nq > 0) {
+        { FE_PROF("k_p2_upper", s); k_p2_upper<<<fe_grid(nq, P2_BLOCK), P2_BLOCK, 0, s>>>(p1->row_ptr, p1->col_idx, nq, t.ucnt, t.dpos); }
+        FE_LAUNCHED("k_p2_upper");
+    }
+    int64_t ne = 0;
+    if ((st = fe_exclusive_scan(t.ucnt, t.eoff, nq, s, &ne))) return fail(st);          // synchronises
+    if ((int64_t)nq + ne >= INT32_MAX) return fail(fe_fail(FE_ERR_LIMIT, "too many P2 dofs"));
+    const int32_t ndof = (int32_t)(nq + ne);
+    p->ne = ne;
+    p->ndof = ndof;
+    // element dofs and the dofs' element counts
+    if ((st = fe_alloc_n(&p->edof, 6 * (size_t)nme, "element dofs"))) return fail(st);
+    if ((st = fe_alloc_n(&t.deg, (size_t)ndof + 1, "dof valences"))) return fail(st);
+    if (cudaMemsetAsync(t.deg, 0, sizeof(int32_t) * ((size_t)ndof + 1), s) != cudaSuccess) return fail(fe_fail(FE_ERR_CUDA, "memset"));
+    if (nme > 0) {
+        { FE_PROF("k_p2_edof", s); k_p2_edof<<<fe_grid(nme, P2_BLOCK, 16), P2_BLOCK, 0, s>>>(m->me, nme, nq, p1->row_ptr, p1->col_idx, t.eoff, t.dpos, p->edof, t.deg); }
+        FE_LAUNCHED("k_p2_edof");
+    }
+    if ((st = fe_alloc_n(&t.vptr, (size_t)ndof + 1, "dof pointers"))) return fail(st);
+    if ((st = fe_alloc_n(&t.cur, (size_t)ndof + 1, "bucket cursors"))) return fail(st);
+    if ((st = fe_exclusive_scan(t.deg, t.vptr, ndof, s, nullptr, 1, t.cur))) return fail(st);
+    if ((st = fe_alloc_n(&t.inc, 6 * (size_t)nme, "dof incidences"))) return fail(st);
+    if (nme > 0) {
+        { FE_PROF("k_p2_fill", s); k_p2_fill<<<fe_grid(nme, P2_BLOCK, 16), P2_BLOCK, 0, s>>>(p->edof, nme, t.cur, t.inc); }
+        FE_LAUNCHED("k_p2_fill");
+    }
+    // rows
+    if ((st = fe_alloc_n(&t.cnt, (size_t)ndof + 1, "row counts"))) return fail(st);
+    if ((st = fe_alloc_n(&t.tmp, 36 * (size_t)nme + 1, "row columns"))) return fail(st);
+    if ((st = fe_alloc_n(&t.big, (size_t)ndof + 1, "long rows"))) return fail(st);
+    if ((st = fe_alloc_n(&t.counters, 4, "counters"))) return fail(st);
+    if ((st = fe_alloc_n(&p->map, 36 * (size_t)nme, "element-to-nnz map"))) return fail(st);
+    if (cudaMemsetAsync(t.counters, 0, 4 * sizeof(int32_t), s) != cudaSuccess) return fail(fe_fail(FE_ERR_CUDA, "memset"));
+    if (ndof > 0) {
+        { FE_PROF("k_p2_rows", s); k_p2_rows<<<fe_grid(((int64_t)ndof + P2_WARPS - 1) / P2_WARPS, 1, 12), P2_WARPS * 32, 0, s>>>(
+              t.vptr, t.inc, p->edof, ndof, t.tmp, t.cnt, p->map, t.big, t.counters); }
+        FE_LAUNCHED("k_p2_rows");
+        const size_t big_smem = sizeof(P2Smem<BIG_TS, BIG_EMAX>);
+        FE_CUDA(cudaFuncSetAttribute(k_p2_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem));
+        { FE_PROF("k_p2_rows_big", s); k_p2_rows_big<<<fe_sm_count(), 32, big_smem, s>>>(t.vptr, t.inc, p->edof, t.big, t.counters,
+                                                                                          t.tmp, t.cnt, p->map, t.counters + 1); }
+        FE_LAUNCHED("k_p2_rows_big");
+    }
+    if ((st = fe_alloc_n(&p->row_ptr, (size_t)ndof + 1, "row_ptr"))) return fail(st);
+    int64_t nnz = 0;
+    if ((st = fe_exclusive_scan(t.cnt, p->row_ptr, ndof, s, &nnz))) return fail(st);   // synchronises
+    int too_big = 0;
+    if (cudaMemcpyAsync(&too_big, t.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(fe_fail(FE_ERR_CUDA, "flag read-back"));
+    if (too_big)
+        return fail(fe_fail(FE_ERR_LIMIT, "a vertex belongs to more than FE_P2_MAX_VALENCE=" +
+                                              std::to_string(FE_P2_MAX_VALENCE) + " triangles"));
+    p->nnz = nnz;
+    if ((st = fe_alloc_n(&p->col_idx, (size_t)nnz, "col_idx"))) return fail(st);
+    if (ndof > 0) {
+        { FE_PROF("k_p2_cols", s); k_p2_cols<<<fe_grid(((int64_t)ndof + 7) / 8, 1, 8), P2_BLOCK, 0, s>>>(t.vptr, p->row_ptr, ndof, t.tmp, p->col_idx); }
+        FE_LAUNCHED("k_p2_cols");
+    }
+    if (nme > 0) {
+        { FE_PROF("k_p2_map_base", s); k_p2_map_base<<<fe_grid(36 * (int64_t)nme, P2_BLOCK), P2_BLOCK, 0, s>>>(p->edof, nme, p->row_ptr, p->map); }
+        FE_LAUNCHED("k_p2_map_base");
+    }
+    *out = p;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_p2_pattern_info(fe_p2_pattern p, int64_t* n_dofs, int64_t* nnz, const int32_t** row_ptr,
+                                        const int32_t** col_idx) {
+    if (!p) return fe_fail(FE_ERR_INVALID_ARG, "null pattern");
+    if (n_dofs) *n_dofs = p->ndof;
+    if (nnz) *nnz = p->nnz;
+    if (row_ptr) *row_ptr = p->row_ptr;
+    if (col_idx) *col_idx = p->col_idx;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_p2_pattern_dofs(fe_p2_pattern p, const int32_t** edof, const int32_t** map, int64_t* n_edges) {
+    if (!p) return fe_fail(FE_ERR_INVALID_ARG, "null pattern");
+    if (edof) *edof = p->edof;
+    if (map) *map = p->map;
+    if (n_edges) *n_edges = p->ne;
+    return FE_OK;
+}
+
+extern "C" fe_status fe_p2_assemble(fe_mesh m, fe_p2_pattern p, int kind, double* values, int64_t cap, fe_stream stream) {
+    if (!m || !p) return fe_fail(FE_ERR_INVALID_ARG, "null mesh or pattern");
+    if (m->topology_id != p->topology_id) return fe_fail(FE_ERR_INVALID_ARG, "the pattern was built for another mesh");
+    if (kind != FE_P2_MASS && kind != FE_P2_STIFF) return fe_fail(FE_ERR_INVALID_ARG, "unknown kind");
+    if (cap < p->nnz) return fe_fail(FE_ERR_BUFFER_TOO_SMALL, "cap is below nnz");
+    if (!values && p->nnz > 0) return fe_fail(FE_ERR_INVALID_ARG, "values is null");
+    cudaStream_t s = (cudaStream_t)stream;
+    FeStreamScope scope(s);
+    m->last_stream = s;
+    p->last_stream = s;
+    if (p->nnz == 0) return FE_OK;
+    FE_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * (size_t)p->nnz, s));
+    const int32_t nme = m->nme;
+    if (nme > 0) {
+        FE_PROF("k_p2_atomic", s);
+        const unsigned g = fe_grid(nme, P2_BLOCK, 8);
+        if (kind == FE_P2_MASS) k_p2_atomic<FE_P2_MASS><<<g, P2_BLOCK, 0, s>>>(m->me, nme, m->q, p->map, values);
+        else k_p2_atomic<FE_P2_STIFF><<<g, P2_BLOCK, 0, s>>>(m->me, nme, m->q, p->map, values);
+    }
+    FE_LAUNCHED("k_p2_atomic");
+    return FE_OK;
+}

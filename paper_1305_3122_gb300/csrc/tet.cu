@@ -21,6 +21,7 @@
 // at 4 * vptr[i] before any offset is known.
 #include "ff.cuh"
 #include "internal.cuh"
+#include "rowhash.cuh"
 
 namespace {
 
@@ -127,36 +128,6 @@ struct RowSmem {
     int4 e[EMAX];        // the row's bucket records
     int32_t ucount;
 };
-
-__device__ __forceinline__ uint32_t tet_hash(int32_t id) { return (uint32_t)id * 0x9E3779B1u; }
-
-// Slot of id (inserted if absent); *fresh tells whether this call inserted it. The table always
-// has a free slot (TS > the row's distinct ids), so the probe ends within TS steps.
-template <int TS>
-__device__ __forceinline__ int tab_insert(int32_t* tab, int32_t id, bool* fresh) {
-    constexpr int SH = 32 - (TS == 128 ? 7 : 12);
-    static_assert(TS == 128 || TS == 4096, "table sizes");
-    int s = (int)(tet_hash(id) >> SH);
-    for (int step = 0; step < TS; step++) {
-        int32_t old = atomicCAS(&tab[s], -1, id);
-        if (old == -1) { *fresh = true; return s; }
-        if (old == id) { *fresh = false; return s; }
-        s = (s + 1) & (TS - 1);
-    }
-    *fresh = false;
-    return 0;    // not reached: the table is never full
-}
-
-template <int TS>
-__device__ __forceinline__ int tab_find(const int32_t* tab, int32_t id) {
-    constexpr int SH = 32 - (TS == 128 ? 7 : 12);
-    int s = (int)(tet_hash(id) >> SH);
-    for (int step = 0; step < TS; step++) {
-        if (tab[s] == id) return s;
-        s = (s + 1) & (TS - 1);
-    }
-    return 0;    // not reached: every id looked up was inserted
-}
 
 // One row by one warp: distinct columns (sorted, into tmp at 3 vptr[i] + i), their count, the
 // relative map of every incidence, and (GATHER) the within-row segment starts (into tmp2) and the

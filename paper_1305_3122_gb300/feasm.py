@@ -55,6 +55,11 @@ SIGNATURES = {
     "fe_tet_pattern_map": (_INT, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
     "fe_tet_pattern_destroy": (None, [_P]),
     "fe_tet_assemble": (_INT, [_P, _P, _INT, _P, _INT, _P, _I64, _P]),
+    "fe_p2_pattern_build": (_INT, [_P, _P, _P, ctypes.POINTER(_P)]),
+    "fe_p2_pattern_info": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "fe_p2_pattern_dofs": (_INT, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
+    "fe_p2_pattern_destroy": (None, [_P]),
+    "fe_p2_assemble": (_INT, [_P, _P, _INT, _P, _I64, _P]),
     "fe_assemble_stiff_wmass_host": (_INT, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "fe_batch_create": (_INT, [_I32, _P, _P, ctypes.POINTER(_P)]),
     "fe_batch_tune": (_INT, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
@@ -332,6 +337,58 @@ def tet_assemble(mesh: TetMesh, pattern: TetPattern, kind: int, w: torch.Tensor 
         raise ValueError("out must be a contiguous float64 CUDA tensor")
     _check(lib().fe_tet_assemble(mesh.handle, pattern.handle, kind, _dptr(w, torch.float64, "w"), variant,
                                  out.data_ptr(), out.numel(), _stream(stream)), "fe_tet_assemble")
+    return out
+
+
+P2_MASS, P2_STIFF = 0, 1
+
+
+class P2Pattern:
+    """P2 (quadratic) dofs, CSR structure and map of a triangle mesh (fe_p2_pattern_build): vertex i
+    is dof i, the edges follow in ascending (smaller id, larger id) order. Built from the mesh's
+    scalar pattern, whose structure numbers the edges."""
+
+    def __init__(self, mesh: Mesh, pattern: Pattern, stream=None):
+        h = _P()
+        _check(lib().fe_p2_pattern_build(mesh.handle, pattern.handle, _stream(stream), ctypes.byref(h)),
+               "fe_p2_pattern_build")
+        self._h = h
+        self.mesh = mesh
+        n, nnz, rp, ci = _I64(), _I64(), _P(), _P()
+        _check(lib().fe_p2_pattern_info(h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci)),
+               "fe_p2_pattern_info")
+        self.n_rows, self.nnz = n.value, nnz.value
+        self.row_ptr = _view_i32(rp.value, self.n_rows + 1, self)
+        self.col_idx = _view_i32(ci.value, self.nnz, self)
+        ed, mp, ne = _P(), _P(), _I64()
+        _check(lib().fe_p2_pattern_dofs(h, ctypes.byref(ed), ctypes.byref(mp), ctypes.byref(ne)), "fe_p2_pattern_dofs")
+        self.n_edges = ne.value
+        self.edof = _view_i32(ed.value, 6 * mesh.nme, self)
+        self.map = _view_i32(mp.value, 36 * mesh.nme, self)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def new_values(self) -> torch.Tensor:
+        return torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fe_p2_pattern_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def p2_assemble(mesh: Mesh, pattern: P2Pattern, kind: int, out=None, stream=None) -> torch.Tensor:
+    """Values of the P2 mass (P2_MASS) or stiffness (P2_STIFF) on the P2 pattern (fe_p2_assemble)."""
+    out = pattern.new_values() if out is None else out
+    if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 CUDA tensor")
+    _check(lib().fe_p2_assemble(mesh.handle, pattern.handle, kind, out.data_ptr(), out.numel(), _stream(stream)),
+           "fe_p2_assemble")
     return out
 
 

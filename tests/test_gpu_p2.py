@@ -1,0 +1,120 @@
+"""P2 (quadratic) triangles through the C ABI against the oracle.
+
+Dof numbering, row_ptr / col_idx and the element map are compared bit-exactly, values within 1e-13
+of each row's largest |a_ij|. Meshes: jittered node-permuted squares (several warps and blocks), a
+fan whose centre belongs to 70 triangles (the long-row kernel), the one- and two-triangle meshes,
+and the 1024 x 1024-cell square at full size on sampled rows.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1305_3122_gb300 import feasm, meshgen
+from tests.gpu_common import assert_csr_equal, assert_values_close
+from tests.test_gpu_parity import fan_mesh
+
+pytestmark = pytest.mark.gpu
+
+KINDS = {"mass": (feasm.P2_MASS, oracle.MASS), "stiff": (feasm.P2_STIFF, oracle.STIFF)}
+
+
+def _cases():
+    out = {}
+    for N, seed in ((1, 1), (5, 2), (37, 3)):
+        m = meshgen.square_mesh(N, seed)
+        out[f"square{N}"] = (m.q, m.me)
+    out["fan70"] = fan_mesh(70)
+    q2 = np.array([[0.0, 1.0, 1.0, 0.0], [0.0, 0.0, 1.0, 1.0]])
+    me2 = np.array([[0, 0], [1, 2], [2, 3]], np.int32)
+    out["two"] = (q2, me2)
+    out["one"] = (q2, me2[:, :1].copy())
+    return out
+
+
+CASES = _cases()
+
+
+def _build(q, me):
+    mesh = feasm.Mesh(q, me)
+    pat = feasm.Pattern(mesh)
+    return mesh, feasm.P2Pattern(mesh, pat), pat
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_p2_dofs_pattern_and_map(case):
+    q, me = CASES[case]
+    mesh, p2, _ = _build(q, me)
+    I, J, K, ndof = oracle.p2_triplets(oracle.MASS, q, me)
+    assert p2.n_rows == ndof
+    nme = me.shape[1]
+    edof = p2.edof.cpu().numpy().reshape(nme, 6)
+    np.testing.assert_array_equal(edof, I.reshape(nme, 36)[:, :6])        # c = 36k + il (jl = 0)
+    rp, ci, _ = oracle.p2_assemble(oracle.MASS, q, me)
+    assert_csr_equal(p2.row_ptr.cpu(), p2.col_idx.cpu(), rp, ci)
+    mp = p2.map.cpu().numpy().reshape(nme, 6, 6)
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    np.testing.assert_array_equal(rows[mp], edof[:, :, None].repeat(6, axis=2))
+    np.testing.assert_array_equal(ci[mp], edof[:, None, :].repeat(6, axis=1))
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("kind", sorted(KINDS))
+def test_p2_values(case, kind):
+    q, me = CASES[case]
+    mesh, p2, _ = _build(q, me)
+    kg, ko = KINDS[kind]
+    got = feasm.p2_assemble(mesh, p2, kg)
+    rp, ci, va = oracle.p2_assemble(ko, q, me)
+    assert_values_close(rp, got.cpu().numpy(), va)
+
+
+def test_p2_quadratic_energy():
+    """u^T S u = int |grad u|^2 and u^T M u = int u^2 for u = x y, interpolated exactly by P2."""
+    m = meshgen.square_mesh(50, 6)
+    mesh, p2, _ = _build(m.q, m.me)
+    u = torch.tensor(oracle.p2_dof_values(m.q, m.me, lambda x, y: x * y), device="cuda")
+    for kind, want in ((feasm.P2_STIFF, 2.0 / 3.0), (feasm.P2_MASS, 1.0 / 9.0)):
+        A = torch.sparse_csr_tensor(p2.row_ptr.long(), p2.col_idx.long(), feasm.p2_assemble(mesh, p2, kind),
+                                    size=(p2.n_rows, p2.n_rows))
+        assert float(u @ (A @ u)) == pytest.approx(want, rel=1e-12)
+
+
+def test_p2_errors():
+    m = meshgen.square_mesh(4, 1)
+    mesh, p2, pat = _build(m.q, m.me)
+    other = feasm.Mesh(m.q, m.me)
+    with pytest.raises(feasm.FeasmError):
+        feasm.P2Pattern(other, pat)                       # pattern of another mesh
+    with pytest.raises(feasm.FeasmError):
+        feasm.p2_assemble(other, p2, feasm.P2_STIFF)
+    with pytest.raises(feasm.FeasmError):
+        feasm.p2_assemble(mesh, p2, 9)
+    with pytest.raises(feasm.FeasmError) as e:
+        feasm.p2_assemble(mesh, p2, feasm.P2_MASS, out=torch.empty(p2.nnz - 1, dtype=torch.float64, device="cuda"))
+    assert e.value.status == 5
+    pat2 = feasm.Pattern(mesh, dofs=2, map=False)
+    with pytest.raises(feasm.FeasmError):
+        feasm.P2Pattern(mesh, pat2)                       # needs the scalar pattern
+
+
+def test_p2_full_size_sampled_rows():
+    """1024 x 1024 cells (1,050,625 vertices, 3,147,776 edges, 2,097,152 triangles): sampled vertex
+    and edge rows of M and S against the oracle's triplets."""
+    seed = 13053122 + 7
+    m = meshgen.square_mesh(1024, seed)
+    mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))
+    pat = feasm.Pattern(mesh, map=False)
+    p2 = feasm.P2Pattern(mesh, pat)
+    assert p2.n_rows == m.nq + 3 * 1024 * 1024 + 2 * 1024
+    rows = np.concatenate([meshgen.sample_indices(seed, 6, m.nq), m.nq + meshgen.sample_indices(seed + 1, 6, p2.n_edges)])
+    rp = p2.row_ptr.cpu().numpy()
+    ci = p2.col_idx.cpu().numpy()
+    for kg, ko in KINDS.values():
+        got = feasm.p2_assemble(mesh, p2, kg).cpu().numpy()
+        want = oracle.p2_row_values(ko, m.q, m.me, rows)
+        for r, (cols, vals) in zip(rows, want):
+            np.testing.assert_array_equal(ci[rp[r]:rp[r + 1]], cols)
+            assert np.abs(got[rp[r]:rp[r + 1]] - vals).max() <= 1e-13 * np.abs(vals).max()
