@@ -24,52 +24,100 @@ enum { BAD_RANGE = 1, BAD_REPEAT = 2, BAD_ORIENT = 4 };
 // coordinates; its pass assumes ids already checked).
 enum { VAL_TOPOLOGY = 1, VAL_ORIENT = 2 };
 
-// Every triangle: vertex ids in range, three distinct vertices, counter-clockwise. The sign of
-// D = (p1 - p0) x (p2 - p0) is first taken from truncated-float coordinates; the float result is
+// Sign of D = (p1 - p0) x (p2 - p0) > 0, first from truncated-float coordinates; the float result is
 // trusted when it exceeds a bound on its error (coordinate truncation 2^-23 |p|, float rounding of
 // the differences and products), otherwise D is recomputed in FP64 from edge vectors
-// v = p2 - p0, w = p0 - p1 as the oracle does. Also counts each vertex's triangles (the row digit
-// of the pattern build's counting sort), so a pattern build can skip that pass.
+// v = p2 - p0, w = p0 - p1 as the oracle does.
+__device__ __forceinline__ bool tri_positive(double2 p0, double2 p1, double2 p2) {
+    float x0 = fe_trunc_float(p0.x), y0 = fe_trunc_float(p0.y);
+    float ax = fe_trunc_float(p1.x) - x0, ay = fe_trunc_float(p1.y) - y0;
+    float bx = fe_trunc_float(p2.x) - x0, by = fe_trunc_float(p2.y) - y0;
+    float Df = ax * by - ay * bx;
+    float M = fmaxf(fmaxf(fmaxf(fabsf(x0), fabsf(y0)), fmaxf(fabsf(ax), fabsf(ay))), fmaxf(fabsf(bx), fabsf(by)));
+    float err = 3.0e-6f * M * (fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by));   // > 2^-19 bound
+    if (fabsf(Df) > err && M < 1e18f && M > 1e-18f) return Df > 0.0f;
+    double vx = p2.x - p0.x, vy = p2.y - p0.y, wx = p0.x - p1.x, wy = p0.y - p1.y;
+    return vx * wy - wx * vy > 0.0;
+}
+
+__device__ __forceinline__ void report(int* __restrict__ word, int bad, int64_t k) {
+    if (bad) {
+        atomicOr(&word[0], bad);
+        atomicMin(&word[bad == BAD_RANGE ? 1 : bad == BAD_REPEAT ? 2 : 3], (int)k);
+    }
+}
+
+// Every triangle: vertex ids in range, three distinct vertices, counter-clockwise (tri_positive).
+// Also counts each vertex's triangles (the row digit of the pattern build's counting sort), so a
+// pattern build can skip that pass. One thread takes two consecutive triangles: a vertex they share
+// (mesh generators list neighbouring triangles together; the two triangles of a cell share two) is
+// counted with one atomic and its coordinates are loaded once. Every triangle's checks and report
+// are its own.
 __global__ void k_validate(const double2* __restrict__ q, int32_t nq, const int32_t* __restrict__ me,
                            int32_t nme, int* __restrict__ word, int32_t* __restrict__ deg, int mode) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
-        int32_t v0 = me[k], v1 = me[nme + k], v2 = me[2 * (int64_t)nme + k];
-        int bad = 0;
-        if (v0 < 0 || v0 >= nq || v1 < 0 || v1 >= nq || v2 < 0 || v2 >= nq) {
-            if (mode & VAL_TOPOLOGY) bad = BAD_RANGE;
-        } else {
-            if (mode & VAL_TOPOLOGY) {
-                atomicAdd(&deg[v0], 1);
-                atomicAdd(&deg[v1], 1);
-                atomicAdd(&deg[v2], 1);
-            }
-            if (v0 == v1 || v1 == v2 || v0 == v2) {
-                if (mode & VAL_TOPOLOGY) bad = BAD_REPEAT;
-            } else if (mode & VAL_ORIENT) {
-                double2 p0 = q[v0], p1 = q[v1], p2 = q[v2];
-                float x0 = fe_trunc_float(p0.x), y0 = fe_trunc_float(p0.y);
-                float ax = fe_trunc_float(p1.x) - x0, ay = fe_trunc_float(p1.y) - y0;
-                float bx = fe_trunc_float(p2.x) - x0, by = fe_trunc_float(p2.y) - y0;
-                float Df = ax * by - ay * bx;
-                float M = fmaxf(fmaxf(fmaxf(fabsf(x0), fabsf(y0)), fmaxf(fabsf(ax), fabsf(ay))),
-                                fmaxf(fabsf(bx), fabsf(by)));
-                float err = 3.0e-6f * M * (fabsf(ax) + fabsf(ay) + fabsf(bx) + fabsf(by));   // > 2^-19 bound
-                bool sure = fabsf(Df) > err && M < 1e18f && M > 1e-18f;
-                bool pos;
-                if (sure) {
-                    pos = Df > 0.0f;
-                } else {
-                    double vx = p2.x - p0.x, vy = p2.y - p0.y, wx = p0.x - p1.x, wy = p0.y - p1.y;
-                    pos = vx * wy - wx * vy > 0.0;
+    const int64_t npair = ((int64_t)nme + 1) / 2;
+    for (int64_t pi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pi < npair; pi += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k0 = 2 * pi, k1 = k0 + 1;
+        const bool has1 = k1 < nme;
+        int32_t v[3], u[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            v[a] = me[a * (int64_t)nme + k0];
+            u[a] = has1 ? me[a * (int64_t)nme + k1] : 0;
+        }
+        const bool in0 = v[0] >= 0 && v[0] < nq && v[1] >= 0 && v[1] < nq && v[2] >= 0 && v[2] < nq;
+        const bool in1 = has1 && u[0] >= 0 && u[0] < nq && u[1] >= 0 && u[1] < nq && u[2] >= 0 && u[2] < nq;
+        // m[b]: the vertex of the first triangle equal to u[b] (-1: none, or not both in range)
+        int m[3] = {-1, -1, -1};
+        if (in0 && in1) {
+#pragma unroll
+            for (int b = 0; b < 3; b++)
+#pragma unroll
+                for (int a = 2; a >= 0; a--)
+                    if (u[b] == v[a]) m[b] = a;
+        }
+        if (mode & VAL_TOPOLOGY) {
+            if (in0) {
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const int c = 1 + (m[0] == a) + (m[1] == a) + (m[2] == a);
+                    atomicAdd(&deg[v[a]], c);
                 }
-                if (!pos) bad = BAD_ORIENT;
+            }
+            if (in1) {
+#pragma unroll
+                for (int b = 0; b < 3; b++)
+                    if (m[b] < 0) atomicAdd(&deg[u[b]], 1);
             }
         }
-        if (bad) {
-            atomicOr(&word[0], bad);
-            int slot = bad == BAD_RANGE ? 1 : bad == BAD_REPEAT ? 2 : 3;
-            atomicMin(&word[slot], (int)k);
+        const bool rep0 = v[0] == v[1] || v[1] == v[2] || v[0] == v[2];
+        const bool rep1 = u[0] == u[1] || u[1] == u[2] || u[0] == u[2];
+        int bad0 = 0, bad1 = 0;
+        if (!in0) bad0 = (mode & VAL_TOPOLOGY) ? BAD_RANGE : 0;
+        else if (rep0) bad0 = (mode & VAL_TOPOLOGY) ? BAD_REPEAT : 0;
+        if (has1) {
+            if (!in1) bad1 = (mode & VAL_TOPOLOGY) ? BAD_RANGE : 0;
+            else if (rep1) bad1 = (mode & VAL_TOPOLOGY) ? BAD_REPEAT : 0;
         }
+        if (mode & VAL_ORIENT) {
+            double2 pv[3], pu[3];
+            const bool o0 = in0 && !rep0, o1 = in1 && !rep1;
+            if (o0 || (in0 && in1)) {
+#pragma unroll
+                for (int a = 0; a < 3; a++) pv[a] = q[v[a]];
+            }
+            if (o1) {
+#pragma unroll
+                for (int b = 0; b < 3; b++) {                     // conditional selects: no local memory
+                    if (m[b] < 0) pu[b] = q[u[b]];
+                    else pu[b] = m[b] == 0 ? pv[0] : (m[b] == 1 ? pv[1] : pv[2]);
+                }
+            }
+            if (o0 && !tri_positive(pv[0], pv[1], pv[2])) bad0 = BAD_ORIENT;
+            if (o1 && !tri_positive(pu[0], pu[1], pu[2])) bad1 = BAD_ORIENT;
+        }
+        report(word, bad0, k0);
+        if (has1) report(word, bad1, k1);
     }
 }
 
@@ -149,7 +197,7 @@ extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, co
     if (e == cudaSuccess) e = cudaMemsetAsync(m->err + 1, 0x7F, 3 * sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->deg, 0, sizeof(int32_t) * ((size_t)nq + 1), s);
     if (e == cudaSuccess && nme > 0) {
-        { FE_PROF("k_validate", s); k_validate<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg, VAL_TOPOLOGY | VAL_ORIENT); }
+        { FE_PROF("k_validate", s); k_validate<<<fe_grid(((int64_t)nme + 1) / 2, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg, VAL_TOPOLOGY | VAL_ORIENT); }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(word, m->err, sizeof word, cudaMemcpyDeviceToHost, s);
@@ -199,7 +247,7 @@ fe_status fe_mesh_create_topology(int32_t nq, int32_t nme, int32_t* me_dev, cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(m->err + 1, 0x7F, 3 * sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->deg, 0, sizeof(int32_t) * ((size_t)nq + 1), s);
     if (e == cudaSuccess && nme > 0) {
-        { FE_PROF("k_validate", s); k_validate<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg, VAL_TOPOLOGY); }
+        { FE_PROF("k_validate", s); k_validate<<<fe_grid(((int64_t)nme + 1) / 2, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg, VAL_TOPOLOGY); }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(word, m->err, sizeof word, cudaMemcpyDeviceToHost, s);
@@ -224,7 +272,7 @@ fe_status fe_mesh_attach_coords(fe_mesh m, const double* q_dev, cudaStream_t s) 
     if (e == cudaSuccess) e = cudaMemsetAsync(m->err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->err + 1, 0x7F, 3 * sizeof(int), s);
     if (e == cudaSuccess && nme > 0) {
-        { FE_PROF("k_validate", s); k_validate<<<fe_grid(nme, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg, VAL_ORIENT); }
+        { FE_PROF("k_validate", s); k_validate<<<fe_grid(((int64_t)nme + 1) / 2, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg, VAL_ORIENT); }
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return fe_cuda_fail(e, "orientation check");
