@@ -18,9 +18,10 @@
 // diagonal, a scan, and a binary search of the other vertex in the smaller vertex's row.
 //
 // Pattern: every element couples its six dofs. The incidences (element k, local dof a) are bucketed
-// by dof with a counting sort; one warp per row merges the dofs of the row's elements in a
-// shared-memory hash table (rowhash.cuh), ranks them (the sorted columns) and writes each
-// incidence's six in-row positions: the element-to-nnz map, row-major per element
+// by dof with a counting sort; one warp per vertex row merges the dofs of the row's elements in a
+// shared-memory hash table (rowhash.cuh), and one thread per edge row (at most two elements) sorts
+// its at most 12 ids in registers; either ranks the distinct ids (the sorted columns) and writes
+// each incidence's six in-row positions: the element-to-nnz map, row-major per element
 // (map[36k + 6 il + jl]), made absolute once the offsets are known. Assembly: one thread per
 // element, FP64, 36 FP64 atomics.
 #include "internal.cuh"
@@ -143,14 +144,14 @@ __device__ void p2_row(int32_t r, int32_t beg, int32_t d, const int32_t* __restr
 }
 
 __global__ void __launch_bounds__(P2_WARPS * 32) k_p2_rows(const int32_t* __restrict__ vptr, const int32_t* __restrict__ inc,
-                                                           const int32_t* __restrict__ edof, int32_t ndof,
+                                                           const int32_t* __restrict__ edof, int32_t nrows,
                                                            int32_t* __restrict__ tmp, int32_t* __restrict__ cnt,
                                                            int32_t* __restrict__ map, int32_t* __restrict__ big_list,
                                                            int32_t* __restrict__ big_count) {
     __shared__ P2Smem<FAST_TS, FAST_EMAX> sm_all[P2_WARPS];
     P2Smem<FAST_TS, FAST_EMAX>& sm = sm_all[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    for (int64_t rr = (int64_t)blockIdx.x * P2_WARPS + (threadIdx.x >> 5); rr < ndof; rr += (int64_t)gridDim.x * P2_WARPS) {
+    for (int64_t rr = (int64_t)blockIdx.x * P2_WARPS + (threadIdx.x >> 5); rr < nrows; rr += (int64_t)gridDim.x * P2_WARPS) {
         const int32_t r = (int32_t)rr, beg = vptr[r], d = vptr[r + 1] - beg;
         if (d == 0) {
             if (lane == 0) cnt[r] = 0;
@@ -161,6 +162,62 @@ __global__ void __launch_bounds__(P2_WARPS * 32) k_p2_rows(const int32_t* __rest
             continue;
         }
         p2_row<FAST_TS, FAST_EMAX>(r, beg, d, inc, edof, sm, tmp, cnt, map);
+    }
+}
+
+// Edge rows (dofs nq .. ndof - 1), one thread each: an edge lies in at most two triangles of a
+// manifold mesh, so its row merges at most 12 ids, sorted in registers (a fixed compare-exchange
+// sequence: static indices only); the rank of a value is the number of distinct smaller ones.
+// Rows with more elements go to the long-row list.
+__global__ void __launch_bounds__(P2_BLOCK) k_p2_edge_rows(const int32_t* __restrict__ vptr, const int32_t* __restrict__ inc,
+                                                           const int32_t* __restrict__ edof, int32_t nq, int32_t ndof,
+                                                           int32_t* __restrict__ tmp, int32_t* __restrict__ cnt,
+                                                           int32_t* __restrict__ map, int32_t* __restrict__ big_list,
+                                                           int32_t* __restrict__ big_count) {
+    for (int64_t rr = nq + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < ndof; rr += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = (int32_t)rr, beg = vptr[r], d = vptr[r + 1] - beg;
+        if (d > 2) {
+            big_list[atomicAdd(big_count, 1)] = r;
+            continue;
+        }
+        int32_t key[2] = {d > 0 ? inc[beg] : -1, d > 1 ? inc[beg + 1] : -1};
+        int32_t x[12];
+#pragma unroll
+        for (int t = 0; t < 2; t++)
+#pragma unroll
+            for (int j = 0; j < 6; j++) x[6 * t + j] = key[t] >= 0 ? edof[6 * (int64_t)(key[t] / 6) + j] : INT32_MAX;
+#pragma unroll
+        for (int i = 1; i < 12; i++)
+#pragma unroll
+            for (int j = i; j > 0; j--) {
+                const int32_t lo = min(x[j - 1], x[j]), hi = max(x[j - 1], x[j]);
+                x[j - 1] = lo;
+                x[j] = hi;
+            }
+        const int64_t tb = 6 * (int64_t)beg;
+        int u = 0;
+#pragma unroll
+        for (int i = 0; i < 12; i++) {
+            const bool first = x[i] != INT32_MAX && (i == 0 || x[i] != x[i - 1]);
+            if (first) tmp[tb + u] = x[i];
+            u += first;
+        }
+        cnt[r] = u;
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            if (key[t] < 0) continue;
+            const int32_t kk = key[t] / 6, a = key[t] - 6 * kk;
+            const int32_t* e = edof + 6 * (int64_t)kk;
+            int32_t* o = map + 36 * (int64_t)kk + 6 * a;
+#pragma unroll
+            for (int jl = 0; jl < 6; jl++) {
+                const int32_t v = e[jl];
+                int rank = 0;
+#pragma unroll
+                for (int i = 0; i < 12; i++) rank += x[i] < v && (i == 0 || x[i] != x[i - 1]);
+                o[jl] = rank;
+            }
+        }
     }
 }
 
@@ -185,14 +242,13 @@ __global__ void __launch_bounds__(32) k_p2_rows_big(const int32_t* __restrict__ 
     }
 }
 
+// One thread per row (rows are short: many rows in flight hide the latency of each).
 __global__ void __launch_bounds__(P2_BLOCK) k_p2_cols(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
                                                       int32_t ndof, const int32_t* __restrict__ tmp, int32_t* __restrict__ col_idx) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (P2_BLOCK / 32);
-    for (int64_t rr = (int64_t)blockIdx.x * (P2_BLOCK / 32) + (threadIdx.x >> 5); rr < ndof; rr += nwarps) {
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < ndof; rr += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = (int32_t)rr, rb = row_ptr[r], u = row_ptr[r + 1] - rb;
         const int64_t tb = 6 * (int64_t)vptr[r];
-        for (int c = lane; c < u; c += 32) col_idx[rb + c] = tmp[tb + c];
+        for (int c = 0; c < u; c++) col_idx[rb + c] = tmp[tb + c];
     }
 }
 
@@ -359,9 +415,16 @@ extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, fe_stream str
     if ((st = fe_alloc_n(&p->map, 36 * (size_t)nme, "element-to-nnz map"))) return fail(st);
     if (cudaMemsetAsync(t.counters, 0, 4 * sizeof(int32_t), s) != cudaSuccess) return fail(fe_fail(FE_ERR_CUDA, "memset"));
     if (ndof > 0) {
-        { FE_PROF("k_p2_rows", s); k_p2_rows<<<fe_grid(((int64_t)ndof + P2_WARPS - 1) / P2_WARPS, 1, 12), P2_WARPS * 32, 0, s>>>(
-              t.vptr, t.inc, p->edof, ndof, t.tmp, t.cnt, p->map, t.big, t.counters); }
-        FE_LAUNCHED("k_p2_rows");
+        if (nq > 0) {
+            { FE_PROF("k_p2_rows", s); k_p2_rows<<<fe_grid(((int64_t)nq + P2_WARPS - 1) / P2_WARPS, 1, 12), P2_WARPS * 32, 0, s>>>(
+                  t.vptr, t.inc, p->edof, nq, t.tmp, t.cnt, p->map, t.big, t.counters); }
+            FE_LAUNCHED("k_p2_rows");
+        }
+        if (ndof > nq) {
+            { FE_PROF("k_p2_edge_rows", s); k_p2_edge_rows<<<fe_grid((int64_t)ndof - nq, P2_BLOCK, 8), P2_BLOCK, 0, s>>>(
+                  t.vptr, t.inc, p->edof, nq, ndof, t.tmp, t.cnt, p->map, t.big, t.counters); }
+            FE_LAUNCHED("k_p2_edge_rows");
+        }
         const size_t big_smem = sizeof(P2Smem<BIG_TS, BIG_EMAX>);
         FE_CUDA(cudaFuncSetAttribute(k_p2_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem));
         { FE_PROF("k_p2_rows_big", s); k_p2_rows_big<<<fe_sm_count(), 32, big_smem, s>>>(t.vptr, t.inc, p->edof, t.big, t.counters,
@@ -381,7 +444,7 @@ extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, fe_stream str
     p->nnz = nnz;
     if ((st = fe_alloc_n(&p->col_idx, (size_t)nnz, "col_idx"))) return fail(st);
     if (ndof > 0) {
-        { FE_PROF("k_p2_cols", s); k_p2_cols<<<fe_grid(((int64_t)ndof + 7) / 8, 1, 8), P2_BLOCK, 0, s>>>(t.vptr, p->row_ptr, ndof, t.tmp, p->col_idx); }
+        { FE_PROF("k_p2_cols", s); k_p2_cols<<<fe_grid(ndof, P2_BLOCK, 8), P2_BLOCK, 0, s>>>(t.vptr, p->row_ptr, ndof, t.tmp, p->col_idx); }
         FE_LAUNCHED("k_p2_cols");
     }
     if (nme > 0) {
