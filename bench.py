@@ -389,13 +389,24 @@ def recorded_traffic(name: str, cells: int, traffic_path: str | None):
     return rec.get("bytes")
 
 
+# What limits a kernel below its HBM roof, from its ncu captures (profiles/).
+LIMITS = {
+    "k_fan_scalar": "instruction issue: double-float arithmetic on the FP32 and integer pipes (issue slots 61% busy "
+                    "at 1024^2, profiles/k_fan_scalar_1024.md); at 2048^2 also the random vertex-record gathers, "
+                    "which miss L2 (traffic above)",
+}
+
+
 def _roofline(name, nbytes, ms, hbm, peak_kind, traffic_path, cells=N_CELLS):
     achieved = nbytes / (ms / 1e3) / 1e9 if nbytes else None
     traffic = recorded_traffic(name, cells, traffic_path)
-    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
-            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
-            "traffic": traffic, "algorithmic_bytes": nbytes, "ms_per_launch": round(ms, 5),
-            "peak_source": f"{peak_kind} HBM copy bandwidth"}
+    out = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+           "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
+           "traffic": traffic, "algorithmic_bytes": nbytes, "ms_per_launch": round(ms, 5),
+           "peak_source": f"{peak_kind} HBM copy bandwidth"}
+    if name in LIMITS:
+        out["limit"] = LIMITS[name]
+    return out
 
 
 def assemble_only(feasm, torch, mesh, pat, w_d, variant, S, M, flush, stream, args, m, nnz, hbm, peak_kind):
