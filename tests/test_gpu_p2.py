@@ -82,6 +82,25 @@ def test_p2_quadratic_energy():
         assert float(u @ (A @ u)) == pytest.approx(want, rel=1e-12)
 
 
+def test_p2_empty_mesh_and_isolated_vertex():
+    """No triangle: the P2 dofs are the vertices alone and every row is empty. A vertex in no
+    triangle keeps an empty row next to a meshed one."""
+    q = np.zeros((2, 5))
+    mesh = feasm.Mesh(q, np.zeros((3, 0), np.int32))
+    p2 = feasm.P2Pattern(mesh, feasm.Pattern(mesh))
+    assert p2.n_rows == 5 and p2.nnz == 0 and p2.n_edges == 0
+    assert p2.row_ptr.cpu().tolist() == [0] * 6
+    assert feasm.p2_assemble(mesh, p2, feasm.P2_STIFF).numel() == 0
+    q = np.array([[0.0, 1.0, 0.0, 5.0], [0.0, 0.0, 1.0, 5.0]])           # vertex 3 in no triangle
+    me = np.array([[0], [1], [2]], np.int32)
+    mesh = feasm.Mesh(q, me)
+    p2 = feasm.P2Pattern(mesh, feasm.Pattern(mesh))
+    rp, ci, va = oracle.p2_assemble(oracle.STIFF, q, me)
+    assert_csr_equal(p2.row_ptr.cpu(), p2.col_idx.cpu(), rp, ci)
+    assert rp[4] - rp[3] == 0
+    assert_values_close(rp, feasm.p2_assemble(mesh, p2, feasm.P2_STIFF).cpu().numpy(), va)
+
+
 def test_p2_errors():
     m = meshgen.square_mesh(4, 1)
     mesh, p2, pat = _build(m.q, m.me)
