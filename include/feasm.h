@@ -241,8 +241,9 @@ fe_status fe_tet_mesh_create(int32_t nq, int32_t nme, const double* q, const int
 void fe_tet_mesh_destroy(fe_tet_mesh mesh);
 
 /* CSR structure (columns ascending in each row) and the element-to-nnz map of a tetrahedral mesh.
- * flags: FE_PATTERN_GATHER adds the per-non-zero contribution lists and the staging buffer of
- * FE_VARIANT_GATHER (other bits are ignored; the map is always built). Synchronises once (nnz). */
+ * flags: FE_PATTERN_GATHER adds what FE_VARIANT_GATHER needs: each row's incidences in ascending
+ * element order with the in-row positions of their columns, and the staging buffer (other bits
+ * are ignored; the map is always built). Synchronises once (nnz). */
 fe_status fe_tet_pattern_build(fe_tet_mesh mesh, int flags, fe_stream stream, fe_tet_pattern* out);
 fe_status fe_tet_pattern_info(fe_tet_pattern pattern, int64_t* n_rows, int64_t* nnz, const int32_t** row_ptr,
                               const int32_t** col_idx);
@@ -253,9 +254,10 @@ void fe_tet_pattern_destroy(fe_tet_pattern pattern);
 
 /* Values of one matrix kind (FE_TET_MASS, FE_TET_WMASS with w[nq] device FP64, FE_TET_STIFF) on
  * the pattern's structure, into values[0 .. nnz) (device, capacity cap). variant: FE_VARIANT_ATOMIC
- * (FP64 atomicAdd after zeroing) or FE_VARIANT_GATHER (element values staged, then each non-zero
- * sums its contributions in ascending element order: bit-identical from run to run; needs a
- * pattern built with FE_PATTERN_GATHER). Element arithmetic in FP64. */
+ * (FP64 atomicAdd after zeroing) or FE_VARIANT_GATHER (element values staged, then each row sums
+ * its incidences' element rows, so that each non-zero adds its contributions in ascending element
+ * order: bit-identical from run to run; needs a pattern built with FE_PATTERN_GATHER). Element
+ * arithmetic in FP64. */
 fe_status fe_tet_assemble(fe_tet_mesh mesh, fe_tet_pattern pattern, int kind, const double* w, int variant,
                           double* values, int64_t cap, fe_stream stream);
 

@@ -75,9 +75,14 @@ struct fe_tet_pattern_s {
     int32_t* row_ptr = nullptr;           // [nq + 1]
     int32_t* col_idx = nullptr;           // [nnz]
     int32_t* map = nullptr;               // [16 nme]: map[16k + 4 il + jl] = position of (me[il][k], me[jl][k])
-    int32_t* seg_ptr = nullptr;           // [nnz + 1] into perm (FE_PATTERN_GATHER)
-    int32_t* perm = nullptr;              // [16 nme] staging indices 16k + 4 il + jl, by non-zero, ascending k
-    double* kg = nullptr;                 // [16 nme] staged element values (FE_PATTERN_GATHER)
+    // FE_PATTERN_GATHER: each row's incidences in ascending element order and the staging buffer
+    int32_t* vptr = nullptr;              // [nq + 1] start of row i's incidences
+    int32_t* inc = nullptr;               // [4 nme] keys 4k + a (row i = me[a][k]), ascending within a row
+    uint2* islot = nullptr;               // [4 nme] in-row positions of columns jl = 0..3, 16 bits each
+    int32_t* long_rows = nullptr;         // [nq + 1] rows with more columns than one thread sums
+    int32_t* n_long = nullptr;            // [2] their number, and 1 if a row is longer than 16 (device)
+    int32_t n_long_host[2] = {0, 0};
+    double* kg = nullptr;                 // [16 nme] staged element values
     cudaStream_t last_stream = nullptr;
 };
 

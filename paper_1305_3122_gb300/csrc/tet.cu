@@ -16,9 +16,12 @@
 // ids (their rank is the column's position in the sorted row), and writes, for every incidence,
 // the in-row positions of its four columns: the element-to-nnz map, row-major per element
 // (map[16k + 4 il + jl]), relative to the row start until the offsets are known. For the
-// deterministic gather variant the warp also writes each non-zero's contributions in ascending
-// element order: row i has exactly 4 * (its valence) contributions, so its part of the list starts
-// at 4 * vptr[i] before any offset is known.
+// deterministic gather variant the warp also lists the row's incidences in ascending element order,
+// each with the in-row positions of its four columns: row i has exactly (its valence) incidences,
+// so its part of the list starts at vptr[i] before any offset is known. The assembly then stages
+// the element matrices and sums each row from that list (row a of element k is the 32-byte sector
+// at 16k + 4a of the staging buffer), so every non-zero adds its contributions in ascending
+// element order.
 #include "ff.cuh"
 #include "internal.cuh"
 #include "rowhash.cuh"
@@ -31,6 +34,10 @@ constexpr int FAST_TS = 128;                 // hash-table slots per warp, fast 
 constexpr int FAST_EMAX = 42;                // fast rows: at most 42 tetrahedra (3 * 42 + 1 ids < 128)
 constexpr int BIG_TS = 4096;                 // one warp per block for rows up to FE_TET_MAX_VALENCE
 constexpr int BIG_EMAX = FE_TET_MAX_VALENCE;
+constexpr int RS_BLOCK = 128;                // row sums: threads per block, one row each
+constexpr int RS_MAX = 32;                   // row sums: longest row summed by one thread (longer: one warp)
+constexpr int RS_SHORT = 16;                 // row sums: smaller accumulators when no row is longer (twice
+                                             // the resident blocks and more L1: 1.30 against 2.80 ms at 128^3)
 static_assert(3 * BIG_EMAX + 1 < BIG_TS, "the big-row table must hold every distinct id");
 static_assert(3 * FAST_EMAX + 1 < FAST_TS, "the fast-row table must hold every distinct id");
 
@@ -124,18 +131,26 @@ struct RowSmem {
     int32_t rnk[TS];     // rank (column position) of each slot's id
     int32_t uid[TS];     // the distinct ids, in insertion order
     int32_t uslot[TS];   // their slots
-    int32_t cum[TS];     // by rank: multiplicities, then their exclusive prefix (gather lists)
     int4 e[EMAX];        // the row's bucket records
     int32_t ucount;
 };
 
+// Where the gather lists of the deterministic variant go.
+struct RowLists {
+    int32_t* inc;        // [4 nme]: the keys 4k + a of each row's incidences, ascending, row i from vptr[i]
+    uint2* islot;        // [4 nme]: the in-row positions of their columns jl = 0..3, 16 bits each
+    int32_t* long_rows;  // rows with more than RS_MAX columns
+    int32_t* n_long;     // their number
+    int32_t* any_over_short;  // set when a row has more than RS_SHORT columns
+};
+
 // One row by one warp: distinct columns (sorted, into tmp at 3 vptr[i] + i), their count, the
-// relative map of every incidence, and (GATHER) the within-row segment starts (into tmp2) and the
-// contribution lists (into perm at 4 vptr[i]).
+// relative map of every incidence, and (GATHER) the row's incidence list in ascending element
+// order with the positions of their columns.
 template <int TS, int EMAX, bool GATHER>
 __device__ void tet_row(int32_t i, int32_t beg, int32_t d, const int4* __restrict__ adj, RowSmem<TS, EMAX>& sm,
-                        int32_t* __restrict__ tmp, int32_t* __restrict__ tmp2, int32_t* __restrict__ cnt,
-                        int32_t* __restrict__ map, int32_t* __restrict__ perm) {
+                        int32_t* __restrict__ tmp, int32_t* __restrict__ cnt, int32_t* __restrict__ map,
+                        const RowLists& rl) {
     const int lane = threadIdx.x & 31;
     for (int s = lane; s < TS; s += 32) {
         sm.tab[s] = -1;
@@ -167,7 +182,6 @@ __device__ void tet_row(int32_t i, int32_t beg, int32_t d, const int4* __restric
         for (int qq = 0; qq < u; qq++) r += sm.uid[qq] < id;
         sm.rnk[sm.uslot[p]] = r;
         tmp[tb + r] = id;
-        if (GATHER) sm.cum[r] = sm.mult[sm.uslot[p]];
     }
     __syncwarp();
     // relative map: the four column positions of each incidence, one 16-byte store
@@ -186,62 +200,28 @@ __device__ void tet_row(int32_t i, int32_t beg, int32_t d, const int4* __restric
             o[jl] = off == 0 ? ri : off == 1 ? rx : off == 2 ? ry : rz;
         }
         *reinterpret_cast<int4*>(map + 16 * (int64_t)k + 4 * a) = make_int4(o[0], o[1], o[2], o[3]);
-    }
-    if (GATHER) {
-        // exclusive prefix of the multiplicities by rank: the start of each column's list
-        int32_t run = 0;
-        for (int base = 0; base < u; base += 32) {
-            const int r = base + lane;
-            const int32_t v = r < u ? sm.cum[r] : 0;
-            int32_t incl = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (r < u) {
-                sm.cum[r] = run + incl - v;
-                tmp2[tb + r] = run + incl - v;
-            }
-            run += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        __syncwarp();
-        // each incidence places its four contributions: a column's list is in ascending element
-        // order (keys 4k + a are distinct within a row), so the place is the column's start plus
-        // the number of earlier-element incidences that touch the column (every one touches the
-        // row's own vertex)
-        for (int t = lane; t < d; t += 32) {
-            const int4 r = sm.e[t];
-            const int32_t key = r.w;
-            int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-            for (int tt = 0; tt < d; tt++) {
-                const int4 o = sm.e[tt];
-                const int before = o.w < key;
-                c0 += before;
-                c1 += before & (o.x == r.x || o.y == r.x || o.z == r.x);
-                c2 += before & (o.x == r.y || o.y == r.y || o.z == r.y);
-                c3 += before & (o.x == r.z || o.y == r.z || o.z == r.z);
-            }
-            const int a = r.w & 3;
-            const int32_t k = r.w >> 2;
-            int32_t* pr = perm + 4 * (int64_t)beg;
-            const int32_t base = 16 * k + 4 * a;
-            pr[sm.cum[sm.rnk[tab_find<TS>(sm.tab, i)]] + c0] = base + a;
-            pr[sm.cum[sm.rnk[tab_find<TS>(sm.tab, r.x)]] + c1] = base + ((a + 1) & 3);
-            pr[sm.cum[sm.rnk[tab_find<TS>(sm.tab, r.y)]] + c2] = base + ((a + 2) & 3);
-            pr[sm.cum[sm.rnk[tab_find<TS>(sm.tab, r.z)]] + c3] = base + ((a + 3) & 3);
+        if (GATHER) {
+            // the incidence's place in the row's ascending element order (the keys 4k + a of one
+            // row are distinct)
+            int c0 = 0;
+            for (int tt = 0; tt < d; tt++) c0 += sm.e[tt].w < r.w;
+            rl.inc[beg + c0] = r.w;
+            rl.islot[beg + c0] = make_uint2((unsigned)o[0] | ((unsigned)o[1] << 16), (unsigned)o[2] | ((unsigned)o[3] << 16));
         }
     }
-    if (lane == 0) cnt[i] = u;
+    if (lane == 0) {
+        cnt[i] = u;
+        if (GATHER && u > RS_MAX) rl.long_rows[atomicAdd(rl.n_long, 1)] = i;
+        if (GATHER && u > RS_SHORT) *rl.any_over_short = 1;
+    }
     __syncwarp();
 }
 
 // Rows with at most FAST_EMAX tetrahedra, one warp each; longer rows are listed for k_tet_rows_big.
 template <bool GATHER>
 __global__ void __launch_bounds__(ROW_WARPS * 32, 12) k_tet_rows(const int32_t* __restrict__ vptr, const int4* __restrict__ adj,
-                                                            int32_t nq, int32_t* __restrict__ tmp, int32_t* __restrict__ tmp2,
-                                                            int32_t* __restrict__ cnt, int32_t* __restrict__ map,
-                                                            int32_t* __restrict__ perm, int32_t* __restrict__ big_list,
+                                                            int32_t nq, int32_t* __restrict__ tmp, int32_t* __restrict__ cnt,
+                                                            int32_t* __restrict__ map, RowLists rl, int32_t* __restrict__ big_list,
                                                             int32_t* __restrict__ big_count) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RowSmem<FAST_TS, FAST_EMAX>& sm = reinterpret_cast<RowSmem<FAST_TS, FAST_EMAX>*>(smem_raw)[threadIdx.x >> 5];
@@ -258,7 +238,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32, 12) k_tet_rows(const int32_t* 
             if (lane == 0) big_list[atomicAdd(big_count, 1)] = i;
             continue;
         }
-        tet_row<FAST_TS, FAST_EMAX, GATHER>(i, beg, d, adj, sm, tmp, tmp2, cnt, map, perm);
+        tet_row<FAST_TS, FAST_EMAX, GATHER>(i, beg, d, adj, sm, tmp, cnt, map, rl);
     }
 }
 
@@ -266,8 +246,7 @@ template <bool GATHER>
 __global__ void __launch_bounds__(32) k_tet_rows_big(const int32_t* __restrict__ vptr, const int4* __restrict__ adj,
                                                      const int32_t* __restrict__ big_list,
                                                      const int32_t* __restrict__ big_count, int32_t* __restrict__ tmp,
-                                                     int32_t* __restrict__ tmp2, int32_t* __restrict__ cnt,
-                                                     int32_t* __restrict__ map, int32_t* __restrict__ perm,
+                                                     int32_t* __restrict__ cnt, int32_t* __restrict__ map, RowLists rl,
                                                      int* __restrict__ too_big) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RowSmem<BIG_TS, BIG_EMAX>& sm = *reinterpret_cast<RowSmem<BIG_TS, BIG_EMAX>*>(smem_raw);
@@ -282,27 +261,20 @@ __global__ void __launch_bounds__(32) k_tet_rows_big(const int32_t* __restrict__
             }
             continue;
         }
-        tet_row<BIG_TS, BIG_EMAX, GATHER>(i, beg, d, adj, sm, tmp, tmp2, cnt, map, perm);
+        tet_row<BIG_TS, BIG_EMAX, GATHER>(i, beg, d, adj, sm, tmp, cnt, map, rl);
     }
 }
 
-// Columns (and segment starts) into their final places, one warp per row.
-template <bool GATHER>
+// Columns into their final places, one warp per row.
 __global__ void __launch_bounds__(TET_BLOCK) k_tet_cols(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
-                                                        int32_t nq, const int32_t* __restrict__ tmp,
-                                                        const int32_t* __restrict__ tmp2, int32_t* __restrict__ col_idx,
-                                                        int32_t* __restrict__ seg_ptr) {
+                                                        int32_t nq, const int32_t* __restrict__ tmp, int32_t* __restrict__ col_idx) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (TET_BLOCK / 32);
     for (int64_t r = (int64_t)blockIdx.x * (TET_BLOCK / 32) + (threadIdx.x >> 5); r < nq; r += nwarps) {
         const int32_t i = (int32_t)r;
         const int32_t rb = row_ptr[i], u = row_ptr[i + 1] - rb;
-        const int32_t beg = vptr[i];
-        const int64_t tb = 3 * (int64_t)beg + i;
-        for (int c = lane; c < u; c += 32) {
-            col_idx[rb + c] = tmp[tb + c];
-            if (GATHER) seg_ptr[rb + c] = 4 * beg + tmp2[tb + c];
-        }
+        const int64_t tb = 3 * (int64_t)vptr[i] + i;
+        for (int c = lane; c < u; c += 32) col_idx[rb + c] = tmp[tb + c];
     }
 }
 
@@ -316,8 +288,6 @@ __global__ void k_tet_map_base(const int32_t* __restrict__ me, int32_t nme, cons
         map[c] += row_ptr[me[il * (int64_t)nme + k]];
     }
 }
-
-__global__ void k_tet_set_last(int32_t* seg_ptr, int64_t nnz, int32_t v) { seg_ptr[nnz] = v; }
 
 // ------------------------------------------------------------------ element matrices
 
@@ -459,26 +429,91 @@ __global__ void __launch_bounds__(TET_BLOCK) k_tet_stage(const int32_t* __restri
     }
 }
 
-// Each non-zero sums its staged contributions in ascending element order.
-__global__ void __launch_bounds__(TET_BLOCK) k_tet_gather(const int32_t* __restrict__ seg_ptr, const int32_t* __restrict__ perm,
-                                                          const double* __restrict__ kg, int64_t nnz,
-                                                          double* __restrict__ val) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t s0 = seg_ptr[p], s1 = seg_ptr[p + 1];
-        double s = 0.0;
-        // four contributions per step, loaded together and added one by one in ascending order
-        for (int32_t b = s0; b < s1; b += 4) {
-            int32_t c[4];
-            double v[4];
+// Row sums of the staged element matrices, one row per thread: the row's incidences in ascending
+// element order each add row a of element k (the 32-byte sector at kg[16k + 4a]) to the row's
+// accumulators in shared memory, at the in-row positions of the four columns. Accumulators start
+// at -0.0, so every sum equals its first contribution followed by the others in ascending element
+// order, bit for bit. Rows with more than RMAX columns are left to k_tet_rowsum_long. Four
+// incidences are loaded before any is added (four random sectors in flight per thread), and the
+// next four's keys and slots are loaded meanwhile.
+template <int RMAX>
+__global__ void __launch_bounds__(RS_BLOCK) k_tet_rowsum(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
+                                                         int32_t nq, const int32_t* __restrict__ inc,
+                                                         const uint2* __restrict__ islot, const double* __restrict__ kg,
+                                                         double* __restrict__ val) {
+    __shared__ double acc[RMAX * RS_BLOCK];
+    double* a = acc + threadIdx.x;                       // column c of this thread's row at a[c * RS_BLOCK]
+    for (int64_t r = blockIdx.x * (int64_t)RS_BLOCK + threadIdx.x; r < nq; r += (int64_t)gridDim.x * RS_BLOCK) {
+        const int32_t rb = row_ptr[r], u = row_ptr[r + 1] - rb;
+        if (u > RMAX) continue;
+        const int32_t b0 = vptr[r], d = vptr[r + 1] - b0;
+        for (int c = 0; c < u; c++) a[c * RS_BLOCK] = -0.0;
+        int32_t key[4];
+        uint2 sl[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) c[u] = b + u < s1 ? perm[b + u] : 0;
-#pragma unroll
-            for (int u = 0; u < 4; u++) v[u] = b + u < s1 ? kg[c[u]] : 0.0;
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-                if (b + u < s1) s = b + u == s0 ? v[u] : s + v[u];
+        for (int j = 0; j < 4; j++) {
+            key[j] = j < d ? inc[b0 + j] : 0;
+            sl[j] = j < d ? islot[b0 + j] : make_uint2(0u, 0u);
         }
-        val[p] = s;
+        for (int32_t t0 = 0; t0 < d; t0 += 4) {
+            double2 v[4][2];
+            uint2 cs[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                cs[j] = sl[j];
+                if (t0 + j < d) {
+                    const double2* e = reinterpret_cast<const double2*>(kg + 4 * (int64_t)key[j]);
+                    v[j][0] = e[0];
+                    v[j][1] = e[1];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int32_t tn = t0 + 4 + j;
+                key[j] = tn < d ? inc[b0 + tn] : 0;
+                sl[j] = tn < d ? islot[b0 + tn] : make_uint2(0u, 0u);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (t0 + j < d) {
+                    a[(cs[j].x & 0xFFFFu) * RS_BLOCK] += v[j][0].x;
+                    a[(cs[j].x >> 16) * RS_BLOCK] += v[j][0].y;
+                    a[(cs[j].y & 0xFFFFu) * RS_BLOCK] += v[j][1].x;
+                    a[(cs[j].y >> 16) * RS_BLOCK] += v[j][1].y;
+                }
+            }
+        }
+        for (int c = 0; c < u; c++) val[rb + c] = a[c * RS_BLOCK];
+    }
+}
+
+// The rows with more than RS_MAX columns, one warp each: lane l owns the columns c = l (mod 32)
+// and adds their contributions in ascending element order (accumulators in dynamic shared
+// memory, 3 FE_TET_MAX_VALENCE + 1 doubles at most).
+__global__ void __launch_bounds__(32) k_tet_rowsum_long(const int32_t* __restrict__ long_rows, const int32_t* __restrict__ n_long,
+                                                        const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
+                                                        const int32_t* __restrict__ inc, const uint2* __restrict__ islot,
+                                                        const double* __restrict__ kg, double* __restrict__ val) {
+    extern __shared__ double accl[];
+    const int lane = threadIdx.x;
+    const int32_t n = *n_long;
+    for (int32_t b = blockIdx.x; b < n; b += gridDim.x) {
+        const int32_t i = long_rows[b];
+        const int32_t rb = row_ptr[i], u = row_ptr[i + 1] - rb;
+        const int32_t b0 = vptr[i], d = vptr[i + 1] - b0;
+        for (int c = lane; c < u; c += 32) accl[c] = -0.0;
+        __syncwarp();
+        for (int32_t t = 0; t < d; t++) {
+            const int32_t key = inc[b0 + t];
+            const uint2 sl = islot[b0 + t];
+            const unsigned c4[4] = {sl.x & 0xFFFFu, sl.x >> 16, sl.y & 0xFFFFu, sl.y >> 16};
+#pragma unroll
+            for (int jl = 0; jl < 4; jl++)
+                if ((int)(c4[jl] & 31u) == lane) accl[c4[jl]] += kg[4 * (int64_t)key + jl];
+        }
+        __syncwarp();
+        for (int c = lane; c < u; c += 32) val[rb + c] = accl[c];
+        __syncwarp();
     }
 }
 
@@ -572,32 +607,33 @@ extern "C" void fe_tet_pattern_destroy(fe_tet_pattern p) {
     if (!p) return;
     FeStreamScope scope(p->last_stream);
     fe_free(p->row_ptr); fe_free(p->col_idx); fe_free(p->map);
-    fe_free(p->seg_ptr); fe_free(p->perm); fe_free(p->kg);
+    fe_free(p->vptr); fe_free(p->inc); fe_free(p->islot); fe_free(p->long_rows); fe_free(p->n_long); fe_free(p->kg);
     delete p;
 }
 
 namespace {
 struct TetTemps {
-    int32_t *vptr = nullptr, *cur = nullptr, *cnt = nullptr, *tmp = nullptr, *tmp2 = nullptr;
+    int32_t *vptr = nullptr, *cur = nullptr, *cnt = nullptr, *tmp = nullptr;
     int32_t *big = nullptr, *counters = nullptr;
     int4* adj = nullptr;
     ~TetTemps() {
-        fe_free(vptr); fe_free(cur); fe_free(cnt); fe_free(tmp); fe_free(tmp2);
+        fe_free(vptr); fe_free(cur); fe_free(cnt); fe_free(tmp);
         fe_free(big); fe_free(counters); fe_free(adj);
     }
 };
 
 template <bool GATHER>
 fe_status tet_rows(const TetTemps& t, int32_t nq, fe_tet_pattern p, cudaStream_t s) {
+    const RowLists rl{p->inc, p->islot, p->long_rows, p->n_long, p->n_long ? p->n_long + 1 : nullptr};
     const size_t fast_smem = ROW_WARPS * sizeof(RowSmem<FAST_TS, FAST_EMAX>);
     const size_t big_smem = sizeof(RowSmem<BIG_TS, BIG_EMAX>);
     FE_CUDA(cudaFuncSetAttribute(k_tet_rows<GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast_smem));
     FE_CUDA(cudaFuncSetAttribute(k_tet_rows_big<GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem));
     { FE_PROF("k_tet_rows", s); k_tet_rows<GATHER><<<fe_grid(((int64_t)nq + ROW_WARPS - 1) / ROW_WARPS, 1, 8), ROW_WARPS * 32, fast_smem, s>>>(
-          t.vptr, t.adj, nq, t.tmp, t.tmp2, t.cnt, p->map, p->perm, t.big, t.counters); }
+          t.vptr, t.adj, nq, t.tmp, t.cnt, p->map, rl, t.big, t.counters); }
     FE_LAUNCHED("k_tet_rows");
     { FE_PROF("k_tet_rows_big", s); k_tet_rows_big<GATHER><<<fe_sm_count(), 32, big_smem, s>>>(
-          t.vptr, t.adj, t.big, t.counters, t.tmp, t.tmp2, t.cnt, p->map, p->perm, t.counters + 1); }
+          t.vptr, t.adj, t.big, t.counters, t.tmp, t.cnt, p->map, rl, t.counters + 1); }
     FE_LAUNCHED("k_tet_rows_big");
     return FE_OK;
 }
@@ -638,11 +674,16 @@ extern "C" fe_status fe_tet_pattern_build(fe_tet_mesh m, int flags, fe_stream st
     }
     if ((st = fe_alloc_n(&t.cnt, (size_t)nq + 1, "row counts"))) return fail(st);
     if ((st = fe_alloc_n(&t.tmp, (size_t)tcap, "row columns"))) return fail(st);
-    if (gather && (st = fe_alloc_n(&t.tmp2, (size_t)tcap, "row segment starts"))) return fail(st);
     if ((st = fe_alloc_n(&t.big, (size_t)nq + 1, "long rows"))) return fail(st);
     if ((st = fe_alloc_n(&t.counters, 4, "counters"))) return fail(st);
     if ((st = fe_alloc_n(&p->map, 16 * (size_t)nme, "element-to-nnz map"))) return fail(st);
-    if (gather && (st = fe_alloc_n(&p->perm, 16 * (size_t)nme, "contribution lists"))) return fail(st);
+    if (gather) {
+        if ((st = fe_alloc_n(&p->inc, (size_t)n4, "row incidence lists"))) return fail(st);
+        if ((st = fe_alloc_n(&p->islot, (size_t)n4, "row incidence column slots"))) return fail(st);
+        if ((st = fe_alloc_n(&p->long_rows, (size_t)nq + 1, "long rows"))) return fail(st);
+        if ((st = fe_alloc_n(&p->n_long, 2, "long-row count and longest row"))) return fail(st);
+        if (cudaMemsetAsync(p->n_long, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return fail(fe_fail(FE_ERR_CUDA, "memset"));
+    }
     if (cudaMemsetAsync(t.counters, 0, 4 * sizeof(int32_t), s) != cudaSuccess) return fail(fe_fail(FE_ERR_CUDA, "memset"));
     if (nq > 0) {
         st = gather ? tet_rows<true>(t, nq, p, s) : tet_rows<false>(t, nq, p, s);
@@ -653,6 +694,7 @@ extern "C" fe_status fe_tet_pattern_build(fe_tet_mesh m, int flags, fe_stream st
     if ((st = fe_exclusive_scan(t.cnt, p->row_ptr, nq, s, &nnz))) return fail(st);   // synchronises
     int too_big = 0;
     if (cudaMemcpyAsync(&too_big, t.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        (gather && cudaMemcpyAsync(p->n_long_host, p->n_long, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return fail(fe_fail(FE_ERR_CUDA, "flag read-back"));
     if (too_big)
@@ -660,15 +702,10 @@ extern "C" fe_status fe_tet_pattern_build(fe_tet_mesh m, int flags, fe_stream st
                                               std::to_string(FE_TET_MAX_VALENCE) + " tetrahedra"));
     p->nnz = nnz;
     if ((st = fe_alloc_n(&p->col_idx, (size_t)nnz, "col_idx"))) return fail(st);
-    if (gather && (st = fe_alloc_n(&p->seg_ptr, (size_t)nnz + 1, "seg_ptr"))) return fail(st);
     if (gather && (st = fe_alloc_n(&p->kg, 16 * (size_t)nme, "element value staging"))) return fail(st);
     if (nq > 0) {
         const unsigned g = fe_grid(((int64_t)nq + 7) / 8, 1, 8);
-        if (gather) {
-            { FE_PROF("k_tet_cols", s); k_tet_cols<true><<<g, TET_BLOCK, 0, s>>>(t.vptr, p->row_ptr, nq, t.tmp, t.tmp2, p->col_idx, p->seg_ptr); }
-        } else {
-            { FE_PROF("k_tet_cols", s); k_tet_cols<false><<<g, TET_BLOCK, 0, s>>>(t.vptr, p->row_ptr, nq, t.tmp, nullptr, p->col_idx, nullptr); }
-        }
+        { FE_PROF("k_tet_cols", s); k_tet_cols<<<g, TET_BLOCK, 0, s>>>(t.vptr, p->row_ptr, nq, t.tmp, p->col_idx); }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(fe_cuda_fail(e, "k_tet_cols"));
     }
@@ -677,10 +714,9 @@ extern "C" fe_status fe_tet_pattern_build(fe_tet_mesh m, int flags, fe_stream st
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(fe_cuda_fail(e, "k_tet_map_base"));
     }
-    if (gather) {
-        { FE_PROF("k_tet_set_last", s); k_tet_set_last<<<1, 1, 0, s>>>(p->seg_ptr, nnz, 16 * nme); }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return fail(fe_cuda_fail(e, "k_tet_set_last"));
+    if (gather) {                                // the row sums need the incidence offsets
+        p->vptr = t.vptr;
+        t.vptr = nullptr;
     }
     *out = p;
     return FE_OK;
@@ -740,7 +776,18 @@ extern "C" fe_status fe_tet_assemble(fe_tet_mesh m, fe_tet_pattern p, int kind, 
         else k_tet_stage<FE_TET_STIFF><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->kg);
     }
     FE_LAUNCHED("k_tet_stage");
-    { FE_PROF("k_tet_gather", s); k_tet_gather<<<fe_grid(p->nnz, TET_BLOCK, 8), TET_BLOCK, 0, s>>>(p->seg_ptr, p->perm, p->kg, p->nnz, values); }
-    FE_LAUNCHED("k_tet_gather");
+    {
+        FE_PROF("k_tet_rowsum", s);
+        if (!p->n_long_host[1])
+            k_tet_rowsum<RS_SHORT><<<fe_grid(m->nq, RS_BLOCK, 16), RS_BLOCK, 0, s>>>(p->vptr, p->row_ptr, m->nq, p->inc, p->islot, p->kg, values);
+        else
+            k_tet_rowsum<RS_MAX><<<fe_grid(m->nq, RS_BLOCK, 8), RS_BLOCK, 0, s>>>(p->vptr, p->row_ptr, m->nq, p->inc, p->islot, p->kg, values);
+    }
+    FE_LAUNCHED("k_tet_rowsum");
+    if (p->n_long_host[0] > 0) {
+        const size_t sm = (3 * (size_t)FE_TET_MAX_VALENCE + 1) * sizeof(double);
+        { FE_PROF("k_tet_rowsum_long", s); k_tet_rowsum_long<<<fe_sm_count() * 8, 32, sm, s>>>(p->long_rows, p->n_long, p->vptr, p->row_ptr, p->inc, p->islot, p->kg, values); }
+        FE_LAUNCHED("k_tet_rowsum_long");
+    }
     return FE_OK;
 }

@@ -2,8 +2,9 @@
 
 row_ptr / col_idx / map are compared bit-exactly; values within 1e-13 of each row's largest |a_ij|;
 the gather variant must be bit-identical from run to run. Meshes: jittered, node-permuted cube
-meshes (several warps and blocks, ragged tails), a star whose centre belongs to 80 or 1000
-tetrahedra (the long-row kernel), and the 128^3-cell cube at full size on sampled rows.
+meshes (several warps and blocks, ragged tails), stars whose centre belongs to 40 tetrahedra (rows
+of 22 and 23 columns: the gather variant's 32-column row sums) or to 80 and 1000 (the long-row
+kernels), and the 128^3-cell cube at full size on sampled rows.
 """
 from __future__ import annotations
 
@@ -44,6 +45,7 @@ def _cases():
     for N, seed in ((1, 1), (3, 2), (7, 3), (12, 4)):
         m = meshgen.cube_mesh(N, seed)
         out[f"cube{N}"] = (m.q, m.me)
+    out["star20"] = star_mesh(20)      # rows of 22 and 23 columns: the 32-column row sums, no long rows
     out["star40"] = star_mesh(40)
     out["star500"] = star_mesh(500)
     return out
