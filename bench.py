@@ -544,16 +544,20 @@ def tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 128) -
 
 def p2(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 1024) -> dict:
     """P2 (quadratic) triangles on the 1024 x 1024-cell square (jittered, node-permuted): the P2
-    pattern from the scalar one, and the mass and stiffness by FP64 atomics."""
+    pattern from the scalar one (with and without the ordered variant's row lists), and the mass
+    and stiffness by FP64 atomics and by ordered row sums."""
     seed = 13053122 + 7
     m = meshgen.square_mesh(cells, seed)
     mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))
     pat = feasm.Pattern(mesh, map=False)
     ms_pat = _time_calls(torch, lambda: feasm.P2Pattern(mesh, pat).close(), flush, reps=5)
-    p2p = feasm.P2Pattern(mesh, pat)
+    ms_pat_g = _time_calls(torch, lambda: feasm.P2Pattern(mesh, pat, gather=True).close(), flush, reps=5)
+    p2p = feasm.P2Pattern(mesh, pat, gather=True)
     out = p2p.new_values()
     ms_m = _time_calls(torch, lambda: feasm.p2_assemble(mesh, p2p, feasm.P2_MASS, out), flush)
     ms_s = _time_calls(torch, lambda: feasm.p2_assemble(mesh, p2p, feasm.P2_STIFF, out), flush)
+    ms_mg = _time_calls(torch, lambda: feasm.p2_assemble(mesh, p2p, feasm.P2_MASS, out, variant=feasm.GATHER), flush)
+    ms_sg = _time_calls(torch, lambda: feasm.p2_assemble(mesh, p2p, feasm.P2_STIFF, out, variant=feasm.GATHER), flush)
     feasm.profile_reset()
     feasm.profile_enable(True)
     _time_calls(torch, lambda: feasm.p2_assemble(mesh, p2p, feasm.P2_STIFF, out), flush)
@@ -563,7 +567,8 @@ def p2(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 1024) -> dict:
     nbytes = 12 * m.nme + 16 * m.nq + 144 * m.nme + 8 * p2p.nnz          # me, q, map, values
     return {"workload": f"P2 M and S of the {cells}x{cells}-cell square (nq={m.nq}, edges={p2p.n_edges}, "
                         f"dofs={p2p.n_rows}, nme={m.nme}, nnz={p2p.nnz})",
-            "pattern_ms": round(ms_pat, 4), "M_ms": round(ms_m, 4), "S_ms": round(ms_s, 4),
+            "pattern_ms": round(ms_pat, 4), "pattern_gather_ms": round(ms_pat_g, 4), "M_ms": round(ms_m, 4),
+            "S_ms": round(ms_s, 4), "M_gather_ms": round(ms_mg, 4), "S_gather_ms": round(ms_sg, 4),
             "S_melem_s": round(m.nme / ms_s / 1e3, 1), "k_p2_atomic_S_ms": round(k_ms, 4),
             "roofline": {"kernel": "k_p2_atomic<S>", "bound": "hbm", "algorithmic_bytes": nbytes,
                          "achieved": round(nbytes / k_ms / 1e6, 1), "peak": hbm, "unit": "GB/s",

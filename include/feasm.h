@@ -271,15 +271,18 @@ fe_status fe_tet_assemble(fe_tet_mesh mesh, fe_tet_pattern pattern, int kind, co
  * M^e_ij = int_T phi_i phi_j and S^e_ij = int_T grad phi_i . grad phi_j.
  * Global dofs: vertex i is dof i; the nE edges are dofs nq .. nq + nE - 1, numbered in ascending
  * order of (smaller vertex id, larger vertex id). The structure is the structural sum, as for
- * P1. Assembly by FP64 element matrices and FP64 atomics (values zeroed first). */
+ * P1. Assembly by FP64 element matrices, scattered by FP64 atomics (values zeroed first) or, for
+ * FE_VARIANT_GATHER, staged and summed row by row in ascending element order. */
 enum { FE_P2_MASS = 0, FE_P2_STIFF = 1 };
 
 /* Most triangles around one vertex for a P2 pattern (FE_ERR_LIMIT above it). */
 #define FE_P2_MAX_VALENCE 680
 
 /* Dofs, CSR structure and element-to-nnz map from a mesh and its scalar (dofs = 1) pattern, whose
- * structure numbers the edges. Synchronises (the edge count, nnz). */
-fe_status fe_p2_pattern_build(fe_mesh mesh, fe_pattern scalar_pattern, fe_stream stream, fe_p2_pattern* out);
+ * structure numbers the edges. flags: FE_PATTERN_GATHER adds what FE_VARIANT_GATHER needs (each
+ * row's incidences in ascending element order and the staging buffer); other bits are ignored.
+ * Synchronises (the edge count, nnz). */
+fe_status fe_p2_pattern_build(fe_mesh mesh, fe_pattern scalar_pattern, int flags, fe_stream stream, fe_p2_pattern* out);
 fe_status fe_p2_pattern_info(fe_p2_pattern pattern, int64_t* n_dofs, int64_t* nnz, const int32_t** row_ptr,
                              const int32_t** col_idx);
 /* edof (device, [nme][6] int32): each triangle's dofs in local order; map (device, 36 nme):
@@ -287,8 +290,13 @@ fe_status fe_p2_pattern_info(fe_p2_pattern pattern, int64_t* n_dofs, int64_t* nn
 fe_status fe_p2_pattern_dofs(fe_p2_pattern pattern, const int32_t** edof, const int32_t** map, int64_t* n_edges);
 void fe_p2_pattern_destroy(fe_p2_pattern pattern);
 
-/* Values of FE_P2_MASS or FE_P2_STIFF into values[0 .. nnz) (device, capacity cap). */
-fe_status fe_p2_assemble(fe_mesh mesh, fe_p2_pattern pattern, int kind, double* values, int64_t cap, fe_stream stream);
+/* Values of FE_P2_MASS or FE_P2_STIFF into values[0 .. nnz) (device, capacity cap). variant:
+ * FE_VARIANT_ATOMIC (FP64 atomicAdd after zeroing) or FE_VARIANT_GATHER (element matrices staged,
+ * then each row sums its incidences' element rows, so that each non-zero adds its contributions
+ * in ascending element order: bit-identical from run to run; needs a pattern built with
+ * FE_PATTERN_GATHER). */
+fe_status fe_p2_assemble(fe_mesh mesh, fe_p2_pattern pattern, int kind, int variant, double* values, int64_t cap,
+                         fe_stream stream);
 
 /* -------------------------------------------------------------------- zero dropping ---- */
 

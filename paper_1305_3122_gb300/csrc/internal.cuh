@@ -97,6 +97,15 @@ struct fe_p2_pattern_s {
     int32_t* col_idx = nullptr;           // [nnz]
     int32_t* edof = nullptr;              // [nme][6] element dofs (vertices, then edges (0,1), (1,2), (2,0))
     int32_t* map = nullptr;               // [36 nme] map[36k + 6 il + jl] = position of (edof[k][il], edof[k][jl])
+    // FE_PATTERN_GATHER: each row's incidences in ascending element order and the staging buffer
+    int flags = 0;
+    int32_t* vptr = nullptr;              // [ndof + 1] start of row r's incidences
+    int4* rrec = nullptr;                 // [6 nme] {key 6k + a (row r = edof[k][a]), six 16-bit column positions},
+                                          // ascending keys within a row
+    int32_t* long_rows = nullptr;         // [ndof + 1] rows with more columns than one thread sums
+    int32_t* n_long = nullptr;            // [1] their number (device)
+    int32_t n_long_host = 0;
+    double* kg = nullptr;                 // [36 nme] staged element values
     cudaStream_t last_stream = nullptr;
 };
 

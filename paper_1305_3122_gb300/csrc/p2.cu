@@ -23,7 +23,10 @@
 // its at most 12 ids in registers; either ranks the distinct ids (the sorted columns) and writes
 // each incidence's six in-row positions: the element-to-nnz map, row-major per element
 // (map[36k + 6 il + jl]), made absolute once the offsets are known. Assembly: one thread per
-// element, FP64, 36 FP64 atomics.
+// element, FP64, 36 FP64 atomics; or (the deterministic variant) the element matrices staged and
+// one thread per row adding the row's incidences in ascending element order (the row passes also
+// list each row's incidences in ascending element order with their column positions), so that every non-zero sums its
+// contributions in ascending element order, bit-identical from run to run.
 #include "internal.cuh"
 #include "rowhash.cuh"
 
@@ -34,6 +37,19 @@ constexpr int P2_WARPS = 4;
 constexpr int FAST_TS = 128, FAST_EMAX = 21;             // 6 * 21 ids < 128
 constexpr int BIG_TS = 4096, BIG_EMAX = FE_P2_MAX_VALENCE;
 static_assert(6 * FAST_EMAX < FAST_TS && 6 * BIG_EMAX < BIG_TS, "tables hold every id");
+constexpr int RS_BLOCK = 128;                // row sums: one row per thread
+constexpr int RS_VERTEX = 32;                // row sums: accumulators of a vertex row (1 + 3 d columns at valence d)
+constexpr int RS_EDGE = 16;                  // row sums: accumulators of an edge row (at most 12 columns for two triangles)
+constexpr int RS_LONG_MAX = 6 * BIG_EMAX;    // columns of the longest row
+
+// Where the row passes put the deterministic variant's lists (rrec null: no lists).
+struct P2Lists {
+    int4* rrec;          // [6 nme]: each row's incidences in ascending element order, row r from vptr[r]:
+                         // {key 6k + a, then the in-row positions of columns jl = 0..5, 16 bits each}
+    int32_t* long_rows;  // rows with more columns than their thread's accumulators
+    int32_t* n_long;
+    int32_t nq;
+};
 
 // Entries right of the diagonal in each scalar row (0 for an empty row), and the diagonal's place.
 __global__ void k_p2_upper(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t nq,
@@ -105,7 +121,7 @@ struct P2Smem {
 template <int TS, int EMAX>
 __device__ void p2_row(int32_t r, int32_t beg, int32_t d, const int32_t* __restrict__ inc, const int32_t* __restrict__ edof,
                        P2Smem<TS, EMAX>& sm, int32_t* __restrict__ tmp, int32_t* __restrict__ cnt,
-                       int32_t* __restrict__ map) {
+                       int32_t* __restrict__ map, const P2Lists& ls) {
     const int lane = threadIdx.x & 31;
     for (int s = lane; s < TS; s += 32) sm.tab[s] = -1;
     if (lane == 0) sm.ucount = 0;
@@ -135,11 +151,24 @@ __device__ void p2_row(int32_t r, int32_t beg, int32_t d, const int32_t* __restr
     for (int t = lane; t < d; t += 32) {
         const int32_t kk = sm.key[t] / 6, a = sm.key[t] - 6 * (sm.key[t] / 6);
         const int32_t* e = edof + 6 * (int64_t)kk;
-        int32_t* o = map + 36 * (int64_t)kk + 6 * a;
+        int32_t* mo = map + 36 * (int64_t)kk + 6 * a;
+        int32_t o[6];
 #pragma unroll
-        for (int jl = 0; jl < 6; jl++) o[jl] = sm.rnk[tab_find<TS>(sm.tab, e[jl])];
+        for (int jl = 0; jl < 6; jl++) {
+            o[jl] = sm.rnk[tab_find<TS>(sm.tab, e[jl])];
+            mo[jl] = o[jl];
+        }
+        if (ls.rrec) {                                       // the incidence's place in element order
+            int c0 = 0;
+            for (int tt = 0; tt < d; tt++) c0 += sm.key[tt] < sm.key[t];
+            ls.rrec[beg + c0] = make_int4(sm.key[t], (int)((unsigned)o[0] | ((unsigned)o[1] << 16)),
+                                          (int)((unsigned)o[2] | ((unsigned)o[3] << 16)), (int)((unsigned)o[4] | ((unsigned)o[5] << 16)));
+        }
     }
-    if (lane == 0) cnt[r] = u;
+    if (lane == 0) {
+        cnt[r] = u;
+        if (ls.rrec && u > (r < ls.nq ? RS_VERTEX : RS_EDGE)) ls.long_rows[atomicAdd(ls.n_long, 1)] = r;
+    }
     __syncwarp();
 }
 
@@ -147,7 +176,7 @@ __global__ void __launch_bounds__(P2_WARPS * 32) k_p2_rows(const int32_t* __rest
                                                            const int32_t* __restrict__ edof, int32_t nrows,
                                                            int32_t* __restrict__ tmp, int32_t* __restrict__ cnt,
                                                            int32_t* __restrict__ map, int32_t* __restrict__ big_list,
-                                                           int32_t* __restrict__ big_count) {
+                                                           int32_t* __restrict__ big_count, P2Lists ls) {
     __shared__ P2Smem<FAST_TS, FAST_EMAX> sm_all[P2_WARPS];
     P2Smem<FAST_TS, FAST_EMAX>& sm = sm_all[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -161,7 +190,7 @@ __global__ void __launch_bounds__(P2_WARPS * 32) k_p2_rows(const int32_t* __rest
             if (lane == 0) big_list[atomicAdd(big_count, 1)] = r;
             continue;
         }
-        p2_row<FAST_TS, FAST_EMAX>(r, beg, d, inc, edof, sm, tmp, cnt, map);
+        p2_row<FAST_TS, FAST_EMAX>(r, beg, d, inc, edof, sm, tmp, cnt, map, ls);
     }
 }
 
@@ -173,7 +202,7 @@ __global__ void __launch_bounds__(P2_BLOCK) k_p2_edge_rows(const int32_t* __rest
                                                            const int32_t* __restrict__ edof, int32_t nq, int32_t ndof,
                                                            int32_t* __restrict__ tmp, int32_t* __restrict__ cnt,
                                                            int32_t* __restrict__ map, int32_t* __restrict__ big_list,
-                                                           int32_t* __restrict__ big_count) {
+                                                           int32_t* __restrict__ big_count, P2Lists ls) {
     for (int64_t rr = nq + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < ndof; rr += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = (int32_t)rr, beg = vptr[r], d = vptr[r + 1] - beg;
         if (d > 2) {
@@ -209,6 +238,7 @@ __global__ void __launch_bounds__(P2_BLOCK) k_p2_edge_rows(const int32_t* __rest
             const int32_t kk = key[t] / 6, a = key[t] - 6 * kk;
             const int32_t* e = edof + 6 * (int64_t)kk;
             int32_t* o = map + 36 * (int64_t)kk + 6 * a;
+            unsigned sl[6];
 #pragma unroll
             for (int jl = 0; jl < 6; jl++) {
                 const int32_t v = e[jl];
@@ -216,6 +246,12 @@ __global__ void __launch_bounds__(P2_BLOCK) k_p2_edge_rows(const int32_t* __rest
 #pragma unroll
                 for (int i = 0; i < 12; i++) rank += x[i] < v && (i == 0 || x[i] != x[i - 1]);
                 o[jl] = rank;
+                sl[jl] = (unsigned)rank;
+            }
+            if (ls.rrec) {                                   // ascending element order (at most 12 columns: no long row)
+                const int c0 = d > 1 && key[1 - t] < key[t];
+                ls.rrec[beg + c0] = make_int4(key[t], (int)(sl[0] | (sl[1] << 16)), (int)(sl[2] | (sl[3] << 16)),
+                                              (int)(sl[4] | (sl[5] << 16)));
             }
         }
     }
@@ -225,7 +261,7 @@ __global__ void __launch_bounds__(32) k_p2_rows_big(const int32_t* __restrict__ 
                                                     const int32_t* __restrict__ edof, const int32_t* __restrict__ big_list,
                                                     const int32_t* __restrict__ big_count, int32_t* __restrict__ tmp,
                                                     int32_t* __restrict__ cnt, int32_t* __restrict__ map,
-                                                    int* __restrict__ too_big) {
+                                                    int* __restrict__ too_big, P2Lists ls) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     P2Smem<BIG_TS, BIG_EMAX>& sm = *reinterpret_cast<P2Smem<BIG_TS, BIG_EMAX>*>(smem_raw);
     const int32_t n = *big_count;
@@ -238,7 +274,7 @@ __global__ void __launch_bounds__(32) k_p2_rows_big(const int32_t* __restrict__ 
             }
             continue;
         }
-        p2_row<BIG_TS, BIG_EMAX>(r, beg, d, inc, edof, sm, tmp, cnt, map);
+        p2_row<BIG_TS, BIG_EMAX>(r, beg, d, inc, edof, sm, tmp, cnt, map, ls);
     }
 }
 
@@ -272,7 +308,7 @@ __device__ __forceinline__ void p2_elem(double2 p0, double2 p1, double2 p2, doub
     const double D = ex[1] * ey[2] - ex[2] * ey[1];
     const double T = 0.5 * D;
     if (KIND == FE_P2_MASS) {
-        const double m = T / 180.0;
+        const double m = T * (1.0 / 180.0);                  // constant reciprocals: no run-time division
         const double a = 6.0 * m, b = -m, c = -4.0 * m, d = 32.0 * m, e = 16.0 * m;
         const double tbl[6][6] = {{a, b, b, 0.0, c, 0.0}, {b, a, b, 0.0, 0.0, c}, {b, b, a, c, 0.0, 0.0},
                                   {0.0, 0.0, c, d, e, e}, {c, 0.0, 0.0, e, d, e}, {0.0, c, 0.0, e, e, d}};
@@ -297,7 +333,7 @@ __device__ __forceinline__ void p2_elem(double2 p0, double2 p1, double2 p2, doub
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
-        for (int b = 0; b < 3; b++) E[a][b] = a == b ? G[a][a] : -G[a][b] / 3.0;
+        for (int b = 0; b < 3; b++) E[a][b] = a == b ? G[a][a] : -G[a][b] * (1.0 / 3.0);
     // vertex - edge: 4/3 T G_ac for the edge (a, c), 0 for the opposite edge
 #pragma unroll
     for (int a = 0; a < 3; a++)
@@ -337,12 +373,111 @@ __global__ void __launch_bounds__(P2_BLOCK) k_p2_atomic(const int32_t* __restric
     }
 }
 
+// The element matrices into the staging buffer, row-major per element (kg[36k + 6 il + jl]). The
+// block's STAGE_BLOCK matrices go through shared memory (rows padded to 37 doubles, so the
+// threads' writes fall in different banks) and leave as one contiguous range written with
+// coalesced 16-byte stores; each thread writing its own 288 bytes directly would make every
+// store instruction touch 32 different lines.
+constexpr int STAGE_BLOCK = 128, STAGE_PAD = 37;
+
+template <int KIND>
+__global__ void __launch_bounds__(STAGE_BLOCK) k_p2_stage(const int32_t* __restrict__ me, int32_t nme, const double2* __restrict__ q,
+                                                          double* __restrict__ kg) {
+    __shared__ double tile[STAGE_BLOCK * STAGE_PAD];
+    for (int64_t k0 = (int64_t)blockIdx.x * STAGE_BLOCK; k0 < nme; k0 += (int64_t)gridDim.x * STAGE_BLOCK) {
+        const int64_t k = k0 + threadIdx.x;
+        if (k < nme) {
+            double E[6][6];
+            p2_elem<KIND>(q[me[k]], q[me[nme + k]], q[me[2 * (int64_t)nme + k]], E);
+#pragma unroll
+            for (int il = 0; il < 6; il++)
+#pragma unroll
+                for (int jl = 0; jl < 6; jl++) tile[threadIdx.x * STAGE_PAD + 6 * il + jl] = E[il][jl];
+        }
+        __syncthreads();
+        const int n = (int)min((int64_t)STAGE_BLOCK, (int64_t)nme - k0);
+        double2* o = reinterpret_cast<double2*>(kg + 36 * k0);
+        for (int c = threadIdx.x; c < 18 * n; c += STAGE_BLOCK) {       // 18 pairs per element
+            const int e = c / 18, j = 2 * (c - 18 * e);
+            o[c] = make_double2(tile[e * STAGE_PAD + j], tile[e * STAGE_PAD + j + 1]);
+        }
+        __syncthreads();
+    }
+}
+
+// Row sums of the staged matrices for the rows [r0, r1), one row per thread: the row's incidences
+// in ascending element order (records streamed from the row's list) each add row a of element k
+// (kg[36k + 6a ..], 48 bytes) into the row's accumulators in shared memory at the record's six
+// column positions. Accumulators start at -0.0, so every sum equals its first contribution
+// followed by the others in ascending element order, bit for bit. Rows with more than RMAX
+// columns are left to k_p2_rowsum_long.
+template <int RMAX>
+__global__ void __launch_bounds__(RS_BLOCK) k_p2_rowsum(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
+                                                        int32_t r0, int32_t r1, const int4* __restrict__ rrec,
+                                                        const double* __restrict__ kg, double* __restrict__ val) {
+    __shared__ double acc[RMAX * RS_BLOCK];
+    double* a = acc + threadIdx.x;                       // column c of this thread's row at a[c * RS_BLOCK]
+    for (int64_t rr = r0 + blockIdx.x * (int64_t)RS_BLOCK + threadIdx.x; rr < r1; rr += (int64_t)gridDim.x * RS_BLOCK) {
+        const int32_t rb = row_ptr[rr], u = row_ptr[rr + 1] - rb;
+        if (u > RMAX) continue;
+        const int32_t b0 = vptr[rr], d = vptr[rr + 1] - b0;
+        for (int c = 0; c < u; c++) a[c * RS_BLOCK] = -0.0;
+        int4 rec = d > 0 ? rrec[b0] : make_int4(0, 0, 0, 0);
+        for (int32_t t = 0; t < d; t++) {
+            const double2* e = reinterpret_cast<const double2*>(kg + 6 * (int64_t)rec.x);     // 36k + 6a
+            double2 v[3];
+#pragma unroll
+            for (int j = 0; j < 3; j++) v[j] = e[j];
+            const unsigned sl[3] = {(unsigned)rec.y, (unsigned)rec.z, (unsigned)rec.w};
+            if (t + 1 < d) rec = rrec[b0 + t + 1];
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                a[(sl[j] & 0xFFFFu) * RS_BLOCK] += v[j].x;
+                a[(sl[j] >> 16) * RS_BLOCK] += v[j].y;
+            }
+        }
+        for (int c = 0; c < u; c++) val[rb + c] = a[c * RS_BLOCK];
+    }
+}
+
+// The long rows, one warp each: lane l owns the columns c = l (mod 32) and adds their
+// contributions in ascending element order (accumulators in dynamic shared memory, RS_LONG_MAX
+// doubles at most).
+__global__ void __launch_bounds__(32) k_p2_rowsum_long(const int32_t* __restrict__ long_rows, const int32_t* __restrict__ n_long,
+                                                       const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
+                                                       const int4* __restrict__ rrec, const double* __restrict__ kg,
+                                                       double* __restrict__ val) {
+    extern __shared__ double accl[];
+    const int lane = threadIdx.x;
+    const int32_t n = *n_long;
+    for (int32_t b = blockIdx.x; b < n; b += gridDim.x) {
+        const int32_t r = long_rows[b];
+        const int32_t rb = row_ptr[r], u = row_ptr[r + 1] - rb;
+        const int32_t b0 = vptr[r], d = vptr[r + 1] - b0;
+        for (int c = lane; c < u; c += 32) accl[c] = -0.0;
+        __syncwarp();
+        for (int32_t t = 0; t < d; t++) {
+            const int4 rec = rrec[b0 + t];
+            const int64_t base = 6 * (int64_t)rec.x;
+            const unsigned c6[6] = {(unsigned)rec.y & 0xFFFFu, (unsigned)rec.y >> 16, (unsigned)rec.z & 0xFFFFu,
+                                    (unsigned)rec.z >> 16, (unsigned)rec.w & 0xFFFFu, (unsigned)rec.w >> 16};
+#pragma unroll
+            for (int jl = 0; jl < 6; jl++)
+                if ((int)(c6[jl] & 31u) == lane) accl[c6[jl]] += kg[base + jl];
+        }
+        __syncwarp();
+        for (int c = lane; c < u; c += 32) val[rb + c] = accl[c];
+        __syncwarp();
+    }
+}
+
 }  // namespace
 
 extern "C" void fe_p2_pattern_destroy(fe_p2_pattern p) {
     if (!p) return;
     FeStreamScope scope(p->last_stream);
     fe_free(p->row_ptr); fe_free(p->col_idx); fe_free(p->map); fe_free(p->edof);
+    fe_free(p->vptr); fe_free(p->rrec); fe_free(p->long_rows); fe_free(p->n_long); fe_free(p->kg);
     delete p;
 }
 
@@ -357,7 +492,7 @@ struct P2Temps {
 };
 }  // namespace
 
-extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, fe_stream stream, fe_p2_pattern* out) {
+extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, int flags, fe_stream stream, fe_p2_pattern* out) {
     if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     fe_status st;
@@ -366,7 +501,9 @@ extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, fe_stream str
     if (36 * (int64_t)nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "36*nme must be < 2^31");
     cudaStream_t s = (cudaStream_t)stream;
     FeStreamScope scope(s);
+    const bool gather = (flags & FE_PATTERN_GATHER) != 0;
     fe_p2_pattern p = new fe_p2_pattern_s();
+    p->flags = gather ? FE_PATTERN_GATHER : 0;
     p->nq = nq;
     p->nme = nme;
     p->topology_id = m->topology_id;
@@ -414,21 +551,28 @@ extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, fe_stream str
     if ((st = fe_alloc_n(&t.counters, 4, "counters"))) return fail(st);
     if ((st = fe_alloc_n(&p->map, 36 * (size_t)nme, "element-to-nnz map"))) return fail(st);
     if (cudaMemsetAsync(t.counters, 0, 4 * sizeof(int32_t), s) != cudaSuccess) return fail(fe_fail(FE_ERR_CUDA, "memset"));
+    if (gather) {
+        if ((st = fe_alloc_n(&p->rrec, 6 * (size_t)nme, "row incidence records"))) return fail(st);
+        if ((st = fe_alloc_n(&p->long_rows, (size_t)ndof + 1, "long rows"))) return fail(st);
+        if ((st = fe_alloc_n(&p->n_long, 1, "long-row count"))) return fail(st);
+        if (cudaMemsetAsync(p->n_long, 0, sizeof(int32_t), s) != cudaSuccess) return fail(fe_fail(FE_ERR_CUDA, "memset"));
+    }
+    const P2Lists ls{p->rrec, p->long_rows, p->n_long, nq};
     if (ndof > 0) {
         if (nq > 0) {
             { FE_PROF("k_p2_rows", s); k_p2_rows<<<fe_grid(((int64_t)nq + P2_WARPS - 1) / P2_WARPS, 1, 12), P2_WARPS * 32, 0, s>>>(
-                  t.vptr, t.inc, p->edof, nq, t.tmp, t.cnt, p->map, t.big, t.counters); }
+                  t.vptr, t.inc, p->edof, nq, t.tmp, t.cnt, p->map, t.big, t.counters, ls); }
             FE_LAUNCHED("k_p2_rows");
         }
         if (ndof > nq) {
             { FE_PROF("k_p2_edge_rows", s); k_p2_edge_rows<<<fe_grid((int64_t)ndof - nq, P2_BLOCK, 8), P2_BLOCK, 0, s>>>(
-                  t.vptr, t.inc, p->edof, nq, ndof, t.tmp, t.cnt, p->map, t.big, t.counters); }
+                  t.vptr, t.inc, p->edof, nq, ndof, t.tmp, t.cnt, p->map, t.big, t.counters, ls); }
             FE_LAUNCHED("k_p2_edge_rows");
         }
         const size_t big_smem = sizeof(P2Smem<BIG_TS, BIG_EMAX>);
         FE_CUDA(cudaFuncSetAttribute(k_p2_rows_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem));
         { FE_PROF("k_p2_rows_big", s); k_p2_rows_big<<<fe_sm_count(), 32, big_smem, s>>>(t.vptr, t.inc, p->edof, t.big, t.counters,
-                                                                                          t.tmp, t.cnt, p->map, t.counters + 1); }
+                                                                                          t.tmp, t.cnt, p->map, t.counters + 1, ls); }
         FE_LAUNCHED("k_p2_rows_big");
     }
     if ((st = fe_alloc_n(&p->row_ptr, (size_t)ndof + 1, "row_ptr"))) return fail(st);
@@ -436,6 +580,7 @@ extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, fe_stream str
     if ((st = fe_exclusive_scan(t.cnt, p->row_ptr, ndof, s, &nnz))) return fail(st);   // synchronises
     int too_big = 0;
     if (cudaMemcpyAsync(&too_big, t.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        (gather && cudaMemcpyAsync(&p->n_long_host, p->n_long, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return fail(fe_fail(FE_ERR_CUDA, "flag read-back"));
     if (too_big)
@@ -450,6 +595,11 @@ extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, fe_stream str
     if (nme > 0) {
         { FE_PROF("k_p2_map_base", s); k_p2_map_base<<<fe_grid(36 * (int64_t)nme, P2_BLOCK), P2_BLOCK, 0, s>>>(p->edof, nme, p->row_ptr, p->map); }
         FE_LAUNCHED("k_p2_map_base");
+    }
+    if (gather) {
+        if ((st = fe_alloc_n(&p->kg, 36 * (size_t)nme, "element value staging"))) return fail(st);
+        p->vptr = t.vptr;                            // the row sums need the incidence offsets
+        t.vptr = nullptr;
     }
     *out = p;
     return FE_OK;
@@ -473,10 +623,15 @@ extern "C" fe_status fe_p2_pattern_dofs(fe_p2_pattern p, const int32_t** edof, c
     return FE_OK;
 }
 
-extern "C" fe_status fe_p2_assemble(fe_mesh m, fe_p2_pattern p, int kind, double* values, int64_t cap, fe_stream stream) {
+extern "C" fe_status fe_p2_assemble(fe_mesh m, fe_p2_pattern p, int kind, int variant, double* values, int64_t cap,
+                                    fe_stream stream) {
     if (!m || !p) return fe_fail(FE_ERR_INVALID_ARG, "null mesh or pattern");
     if (m->topology_id != p->topology_id) return fe_fail(FE_ERR_INVALID_ARG, "the pattern was built for another mesh");
     if (kind != FE_P2_MASS && kind != FE_P2_STIFF) return fe_fail(FE_ERR_INVALID_ARG, "unknown kind");
+    if (variant != FE_VARIANT_ATOMIC && variant != FE_VARIANT_GATHER)
+        return fe_fail(FE_ERR_INVALID_ARG, "P2 takes FE_VARIANT_ATOMIC or FE_VARIANT_GATHER");
+    if (variant == FE_VARIANT_GATHER && !(p->flags & FE_PATTERN_GATHER))
+        return fe_fail(FE_ERR_INVALID_ARG, "FE_VARIANT_GATHER needs a P2 pattern built with FE_PATTERN_GATHER");
     if (cap < p->nnz) return fe_fail(FE_ERR_BUFFER_TOO_SMALL, "cap is below nnz");
     if (!values && p->nnz > 0) return fe_fail(FE_ERR_INVALID_ARG, "values is null");
     cudaStream_t s = (cudaStream_t)stream;
@@ -484,8 +639,35 @@ extern "C" fe_status fe_p2_assemble(fe_mesh m, fe_p2_pattern p, int kind, double
     m->last_stream = s;
     p->last_stream = s;
     if (p->nnz == 0) return FE_OK;
-    FE_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * (size_t)p->nnz, s));
     const int32_t nme = m->nme;
+    if (variant == FE_VARIANT_GATHER) {
+        if (nme > 0) {
+            FE_PROF("k_p2_stage", s);
+            const unsigned g = fe_grid(nme, STAGE_BLOCK, 4);
+            if (kind == FE_P2_MASS) k_p2_stage<FE_P2_MASS><<<g, STAGE_BLOCK, 0, s>>>(m->me, nme, m->q, p->kg);
+            else k_p2_stage<FE_P2_STIFF><<<g, STAGE_BLOCK, 0, s>>>(m->me, nme, m->q, p->kg);
+        }
+        FE_LAUNCHED("k_p2_stage");
+        const int32_t nq = p->nq, ndof = p->ndof;
+        if (nq > 0) {
+            { FE_PROF("k_p2_rowsum<32> (vertex rows)", s); k_p2_rowsum<RS_VERTEX><<<fe_grid(nq, RS_BLOCK, 8), RS_BLOCK, 0, s>>>(
+                  p->vptr, p->row_ptr, 0, nq, p->rrec, p->kg, values); }
+            FE_LAUNCHED("k_p2_rowsum (vertex rows)");
+        }
+        if (ndof > nq) {
+            { FE_PROF("k_p2_rowsum<16> (edge rows)", s); k_p2_rowsum<RS_EDGE><<<fe_grid((int64_t)ndof - nq, RS_BLOCK, 16), RS_BLOCK, 0, s>>>(
+                  p->vptr, p->row_ptr, nq, ndof, p->rrec, p->kg, values); }
+            FE_LAUNCHED("k_p2_rowsum (edge rows)");
+        }
+        if (p->n_long_host > 0) {
+            const size_t sm = (size_t)RS_LONG_MAX * sizeof(double);
+            { FE_PROF("k_p2_rowsum_long", s); k_p2_rowsum_long<<<fe_sm_count() * 8, 32, sm, s>>>(
+                  p->long_rows, p->n_long, p->vptr, p->row_ptr, p->rrec, p->kg, values); }
+            FE_LAUNCHED("k_p2_rowsum_long");
+        }
+        return FE_OK;
+    }
+    FE_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * (size_t)p->nnz, s));
     if (nme > 0) {
         FE_PROF("k_p2_atomic", s);
         const unsigned g = fe_grid(nme, P2_BLOCK, 8);

@@ -55,11 +55,11 @@ SIGNATURES = {
     "fe_tet_pattern_map": (_INT, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
     "fe_tet_pattern_destroy": (None, [_P]),
     "fe_tet_assemble": (_INT, [_P, _P, _INT, _P, _INT, _P, _I64, _P]),
-    "fe_p2_pattern_build": (_INT, [_P, _P, _P, ctypes.POINTER(_P)]),
+    "fe_p2_pattern_build": (_INT, [_P, _P, _INT, _P, ctypes.POINTER(_P)]),
     "fe_p2_pattern_info": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "fe_p2_pattern_dofs": (_INT, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
     "fe_p2_pattern_destroy": (None, [_P]),
-    "fe_p2_assemble": (_INT, [_P, _P, _INT, _P, _I64, _P]),
+    "fe_p2_assemble": (_INT, [_P, _P, _INT, _INT, _P, _I64, _P]),
     "fe_assemble_stiff_wmass_host": (_INT, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "fe_batch_create": (_INT, [_I32, _P, _P, ctypes.POINTER(_P)]),
     "fe_batch_tune": (_INT, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
@@ -346,11 +346,13 @@ P2_MASS, P2_STIFF = 0, 1
 class P2Pattern:
     """P2 (quadratic) dofs, CSR structure and map of a triangle mesh (fe_p2_pattern_build): vertex i
     is dof i, the edges follow in ascending (smaller id, larger id) order. Built from the mesh's
-    scalar pattern, whose structure numbers the edges."""
+    scalar pattern, whose structure numbers the edges. gather=True adds the row lists of the
+    deterministic variant (GATHER)."""
 
-    def __init__(self, mesh: Mesh, pattern: Pattern, stream=None):
+    def __init__(self, mesh: Mesh, pattern: Pattern, gather: bool = False, stream=None):
         h = _P()
-        _check(lib().fe_p2_pattern_build(mesh.handle, pattern.handle, _stream(stream), ctypes.byref(h)),
+        flags = PATTERN_GATHER if gather else 0
+        _check(lib().fe_p2_pattern_build(mesh.handle, pattern.handle, flags, _stream(stream), ctypes.byref(h)),
                "fe_p2_pattern_build")
         self._h = h
         self.mesh = mesh
@@ -382,13 +384,14 @@ class P2Pattern:
         self.close()
 
 
-def p2_assemble(mesh: Mesh, pattern: P2Pattern, kind: int, out=None, stream=None) -> torch.Tensor:
-    """Values of the P2 mass (P2_MASS) or stiffness (P2_STIFF) on the P2 pattern (fe_p2_assemble)."""
+def p2_assemble(mesh: Mesh, pattern: P2Pattern, kind: int, out=None, stream=None, variant: int = ATOMIC) -> torch.Tensor:
+    """Values of the P2 mass (P2_MASS) or stiffness (P2_STIFF) on the P2 pattern (fe_p2_assemble),
+    by FP64 atomics (ATOMIC) or by ordered row sums (GATHER, a pattern built with gather=True)."""
     out = pattern.new_values() if out is None else out
     if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
         raise ValueError("out must be a contiguous float64 CUDA tensor")
-    _check(lib().fe_p2_assemble(mesh.handle, pattern.handle, kind, out.data_ptr(), out.numel(), _stream(stream)),
-           "fe_p2_assemble")
+    _check(lib().fe_p2_assemble(mesh.handle, pattern.handle, kind, variant, out.data_ptr(), out.numel(),
+                                _stream(stream)), "fe_p2_assemble")
     return out
 
 

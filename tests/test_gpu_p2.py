@@ -1,9 +1,11 @@
 """P2 (quadratic) triangles through the C ABI against the oracle.
 
 Dof numbering, row_ptr / col_idx and the element map are compared bit-exactly, values within 1e-13
-of each row's largest |a_ij|. Meshes: jittered node-permuted squares (several warps and blocks), a
-fan whose centre belongs to 70 triangles (the long-row kernel), the one- and two-triangle meshes,
-and the 1024 x 1024-cell square at full size on sampled rows.
+of each row's largest |a_ij| for both variants (FP64 atomics, ordered row sums); the ordered
+variant must be bit-identical from run to run. Meshes: jittered node-permuted squares (several
+warps and blocks), fans whose centre belongs to 8 triangles (a 25-column vertex row), 12 (37
+columns: a long row from the warp pass) and 70 (the long-row pass), the one- and two-triangle
+meshes, and the 1024 x 1024-cell square at full size on sampled rows.
 """
 from __future__ import annotations
 
@@ -19,6 +21,7 @@ from tests.test_gpu_parity import fan_mesh
 pytestmark = pytest.mark.gpu
 
 KINDS = {"mass": (feasm.P2_MASS, oracle.MASS), "stiff": (feasm.P2_STIFF, oracle.STIFF)}
+VARIANTS = {"atomic": feasm.ATOMIC, "gather": feasm.GATHER}
 
 
 def _cases():
@@ -26,6 +29,8 @@ def _cases():
     for N, seed in ((1, 1), (5, 2), (37, 3)):
         m = meshgen.square_mesh(N, seed)
         out[f"square{N}"] = (m.q, m.me)
+    out["fan8"] = fan_mesh(8)
+    out["fan12"] = fan_mesh(12)
     out["fan70"] = fan_mesh(70)
     q2 = np.array([[0.0, 1.0, 1.0, 0.0], [0.0, 0.0, 1.0, 1.0]])
     me2 = np.array([[0, 0], [1, 2], [2, 3]], np.int32)
@@ -37,10 +42,10 @@ def _cases():
 CASES = _cases()
 
 
-def _build(q, me):
+def _build(q, me, gather=False):
     mesh = feasm.Mesh(q, me)
     pat = feasm.Pattern(mesh)
-    return mesh, feasm.P2Pattern(mesh, pat), pat
+    return mesh, feasm.P2Pattern(mesh, pat, gather=gather), pat
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
@@ -62,13 +67,32 @@ def test_p2_dofs_pattern_and_map(case):
 
 @pytest.mark.parametrize("case", sorted(CASES))
 @pytest.mark.parametrize("kind", sorted(KINDS))
-def test_p2_values(case, kind):
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+def test_p2_values(case, kind, variant):
     q, me = CASES[case]
-    mesh, p2, _ = _build(q, me)
+    v = VARIANTS[variant]
+    mesh, p2, _ = _build(q, me, gather=v == feasm.GATHER)
     kg, ko = KINDS[kind]
-    got = feasm.p2_assemble(mesh, p2, kg)
+    got = feasm.p2_assemble(mesh, p2, kg, variant=v)
     rp, ci, va = oracle.p2_assemble(ko, q, me)
+    assert_csr_equal(p2.row_ptr.cpu(), p2.col_idx.cpu(), rp, ci)
     assert_values_close(rp, got.cpu().numpy(), va)
+
+
+@pytest.mark.parametrize("case", ["square37", "fan12", "fan70"])
+def test_p2_gather_bit_identical_runs(case):
+    """The ordered variant sums each non-zero in ascending element order: ten runs, one result,
+    and both variants' patterns alike."""
+    q, me = CASES[case]
+    mesh, p2, pat = _build(q, me, gather=True)
+    p2a = feasm.P2Pattern(mesh, pat)
+    np.testing.assert_array_equal(p2.col_idx.cpu().numpy(), p2a.col_idx.cpu().numpy())
+    np.testing.assert_array_equal(p2.map.cpu().numpy(), p2a.map.cpu().numpy())
+    for kind in (feasm.P2_MASS, feasm.P2_STIFF):
+        first = feasm.p2_assemble(mesh, p2, kind, variant=feasm.GATHER).cpu().numpy()
+        for _ in range(9):
+            again = feasm.p2_assemble(mesh, p2, kind, variant=feasm.GATHER).cpu().numpy()
+            assert np.array_equal(first.view(np.int64), again.view(np.int64))
 
 
 def test_p2_quadratic_energy():
@@ -87,18 +111,20 @@ def test_p2_empty_mesh_and_isolated_vertex():
     triangle keeps an empty row next to a meshed one."""
     q = np.zeros((2, 5))
     mesh = feasm.Mesh(q, np.zeros((3, 0), np.int32))
-    p2 = feasm.P2Pattern(mesh, feasm.Pattern(mesh))
+    p2 = feasm.P2Pattern(mesh, feasm.Pattern(mesh), gather=True)
     assert p2.n_rows == 5 and p2.nnz == 0 and p2.n_edges == 0
     assert p2.row_ptr.cpu().tolist() == [0] * 6
     assert feasm.p2_assemble(mesh, p2, feasm.P2_STIFF).numel() == 0
+    assert feasm.p2_assemble(mesh, p2, feasm.P2_STIFF, variant=feasm.GATHER).numel() == 0
     q = np.array([[0.0, 1.0, 0.0, 5.0], [0.0, 0.0, 1.0, 5.0]])           # vertex 3 in no triangle
     me = np.array([[0], [1], [2]], np.int32)
     mesh = feasm.Mesh(q, me)
-    p2 = feasm.P2Pattern(mesh, feasm.Pattern(mesh))
+    p2 = feasm.P2Pattern(mesh, feasm.Pattern(mesh), gather=True)
     rp, ci, va = oracle.p2_assemble(oracle.STIFF, q, me)
     assert_csr_equal(p2.row_ptr.cpu(), p2.col_idx.cpu(), rp, ci)
     assert rp[4] - rp[3] == 0
-    assert_values_close(rp, feasm.p2_assemble(mesh, p2, feasm.P2_STIFF).cpu().numpy(), va)
+    for v in (feasm.ATOMIC, feasm.GATHER):
+        assert_values_close(rp, feasm.p2_assemble(mesh, p2, feasm.P2_STIFF, variant=v).cpu().numpy(), va)
 
 
 def test_p2_errors():
@@ -117,6 +143,10 @@ def test_p2_errors():
     pat2 = feasm.Pattern(mesh, dofs=2, map=False)
     with pytest.raises(feasm.FeasmError):
         feasm.P2Pattern(mesh, pat2)                       # needs the scalar pattern
+    with pytest.raises(feasm.FeasmError):
+        feasm.p2_assemble(mesh, p2, feasm.P2_STIFF, variant=feasm.GATHER)    # pattern without the row lists
+    with pytest.raises(feasm.FeasmError):
+        feasm.p2_assemble(mesh, p2, feasm.P2_STIFF, variant=feasm.ROW)       # no row-owner P2 kernel
 
 
 def test_p2_full_size_sampled_rows():
@@ -126,14 +156,15 @@ def test_p2_full_size_sampled_rows():
     m = meshgen.square_mesh(1024, seed)
     mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))
     pat = feasm.Pattern(mesh, map=False)
-    p2 = feasm.P2Pattern(mesh, pat)
+    p2 = feasm.P2Pattern(mesh, pat, gather=True)
     assert p2.n_rows == m.nq + 3 * 1024 * 1024 + 2 * 1024
     rows = np.concatenate([meshgen.sample_indices(seed, 6, m.nq), m.nq + meshgen.sample_indices(seed + 1, 6, p2.n_edges)])
     rp = p2.row_ptr.cpu().numpy()
     ci = p2.col_idx.cpu().numpy()
     for kg, ko in KINDS.values():
-        got = feasm.p2_assemble(mesh, p2, kg).cpu().numpy()
         want = oracle.p2_row_values(ko, m.q, m.me, rows)
-        for r, (cols, vals) in zip(rows, want):
-            np.testing.assert_array_equal(ci[rp[r]:rp[r + 1]], cols)
-            assert np.abs(got[rp[r]:rp[r + 1]] - vals).max() <= 1e-13 * np.abs(vals).max()
+        for v in (feasm.ATOMIC, feasm.GATHER):
+            got = feasm.p2_assemble(mesh, p2, kg, variant=v).cpu().numpy()
+            for r, (cols, vals) in zip(rows, want):
+                np.testing.assert_array_equal(ci[rp[r]:rp[r + 1]], cols)
+                assert np.abs(got[rp[r]:rp[r + 1]] - vals).max() <= 1e-13 * np.abs(vals).max()
