@@ -4,8 +4,9 @@ Dof numbering, row_ptr / col_idx and the element map are compared bit-exactly, v
 of each row's largest |a_ij| for both variants (FP64 atomics, ordered row sums); the ordered
 variant must be bit-identical from run to run. Meshes: jittered node-permuted squares (several
 warps and blocks), fans whose centre belongs to 8 triangles (a 25-column vertex row), 12 (37
-columns: a long row from the warp pass) and 70 (the long-row pass), the one- and two-triangle
-meshes, and the 1024 x 1024-cell square at full size on sampled rows.
+columns: a long row from the warp pass) and 70 (the long-row pass), five triangles on one edge
+(an 18-column edge row), the one- and two-triangle meshes, and the 1024 x 1024-cell square at full
+size on sampled rows.
 """
 from __future__ import annotations
 
@@ -32,6 +33,11 @@ def _cases():
     out["fan8"] = fan_mesh(8)
     out["fan12"] = fan_mesh(12)
     out["fan70"] = fan_mesh(70)
+    # five triangles on one edge (0, 1): the edge's dof row has 18 columns (2 + 5 vertices, 1 + 10
+    # edges), longer than an edge row's accumulators: the long-row kernel through the big-row pass
+    qb = np.array([[0.0, 1.0, 0.5, 0.4, 0.6, 0.5, 0.3], [0.0, 0.0, 1.0, 2.0, 3.0, -1.0, -2.0]])
+    meb = np.array([[0, 0, 0, 1, 1], [1, 1, 1, 0, 0], [2, 3, 4, 5, 6]], np.int32)
+    out["book5"] = (qb, meb)
     q2 = np.array([[0.0, 1.0, 1.0, 0.0], [0.0, 0.0, 1.0, 1.0]])
     me2 = np.array([[0, 0], [1, 2], [2, 3]], np.int32)
     out["two"] = (q2, me2)
@@ -79,7 +85,7 @@ def test_p2_values(case, kind, variant):
     assert_values_close(rp, got.cpu().numpy(), va)
 
 
-@pytest.mark.parametrize("case", ["square37", "fan12", "fan70"])
+@pytest.mark.parametrize("case", ["square37", "fan12", "fan70", "book5"])
 def test_p2_gather_bit_identical_runs(case):
     """The ordered variant sums each non-zero in ascending element order: ten runs, one result,
     and both variants' patterns alike."""
