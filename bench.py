@@ -343,6 +343,10 @@ def run_ours(args) -> int:
             "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 5), "launches": int(v[1]),
                             "share": round(v[0] / sum(x[0] for x in prof.values()), 4)} for k, v in sorted(prof.items())},
             "assemble_only": asm}
+    # end to end through the host-buffer call, right after the device-resident step (before the
+    # other legs fill the device memory pools)
+    if not args.no_e2e:
+        line["e2e"] = e2e(feasm, torch, m, w, args)
     if not args.no_batched:
         line["batched"] = batched(feasm, meshgen, torch, args)
     if not args.no_other:
@@ -351,8 +355,6 @@ def run_ours(args) -> int:
         line["drop_zeros"] = drop_zeros(feasm, torch, pat0, S, flush, hbm, peak_kind, cells=args.cells)
         line["tetrahedra"] = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind)
         line["p2"] = p2(feasm, meshgen, torch, flush, hbm, peak_kind)
-    if not args.no_e2e:
-        line["e2e"] = e2e(feasm, torch, m, w, args)
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample()
     print(json.dumps(line), flush=True)
