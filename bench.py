@@ -159,6 +159,71 @@ def cpu_oracle_sample(target_s: float = 10.0, n_cells: int = 512) -> dict:
                       f"(nme={m.nme}), {el:.1f} s, single-threaded C oracle"}
 
 
+def _oracle_rate(fn, units: float, target_s: float) -> tuple[float, int, float]:
+    """Repeat fn() for about target_s seconds; units processed per second, repetitions, seconds."""
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        fn()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= target_s:
+            return reps * units / el, reps, el
+
+
+def cpu_oracle_legs(legs, target_s: float = 2.0) -> dict:
+    """The oracle beside each other leg: each leg's computation by the single-threaded C oracle on
+    a bounded sample of that leg's workload (same recipe, smaller size), in the leg's own unit."""
+    import oracle
+    from paper_1305_3122_gb300 import meshgen
+
+    out = {}
+
+    def entry(rate, unit, reps, el, what):
+        return {"value": round(rate, 4), "unit": unit, "cores": 1, "kind": "oracle",
+                "sample": f"{reps} x {what}, {el:.1f} s"}
+
+    if "elasticity" in legs:
+        m = meshgen.square_mesh(256, 13053122 + 3)
+        r = _oracle_rate(lambda: oracle.assemble(oracle.ELAS, m.q, m.me, lam=1.0, mu=0.5), m.nme / 1e6, target_s)
+        out["elasticity"] = entry(*r[:1], "Melem/s", r[1], r[2], f"K (lambda 1, mu 0.5) on the 256x256-cell mesh (nme={m.nme})")
+    if "adjoint" in legs:
+        seed = 13053122 + 5
+        m = meshgen.square_mesh(256, seed)
+        w = meshgen.vertex_weights(m, seed)
+        rp, ci, _ = oracle.assemble(oracle.STIFF, m.q, m.me)
+        GS, GM = meshgen.upstream_gradients(seed, len(ci))
+
+        def adj():
+            dq, dw = oracle.adjoint(oracle.STIFF, m.q, m.me, rp, ci, GS, w)
+            oracle.adjoint(oracle.WMASS, m.q, m.me, rp, ci, GM, w, dq, dw)
+        r = _oracle_rate(adj, m.nme / 1e6, target_s)
+        out["adjoint"] = entry(r[0], "Melem/s", r[1], r[2], f"dL/dq, dL/dw of <G_S, S> + <G_M, M^[w]> on the 256x256-cell mesh (nme={m.nme})")
+    if "drop_zeros" in legs:
+        m = meshgen.square_mesh(512, SEED)
+        rp, ci, va = oracle.assemble(oracle.STIFF, m.q, m.me)
+        r = _oracle_rate(lambda: oracle.drop_zeros(rp, ci, va), len(va) / 1e9, target_s)
+        out["drop_zeros"] = entry(r[0], "Gentries/s", r[1], r[2], f"zero dropping of S on the 512x512-cell mesh (nnz={len(va)})")
+    if "tetrahedra" in legs:
+        m = meshgen.cube_mesh(24, 13053122 + 6)
+        r = _oracle_rate(lambda: oracle.tet_assemble(oracle.STIFF, m.q, m.me), m.nme / 1e6, target_s)
+        out["tetrahedra"] = entry(r[0], "Melem/s", r[1], r[2], f"S on the 24^3-cell cube (nme={m.nme})")
+    if "p2" in legs:
+        m = meshgen.square_mesh(48, 13053122 + 7)
+        r = _oracle_rate(lambda: oracle.p2_assemble(oracle.STIFF, m.q, m.me), m.nme / 1e6, target_s)
+        out["p2"] = entry(r[0], "Melem/s", r[1], r[2], f"P2 S on the 48x48-cell square (nme={m.nme})")
+    if "batched" in legs:
+        ms = meshgen.batch_meshes(13053122 + 4, count=8)
+        n = sum(x.nme for x in ms)
+
+        def batch():
+            for x in ms:
+                oracle.assemble(oracle.STIFF, x.q, x.me)
+                oracle.assemble(oracle.MASS, x.q, x.me)
+        r = _oracle_rate(batch, n / 1e6, target_s)
+        out["batched"] = entry(r[0], "Melem/s", r[1], r[2], f"S + M of the batch recipe's first 8 meshes (nme={n})")
+    return out
+
+
 def run_reference(args) -> int:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -357,6 +422,9 @@ def run_ours(args) -> int:
         line["p2"] = p2(feasm, meshgen, torch, flush, hbm, peak_kind)
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample()
+        legs = [k for k in ("batched", "elasticity", "adjoint", "drop_zeros", "tetrahedra", "p2") if k in line]
+        if legs:
+            line["cpu_baseline"]["legs"] = cpu_oracle_legs(legs)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
