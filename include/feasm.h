@@ -390,6 +390,18 @@ fe_status fe_profile_reset(void);
 fe_status fe_profile_read(int32_t max_entries, char* names, double* total_ms, int64_t* launches,
                           int32_t* count);
 
+/* ----------------------------------------------------------------------- test hooks ---- */
+
+/* Allocation-failure injection, for the tests of the error paths (not in the paper): after
+ * fe_debug_fail_alloc(n) with n >= 1, the n-th device allocation the library makes from then on
+ * fails as if the device were out of memory. The call that makes it returns FE_ERR_OOM, having
+ * released everything it had allocated. Later allocations succeed again; n <= 0 switches the
+ * injection off. Process-wide. fe_debug_pool_used returns the bytes currently allocated from the
+ * library's device memory pool (the memory that meshes, patterns, batches and running calls
+ * hold), so that a test can check that a failed call left nothing behind. */
+void fe_debug_fail_alloc(int64_t n);
+fe_status fe_debug_pool_used(int64_t* bytes);
+
 /* ---------------------------------------------------------------------------- status ---- */
 
 const char* fe_status_string(fe_status status);

@@ -189,6 +189,7 @@ __global__ void k_adjoint_gather(const int32_t* __restrict__ vptr, const int32_t
 
 extern "C" fe_status fe_adjoint_stiff_wmass(fe_mesh m, fe_pattern p, const double* w, const double* gS,
                                             const double* gM, int variant, double* dq, double* dw, fe_stream stream) {
+    FE_RANGE(__func__);
     fe_status st;
     if ((st = fe_check_pair(m, p, 1))) return st;
     if (variant != FE_VARIANT_ATOMIC && variant != FE_VARIANT_GATHER) return fe_fail(FE_ERR_INVALID_ARG, "unknown variant");

@@ -346,25 +346,30 @@ static fe_status scalar(int kind, fe_mesh m, fe_pattern p, const double* w, int 
 }
 
 extern "C" fe_status fe_assemble_mass(fe_mesh m, fe_pattern p, int variant, double* values, int64_t cap, fe_stream s) {
+    FE_RANGE(__func__);
     return scalar(K_MASS, m, p, nullptr, variant, values, nullptr, cap, (cudaStream_t)s);
 }
 
 extern "C" fe_status fe_assemble_wmass(fe_mesh m, fe_pattern p, const double* w, int variant, double* values,
                                        int64_t cap, fe_stream s) {
+    FE_RANGE(__func__);
     return scalar(K_WMASS, m, p, w, variant, values, nullptr, cap, (cudaStream_t)s);
 }
 
 extern "C" fe_status fe_assemble_stiff(fe_mesh m, fe_pattern p, int variant, double* values, int64_t cap, fe_stream s) {
+    FE_RANGE(__func__);
     return scalar(K_STIFF, m, p, nullptr, variant, values, nullptr, cap, (cudaStream_t)s);
 }
 
 extern "C" fe_status fe_assemble_stiff_wmass(fe_mesh m, fe_pattern p, const double* w, int variant, double* S,
                                              double* Mw, int64_t cap, fe_stream s) {
+    FE_RANGE(__func__);
     return scalar(K_STIFF_WMASS, m, p, w, variant, S, Mw, cap, (cudaStream_t)s);
 }
 
 extern "C" fe_status fe_assemble_elas(fe_mesh m, fe_pattern p, double lam, double mu, int variant, double* values,
                                       int64_t cap, fe_stream stream) {
+    FE_RANGE(__func__);
     fe_status st;
     if ((st = fe_check_pair(m, p, 2))) return st;
     if ((st = check_variant(p, variant))) return st;
@@ -425,6 +430,7 @@ static fe_status noalloc_scratch(double** out) {
 
 extern "C" fe_status fe_assemble_stiff_wmass_noalloc(fe_mesh m, fe_pattern p, const double* w, double* S, double* Mw,
                                                      int64_t cap, fe_stream stream) {
+    FE_RANGE(__func__);
     fe_status st;
     if ((st = fe_check_pair(m, p, 1))) return st;
     if (!(p->flags & FE_PATTERN_GATHER))

@@ -195,6 +195,7 @@ extern "C" void fe_batch_destroy(fe_batch b) {
 }
 
 extern "C" fe_status fe_batch_create(int32_t n, const fe_mesh* meshes, const fe_pattern* patterns, fe_batch* out) {
+    FE_RANGE(__func__);
     if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     if (n < 0 || (n > 0 && (!meshes || !patterns))) return fe_fail(FE_ERR_INVALID_ARG, "bad mesh list");
@@ -278,6 +279,7 @@ extern "C" fe_status fe_batch_get_config(fe_batch b, int32_t* variant, int32_t* 
 }
 
 extern "C" fe_status fe_batch_assemble_stiff_mass(fe_batch b, double* const* S, double* const* M, fe_stream stream) {
+    FE_RANGE(__func__);
     if (!b) return fe_fail(FE_ERR_INVALID_ARG, "null batch");
     cudaStream_t s = (cudaStream_t)stream;
     fe_status st = set_outputs(b, S, M, s);
@@ -288,6 +290,7 @@ extern "C" fe_status fe_batch_assemble_stiff_mass(fe_batch b, double* const* S, 
 }
 
 extern "C" fe_status fe_batch_assemble_stiff_mass_plain(fe_batch b, double* const* S, double* const* M, fe_stream stream) {
+    FE_RANGE(__func__);
     if (!b) return fe_fail(FE_ERR_INVALID_ARG, "null batch");
     if (!S || !M) return fe_fail(FE_ERR_INVALID_ARG, "null output table");
     cudaStream_t s = (cudaStream_t)stream;
@@ -315,6 +318,7 @@ extern "C" fe_status fe_batch_assemble_stiff_mass_plain(fe_batch b, double* cons
 
 extern "C" fe_status fe_batch_tune(fe_batch b, double* const* S, double* const* M, fe_stream stream, int32_t* block_out,
                                    int32_t* tile_out) {
+    FE_RANGE(__func__);
     if (!b) return fe_fail(FE_ERR_INVALID_ARG, "null batch");
     cudaStream_t s = (cudaStream_t)stream;
     fe_status st = set_outputs(b, S, M, s);

@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(CZ_BLOCK) k_compact_rows(const int32_t* __rest
 extern "C" fe_status fe_csr_drop_zeros(int64_t n_rows, const int32_t* row_ptr, const int32_t* col_idx,
                                        const double* values, int32_t* row_ptr_out, int32_t* col_idx_out,
                                        double* values_out, int64_t cap, int64_t* nnz_out, fe_stream stream) {
+    FE_RANGE(__func__);
     if (!nnz_out) return fe_fail(FE_ERR_INVALID_ARG, "nnz_out is null");
     *nnz_out = 0;
     if (n_rows < 0 || n_rows >= INT32_MAX) return fe_fail(FE_ERR_INVALID_ARG, "n_rows must be in [0, 2^31 - 1)");

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -194,6 +195,16 @@ inline fe_status fe_alloc_n(T** p, size_t n, const char* what) {
 void fe_free(void* p);
 
 // ------------------------------------------------------------------------ launch shapes
+
+// NVTX range over an entry point (named after the function), shown by Nsight tools; without a tool
+// attached the push and pop return at once.
+struct FeRange {
+    explicit FeRange(const char* name) { nvtxRangePushA(name); }
+    ~FeRange() { nvtxRangePop(); }
+    FeRange(const FeRange&) = delete;
+    FeRange& operator=(const FeRange&) = delete;
+};
+#define FE_RANGE(name) FeRange fe_range_(name)
 
 int fe_sm_count();
 inline unsigned fe_grid(int64_t n, int block, int per_sm = 8) {

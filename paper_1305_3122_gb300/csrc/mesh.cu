@@ -162,6 +162,7 @@ extern "C" void fe_mesh_destroy(fe_mesh m) {
 
 extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, const int32_t* me,
                                     int ptr_kind, fe_stream stream, fe_mesh* out) {
+    FE_RANGE(__func__);
     if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     if (nq < 0 || nme < 0) return fe_fail(FE_ERR_INVALID_ARG, "nq and nme must be >= 0");
@@ -287,6 +288,7 @@ fe_status fe_mesh_orientation_status(const int word[4]) {
 }
 
 extern "C" fe_status fe_mesh_set_coords(fe_mesh m, const double* q, int ptr_kind, fe_stream stream) {
+    FE_RANGE(__func__);
     if (!m || (m->nq > 0 && !q)) return fe_fail(FE_ERR_INVALID_ARG, "null mesh or q");
     if (ptr_kind == FE_PTR_DEVICE_BORROW) ptr_kind = FE_PTR_DEVICE;
     if (ptr_kind != FE_PTR_HOST && ptr_kind != FE_PTR_DEVICE) return fe_fail(FE_ERR_INVALID_ARG, "bad ptr_kind");
@@ -296,6 +298,7 @@ extern "C" fe_status fe_mesh_set_coords(fe_mesh m, const double* q, int ptr_kind
 }
 
 extern "C" fe_status fe_mesh_check(fe_mesh m, fe_stream stream) {
+    FE_RANGE(__func__);
     if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");
     cudaStream_t s = (cudaStream_t)stream;
     int word = 0;

@@ -493,6 +493,7 @@ struct P2Temps {
 }  // namespace
 
 extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, int flags, fe_stream stream, fe_p2_pattern* out) {
+    FE_RANGE(__func__);
     if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     fe_status st;
@@ -625,6 +626,7 @@ extern "C" fe_status fe_p2_pattern_dofs(fe_p2_pattern p, const int32_t** edof, c
 
 extern "C" fe_status fe_p2_assemble(fe_mesh m, fe_p2_pattern p, int kind, int variant, double* values, int64_t cap,
                                     fe_stream stream) {
+    FE_RANGE(__func__);
     if (!m || !p) return fe_fail(FE_ERR_INVALID_ARG, "null mesh or pattern");
     if (m->topology_id != p->topology_id) return fe_fail(FE_ERR_INVALID_ARG, "the pattern was built for another mesh");
     if (kind != FE_P2_MASS && kind != FE_P2_STIFF) return fe_fail(FE_ERR_INVALID_ARG, "unknown kind");

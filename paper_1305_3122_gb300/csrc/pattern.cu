@@ -715,6 +715,7 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
 }
 
 extern "C" fe_status fe_pattern_build(fe_mesh m, int dofs, int flags, fe_stream stream, fe_pattern* out) {
+    FE_RANGE(__func__);
     if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");

@@ -820,6 +820,7 @@ cudaStream_t side_stream() {
 extern "C" fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const double* q, const int32_t* me,
                                                   const double* w, int32_t* row_ptr, int32_t* col_idx, double* S,
                                                   double* Mw, int64_t cap, int64_t* nnz_out, fe_stream stream) {
+    FE_RANGE(__func__);
     if (!nnz_out || !row_ptr) return fe_fail(FE_ERR_INVALID_ARG, "row_ptr or nnz_out is null");
     *nnz_out = 0;
     if (nq < 0 || nme < 0) return fe_fail(FE_ERR_INVALID_ARG, "nq and nme must be >= 0");

@@ -2,6 +2,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "internal.cuh"
@@ -48,8 +49,31 @@ static cudaError_t pool_for_device(cudaMemPool_t* out) {
     return cudaSuccess;
 }
 
+// Allocation-failure injection (fe_debug_fail_alloc): the count of allocations still to pass
+// before the one that fails; 0: off.
+static std::atomic<int64_t> g_fail_alloc{0};
+
+extern "C" void fe_debug_fail_alloc(int64_t n) { g_fail_alloc.store(n > 0 ? n : 0); }
+
+extern "C" fe_status fe_debug_pool_used(int64_t* bytes) {
+    if (!bytes) return fe_fail(FE_ERR_INVALID_ARG, "bytes is null");
+    cudaMemPool_t pool;
+    uint64_t v = 0;
+    cudaError_t e = pool_for_device(&pool);
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v);
+    if (e != cudaSuccess) return fe_cuda_fail(e, "allocation pool attribute");
+    *bytes = (int64_t)v;
+    return FE_OK;
+}
+
 fe_status fe_alloc(void** p, size_t bytes, const char* what) {
     *p = nullptr;
+    int64_t c = g_fail_alloc.load();
+    while (c > 0 && !g_fail_alloc.compare_exchange_weak(c, c - 1)) {
+    }
+    if (c == 1)
+        return fe_fail(FE_ERR_OOM, std::string("device allocation of ") + std::to_string(bytes) + " bytes for " + what +
+                                       ": injected failure (fe_debug_fail_alloc)");
     cudaMemPool_t pool;
     cudaError_t e = pool_for_device(&pool);
     if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, t_stream);

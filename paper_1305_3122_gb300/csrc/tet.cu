@@ -536,6 +536,7 @@ extern "C" void fe_tet_mesh_destroy(fe_tet_mesh m) {
 
 extern "C" fe_status fe_tet_mesh_create(int32_t nq, int32_t nme, const double* q, const int32_t* me, int ptr_kind,
                                         fe_stream stream, fe_tet_mesh* out) {
+    FE_RANGE(__func__);
     if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     if (nq < 0 || nme < 0) return fe_fail(FE_ERR_INVALID_ARG, "nq and nme must be >= 0");
@@ -643,6 +644,7 @@ fe_status tet_rows(const TetTemps& t, int32_t nq, fe_tet_pattern p, cudaStream_t
 }  // namespace
 
 extern "C" fe_status fe_tet_pattern_build(fe_tet_mesh m, int flags, fe_stream stream, fe_tet_pattern* out) {
+    FE_RANGE(__func__);
     if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");
@@ -744,6 +746,7 @@ extern "C" fe_status fe_tet_pattern_map(fe_tet_pattern p, const int32_t** map, i
 
 extern "C" fe_status fe_tet_assemble(fe_tet_mesh m, fe_tet_pattern p, int kind, const double* w, int variant,
                                      double* values, int64_t cap, fe_stream stream) {
+    FE_RANGE(__func__);
     if (!m || !p) return fe_fail(FE_ERR_INVALID_ARG, "null mesh or pattern");
     if (m->topology_id != p->topology_id) return fe_fail(FE_ERR_INVALID_ARG, "the pattern was built for another mesh");
     if (kind != FE_TET_MASS && kind != FE_TET_WMASS && kind != FE_TET_STIFF) return fe_fail(FE_ERR_INVALID_ARG, "unknown kind");

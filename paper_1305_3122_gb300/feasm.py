@@ -72,6 +72,8 @@ SIGNATURES = {
     "fe_profile_enable": (_INT, [_INT]),
     "fe_profile_reset": (_INT, []),
     "fe_profile_read": (_INT, [_I32, _P, _P, _P, ctypes.POINTER(_I32)]),
+    "fe_debug_fail_alloc": (None, [_I64]),
+    "fe_debug_pool_used": (_INT, [ctypes.POINTER(_I64)]),
     "fe_status_string": (ctypes.c_char_p, [_INT]),
     "fe_last_error": (ctypes.c_char_p, []),
 }
@@ -470,6 +472,19 @@ def adjoint_stiff_wmass(mesh: Mesh, pattern: Pattern, w: torch.Tensor, gS: torch
                                         _dptr(gS, torch.float64, "gS"), _dptr(gM, torch.float64, "gM"), variant,
                                         dq.data_ptr(), dw.data_ptr(), _stream(stream)), "fe_adjoint_stiff_wmass")
     return dq, dw
+
+
+def debug_fail_alloc(n: int):
+    """Make the n-th device allocation of the library from now on fail with FE_ERR_OOM (n <= 0:
+    off); a test hook for the error paths (fe_debug_fail_alloc)."""
+    lib().fe_debug_fail_alloc(int(n))
+
+
+def debug_pool_used() -> int:
+    """Bytes currently allocated from the library's device memory pool (fe_debug_pool_used)."""
+    v = _I64()
+    _check(lib().fe_debug_pool_used(ctypes.byref(v)), "fe_debug_pool_used")
+    return v.value
 
 
 def profile_enable(on: bool = True):
