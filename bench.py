@@ -765,9 +765,12 @@ def e2e(feasm, torch, m, w, args) -> dict:
         out = step()
         t.append(time.perf_counter() - t0)
     el = sum(t) / len(t)
+    ts = sorted(t)
     h2d = q_h.numel() * 8 + me_h.numel() * 4 + w_h.numel() * 8
     d2h = sum(v.numel() * v.element_size() for k, v in out.items() if k != "nnz")
     return {"value": round(m.nme / el / 1e6, 3), "unit": UNIT, "ms_per_step": round(el * 1e3, 3),
+            "median_ms": round(ts[len(ts) // 2] * 1e3, 3), "p90_ms": round(ts[int(0.9 * (len(ts) - 1))] * 1e3, 3),
+            "max_ms": round(ts[-1] * 1e3, 3),
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "api": ("feasm.assemble_host('stiff_wmass', ...) from pinned host arrays to pinned host CSR arrays: one "
                     "fe_assemble_stiff_wmass_host call (uploads, validation, pattern, assembly, downloads overlapped "
