@@ -174,3 +174,13 @@ def test_p2_full_size_sampled_rows():
             for r, (cols, vals) in zip(rows, want):
                 np.testing.assert_array_equal(ci[rp[r]:rp[r + 1]], cols)
                 assert np.abs(got[rp[r]:rp[r + 1]] - vals).max() <= 1e-13 * np.abs(vals).max()
+    # every row, both variants: S 1 = 0 (relative to each row's largest entry) and the entries of
+    # M sum to the square's area, 1 (the P2 functions sum to one; the boundary is not jittered)
+    row_of = torch.repeat_interleave(torch.arange(p2.n_rows, device="cuda"), torch.diff(p2.row_ptr.long()))
+    for v in (feasm.ATOMIC, feasm.GATHER):
+        S = feasm.p2_assemble(mesh, p2, feasm.P2_STIFF, variant=v)
+        rs = torch.zeros(p2.n_rows, dtype=torch.float64, device="cuda").index_add_(0, row_of, S)
+        rmax = torch.zeros(p2.n_rows, dtype=torch.float64, device="cuda").index_reduce_(0, row_of, S.abs(), "amax")
+        assert float((rs.abs() / rmax).max()) <= 1e-13
+        M = feasm.p2_assemble(mesh, p2, feasm.P2_MASS, variant=v)
+        assert abs(float(M.sum()) - 1.0) <= 1e-12

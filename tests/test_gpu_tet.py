@@ -204,3 +204,13 @@ def test_tet_full_size_sampled_rows():
                 np.testing.assert_array_equal(ci[rp[r]:rp[r + 1]], cols)
                 g = got[rp[r]:rp[r + 1]]
                 assert np.abs(g - vals).max() <= 1e-13 * np.abs(vals).max()
+    # every row, both variants: S 1 = 0 (relative to each row's largest entry) and the entries of
+    # M sum to the cube's volume, 1 (its boundary nodes are not jittered)
+    row_of = torch.repeat_interleave(torch.arange(m.nq, device="cuda"), torch.diff(pat.row_ptr.long()))
+    for variant in (feasm.ATOMIC, feasm.GATHER):
+        S = feasm.tet_assemble(mesh, pat, feasm.TET_STIFF, None, variant)
+        rs = torch.zeros(m.nq, dtype=torch.float64, device="cuda").index_add_(0, row_of, S)
+        rmax = torch.zeros(m.nq, dtype=torch.float64, device="cuda").index_reduce_(0, row_of, S.abs(), "amax")
+        assert float((rs.abs() / rmax).max()) <= 1e-13
+        M = feasm.tet_assemble(mesh, pat, feasm.TET_MASS, None, variant)
+        assert abs(float(M.sum()) - 1.0) <= 1e-12
