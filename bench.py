@@ -649,13 +649,16 @@ def tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 128) -
     k_ms = prof["k_tet_atomic"][0] / prof["k_tet_atomic"][1]
     ops = TET_STIFF_FP64_OPS * m.nme
     nbytes = 16 * m.nme + 32 * m.nq + 64 * m.nme + 8 * pat.nnz     # me, vertex records, map, values
+    fp64_g = feasm.measure_fp64_rate() / 1e9                        # measured FP64 issue rate
     return {"workload": f"S, M^w, M of the {cells}^3-cell cube (nq={m.nq}, nme={m.nme} tetrahedra, nnz={pat.nnz})",
             "mesh_ms": round(ms_mesh, 4), "pattern_ms": round(ms_pat, 4), "pattern_gather_ms": round(ms_pat_g, 4),
             **res, "S_atomic_melem_s": round(m.nme / res["S_atomic_ms"] / 1e3, 1),
             "roofline": {"kernel": "k_tet_atomic<S>", "bound": "fp64", "algorithmic_ops": ops,
-                         "achieved": round(ops / k_ms / 1e6, 1), "peak": round(FP64_PEAK_G, 1),
-                         "unit": "G FP64 instr/s", "frac": round(ops / k_ms / 1e6 / FP64_PEAK_G, 4),
-                         "peak_source": "2 FP64 instructions per SM per clock x 152 SMs x 2.07 GHz",
+                         "achieved": round(ops / k_ms / 1e6, 1), "peak": round(fp64_g, 1),
+                         "unit": "G FP64 instr/s", "frac": round(ops / k_ms / 1e6 / fp64_g, 4),
+                         "peak_source": "measured: independent FP64 fused multiply-add chains on every SM (fe_measure_fp64_rate)",
+                         "nominal_peak": round(FP64_PEAK_G, 1),
+                         "nominal_peak_source": "2 FP64 instructions per SM per clock x 152 SMs x 2.07 GHz",
                          "hbm_frac": round(nbytes / k_ms / 1e6 / hbm, 4), "hbm_peak_source": f"{peak_kind} HBM copy bandwidth"}}
 
 

@@ -390,6 +390,12 @@ fe_status fe_profile_reset(void);
 fe_status fe_profile_read(int32_t max_entries, char* names, double* total_ms, int64_t* launches,
                           int32_t* count);
 
+/* FP64 issue rate of this GPU, measured (measurement support; not in the paper): independent
+ * fused multiply-add chains on every SM, 8 blocks of 256 threads per SM, timed with CUDA events
+ * on stream: the fastest of five launches after two warm-up ones. *instr_per_s gets the FP64
+ * instructions (one per thread and FMA) per second. Synchronises the stream; takes about 0.1 s. */
+fe_status fe_measure_fp64_rate(double* instr_per_s, fe_stream stream);
+
 /* ----------------------------------------------------------------------- test hooks ---- */
 
 /* Allocation-failure injection, for the tests of the error paths (not in the paper): after

@@ -98,6 +98,63 @@ int fe_sm_count() {
     return n > 0 ? n : 1;
 }
 
+// ------------------------------------------------------------------ FP64 rate probe
+
+// Independent fused multiply-add chains: each thread keeps FP64_CHAINS accumulators, so the FP64
+// pipe always has independent work and the rate measured is its issue rate. b and c are kernel
+// arguments (nothing folds at compile time); the store happens only for a sum the inputs cannot
+// produce, so the chains are kept without a store per thread.
+constexpr int FP64_CHAINS = 8;
+
+__global__ void __launch_bounds__(256) k_fp64_rate(double* __restrict__ sink, int iters, double b, double c) {
+    double a[FP64_CHAINS];
+#pragma unroll
+    for (int j = 0; j < FP64_CHAINS; j++) a[j] = 1e-3 * (double)(threadIdx.x + j);
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < FP64_CHAINS; j++) a[j] = fma(a[j], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < FP64_CHAINS; j++) s += a[j];
+    if (s == -1.0) sink[0] = s;
+}
+
+extern "C" fe_status fe_measure_fp64_rate(double* instr_per_s, fe_stream stream) {
+    FE_RANGE(__func__);
+    if (!instr_per_s) return fe_fail(FE_ERR_INVALID_ARG, "instr_per_s is null");
+    *instr_per_s = 0.0;
+    cudaStream_t s = (cudaStream_t)stream;
+    FeStreamScope scope(s);
+    double* sink = nullptr;
+    fe_status st = fe_alloc_n(&sink, 1, "probe sink");
+    if (st) return st;
+    const int blocks = fe_sm_count() * 8, threads = 256, iters = 2048;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // two warm-up launches (the clocks ramp up over the first ones), then the fastest of five
+    float ms = 0.f;
+    for (int r = 0; r < 7 && e == cudaSuccess; r++) {
+        if (r >= 2) cudaEventRecord(e0, s);
+        k_fp64_rate<<<blocks, threads, 0, s>>>(sink, iters, 0.999999, 1e-7);
+        if (r < 2) continue;
+        cudaEventRecord(e1, s);
+        e = cudaGetLastError();
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess && (ms == 0.f || t < ms)) ms = t;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    fe_free(sink);
+    if (e != cudaSuccess) return fe_cuda_fail(e, "FP64 rate probe");
+    const double n = (double)blocks * threads * FP64_CHAINS * iters;
+    *instr_per_s = ms > 0.f ? n / (ms * 1e-3) : 0.0;
+    return FE_OK;
+}
+
 extern "C" const char* fe_status_string(fe_status st) {
     switch (st) {
         case FE_OK: return "FE_OK";

@@ -72,6 +72,7 @@ SIGNATURES = {
     "fe_profile_enable": (_INT, [_INT]),
     "fe_profile_reset": (_INT, []),
     "fe_profile_read": (_INT, [_I32, _P, _P, _P, ctypes.POINTER(_I32)]),
+    "fe_measure_fp64_rate": (_INT, [ctypes.POINTER(_D), _P]),
     "fe_debug_fail_alloc": (None, [_I64]),
     "fe_debug_pool_used": (_INT, [ctypes.POINTER(_I64)]),
     "fe_status_string": (ctypes.c_char_p, [_INT]),
@@ -472,6 +473,13 @@ def adjoint_stiff_wmass(mesh: Mesh, pattern: Pattern, w: torch.Tensor, gS: torch
                                         _dptr(gS, torch.float64, "gS"), _dptr(gM, torch.float64, "gM"), variant,
                                         dq.data_ptr(), dw.data_ptr(), _stream(stream)), "fe_adjoint_stiff_wmass")
     return dq, dw
+
+
+def measure_fp64_rate(stream=None) -> float:
+    """Measured FP64 instructions per second of this GPU (fe_measure_fp64_rate)."""
+    v = _D()
+    _check(lib().fe_measure_fp64_rate(ctypes.byref(v), _stream(stream)), "fe_measure_fp64_rate")
+    return v.value
 
 
 def debug_fail_alloc(n: int):
