@@ -800,6 +800,7 @@ def main() -> int:
     ap.add_argument("--only", choices=["elasticity", "adjoint", "drop_zeros", "tetrahedra", "p2"],
                     help="run this one leg alone and print its object (for profiling; no headline step)")
     ap.add_argument("--tet-cells", type=int, default=128, help="cells per side of the tetrahedra leg's cube")
+    ap.add_argument("--p2-cells", type=int, default=1024, help="cells per side of the P2 leg's square")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)    # at least 3 untimed warm-up steps
     if args.impl == "reference":
@@ -822,7 +823,7 @@ def run_leg(args) -> int:
     elif args.only == "tetrahedra":
         out = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind, cells=args.tet_cells)
     elif args.only == "p2":
-        out = p2(feasm, meshgen, torch, flush, hbm, peak_kind)
+        out = p2(feasm, meshgen, torch, flush, hbm, peak_kind, cells=args.p2_cells)
     else:
         m = meshgen.square_mesh(args.cells, 13053122 + 2)
         mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))

@@ -39,7 +39,7 @@ constexpr int BIG_TS = 4096, BIG_EMAX = FE_P2_MAX_VALENCE;
 static_assert(6 * FAST_EMAX < FAST_TS && 6 * BIG_EMAX < BIG_TS, "tables hold every id");
 constexpr int RS_BLOCK = 128;                // row sums: one row per thread
 constexpr int RS_VERTEX = 32;                // row sums: accumulators of a vertex row (1 + 3 d columns at valence d)
-constexpr int RS_EDGE = 16;                  // row sums: accumulators of an edge row (at most 12 columns for two triangles)
+constexpr int RS_EDGE_MAX = 12;              // row sums: columns of an edge row in at most two triangles
 constexpr int RS_LONG_MAX = 6 * BIG_EMAX;    // columns of the longest row
 
 // Where the row passes put the deterministic variant's lists (rrec null: no lists).
@@ -167,7 +167,9 @@ __device__ void p2_row(int32_t r, int32_t beg, int32_t d, const int32_t* __restr
     }
     if (lane == 0) {
         cnt[r] = u;
-        if (ls.rrec && u > (r < ls.nq ? RS_VERTEX : RS_EDGE)) ls.long_rows[atomicAdd(ls.n_long, 1)] = r;
+        // long: a vertex row longer than its thread's accumulators, or an edge row here (an edge in more
+        // than two triangles: the edge-row sums handle at most two)
+        if (ls.rrec && (r >= ls.nq || u > RS_VERTEX)) ls.long_rows[atomicAdd(ls.n_long, 1)] = r;
     }
     __syncwarp();
 }
@@ -430,13 +432,76 @@ __global__ void __launch_bounds__(RS_BLOCK) k_p2_rowsum(const int32_t* __restric
             for (int j = 0; j < 3; j++) v[j] = e[j];
             const unsigned sl[3] = {(unsigned)rec.y, (unsigned)rec.z, (unsigned)rec.w};
             if (t + 1 < d) rec = rrec[b0 + t + 1];
+            // an incidence's six columns are distinct: all six accumulators are read before any is
+            // written back, so the six updates overlap instead of waiting on one another
+            double* pc[6];
+            double y[6];
 #pragma unroll
             for (int j = 0; j < 3; j++) {
-                a[(sl[j] & 0xFFFFu) * RS_BLOCK] += v[j].x;
-                a[(sl[j] >> 16) * RS_BLOCK] += v[j].y;
+                pc[2 * j] = a + (sl[j] & 0xFFFFu) * RS_BLOCK;
+                pc[2 * j + 1] = a + (sl[j] >> 16) * RS_BLOCK;
+            }
+#pragma unroll
+            for (int j = 0; j < 6; j++) y[j] = *pc[j];
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                *pc[2 * j] = y[2 * j] + v[j].x;
+                *pc[2 * j + 1] = y[2 * j + 1] + v[j].y;
             }
         }
         for (int c = 0; c < u; c++) val[rb + c] = a[c * RS_BLOCK];
+    }
+}
+
+// Row sums of the edge rows in at most two triangles, one row per thread, in registers: column c
+// takes the first incidence's entry at c, then adds the second's (ascending element order). The
+// first value is taken as it is, which is bit for bit what adding it to -0.0 gives, so the sums
+// equal those of k_p2_rowsum. Edge rows in more triangles are listed for k_p2_rowsum_long.
+__global__ void __launch_bounds__(RS_BLOCK) k_p2_rowsum_edge(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
+                                                             int32_t r0, int32_t r1, const int4* __restrict__ rrec,
+                                                             const double* __restrict__ kg, double* __restrict__ val) {
+    for (int64_t rr = r0 + blockIdx.x * (int64_t)RS_BLOCK + threadIdx.x; rr < r1; rr += (int64_t)gridDim.x * RS_BLOCK) {
+        const int32_t b0 = vptr[rr], d = vptr[rr + 1] - b0;
+        if (d > 2) continue;
+        const int32_t rb = row_ptr[rr], u = row_ptr[rr + 1] - rb;
+        double v[2][6];
+        unsigned sl[2][6];
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            const int4 rec = t < d ? rrec[b0 + t] : make_int4(0, -1, -1, -1);   // -1: no column
+            if (t < d) {
+                const double2* e = reinterpret_cast<const double2*>(kg + 6 * (int64_t)rec.x);
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    const double2 x = e[j];
+                    v[t][2 * j] = x.x;
+                    v[t][2 * j + 1] = x.y;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 6; j++) v[t][j] = 0.0;
+            }
+            const unsigned w3[3] = {(unsigned)rec.y, (unsigned)rec.z, (unsigned)rec.w};
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                sl[t][2 * j] = w3[j] & 0xFFFFu;
+                sl[t][2 * j + 1] = w3[j] >> 16;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < RS_EDGE_MAX; c++) {
+            if (c >= u) break;
+            double x0 = 0.0, x1 = 0.0;
+            bool f0 = false, f1 = false;
+#pragma unroll
+            for (int j = 0; j < 6; j++) {
+                if (sl[0][j] == (unsigned)c) { x0 = v[0][j]; f0 = true; }
+                if (sl[1][j] == (unsigned)c) { x1 = v[1][j]; f1 = true; }
+            }
+            double a = f0 ? x0 : -0.0;
+            if (f1) a = a + x1;
+            val[rb + c] = a;
+        }
     }
 }
 
@@ -657,7 +722,7 @@ extern "C" fe_status fe_p2_assemble(fe_mesh m, fe_p2_pattern p, int kind, int va
             FE_LAUNCHED("k_p2_rowsum (vertex rows)");
         }
         if (ndof > nq) {
-            { FE_PROF("k_p2_rowsum<16> (edge rows)", s); k_p2_rowsum<RS_EDGE><<<fe_grid((int64_t)ndof - nq, RS_BLOCK, 16), RS_BLOCK, 0, s>>>(
+            { FE_PROF("k_p2_rowsum_edge", s); k_p2_rowsum_edge<<<fe_grid((int64_t)ndof - nq, RS_BLOCK, 16), RS_BLOCK, 0, s>>>(
                   p->vptr, p->row_ptr, nq, ndof, p->rrec, p->kg, values); }
             FE_LAUNCHED("k_p2_rowsum (edge rows)");
         }

@@ -476,13 +476,20 @@ __global__ void __launch_bounds__(RS_BLOCK) k_tet_rowsum(const int32_t* __restri
                 key[j] = tn < d ? inc[b0 + tn] : 0;
                 sl[j] = tn < d ? islot[b0 + tn] : make_uint2(0u, 0u);
             }
+            // an incidence's four columns are distinct: its four accumulators are read before any
+            // is written back, so the four updates overlap instead of waiting on one another
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 if (t0 + j < d) {
-                    a[(cs[j].x & 0xFFFFu) * RS_BLOCK] += v[j][0].x;
-                    a[(cs[j].x >> 16) * RS_BLOCK] += v[j][0].y;
-                    a[(cs[j].y & 0xFFFFu) * RS_BLOCK] += v[j][1].x;
-                    a[(cs[j].y >> 16) * RS_BLOCK] += v[j][1].y;
+                    double* p0 = a + (cs[j].x & 0xFFFFu) * RS_BLOCK;
+                    double* p1 = a + (cs[j].x >> 16) * RS_BLOCK;
+                    double* p2 = a + (cs[j].y & 0xFFFFu) * RS_BLOCK;
+                    double* p3 = a + (cs[j].y >> 16) * RS_BLOCK;
+                    const double y0 = *p0, y1 = *p1, y2 = *p2, y3 = *p3;
+                    *p0 = y0 + v[j][0].x;
+                    *p1 = y1 + v[j][0].y;
+                    *p2 = y2 + v[j][1].x;
+                    *p3 = y3 + v[j][1].y;
                 }
             }
         }
