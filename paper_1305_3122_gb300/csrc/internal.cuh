@@ -104,8 +104,8 @@ struct fe_p2_pattern_s {
     int4* rrec = nullptr;                 // [6 nme] {key 6k + a (row r = edof[k][a]), six 16-bit column positions},
                                           // ascending keys within a row
     int32_t* long_rows = nullptr;         // [ndof + 1] rows with more columns than one thread sums
-    int32_t* n_long = nullptr;            // [1] their number (device)
-    int32_t n_long_host = 0;
+    int32_t* n_long = nullptr;            // [2] their number, and 1 if a vertex row is longer than 24 (device)
+    int32_t n_long_host[2] = {0, 0};
     double* kg = nullptr;                 // [36 nme] staged element values
     cudaStream_t last_stream = nullptr;
 };

@@ -39,6 +39,8 @@ constexpr int BIG_TS = 4096, BIG_EMAX = FE_P2_MAX_VALENCE;
 static_assert(6 * FAST_EMAX < FAST_TS && 6 * BIG_EMAX < BIG_TS, "tables hold every id");
 constexpr int RS_BLOCK = 128;                // row sums: one row per thread
 constexpr int RS_VERTEX = 32;                // row sums: accumulators of a vertex row (1 + 3 d columns at valence d)
+constexpr int RS_VERTEX_SHORT = 24;          // row sums: fewer accumulators when no vertex row is longer (8
+                                             // resident blocks per SM instead of 6)
 constexpr int RS_EDGE_MAX = 12;              // row sums: columns of an edge row in at most two triangles
 constexpr int RS_LONG_MAX = 6 * BIG_EMAX;    // columns of the longest row
 
@@ -47,7 +49,7 @@ struct P2Lists {
     int4* rrec;          // [6 nme]: each row's incidences in ascending element order, row r from vptr[r]:
                          // {key 6k + a, then the in-row positions of columns jl = 0..5, 16 bits each}
     int32_t* long_rows;  // rows with more columns than their thread's accumulators
-    int32_t* n_long;
+    int32_t* n_long;     // their number, then 1 if a vertex row has more than RS_VERTEX_SHORT columns
     int32_t nq;
 };
 
@@ -170,6 +172,7 @@ __device__ void p2_row(int32_t r, int32_t beg, int32_t d, const int32_t* __restr
         // long: a vertex row longer than its thread's accumulators, or an edge row here (an edge in more
         // than two triangles: the edge-row sums handle at most two)
         if (ls.rrec && (r >= ls.nq || u > RS_VERTEX)) ls.long_rows[atomicAdd(ls.n_long, 1)] = r;
+        if (ls.rrec && r < ls.nq && u > RS_VERTEX_SHORT) ls.n_long[1] = 1;
     }
     __syncwarp();
 }
@@ -620,8 +623,8 @@ extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, int flags, fe
     if (gather) {
         if ((st = fe_alloc_n(&p->rrec, 6 * (size_t)nme, "row incidence records"))) return fail(st);
         if ((st = fe_alloc_n(&p->long_rows, (size_t)ndof + 1, "long rows"))) return fail(st);
-        if ((st = fe_alloc_n(&p->n_long, 1, "long-row count"))) return fail(st);
-        if (cudaMemsetAsync(p->n_long, 0, sizeof(int32_t), s) != cudaSuccess) return fail(fe_fail(FE_ERR_CUDA, "memset"));
+        if ((st = fe_alloc_n(&p->n_long, 2, "long-row count and flag"))) return fail(st);
+        if (cudaMemsetAsync(p->n_long, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return fail(fe_fail(FE_ERR_CUDA, "memset"));
     }
     const P2Lists ls{p->rrec, p->long_rows, p->n_long, nq};
     if (ndof > 0) {
@@ -646,7 +649,7 @@ extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, int flags, fe
     if ((st = fe_exclusive_scan(t.cnt, p->row_ptr, ndof, s, &nnz))) return fail(st);   // synchronises
     int too_big = 0;
     if (cudaMemcpyAsync(&too_big, t.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        (gather && cudaMemcpyAsync(&p->n_long_host, p->n_long, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+        (gather && cudaMemcpyAsync(p->n_long_host, p->n_long, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return fail(fe_fail(FE_ERR_CUDA, "flag read-back"));
     if (too_big)
@@ -717,8 +720,13 @@ extern "C" fe_status fe_p2_assemble(fe_mesh m, fe_p2_pattern p, int kind, int va
         FE_LAUNCHED("k_p2_stage");
         const int32_t nq = p->nq, ndof = p->ndof;
         if (nq > 0) {
-            { FE_PROF("k_p2_rowsum<32> (vertex rows)", s); k_p2_rowsum<RS_VERTEX><<<fe_grid(nq, RS_BLOCK, 8), RS_BLOCK, 0, s>>>(
-                  p->vptr, p->row_ptr, 0, nq, p->rrec, p->kg, values); }
+            FE_PROF("k_p2_rowsum (vertex rows)", s);
+            if (!p->n_long_host[1])
+                k_p2_rowsum<RS_VERTEX_SHORT><<<fe_grid(nq, RS_BLOCK, 8), RS_BLOCK, 0, s>>>(p->vptr, p->row_ptr, 0, nq, p->rrec,
+                                                                                         p->kg, values);
+            else
+                k_p2_rowsum<RS_VERTEX><<<fe_grid(nq, RS_BLOCK, 8), RS_BLOCK, 0, s>>>(p->vptr, p->row_ptr, 0, nq, p->rrec, p->kg,
+                                                                                   values);
             FE_LAUNCHED("k_p2_rowsum (vertex rows)");
         }
         if (ndof > nq) {
@@ -726,7 +734,7 @@ extern "C" fe_status fe_p2_assemble(fe_mesh m, fe_p2_pattern p, int kind, int va
                   p->vptr, p->row_ptr, nq, ndof, p->rrec, p->kg, values); }
             FE_LAUNCHED("k_p2_rowsum (edge rows)");
         }
-        if (p->n_long_host > 0) {
+        if (p->n_long_host[0] > 0) {
             const size_t sm = (size_t)RS_LONG_MAX * sizeof(double);
             { FE_PROF("k_p2_rowsum_long", s); k_p2_rowsum_long<<<fe_sm_count() * 8, 32, sm, s>>>(
                   p->long_rows, p->n_long, p->vptr, p->row_ptr, p->rrec, p->kg, values); }
