@@ -20,6 +20,7 @@ weak scaling); value = all ranks' triangles / the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import math
@@ -280,10 +281,15 @@ def run_reference(args) -> int:
 
     for _ in range(args.warmup):
         step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    el = time.perf_counter() - t0
+    gc.collect()
+    gc.disable()                         # as in the GPU arm's timed regions
+    try:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        el = time.perf_counter() - t0
+    finally:
+        gc.enable()
     value = args.steps * m.nme / el / 1e6
     sample = (f"each step: S + M^[w] by the single-threaded FP64 C oracle (triplets + sparse) on the "
               f"{n_cells}x{n_cells}-cell mesh of the same recipe (nme={m.nme}), a bounded sample of the "
@@ -379,16 +385,23 @@ def run_ours(args) -> int:
         step()
         flush.fill_(1)
     def timed_steps():
+        # the collector is off while timing (as timeit does): a full collection of this process's
+        # objects takes tens of milliseconds and would stall the host between launches
         times = []
-        for _ in range(args.steps):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
+        gc.collect()
+        gc.disable()
+        try:
+            for _ in range(args.steps):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        finally:
+            gc.enable()
         torch.cuda.synchronize()
         return times
 
@@ -763,10 +776,15 @@ def e2e(feasm, torch, m, w, args) -> dict:
     for _ in range(max(args.warmup - 1, 1)):
         step()
     t = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        out = step()
-        t.append(time.perf_counter() - t0)
+    gc.collect()
+    gc.disable()                         # no collector pauses inside the timed steps (as timeit)
+    try:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            out = step()
+            t.append(time.perf_counter() - t0)
+    finally:
+        gc.enable()
     el = sum(t) / len(t)
     ts = sorted(t)
     h2d = q_h.numel() * 8 + me_h.numel() * 4 + w_h.numel() * 8
