@@ -115,6 +115,7 @@ struct P2Smem {
     int32_t uid[TS];
     int32_t uslot[TS];
     int32_t key[EMAX];
+    int16_t xs[6 * EMAX];   // the slot of each incidence's six ids
     int32_t ucount;
 };
 
@@ -133,6 +134,7 @@ __device__ void p2_row(int32_t r, int32_t beg, int32_t d, const int32_t* __restr
         const int32_t id = edof[6 * (int64_t)(sm.key[x / 6] / 6) + x % 6];
         bool fresh;
         const int s = tab_insert<TS>(sm.tab, id, &fresh);
+        sm.xs[x] = (int16_t)s;
         if (fresh) {
             const int p = atomicAdd(&sm.ucount, 1);
             sm.uid[p] = id;
@@ -152,12 +154,11 @@ __device__ void p2_row(int32_t r, int32_t beg, int32_t d, const int32_t* __restr
     __syncwarp();
     for (int t = lane; t < d; t += 32) {
         const int32_t kk = sm.key[t] / 6, a = sm.key[t] - 6 * (sm.key[t] / 6);
-        const int32_t* e = edof + 6 * (int64_t)kk;
         int32_t* mo = map + 36 * (int64_t)kk + 6 * a;
         int32_t o[6];
 #pragma unroll
         for (int jl = 0; jl < 6; jl++) {
-            o[jl] = sm.rnk[tab_find<TS>(sm.tab, e[jl])];
+            o[jl] = sm.rnk[sm.xs[6 * t + jl]];          // the slot its insertion got
             mo[jl] = o[jl];
         }
         if (ls.rrec) {                                       // the incidence's place in element order

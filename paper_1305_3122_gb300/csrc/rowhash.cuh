@@ -15,7 +15,8 @@ struct RowTableShift {
     static constexpr int value = 32 - (TS == 128 ? 7 : 12);
 };
 
-// Slot of id (inserted if absent); *fresh tells whether this call inserted it.
+// Slot of id (inserted if absent); *fresh tells whether this call inserted it. Callers keep the
+// slot of each insertion, so no id is looked up again.
 template <int TS>
 __device__ __forceinline__ int tab_insert(int32_t* tab, int32_t id, bool* fresh) {
     int s = (int)(fe_row_hash(id) >> RowTableShift<TS>::value);
@@ -27,14 +28,4 @@ __device__ __forceinline__ int tab_insert(int32_t* tab, int32_t id, bool* fresh)
     }
     *fresh = false;
     return 0;    // not reached: the table is never full
-}
-
-template <int TS>
-__device__ __forceinline__ int tab_find(const int32_t* tab, int32_t id) {
-    int s = (int)(fe_row_hash(id) >> RowTableShift<TS>::value);
-    for (int step = 0; step < TS; step++) {
-        if (tab[s] == id) return s;
-        s = (s + 1) & (TS - 1);
-    }
-    return 0;    // not reached: every id looked up was inserted
 }

@@ -12,7 +12,7 @@
 // Pattern (the structural half of sparse()): a counting sort by vertex drops, for each
 // tetrahedron k and each of its vertices a, the record (its three other vertices, 4k + a) into the
 // bucket of vertex me[a][k]. One warp per row then inserts the row's neighbour ids into a
-// shared-memory hash table (repeats merge; each slot counts its multiplicity), ranks the distinct
+// shared-memory hash table (repeats merge; each insertion keeps the slot it got), ranks the distinct
 // ids (their rank is the column's position in the sorted row), and writes, for every incidence,
 // the in-row positions of its four columns: the element-to-nnz map, row-major per element
 // (map[16k + 4 il + jl]), relative to the row start until the offsets are known. For the
@@ -127,11 +127,11 @@ __global__ void k_tet_fill(const int32_t* __restrict__ me, int32_t nme, int32_t*
 template <int TS, int EMAX>
 struct RowSmem {
     int32_t tab[TS];     // ids (-1: empty)
-    int32_t mult[TS];    // multiplicity of each id (incidences that touch the column)
     int32_t rnk[TS];     // rank (column position) of each slot's id
     int32_t uid[TS];     // the distinct ids, in insertion order
     int32_t uslot[TS];   // their slots
     int4 e[EMAX];        // the row's bucket records
+    int16_t xs[4 * EMAX];  // the slot of each incidence's four ids (the row's vertex, then x, y, z)
     int32_t ucount;
 };
 
@@ -154,7 +154,6 @@ __device__ void tet_row(int32_t i, int32_t beg, int32_t d, const int4* __restric
     const int lane = threadIdx.x & 31;
     for (int s = lane; s < TS; s += 32) {
         sm.tab[s] = -1;
-        sm.mult[s] = 0;
     }
     if (lane == 0) sm.ucount = 0;
     for (int t = lane; t < d; t += 32) sm.e[t] = adj[beg + t];
@@ -166,7 +165,7 @@ __device__ void tet_row(int32_t i, int32_t beg, int32_t d, const int4* __restric
         const int32_t id = q == 0 ? i : q == 1 ? r.x : q == 2 ? r.y : r.z;
         bool fresh;
         const int s = tab_insert<TS>(sm.tab, id, &fresh);
-        atomicAdd(&sm.mult[s], 1);
+        sm.xs[x] = (int16_t)s;
         if (fresh) {
             const int p = atomicAdd(&sm.ucount, 1);
             sm.uid[p] = id;
@@ -189,10 +188,10 @@ __device__ void tet_row(int32_t i, int32_t beg, int32_t d, const int4* __restric
         const int4 r = sm.e[t];
         const int a = r.w & 3;
         const int32_t k = r.w >> 2;
-        const int ri = sm.rnk[tab_find<TS>(sm.tab, i)];
-        const int rx = sm.rnk[tab_find<TS>(sm.tab, r.x)];
-        const int ry = sm.rnk[tab_find<TS>(sm.tab, r.y)];
-        const int rz = sm.rnk[tab_find<TS>(sm.tab, r.z)];
+        const int ri = sm.rnk[sm.xs[4 * t]];
+        const int rx = sm.rnk[sm.xs[4 * t + 1]];
+        const int ry = sm.rnk[sm.xs[4 * t + 2]];
+        const int rz = sm.rnk[sm.xs[4 * t + 3]];
         int o[4];
 #pragma unroll
         for (int jl = 0; jl < 4; jl++) {
