@@ -6,13 +6,20 @@ is one pass of the whole path over resident device inputs, as one sparse() call 
 would do it: mesh validation (fe_mesh_create), the structural pattern (fe_pattern_build) and
 the values of S and M^[w] (fe_assemble_stiff_wmass). The value is triangles per second over
 the timed steps. Also reported:
-  - assemble_only: the values with the pattern built once beforehand (repeated assembly);
+  - assemble_only: the values with the pattern built once beforehand (repeated assembly), L2
+    flushed between calls, and warm (back to back, the time-stepping use);
   - batched: 256 uneven meshes (N log-uniform in [16, 512]) in one graph-replayed persistent
     launch vs 256 plain launches;
-  - e2e: the same step from pinned host arrays to host CSR arrays through the public API;
+  - e2e: the same step from pinned host arrays to host CSR arrays through the public API (mean,
+    median, p90 and max of the steps);
   - roofline of the dominant kernel, timed live with the library's own CUDA events;
-  - cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload.
+  - the other legs: plane elasticity, the adjoint, zero dropping, tetrahedra (with an FP64
+    roofline against the measured FP64 rate) and P2 triangles, each with both scatter variants
+    where it has them;
+  - cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload, single-threaded,
+    on all host cores (one process per core), and beside every other leg.
 Between timed steps L2 is flushed by writing a 512 MB buffer (outside the timed intervals).
+Python's collector is off inside the timed regions.
 
 Multi-GPU (torchrun): every rank assembles its own replica of the workload (no collective;
 weak scaling); value = all ranks' triangles / the slowest rank's time.
