@@ -197,8 +197,9 @@ fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const double* q,
                                        double* Mw, int64_t cap, int64_t* nnz, fe_stream stream);
 
 /* S and M^w as fe_assemble_stiff_wmass with FE_VARIANT_GATHER, for callers that must not have
- * device memory allocated during the call (work being captured into a CUDA graph, frameworks
- * that own all device memory through their own pool, loops with hard latency budgets). The
+ * device memory allocated during the call (frameworks that own all device memory through their
+ * own pool and forbid hidden allocations, plug-ins loaded into such hosts, loops with hard
+ * latency budgets where an allocation could stall). The
  * element values are staged in a fixed device array built into the library (18 MiB, resident on
  * every GPU that loads the library until the process exits) instead of the pattern's buffer;
  * the call performs no allocation of any kind. The paper has no counterpart.

@@ -398,11 +398,12 @@ extern "C" fe_status fe_assemble_elas(fe_mesh m, fe_pattern p, double lam, doubl
 //
 // fe_assemble_stiff_wmass_noalloc runs the staged-gather assembly of S and M^w with its staging
 // buffer in a fixed, file-scope device array instead of memory from an allocator. It serves
-// callers that must not allocate device memory during the call: code that is being recorded
-// into a CUDA graph (allocations are not allowed there), a host framework that owns all device
-// memory through its own pool and forbids hidden allocations, or a loop with a hard latency
-// budget where an allocation could stall. The array is FE_NOALLOC_MAX_TRIANGLES * 18 doubles
-// (18 MiB) and stays resident on every GPU that loads the library until the process exits.
+// callers that must not allocate device memory during the call: a host framework that owns all
+// device memory through its own pool and forbids hidden allocations (a second allocator would
+// fragment or overcommit its budget), a solver plug-in loaded into such a host, or a loop with
+// a hard latency budget where an allocation could stall. The array is
+// FE_NOALLOC_MAX_TRIANGLES * 18 doubles (18 MiB) and stays resident on every GPU that loads the
+// library until the process exits.
 
 #include <mutex>
 
@@ -447,12 +448,14 @@ extern "C" fe_status fe_assemble_stiff_wmass_noalloc(fe_mesh m, fe_pattern p, co
     const int32_t nme = m->nme;
     if (nme == 0) return FE_OK;   // then nnz == 0 as well
     cudaStream_t s = (cudaStream_t)stream;
+    // the handles' device memory is freed in order on the last stream that used them
+    m->last_stream = p->last_stream = s;
     // every staged entry is written before it is read, so nothing needs zeroing between calls
     double* kg0 = scratch;
     double* kg1 = scratch + 9 * (size_t)nme;
-    k_scalar_stage<K_STIFF_WMASS><<<fe_grid(nme, STAGE_BLOCK), STAGE_BLOCK, 0, s>>>(m->q, m->me, nme, w, kg0, kg1, m->err);
+    { FE_PROF("k_scalar_stage", s); k_scalar_stage<K_STIFF_WMASS><<<fe_grid(nme, STAGE_BLOCK), STAGE_BLOCK, 0, s>>>(m->q, m->me, nme, w, kg0, kg1, m->err); }
     FE_LAUNCHED("k_scalar_stage (no-alloc)");
-    k_seg_gather<true><<<fe_grid(p->nnz, 256), 256, 0, s>>>(p->seg_ptr, p->perm, p->nnz, kg0, kg1, S, Mw);
+    { FE_PROF("k_seg_gather", s); k_seg_gather<true><<<fe_grid(p->nnz, 256), 256, 0, s>>>(p->seg_ptr, p->perm, p->nnz, kg0, kg1, S, Mw); }
     FE_LAUNCHED("k_seg_gather (no-alloc)");
     return FE_OK;
 }
