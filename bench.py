@@ -12,6 +12,10 @@ the timed steps. Also reported:
     launch vs 256 plain launches;
   - e2e: the same step from pinned host arrays to host CSR arrays through the public API (mean,
     median, p90 and max of the steps);
+  - arith: the arithmetic of the element stage (the default row-owner variant computes in
+    double-float on the FP32 pipes), and fp64_variants: the same step by the two variants whose
+    element arithmetic is plain FP64 (staged gather, FP64 atomics);
+  - per-kernel shares of the step, each with its algorithmic bytes and HBM fraction;
   - roofline of the dominant kernel, timed live with the library's own CUDA events;
   - the other legs: plane elasticity, the adjoint, zero dropping, tetrahedra (with an FP64
     roofline against the measured FP64 rate) and P2 triangles, each with both scatter variants
@@ -71,12 +75,11 @@ def algorithmic_bytes(name: str, nq: int, nme: int, nnz: int) -> int | None:
         "k_seg_gather": 4 * (nnz + 1) + 36 * nme + 2 * 72 * nme + 16 * nnz,
         "k_fan_scalar": 12 * nme + 16 * nq + 8 * nq + 16 * nnz,
         "k_pack_vrec": 16 * nq + 8 * nq + 32 * nq,
-        "k_validate": 12 * nme + 16 * nq,
+        "k_validate": 12 * nme + 16 * nq + 4 * nq,             # me, q; valence counts written
         "k_pack_coords": 32 * nq,
-        "k_count_deg": 12 * nme + 4 * nq,
-        "k_fill_adj": 12 * nme + 8 * nq + 24 * nme,
-        "k_row_count": 8 * nq + 24 * nme,
-        "k_row_fill": 12 * nq + 24 * nme + 4 * nnz,
+        "k_fill_adj": 12 * nme + 8 * nq + 24 * nme,             # me, cursors; bucket records
+        "k_row_analyse": 8 * nq + 24 * nme + 24 * nme + 8 * nq,  # offsets, buckets; fan records, headers
+        "k_col_fill": 12 * nq + 24 * nme + 4 * nnz,             # offsets, fan records; col_idx
         "k_build_map": 12 * nme + 4 * nq + 4 * nnz + 36 * nme,
         "k_tile_sums": 4 * nq,
         "k_tile_scan": 8 * nq,
@@ -303,12 +306,21 @@ def run_reference(args) -> int:
               f"2048x2048 workload")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "arith": "fp64",
+            "data": "synthetic",
+            "config": _config({"sample_of": _config()["workload"],
+                               "step": "S + M^[w] by the CPU oracle (triplets, stable sort, ordered sums) on the "
+                                       "sample mesh; its sort builds the structure, as sparse() does"},
+                              cells=n_cells, nq=m.nq, nme=m.nme, nnz=_nnz_grid(n_cells)),
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _nnz_grid(n: int) -> int:
+    """Stored entries per scalar matrix of the n x n-cell grid: one per vertex, two per edge."""
+    return (n + 1) ** 2 + 2 * (3 * n * n + 2 * n)
 
 
 def _config(extra: dict | None = None, cells: int = N_CELLS, nq: int = 4198401, nme: int = 8388608,
@@ -453,25 +465,34 @@ def run_ours(args) -> int:
 
     # assembly with a prebuilt pattern
     asm = assemble_only(feasm, torch, mesh0, pat0, w_d, variant, S, M, flush, stream, args, m, nnz, hbm, peak_kind)
+    kern = {}
+    tot = sum(x[0] for x in prof.values())
+    for k, v in sorted(prof.items()):
+        kern[k] = {"ms_per_launch": round(v[0] / v[1], 5), "launches": int(v[1]), "share": round(v[0] / tot, 4)}
+        kb = algorithmic_bytes(k, m.nq, m.nme, nnz)
+        if kb:
+            kern[k]["algorithmic_bytes"] = kb
+            kern[k]["hbm_frac"] = round(kb / (v[0] / v[1] / 1e3) / 1e9 / hbm, 4)
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64", "arith": ARITH[args.variant], "data": "synthetic",
             "config": _config({"variant": args.variant, "parallelism": f"replicas{world}" if world > 1 else "single"},
                               cells=args.cells, nq=m.nq, nme=m.nme, nnz=nnz),
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk,
             "ms_per_step_with_kernel_events": round(sum(times_prof) / len(times_prof), 4),
-            "kernels": {k: {"ms_per_launch": round(v[0] / v[1], 5), "launches": int(v[1]),
-                            "share": round(v[0] / sum(x[0] for x in prof.values()), 4)} for k, v in sorted(prof.items())},
+            "kernels": kern,
             "assemble_only": asm}
     # end to end through the host-buffer call, right after the device-resident step (before the
     # other legs fill the device memory pools)
     if not args.no_e2e:
         line["e2e"] = e2e(feasm, torch, m, w, args)
+    if not args.no_fp64_variants and args.variant == "row":
+        line["fp64_variants"] = fp64_variants(feasm, torch, q_d, me_d, w_d, flush, stream, m)
     if not args.no_batched:
-        line["batched"] = batched(feasm, meshgen, torch, args)
+        line["batched"] = batched(feasm, meshgen, torch, args, hbm, peak_kind)
     if not args.no_other:
         line["elasticity"] = elasticity(feasm, meshgen, torch, flush, hbm, peak_kind)
-        line["adjoint"] = adjoint(feasm, meshgen, torch, flush)
+        line["adjoint"] = adjoint(feasm, meshgen, torch, flush, hbm, peak_kind)
         line["drop_zeros"] = drop_zeros(feasm, torch, pat0, S, flush, hbm, peak_kind, cells=args.cells)
         line["tetrahedra"] = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind)
         line["p2"] = p2(feasm, meshgen, torch, flush, hbm, peak_kind)
@@ -486,6 +507,48 @@ def run_ours(args) -> int:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+# The arithmetic each variant's element stage computes in (inputs and outputs are FP64 in all).
+ARITH = {"row": "double-float (pairs of FP32, about 48-bit significands) element arithmetic on the FP32 pipes; "
+                "FP64 inputs, coordinate differences and outputs",
+         "gather": "fp64", "atomic": "fp64"}
+
+
+def fp64_variants(feasm, torch, q_d, me_d, w_d, flush, stream, m, reps: int = 10) -> dict:
+    """The same step (mesh, pattern, S + M^[w]) by the two variants whose element arithmetic is
+    plain FP64: the deterministic staged gather and the FP64 atomics."""
+    out = {}
+    for name, variant in (("gather", feasm.GATHER), ("atomic", feasm.ATOMIC)):
+        gather, use_map = variant == feasm.GATHER, variant == feasm.ATOMIC
+        pat0 = feasm.Pattern(feasm.Mesh(q_d, me_d, borrow=True), gather=gather, map=use_map)
+        S, M = pat0.new_values(), pat0.new_values()
+        pat0.close()
+
+        def step():
+            mesh = feasm.Mesh(q_d, me_d, borrow=True)
+            pat = feasm.Pattern(mesh, gather=gather, map=use_map)
+            feasm.assemble_stiff_wmass(mesh, pat, w_d, variant, S, M)
+            pat.close()
+            mesh.close()
+
+        for _ in range(3):
+            step()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = sum(ts) / len(ts)
+        out[name] = {"ms_per_step": round(ms, 4), "value": round(m.nme / ms / 1e3, 3), "unit": UNIT, "arith": "fp64",
+                     "steps": reps}
+        del S, M
+    return out
 
 
 # Source files whose change invalidates a recorded DRAM-traffic figure of a kernel.
@@ -673,13 +736,16 @@ def tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 128) -
     return {"workload": f"S, M^w, M of the {cells}^3-cell cube (nq={m.nq}, nme={m.nme} tetrahedra, nnz={pat.nnz})",
             "mesh_ms": round(ms_mesh, 4), "pattern_ms": round(ms_pat, 4), "pattern_gather_ms": round(ms_pat_g, 4),
             **res, "S_atomic_melem_s": round(m.nme / res["S_atomic_ms"] / 1e3, 1),
-            "roofline": {"kernel": "k_tet_atomic<S>", "bound": "fp64", "algorithmic_ops": ops,
-                         "achieved": round(ops / k_ms / 1e6, 1), "peak": round(fp64_g, 1),
-                         "unit": "G FP64 instr/s", "frac": round(ops / k_ms / 1e6 / fp64_g, 4),
-                         "peak_source": "measured: independent FP64 fused multiply-add chains on every SM (fe_measure_fp64_rate)",
-                         "nominal_peak": round(FP64_PEAK_G, 1),
-                         "nominal_peak_source": "2 FP64 instructions per SM per clock x 152 SMs x 2.07 GHz",
-                         "hbm_frac": round(nbytes / k_ms / 1e6 / hbm, 4), "hbm_peak_source": f"{peak_kind} HBM copy bandwidth"}}
+            "roofline": {"kernel": "k_tet_atomic<S>", "bound": "hbm", "algorithmic_bytes": nbytes,
+                         "achieved": round(nbytes / k_ms / 1e6, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(nbytes / k_ms / 1e6 / hbm, 4), "peak_source": f"{peak_kind} HBM copy bandwidth",
+                         "limit": "L2 FP64 atomics (16 per tetrahedron): M, which has no arithmetic, takes as long as S",
+                         "fp64": {"algorithmic_ops": ops, "achieved": round(ops / k_ms / 1e6, 1), "peak": round(fp64_g, 1),
+                                  "unit": "G FP64 instr/s", "frac": round(ops / k_ms / 1e6 / fp64_g, 4),
+                                  "peak_source": "measured: independent FP64 fused multiply-add chains on every SM "
+                                                 "(fe_measure_fp64_rate)",
+                                  "nominal_peak": round(FP64_PEAK_G, 1),
+                                  "nominal_peak_source": "2 FP64 instructions per SM per clock x 152 SMs x 2.07 GHz"}}}
 
 
 def p2(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 1024) -> dict:
@@ -716,7 +782,7 @@ def p2(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 1024) -> dict:
                          "note": "36 FP64 atomics per element into values zeroed first; the atomics, not DRAM, set the time"}}
 
 
-def adjoint(feasm, meshgen, torch, flush) -> dict:
+def adjoint(feasm, meshgen, torch, flush, hbm, peak_kind) -> dict:
     """dL/dq, dL/dw of L = <G_S, S> + <G_M, M^[w]> on the 1024 x 1024-cell mesh (deterministic gather)."""
     seed = 13053122 + 5
     m = meshgen.square_mesh(1024, seed)
@@ -727,12 +793,20 @@ def adjoint(feasm, meshgen, torch, flush) -> dict:
     ms_g = _time_calls(torch, lambda: feasm.adjoint_stiff_wmass(mesh, pat, w, GS, GM, feasm.GATHER), flush)
     ms_a = _time_calls(torch, lambda: feasm.adjoint_stiff_wmass(mesh, pat, w, GS, GM, feasm.ATOMIC), flush)
     ms_f = _time_calls(torch, lambda: feasm.assemble_stiff_wmass(mesh, pat, w, feasm.ROW), flush)
+    # compulsory bytes of the backward pass: both upstream arrays, me, q and w read once; dL/dq and
+    # dL/dw written once (the element-to-nnz map is the design's, not the method's)
+    nbytes = 16 * pat.nnz + 12 * m.nme + 16 * m.nq + 8 * m.nq + 16 * m.nq + 8 * m.nq
+    ms_b = min(ms_g, ms_a)
     return {"workload": f"S + M^[w] and adjoint, 1024x1024-cell mesh (nq={m.nq}, nme={m.nme}, nnz={pat.nnz})",
             "forward_ms": round(ms_f, 4), "adjoint_gather_ms": round(ms_g, 4), "adjoint_atomic_ms": round(ms_a, 4),
-            "adjoint_melem_s": round(m.nme / min(ms_g, ms_a) / 1e3, 2)}
+            "adjoint_melem_s": round(m.nme / ms_b / 1e3, 2),
+            "roofline": {"scope": "whole adjoint call (its kernels together), faster variant", "bound": "hbm",
+                         "algorithmic_bytes": nbytes, "achieved": round(nbytes / ms_b / 1e6, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(nbytes / ms_b / 1e6 / hbm, 4),
+                         "peak_source": f"{peak_kind} HBM copy bandwidth"}}
 
 
-def batched(feasm, meshgen, torch, args) -> dict:
+def batched(feasm, meshgen, torch, args, hbm, peak_kind) -> dict:
     seed = 13053122 + 4
     meshes = meshgen.batch_meshes(seed)
     fm = [feasm.Mesh(x.q, x.me) for x in meshes]
@@ -757,7 +831,14 @@ def batched(feasm, meshgen, torch, args) -> dict:
 
     ms_g = timed(b.assemble)
     ms_p = timed(b.assemble_plain)
+    # compulsory bytes: me and q read once, S and M values written once, per mesh
+    nbytes = sum(12 * x.nme + 16 * x.nq + 16 * p.nnz for x, p in zip(meshes, fp))
     return {"meshes": len(meshes), "nme": nme, "graph_ms": round(ms_g, 4), "plain_ms": round(ms_p, 4),
+            "roofline": {"scope": "one graph replay (the persistent launch)", "bound": "hbm", "algorithmic_bytes": nbytes,
+                         "achieved": round(nbytes / ms_g / 1e6, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(nbytes / ms_g / 1e6 / hbm, 4), "peak_source": f"{peak_kind} HBM copy bandwidth",
+                         "l2": "not flushed between the back-to-back replays; the batch's inputs and outputs (~1.5 GB) "
+                               "exceed L2"},
             "graph_melem_s": round(nme / ms_g / 1e3, 2), "plain_melem_s": round(nme / ms_p / 1e3, 2),
             "speedup": round(ms_p / ms_g, 3),
             "tuned": {"variant": {feasm.ROW: "row", feasm.ATOMIC: "atomic"}[variant], "block": block, "tile": tile,
@@ -817,6 +898,7 @@ def main() -> int:
     ap.add_argument("--cells", type=int, default=N_CELLS,
                     help="cells per side of the mesh (the workload is 2048; smaller values are for profiling)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-fp64-variants", action="store_true", help="skip the step timed by the FP64 variants")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip the elasticity, adjoint, zero-dropping, tetrahedra and P2 legs")
@@ -844,7 +926,7 @@ def run_leg(args) -> int:
     if args.only == "elasticity":
         out = elasticity(feasm, meshgen, torch, flush, hbm, peak_kind)
     elif args.only == "adjoint":
-        out = adjoint(feasm, meshgen, torch, flush)
+        out = adjoint(feasm, meshgen, torch, flush, hbm, peak_kind)
     elif args.only == "tetrahedra":
         out = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind, cells=args.tet_cells)
     elif args.only == "p2":

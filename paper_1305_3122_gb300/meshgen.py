@@ -28,7 +28,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 # stream ids (one per purpose, so that changing one draw never shifts another)
-S_JITTER_X, S_JITTER_Y, S_PERM, S_WNOISE, S_SIZES, S_GRAD_S, S_GRAD_M, S_SAMPLE, S_JITTER_Z = range(1, 10)
+S_JITTER_X, S_JITTER_Y, S_PERM, S_WNOISE, S_SIZES, S_GRAD_S, S_GRAD_M, S_SAMPLE, S_JITTER_Z, S_DIAG = range(1, 11)
 
 # seeds of the standard workloads: SEED_BASE + 1 mass on 64 x 64 cells, + 2 stiffness and weighted
 # mass on 2048 x 2048, + 3 elasticity on 1024 x 1024, + 4 the batch of 256 meshes, + 5 the
@@ -93,7 +93,8 @@ class Mesh:
         return self.me.shape[1]
 
 
-def square_mesh(N: int, seed: int, jitter: float = 0.2, permute: bool = True) -> Mesh:
+def square_mesh(N: int, seed: int, jitter: float = 0.2, permute: bool = True, random_diagonals: bool = False,
+                hole: bool = False, stretch: float = 1.0) -> Mesh:
     """Unit square cut into N x N cells, each cell split into two triangles.
 
     Node (i, j) has id ``j*(N+1)+i`` at ``(i/N, j/N)`` before the permutation. Cell (i, j) with
@@ -103,9 +104,27 @@ def square_mesh(N: int, seed: int, jitter: float = 0.2, permute: bool = True) ->
     and in y (h = 1/N); boundary nodes stay put, so the domain stays the unit square. With
     jitter <= 0.2 no triangle can invert. Then the node ids are randomly permuted (element order
     and the local vertex order of each triangle are kept).
+
+    Unstructured variants (the method applies to any triangulation):
+
+    - ``random_diagonals``: each cell takes the diagonal a-c (as above) or b-d, with probability
+      1/2 each from the stream ``S_DIAG``; the b-d split gives (a,b,d) and (b,c,d), also
+      counter-clockwise. An interior vertex then lies in 4 to 8 triangles (4 plus the number of
+      its four cells whose diagonal ends at it), so closed fans of every size 4..8 occur, and
+      boundary vertices have open fans of 1 to 4 triangles. Every triangle is still a right
+      isosceles triangle of legs h before the jitter, so none can invert for jitter <= 0.2.
+    - ``hole`` (needs N >= 8): the cells with N/4 <= i, j < N/2 are removed (a square hole; the
+      nodes strictly inside it belong to no triangle and keep their ids, giving empty rows), and
+      so are the cells (p+1, p) and (p, p+1) with p = (3N)//4, so that node (p+1, p+1) belongs
+      only to the cells (p, p) and (p+1, p+1): two fans that touch at one vertex.
+    - ``stretch``: x is multiplied by this factor after the jitter (the domain becomes
+      [0, stretch] x [0, 1]); triangles keep their orientation but get angles far from 45/90
+      degrees (about 8 to 165 degrees for stretch 7).
     """
     if N < 1:
         raise ValueError("N must be >= 1")
+    if hole and N < 8:
+        raise ValueError("hole needs N >= 8")
     n1 = N + 1
     h = 1.0 / N
     nq = n1 * n1
@@ -128,6 +147,20 @@ def square_mesh(N: int, seed: int, jitter: float = 0.2, permute: bool = True) ->
     me = np.empty((3, 2 * N * N), dtype=np.int64)
     me[0, 0::2], me[1, 0::2], me[2, 0::2] = a, b, c
     me[0, 1::2], me[1, 1::2], me[2, 1::2] = a, c, d
+    if random_diagonals:
+        flip = stream_uniform(seed, S_DIAG, N * N) >= 0.5
+        me[0, 0::2] = np.where(flip, a, me[0, 0::2])
+        me[1, 0::2] = np.where(flip, b, me[1, 0::2])
+        me[2, 0::2] = np.where(flip, d, me[2, 0::2])
+        me[0, 1::2] = np.where(flip, b, me[0, 1::2])
+        me[1, 1::2] = np.where(flip, c, me[1, 1::2])
+        me[2, 1::2] = np.where(flip, d, me[2, 1::2])
+    if hole:
+        lo, hi, p = N // 4, N // 2, (3 * N) // 4
+        gone = (ci >= lo) & (ci < hi) & (cj >= lo) & (cj < hi)
+        gone |= ((ci == p + 1) & (cj == p)) | ((ci == p) & (cj == p + 1))
+        me = me[:, np.repeat(~gone, 2)]
+    x = x * stretch
     q = np.stack([x, y]).astype(np.float64)
     if permute:
         newid = random_permutation(seed, S_PERM, nq)

@@ -80,6 +80,53 @@ def test_stiff_wmass_2048_full_size(mesh_2048, variant):
     assert vm.sum() == pytest.approx(np.sum(D / 2 * (w[me[0]] + w[me[1]] + w[me[2]]) / 3), rel=1e-12)
 
 
+@pytest.fixture(scope="module")
+def mesh_2048_unstructured():
+    seed = meshgen.SEED_BASE + 12
+    m = meshgen.square_mesh(2048, seed, random_diagonals=True, hole=True)
+    return m, meshgen.vertex_weights(m, seed)
+
+
+@pytest.mark.parametrize("variant", [feasm.ATOMIC, feasm.GATHER, feasm.ROW])
+def test_stiff_wmass_2048_unstructured(mesh_2048_unstructured, variant):
+    """The 2048 x 2048-cell square with random cell diagonals, a hole and a pinch vertex: rows of
+    every fan size, empty rows; sampled rows against the oracle, S 1 = 0 on every row and the
+    weighted-mass total, at the size of the headline workload."""
+    m, w = mesh_2048_unstructured
+    mesh = feasm.Mesh(m.q, m.me)
+    pat = feasm.Pattern(mesh, gather=(variant == feasm.GATHER))
+    S, Mw = feasm.assemble_stiff_wmass(mesh, pat, torch.tensor(w, device="cuda"), variant)
+    torch.cuda.synchronize()
+    rp = pat.row_ptr.cpu().numpy()
+    ci = pat.col_idx.cpu().numpy()
+    val = np.bincount(m.me.ravel(), minlength=m.nq)
+    assert np.array_equal(np.diff(rp) == 0, val == 0)          # empty rows exactly at unused vertices
+    # nnz: one diagonal entry per used vertex and two per edge
+    e = np.sort(np.concatenate([m.me[[0, 1]], m.me[[1, 2]], m.me[[2, 0]]], axis=1), axis=0)
+    n_edges = len(np.unique(e[0].astype(np.int64) * m.nq + e[1]))
+    assert pat.nnz == int((val > 0).sum()) + 2 * n_edges
+    # sampled rows: random ones, the unused vertices' neighbours and the vertices of each valence
+    rows = set(int(r) for r in meshgen.sample_indices(7, 48, m.nq))
+    for v in range(1, 9):
+        rows |= set(int(r) for r in np.nonzero(val == v)[0][:3])
+    rows = sorted(rows)
+    vs, vm = S.cpu().numpy(), Mw.cpu().numpy()
+    for kind, va in ((oracle.STIFF, vs), (oracle.WMASS, vm)):
+        for r, (cols, vals) in zip(rows, oracle.csr_row_values(kind, m.q, m.me, rows, w)):
+            np.testing.assert_array_equal(ci[rp[r]:rp[r + 1]], cols)
+            if len(cols):
+                assert np.abs(va[rp[r]:rp[r + 1]] - vals).max() <= ROW_TOL * np.abs(vals).max()
+    _check_map_sampled(m, rp, ci, pat.map.cpu().numpy())
+    rows_t = torch.repeat_interleave(torch.arange(m.nq, device="cuda"), torch.diff(pat.row_ptr.long()))
+    rs = torch.zeros(m.nq, dtype=torch.float64, device="cuda").index_add_(0, rows_t, S)
+    rmax = torch.zeros(m.nq, dtype=torch.float64, device="cuda").index_reduce_(0, rows_t, S.abs(), "amax")
+    assert bool((rs.abs() <= 16 * ROW_TOL * rmax).all())
+    x, y = m.q
+    me = m.me
+    D = (x[me[2]] - x[me[0]]) * (y[me[0]] - y[me[1]]) - (x[me[0]] - x[me[1]]) * (y[me[2]] - y[me[0]])
+    assert vm.sum() == pytest.approx(np.sum(D / 2 * (w[me[0]] + w[me[1]] + w[me[2]]) / 3), rel=1e-12)
+
+
 def test_mass_64_full_oracle():
     m = meshgen.square_mesh(64, meshgen.SEED_BASE + 1)
     mesh = feasm.Mesh(m.q, m.me)
@@ -114,9 +161,15 @@ def test_elasticity_1024_full_size(variant):
 
 # ------------------------------------------------------------------ adjoint
 
+ADJ_MESHES = {"grid96": {}, "rdiag_hole96": dict(random_diagonals=True, hole=True),
+              "rdiag_stretch80": dict(random_diagonals=True, stretch=4.0)}
+
+
+@pytest.mark.parametrize("mesh_kind", sorted(ADJ_MESHES))
 @pytest.mark.parametrize("variant", [feasm.ATOMIC, feasm.GATHER])
-def test_adjoint_vs_oracle(variant):
-    m = meshgen.square_mesh(96, meshgen.SEED_BASE + 5)
+def test_adjoint_vs_oracle(variant, mesh_kind):
+    kw = ADJ_MESHES[mesh_kind]
+    m = meshgen.square_mesh(80 if "stretch" in kw else 96, meshgen.SEED_BASE + 5, **kw)
     w = meshgen.vertex_weights(m, meshgen.SEED_BASE + 5)
     mesh = feasm.Mesh(m.q, m.me)
     pat = feasm.Pattern(mesh, gather=True)
@@ -193,8 +246,24 @@ def batch4():
     return meshes, fm, fp
 
 
+@pytest.fixture(scope="module")
+def batch4_oracle(batch4):
+    """The oracle's S and M for 64 meshes of the batch spanning its size range: every fourth mesh
+    in order of size, from the smallest to the largest."""
+    meshes = batch4[0]
+    order = np.argsort([m.nme for m in meshes], kind="stable")
+    picked = sorted(set(int(i) for i in order[::4]) | {int(order[-1])})
+    out = {}
+    for idx in picked:
+        m = meshes[idx]
+        rp, ci, vs = oracle.assemble(oracle.STIFF, m.q, m.me)
+        _, _, vm = oracle.assemble(oracle.MASS, m.q, m.me)
+        out[idx] = (rp, ci, vs, vm)
+    return out
+
+
 @pytest.mark.parametrize("variant", [feasm.ROW, feasm.ATOMIC])
-def test_batch_matches_plain_and_oracle(batch4, variant):
+def test_batch_matches_plain_and_oracle(batch4, batch4_oracle, variant):
     meshes, fm, fp = batch4
     assert len(meshes) == 256
     b = feasm.Batch(fm, fp)
@@ -203,18 +272,42 @@ def test_batch_matches_plain_and_oracle(batch4, variant):
     S, M = b.assemble()
     S = [t.clone() for t in S]
     M = [t.clone() for t in M]
+    # every mesh against the oracle where it was computed, element by element
+    assert len(batch4_oracle) >= 64
+    for idx, (rp, ci, vs, vm) in batch4_oracle.items():
+        assert_csr_equal(fp[idx].row_ptr.cpu(), fp[idx].col_idx.cpu(), rp, ci)
+        assert_values_close(rp, S[idx].cpu().numpy(), vs)
+        assert_values_close(rp, M[idx].cpu().numpy(), vm)
+    # and all 256 against the per-mesh launches of the same scheme
     Sp, Mp = b.assemble_plain()
     for m, s0, s1, m0, m1, p in zip(meshes, S, Sp, M, Mp, fp):
         rp = p.row_ptr.cpu().numpy()
         assert_values_close(rp, s0.cpu().numpy(), s1.cpu().numpy())
         assert_values_close(rp, m0.cpu().numpy(), m1.cpu().numpy())
-    for idx in (int(np.argmin([mm.nme for mm in meshes])), 7, int(np.argmax([mm.nme for mm in meshes]))):
-        m = meshes[idx]
-        rp, ci, vs = oracle.assemble(oracle.STIFF, m.q, m.me)
-        _, _, vm = oracle.assemble(oracle.MASS, m.q, m.me)
-        assert_csr_equal(fp[idx].row_ptr.cpu(), fp[idx].col_idx.cpu(), rp, ci)
-        assert_values_close(rp, S[idx].cpu().numpy(), vs)
-        assert_values_close(rp, M[idx].cpu().numpy(), vm)
+
+
+@pytest.mark.parametrize("variant", [feasm.ROW, feasm.ATOMIC])
+def test_batch_of_unstructured_meshes_matches_oracle(variant):
+    """A batch of random-diagonal meshes, with holes and stretches, of uneven sizes: every mesh
+    against the oracle."""
+    from tests.test_gpu_parity import bowtie_mesh
+    ms = [meshgen.square_mesh(n, 500 + n, random_diagonals=True, hole=(n >= 8 and n % 2 == 0),
+                              stretch=1.0 + (n % 5)) for n in (3, 8, 17, 40, 64, 130, 211)]
+    cases = [(m.q, m.me) for m in ms] + [bowtie_mesh()]
+    fm = [feasm.Mesh(q, me) for q, me in cases]
+    fp = [feasm.Pattern(x) for x in fm]
+    b = feasm.Batch(fm, fp)
+    for block, tile in ((128, 256), (256, 4096)):
+        b.configure(variant, block, tile)
+        S, M = b.assemble()
+        for (q, me), s, mm, p in zip(cases, S, M, fp):
+            rp, ci, vs = oracle.assemble(oracle.STIFF, q, me)
+            _, _, vm = oracle.assemble(oracle.MASS, q, me)
+            assert_csr_equal(p.row_ptr.cpu(), p.col_idx.cpu(), rp, ci)
+            assert_values_close(rp, s.cpu().numpy(), vs)
+            assert_values_close(rp, mm.cpu().numpy(), vm)
+    for x in fm:
+        x.check()
 
 
 def test_batch_row_variant_is_deterministic(batch4):
@@ -260,10 +353,9 @@ def test_batch_without_map_uses_row_owners():
 def test_batch_general_rows_match_oracle():
     """A batch whose meshes contain general rows (a vertex of valence 70, and a vertex shared by
     two separate fans): the row-owner scheme routes them through its general-row list."""
-    from tests.test_gpu_parity import fan_mesh
+    from tests.test_gpu_parity import bowtie_mesh, fan_mesh
     qf, mef = fan_mesh(70)
-    q2 = np.array([[0.0, 1.0, 0.0, -1.0, 0.0], [0.0, 0.0, 1.0, 0.0, -1.0]])
-    me2 = np.array([[0, 0], [1, 3], [2, 4]], np.int32)          # two triangles touching at vertex 0 only
+    q2, me2 = bowtie_mesh()                                      # two triangles touching at vertex 0 only
     sq = meshgen.square_mesh(9, 77)
     cases = [(qf, mef), (sq.q, sq.me), (q2, me2)]
     fm = [feasm.Mesh(q, me) for q, me in cases]

@@ -5,8 +5,9 @@ of each row's largest |a_ij| for both variants (FP64 atomics, ordered row sums);
 variant must be bit-identical from run to run. Meshes: jittered node-permuted squares (several
 warps and blocks), fans whose centre belongs to 8 triangles (a 25-column vertex row), 12 (37
 columns: a long row from the warp pass) and 70 (the long-row pass), five triangles on one edge
-(an 18-column edge row), the one- and two-triangle meshes, and the 1024 x 1024-cell square at full
-size on sampled rows.
+(an 18-column edge row), the one- and two-triangle meshes, unstructured squares (random cell
+diagonals, a hole, a stretch) and the bow-tie, and the 1024 x 1024-cell square at full size on
+sampled rows.
 """
 from __future__ import annotations
 
@@ -42,6 +43,14 @@ def _cases():
     me2 = np.array([[0, 0], [1, 2], [2, 3]], np.int32)
     out["two"] = (q2, me2)
     out["one"] = (q2, me2[:, :1].copy())
+    # unstructured: random cell diagonals (vertex rows of 4 to 8 triangles), a hole with unused
+    # vertices and a vertex in two fans, a stretched square, and the bow-tie
+    m = meshgen.square_mesh(29, 41, random_diagonals=True, hole=True)
+    out["rdiag_hole29"] = (m.q, m.me)
+    m = meshgen.square_mesh(24, 42, random_diagonals=True, stretch=6.0)
+    out["rdiag_stretch24"] = (m.q, m.me)
+    out["bowtie"] = (np.array([[0.0, 1.0, 0.0, -1.0, 0.0], [0.0, 0.0, 1.0, 0.0, -1.0]]),
+                     np.array([[0, 0], [1, 3], [2, 4]], np.int32))
     return out
 
 

@@ -3,7 +3,10 @@
 row_ptr / col_idx / map are compared bit-exactly; values within 1e-13 of each row's largest
 |a_ij|; the deterministic variant must be bit-identical from run to run. Meshes span several
 thread blocks with ragged tails, plus the edge cases (empty mesh, one triangle, a vertex of
-high valence that takes the shared-memory path, the two-triangle square).
+high valence that takes the shared-memory path, the two-triangle square), and unstructured
+meshes: random cell diagonals (closed fans of every size 4..8), a hole with unused vertices
+and a vertex in two fans, a stretched square with angles from about 4 to 168 degrees, and the
+bow-tie (two triangles touching at one vertex).
 """
 from __future__ import annotations
 
@@ -59,6 +62,31 @@ def fans_mesh(n_fans: int, n_out: int):
     return np.array(pts).T.copy(), np.array(tris, dtype=np.int32).T.copy()
 
 
+def bowtie_mesh():
+    """Two triangles that touch at vertex 0 only: vertex 0's row holds two separate fans."""
+    q = np.array([[0.0, 1.0, 0.0, -1.0, 0.0], [0.0, 0.0, 1.0, 0.0, -1.0]])
+    me = np.array([[0, 0], [1, 3], [2, 4]], np.int32)
+    return q, me
+
+
+def unstructured_cases():
+    """Meshes beyond the valence-6 grid: random cell diagonals (closed fans of 4 to 8 triangles,
+    open fans of 1 to 4), a hole (open fans around it, unused vertices, and a vertex where two
+    fans touch), and a stretched square (angles of about 4 to 168 degrees, so rows mix the
+    double-float and FP64 fan terms)."""
+    out = {}
+    m = meshgen.square_mesh(40, 31, random_diagonals=True)
+    out["rdiag40"] = (m.q, m.me)
+    m = meshgen.square_mesh(33, 32, random_diagonals=True, hole=True)
+    out["rdiag_hole33"] = (m.q, m.me)
+    m = meshgen.square_mesh(30, 33, random_diagonals=True, stretch=7.0)
+    out["rdiag_stretch30"] = (m.q, m.me)
+    m = meshgen.square_mesh(64, 34, random_diagonals=True, hole=True, stretch=2.5)
+    out["rdiag_hole_stretch64"] = (m.q, m.me)
+    out["bowtie"] = bowtie_mesh()
+    return out
+
+
 def _mesh_cases():
     m64 = meshgen.square_mesh(64, meshgen.SEED_BASE + 1)
     m37 = meshgen.square_mesh(37, 5)
@@ -70,7 +98,8 @@ def _mesh_cases():
     return {"square64": (m64.q, m64.me), "square37": (m37.q, m37.me), "fan70": (qf, mef), "fan12": (q12, me12),
             "fans5x4000": (qb, meb),
             "two": (q2, me2),
-            "one": (q2, me2[:, :1].copy())}
+            "one": (q2, me2[:, :1].copy()),
+            **unstructured_cases()}
 
 
 CASES = _mesh_cases()
@@ -116,9 +145,10 @@ def test_scalar_values(case, kind, variant):
     assert_values_close(rp, got.cpu().numpy(), va)
 
 
+@pytest.mark.parametrize("case", ["square64", "rdiag_hole33", "rdiag_stretch30", "bowtie"])
 @pytest.mark.parametrize("variant", VARIANTS)
-def test_stiff_wmass_fused(variant):
-    q, me = CASES["square64"]
+def test_stiff_wmass_fused(case, variant):
+    q, me = CASES[case]
     w = _weights(q)
     mesh = feasm.Mesh(q, me)
     pat = feasm.Pattern(mesh, gather=True)
@@ -129,7 +159,8 @@ def test_stiff_wmass_fused(variant):
     assert_values_close(rp, Mw.cpu().numpy(), vm)
 
 
-@pytest.mark.parametrize("case", ["square37", "fan70", "fan12", "two", "one"])
+@pytest.mark.parametrize("case", ["square37", "fan70", "fan12", "two", "one", "rdiag40", "rdiag_hole33",
+                                  "rdiag_stretch30", "bowtie"])
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_elasticity(case, variant):
     q, me = CASES[case]
@@ -141,9 +172,10 @@ def test_elasticity(case, variant):
     assert_values_close(rp, got.cpu().numpy(), va)
 
 
+@pytest.mark.parametrize("case", ["square64", "rdiag_hole_stretch64"])
 @pytest.mark.parametrize("variant", [feasm.GATHER, feasm.ROW])
-def test_deterministic_bit_identical_runs(variant):
-    q, me = CASES["square64"]
+def test_deterministic_bit_identical_runs(case, variant):
+    q, me = CASES[case]
     w = torch.tensor(_weights(q), device="cuda")
     mesh = feasm.Mesh(q, me)
     pat = feasm.Pattern(mesh, gather=True)
@@ -224,6 +256,24 @@ def test_host_one_shot_matches_device_path():
     assert_csr_equal(out["row_ptr"].numpy(), out["col_idx"].numpy(), rp, ci)
     assert_values_close(rp, out["S"].numpy(), vs)
     assert_values_close(rp, out["Mw"].numpy(), vm)
+
+
+@pytest.mark.parametrize("case", ["rdiag_hole33", "rdiag_stretch30"])
+def test_host_one_shot_on_unstructured_meshes(case):
+    """The pipelined host call (row blocks, empty rows inside the hole) equals the device-resident
+    row-owner call bit for bit and the oracle within tolerance."""
+    q, me = CASES[case]
+    w = _weights(q)
+    out = feasm.assemble_stiff_wmass_host(q, me, w)
+    rp, ci, vs = oracle.assemble(oracle.STIFF, q, me)
+    _, _, vm = oracle.assemble(oracle.WMASS, q, me, w)
+    assert_csr_equal(out["row_ptr"], out["col_idx"], rp, ci)
+    assert_values_close(rp, out["S"].numpy(), vs)
+    assert_values_close(rp, out["Mw"].numpy(), vm)
+    mesh = feasm.Mesh(q, me)
+    pat = feasm.Pattern(mesh, map=False)
+    S, Mw = feasm.assemble_stiff_wmass(mesh, pat, torch.tensor(w, device="cuda"), feasm.ROW)
+    assert torch.equal(S.cpu(), out["S"]) and torch.equal(Mw.cpu(), out["Mw"])
 
 
 def test_row_variant_needs_no_map():
