@@ -93,18 +93,20 @@ __device__ __forceinline__ int row_columns(int32_t i, int32_t beg, int32_t d, co
 // ------------------------------------------------------------------ fans (simple rows)
 
 // A row's fan with exactly D triangles (D <= FAN_MAX): triangle e is (i, J[e], L[e]),
-// counter-clockwise. The analysis is written for a compile-time D (the caller dispatches on the
-// row's valence), so no loop runs over unused slots.
+// counter-clockwise. The analysis is written for a compile-time bound D on the row's valence n:
+// a warp whose rows share their valence dispatches on it (n == D, so no loop runs over unused
+// slots); a warp of mixed valences runs every row with D = FAN_MAX, the n..D-1 slots holding
+// distinct negative ids that match no vertex and no other slot.
 template <int D>
 struct Fan {
     int32_t J[D], L[D];
 };
 
 template <int D>
-__device__ __forceinline__ void load_fan(const int2* __restrict__ adj, int32_t beg, Fan<D>& f) {
+__device__ __forceinline__ void load_fan(const int2* __restrict__ adj, int32_t beg, int n, Fan<D>& f) {
 #pragma unroll
     for (int e = 0; e < D; e++) {
-        int2 p = adj[beg + e];
+        int2 p = e < n ? adj[beg + e] : make_int2(-1 - e, -1 - e);
         f.J[e] = p.x;
         f.L[e] = p.y;
     }
@@ -114,7 +116,7 @@ __device__ __forceinline__ void load_fan(const int2* __restrict__ adj, int32_t b
 // distinct j's and distinct l's, else KIND_GENERAL. start = first triangle of the chain (for a
 // closed fan, the one with the smallest j, so the order does not depend on the bucket order).
 template <int D>
-__device__ __forceinline__ int fan_kind(const Fan<D>& f, int& start) {
+__device__ __forceinline__ int fan_kind(const Fan<D>& f, int n, int& start) {
     int nstart = 0, dup = 0, minj = INT32_MAX, minj_e = 0;
     start = 0;
 #pragma unroll
@@ -125,8 +127,8 @@ __device__ __forceinline__ int fan_kind(const Fan<D>& f, int& start) {
             is_l |= f.L[g] == f.J[e];
             if (g > e) dup |= (f.J[g] == f.J[e]) | (f.L[g] == f.L[e]);
         }
-        if (!is_l) { nstart++; start = e; }
-        if (f.J[e] < minj) { minj = f.J[e]; minj_e = e; }
+        if (!is_l) { nstart++; start = e; }                // an unused slot is its own l: never a start
+        if (e < n && f.J[e] < minj) { minj = f.J[e]; minj_e = e; }
     }
     if (dup || nstart > 1) return KIND_GENERAL;
     if (nstart == 0) start = minj_e;
@@ -137,6 +139,7 @@ __device__ __forceinline__ int fan_kind(const Fan<D>& f, int& start) {
         if (e == start) { jstart = f.J[e]; lcur = f.L[e]; }
 #pragma unroll
     for (int s = 1; s < D; s++) {
+        if (s >= n) break;
         bool found = false;
         int32_t lnext = 0;
 #pragma unroll
@@ -152,10 +155,10 @@ __device__ __forceinline__ int fan_kind(const Fan<D>& f, int& start) {
 // Column position of vertex x in the row of vertex i with fan f (kind closed/open, last
 // neighbour lend): the number of row entries below x.
 template <int D>
-__device__ __forceinline__ int fan_pos(const Fan<D>& f, int32_t i, int kind, int32_t lend, int32_t x) {
+__device__ __forceinline__ int fan_pos(const Fan<D>& f, int n, int32_t i, int kind, int32_t lend, int32_t x) {
     int p = (i < x) + (kind == KIND_OPEN && lend < x);
 #pragma unroll
-    for (int e = 0; e < D; e++) p += f.J[e] < x;
+    for (int e = 0; e < D; e++) p += (e < n) & (f.J[e] < x);
     return p;
 }
 
@@ -164,7 +167,7 @@ __device__ __forceinline__ int fan_pos(const Fan<D>& f, int32_t i, int kind, int
 // pos(n_e))) and the header (n_d, pos_self | pos_nd << 14 | kind << 28). None of it depends on
 // the row's CSR offset.
 template <int D>
-__device__ __forceinline__ void simple_row_records(int32_t i, int32_t beg, int kind, int start, const Fan<D>& f,
+__device__ __forceinline__ void simple_row_records(int32_t i, int32_t beg, int n, int kind, int start, const Fan<D>& f,
                                                    int2* __restrict__ fan, int2* __restrict__ hdr) {
     int32_t jcur = 0, lcur = 0;
 #pragma unroll
@@ -174,17 +177,19 @@ __device__ __forceinline__ void simple_row_records(int32_t i, int32_t beg, int k
     int32_t lend = lcur;
 #pragma unroll
     for (int s = 1; s < D; s++) {
+        if (s >= n) break;
         int32_t nl = lend;
 #pragma unroll
         for (int e = 0; e < D; e++)
             if (f.J[e] == lend) nl = f.L[e];
         lend = nl;
     }
-    int pself = fan_pos(f, i, kind, lend, i);
-    int pend = fan_pos(f, i, kind, lend, lend);
+    int pself = fan_pos(f, n, i, kind, lend, i);
+    int pend = fan_pos(f, n, i, kind, lend, lend);
 #pragma unroll
     for (int s = 0; s < D; s++) {
-        fan[beg + s] = make_int2(jcur, fan_pos(f, i, kind, lend, jcur));
+        if (s >= n) break;
+        fan[beg + s] = make_int2(jcur, fan_pos(f, n, i, kind, lend, jcur));
         int32_t nl = lcur;
 #pragma unroll
         for (int e = 0; e < D; e++)
@@ -195,18 +200,18 @@ __device__ __forceinline__ void simple_row_records(int32_t i, int32_t beg, int k
     hdr[i] = make_int2(lend, pself | (pend << 14) | (kind << 28));
 }
 
-// A simple row of valence D: returns its column count, or 0 if the fan is not simple (then
+// A simple row of valence n <= D: returns its column count, or 0 if the fan is not simple (then
 // nothing is written).
 template <int D>
-__device__ __forceinline__ int32_t simple_row(int32_t i, int32_t beg, const int2* __restrict__ adj,
+__device__ __forceinline__ int32_t simple_row(int32_t i, int32_t beg, int n, const int2* __restrict__ adj,
                                               int2* __restrict__ fan, int2* __restrict__ hdr) {
     Fan<D> f;
-    load_fan<D>(adj, beg, f);
+    load_fan<D>(adj, beg, n, f);
     int start;
-    int kind = fan_kind<D>(f, start);
+    int kind = fan_kind<D>(f, n, start);
     if (kind == KIND_GENERAL) return 0;
-    simple_row_records<D>(i, beg, kind, start, f, fan, hdr);
-    return D + 1 + (kind == KIND_OPEN);
+    simple_row_records<D>(i, beg, n, kind, start, f, fan, hdr);
+    return n + 1 + (kind == KIND_OPEN);
 }
 
 // Row analysis, once per row: the column count, and everything of the row that does not depend
@@ -225,15 +230,22 @@ __global__ void k_row_analyse(const int32_t* __restrict__ vptr, const int2* __re
         if (d == 0) { row_nnz[i] = 0; hdr[i] = make_int2(-1, KIND_GENERAL << 28); continue; }
         if (d <= FAN_MAX) {
             int32_t cnt = 0;
-            switch (d) {
-                case 1: cnt = simple_row<1>(i, beg, adj, fan, hdr); break;
-                case 2: cnt = simple_row<2>(i, beg, adj, fan, hdr); break;
-                case 3: cnt = simple_row<3>(i, beg, adj, fan, hdr); break;
-                case 4: cnt = simple_row<4>(i, beg, adj, fan, hdr); break;
-                case 5: cnt = simple_row<5>(i, beg, adj, fan, hdr); break;
-                case 6: cnt = simple_row<6>(i, beg, adj, fan, hdr); break;
-                case 7: cnt = simple_row<7>(i, beg, adj, fan, hdr); break;
-                default: cnt = simple_row<8>(i, beg, adj, fan, hdr); break;
+            // the warp's rows of valence 1..FAN_MAX: one specialisation if they share their valence,
+            // else the bounded form for all (not one specialisation after another)
+            const unsigned here = __activemask();
+            if (__match_any_sync(here, d) == here) {
+                switch (d) {
+                    case 1: cnt = simple_row<1>(i, beg, 1, adj, fan, hdr); break;
+                    case 2: cnt = simple_row<2>(i, beg, 2, adj, fan, hdr); break;
+                    case 3: cnt = simple_row<3>(i, beg, 3, adj, fan, hdr); break;
+                    case 4: cnt = simple_row<4>(i, beg, 4, adj, fan, hdr); break;
+                    case 5: cnt = simple_row<5>(i, beg, 5, adj, fan, hdr); break;
+                    case 6: cnt = simple_row<6>(i, beg, 6, adj, fan, hdr); break;
+                    case 7: cnt = simple_row<7>(i, beg, 7, adj, fan, hdr); break;
+                    default: cnt = simple_row<8>(i, beg, 8, adj, fan, hdr); break;
+                }
+            } else {
+                cnt = simple_row<FAN_MAX>(i, beg, d, adj, fan, hdr);
             }
             static_assert(FAN_MAX == 8, "the valence dispatch covers 1..8");
             if (cnt > 0) {
