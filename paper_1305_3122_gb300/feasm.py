@@ -111,9 +111,18 @@ def _check(status: int, what: str):
         raise FeasmError(status, f"{what}: {L.fe_status_string(status).decode()}: {L.fe_last_error().decode()}")
 
 
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(stream=None) -> int:
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return s.cuda_stream
+    """The cudaStream_t to pass: the given torch stream's, else the current stream's (read
+    without building a torch.cuda.Stream object when PyTorch offers that, which saves host time
+    in every call)."""
+    if stream is not None:
+        return stream.cuda_stream
+    if _raw_stream is not None:
+        return _raw_stream(torch.cuda.current_device())
+    return torch.cuda.current_stream().cuda_stream
 
 
 def _dptr(t: torch.Tensor | None, dtype: torch.dtype, what: str) -> int | None:
@@ -216,13 +225,34 @@ class Pattern:
         _check(lib().fe_pattern_info(h, ctypes.byref(n_rows), ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci)),
                "fe_pattern_info")
         self.n_rows, self.nnz = n_rows.value, nnz.value
-        self.row_ptr = _view_i32(rp.value, self.n_rows + 1, self)
-        self.col_idx = _view_i32(ci.value, self.nnz, self)
-        self.map = None
+        self._rp, self._ci = rp.value, ci.value
+        self._map = None
         if map or gather:
             mp, ml = _P(), _I64()
             _check(lib().fe_pattern_map(h, ctypes.byref(mp), ctypes.byref(ml)), "fe_pattern_map")
-            self.map = _view_i32(mp.value, ml.value, self)
+            self._map = (mp.value, ml.value)
+        self._views = {}
+
+    # The CSR arrays and the map are zero-copy views of the pattern's device memory, made on
+    # first access (making a view costs tens of microseconds of host time, which a build that is
+    # only used through the library's own calls need not pay).
+    def _view(self, key, ptr, n):
+        v = self._views.get(key)
+        if v is None:
+            v = self._views[key] = _view_i32(ptr, n, self)
+        return v
+
+    @property
+    def row_ptr(self) -> torch.Tensor:
+        return self._view("row_ptr", self._rp, self.n_rows + 1)
+
+    @property
+    def col_idx(self) -> torch.Tensor:
+        return self._view("col_idx", self._ci, self.nnz)
+
+    @property
+    def map(self) -> torch.Tensor | None:
+        return None if self._map is None else self._view("map", *self._map)
 
     @property
     def handle(self):
