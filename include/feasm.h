@@ -352,6 +352,20 @@ fe_status fe_batch_create(int32_t n, const fe_mesh* meshes, const fe_pattern* pa
 fe_status fe_batch_tune(fe_batch batch, double* const* S_values, double* const* M_values,
                         fe_stream stream, int32_t* block, int32_t* tile);
 
+/* fe_batch_tune with a file cache of its choices, so that a later process (or a later batch of
+ * the same shape) skips the timing. cache_path names a JSON file (NULL or "": the path in the
+ * environment variable FEASM_TUNE_CACHE; neither set: plain fe_batch_tune). Each entry is keyed
+ * by the device's name and SM count and by the batch's signature (a hash of every mesh's vertex,
+ * triangle and non-zero counts, in order, and of whether all patterns carry the element map).
+ * A cached choice is configured without timing (*from_cache = 1, if not NULL); otherwise the
+ * candidates are timed as by fe_batch_tune and the choice is added to the file (written to a
+ * temporary name and renamed over it; FE_ERR_INVALID_ARG if it cannot be written). The cache
+ * belongs to the tuning call, not to batch creation, because timing needs the output buffers.
+ * Not in the paper (its assembly has no launch parameters). Synchronises. */
+fe_status fe_batch_tune_cached(fe_batch batch, const char* cache_path, double* const* S_values,
+                               double* const* M_values, fe_stream stream, int32_t* block,
+                               int32_t* tile, int32_t* from_cache);
+
 /* Sets the scheme and launch shape explicitly: variant FE_VARIANT_ROW (block 64..256) or
  * FE_VARIANT_ATOMIC (block 64..1024), block a multiple of 32, tile >= 1. Synchronises the
  * device (the graph may be in flight) and recaptures the graph. */

@@ -364,3 +364,160 @@ extern "C" fe_status fe_batch_tune(fe_batch b, double* const* S, double* const* 
     if (tile_out) *tile_out = bt;
     return FE_OK;
 }
+
+// ---------------------------------------------------------------- tuning cache
+//
+// fe_batch_tune_cached keeps each tuning result in a small JSON file: one object mapping a key to
+// the chosen scheme and shape,
+//   {
+//   "<device>|sm<count>|n<meshes>|<signature>": {"variant": 2, "block": 256, "tile": 1024, "ms": 0.98},
+//   ...
+//   }
+// The signature is a 64-bit FNV-1a hash of every mesh's vertex, triangle and non-zero counts and
+// of whether all patterns carry the element map (what the candidates' times depend on). The file
+// is read and rewritten whole (written to a temporary name, then renamed over the old file), one
+// entry per line; the reader accepts the files this writer produces.
+
+#include <stdio.h>
+#include <stdlib.h>
+#include <unistd.h>
+
+#include <map>
+#include <string>
+
+namespace {
+
+struct TuneChoice {
+    int variant = 0, block = 0, tile = 0;
+    double ms = 0.0;
+};
+
+uint64_t fnv1a(uint64_t h, uint64_t v) {
+    for (int i = 0; i < 8; i++) {
+        h ^= (v >> (8 * i)) & 0xFFu;
+        h *= 0x100000001B3ull;
+    }
+    return h;
+}
+
+std::string tune_key(fe_batch b) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) prop.name[0] = 0, prop.multiProcessorCount = 0;
+    uint64_t h = 0xCBF29CE484222325ull;
+    h = fnv1a(h, (uint64_t)b->n);
+    h = fnv1a(h, b->has_map ? 1u : 0u);
+    for (int32_t m = 0; m < b->n; m++) {
+        h = fnv1a(h, (uint64_t)(uint32_t)b->meshes[m]->nq);
+        h = fnv1a(h, (uint64_t)(uint32_t)b->meshes[m]->nme);
+        h = fnv1a(h, (uint64_t)b->patterns[m]->nnz);
+    }
+    std::string name(prop.name);
+    for (char& c : name)
+        if (c == '"' || c == '\\' || c == '|' || (unsigned char)c < 32) c = '_';
+    char buf[64];
+    snprintf(buf, sizeof buf, "|sm%d|n%d|%016llx", prop.multiProcessorCount, (int)b->n, (unsigned long long)h);
+    return name + buf;
+}
+
+// Entries of a cache file ("" or unreadable: none).
+std::map<std::string, TuneChoice> read_cache(const char* path) {
+    std::map<std::string, TuneChoice> out;
+    FILE* f = fopen(path, "r");
+    if (!f) return out;
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        char* q0 = strchr(line, '"');
+        if (!q0) continue;
+        char* q1 = strchr(q0 + 1, '"');
+        if (!q1) continue;
+        TuneChoice c;
+        const char* v = strstr(q1, "\"variant\":");
+        const char* bl = strstr(q1, "\"block\":");
+        const char* t = strstr(q1, "\"tile\":");
+        const char* ms = strstr(q1, "\"ms\":");
+        if (!v || !bl || !t) continue;
+        c.variant = atoi(v + 10);
+        c.block = atoi(bl + 8);
+        c.tile = atoi(t + 7);
+        c.ms = ms ? atof(ms + 5) : 0.0;
+        out[std::string(q0 + 1, q1)] = c;
+    }
+    fclose(f);
+    return out;
+}
+
+bool write_cache(const char* path, const std::map<std::string, TuneChoice>& entries) {
+    std::string tmp = std::string(path) + ".tmp" + std::to_string((long long)getpid());
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    fputs("{\n", f);
+    size_t k = 0;
+    for (const auto& e : entries) {
+        fprintf(f, "\"%s\": {\"variant\": %d, \"block\": %d, \"tile\": %d, \"ms\": %.6f}%s\n", e.first.c_str(),
+                e.second.variant, e.second.block, e.second.tile, e.second.ms, ++k < entries.size() ? "," : "");
+    }
+    fputs("}\n", f);
+    bool ok = fclose(f) == 0;
+    if (ok) ok = rename(tmp.c_str(), path) == 0;
+    if (!ok) remove(tmp.c_str());
+    return ok;
+}
+
+}  // namespace
+
+extern "C" fe_status fe_batch_tune_cached(fe_batch b, const char* cache_path, double* const* S, double* const* M,
+                                          fe_stream stream, int32_t* block_out, int32_t* tile_out,
+                                          int32_t* from_cache) {
+    FE_RANGE(__func__);
+    if (!b) return fe_fail(FE_ERR_INVALID_ARG, "null batch");
+    if (from_cache) *from_cache = 0;
+    const char* path = cache_path && cache_path[0] ? cache_path : getenv("FEASM_TUNE_CACHE");
+    if (!path || !path[0]) return fe_batch_tune(b, S, M, stream, block_out, tile_out);
+    const std::string key = tune_key(b);
+    std::map<std::string, TuneChoice> entries = read_cache(path);
+    auto it = entries.find(key);
+    if (it != entries.end()) {
+        const TuneChoice& c = it->second;
+        const bool usable = (c.variant == FE_VARIANT_ROW || (c.variant == FE_VARIANT_ATOMIC && b->has_map)) &&
+                            c.block >= 64 && c.block <= max_block(c.variant) && c.block % 32 == 0 && c.tile >= 1;
+        if (usable) {
+            fe_status st = set_outputs(b, S, M, (cudaStream_t)stream);
+            if (!st) st = fe_batch_configure(b, c.variant, c.block, c.tile);
+            if (st) return st;
+            if (block_out) *block_out = c.block;
+            if (tile_out) *tile_out = c.tile;
+            if (from_cache) *from_cache = 1;
+            return FE_OK;
+        }
+    }
+    int32_t blk = 0, tl = 0;
+    fe_status st = fe_batch_tune(b, S, M, stream, &blk, &tl);
+    if (st) return st;
+    // the chosen configuration's time, for the record (one more timed replay set)
+    TuneChoice c;
+    c.variant = b->variant;
+    c.block = blk;
+    c.tile = tl;
+    {
+        cudaStream_t s = (cudaStream_t)stream;
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 5; r++) launch_batch(b, s);
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) c.ms = ms / 5;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+    }
+    entries = read_cache(path);                        // another process may have added entries meanwhile
+    entries[key] = c;
+    if (!write_cache(path, entries))
+        return fe_fail(FE_ERR_INVALID_ARG, std::string("could not write the tuning cache ") + path);
+    if (block_out) *block_out = blk;
+    if (tile_out) *tile_out = tl;
+    return FE_OK;
+}

@@ -63,6 +63,8 @@ SIGNATURES = {
     "fe_assemble_stiff_wmass_host": (_INT, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "fe_batch_create": (_INT, [_I32, _P, _P, ctypes.POINTER(_P)]),
     "fe_batch_tune": (_INT, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "fe_batch_tune_cached": (_INT, [_P, ctypes.c_char_p, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                    ctypes.POINTER(_I32)]),
     "fe_batch_set_shape": (_INT, [_P, _I32, _I32]),
     "fe_batch_configure": (_INT, [_P, _I32, _I32, _I32]),
     "fe_batch_get_config": (_INT, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
@@ -568,10 +570,19 @@ class Batch:
         self._tables = ((_P * max(n, 1))(*[t.data_ptr() for t in self.S]),
                         (_P * max(n, 1))(*[t.data_ptr() for t in self.M]))
 
-    def tune(self, stream=None) -> tuple[int, int]:
-        b, t = _I32(), _I32()
-        _check(lib().fe_batch_tune(self._h, self._tables[0], self._tables[1], _stream(stream), ctypes.byref(b),
-                                   ctypes.byref(t)), "fe_batch_tune")
+    def tune(self, stream=None, cache: str | None = None) -> tuple[int, int]:
+        """Times the candidates and keeps the fastest (fe_batch_tune). With cache (a file path, or
+        "" for the path in FEASM_TUNE_CACHE) a cached choice for this device and batch shape is
+        used without timing (fe_batch_tune_cached); self.from_cache tells which happened."""
+        b, t, fc = _I32(), _I32(), _I32()
+        if cache is None:
+            _check(lib().fe_batch_tune(self._h, self._tables[0], self._tables[1], _stream(stream), ctypes.byref(b),
+                                       ctypes.byref(t)), "fe_batch_tune")
+        else:
+            _check(lib().fe_batch_tune_cached(self._h, cache.encode(), self._tables[0], self._tables[1],
+                                              _stream(stream), ctypes.byref(b), ctypes.byref(t), ctypes.byref(fc)),
+                   "fe_batch_tune_cached")
+        self.from_cache = bool(fc.value)
         return b.value, t.value
 
     def set_shape(self, block: int, tile: int):
