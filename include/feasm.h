@@ -215,6 +215,34 @@ fe_status fe_assemble_stiff_wmass_noalloc(fe_mesh mesh, fe_pattern pattern, cons
                                           double* S_values, double* Mw_values, int64_t cap,
                                           fe_stream stream);
 
+/* ---------------------------------------------------------- row partitions ---- */
+
+/* One mesh over several ranks (processes, GPUs) by rows, with no exchange of values: row i of
+ * the global matrix is the structural sum (Sections 5-6) over the triangles that contain vertex
+ * i, so a rank that owns the rows [row_begin, row_end) needs exactly the triangles with a vertex
+ * in that range. Triangles with vertices of two ranks are held and computed by both (halo
+ * triangles); each rank writes its own rows, with global column ids, and the ranks' row blocks
+ * in rank order form the whole CSR matrix. Not in the paper (one Matlab process); the calls
+ * communicate nothing, the caller launches the ranks and collects their blocks.
+ *
+ * fe_mesh_create_part: from the global mesh (q [2][nq], me [3][nme], host or device as for
+ * fe_mesh_create), keeps the triangles touching [row_begin, row_end) in ascending order with
+ * their global vertex ids (the selection and compaction run on the device) and all nq
+ * coordinates. Checks the kept triangles as fe_mesh_create does, reporting global triangle
+ * indices, and any vertex id outside [0, nq) (FE_ERR_INDEX_RANGE); 0 <= row_begin <= row_end
+ * <= nq (FE_ERR_INVALID_ARG). Synchronises. Destroy with fe_mesh_destroy. */
+fe_status fe_mesh_create_part(int32_t nq, int32_t nme, const double* q, const int32_t* me, int ptr_kind,
+                              int32_t row_begin, int32_t row_end, fe_stream stream, fe_mesh* out);
+
+/* The CSR rows [row_begin, row_end) of a part (within its owned rows) or of a whole mesh, as a
+ * pattern of n_rows = row_end - row_begin rows whose row_ptr starts at 0 and whose col_idx holds
+ * global column ids (fe_pattern_info). Scalar (dofs_per_vertex 1) and without the map or the
+ * gather lists: it assembles with FE_VARIANT_ROW only (fe_assemble_mass, _wmass, _stiff,
+ * _stiff_wmass), into outputs of capacity >= its nnz, each row's values bit-identical to the
+ * whole mesh's row-owner assembly. Synchronises. */
+fe_status fe_pattern_build_part(fe_mesh mesh, int32_t row_begin, int32_t row_end, fe_stream stream,
+                                fe_pattern* out);
+
 /* ---------------------------------------------------------- tetrahedra (3-D P1) ---- */
 
 /* The paper states that its method extends to three dimensions without giving the formulas. These

@@ -291,6 +291,8 @@ static fe_status check_out(fe_pattern p, const double* values, int64_t cap) {
 static fe_status check_variant(fe_pattern p, int variant) {
     if (variant != FE_VARIANT_ATOMIC && variant != FE_VARIANT_GATHER && variant != FE_VARIANT_ROW)
         return fe_fail(FE_ERR_INVALID_ARG, "unknown variant");
+    if (p->row1 >= 0 && variant != FE_VARIANT_ROW)
+        return fe_fail(FE_ERR_INVALID_ARG, "a row-window pattern (fe_pattern_build_part) assembles with FE_VARIANT_ROW only");
     if (variant == FE_VARIANT_GATHER && !(p->flags & FE_PATTERN_GATHER))
         return fe_fail(FE_ERR_INVALID_ARG, "FE_VARIANT_GATHER needs a pattern built with FE_PATTERN_GATHER");
     if (variant == FE_VARIANT_ATOMIC && !p->map)

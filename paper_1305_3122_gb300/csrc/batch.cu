@@ -207,6 +207,7 @@ extern "C" fe_status fe_batch_create(int32_t n, const fe_mesh* meshes, const fe_
     b->n = n;
     for (int32_t m = 0; m < n; m++) {
         fe_status st = fe_check_pair(meshes[m], patterns[m], 1);
+        if (!st && patterns[m]->row1 >= 0) st = fe_fail(FE_ERR_INVALID_ARG, "batches take whole-mesh patterns, not row windows");
         if (st) { fe_batch_destroy(b); return st; }
         fe_mesh me = meshes[m];
         fe_pattern p = patterns[m];

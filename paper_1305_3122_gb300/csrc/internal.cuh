@@ -20,6 +20,8 @@ struct fe_mesh_s {
     int* err = nullptr;         // device error word: bit 0 = a triangle with signed area <= 0,
                                 // bit 1 = a value outside the double-float range (see ff.cuh)
     uint64_t topology_id = 0;   // identifies the connectivity (patterns remember it)
+    int32_t part0 = 0, part1 = -1;        // a rank's share of a row partition: owned rows [part0, part1)
+                                          // (part1 < 0: a whole mesh)
     cudaStream_t last_stream = nullptr;   // frees are ordered on the last stream that used the handle
 };
 
@@ -50,6 +52,10 @@ struct fe_pattern_s {
                                           // kind << 28), kind 0 closed / 1 open; kind 2 = general row
     int32_t* gen_rows = nullptr;          // general rows (assembled one block per row)
     int32_t n_gen = 0;
+    // row window (fe_pattern_build_part): the pattern exposes rows [row0, row1) only; row1 < 0: all
+    int32_t row0 = 0, row1 = -1;
+    int32_t* row_ptr_w = nullptr;         // [row1 - row0 + 1] the window's offsets, from 0
+    int64_t base_w = 0;                   // row_ptr[row0]: the window's first entry in the full arrays
     cudaStream_t last_stream = nullptr;
 };
 

@@ -567,6 +567,7 @@ extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, int flags, fe
     *out = nullptr;
     fe_status st;
     if ((st = fe_check_pair(m, p1, 1))) return st;
+    if (p1->row1 >= 0) return fe_fail(FE_ERR_INVALID_ARG, "the P2 pattern needs a whole-mesh scalar pattern, not a row window");
     const int32_t nq = m->nq, nme = m->nme;
     if (36 * (int64_t)nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "36*nme must be < 2^31");
     cudaStream_t s = (cudaStream_t)stream;

@@ -575,7 +575,7 @@ extern "C" void fe_pattern_destroy(fe_pattern p) {
     fe_free(p->row_ptr); fe_free(p->col_idx); fe_free(p->map);
     fe_free(p->row_ptr2); fe_free(p->col_idx2);
     fe_free(p->seg_ptr); fe_free(p->perm); fe_free(p->vptr); fe_free(p->vel); fe_free(p->kg);
-    fe_free(p->fan); fe_free(p->hdr); fe_free(p->gen_rows);
+    fe_free(p->fan); fe_free(p->hdr); fe_free(p->gen_rows); fe_free(p->row_ptr_w);
     delete p;
 }
 
@@ -758,6 +758,11 @@ extern "C" fe_status fe_pattern_info(fe_pattern p, int64_t* n_rows, int64_t* nnz
     if (!p) return fe_fail(FE_ERR_INVALID_ARG, "null pattern");
     if (n_rows) *n_rows = p->n_rows;
     if (nnz) *nnz = p->nnz;
+    if (p->row1 >= 0) {                                   // a row window: its rows only
+        if (row_ptr) *row_ptr = p->row_ptr_w;
+        if (col_idx) *col_idx = p->col_idx + p->base_w;
+        return FE_OK;
+    }
     if (row_ptr) *row_ptr = p->dofs == 2 ? p->row_ptr2 : p->row_ptr;
     if (col_idx) *col_idx = p->dofs == 2 ? p->col_idx2 : p->col_idx;
     return FE_OK;

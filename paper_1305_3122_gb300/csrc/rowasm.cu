@@ -456,14 +456,17 @@ __device__ __forceinline__ void general_row(int32_t i, const int32_t* __restrict
     }
 }
 
+// General rows of the list that lie in [r0, r1) (a row window), one block each.
 template <int KIND>
 __global__ void k_general_scalar(const int32_t* __restrict__ gen, const int32_t* __restrict__ row_ptr,
                                  const int32_t* __restrict__ col_idx, const int32_t* __restrict__ vptr,
                                  const int2* __restrict__ fan, const double2* __restrict__ q,
                                  const double* __restrict__ w, Consts cs, double* __restrict__ out0,
-                                 double* __restrict__ out1, int* __restrict__ err) {
+                                 double* __restrict__ out1, int* __restrict__ err, int32_t r0, int32_t r1) {
+    const int32_t i = gen[blockIdx.x];
+    if (i < r0 || i >= r1) return;
     int bad = 0, orient = 0;
-    general_row<KIND>(gen[blockIdx.x], row_ptr, col_idx, vptr, fan, q, w, cs, out0, out1, bad, orient);
+    general_row<KIND>(i, row_ptr, col_idx, vptr, fan, q, w, cs, out0, out1, bad, orient);
     if (bad) atomicOr(err, 2);
     if (orient) atomicOr(err, 1);
 }
@@ -736,12 +739,20 @@ static fe_status launch_scalar(fe_mesh m, fe_pattern p, const double* w, double*
             return fe_cuda_fail(e0, "k_pack_vrec");
         }
     }
-    { FE_PROF("k_fan_scalar", s); k_fan_scalar<KIND><<<fe_grid(m->nq, FAN_SCALAR_BLOCK, FanOcc<KIND>::blocks), FAN_SCALAR_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, 0, m->nq, cs, out0, out1, m->err); }
+    // a row window (fe_pattern_build_part) assembles its rows only, into an output that holds
+    // just them: the output pointers are shifted back by the window's first entry
+    const bool win = p->row1 >= 0;
+    const int32_t r0 = win ? p->row0 : 0, r1 = win ? p->row1 : m->nq;
+    if (win) {
+        out0 -= p->base_w;
+        if (out1) out1 -= p->base_w;
+    }
+    if (r1 > r0) { FE_PROF("k_fan_scalar", s); k_fan_scalar<KIND><<<fe_grid(r1 - r0, FAN_SCALAR_BLOCK, FanOcc<KIND>::blocks), FAN_SCALAR_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, r0, r1, cs, out0, out1, m->err); }
     cudaError_t e = cudaGetLastError();
     fe_free(vr);
     if (e != cudaSuccess) return fe_cuda_fail(e, "k_fan_scalar");
     if (p->n_gen > 0) {
-        { FE_PROF("k_general_scalar", s); k_general_scalar<KIND><<<p->n_gen, GEN_BLOCK, 0, s>>>(p->gen_rows, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q, w, cs, out0, out1, m->err); }
+        { FE_PROF("k_general_scalar", s); k_general_scalar<KIND><<<p->n_gen, GEN_BLOCK, 0, s>>>(p->gen_rows, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q, w, cs, out0, out1, m->err, r0, r1); }
         FE_LAUNCHED("k_general_scalar");
     }
     return FE_OK;
@@ -912,7 +923,7 @@ extern "C" fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const
     if (p->n_gen > 0) {
         FE_PROF("k_general_scalar", s);
         k_general_scalar<W_S | W_W><<<p->n_gen, GEN_BLOCK, 0, s>>>(p->gen_rows, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q,
-                                                                   wd, cs, Sd, Md, m->err);
+                                                                   wd, cs, Sd, Md, m->err, 0, nq);
     }
     for (int k = 0; k < E2E_BLOCKS; k++) {
         int32_t r0 = (int32_t)((int64_t)nq * k / E2E_BLOCKS), r1 = (int32_t)((int64_t)nq * (k + 1) / E2E_BLOCKS);

@@ -40,6 +40,8 @@ SIGNATURES = {
     "fe_pattern_info": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "fe_pattern_map": (_INT, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
     "fe_pattern_destroy": (None, [_P]),
+    "fe_mesh_create_part": (_INT, [_I32, _I32, _P, _P, _INT, _I32, _I32, _P, ctypes.POINTER(_P)]),
+    "fe_pattern_build_part": (_INT, [_P, _I32, _I32, _P, ctypes.POINTER(_P)]),
     "fe_assemble_mass": (_INT, [_P, _P, _INT, _P, _I64, _P]),
     "fe_assemble_wmass": (_INT, [_P, _P, _P, _INT, _P, _I64, _P]),
     "fe_assemble_stiff": (_INT, [_P, _P, _INT, _P, _I64, _P]),
@@ -184,6 +186,34 @@ class Mesh:
         _check(L.fe_mesh_create(self.nq, self.nme, qp, mp, kind, _stream(stream), ctypes.byref(h)), "fe_mesh_create")
         self._h = h
 
+    @classmethod
+    def part(cls, q, me, row_begin: int, row_end: int, stream=None) -> "Mesh":
+        """A rank's share of a row partition (fe_mesh_create_part): the triangles of the global
+        mesh (q [2, nq], me [3, nme], host or CUDA) that touch the owned vertices
+        [row_begin, row_end), with global vertex ids."""
+        self = cls.__new__(cls)
+        self._h = None
+        self._me_ref = None
+        if isinstance(q, torch.Tensor) and q.is_cuda:
+            qd, med = q.contiguous(), me.contiguous()
+            qp, mp, kind = _dptr(qd, torch.float64, "q"), _dptr(med, torch.int32, "me"), PTR_DEVICE
+        else:
+            qd = np.ascontiguousarray(q.cpu().numpy() if isinstance(q, torch.Tensor) else q, dtype=np.float64)
+            med = np.ascontiguousarray(me.cpu().numpy() if isinstance(me, torch.Tensor) else me, dtype=np.int32)
+            qp, mp, kind = qd.ctypes.data, med.ctypes.data, PTR_HOST
+        if qd.shape[0] != 2 or med.shape[0] != 3:
+            raise ValueError("q must be [2, nq] and me must be [3, nme]")
+        nq, nme_global = int(qd.shape[1]), int(med.shape[1])
+        h = _P()
+        _check(lib().fe_mesh_create_part(nq, nme_global, qp, mp, kind, int(row_begin), int(row_end), _stream(stream),
+                                         ctypes.byref(h)), "fe_mesh_create_part")
+        self._h = h
+        n1, n2 = _I32(), _I32()
+        _check(lib().fe_mesh_info(h, ctypes.byref(n1), ctypes.byref(n2)), "fe_mesh_info")
+        self.nq, self.nme = n1.value, n2.value
+        self.rows = (int(row_begin), int(row_end))
+        return self
+
     @property
     def handle(self):
         return self._h
@@ -213,12 +243,20 @@ class Mesh:
 class Pattern:
     """CSR structure and element-to-nnz map of a mesh (fe_pattern_build)."""
 
-    def __init__(self, mesh: Mesh, dofs: int = 1, gather: bool = False, map: bool = True, stream=None):
+    def __init__(self, mesh: Mesh, dofs: int = 1, gather: bool = False, map: bool = True, stream=None,
+                 rows: tuple[int, int] | None = None):
         """gather: also build what FE_VARIANT_GATHER needs; map: also the element-to-nnz map
-        (FE_VARIANT_ATOMIC, the adjoint, atomic batches). FE_VARIANT_ROW works with any pattern."""
+        (FE_VARIANT_ATOMIC, the adjoint, atomic batches). FE_VARIANT_ROW works with any pattern.
+        rows=(begin, end): only those rows (fe_pattern_build_part; scalar, no map, FE_VARIANT_ROW)."""
         h = _P()
-        flags = (PATTERN_GATHER if gather else 0) | (PATTERN_MAP if map else 0)
-        _check(lib().fe_pattern_build(mesh.handle, dofs, flags, _stream(stream), ctypes.byref(h)), "fe_pattern_build")
+        if rows is not None:
+            gather, map = False, False
+            _check(lib().fe_pattern_build_part(mesh.handle, int(rows[0]), int(rows[1]), _stream(stream),
+                                               ctypes.byref(h)), "fe_pattern_build_part")
+        else:
+            flags = (PATTERN_GATHER if gather else 0) | (PATTERN_MAP if map else 0)
+            _check(lib().fe_pattern_build(mesh.handle, dofs, flags, _stream(stream), ctypes.byref(h)), "fe_pattern_build")
+        self.rows = rows
         self._h = h
         self.mesh = mesh
         self.dofs = dofs
@@ -264,8 +302,9 @@ class Pattern:
         return torch.empty(self.nnz, dtype=torch.float64, device="cuda")
 
     def to_sparse_csr(self, values: torch.Tensor) -> torch.Tensor:
+        n_cols = self.mesh.nq * self.dofs if self.rows is not None else self.n_rows
         return torch.sparse_csr_tensor(self.row_ptr.long(), self.col_idx.long(), values,
-                                       size=(self.n_rows, self.n_rows))
+                                       size=(self.n_rows, n_cols))
 
     def close(self):
         """Release the pattern's device arrays now (views of them become invalid)."""

@@ -45,6 +45,8 @@ class _Fixtures:
         small = [meshgen.square_mesh(n, 5 + n) for n in (3, 6)]
         self.bmesh = [feasm.Mesh(x.q, x.me) for x in small]
         self.bpat = [feasm.Pattern(x) for x in self.bmesh]
+        self.part = feasm.Mesh.part(m.q, m.me, 20, 90)
+        self.part_pat = feasm.Pattern(self.part, rows=(20, 90))
 
 
 def _scenarios(fx: _Fixtures) -> dict:
@@ -75,6 +77,9 @@ def _scenarios(fx: _Fixtures) -> dict:
         "p2_gather": lambda: feasm.p2_assemble(fx.mesh, fx.p2, feasm.P2_STIFF, variant=feasm.GATHER),
         "host_call": lambda: feasm.assemble_host("stiff_wmass", m.q, m.me, fx.w.cpu().numpy(), variant=feasm.ROW),
         "batch": batch,
+        "mesh_part": lambda: feasm.Mesh.part(m.q, m.me, 20, 90),
+        "pattern_part": lambda: feasm.Pattern(fx.part, rows=(30, 80)),
+        "assemble_part": lambda: feasm.assemble_stiff_wmass(fx.part, fx.part_pat, fx.w, feasm.ROW),
     }
 
 
@@ -111,10 +116,10 @@ def _fx() -> _Fixtures:
 
 NAMES = ["mesh", "pattern", "pattern_gather", "pattern_dofs2", "assemble_row", "assemble_atomic", "assemble_gather",
          "elasticity", "adjoint_gather", "adjoint_atomic", "drop_zeros", "tet_mesh", "tet_pattern", "tet_gather",
-         "p2_pattern", "p2_gather", "host_call", "batch"]
+         "p2_pattern", "p2_gather", "host_call", "batch", "mesh_part", "pattern_part", "assemble_part"]
 # calls that certainly allocate device memory (assembly calls may work in the pattern's buffers)
 ALLOCATING = {"mesh", "pattern", "pattern_gather", "pattern_dofs2", "drop_zeros", "tet_mesh", "tet_pattern",
-              "p2_pattern", "host_call", "batch"}
+              "p2_pattern", "host_call", "batch", "mesh_part", "pattern_part"}
 
 
 @pytest.mark.parametrize("name", NAMES)
