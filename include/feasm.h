@@ -449,6 +449,15 @@ fe_status fe_measure_fp64_rate(double* instr_per_s, fe_stream stream);
  * library's device memory pool (the memory that meshes, patterns, batches and running calls
  * hold), so that a test can check that a failed call left nothing behind. */
 void fe_debug_fail_alloc(int64_t n);
+
+/* Bounds-checked builds. A library compiled with -DFEASM_BOUNDS_CHECK checks every index it
+ * derives itself (element-to-nnz map entries, permutation and incidence entries, fan records,
+ * bucket slots, in-row column positions) against the array it addresses, counts the ones out of
+ * range and redirects those accesses to element 0 instead of trapping. *checked is 1 in such a
+ * build (0 otherwise); *violations is the count since the last reset (always 0 in an ordinary
+ * build); reset != 0 clears it. Synchronises the device. Not in the paper (a testing aid, in place
+ * of a memory checker). */
+fe_status fe_debug_bounds(int32_t* checked, int64_t* violations, int32_t reset);
 fe_status fe_debug_pool_used(int64_t* bytes);
 
 /* ---------------------------------------------------------------------------- status ---- */

@@ -35,7 +35,17 @@ def _newest_header() -> float:
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-def build(verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(verbose: bool = False, extra: list[str] | None = None, checked: bool = False) -> str:
+    """Builds libfeasm.so; checked=True builds libfeasm_checked.so instead, with -DFEASM_BOUNDS_CHECK
+    (every derived index range-checked and counted, see fe_debug_bounds), in its own object folder."""
+    global OBJ, LIB
+    if checked:
+        obj0, lib0 = OBJ, LIB
+        OBJ, LIB = os.path.join(HERE, "_build_checked"), os.path.join(HERE, "libfeasm_checked.so")
+        try:
+            return build(verbose, (extra or []) + ["-DFEASM_BOUNDS_CHECK"])
+        finally:
+            OBJ, LIB = obj0, lib0
     os.makedirs(OBJ, exist_ok=True)
     nvcc = _nvcc()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))

@@ -20,7 +20,9 @@
 // output. The 18 upstream values of a triangle enter linearly, so they are split with a common
 // power-of-two scale (magnitude about 1) and the outputs are scaled back exactly.
 struct AdjConsts {
-    ff c60;    // 1/60
+    ff c60;        // 1/60
+    int64_t nnz;   // stored entries of the upstream arrays (bounds-checked builds)
+    int64_t n3;    // incidences, 3 nme (bounds-checked builds)
 };
 
 template <bool WS, bool WM>
@@ -43,8 +45,8 @@ __device__ __forceinline__ void elem_adjoint(const double2* __restrict__ q, cons
     unsigned emax = 0;
 #pragma unroll
     for (int t = 0; t < 9; t++) {
-        if (WS) { gsr[t] = gS[mk[t]]; emax = max(emax, fp64_biased_exponent(gsr[t])); }
-        if (WM) { gmr[t] = gM[mk[t]]; emax = max(emax, fp64_biased_exponent(gmr[t])); }
+        if (WS) { gsr[t] = gS[FE_IDX(mk[t], cs.nnz)]; emax = max(emax, fp64_biased_exponent(gsr[t])); }
+        if (WM) { gmr[t] = gM[FE_IDX(mk[t], cs.nnz)]; emax = max(emax, fp64_biased_exponent(gmr[t])); }
     }
     const int k = ff_group_scale(emax);
     ff dA = z_ff();                                             // dL/dA (scaled)
@@ -152,7 +154,7 @@ __global__ void k_adjoint_stage(const double2* __restrict__ q, const int32_t* __
 
 __global__ void k_adjoint_gather(const int32_t* __restrict__ vptr, const int32_t* __restrict__ vel, int32_t nq,
                                  const double* __restrict__ stage, bool want_w, double* __restrict__ dq,
-                                 double* __restrict__ dw) {
+                                 double* __restrict__ dw, int64_t n3) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
         double sx = 0.0, sy = 0.0, sw = 0.0;
         const int32_t s0 = vptr[i], s1 = vptr[i + 1];
@@ -162,7 +164,7 @@ __global__ void k_adjoint_gather(const int32_t* __restrict__ vptr, const int32_t
             int32_t e[4];
             double vx[4], vy[4], vw[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) e[u] = b + u < s1 ? vel[b + u] : 0;
+            for (int u = 0; u < 4; u++) e[u] = b + u < s1 ? FE_IDX(vel[FE_IDX(b + u, n3)], n3) : 0;
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const int32_t k = e[u] / 3, a = e[u] - 3 * k;
@@ -208,6 +210,8 @@ extern "C" fe_status fe_adjoint_stiff_wmass(fe_mesh m, fe_pattern p, const doubl
         cs.c60.h = (float)c;
         cs.c60.l = (float)(c - (double)cs.c60.h);
     }
+    cs.nnz = p->nnz;
+    cs.n3 = 3 * (int64_t)nme;
     if (variant == FE_VARIANT_ATOMIC || nme == 0) {
         FE_CUDA(cudaMemsetAsync(dq, 0, 2 * sizeof(double) * nq, s));
         FE_CUDA(cudaMemsetAsync(dw, 0, sizeof(double) * nq, s));
@@ -236,7 +240,7 @@ extern "C" fe_status fe_adjoint_stiff_wmass(fe_mesh m, fe_pattern p, const doubl
         else k_adjoint_stage<false, true><<<g, 256, 0, s>>>(m->q, m->me, nme, p->map, w, gS, gM, cs, p->kg, m->err);
     }
     FE_LAUNCHED("k_adjoint_stage");
-    { FE_PROF("k_adjoint_gather", s); k_adjoint_gather<<<fe_grid(nq, 256), 256, 0, s>>>(p->vptr, p->vel, nq, p->kg, gM != nullptr, dq, dw); }
+    { FE_PROF("k_adjoint_gather", s); k_adjoint_gather<<<fe_grid(nq, 256), 256, 0, s>>>(p->vptr, p->vel, nq, p->kg, gM != nullptr, dq, dw, 3 * (int64_t)nme); }
     FE_LAUNCHED("k_adjoint_gather");
     return FE_OK;
 }

@@ -93,7 +93,8 @@ __device__ __forceinline__ void flag_orientation(double D, int* err) {
 template <int KIND>
 __global__ void k_scalar_atomic(const double2* __restrict__ q, const int32_t* __restrict__ me, int32_t nme,
                                 const int32_t* __restrict__ map, const double* __restrict__ w,
-                                double* __restrict__ out0, double* __restrict__ out1, int* __restrict__ err) {
+                                double* __restrict__ out0, double* __restrict__ out1, int* __restrict__ err,
+                                int64_t nnz) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
         int32_t v0 = me[k], v1 = me[nme + k], v2 = me[2 * (int64_t)nme + k];
         Geo g = geometry(q, v0, v1, v2);
@@ -108,7 +109,7 @@ __global__ void k_scalar_atomic(const double2* __restrict__ q, const int32_t* __
         for (int b = 0; b < 3; b++)
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                int32_t p = mk[3 * b + a];
+                int32_t p = FE_IDX(mk[3 * b + a], nnz);
                 atomicAdd(&out0[p], E[3 * a + b]);
                 if (KIND == K_STIFF_WMASS) atomicAdd(&out1[p], F[3 * a + b]);
             }
@@ -158,7 +159,7 @@ __global__ void k_scalar_stage(const double2* __restrict__ q, const int32_t* __r
 template <bool TWO>
 __global__ void k_seg_gather(const int32_t* __restrict__ seg_ptr, const int32_t* __restrict__ perm, int64_t nnz,
                              const double* __restrict__ kg0, const double* __restrict__ kg1,
-                             double* __restrict__ out0, double* __restrict__ out1) {
+                             double* __restrict__ out0, double* __restrict__ out1, int64_t nkg) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t s0 = seg_ptr[p], s1 = seg_ptr[p + 1];
         double a0 = 0.0, a1 = 0.0;
@@ -169,7 +170,7 @@ __global__ void k_seg_gather(const int32_t* __restrict__ seg_ptr, const int32_t*
             int32_t c[4];
             double v0[4], v1[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) c[u] = b + u < s1 ? perm[b + u] : 0;
+            for (int u = 0; u < 4; u++) c[u] = b + u < s1 ? FE_IDX(perm[FE_IDX(b + u, nkg)], nkg) : 0;
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 v0[u] = b + u < s1 ? kg0[c[u]] : 0.0;
@@ -198,7 +199,7 @@ __device__ __forceinline__ int32_t pos2(int32_t p, int32_t rb, int32_t g, int al
 
 __global__ void k_elas_atomic(const double2* __restrict__ q, const int32_t* __restrict__ me, int32_t nme,
                               const int32_t* __restrict__ map, const int32_t* __restrict__ row_ptr,
-                              double lam, double mu, double* __restrict__ out, int* __restrict__ err) {
+                              double lam, double mu, double* __restrict__ out, int* __restrict__ err, int64_t nnz4) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
         int32_t v[3] = {me[k], me[nme + k], me[2 * (int64_t)nme + k]};
         Geo g = geometry(q, v[0], v[1], v[2]);
@@ -218,7 +219,7 @@ __global__ void k_elas_atomic(const double2* __restrict__ q, const int32_t* __re
                 for (int al = 0; al < 2; al++)
 #pragma unroll
                     for (int be = 0; be < 2; be++)
-                        atomicAdd(&out[pos2(p, rb[a], dg[a], al, be)], K[6 * (2 * a + al) + 2 * b + be]);
+                        atomicAdd(&out[FE_IDX(pos2(p, rb[a], dg[a], al, be), nnz4)], K[6 * (2 * a + al) + 2 * b + be]);
             }
     }
 }
@@ -251,14 +252,15 @@ __global__ void k_elas_stage(const double2* __restrict__ q, const int32_t* __res
 // One thread per scalar row i: for each scalar non-zero (i, j) and each of its contributions
 // c = 9k + 3b + a (ascending), add the 2x2 block K^e[2a+alpha][2b+beta] of triangle k.
 __global__ void k_elas_gather(const int32_t* __restrict__ row_ptr, int32_t nq, const int32_t* __restrict__ seg_ptr,
-                              const int32_t* __restrict__ perm, const double* __restrict__ kg, double* __restrict__ out) {
+                              const int32_t* __restrict__ perm, const double* __restrict__ kg, double* __restrict__ out,
+                              int64_t ncontrib) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
         int32_t rb = row_ptr[r], g = row_ptr[r + 1] - rb;
         for (int32_t t = 0; t < g; t++) {
             int32_t p = rb + t;
             double acc[2][2];
             for (int32_t s = seg_ptr[p]; s < seg_ptr[p + 1]; s++) {
-                int32_t c = perm[s];
+                int32_t c = FE_IDX(perm[FE_IDX(s, ncontrib)], ncontrib);
                 int32_t k = c / 9;
                 int32_t rr = c - 9 * k;
                 int b = rr / 3, a = rr - 3 * b;
@@ -320,10 +322,10 @@ static fe_status scalar(int kind, fe_mesh m, fe_pattern p, const double* w, int 
         if (nme == 0) return FE_OK;
         unsigned grid = fe_grid(nme, 256);
         switch (kind) {
-            case K_MASS: { FE_PROF("k_scalar_atomic", s); k_scalar_atomic<K_MASS><<<grid, 256, 0, s>>>(m->q, m->me, nme, p->map, w, out0, out1, m->err); } break;
-            case K_WMASS: { FE_PROF("k_scalar_atomic", s); k_scalar_atomic<K_WMASS><<<grid, 256, 0, s>>>(m->q, m->me, nme, p->map, w, out0, out1, m->err); } break;
-            case K_STIFF: { FE_PROF("k_scalar_atomic", s); k_scalar_atomic<K_STIFF><<<grid, 256, 0, s>>>(m->q, m->me, nme, p->map, w, out0, out1, m->err); } break;
-            default: { FE_PROF("k_scalar_atomic", s); k_scalar_atomic<K_STIFF_WMASS><<<grid, 256, 0, s>>>(m->q, m->me, nme, p->map, w, out0, out1, m->err); } break;
+            case K_MASS: { FE_PROF("k_scalar_atomic", s); k_scalar_atomic<K_MASS><<<grid, 256, 0, s>>>(m->q, m->me, nme, p->map, w, out0, out1, m->err, p->nnz); } break;
+            case K_WMASS: { FE_PROF("k_scalar_atomic", s); k_scalar_atomic<K_WMASS><<<grid, 256, 0, s>>>(m->q, m->me, nme, p->map, w, out0, out1, m->err, p->nnz); } break;
+            case K_STIFF: { FE_PROF("k_scalar_atomic", s); k_scalar_atomic<K_STIFF><<<grid, 256, 0, s>>>(m->q, m->me, nme, p->map, w, out0, out1, m->err, p->nnz); } break;
+            default: { FE_PROF("k_scalar_atomic", s); k_scalar_atomic<K_STIFF_WMASS><<<grid, 256, 0, s>>>(m->q, m->me, nme, p->map, w, out0, out1, m->err, p->nnz); } break;
         }
         FE_LAUNCHED("k_scalar_atomic");
         return FE_OK;
@@ -340,9 +342,9 @@ static fe_status scalar(int kind, fe_mesh m, fe_pattern p, const double* w, int 
     }
     FE_LAUNCHED("k_scalar_stage");
     if (kind == K_STIFF_WMASS)
-        { FE_PROF("k_seg_gather", s); k_seg_gather<true><<<fe_grid(p->nnz, 256), 256, 0, s>>>(p->seg_ptr, p->perm, p->nnz, kg0, kg1, out0, out1); }
+        { FE_PROF("k_seg_gather", s); k_seg_gather<true><<<fe_grid(p->nnz, 256), 256, 0, s>>>(p->seg_ptr, p->perm, p->nnz, kg0, kg1, out0, out1, 9 * (int64_t)nme); }
     else
-        { FE_PROF("k_seg_gather", s); k_seg_gather<false><<<fe_grid(p->nnz, 256), 256, 0, s>>>(p->seg_ptr, p->perm, p->nnz, kg0, nullptr, out0, nullptr); }
+        { FE_PROF("k_seg_gather", s); k_seg_gather<false><<<fe_grid(p->nnz, 256), 256, 0, s>>>(p->seg_ptr, p->perm, p->nnz, kg0, nullptr, out0, nullptr, 9 * (int64_t)nme); }
     FE_LAUNCHED("k_seg_gather");
     return FE_OK;
 }
@@ -384,14 +386,14 @@ extern "C" fe_status fe_assemble_elas(fe_mesh m, fe_pattern p, double lam, doubl
     if (variant == FE_VARIANT_ATOMIC) {
         if (p->nnz > 0) FE_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * p->nnz, s));
         if (nme == 0) return FE_OK;
-        { FE_PROF("k_elas_atomic", s); k_elas_atomic<<<fe_grid(nme, 256), 256, 0, s>>>(m->q, m->me, nme, p->map, p->row_ptr, lam, mu, values, m->err); }
+        { FE_PROF("k_elas_atomic", s); k_elas_atomic<<<fe_grid(nme, 256), 256, 0, s>>>(m->q, m->me, nme, p->map, p->row_ptr, lam, mu, values, m->err, p->nnz); }
         FE_LAUNCHED("k_elas_atomic");
         return FE_OK;
     }
     if (nme == 0) return FE_OK;
     { FE_PROF("k_elas_stage", s); k_elas_stage<<<fe_grid(nme, ELAS_STAGE_BLOCK), ELAS_STAGE_BLOCK, 0, s>>>(m->q, m->me, nme, lam, mu, p->kg, m->err); }
     FE_LAUNCHED("k_elas_stage");
-    { FE_PROF("k_elas_gather", s); k_elas_gather<<<fe_grid(m->nq, 128), 128, 0, s>>>(p->row_ptr, m->nq, p->seg_ptr, p->perm, p->kg, values); }
+    { FE_PROF("k_elas_gather", s); k_elas_gather<<<fe_grid(m->nq, 128), 128, 0, s>>>(p->row_ptr, m->nq, p->seg_ptr, p->perm, p->kg, values, 9 * (int64_t)nme); }
     FE_LAUNCHED("k_elas_gather");
     return FE_OK;
 }
@@ -457,7 +459,7 @@ extern "C" fe_status fe_assemble_stiff_wmass_noalloc(fe_mesh m, fe_pattern p, co
     double* kg1 = scratch + 9 * (size_t)nme;
     { FE_PROF("k_scalar_stage", s); k_scalar_stage<K_STIFF_WMASS><<<fe_grid(nme, STAGE_BLOCK), STAGE_BLOCK, 0, s>>>(m->q, m->me, nme, w, kg0, kg1, m->err); }
     FE_LAUNCHED("k_scalar_stage (no-alloc)");
-    { FE_PROF("k_seg_gather", s); k_seg_gather<true><<<fe_grid(p->nnz, 256), 256, 0, s>>>(p->seg_ptr, p->perm, p->nnz, kg0, kg1, S, Mw); }
+    { FE_PROF("k_seg_gather", s); k_seg_gather<true><<<fe_grid(p->nnz, 256), 256, 0, s>>>(p->seg_ptr, p->perm, p->nnz, kg0, kg1, S, Mw, 9 * (int64_t)nme); }
     FE_LAUNCHED("k_seg_gather (no-alloc)");
     return FE_OK;
 }

@@ -69,7 +69,7 @@ __global__ void k_batch_zero(const MeshDesc* __restrict__ desc, int32_t n, doubl
 
 __device__ __forceinline__ void tri_stiff_mass(const double2* __restrict__ q, const int32_t* __restrict__ me,
                                                int32_t nme, int32_t k, const int32_t* __restrict__ mk,
-                                               double* __restrict__ S, double* __restrict__ M) {
+                                               double* __restrict__ S, double* __restrict__ M, int32_t nnz) {
     int32_t v0 = me[k], v1 = me[nme + k], v2 = me[2 * nme + k];
     double2 p0 = q[v0], p1 = q[v1], p2 = q[v2];
     double ex[3] = {p1.x - p2.x, p2.x - p0.x, p0.x - p1.x};
@@ -81,7 +81,7 @@ __device__ __forceinline__ void tri_stiff_mass(const double2* __restrict__ q, co
     for (int b = 0; b < 3; b++)
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            int32_t p = mk[3 * b + a];
+            int32_t p = FE_IDX(mk[3 * b + a], nnz);
             atomicAdd(&S[p], (ex[a] * ex[b] + ey[a] * ey[b]) * inv);
             atomicAdd(&M[p], a == b ? dia : off);
         }
@@ -95,14 +95,14 @@ __global__ void k_batch_asm(const MeshDesc* __restrict__ desc, const Tile* __res
         double* s = S[tl.mesh];
         double* mm = M[tl.mesh];
         for (int32_t k = tl.k0 + threadIdx.x; k < tl.k1; k += blockDim.x)
-            tri_stiff_mass(d.q, d.me, d.nme, k, d.map + 9 * (int64_t)k, s, mm);
+            tri_stiff_mass(d.q, d.me, d.nme, k, d.map + 9 * (int64_t)k, s, mm, d.nnz);
     }
 }
 
 // Plain form: one kernel per mesh.
 __global__ void k_mesh_asm(MeshDesc d, double* __restrict__ S, double* __restrict__ M) {
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < d.nme; k += gridDim.x * blockDim.x)
-        tri_stiff_mass(d.q, d.me, d.nme, k, d.map + 9 * (int64_t)k, S, M);
+        tri_stiff_mass(d.q, d.me, d.nme, k, d.map + 9 * (int64_t)k, S, M, d.nnz);
 }
 
 static void drop_graph(fe_batch b) {
@@ -215,7 +215,8 @@ extern "C" fe_status fe_batch_create(int32_t n, const fe_mesh* meshes, const fe_
         b->patterns.push_back(p);
         b->has_map = b->has_map && p->map != nullptr;
         desc[m] = {me->q, me->me, p->map, me->nme, (int32_t)p->nnz};
-        rdesc[m] = {p->row_ptr, p->col_idx, p->vptr, p->fan, p->hdr, me->q, me->err, me->nq};
+        rdesc[m] = {p->row_ptr, p->col_idx, p->vptr, p->fan, p->hdr, me->q, me->err, me->nq, 3 * (int64_t)me->nme,
+                    p->nnz_scalar};
         if (p->n_gen > 0) {
             std::vector<int32_t> rows(p->n_gen);
             cudaError_t e = cudaMemcpy(rows.data(), p->gen_rows, sizeof(int32_t) * p->n_gen, cudaMemcpyDeviceToHost);

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 
 #include "../../include/feasm.h"
 
@@ -151,6 +152,7 @@ struct fe_row_mesh {
     const double2* q;
     int* err;
     int32_t nq;
+    int64_t n_inc, nnz;      // fan records (3 nme) and stored entries (bounds-checked builds)
 };
 struct fe_row_tile {
     int32_t mesh, r0, r1;
@@ -199,6 +201,44 @@ inline fe_status fe_alloc_n(T** p, size_t n, const char* what) {
     return fe_alloc(reinterpret_cast<void**>(p), n * sizeof(T) + (n == 0 ? sizeof(T) : 0), what);
 }
 void fe_free(void* p);
+
+// ------------------------------------------------------------------------ bounds-checked builds
+//
+// Built with -DFEASM_BOUNDS_CHECK, FE_IDX(i, n) checks an index that the library derived itself
+// (an element-to-nnz map entry, a permutation entry, a fan record, a bucket or incidence slot, an
+// in-row column position) against the size n of the array it addresses. An index outside [0, n)
+// is counted in this source file's device counter and replaced by 0, so the access stays inside
+// the array and nothing traps; fe_debug_bounds reads and clears the counters of all files. In
+// the ordinary build FE_IDX(i, n) is i and n is not evaluated.
+#ifdef FEASM_BOUNDS_CHECK
+void fe_oob_register(unsigned long long (*reader)(int reset));
+namespace {
+__device__ unsigned long long fe_oob_count = 0;
+__device__ __forceinline__ int64_t fe_idx_check(int64_t i, int64_t n) {
+    if (i < 0 || i >= n) {
+        atomicAdd(&fe_oob_count, 1ull);
+        return 0;
+    }
+    return i;
+}
+unsigned long long fe_oob_read(int reset) {
+    unsigned long long h = 0;
+    cudaMemcpyFromSymbol(&h, fe_oob_count, sizeof h);
+    if (reset) {
+        const unsigned long long z = 0;
+        cudaMemcpyToSymbol(fe_oob_count, &z, sizeof z);
+    }
+    return h;
+}
+struct FeOobRegistrar {
+    FeOobRegistrar() { fe_oob_register(&fe_oob_read); }
+};
+FeOobRegistrar fe_oob_registrar;
+}  // namespace
+#define FE_IDX(i, n) ((std::decay<decltype(i)>::type)fe_idx_check((int64_t)(i), (int64_t)(n)))
+#else
+#define FE_IDX(i, n) (i)
+#endif
 
 // ------------------------------------------------------------------------ launch shapes
 

@@ -104,7 +104,7 @@ __global__ void k_p2_fill(const int32_t* __restrict__ edof, int32_t nme, int32_t
                           int32_t* __restrict__ inc) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int a = 0; a < 6; a++) inc[atomicAdd(&cur[edof[6 * k + a]], 1)] = 6 * (int32_t)k + a;
+        for (int a = 0; a < 6; a++) inc[FE_IDX(atomicAdd(&cur[edof[6 * k + a]], 1), 6 * (int64_t)nme)] = 6 * (int32_t)k + a;
     }
 }
 
@@ -367,7 +367,7 @@ __device__ __forceinline__ void p2_elem(double2 p0, double2 p1, double2 p2, doub
 
 template <int KIND>
 __global__ void __launch_bounds__(P2_BLOCK) k_p2_atomic(const int32_t* __restrict__ me, int32_t nme, const double2* __restrict__ q,
-                                                        const int32_t* __restrict__ map, double* __restrict__ val) {
+                                                        const int32_t* __restrict__ map, double* __restrict__ val, int64_t nnz) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
         double E[6][6];
         p2_elem<KIND>(q[me[k]], q[me[nme + k]], q[me[2 * (int64_t)nme + k]], E);
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(P2_BLOCK) k_p2_atomic(const int32_t* __restric
 #pragma unroll
         for (int il = 0; il < 6; il++)
 #pragma unroll
-            for (int jl = 0; jl < 6; jl++) atomicAdd(&val[mk[6 * il + jl]], E[il][jl]);
+            for (int jl = 0; jl < 6; jl++) atomicAdd(&val[FE_IDX(mk[6 * il + jl], nnz)], E[il][jl]);
     }
 }
 
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(STAGE_BLOCK) k_p2_stage(const int32_t* __restr
 template <int RMAX>
 __global__ void __launch_bounds__(RS_BLOCK) k_p2_rowsum(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
                                                         int32_t r0, int32_t r1, const int4* __restrict__ rrec,
-                                                        const double* __restrict__ kg, double* __restrict__ val) {
+                                                        const double* __restrict__ kg, double* __restrict__ val, int64_t n6) {
     __shared__ double acc[RMAX * RS_BLOCK];
     double* a = acc + threadIdx.x;                       // column c of this thread's row at a[c * RS_BLOCK]
     for (int64_t rr = r0 + blockIdx.x * (int64_t)RS_BLOCK + threadIdx.x; rr < r1; rr += (int64_t)gridDim.x * RS_BLOCK) {
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(RS_BLOCK) k_p2_rowsum(const int32_t* __restric
         for (int c = 0; c < u; c++) a[c * RS_BLOCK] = -0.0;
         int4 rec = d > 0 ? rrec[b0] : make_int4(0, 0, 0, 0);
         for (int32_t t = 0; t < d; t++) {
-            const double2* e = reinterpret_cast<const double2*>(kg + 6 * (int64_t)rec.x);     // 36k + 6a
+            const double2* e = reinterpret_cast<const double2*>(kg + 6 * (int64_t)FE_IDX(rec.x, n6));   // 36k + 6a
             double2 v[3];
 #pragma unroll
             for (int j = 0; j < 3; j++) v[j] = e[j];
@@ -442,8 +442,8 @@ __global__ void __launch_bounds__(RS_BLOCK) k_p2_rowsum(const int32_t* __restric
             double y[6];
 #pragma unroll
             for (int j = 0; j < 3; j++) {
-                pc[2 * j] = a + (sl[j] & 0xFFFFu) * RS_BLOCK;
-                pc[2 * j + 1] = a + (sl[j] >> 16) * RS_BLOCK;
+                pc[2 * j] = a + FE_IDX(sl[j] & 0xFFFFu, u) * RS_BLOCK;
+                pc[2 * j + 1] = a + FE_IDX(sl[j] >> 16, u) * RS_BLOCK;
             }
 #pragma unroll
             for (int j = 0; j < 6; j++) y[j] = *pc[j];
@@ -725,10 +725,10 @@ extern "C" fe_status fe_p2_assemble(fe_mesh m, fe_p2_pattern p, int kind, int va
             FE_PROF("k_p2_rowsum (vertex rows)", s);
             if (!p->n_long_host[1])
                 k_p2_rowsum<RS_VERTEX_SHORT><<<fe_grid(nq, RS_BLOCK, 8), RS_BLOCK, 0, s>>>(p->vptr, p->row_ptr, 0, nq, p->rrec,
-                                                                                         p->kg, values);
+                                                                                         p->kg, values, 6 * (int64_t)nme);
             else
                 k_p2_rowsum<RS_VERTEX><<<fe_grid(nq, RS_BLOCK, 8), RS_BLOCK, 0, s>>>(p->vptr, p->row_ptr, 0, nq, p->rrec, p->kg,
-                                                                                   values);
+                                                                                   values, 6 * (int64_t)nme);
             FE_LAUNCHED("k_p2_rowsum (vertex rows)");
         }
         if (ndof > nq) {
@@ -748,8 +748,8 @@ extern "C" fe_status fe_p2_assemble(fe_mesh m, fe_p2_pattern p, int kind, int va
     if (nme > 0) {
         FE_PROF("k_p2_atomic", s);
         const unsigned g = fe_grid(nme, P2_BLOCK, 8);
-        if (kind == FE_P2_MASS) k_p2_atomic<FE_P2_MASS><<<g, P2_BLOCK, 0, s>>>(m->me, nme, m->q, p->map, values);
-        else k_p2_atomic<FE_P2_STIFF><<<g, P2_BLOCK, 0, s>>>(m->me, nme, m->q, p->map, values);
+        if (kind == FE_P2_MASS) k_p2_atomic<FE_P2_MASS><<<g, P2_BLOCK, 0, s>>>(m->me, nme, m->q, p->map, values, p->nnz);
+        else k_p2_atomic<FE_P2_STIFF><<<g, P2_BLOCK, 0, s>>>(m->me, nme, m->q, p->map, values, p->nnz);
     }
     FE_LAUNCHED("k_p2_atomic");
     return FE_OK;

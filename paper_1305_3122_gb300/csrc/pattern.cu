@@ -43,7 +43,7 @@ __global__ void k_fill_adj(const int32_t* __restrict__ me, int32_t nme, int32_t*
         int32_t v[3] = {me[k], me[nme + k], me[2 * (int64_t)nme + k]};
         int32_t slot[3];
 #pragma unroll
-        for (int a = 0; a < 3; a++) slot[a] = atomicAdd(&cur[v[a]], 1);
+        for (int a = 0; a < 3; a++) slot[a] = FE_IDX(atomicAdd(&cur[v[a]], 1), 3 * (int64_t)nme);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             adj[slot[a]] = make_int2(v[(a + 1) % 3], v[(a + 2) % 3]);
@@ -314,6 +314,7 @@ __global__ void __launch_bounds__(CF_BLOCK) k_col_fill(const int32_t* __restrict
         const int32_t hi = __shfl_sync(0xffffffffu, e, last);
         const bool staged = active && !any_general && hi - lo <= CF_STAGE;   // warp-uniform
         auto put = [&](int32_t at, int32_t v) {
+            at = o + FE_IDX(at - o, e - o);                  // a column position inside its row
             if (staged) st[at - lo] = v;
             else col_idx[at] = v;
         };
@@ -428,7 +429,7 @@ __device__ __forceinline__ void contrib_key(int32_t i, int2 p, int32_t e, long l
 __global__ void k_row_perm(const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase, const int2* __restrict__ adj,
                            int32_t* __restrict__ vel,
                            int32_t nq, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ seg_ptr,
-                           int32_t* __restrict__ perm) {
+                           int32_t* __restrict__ perm, int64_t n9) {
     long long keys[3 * FAST_DEG];
     int32_t ev[FAST_DEG];
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
@@ -442,12 +443,12 @@ __global__ void k_row_perm(const int32_t* __restrict__ vptr, const int32_t* __re
             n += 3;
         }
         isort64(keys, n);
-        int32_t o = row_ptr[i];
+        int32_t o = row_ptr[i], u = row_ptr[i + 1] - o;
         int32_t cbase = 3 * beg;   // this row's contributions occupy perm[3*vptr[i] .. 3*vptr[i+1])
         int t = 0;
         for (int s = 0; s < n; s++) {
-            if (s == 0 || (keys[s] >> 32) != (keys[s - 1] >> 32)) seg_ptr[o + t++] = cbase + s;
-            perm[cbase + s] = (int32_t)(keys[s] & 0xffffffffLL);
+            if (s == 0 || (keys[s] >> 32) != (keys[s - 1] >> 32)) seg_ptr[o + FE_IDX(t++, u)] = cbase + s;
+            perm[FE_IDX(cbase + s, n9)] = FE_IDX((int32_t)(keys[s] & 0xffffffffLL), n9);
         }
         isort32(ev, d);
         for (int32_t s = 0; s < d; s++) vel[beg + s] = ev[s];
@@ -665,7 +666,7 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
                                                                                                        p->gen_rows, t.counters + 1); }
             FE_LAUNCHED("k_row_big_pairs");
             if (gather) {
-                { FE_PROF("k_row_perm", s); k_row_perm<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, p->vptr, t.adj, p->vel, nq, p->row_ptr, p->seg_ptr, p->perm); }
+                { FE_PROF("k_row_perm", s); k_row_perm<<<fe_grid(nq, 128), 128, 0, s>>>(p->vptr, p->vptr, t.adj, p->vel, nq, p->row_ptr, p->seg_ptr, p->perm, 9 * (int64_t)nme); }
                 FE_LAUNCHED("k_row_perm");
                 size_t sm = 3 * (size_t)FE_MAX_VALENCE * (sizeof(long long) + sizeof(int32_t) + 1) +
                             (size_t)FE_MAX_VALENCE * sizeof(int32_t);

@@ -278,6 +278,20 @@ __device__ __noinline__ void fan_terms_fp64(const double2* __restrict__ q, int32
 // FP64 value of a row entry.
 __device__ __forceinline__ void put(double* __restrict__ out, int32_t at, ff v) { out[at] = ff_to_double(v); }
 
+// Sizes the bounds-checked build checks derived indices against: vertices, fan records (3 nme),
+// stored entries of the output.
+struct Lim {
+    int32_t nq;
+    int64_t n_inc, nnz;
+};
+
+// A fan record (neighbour id, column position) at index t of the fan records.
+__device__ __forceinline__ int2 fan_rec(const int2* __restrict__ fan, int64_t t, const Lim& lim) {
+    int2 r = fan[FE_IDX(t, lim.n_inc)];
+    r.x = FE_IDX(r.x, lim.nq);
+    return r;
+}
+
 }  // namespace
 
 // One simple row of the scalar kinds (S, M^w, M, or two of them): see the header of this section.
@@ -287,7 +301,8 @@ template <int KIND>
 __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ vptr,
                                         const int2* __restrict__ fan, const int2* __restrict__ hdr,
                                         const double2* __restrict__ q, const VRec* __restrict__ vr, const Consts& cs,
-                                        double* __restrict__ out0, double* __restrict__ out1, int& bad, int& orient) {
+                                        double* __restrict__ out0, double* __restrict__ out1, int& bad, int& orient,
+                                        const Lim& lim) {
     constexpr bool DS = (KIND & W_S) != 0, DW = (KIND & W_W) != 0, DM = (KIND & W_M) != 0;
     double* __restrict__ outX = DS ? out1 : out0;            // M^w or M
     int2 h = hdr[i];
@@ -297,8 +312,8 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
     int pself = h.y & 0x3FFF;
     // neighbour k of the fan: k < d from the fan records; k == d is the last neighbour of an
     // open fan (from the header) or n_0 again for a closed fan
-    const int2 rec0 = fan[b0];
-    const int2 last = kind == 1 ? make_int2(h.x, (h.y >> 14) & 0x3FFF) : rec0;
+    const int2 rec0 = fan_rec(fan, b0, lim);
+    const int2 last = kind == 1 ? make_int2(FE_IDX(h.x, lim.nq), (h.y >> 14) & 0x3FFF) : rec0;
     FanRaw self = fan_load<KIND>(q, vr, make_int2(i, 0));
     double2 pi = self.p;
     ff wi2 = ff{FADD(self.w.h, self.w.h), FADD(self.w.l, self.w.l)};   // 2 w_i (M^w)
@@ -306,8 +321,8 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
     // gather never waits for its own record (N_k = fan[b0 + k] for k < d, N_d = last); loading
     // the data two ahead costs more in occupancy than it gains
     FanRaw rn = fan_load<KIND>(q, vr, rec0);
-    FanRaw rp = fan_load<KIND>(q, vr, d > 1 ? fan[b0 + 1] : last);
-    int2 recn = d > 2 ? fan[b0 + 2] : last;                  // N_2
+    FanRaw rp = fan_load<KIND>(q, vr, d > 1 ? fan_rec(fan, b0 + 1, lim) : last);
+    int2 recn = d > 2 ? fan_rec(fan, b0 + 2, lim) : last;    // N_2
     FanNb cur = fan_nb<KIND>(rn, pi, bad);
     const int first_pos = cur.pos;
     const ff first_u = DW ? fan_u(wi2, cur) : z_ff();
@@ -318,7 +333,7 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
         rn = rp;                                             // neighbour e + 1 (already loaded)
         if (e + 2 <= d) {
             rp = fan_load<KIND>(q, vr, recn);                // N_{e+2}
-            recn = e + 3 < d ? fan[b0 + e + 3] : last;       // N_{e+3}
+            recn = e + 3 < d ? fan_rec(fan, b0 + e + 3, lim) : last;   // N_{e+3}
         }
         FanNb nxt = fan_nb<KIND>(rn, pi, bad);
         ff D = ff_dot2(cur.x, nxt.x, nxt.y, ff_neg(cur.y));          // r_c x r_n
@@ -352,10 +367,10 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
             if (DS) {
                 ff v = ff_add(caS, sc);
                 ff_acc(dgS, ff_neg(v));
-                put(out0, rb + cur.pos, v);
+                put(out0, FE_IDX(rb + cur.pos, lim.nnz), v);
             }
-            if (DW) put(outX, rb + cur.pos, ff_mul(ff_add(ff_add(ff_mul(sig, fan_u(wi2, cur)), Ap), B), cs.c120));
-            if (DM) put(outX, rb + cur.pos, ff_mul(sig, cs.c24));
+            if (DW) put(outX, FE_IDX(rb + cur.pos, lim.nnz), ff_mul(ff_add(ff_add(ff_mul(sig, fan_u(wi2, cur)), Ap), B), cs.c120));
+            if (DM) put(outX, FE_IDX(rb + cur.pos, lim.nnz), ff_mul(sig, cs.c24));
         }
         caS = sn;
         Dp = D;
@@ -366,29 +381,29 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
         if (DS) {
             ff v = ff_add(caS, fsS);
             ff_acc(dgS, ff_neg(v));
-            put(out0, rb + first_pos, v);
+            put(out0, FE_IDX(rb + first_pos, lim.nnz), v);
         }
-        if (DW) put(outX, rb + first_pos, ff_mul(ff_add(ff_add(ff_mul(Dp, first_u), Ap), fsM), cs.c120));
-        if (DM) put(outX, rb + first_pos, ff_mul(ff_add(Dp, fsD), cs.c24));
+        if (DW) put(outX, FE_IDX(rb + first_pos, lim.nnz), ff_mul(ff_add(ff_add(ff_mul(Dp, first_u), Ap), fsM), cs.c120));
+        if (DM) put(outX, FE_IDX(rb + first_pos, lim.nnz), ff_mul(ff_add(Dp, fsD), cs.c24));
     } else {                                                 // open: n_0 and n_d have one triangle each
         if (DS) {
             ff_acc(dgS, ff_neg(fsS));
             ff_acc(dgS, ff_neg(caS));
-            put(out0, rb + first_pos, fsS);
-            put(out0, rb + cur.pos, caS);
+            put(out0, FE_IDX(rb + first_pos, lim.nnz), fsS);
+            put(out0, FE_IDX(rb + cur.pos, lim.nnz), caS);
         }
         if (DW) {
-            put(outX, rb + first_pos, ff_mul(fsM, cs.c120));
-            put(outX, rb + cur.pos, ff_mul(ff_add(ff_mul(Dp, fan_u(wi2, cur)), Ap), cs.c120));
+            put(outX, FE_IDX(rb + first_pos, lim.nnz), ff_mul(fsM, cs.c120));
+            put(outX, FE_IDX(rb + cur.pos, lim.nnz), ff_mul(ff_add(ff_mul(Dp, fan_u(wi2, cur)), Ap), cs.c120));
         }
         if (DM) {
-            put(outX, rb + first_pos, ff_mul(fsD, cs.c24));
-            put(outX, rb + cur.pos, ff_mul(Dp, cs.c24));
+            put(outX, FE_IDX(rb + first_pos, lim.nnz), ff_mul(fsD, cs.c24));
+            put(outX, FE_IDX(rb + cur.pos, lim.nnz), ff_mul(Dp, cs.c24));
         }
     }
-    if (DS) put(out0, rb + pself, dgS);
-    if (DW) put(outX, rb + pself, ff_mul(ff_add(ff_mul(ff_mulf(wi2, 1.5f), sD), sAB), cs.c60));
-    if (DM) put(outX, rb + pself, ff_mul(sD, cs.c12));
+    if (DS) put(out0, FE_IDX(rb + pself, lim.nnz), dgS);
+    if (DW) put(outX, FE_IDX(rb + pself, lim.nnz), ff_mul(ff_add(ff_mul(ff_mulf(wi2, 1.5f), sD), sAB), cs.c60));
+    if (DM) put(outX, FE_IDX(rb + pself, lim.nnz), ff_mul(sD, cs.c12));
 }
 
 // Resident blocks of 128 threads per SM for each kind: as many as fit without register spills
@@ -403,10 +418,10 @@ __global__ void __launch_bounds__(128, FanOcc<KIND>::blocks) k_fan_scalar(const 
                                                        const int2* __restrict__ fan, const int2* __restrict__ hdr,
                                                        const double2* __restrict__ q, const VRec* __restrict__ vr, int32_t r0,
                                                        int32_t r1, Consts cs, double* __restrict__ out0, double* __restrict__ out1,
-                                                       int* __restrict__ err) {
+                                                       int* __restrict__ err, Lim lim) {
     int bad = 0, orient = 0;
     for (uint32_t r = r0 + blockIdx.x * blockDim.x + threadIdx.x; r < (uint32_t)r1; r += gridDim.x * blockDim.x)
-        fan_row<KIND>((int32_t)r, row_ptr, vptr, fan, hdr, q, vr, cs, out0, out1, bad, orient);
+        fan_row<KIND>((int32_t)r, row_ptr, vptr, fan, hdr, q, vr, cs, out0, out1, bad, orient, lim);
     if (bad) atomicOr(err, 2);
     if (orient) atomicOr(err, 1);
 }
@@ -488,7 +503,8 @@ __global__ void __launch_bounds__(256) k_batch_rows(const fe_row_mesh* __restric
         double* m = M[tl.mesh];
         int bad = 0, orient = 0;
         for (int32_t i = tl.r0 + threadIdx.x; i < tl.r1; i += blockDim.x)
-            fan_row<W_S | W_M>(i, d.row_ptr, d.vptr, d.fan, d.hdr, d.q, nullptr, cs, s, m, bad, orient);
+            fan_row<W_S | W_M>(i, d.row_ptr, d.vptr, d.fan, d.hdr, d.q, nullptr, cs, s, m, bad, orient,
+                               Lim{d.nq, d.n_inc, d.nnz});
         if (bad) atomicOr(d.err, 2);
         if (orient) atomicOr(d.err, 1);
     }
@@ -573,8 +589,9 @@ __device__ __forceinline__ Block2 badd(const Block2& a, const Block2& b) {
     return Block2{ff_add(a.k00, b.k00), ff_add(a.k01, b.k01), ff_add(a.k10, b.k10), ff_add(a.k11, b.k11)};
 }
 
-__device__ __forceinline__ void write_block(double* __restrict__ out, int32_t rb, int32_t u, int t, const Block2& k) {
-    int32_t o0 = 4 * rb + 2 * t, o1 = 4 * rb + 2 * u + 2 * t;
+__device__ __forceinline__ void write_block(double* __restrict__ out, int32_t rb, int32_t u, int t, const Block2& k,
+                                            int64_t nnz4 = INT64_MAX) {
+    int32_t o0 = FE_IDX(4 * rb + 2 * t, nnz4 - 1), o1 = FE_IDX(4 * rb + 2 * u + 2 * t, nnz4 - 1);
     out[o0] = ff_to_double(k.k00);
     out[o0 + 1] = ff_to_double(k.k01);
     out[o1] = ff_to_double(k.k10);
@@ -588,7 +605,7 @@ __device__ __forceinline__ Block2 bneg(const Block2& a) { return Block2{ff_neg(a
 __global__ void __launch_bounds__(256, 2) k_fan_elas(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ vptr,
                                                      const int2* __restrict__ fan, const int2* __restrict__ hdr,
                                                      const double2* __restrict__ q, int32_t nq, Consts cs,
-                                                     double* __restrict__ out, int* __restrict__ err) {
+                                                     double* __restrict__ out, int* __restrict__ err, Lim lim) {
     int bad = 0, orient = 0;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = (int32_t)r;
@@ -597,13 +614,13 @@ __global__ void __launch_bounds__(256, 2) k_fan_elas(const int32_t* __restrict__
         if (kind > 1) continue;
         int32_t rb = row_ptr[i], u = row_ptr[i + 1] - rb, b0 = vptr[i], d = vptr[i + 1] - b0;
         int pself = h.y & 0x3FFF;
-        const int2 rec0 = fan[b0];
-        const int2 last = kind == 1 ? make_int2(h.x, (h.y >> 14) & 0x3FFF) : rec0;
+        const int2 rec0 = fan_rec(fan, b0, lim);
+        const int2 last = kind == 1 ? make_int2(FE_IDX(h.x, lim.nq), (h.y >> 14) & 0x3FFF) : rec0;
         double2 pi = q[i];
         // neighbour data one triangle ahead of use, fan records two ahead (as in the scalar kernel)
         Raw rn = load_raw<0>(q, nullptr, rec0);
-        Raw rp = load_raw<0>(q, nullptr, d > 1 ? fan[b0 + 1] : last);
-        int2 recn = d > 2 ? fan[b0 + 2] : last;
+        Raw rp = load_raw<0>(q, nullptr, d > 1 ? fan_rec(fan, b0 + 1, lim) : last);
+        int2 recn = d > 2 ? fan_rec(fan, b0 + 2, lim) : last;
         Nb cur = make_nb<0>(rn, pi, bad);
         const int first_pos = cur.pos;
         const ff z = ff_make(0.f);
@@ -612,7 +629,7 @@ __global__ void __launch_bounds__(256, 2) k_fan_elas(const int32_t* __restrict__
             rn = rp;
             if (e + 2 <= d) {
                 rp = load_raw<0>(q, nullptr, recn);
-                recn = e + 3 < d ? fan[b0 + e + 3] : last;
+                recn = e + 3 < d ? fan_rec(fan, b0 + e + 3, lim) : last;
             }
             Nb nxt = make_nb<0>(rn, pi, bad);
             // the blocks of columns n_e and n_{e+1}; the FP64 path (badly shaped triangles) fills a
@@ -637,7 +654,7 @@ __global__ void __launch_bounds__(256, 2) k_fan_elas(const int32_t* __restrict__
             } else {
                 Block2 v = badd(ca, kc);
                 ndg = badd(ndg, v);
-                write_block(out, rb, u, cur.pos, v);
+                write_block(out, rb, u, cur.pos, v, 4 * lim.nnz);
             }
             ca = kn;
             cur = nxt;
@@ -645,13 +662,13 @@ __global__ void __launch_bounds__(256, 2) k_fan_elas(const int32_t* __restrict__
         if (kind == 0) {
             Block2 v = badd(fs, ca);
             ndg = badd(ndg, v);
-            write_block(out, rb, u, first_pos, v);
+            write_block(out, rb, u, first_pos, v, 4 * lim.nnz);
         } else {
             ndg = badd(badd(ndg, fs), ca);
-            write_block(out, rb, u, first_pos, fs);
-            write_block(out, rb, u, cur.pos, ca);
+            write_block(out, rb, u, first_pos, fs, 4 * lim.nnz);
+            write_block(out, rb, u, cur.pos, ca, 4 * lim.nnz);
         }
-        write_block(out, rb, u, pself, bneg(ndg));
+        write_block(out, rb, u, pself, bneg(ndg), 4 * lim.nnz);
     }
     if (bad) atomicOr(err, 2);
     if (orient) atomicOr(err, 1);
@@ -747,7 +764,8 @@ static fe_status launch_scalar(fe_mesh m, fe_pattern p, const double* w, double*
         out0 -= p->base_w;
         if (out1) out1 -= p->base_w;
     }
-    if (r1 > r0) { FE_PROF("k_fan_scalar", s); k_fan_scalar<KIND><<<fe_grid(r1 - r0, FAN_SCALAR_BLOCK, FanOcc<KIND>::blocks), FAN_SCALAR_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, r0, r1, cs, out0, out1, m->err); }
+    if (r1 > r0) { FE_PROF("k_fan_scalar", s); k_fan_scalar<KIND><<<fe_grid(r1 - r0, FAN_SCALAR_BLOCK, FanOcc<KIND>::blocks), FAN_SCALAR_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, r0, r1, cs, out0, out1, m->err,
+                                                                                                        Lim{m->nq, 3 * (int64_t)m->nme, win ? p->base_w + p->nnz : p->nnz_scalar}); }
     cudaError_t e = cudaGetLastError();
     fe_free(vr);
     if (e != cudaSuccess) return fe_cuda_fail(e, "k_fan_scalar");
@@ -774,7 +792,8 @@ fe_status fe_row_scalar(int kind_bits, fe_mesh m, fe_pattern p, const double* w,
 fe_status fe_row_elas(fe_mesh m, fe_pattern p, double lam, double mu, double* out, cudaStream_t s) {
     if (m->nq == 0 || p->nnz_scalar == 0) return FE_OK;
     Consts cs = make_consts(lam, mu);
-    { FE_PROF("k_fan_elas", s); k_fan_elas<<<fe_grid(m->nq, FAN_BLOCK, 8), FAN_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, m->nq, cs, out, m->err); }
+    { FE_PROF("k_fan_elas", s); k_fan_elas<<<fe_grid(m->nq, FAN_BLOCK, 8), FAN_BLOCK, 0, s>>>(p->row_ptr, p->vptr, p->fan, p->hdr, m->q, m->nq, cs, out, m->err,
+                                                                                           Lim{m->nq, 3 * (int64_t)m->nme, p->nnz_scalar}); }
     FE_LAUNCHED("k_fan_elas");
     if (p->n_gen > 0) {
         { FE_PROF("k_general_elas", s); k_general_elas<<<p->n_gen, GEN_BLOCK, 0, s>>>(p->gen_rows, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q, cs, out, m->err); }
@@ -930,7 +949,7 @@ extern "C" fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const
         if (r1 > r0) {
             FE_PROF("k_fan_scalar", s);
             k_fan_scalar<W_S | W_W><<<fe_grid(r1 - r0, FAN_SCALAR_BLOCK, FanOcc<W_S | W_W>::blocks), FAN_SCALAR_BLOCK, 0, s>>>(
-                p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, r0, r1, cs, Sd, Md, m->err);
+                p->row_ptr, p->vptr, p->fan, p->hdr, m->q, vr, r0, r1, cs, Sd, Md, m->err, Lim{m->nq, 3 * (int64_t)m->nme, p->nnz_scalar});
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return done(fe_cuda_fail(e, "k_fan_scalar"));

@@ -469,3 +469,40 @@ extern "C" fe_status fe_profile_read(int32_t max_entries, char* names, double* t
     if (count) *count = n;
     return FE_OK;
 }
+
+// ---------------------------------------------------------------- bounds-checked builds
+
+#include <mutex>
+#include <vector>
+
+namespace {
+std::mutex g_oob_mu;
+std::vector<unsigned long long (*)(int)>& oob_readers() {
+    static std::vector<unsigned long long (*)(int)> v;
+    return v;
+}
+}  // namespace
+
+void fe_oob_register(unsigned long long (*reader)(int reset)) {
+    std::lock_guard<std::mutex> lk(g_oob_mu);
+    oob_readers().push_back(reader);
+}
+
+extern "C" fe_status fe_debug_bounds(int32_t* checked, int64_t* violations, int32_t reset) {
+    if (checked) {
+#ifdef FEASM_BOUNDS_CHECK
+        *checked = 1;
+#else
+        *checked = 0;
+#endif
+    }
+    FE_CUDA(cudaDeviceSynchronize());
+    unsigned long long tot = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_oob_mu);
+        for (auto r : oob_readers()) tot += r(reset);
+    }
+    FE_CUDA(cudaGetLastError());
+    if (violations) *violations = (int64_t)tot;
+    return FE_OK;
+}

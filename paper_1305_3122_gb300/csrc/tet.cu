@@ -116,7 +116,7 @@ __global__ void k_tet_fill(const int32_t* __restrict__ me, int32_t nme, int32_t*
         for (int a = 0; a < 4; a++) v[a] = me[a * (int64_t)nme + k];
         int32_t slot[4];
 #pragma unroll
-        for (int a = 0; a < 4; a++) slot[a] = atomicAdd(&cur[v[a]], 1);
+        for (int a = 0; a < 4; a++) slot[a] = FE_IDX(atomicAdd(&cur[v[a]], 1), 4 * (int64_t)nme);
 #pragma unroll
         for (int a = 0; a < 4; a++)
             adj[slot[a]] = make_int4(v[(a + 1) & 3], v[(a + 2) & 3], v[(a + 3) & 3], 4 * (int32_t)k + a);
@@ -396,7 +396,7 @@ __device__ __forceinline__ void tet_load(const int32_t* __restrict__ me, int32_t
 template <int KIND>
 __global__ void __launch_bounds__(TET_BLOCK) k_tet_atomic(const int32_t* __restrict__ me, int32_t nme, const double4_32a* __restrict__ q,
                                                           const double* __restrict__ w, const int32_t* __restrict__ map,
-                                                          double* __restrict__ val) {
+                                                          double* __restrict__ val, int64_t nnz) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
         double4_32a p[4];
         double wl[4], E[4][4];
@@ -406,10 +406,10 @@ __global__ void __launch_bounds__(TET_BLOCK) k_tet_atomic(const int32_t* __restr
 #pragma unroll
         for (int il = 0; il < 4; il++) {
             const int4 m = m4[il];
-            atomicAdd(&val[m.x], E[il][0]);
-            atomicAdd(&val[m.y], E[il][1]);
-            atomicAdd(&val[m.z], E[il][2]);
-            atomicAdd(&val[m.w], E[il][3]);
+            atomicAdd(&val[FE_IDX(m.x, nnz)], E[il][0]);
+            atomicAdd(&val[FE_IDX(m.y, nnz)], E[il][1]);
+            atomicAdd(&val[FE_IDX(m.z, nnz)], E[il][2]);
+            atomicAdd(&val[FE_IDX(m.w, nnz)], E[il][3]);
         }
     }
 }
@@ -442,7 +442,7 @@ template <int RMAX>
 __global__ void __launch_bounds__(RS_BLOCK) k_tet_rowsum(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
                                                          int32_t nq, const int32_t* __restrict__ inc,
                                                          const uint2* __restrict__ islot, const double* __restrict__ kg,
-                                                         double* __restrict__ val) {
+                                                         double* __restrict__ val, int64_t n4) {
     __shared__ double acc[RMAX * RS_BLOCK];
     double* a = acc + threadIdx.x;                       // column c of this thread's row at a[c * RS_BLOCK]
     for (int64_t r = blockIdx.x * (int64_t)RS_BLOCK + threadIdx.x; r < nq; r += (int64_t)gridDim.x * RS_BLOCK) {
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(RS_BLOCK) k_tet_rowsum(const int32_t* __restri
             for (int j = 0; j < 4; j++) {
                 cs[j] = sl[j];
                 if (t0 + j < d) {
-                    const double2* e = reinterpret_cast<const double2*>(kg + 4 * (int64_t)key[j]);
+                    const double2* e = reinterpret_cast<const double2*>(kg + 4 * (int64_t)FE_IDX(key[j], n4));
                     v[j][0] = e[0];
                     v[j][1] = e[1];
                 }
@@ -480,10 +480,10 @@ __global__ void __launch_bounds__(RS_BLOCK) k_tet_rowsum(const int32_t* __restri
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 if (t0 + j < d) {
-                    double* p0 = a + (cs[j].x & 0xFFFFu) * RS_BLOCK;
-                    double* p1 = a + (cs[j].x >> 16) * RS_BLOCK;
-                    double* p2 = a + (cs[j].y & 0xFFFFu) * RS_BLOCK;
-                    double* p3 = a + (cs[j].y >> 16) * RS_BLOCK;
+                    double* p0 = a + FE_IDX(cs[j].x & 0xFFFFu, u) * RS_BLOCK;
+                    double* p1 = a + FE_IDX(cs[j].x >> 16, u) * RS_BLOCK;
+                    double* p2 = a + FE_IDX(cs[j].y & 0xFFFFu, u) * RS_BLOCK;
+                    double* p3 = a + FE_IDX(cs[j].y >> 16, u) * RS_BLOCK;
                     const double y0 = *p0, y1 = *p1, y2 = *p2, y3 = *p3;
                     *p0 = y0 + v[j][0].x;
                     *p1 = y1 + v[j][0].y;
@@ -774,9 +774,9 @@ extern "C" fe_status fe_tet_assemble(fe_tet_mesh m, fe_tet_pattern p, int kind, 
         FE_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * (size_t)p->nnz, s));
         if (nme > 0) {
             FE_PROF("k_tet_atomic", s);
-            if (kind == FE_TET_MASS) k_tet_atomic<FE_TET_MASS><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->map, values);
-            else if (kind == FE_TET_WMASS) k_tet_atomic<FE_TET_WMASS><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->map, values);
-            else k_tet_atomic<FE_TET_STIFF><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->map, values);
+            if (kind == FE_TET_MASS) k_tet_atomic<FE_TET_MASS><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->map, values, p->nnz);
+            else if (kind == FE_TET_WMASS) k_tet_atomic<FE_TET_WMASS><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->map, values, p->nnz);
+            else k_tet_atomic<FE_TET_STIFF><<<g, TET_BLOCK, 0, s>>>(m->me, nme, m->q, w, p->map, values, p->nnz);
         }
         FE_LAUNCHED("k_tet_atomic");
         return FE_OK;
@@ -791,9 +791,9 @@ extern "C" fe_status fe_tet_assemble(fe_tet_mesh m, fe_tet_pattern p, int kind, 
     {
         FE_PROF("k_tet_rowsum", s);
         if (!p->n_long_host[1])
-            k_tet_rowsum<RS_SHORT><<<fe_grid(m->nq, RS_BLOCK, 16), RS_BLOCK, 0, s>>>(p->vptr, p->row_ptr, m->nq, p->inc, p->islot, p->kg, values);
+            k_tet_rowsum<RS_SHORT><<<fe_grid(m->nq, RS_BLOCK, 16), RS_BLOCK, 0, s>>>(p->vptr, p->row_ptr, m->nq, p->inc, p->islot, p->kg, values, 4 * (int64_t)nme);
         else
-            k_tet_rowsum<RS_MAX><<<fe_grid(m->nq, RS_BLOCK, 8), RS_BLOCK, 0, s>>>(p->vptr, p->row_ptr, m->nq, p->inc, p->islot, p->kg, values);
+            k_tet_rowsum<RS_MAX><<<fe_grid(m->nq, RS_BLOCK, 8), RS_BLOCK, 0, s>>>(p->vptr, p->row_ptr, m->nq, p->inc, p->islot, p->kg, values, 4 * (int64_t)nme);
     }
     FE_LAUNCHED("k_tet_rowsum");
     if (p->n_long_host[0] > 0) {

@@ -16,7 +16,8 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfeasm.so")
+# FEASM_LIBRARY selects another build of the same library (the bounds-checked one, say)
+LIB_PATH = os.environ.get("FEASM_LIBRARY") or os.path.join(_HERE, "libfeasm.so")
 
 FE_OK = 0
 PTR_HOST, PTR_DEVICE, PTR_DEVICE_BORROW = 0, 1, 2
@@ -79,6 +80,7 @@ SIGNATURES = {
     "fe_measure_fp64_rate": (_INT, [ctypes.POINTER(_D), _P]),
     "fe_debug_fail_alloc": (None, [_I64]),
     "fe_debug_pool_used": (_INT, [ctypes.POINTER(_I64)]),
+    "fe_debug_bounds": (_INT, [ctypes.POINTER(_I32), ctypes.POINTER(_I64), _I32]),
     "fe_status_string": (ctypes.c_char_p, [_INT]),
     "fe_last_error": (ctypes.c_char_p, []),
 }
@@ -564,6 +566,13 @@ def debug_pool_used() -> int:
     v = _I64()
     _check(lib().fe_debug_pool_used(ctypes.byref(v)), "fe_debug_pool_used")
     return v.value
+
+
+def debug_bounds(reset: bool = False) -> tuple[bool, int]:
+    """(built with bounds checks, out-of-range derived indices counted so far) (fe_debug_bounds)."""
+    c, v = _I32(), _I64()
+    _check(lib().fe_debug_bounds(ctypes.byref(c), ctypes.byref(v), 1 if reset else 0), "fe_debug_bounds")
+    return bool(c.value), v.value
 
 
 def profile_enable(on: bool = True):
