@@ -75,6 +75,12 @@ def lib() -> ctypes.CDLL:
         _lib.or_p2_assemble.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, I64, P, P, P]
         for f in ("or_p2_triplets", "or_p2_assemble"):
             getattr(_lib, f).restype = ctypes.c_int
+        _lib.or_p3_elem_mass.argtypes = [D, P]
+        _lib.or_p3_elem_stiff.argtypes = [P, P, D, P]
+        _lib.or_p3_triplets.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, P, P]
+        _lib.or_p3_assemble.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, I64, P, P, P]
+        for f in ("or_p3_triplets", "or_p3_assemble"):
+            getattr(_lib, f).restype = ctypes.c_int
         for f in ("or_triplets", "or_sparse", "or_assemble", "or_adjoint"):
             getattr(_lib, f).restype = ctypes.c_int
     return _lib
@@ -383,6 +389,109 @@ def p2_row_values(kind: int, q, me, rows):
                 if dof[il] != r:
                     continue
                 for jl in range(6):
+                    acc[dof[jl]] = acc.get(dof[jl], 0.0) + E[il, jl]
+        cols = np.array(sorted(acc), dtype=np.int64)
+        out.append((cols, np.array([acc[c] for c in cols])))
+    return out
+
+
+# ------------------------------------------------------------------ P3 triangles
+
+def p3_elem_mass(area: float) -> np.ndarray:
+    E = np.empty(100)
+    lib().or_p3_elem_mass(area, _p(E))
+    return E.reshape(10, 10)
+
+
+def p3_elem_stiff(x, y, area: float) -> np.ndarray:
+    E = np.empty(100)
+    lib().or_p3_elem_stiff(_p(_f64(x)), _p(_f64(y)), area, _p(E))
+    return E.reshape(10, 10)
+
+
+def p3_triplets(kind: int, q, me):
+    """(Ig, Jg, Kg, ndof) of the P3 matrices, entry c = 100k + 10*jl + il; dofs: vertices, two per
+    edge (edges in ascending (smaller id, larger id) order, the node nearer the smaller id first),
+    then one bubble per triangle."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    I = np.empty(100 * nme, np.int32)
+    J = np.empty_like(I)
+    K = np.empty(100 * nme)
+    ndof = ctypes.c_int64(0)
+    bad = ctypes.c_int64(-1)
+    st = lib().or_p3_triplets(kind, nq, nme, _p(q), _p(me), _p(I), _p(J), _p(K), ctypes.byref(ndof), ctypes.byref(bad))
+    if st:
+        raise OracleError(st, f"p3_triplets (element {bad.value})")
+    return I, J, K, ndof.value
+
+
+def p3_assemble(kind: int, q, me):
+    """Global P3 CSR (row_ptr, col_idx, val) of a triangle mesh (kind MASS or STIFF)."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    cap = max(100 * nme, 1)
+    row_ptr = np.empty(nq + 7 * nme + 1, np.int32)
+    col_idx = np.empty(cap, np.int32)
+    val = np.empty(cap)
+    nnz, ndof, bad = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(-1)
+    st = lib().or_p3_assemble(kind, nq, nme, _p(q), _p(me), _p(row_ptr), _p(col_idx), _p(val), cap,
+                              ctypes.byref(nnz), ctypes.byref(ndof), ctypes.byref(bad))
+    if st:
+        raise OracleError(st, f"p3_assemble (element {bad.value})")
+    return row_ptr[:ndof.value + 1].copy(), col_idx[:nnz.value].copy(), val[:nnz.value].copy()
+
+
+def p3_dof_points(q, me):
+    """Coordinates [2, ndof] of the P3 dofs in the oracle's numbering: the vertices, the two nodes
+    of each edge at 1/3 and 2/3 (nearer the smaller id first), the centroids (for interpolating
+    test functions)."""
+    q, me = _f64(q), _i32(me)
+    keys = _p2_edge_keys(me)
+    lo, hi = keys >> 32, keys & 0xFFFFFFFF
+    n1 = (2 * q[:, lo] + q[:, hi]) / 3
+    n2 = (q[:, lo] + 2 * q[:, hi]) / 3
+    edge_nodes = np.empty((2, 2 * len(keys)))
+    edge_nodes[:, 0::2], edge_nodes[:, 1::2] = n1, n2
+    cen = (q[:, me[0]] + q[:, me[1]] + q[:, me[2]]) / 3
+    return np.concatenate([q, edge_nodes, cen], axis=1)
+
+
+def p3_row_values(kind: int, q, me, rows):
+    """Oracle values of selected P3 rows only (for meshes too large to assemble whole): the element
+    matrices of the triangles containing each row's dof, summed per column in ascending element
+    order. Returns a list of (cols, vals) in ascending column order."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    keys = _p2_edge_keys(me)
+    ne = len(keys)
+    out = []
+    for r in rows:
+        r = int(r)
+        if r < nq:
+            ks = np.nonzero((me == r).any(axis=0))[0]
+        elif r < nq + 2 * ne:
+            e = (r - nq) // 2
+            lo, hi = int(keys[e] >> 32), int(keys[e] & 0xFFFFFFFF)
+            ks = np.nonzero((me == lo).any(axis=0) & (me == hi).any(axis=0))[0]
+        else:
+            ks = np.array([r - nq - 2 * ne])
+        acc = {}
+        for k in ks:
+            v = [int(t) for t in me[:, k]]
+            x, y = q[0, v], q[1, v]
+            area = double_area(x, y) / 2
+            E = p3_elem_mass(area) if kind == MASS else p3_elem_stiff(x, y, area)
+            dof = list(v)
+            for t in range(3):
+                a, b = v[t], v[(t + 1) % 3]
+                e = int(np.searchsorted(keys, (min(a, b) << 32) | max(a, b)))
+                dof += [nq + 2 * e + (0 if a < b else 1), nq + 2 * e + (1 if a < b else 0)]
+            dof.append(nq + 2 * ne + int(k))
+            for il in range(10):
+                if dof[il] != r:
+                    continue
+                for jl in range(10):
                     acc[dof[jl]] = acc.get(dof[jl], 0.0) + E[il, jl]
         cols = np.array(sorted(acc), dtype=np.int64)
         out.append((cols, np.array([acc[c] for c in cols])))

@@ -703,3 +703,187 @@ int or_p2_assemble(int kind, int64_t nq, int64_t nme, const double* q, const int
     free(I); free(J); free(K);
     return st;
 }
+
+/* ----------------------------------------------- P3 triangles (cubic, 10 dofs) ---- */
+
+/* The paper states that the method extends to P_k elements and gives no formulas. These are the P3
+ * (cubic) matrices on a triangle T with vertices p0, p1, p2, written from the definitions, as for
+ * P2 above but with cubic Lagrange functions in the barycentric coordinates l0, l1, l2:
+ *   local dofs 0, 1, 2: the vertices, phi_a = l_a (3 l_a - 1)(3 l_a - 2) / 2;
+ *   local dofs 3..8: two per edge, for the edges (0,1), (1,2), (2,0) in turn: on edge (a, b) the
+ *     node at 2/3 p_a + 1/3 p_b, phi = 9/2 l_a l_b (3 l_a - 1), then the node at 1/3 p_a + 2/3 p_b,
+ *     phi = 9/2 l_a l_b (3 l_b - 1);
+ *   local dof 9: the centroid, the bubble 27 l0 l1 l2;
+ *   mass M^e_ij = int_T phi_i phi_j, stiffness S^e_ij = int_T grad phi_i . grad phi_j, every
+ *   product integrated exactly with int_T l0^a l1^b l2^c = 2|T| a! b! c! / (a + b + c + 2)!.
+ * Global dofs: vertex i is dof i; edge e (the edges numbered in ascending order of (smaller id,
+ * larger id), as for P2) owns dofs nq + 2e (its node nearer the smaller vertex id) and nq + 2e + 1
+ * (nearer the larger); element k's bubble is dof nq + 2 ne + k. Element k writes
+ * c = 100k + 10*jl + il (column-wise). */
+
+#define P3_DEG 7      /* exponents 0..6 per barycentric coordinate (products of two cubics) */
+typedef struct { double c[P3_DEG][P3_DEG][P3_DEG]; } p3_poly;
+
+static void p3_zero(p3_poly* p) { memset(p, 0, sizeof *p); }
+
+static void p3_mul(const p3_poly* a, const p3_poly* b, p3_poly* out) {
+    p3_zero(out);
+    for (int i = 0; i < P3_DEG; i++)
+        for (int j = 0; j < P3_DEG - i; j++)
+            for (int k = 0; k < P3_DEG - i - j; k++) {
+                double x = a->c[i][j][k];
+                if (x == 0.0) continue;
+                for (int u = 0; u < P3_DEG - i; u++)
+                    for (int v = 0; v < P3_DEG - j; v++)
+                        for (int w = 0; w < P3_DEG - k; w++) {
+                            double y = b->c[u][v][w];
+                            if (y != 0.0 && i + u + j + v + k + w < P3_DEG) out->c[i + u][j + v][k + w] += x * y;
+                        }
+            }
+}
+
+static void p3_diff(const p3_poly* a, int var, p3_poly* out) {
+    p3_zero(out);
+    for (int i = 0; i < P3_DEG; i++)
+        for (int j = 0; j < P3_DEG; j++)
+            for (int k = 0; k < P3_DEG; k++) {
+                double x = a->c[i][j][k];
+                if (x == 0.0) continue;
+                if (var == 0 && i > 0) out->c[i - 1][j][k] += i * x;
+                if (var == 1 && j > 0) out->c[i][j - 1][k] += j * x;
+                if (var == 2 && k > 0) out->c[i][j][k - 1] += k * x;
+            }
+}
+
+static double p3_fact(int n) { double f = 1.0; for (int i = 2; i <= n; i++) f *= i; return f; }
+
+static double p3_integrate(const p3_poly* a, double area) {
+    double s = 0.0;
+    for (int i = 0; i < P3_DEG; i++)
+        for (int j = 0; j < P3_DEG; j++)
+            for (int k = 0; k < P3_DEG; k++)
+                if (a->c[i][j][k] != 0.0)
+                    s += a->c[i][j][k] * 2.0 * area * p3_fact(i) * p3_fact(j) * p3_fact(k) / p3_fact(i + j + k + 2);
+    return s;
+}
+
+/* adds coef * l0^e0 l1^e1 l2^e2 to p */
+static void p3_add(p3_poly* p, double coef, int e0, int e1, int e2) { p->c[e0][e1][e2] += coef; }
+
+/* the ten basis functions as polynomials in (l0, l1, l2) */
+static void p3_basis(p3_poly phi[10]) {
+    for (int a = 0; a < 10; a++) p3_zero(&phi[a]);
+    for (int a = 0; a < 3; a++) {                     /* l (3l - 1)(3l - 2)/2 = 9/2 l^3 - 9/2 l^2 + l */
+        int e[3] = {0, 0, 0};
+        e[a] = 3; p3_add(&phi[a], 4.5, e[0], e[1], e[2]);
+        e[a] = 2; p3_add(&phi[a], -4.5, e[0], e[1], e[2]);
+        e[a] = 1; p3_add(&phi[a], 1.0, e[0], e[1], e[2]);
+    }
+    const int ea[3] = {0, 1, 2}, eb[3] = {1, 2, 0};
+    for (int t = 0; t < 3; t++) {
+        for (int side = 0; side < 2; side++) {        /* 9/2 l_a l_b (3 l_n - 1), n = a then b */
+            const int n = side == 0 ? ea[t] : eb[t];
+            p3_poly* f = &phi[3 + 2 * t + side];
+            int e[3] = {0, 0, 0};
+            e[ea[t]] += 1; e[eb[t]] += 1; e[n] += 1;
+            p3_add(f, 13.5, e[0], e[1], e[2]);
+            e[n] -= 1;
+            p3_add(f, -4.5, e[0], e[1], e[2]);
+        }
+    }
+    p3_add(&phi[9], 27.0, 1, 1, 1);
+}
+
+void or_p3_elem_mass(double area, double E[100]) {
+    p3_poly phi[10], prod;
+    p3_basis(phi);
+    for (int i = 0; i < 10; i++)
+        for (int j = 0; j < 10; j++) {
+            p3_mul(&phi[i], &phi[j], &prod);
+            E[10 * i + j] = p3_integrate(&prod, area);
+        }
+}
+
+void or_p3_elem_stiff(const double x[3], const double y[3], double area, double E[100]) {
+    double ex[3], ey[3];
+    edges(x, y, ex, ey);
+    double g[3][2];                                   /* grad l_a = (e_a,y, -e_a,x) / (2|T|), Eq. (4) */
+    for (int a = 0; a < 3; a++) {
+        g[a][0] = ey[a] / (2.0 * area);
+        g[a][1] = -ex[a] / (2.0 * area);
+    }
+    p3_poly phi[10], prod;
+    p3_poly(*d)[3] = (p3_poly(*)[3])malloc(sizeof(p3_poly[10][3]));   /* 80 KB: off the stack */
+    if (!d) { for (int t = 0; t < 100; t++) E[t] = 0.0; return; }
+    p3_basis(phi);
+    for (int i = 0; i < 10; i++)
+        for (int k = 0; k < 3; k++) p3_diff(&phi[i], k, &d[i][k]);
+    for (int i = 0; i < 10; i++)
+        for (int j = 0; j < 10; j++) {
+            double s = 0.0;
+            for (int k = 0; k < 3; k++)
+                for (int l = 0; l < 3; l++) {
+                    p3_mul(&d[i][k], &d[j][l], &prod);
+                    s += (g[k][0] * g[l][0] + g[k][1] * g[l][1]) * p3_integrate(&prod, area);
+                }
+            E[10 * i + j] = s;
+        }
+    free(d);
+}
+
+/* Ig, Jg, Kg of the P3 matrices (OR_MASS or OR_STIFF); *ndof = nq + 2 ne + nme. */
+int or_p3_triplets(int kind, int64_t nq, int64_t nme, const double* q, const int32_t* me, int32_t* I, int32_t* J,
+                   double* K, int64_t* ndof, int64_t* bad_element) {
+    if ((kind != OR_MASS && kind != OR_STIFF) || nq < 0 || nme < 0) return OR_ERR_ARG;
+    int64_t* keys = NULL;
+    int64_t ne = or_p2_edges(nq, nme, me, &keys);
+    if (ne < 0) return OR_ERR_NOMEM;
+    *ndof = nq + 2 * ne + nme;
+    for (int64_t k = 0; k < nme; k++) {
+        int32_t v[3];
+        double x[3], y[3], E[100];
+        int st = gather_element(nq, q, nme, me, k, v, x, y);
+        if (st) { if (bad_element) *bad_element = k; free(keys); return st; }
+        double D = or_double_area(x, y);
+        if (!(D > 0.0)) { if (bad_element) *bad_element = k; free(keys); return OR_ERR_ORIENT; }
+        double area = D / 2.0;
+        if (kind == OR_MASS) or_p3_elem_mass(area, E);
+        else or_p3_elem_stiff(x, y, area, E);
+        int32_t dof[10];
+        for (int a = 0; a < 3; a++) dof[a] = v[a];
+        for (int t = 0; t < 3; t++) {
+            int32_t a = v[t], b = v[(t + 1) % 3];
+            int64_t e = p2_edge_id(keys, ne, a, b);
+            dof[3 + 2 * t] = (int32_t)(nq + 2 * e + (a < b ? 0 : 1));       /* the node nearer a */
+            dof[4 + 2 * t] = (int32_t)(nq + 2 * e + (a < b ? 1 : 0));       /* the node nearer b */
+        }
+        dof[9] = (int32_t)(nq + 2 * ne + k);
+        for (int jl = 0; jl < 10; jl++)
+            for (int il = 0; il < 10; il++) {
+                int64_t c = 100 * k + 10 * jl + il;
+                I[c] = dof[il];
+                J[c] = dof[jl];
+                K[c] = E[10 * il + jl];
+            }
+    }
+    free(keys);
+    return OR_OK;
+}
+
+/* One full P3 assembly: triplets, then sparse(). row_ptr needs nq + 6 nme + nme + 1 entries (an
+ * upper bound on ndof + 1); cap >= 100 nme always suffices. */
+int or_p3_assemble(int kind, int64_t nq, int64_t nme, const double* q, const int32_t* me, int32_t* row_ptr,
+                   int32_t* col_idx, double* val, int64_t cap, int64_t* nnz_out, int64_t* ndof_out,
+                   int64_t* bad_element) {
+    int64_t ntrip = 100 * nme;
+    int32_t* I = (int32_t*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(int32_t));
+    int32_t* J = (int32_t*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(int32_t));
+    double* K = (double*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(double));
+    int st = (I && J && K) ? OR_OK : OR_ERR_NOMEM;
+    int64_t ndof = nq;
+    if (!st) st = or_p3_triplets(kind, nq, nme, q, me, I, J, K, &ndof, bad_element);
+    if (!st) st = or_sparse(ndof, ndof, ntrip, I, J, K, row_ptr, col_idx, val, cap, nnz_out);
+    *ndof_out = ndof;
+    free(I); free(J); free(K);
+    return st;
+}
