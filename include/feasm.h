@@ -68,6 +68,7 @@ typedef struct fe_batch_s* fe_batch;      /* a set of (mesh, pattern) assembled 
 typedef struct fe_tet_mesh_s* fe_tet_mesh;       /* tetrahedral mesh: device q [3][nq], me [4][nme] */
 typedef struct fe_tet_pattern_s* fe_tet_pattern; /* CSR structure and map of a tetrahedral mesh */
 typedef struct fe_p2_pattern_s* fe_p2_pattern;   /* P2 dofs, CSR structure and map of a triangle mesh */
+typedef struct fe_p3_pattern_s* fe_p3_pattern;   /* P3 dofs, CSR structure and map of a triangle mesh */
 
 /* Where the arrays passed to fe_mesh_create live. FE_PTR_DEVICE_BORROW: device memory, and the
  * mesh uses the caller's me in place instead of copying it (q is always packed into the mesh's
@@ -325,6 +326,44 @@ void fe_p2_pattern_destroy(fe_p2_pattern pattern);
  * in ascending element order: bit-identical from run to run; needs a pattern built with
  * FE_PATTERN_GATHER). */
 fe_status fe_p2_assemble(fe_mesh mesh, fe_p2_pattern pattern, int kind, int variant, double* values, int64_t cap,
+                         fe_stream stream);
+
+/* ------------------------------------------------------------- P3 triangles (cubic) ---- */
+
+/* The P_k extension for k = 3 (the paper announces P_k without formulas). Local dofs, with the
+ * barycentric coordinates l0, l1, l2 of a triangle:
+ *   0, 1, 2   the vertices, l_a (3 l_a - 1)(3 l_a - 2) / 2;
+ *   3..8      two per edge, for the edges (0,1), (1,2), (2,0) in turn: on edge (a, b) the node at
+ *             2/3 p_a + 1/3 p_b, 9/2 l_a l_b (3 l_a - 1), then the node at 1/3 p_a + 2/3 p_b,
+ *             9/2 l_a l_b (3 l_b - 1);
+ *   9         the centroid, 27 l0 l1 l2;
+ * M^e_ij = int_T phi_i phi_j and S^e_ij = int_T grad phi_i . grad phi_j. Global dofs: vertex i
+ * is dof i; edge e (the nE edges numbered as for P2) owns dofs nq + 2e (its node nearer the
+ * smaller vertex id) and nq + 2e + 1; triangle k's bubble is dof nq + 2 nE + k. The structure is
+ * the structural sum. Assembly by FP64 element matrices, scattered by FP64 atomics (values zeroed
+ * first) or, for FE_VARIANT_GATHER, staged and summed row by row in ascending element order
+ * (bit-identical from run to run). */
+enum { FE_P3_MASS = 0, FE_P3_STIFF = 1 };
+
+/* Most triangles around one vertex for a P3 pattern (FE_ERR_LIMIT above it). */
+#define FE_P3_MAX_VALENCE 400
+
+/* Dofs, CSR structure and element-to-nnz map from a mesh and its whole-mesh scalar (dofs = 1)
+ * pattern, whose structure numbers the edges. flags: FE_PATTERN_GATHER adds what
+ * FE_VARIANT_GATHER needs (each row's incidences in ascending element order with their column
+ * positions, and the staging buffer); other bits are ignored. 100 nme < 2^31 (FE_ERR_LIMIT).
+ * Synchronises (the edge count, nnz). */
+fe_status fe_p3_pattern_build(fe_mesh mesh, fe_pattern scalar_pattern, int flags, fe_stream stream, fe_p3_pattern* out);
+fe_status fe_p3_pattern_info(fe_p3_pattern pattern, int64_t* n_dofs, int64_t* nnz, const int32_t** row_ptr,
+                             const int32_t** col_idx);
+/* edof (device, [nme][10] int32): each triangle's dofs in local order; map (device, 100 nme):
+ * map[100k + 10 il + jl] = position of (edof[k][il], edof[k][jl]); *n_edges = nE. */
+fe_status fe_p3_pattern_dofs(fe_p3_pattern pattern, const int32_t** edof, const int32_t** map, int64_t* n_edges);
+void fe_p3_pattern_destroy(fe_p3_pattern pattern);
+
+/* Values of FE_P3_MASS or FE_P3_STIFF into values[0 .. nnz) (device, capacity cap). variant:
+ * FE_VARIANT_ATOMIC or FE_VARIANT_GATHER (needs a pattern built with FE_PATTERN_GATHER). */
+fe_status fe_p3_assemble(fe_mesh mesh, fe_p3_pattern pattern, int kind, int variant, double* values, int64_t cap,
                          fe_stream stream);
 
 /* -------------------------------------------------------------------- zero dropping ---- */

@@ -117,6 +117,26 @@ struct fe_p2_pattern_s {
     cudaStream_t last_stream = nullptr;
 };
 
+// P3 (cubic) triangle patterns (p3.cu).
+struct fe_p3_pattern_s {
+    int32_t nq = 0, nme = 0;
+    int64_t ne = 0;                       // edges: dofs nq .. nq + 2 ne - 1, two per edge
+    int32_t ndof = 0;                     // nq + 2 ne + nme (the bubbles last)
+    uint64_t topology_id = 0;
+    int64_t nnz = 0;
+    int32_t* row_ptr = nullptr;           // [ndof + 1]
+    int32_t* col_idx = nullptr;           // [nnz]
+    int32_t* edof = nullptr;              // [nme][10] element dofs
+    int32_t* map = nullptr;               // [100 nme] map[100k + 10 il + jl] = position of (edof[k][il], edof[k][jl])
+    // FE_PATTERN_GATHER: each row's incidences in ascending element order and the staging buffer
+    int flags = 0;
+    int32_t* vptr = nullptr;              // [ndof + 1] start of row r's incidences
+    int32_t* ikey = nullptr;              // [10 nme] keys 10k + a (row r = edof[k][a]), ascending within a row
+    int32_t* ipos = nullptr;              // [10 nme][5] the incidence's ten in-row column positions, 16 bits each
+    double* kg = nullptr;                 // [100 nme] staged element values, row-major per element
+    cudaStream_t last_stream = nullptr;
+};
+
 uint64_t fe_next_topology_id();
 
 // Staged mesh creation for the one-shot host call (mesh.cu): the connectivity (device array,

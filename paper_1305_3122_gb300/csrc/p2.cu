@@ -28,6 +28,7 @@
 // list each row's incidences in ascending element order with their column positions), so that every non-zero sums its
 // contributions in ascending element order, bit-identical from run to run.
 #include "internal.cuh"
+#include "edges.cuh"
 #include "rowhash.cuh"
 
 namespace {
@@ -53,44 +54,14 @@ struct P2Lists {
     int32_t nq;
 };
 
-// Entries right of the diagonal in each scalar row (0 for an empty row), and the diagonal's place.
-__global__ void k_p2_upper(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx, int32_t nq,
-                           int32_t* __restrict__ ucnt, int32_t* __restrict__ dpos) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = (int32_t)r, b = row_ptr[i], n = row_ptr[i + 1] - b;
-        int lo = 0, hi = n;                                   // first column >= i
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (col_idx[b + mid] < i) lo = mid + 1;
-            else hi = mid;
-        }
-        dpos[i] = lo;
-        ucnt[i] = n > 0 ? n - lo - 1 : 0;
-    }
-}
-
-__device__ __forceinline__ int32_t p2_edge(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                                           const int32_t* __restrict__ eoff, const int32_t* __restrict__ dpos,
-                                           int32_t u, int32_t v) {
-    const int32_t a = min(u, v), c = max(u, v);
-    const int32_t b = row_ptr[a];
-    int lo = dpos[a] + 1, hi = row_ptr[a + 1] - b - 1;        // c lies right of the diagonal
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (col_idx[b + mid] < c) lo = mid + 1;
-        else hi = mid;
-    }
-    return eoff[a] + (lo - dpos[a] - 1);
-}
-
 // edof[6k .. 6k+5]: the element's dofs; also counts each dof's elements.
 __global__ void k_p2_edof(const int32_t* __restrict__ me, int32_t nme, int32_t nq, const int32_t* __restrict__ row_ptr,
                           const int32_t* __restrict__ col_idx, const int32_t* __restrict__ eoff,
                           const int32_t* __restrict__ dpos, int32_t* __restrict__ edof, int32_t* __restrict__ deg) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v0 = me[k], v1 = me[nme + k], v2 = me[2 * (int64_t)nme + k];
-        int32_t d[6] = {v0, v1, v2, nq + p2_edge(row_ptr, col_idx, eoff, dpos, v0, v1),
-                        nq + p2_edge(row_ptr, col_idx, eoff, dpos, v1, v2), nq + p2_edge(row_ptr, col_idx, eoff, dpos, v2, v0)};
+        int32_t d[6] = {v0, v1, v2, nq + edge_rank(row_ptr, col_idx, eoff, dpos, v0, v1),
+                        nq + edge_rank(row_ptr, col_idx, eoff, dpos, v1, v2), nq + edge_rank(row_ptr, col_idx, eoff, dpos, v2, v0)};
         int2* o = reinterpret_cast<int2*>(edof + 6 * k);
         o[0] = make_int2(d[0], d[1]);
         o[1] = make_int2(d[2], d[3]);
@@ -590,8 +561,8 @@ extern "C" fe_status fe_p2_pattern_build(fe_mesh m, fe_pattern p1, int flags, fe
     if ((st = fe_alloc_n(&t.dpos, (size_t)nq + 1, "diagonal places"))) return fail(st);
     if ((st = fe_alloc_n(&t.eoff, (size_t)nq + 1, "edge offsets"))) return fail(st);
     if (nq > 0) {
-        { FE_PROF("k_p2_upper", s); k_p2_upper<<<fe_grid(nq, P2_BLOCK), P2_BLOCK, 0, s>>>(p1->row_ptr, p1->col_idx, nq, t.ucnt, t.dpos); }
-        FE_LAUNCHED("k_p2_upper");
+        { FE_PROF("k_edge_upper", s); k_edge_upper<<<fe_grid(nq, P2_BLOCK), P2_BLOCK, 0, s>>>(p1->row_ptr, p1->col_idx, nq, t.ucnt, t.dpos); }
+        FE_LAUNCHED("k_edge_upper");
     }
     int64_t ne = 0;
     if ((st = fe_exclusive_scan(t.ucnt, t.eoff, nq, s, &ne))) return fail(st);          // synchronises

@@ -63,6 +63,11 @@ SIGNATURES = {
     "fe_p2_pattern_dofs": (_INT, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
     "fe_p2_pattern_destroy": (None, [_P]),
     "fe_p2_assemble": (_INT, [_P, _P, _INT, _INT, _P, _I64, _P]),
+    "fe_p3_pattern_build": (_INT, [_P, _P, _INT, _P, ctypes.POINTER(_P)]),
+    "fe_p3_pattern_info": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "fe_p3_pattern_dofs": (_INT, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
+    "fe_p3_pattern_destroy": (None, [_P]),
+    "fe_p3_assemble": (_INT, [_P, _P, _INT, _INT, _P, _I64, _P]),
     "fe_assemble_stiff_wmass_host": (_INT, [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "fe_batch_create": (_INT, [_I32, _P, _P, ctypes.POINTER(_P)]),
     "fe_batch_tune": (_INT, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
@@ -468,6 +473,61 @@ def p2_assemble(mesh: Mesh, pattern: P2Pattern, kind: int, out=None, stream=None
         raise ValueError("out must be a contiguous float64 CUDA tensor")
     _check(lib().fe_p2_assemble(mesh.handle, pattern.handle, kind, variant, out.data_ptr(), out.numel(),
                                 _stream(stream)), "fe_p2_assemble")
+    return out
+
+
+P3_MASS, P3_STIFF = 0, 1
+
+
+class P3Pattern:
+    """P3 (cubic) dofs, CSR structure and map of a triangle mesh (fe_p3_pattern_build): vertex i is
+    dof i; edge e owns dofs nq + 2e and nq + 2e + 1 (the node nearer its smaller vertex id first);
+    triangle k's bubble is dof nq + 2 nE + k. Built from the mesh's scalar pattern, whose structure
+    numbers the edges. gather=True adds the row lists of the deterministic variant (GATHER)."""
+
+    def __init__(self, mesh: Mesh, pattern: Pattern, gather: bool = False, stream=None):
+        h = _P()
+        flags = PATTERN_GATHER if gather else 0
+        _check(lib().fe_p3_pattern_build(mesh.handle, pattern.handle, flags, _stream(stream), ctypes.byref(h)),
+               "fe_p3_pattern_build")
+        self._h = h
+        self.mesh = mesh
+        n, nnz, rp, ci = _I64(), _I64(), _P(), _P()
+        _check(lib().fe_p3_pattern_info(h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci)),
+               "fe_p3_pattern_info")
+        self.n_rows, self.nnz = n.value, nnz.value
+        self.row_ptr = _view_i32(rp.value, self.n_rows + 1, self)
+        self.col_idx = _view_i32(ci.value, self.nnz, self)
+        ed, mp, ne = _P(), _P(), _I64()
+        _check(lib().fe_p3_pattern_dofs(h, ctypes.byref(ed), ctypes.byref(mp), ctypes.byref(ne)), "fe_p3_pattern_dofs")
+        self.n_edges = ne.value
+        self.edof = _view_i32(ed.value, 10 * mesh.nme, self)
+        self.map = _view_i32(mp.value, 100 * mesh.nme, self)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def new_values(self) -> torch.Tensor:
+        return torch.empty(self.nnz, dtype=torch.float64, device="cuda")
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fe_p3_pattern_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def p3_assemble(mesh: Mesh, pattern: P3Pattern, kind: int, out=None, stream=None, variant: int = ATOMIC) -> torch.Tensor:
+    """Values of the P3 mass (P3_MASS) or stiffness (P3_STIFF) on the P3 pattern (fe_p3_assemble),
+    by FP64 atomics (ATOMIC) or by ordered row sums (GATHER, a pattern built with gather=True)."""
+    out = pattern.new_values() if out is None else out
+    if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 CUDA tensor")
+    _check(lib().fe_p3_assemble(mesh.handle, pattern.handle, kind, variant, out.data_ptr(), out.numel(),
+                                _stream(stream)), "fe_p3_assemble")
     return out
 
 

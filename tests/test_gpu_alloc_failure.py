@@ -47,6 +47,7 @@ class _Fixtures:
         self.bpat = [feasm.Pattern(x) for x in self.bmesh]
         self.part = feasm.Mesh.part(m.q, m.me, 20, 90)
         self.part_pat = feasm.Pattern(self.part, rows=(20, 90))
+        self.p3 = feasm.P3Pattern(self.mesh, self.pat, gather=True)
 
 
 def _scenarios(fx: _Fixtures) -> dict:
@@ -80,6 +81,9 @@ def _scenarios(fx: _Fixtures) -> dict:
         "mesh_part": lambda: feasm.Mesh.part(m.q, m.me, 20, 90),
         "pattern_part": lambda: feasm.Pattern(fx.part, rows=(30, 80)),
         "assemble_part": lambda: feasm.assemble_stiff_wmass(fx.part, fx.part_pat, fx.w, feasm.ROW),
+        "p3_pattern": lambda: feasm.P3Pattern(fx.mesh, fx.pat, gather=True),
+        "p3_gather": lambda: feasm.p3_assemble(fx.mesh, fx.p3, feasm.P3_STIFF, variant=feasm.GATHER),
+        "p3_atomic": lambda: feasm.p3_assemble(fx.mesh, fx.p3, feasm.P3_MASS, variant=feasm.ATOMIC),
     }
 
 
@@ -116,10 +120,11 @@ def _fx() -> _Fixtures:
 
 NAMES = ["mesh", "pattern", "pattern_gather", "pattern_dofs2", "assemble_row", "assemble_atomic", "assemble_gather",
          "elasticity", "adjoint_gather", "adjoint_atomic", "drop_zeros", "tet_mesh", "tet_pattern", "tet_gather",
-         "p2_pattern", "p2_gather", "host_call", "batch", "mesh_part", "pattern_part", "assemble_part"]
+         "p2_pattern", "p2_gather", "host_call", "batch", "mesh_part", "pattern_part", "assemble_part", "p3_pattern",
+         "p3_gather", "p3_atomic"]
 # calls that certainly allocate device memory (assembly calls may work in the pattern's buffers)
 ALLOCATING = {"mesh", "pattern", "pattern_gather", "pattern_dofs2", "drop_zeros", "tet_mesh", "tet_pattern",
-              "p2_pattern", "host_call", "batch", "mesh_part", "pattern_part"}
+              "p2_pattern", "host_call", "batch", "mesh_part", "pattern_part", "p3_pattern"}
 
 
 @pytest.mark.parametrize("name", NAMES)

@@ -49,6 +49,11 @@ for name, (q, me) in sorted(CASES.items()):
         rp2, _, va2 = oracle.p2_assemble(oracle.STIFF, q, me)
         for v in (feasm.ATOMIC, feasm.GATHER):
             assert_values_close(rp2, feasm.p2_assemble(mesh, p2, feasm.P2_STIFF, variant=v).cpu().numpy(), va2)
+    if mesh.nme > 0 and name != "fans5x4000":                 # P3 takes valences up to 400
+        p3 = feasm.P3Pattern(mesh, feasm.Pattern(mesh), gather=True)
+        rp3, _, va3 = oracle.p3_assemble(oracle.STIFF, q, me)
+        for v in (feasm.ATOMIC, feasm.GATHER):
+            assert_values_close(rp3, feasm.p3_assemble(mesh, p3, feasm.P3_STIFF, variant=v).cpu().numpy(), va3)
     for r0, r1 in partition.row_ranges(mesh.nq, 2):
         part = feasm.Mesh.part(q, me, r0, r1)
         pp = feasm.Pattern(part, rows=(r0, r1))
