@@ -17,9 +17,8 @@ the timed steps. Also reported:
     element arithmetic is plain FP64 (staged gather, FP64 atomics);
   - per-kernel shares of the step, each with its algorithmic bytes and HBM fraction;
   - roofline of the dominant kernel, timed live with the library's own CUDA events;
-  - the other legs: plane elasticity, the adjoint, zero dropping, tetrahedra (with an FP64
-    roofline against the measured FP64 rate) and P2 triangles, each with both scatter variants
-    where it has them;
+  - the other legs: plane elasticity, the adjoint, zero dropping, tetrahedra, P2 and P3 triangles,
+    each with both scatter variants where it has them;
   - cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload, single-threaded,
     on all host cores (one process per core), and beside every other leg.
 Between timed steps L2 is flushed by writing a 512 MB buffer (outside the timed intervals).
@@ -257,6 +256,10 @@ def cpu_oracle_legs(legs, target_s: float = 2.0) -> dict:
         m = meshgen.square_mesh(48, 13053122 + 7)
         r = _oracle_rate(lambda: oracle.p2_assemble(oracle.STIFF, m.q, m.me), m.nme / 1e6, target_s)
         out["p2"] = entry(r[0], "Melem/s", r[1], r[2], f"P2 S on the 48x48-cell square (nme={m.nme})")
+    if "p3" in legs:
+        m = meshgen.square_mesh(32, 13053122 + 8)
+        r = _oracle_rate(lambda: oracle.p3_assemble(oracle.STIFF, m.q, m.me), m.nme / 1e6, target_s)
+        out["p3"] = entry(r[0], "Melem/s", r[1], r[2], f"P3 S on the 32x32-cell square (nme={m.nme})")
     if "batched" in legs:
         ms = meshgen.batch_meshes(13053122 + 4, count=8)
         n = sum(x.nme for x in ms)
@@ -496,10 +499,11 @@ def run_ours(args) -> int:
         line["drop_zeros"] = drop_zeros(feasm, torch, pat0, S, flush, hbm, peak_kind, cells=args.cells)
         line["tetrahedra"] = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind)
         line["p2"] = p2(feasm, meshgen, torch, flush, hbm, peak_kind)
+        line["p3"] = p3(feasm, meshgen, torch, flush, hbm, peak_kind)
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample()
         line["cpu_baseline"]["all_cores"] = cpu_oracle_all_cores()
-        legs = [k for k in ("batched", "elasticity", "adjoint", "drop_zeros", "tetrahedra", "p2") if k in line]
+        legs = [k for k in ("batched", "elasticity", "adjoint", "drop_zeros", "tetrahedra", "p2", "p3") if k in line]
         if legs:
             line["cpu_baseline"]["legs"] = cpu_oracle_legs(legs)
     print(json.dumps(line), flush=True)
@@ -782,6 +786,39 @@ def p2(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 1024) -> dict:
                          "note": "36 FP64 atomics per element into values zeroed first; the atomics, not DRAM, set the time"}}
 
 
+def p3(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 1024) -> dict:
+    """P3 (cubic) triangles on the 1024 x 1024-cell square (jittered, node-permuted): the P3 pattern
+    from the scalar one (with and without the ordered variant's row lists), and the mass and
+    stiffness by FP64 atomics and by ordered row sums."""
+    seed = 13053122 + 8
+    m = meshgen.square_mesh(cells, seed)
+    mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))
+    pat = feasm.Pattern(mesh, map=False)
+    ms_pat = _time_calls(torch, lambda: feasm.P3Pattern(mesh, pat).close(), flush, reps=5)
+    ms_pat_g = _time_calls(torch, lambda: feasm.P3Pattern(mesh, pat, gather=True).close(), flush, reps=5)
+    p3p = feasm.P3Pattern(mesh, pat, gather=True)
+    out = p3p.new_values()
+    res = {}
+    for kn, k in (("M", feasm.P3_MASS), ("S", feasm.P3_STIFF)):
+        for vn, v in (("atomic", feasm.ATOMIC), ("gather", feasm.GATHER)):
+            res[f"{kn}_{vn}_ms"] = round(_time_calls(torch, lambda: feasm.p3_assemble(mesh, p3p, k, out, variant=v), flush), 4)
+    feasm.profile_reset()
+    feasm.profile_enable(True)
+    _time_calls(torch, lambda: feasm.p3_assemble(mesh, p3p, feasm.P3_STIFF, out), flush)
+    feasm.profile_enable(False)
+    prof = feasm.profile_read()
+    k_ms = prof["k_p3_atomic"][0] / prof["k_p3_atomic"][1]
+    nbytes = 12 * m.nme + 16 * m.nq + 400 * m.nme + 8 * p3p.nnz          # me, q, map, values
+    return {"workload": f"P3 M and S of the {cells}x{cells}-cell square (nq={m.nq}, edges={p3p.n_edges}, "
+                        f"dofs={p3p.n_rows}, nme={m.nme}, nnz={p3p.nnz})",
+            "pattern_ms": round(ms_pat, 4), "pattern_gather_ms": round(ms_pat_g, 4), **res,
+            "S_melem_s": round(m.nme / res["S_atomic_ms"] / 1e3, 1), "k_p3_atomic_S_ms": round(k_ms, 4),
+            "roofline": {"kernel": "k_p3_atomic<S>", "bound": "hbm", "algorithmic_bytes": nbytes,
+                         "achieved": round(nbytes / k_ms / 1e6, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(nbytes / k_ms / 1e6 / hbm, 4), "peak_source": f"{peak_kind} HBM copy bandwidth",
+                         "note": "100 FP64 atomics per element into values zeroed first"}}
+
+
 def adjoint(feasm, meshgen, torch, flush, hbm, peak_kind) -> dict:
     """dL/dq, dL/dw of L = <G_S, S> + <G_M, M^[w]> on the 1024 x 1024-cell mesh (deterministic gather)."""
     seed = 13053122 + 5
@@ -906,7 +943,7 @@ def main() -> int:
     ap.add_argument("--no-other", action="store_true", help="skip the elasticity, adjoint, zero-dropping, tetrahedra and P2 legs")
     ap.add_argument("--traffic", default=os.path.join(ROOT, "profiles", "traffic.json"),
                     help="per-kernel DRAM bytes per launch from an ncu capture (JSON)")
-    ap.add_argument("--only", choices=["elasticity", "adjoint", "drop_zeros", "tetrahedra", "p2"],
+    ap.add_argument("--only", choices=["elasticity", "adjoint", "drop_zeros", "tetrahedra", "p2", "p3"],
                     help="run this one leg alone and print its object (for profiling; no headline step)")
     ap.add_argument("--tet-cells", type=int, default=128, help="cells per side of the tetrahedra leg's cube")
     ap.add_argument("--p2-cells", type=int, default=1024, help="cells per side of the P2 leg's square")
@@ -933,6 +970,8 @@ def run_leg(args) -> int:
         out = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind, cells=args.tet_cells)
     elif args.only == "p2":
         out = p2(feasm, meshgen, torch, flush, hbm, peak_kind, cells=args.p2_cells)
+    elif args.only == "p3":
+        out = p3(feasm, meshgen, torch, flush, hbm, peak_kind, cells=args.p2_cells)
     else:
         m = meshgen.square_mesh(args.cells, 13053122 + 2)
         mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))

@@ -134,6 +134,8 @@ struct fe_p3_pattern_s {
     int32_t* ikey = nullptr;              // [10 nme] keys 10k + a (row r = edof[k][a]), ascending within a row
     int32_t* ipos = nullptr;              // [10 nme][5] the incidence's ten in-row column positions, 16 bits each
     double* kg = nullptr;                 // [100 nme] staged element values, row-major per element
+    int32_t* long_rows = nullptr;         // rows of more columns than one warp's fast accumulators
+    int32_t n_long = 0;
     cudaStream_t last_stream = nullptr;
 };
 

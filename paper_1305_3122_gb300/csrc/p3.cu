@@ -40,6 +40,8 @@ constexpr int FAST_TS = 128, FAST_EMAX = 12;                  // 10 * 12 ids < 1
 constexpr int BIG_TS = 4096, BIG_EMAX = FE_P3_MAX_VALENCE;    // 10 * 400 ids < 4096 slots
 static_assert(10 * FAST_EMAX < FAST_TS && 10 * BIG_EMAX < BIG_TS, "tables hold every id");
 constexpr int RS_FAST = 10 * FAST_EMAX;                       // row-sum accumulators of a warp (fast rows)
+constexpr int RS_SHORT = 16;                                  // row-sum accumulators of a thread (edge and bubble rows)
+constexpr int RS_BLOCK = 128;
 
 // Element dofs (edof[10k .. 10k+9]) and the dofs' element counts.
 __global__ void k_p3_edof(const int32_t* __restrict__ me, int32_t nme, int32_t nq, const int32_t* __restrict__ row_ptr,
@@ -89,8 +91,10 @@ struct P3Smem {
 
 // Where the row pass puts the deterministic variant's lists (ikey null: no lists).
 struct P3Lists {
-    int32_t* ikey;   // [10 nme] each row's incidence keys 10k + a in ascending order, row r from vptr[r]
-    int32_t* ipos;   // [10 nme][5] their ten in-row column positions, 16 bits each
+    int32_t* ikey;       // [10 nme] each row's incidence keys 10k + a in ascending order, row r from vptr[r]
+    int32_t* ipos;       // [10 nme][5] their ten in-row column positions, 16 bits each
+    int32_t* long_rows;  // rows of more than RS_FAST columns (summed by k_p3_rowsum_long)
+    int32_t* n_long;     // their number
 };
 
 // One row by one warp: its sorted distinct columns into tmp at 10 vptr[r] (each incidence brings
@@ -144,7 +148,10 @@ __device__ void p3_row(int32_t r, int32_t beg, int32_t d, const int32_t* __restr
             for (int j = 0; j < 5; j++) po[j] = (int32_t)((unsigned)o[2 * j] | ((unsigned)o[2 * j + 1] << 16));
         }
     }
-    if (lane == 0) cnt[r] = u;
+    if (lane == 0) {
+        cnt[r] = u;
+        if (ls.ikey && u > RS_FAST) ls.long_rows[atomicAdd(ls.n_long, 1)] = r;
+    }
     __syncwarp();
 }
 
@@ -158,15 +165,76 @@ __global__ void __launch_bounds__(P3_WARPS * 32) k_p3_rows(const int32_t* __rest
     const int lane = threadIdx.x & 31;
     for (int64_t rr = (int64_t)blockIdx.x * P3_WARPS + (threadIdx.x >> 5); rr < nrows; rr += (int64_t)gridDim.x * P3_WARPS) {
         const int32_t r = (int32_t)rr, beg = vptr[r], d = vptr[r + 1] - beg;
-        if (d == 0) {
-            if (lane == 0) cnt[r] = 0;
-            continue;
-        }
+        if (d <= 2) continue;                                    // k_p3_short_rows
         if (d > FAST_EMAX) {
             if (lane == 0) big_list[atomicAdd(big_count, 1)] = r;
             continue;
         }
         p3_row<FAST_TS, FAST_EMAX>(r, beg, d, inc, edof, sm, tmp, cnt, map, ls);
+    }
+}
+
+// The rows of at most two elements (an edge's dofs in a manifold mesh, a bubble, an unused
+// vertex), one thread each: the at most 20 ids sorted in registers (a fixed compare-exchange
+// sequence: static indices only); the rank of a value is the number of distinct smaller ones.
+__global__ void __launch_bounds__(P3_BLOCK) k_p3_short_rows(const int32_t* __restrict__ vptr, const int32_t* __restrict__ inc,
+                                                            const int32_t* __restrict__ edof, int32_t nrows,
+                                                            int32_t* __restrict__ tmp, int32_t* __restrict__ cnt,
+                                                            int32_t* __restrict__ map, P3Lists ls) {
+    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < nrows; rr += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = (int32_t)rr, beg = vptr[r], d = vptr[r + 1] - beg;
+        if (d > 2) continue;
+        int32_t key[2] = {d > 0 ? inc[beg] : -1, d > 1 ? inc[beg + 1] : -1};
+        if (key[1] >= 0 && key[1] < key[0]) {                   // ascending element order
+            const int32_t x = key[0];
+            key[0] = key[1];
+            key[1] = x;
+        }
+        int32_t x[20];
+#pragma unroll
+        for (int t = 0; t < 2; t++)
+#pragma unroll
+            for (int j = 0; j < 10; j++) x[10 * t + j] = key[t] >= 0 ? edof[10 * (int64_t)(key[t] / 10) + j] : INT32_MAX;
+#pragma unroll
+        for (int i = 1; i < 20; i++)
+#pragma unroll
+            for (int j = i; j > 0; j--) {
+                const int32_t lo = min(x[j - 1], x[j]), hi = max(x[j - 1], x[j]);
+                x[j - 1] = lo;
+                x[j] = hi;
+            }
+        const int64_t tb = 10 * (int64_t)beg;
+        int u = 0;
+#pragma unroll
+        for (int i = 0; i < 20; i++) {
+            const bool first = x[i] != INT32_MAX && (i == 0 || x[i] != x[i - 1]);
+            if (first) tmp[tb + u] = x[i];
+            u += first;
+        }
+        cnt[r] = u;
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            if (key[t] < 0) continue;
+            const int32_t kk = key[t] / 10, a = key[t] - 10 * kk;
+            const int32_t* e = edof + 10 * (int64_t)kk;
+            int32_t* o = map + 100 * (int64_t)kk + 10 * a;
+            unsigned sl[10];
+#pragma unroll
+            for (int jl = 0; jl < 10; jl++) {
+                const int32_t v = e[jl];
+                int rank = 0;
+#pragma unroll
+                for (int i = 0; i < 20; i++) rank += x[i] < v && (i == 0 || x[i] != x[i - 1]);
+                o[jl] = rank;
+                sl[jl] = (unsigned)rank;
+            }
+            if (ls.ikey) {                                       // key[] is in ascending order: place t
+                ls.ikey[beg + t] = key[t];
+                int32_t* po = ls.ipos + 5 * (int64_t)(beg + t);
+#pragma unroll
+                for (int j = 0; j < 5; j++) po[j] = (int32_t)(sl[2 * j] | (sl[2 * j + 1] << 16));
+            }
+        }
     }
 }
 
@@ -192,13 +260,26 @@ __global__ void __launch_bounds__(32) k_p3_rows_big(const int32_t* __restrict__ 
     }
 }
 
-// col_idx from the rows' sorted columns, one thread per row.
+// col_idx from the rows' sorted columns: a warp takes 32 consecutive rows and copies them one
+// after another, its lanes over the row's entries (coalesced loads and stores).
 __global__ void __launch_bounds__(P3_BLOCK) k_p3_cols(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
                                                       int32_t ndof, const int32_t* __restrict__ tmp, int32_t* __restrict__ col_idx) {
-    for (int64_t rr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; rr < ndof; rr += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t r = (int32_t)rr, rb = row_ptr[r], u = row_ptr[r + 1] - rb;
-        const int64_t tb = 10 * (int64_t)vptr[r];
-        for (int c = 0; c < u; c++) col_idx[rb + c] = tmp[tb + c];
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r0 = 32 * ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); r0 < ndof; r0 += 32 * warps) {
+        const int64_t mine = r0 + lane;
+        int32_t rb = 0, u = 0;
+        int64_t tb = 0;
+        if (mine < ndof) {
+            rb = row_ptr[mine];
+            u = row_ptr[mine + 1] - rb;
+            tb = 10 * (int64_t)vptr[mine];
+        }
+        for (int j = 0; j < 32 && r0 + j < ndof; j++) {
+            const int32_t b = __shfl_sync(0xffffffffu, rb, j), n = __shfl_sync(0xffffffffu, u, j);
+            const int64_t t = __shfl_sync(0xffffffffu, tb, j);
+            for (int c = lane; c < n; c += 32) col_idx[b + c] = tmp[t + c];
+        }
     }
 }
 
@@ -309,22 +390,64 @@ __global__ void __launch_bounds__(P3_WARPS * 32) k_p3_rowsum(const int32_t* __re
     __shared__ double acc_all[P3_WARPS][RS_FAST];
     double* acc = acc_all[threadIdx.x >> 5];
     for (int64_t rr = (int64_t)blockIdx.x * P3_WARPS + (threadIdx.x >> 5); rr < ndof; rr += (int64_t)gridDim.x * P3_WARPS) {
-        const int32_t r = (int32_t)rr;
-        if (row_ptr[r + 1] - row_ptr[r] > RS_FAST) continue;     // k_p3_rowsum_long
+        const int32_t r = (int32_t)rr, u = row_ptr[r + 1] - row_ptr[r];
+        if (u <= RS_SHORT || u > RS_FAST) continue;             // k_p3_rowsum_short, k_p3_rowsum_long
         p3_rowsum(r, vptr, row_ptr, ikey, ipos, kg, val, acc, n10);
     }
 }
 
-// The rows longer than RS_FAST columns, one warp each, accumulators in dynamic shared memory.
-__global__ void __launch_bounds__(32) k_p3_rowsum_long(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
-                                                       int32_t ndof, const int32_t* __restrict__ ikey,
-                                                       const int32_t* __restrict__ ipos, const double* __restrict__ kg,
-                                                       double* __restrict__ val, int64_t n10) {
-    extern __shared__ double acc_long[];
-    for (int64_t r = blockIdx.x; r < ndof; r += gridDim.x) {
-        if (row_ptr[r + 1] - row_ptr[r] <= RS_FAST) continue;
-        p3_rowsum((int32_t)r, vptr, row_ptr, ikey, ipos, kg, val, acc_long, n10);
+// The rows of at most RS_SHORT columns (an interior edge's two dofs: 16 columns, a bubble: 10),
+// one thread each: accumulators in shared memory (column c of this thread's row at
+// acc[c * RS_BLOCK]), the incidences' ten entries added in ascending element order, starting
+// from -0.0 as in p3_rowsum, so the sums are the same bit for bit.
+__global__ void __launch_bounds__(RS_BLOCK) k_p3_rowsum_short(const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
+                                                              int32_t ndof, const int32_t* __restrict__ ikey,
+                                                              const int32_t* __restrict__ ipos, const double* __restrict__ kg,
+                                                              double* __restrict__ val, int64_t n10) {
+    __shared__ double acc_all[RS_SHORT * RS_BLOCK];
+    double* acc = acc_all + threadIdx.x;
+    for (int64_t r = blockIdx.x * (int64_t)RS_BLOCK + threadIdx.x; r < ndof; r += (int64_t)gridDim.x * RS_BLOCK) {
+        const int32_t rb = row_ptr[r], u = row_ptr[r + 1] - rb;
+        if (u > RS_SHORT) continue;
+        const int32_t b0 = vptr[r], d = vptr[r + 1] - b0;
+        for (int c = 0; c < u; c++) acc[c * RS_BLOCK] = -0.0;
+        for (int32_t t = 0; t < d; t++) {
+            const int32_t key = FE_IDX(ikey[b0 + t], n10);
+            const int32_t* pw = ipos + 5 * (int64_t)(b0 + t);
+            const double2* e = reinterpret_cast<const double2*>(kg + 10 * (int64_t)key);   // 100k + 10a: 16-byte aligned
+            double v[10];
+            unsigned w[5];
+#pragma unroll
+            for (int j = 0; j < 5; j++) {
+                const double2 x = e[j];
+                v[2 * j] = x.x;
+                v[2 * j + 1] = x.y;
+                w[j] = (unsigned)pw[j];
+            }
+            // an incidence's ten columns are distinct: all ten accumulators are read before any
+            // is written back
+            double* pc[10];
+            double y[10];
+#pragma unroll
+            for (int j = 0; j < 10; j++) pc[j] = acc + FE_IDX((int)((w[j >> 1] >> (16 * (j & 1))) & 0xFFFFu), u) * RS_BLOCK;
+#pragma unroll
+            for (int j = 0; j < 10; j++) y[j] = *pc[j];
+#pragma unroll
+            for (int j = 0; j < 10; j++) *pc[j] = y[j] + v[j];
+        }
+        for (int c = 0; c < u; c++) val[rb + c] = acc[c * RS_BLOCK];
     }
+}
+
+// The rows longer than RS_FAST columns (listed by the row pass), one warp each, accumulators in
+// dynamic shared memory.
+__global__ void __launch_bounds__(32) k_p3_rowsum_long(const int32_t* __restrict__ long_rows, int32_t n_long,
+                                                       const int32_t* __restrict__ vptr, const int32_t* __restrict__ row_ptr,
+                                                       const int32_t* __restrict__ ikey, const int32_t* __restrict__ ipos,
+                                                       const double* __restrict__ kg, double* __restrict__ val, int64_t n10) {
+    extern __shared__ double acc_long[];
+    for (int32_t b = blockIdx.x; b < n_long; b += gridDim.x)
+        p3_rowsum(long_rows[b], vptr, row_ptr, ikey, ipos, kg, val, acc_long, n10);
 }
 
 }  // namespace
@@ -452,7 +575,7 @@ extern "C" void fe_p3_pattern_destroy(fe_p3_pattern p) {
     if (!p) return;
     FeStreamScope scope(p->last_stream);
     fe_free(p->row_ptr); fe_free(p->col_idx); fe_free(p->map); fe_free(p->edof);
-    fe_free(p->vptr); fe_free(p->ikey); fe_free(p->ipos); fe_free(p->kg);
+    fe_free(p->vptr); fe_free(p->ikey); fe_free(p->ipos); fe_free(p->kg); fe_free(p->long_rows);
     delete p;
 }
 
@@ -520,9 +643,13 @@ extern "C" fe_status fe_p3_pattern_build(fe_mesh m, fe_pattern p1, int flags, fe
     if (gather) {
         if ((st = fe_alloc_n(&p->ikey, 10 * (size_t)nme, "row incidence keys"))) return fail(st);
         if ((st = fe_alloc_n(&p->ipos, 50 * (size_t)nme, "row incidence positions"))) return fail(st);
+        if ((st = fe_alloc_n(&p->long_rows, (size_t)ndof + 1, "long rows"))) return fail(st);
     }
-    const P3Lists ls{p->ikey, p->ipos};
+    const P3Lists ls{p->ikey, p->ipos, p->long_rows, t.counters + 2};
     if (ndof > 0) {
+        { FE_PROF("k_p3_short_rows", s); k_p3_short_rows<<<fe_grid(ndof, P3_BLOCK, 8), P3_BLOCK, 0, s>>>(
+              t.vptr, t.inc, p->edof, ndof, t.tmp, t.cnt, p->map, ls); }
+        FE_LAUNCHED("k_p3_short_rows");
         { FE_PROF("k_p3_rows", s); k_p3_rows<<<fe_grid(((int64_t)ndof + P3_WARPS - 1) / P3_WARPS, 1, 12), P3_WARPS * 32, 0, s>>>(
               t.vptr, t.inc, p->edof, ndof, t.tmp, t.cnt, p->map, t.big, t.counters, ls); }
         FE_LAUNCHED("k_p3_rows");
@@ -535,10 +662,12 @@ extern "C" fe_status fe_p3_pattern_build(fe_mesh m, fe_pattern p1, int flags, fe
     if ((st = fe_alloc_n(&p->row_ptr, (size_t)ndof + 1, "row_ptr"))) return fail(st);
     int64_t nnz = 0;
     if ((st = fe_exclusive_scan(t.cnt, p->row_ptr, ndof, s, &nnz))) return fail(st);   // synchronises
-    int too_big = 0;
-    if (cudaMemcpyAsync(&too_big, t.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    int flags_h[2] = {0, 0};                                    // a row above the valence limit, long rows
+    if (cudaMemcpyAsync(flags_h, t.counters + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return fail(fe_fail(FE_ERR_CUDA, "flag read-back"));
+    const int too_big = flags_h[0];
+    p->n_long = flags_h[1];
     if (too_big)
         return fail(fe_fail(FE_ERR_LIMIT, "a vertex belongs to more than FE_P3_MAX_VALENCE=" +
                                               std::to_string(FE_P3_MAX_VALENCE) + " triangles"));
@@ -619,15 +748,20 @@ extern "C" fe_status fe_p3_assemble(fe_mesh m, fe_p3_pattern p, int kind, int va
     }
     FE_LAUNCHED("k_p3_stage");
     const int32_t ndof = p->ndof;
+    { FE_PROF("k_p3_rowsum_short", s); k_p3_rowsum_short<<<fe_grid(ndof, RS_BLOCK, 8), RS_BLOCK, 0, s>>>(
+          p->vptr, p->row_ptr, ndof, p->ikey, p->ipos, p->kg, values, 10 * (int64_t)nme); }
+    FE_LAUNCHED("k_p3_rowsum_short");
     { FE_PROF("k_p3_rowsum", s); k_p3_rowsum<<<fe_grid(((int64_t)ndof + P3_WARPS - 1) / P3_WARPS, 1, 12), P3_WARPS * 32, 0, s>>>(
           p->vptr, p->row_ptr, ndof, p->ikey, p->ipos, p->kg, values, 10 * (int64_t)nme); }
     FE_LAUNCHED("k_p3_rowsum");
     // rows of more than RS_FAST columns (vertices of more than 12 triangles): their accumulators in
     // dynamic shared memory, sized for the longest row any P3 pattern can have
-    const size_t long_smem = sizeof(double) * 10 * (size_t)BIG_EMAX;
-    FE_CUDA(cudaFuncSetAttribute(k_p3_rowsum_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)long_smem));
-    { FE_PROF("k_p3_rowsum_long", s); k_p3_rowsum_long<<<fe_sm_count(), 32, long_smem, s>>>(p->vptr, p->row_ptr, ndof, p->ikey, p->ipos,
-                                                                                            p->kg, values, 10 * (int64_t)nme); }
-    FE_LAUNCHED("k_p3_rowsum_long");
+    if (p->n_long > 0) {
+        const size_t long_smem = sizeof(double) * 10 * (size_t)BIG_EMAX;
+        FE_CUDA(cudaFuncSetAttribute(k_p3_rowsum_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)long_smem));
+        { FE_PROF("k_p3_rowsum_long", s); k_p3_rowsum_long<<<(unsigned)min((int64_t)p->n_long, (int64_t)fe_sm_count() * 8), 32, long_smem, s>>>(
+              p->long_rows, p->n_long, p->vptr, p->row_ptr, p->ikey, p->ipos, p->kg, values, 10 * (int64_t)nme); }
+        FE_LAUNCHED("k_p3_rowsum_long");
+    }
     return FE_OK;
 }
