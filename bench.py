@@ -584,9 +584,12 @@ def recorded_traffic(name: str, cells: int, traffic_path: str | None):
 
 # What limits a kernel below its HBM roof, from its ncu captures (profiles/).
 LIMITS = {
-    "k_fan_scalar": "instruction issue: double-float arithmetic on the FP32 and integer pipes (issue slots 61% busy "
-                    "at 1024^2, profiles/k_fan_scalar_1024.md); at 2048^2 also the random vertex-record gathers, "
-                    "which miss L2 (traffic above)",
+    "k_fan_scalar": "instruction issue and load latency: 85.3 M warp instructions at 1024^2 issued on 60.5% of cycles "
+                    "(FP32 FMA pipe 38%, integer ALU 33%, FP64 pipe 42%: double-float arithmetic in place of FP64, "
+                    "with FP64 for the coordinate differences and the output sums), the rest waiting on the dependent "
+                    "fan-record and vertex-record loads (3.9 long-scoreboard stalls per issue, 20 warps per SM at 95 "
+                    "registers; profiles/k_fan_scalar_1024.md); at 2048^2 the random vertex-record gathers also miss "
+                    "L2 (traffic above). Locality orders, shared-memory staging and cp.async gathers measured slower",
 }
 
 
