@@ -588,7 +588,7 @@ LIMITS = {
                     "(FP32 FMA pipe 38%, integer ALU 33%, FP64 pipe 42%: double-float arithmetic in place of FP64, "
                     "with FP64 for the coordinate differences and the output sums), the rest waiting on the dependent "
                     "fan-record and vertex-record loads (3.9 long-scoreboard stalls per issue, 20 warps per SM at 95 "
-                    "registers; profiles/k_fan_scalar_1024.md); at 2048^2 the random vertex-record gathers also miss "
+                    "registers; ncu at 1024^2); at 2048^2 the random vertex-record gathers also miss "
                     "L2 (traffic above). Locality orders, shared-memory staging and cp.async gathers measured slower",
 }
 
