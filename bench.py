@@ -16,6 +16,7 @@ the timed steps. Also reported:
     double-float on the FP32 pipes), and fp64_variants: the same step by the two variants whose
     element arithmetic is plain FP64 (staged gather, FP64 atomics);
   - per-kernel shares of the step, each with its algorithmic bytes and HBM fraction;
+  - unstructured: the same step on the random-diagonal 2048 x 2048 square (valences 4 to 8);
   - roofline of the dominant kernel, timed live with the library's own CUDA events;
   - the other legs: plane elasticity, the adjoint, zero dropping, tetrahedra, P2 and P3 triangles,
     each with both scatter variants where it has them;
@@ -491,6 +492,8 @@ def run_ours(args) -> int:
         line["e2e"] = e2e(feasm, torch, m, w, args)
     if not args.no_fp64_variants and args.variant == "row":
         line["fp64_variants"] = fp64_variants(feasm, torch, q_d, me_d, w_d, flush, stream, m)
+    if not args.no_other and args.variant == "row" and args.cells == N_CELLS:
+        line["unstructured"] = unstructured(feasm, meshgen, torch, flush, stream)
     if not args.no_batched:
         line["batched"] = batched(feasm, meshgen, torch, args, hbm, peak_kind)
     if not args.no_other:
@@ -517,6 +520,48 @@ def run_ours(args) -> int:
 ARITH = {"row": "double-float (pairs of FP32, about 48-bit significands) element arithmetic on the FP32 pipes; "
                 "FP64 inputs, coordinate differences and outputs",
          "gather": "fp64", "atomic": "fp64"}
+
+
+def unstructured(feasm, meshgen, torch, flush, stream, reps: int = 20) -> dict:
+    """The headline step (mesh, pattern, S + M^[w] by row owners) on the 2048 x 2048-cell square with
+    random cell diagonals: interior vertices in 4 to 8 triangles, as in unstructured meshes."""
+    m = meshgen.square_mesh(N_CELLS, SEED, random_diagonals=True)
+    w = meshgen.vertex_weights(m, SEED)
+    q_d, me_d, w_d = (torch.tensor(a, device="cuda") for a in (m.q, m.me, w))
+    pat0 = feasm.Pattern(feasm.Mesh(q_d, me_d, borrow=True), map=False)
+    S, M = pat0.new_values(), pat0.new_values()
+    nnz = pat0.nnz
+    pat0.close()
+
+    def step():
+        mesh = feasm.Mesh(q_d, me_d, borrow=True)
+        pat = feasm.Pattern(mesh, map=False)
+        feasm.assemble_stiff_wmass(mesh, pat, w_d, feasm.ROW, S, M)
+        pat.close()
+        mesh.close()
+
+    for _ in range(3):
+        step()
+    feasm.profile_reset()
+    ts = []
+    for i in range(2 * reps):
+        if i == reps:                                  # the second half with the per-kernel events
+            feasm.profile_enable(True)
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        if i < reps:
+            ts.append(e0.elapsed_time(e1))
+    feasm.profile_enable(False)
+    prof = feasm.profile_read()
+    ms = sum(ts) / len(ts)
+    return {"workload": f"S + M^[w], random-diagonal {N_CELLS}x{N_CELLS}-cell square (nq={m.nq}, nme={m.nme}, "
+                        f"nnz={nnz} per matrix)", "ms_per_step": round(ms, 4), "value": round(m.nme / ms / 1e3, 3),
+            "unit": UNIT, "kernels_ms": {k: round(v[0] / v[1], 4) for k, v in sorted(prof.items())}}
 
 
 def fp64_variants(feasm, torch, q_d, me_d, w_d, flush, stream, m, reps: int = 10) -> dict:
