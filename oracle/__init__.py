@@ -69,6 +69,11 @@ def lib() -> ctypes.CDLL:
         _lib.or_tet_assemble.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, P, I64, P, P]
         for f in ("or_tet_triplets", "or_tet_assemble"):
             getattr(_lib, f).restype = ctypes.c_int
+        _lib.or_tet_elem_elas.argtypes = [P, P, P, D, D, D, P]
+        _lib.or_tet_elas_triplets.argtypes = [I64, I64, P, P, D, D, P, P, P, P]
+        _lib.or_tet_elas_assemble.argtypes = [I64, I64, P, P, D, D, P, P, P, I64, P, P]
+        for f in ("or_tet_elas_triplets", "or_tet_elas_assemble"):
+            getattr(_lib, f).restype = ctypes.c_int
         _lib.or_p2_elem_mass.argtypes = [D, P]
         _lib.or_p2_elem_stiff.argtypes = [P, P, D, P]
         _lib.or_p2_triplets.argtypes = [ctypes.c_int, I64, I64, P, P, P, P, P, P, P]
@@ -295,6 +300,60 @@ def tet_assemble(kind: int, q, me, w=None):
     if st:
         raise OracleError(st, f"tet_assemble (element {bad.value})")
     return row_ptr, col_idx[:nnz.value].copy(), val[:nnz.value].copy()
+
+
+def tet_elem_elas(x, y, z, vol: float, lam: float, mu: float) -> np.ndarray:
+    """12 x 12 3-D elasticity matrix |K| B^T C B of one tetrahedron (local dof 3a + d)."""
+    E = np.empty(144)
+    lib().or_tet_elem_elas(_p(_f64(x)), _p(_f64(y)), _p(_f64(z)), vol, lam, mu, _p(E))
+    return E.reshape(12, 12)
+
+
+def tet_elas_triplets(q, me, lam: float, mu: float):
+    """(Ig, Jg, Kg) of the 3-D elasticity matrix, entry c = 144k + 12*jl + il, dofs 3v + d."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    I = np.empty(144 * nme, np.int32)
+    J = np.empty_like(I)
+    K = np.empty(144 * nme)
+    bad = ctypes.c_int64(-1)
+    st = lib().or_tet_elas_triplets(nq, nme, _p(q), _p(me), lam, mu, _p(I), _p(J), _p(K), ctypes.byref(bad))
+    if st:
+        raise OracleError(st, f"tet_elas_triplets (element {bad.value})")
+    return I, J, K
+
+
+def tet_elas_assemble(q, me, lam: float, mu: float):
+    """Global CSR (row_ptr, col_idx, val) of the 3-D elasticity matrix (3 nq rows)."""
+    q, me = _f64(q), _i32(me)
+    nq, nme = q.shape[1], me.shape[1]
+    cap = max(144 * nme, 1)
+    row_ptr = np.empty(3 * nq + 1, np.int32)
+    col_idx = np.empty(cap, np.int32)
+    val = np.empty(cap)
+    nnz = ctypes.c_int64(0)
+    bad = ctypes.c_int64(-1)
+    st = lib().or_tet_elas_assemble(nq, nme, _p(q), _p(me), lam, mu, _p(row_ptr), _p(col_idx), _p(val), cap,
+                                    ctypes.byref(nnz), ctypes.byref(bad))
+    if st:
+        raise OracleError(st, f"tet_elas_assemble (element {bad.value})")
+    return row_ptr, col_idx[:nnz.value].copy(), val[:nnz.value].copy()
+
+
+def tet_elas_row_values(q, me, lam: float, mu: float, rows):
+    """Oracle values of selected rows (dofs 3v + d) of the 3-D elasticity matrix, for meshes too
+    large to assemble whole: the triplets of the tetrahedra containing vertex v, then sparse()
+    of those whose row is r. Returns a list of (cols, vals) in ascending column order."""
+    q, me = _f64(q), _i32(me)
+    n = 3 * q.shape[1]
+    out = []
+    for r in rows:
+        ks = np.nonzero((me == r // 3).any(axis=0))[0]
+        I, J, K = tet_elas_triplets(q, me[:, ks], lam, mu)
+        sel = I == r
+        rp, ci, va = sparse(I[sel], J[sel], K[sel], n, n)
+        out.append((ci[rp[r]:rp[r + 1]], va[rp[r]:rp[r + 1]]))
+    return out
 
 
 # ------------------------------------------------------------------ P2 triangles

@@ -29,6 +29,8 @@
  *
  * The adjoint (dL/dq, dL/dw for L = sum_p G[p]*A.values[p]) is not in the paper; it is the
  * derivative of the element formulas above, written out term by term in or_adjoint().
+ * The extensions the paper announces without formulas (P1 tetrahedra, 3-D elasticity on them,
+ * P2 and P3 triangles) follow in their own sections below, each from the definitions it states.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -504,6 +506,97 @@ int or_tet_assemble(int kind, int64_t nq, int64_t nme, const double* q, const in
     int st = (I && J && K) ? OR_OK : OR_ERR_NOMEM;
     if (!st) st = or_tet_triplets(kind, nq, nme, q, me, w, I, J, K, bad_element);
     if (!st) st = or_sparse(nq, nq, ntrip, I, J, K, row_ptr, col_idx, val, cap, nnz_out);
+    free(I); free(J); free(K);
+    return st;
+}
+
+/* --------------------------------------- 3-D linear elasticity on tetrahedra (P1) ---- */
+
+/* Section 7's construction carried to three dimensions (the paper announces the 3-D extension
+ * without formulas): small strains, an isotropic material with constant Lame parameters lambda
+ * and mu. Local dof 3a + d is component d (x, y, z) of vertex a. With g = grad(phi_a) (as for
+ * the stiffness above), column 3a + d of the 6 x 12 strain matrix B maps that dof to the Voigt
+ * strain vector (e_xx, e_yy, e_zz, 2 e_xy, 2 e_yz, 2 e_zx):
+ *   column 3a     = (gx, 0,  0,  gy, 0,  gz)
+ *   column 3a + 1 = (0,  gy, 0,  gx, gz, 0 )
+ *   column 3a + 2 = (0,  0,  gz, 0,  gy, gx)
+ * The material matrix is C = lambda (1,1,1,0,0,0)^T (1,1,1,0,0,0) + mu diag(2,2,2,1,1,1), and
+ * K^e = |K| B^T C B (12 x 12, row-major E[12 i + j]). Global dofs are interleaved: vertex v owns
+ * rows 3v, 3v + 1, 3v + 2. Element k writes c = 144k + 12 jl + il (column-wise, Ke = E(:)). */
+void or_tet_elem_elas(const double x[4], const double y[4], const double z[4], double vol,
+                      double lam, double mu, double E[144]) {
+    double g[4][3];
+    tet_gradients(x, y, z, g);
+    double B[6][12];
+    memset(B, 0, sizeof B);
+    for (int a = 0; a < 4; a++) {
+        double gx = g[a][0], gy = g[a][1], gz = g[a][2];
+        B[0][3 * a] = gx;      B[3][3 * a] = gy;      B[5][3 * a] = gz;
+        B[1][3 * a + 1] = gy;  B[3][3 * a + 1] = gx;  B[4][3 * a + 1] = gz;
+        B[2][3 * a + 2] = gz;  B[4][3 * a + 2] = gy;  B[5][3 * a + 2] = gx;
+    }
+    double C[6][6];
+    memset(C, 0, sizeof C);
+    for (int r = 0; r < 3; r++)
+        for (int t = 0; t < 3; t++) C[r][t] = lam + (r == t ? 2.0 * mu : 0.0);
+    for (int r = 3; r < 6; r++) C[r][r] = mu;
+    double CB[6][12];
+    for (int r = 0; r < 6; r++)
+        for (int j = 0; j < 12; j++) {
+            double s = 0.0;
+            for (int t = 0; t < 6; t++) s += C[r][t] * B[t][j];
+            CB[r][j] = s;
+        }
+    for (int i = 0; i < 12; i++)
+        for (int j = 0; j < 12; j++) {
+            double s = 0.0;
+            for (int t = 0; t < 6; t++) s += B[t][i] * CB[t][j];
+            E[12 * i + j] = vol * s;
+        }
+}
+
+/* Ig, Jg, Kg of the 3-D elasticity matrix (144 per tetrahedron, c = 144k + 12 jl + il). */
+int or_tet_elas_triplets(int64_t nq, int64_t nme, const double* q, const int32_t* me, double lam,
+                         double mu, int32_t* I, int32_t* J, double* K, int64_t* bad_element) {
+    if (nq < 0 || nme < 0 || 3 * nq >= INT32_MAX) return OR_ERR_ARG;
+    for (int64_t k = 0; k < nme; k++) {
+        int32_t v[4];
+        double x[4], y[4], z[4], E[144];
+        for (int a = 0; a < 4; a++) {
+            v[a] = me[a * nme + k];
+            if (v[a] < 0 || v[a] >= nq) { if (bad_element) *bad_element = k; return OR_ERR_INDEX; }
+            x[a] = q[v[a]];
+            y[a] = q[nq + v[a]];
+            z[a] = q[2 * nq + v[a]];
+        }
+        for (int a = 0; a < 4; a++)
+            for (int b = a + 1; b < 4; b++)
+                if (v[a] == v[b]) { if (bad_element) *bad_element = k; return OR_ERR_DEGENERATE; }
+        double D = or_tet_volume6(x, y, z);
+        if (!(D > 0.0)) { if (bad_element) *bad_element = k; return OR_ERR_ORIENT; }
+        or_tet_elem_elas(x, y, z, D / 6.0, lam, mu, E);
+        for (int jl = 0; jl < 12; jl++)
+            for (int il = 0; il < 12; il++) {
+                int64_t c = 144 * k + 12 * jl + il;
+                I[c] = 3 * v[il / 3] + il % 3;
+                J[c] = 3 * v[jl / 3] + jl % 3;
+                K[c] = E[12 * il + jl];
+            }
+    }
+    return OR_OK;
+}
+
+/* The 3-D elasticity matrix (3 nq rows): triplets, then sparse() (cap >= 144 nme suffices). */
+int or_tet_elas_assemble(int64_t nq, int64_t nme, const double* q, const int32_t* me, double lam,
+                         double mu, int32_t* row_ptr, int32_t* col_idx, double* val, int64_t cap,
+                         int64_t* nnz_out, int64_t* bad_element) {
+    int64_t ntrip = 144 * nme;
+    int32_t* I = (int32_t*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(int32_t));
+    int32_t* J = (int32_t*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(int32_t));
+    double* K = (double*)malloc((size_t)(ntrip > 0 ? ntrip : 1) * sizeof(double));
+    int st = (I && J && K) ? OR_OK : OR_ERR_NOMEM;
+    if (!st) st = or_tet_elas_triplets(nq, nme, q, me, lam, mu, I, J, K, bad_element);
+    if (!st) st = or_sparse(3 * nq, 3 * nq, ntrip, I, J, K, row_ptr, col_idx, val, cap, nnz_out);
     free(I); free(J); free(K);
     return st;
 }

@@ -204,6 +204,25 @@ def tet_stiff(pts):
     return [[vol * sum(g[a][d] * g[b][d] for d in range(3)) for b in range(4)] for a in range(4)]
 
 
+def tet_elas(pts, lam, mu):
+    """12 x 12 3-D elasticity matrix from the bilinear form
+        a(u, v) = int_K lam div(u) div(v) + 2 mu eps(u) : eps(v),   eps(u) = (grad u + grad u^T) / 2,
+    for the vector basis functions u = phi_a e_alpha (local dof 3a + alpha): grad u has the
+    single row alpha equal to grad(phi_a). No strain vector or material matrix is formed."""
+    vol = volume3(pts)
+    g = [b[1:] for b in barycentric3(pts)]
+    lam, mu = Fraction(lam), Fraction(mu)
+    grads = []
+    for a in range(4):
+        for al in range(3):
+            G = [[g[a][j] if i == al else Fraction(0) for j in range(3)] for i in range(3)]
+            grads.append(G)
+    eps = [[[(G[i][j] + G[j][i]) / 2 for j in range(3)] for i in range(3)] for G in grads]
+    div = [G[0][0] + G[1][1] + G[2][2] for G in grads]
+    return [[vol * (lam * div[I] * div[J] + 2 * mu * sum(eps[I][i][j] * eps[J][i][j] for i in range(3) for j in range(3)))
+             for J in range(12)] for I in range(12)]
+
+
 def tet_assemble_dense(kind, pts_all, me, w=None):
     """Dense global matrix of a tetrahedral mesh, exact (kind in mass, wmass, stiff)."""
     n = len(pts_all)
