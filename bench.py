@@ -18,8 +18,8 @@ the timed steps. Also reported:
   - per-kernel shares of the step, each with its algorithmic bytes and HBM fraction;
   - unstructured: the same step on the random-diagonal 2048 x 2048 square (valences 4 to 8);
   - roofline of the dominant kernel, timed live with the library's own CUDA events;
-  - the other legs: plane elasticity, the adjoint, zero dropping, tetrahedra, P2 and P3 triangles,
-    each with both scatter variants where it has them;
+  - the other legs: plane elasticity, the adjoint, zero dropping, tetrahedra, 3-D elasticity on
+    tetrahedra, P2 and P3 triangles, each with both scatter variants where it has them;
   - cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload, single-threaded,
     on all host cores (one process per core), and beside every other leg.
 Between timed steps L2 is flushed by writing a 512 MB buffer (outside the timed intervals).
@@ -253,6 +253,10 @@ def cpu_oracle_legs(legs, target_s: float = 2.0) -> dict:
         m = meshgen.cube_mesh(24, 13053122 + 6)
         r = _oracle_rate(lambda: oracle.tet_assemble(oracle.STIFF, m.q, m.me), m.nme / 1e6, target_s)
         out["tetrahedra"] = entry(r[0], "Melem/s", r[1], r[2], f"S on the 24^3-cell cube (nme={m.nme})")
+    if "tet_elasticity" in legs:
+        m = meshgen.cube_mesh(12, 13053122 + 9)
+        r = _oracle_rate(lambda: oracle.tet_elas_assemble(m.q, m.me, 1.25, 0.4), m.nme / 1e6, target_s)
+        out["tet_elasticity"] = entry(r[0], "Melem/s", r[1], r[2], f"3-D K (lambda 1.25, mu 0.4) on the 12^3-cell cube (nme={m.nme})")
     if "p2" in legs:
         m = meshgen.square_mesh(48, 13053122 + 7)
         r = _oracle_rate(lambda: oracle.p2_assemble(oracle.STIFF, m.q, m.me), m.nme / 1e6, target_s)
@@ -501,12 +505,14 @@ def run_ours(args) -> int:
         line["adjoint"] = adjoint(feasm, meshgen, torch, flush, hbm, peak_kind)
         line["drop_zeros"] = drop_zeros(feasm, torch, pat0, S, flush, hbm, peak_kind, cells=args.cells)
         line["tetrahedra"] = tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind)
+        line["tet_elasticity"] = tet_elasticity(feasm, meshgen, torch, flush, hbm, peak_kind)
         line["p2"] = p2(feasm, meshgen, torch, flush, hbm, peak_kind)
         line["p3"] = p3(feasm, meshgen, torch, flush, hbm, peak_kind)
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample()
         line["cpu_baseline"]["all_cores"] = cpu_oracle_all_cores()
-        legs = [k for k in ("batched", "elasticity", "adjoint", "drop_zeros", "tetrahedra", "p2", "p3") if k in line]
+        legs = [k for k in ("batched", "elasticity", "adjoint", "drop_zeros", "tetrahedra", "tet_elasticity", "p2", "p3")
+                if k in line]
         if legs:
             line["cpu_baseline"]["legs"] = cpu_oracle_legs(legs)
     print(json.dumps(line), flush=True)
@@ -798,6 +804,52 @@ def tetrahedra(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 128) -
                                                  "(fe_measure_fp64_rate)",
                                   "nominal_peak": round(FP64_PEAK_G, 1),
                                   "nominal_peak_source": "2 FP64 instructions per SM per clock x 152 SMs x 2.07 GHz"}}}
+
+
+def tet_elasticity(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 64) -> dict:
+    """3-D linear elasticity (lambda 1.25, mu 0.4) on the 64^3-cell cube (jittered, node-permuted):
+    the pattern with the elasticity structure (with and without the ordered variant's lists), and
+    K by FP64 atomics and by staged element matrices summed row by row, with the roofline of each."""
+    seed = 13053122 + 9
+    lam, mu = 1.25, 0.4
+    m = meshgen.cube_mesh(cells, seed)
+    mesh = feasm.TetMesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))
+    ms_pat = _time_calls(torch, lambda: feasm.TetPattern(mesh, elas=True).close(), flush, reps=5)
+    ms_pat_g = _time_calls(torch, lambda: feasm.TetPattern(mesh, gather=True, elas=True).close(), flush, reps=5)
+    pat = feasm.TetPattern(mesh, gather=True, elas=True)
+    out = torch.empty(pat.elas_nnz, dtype=torch.float64, device="cuda")
+    ms = {}
+    kern = {}
+    for vn, v in (("atomic", feasm.ATOMIC), ("gather", feasm.GATHER)):
+        ms[vn] = _time_calls(torch, lambda: feasm.tet_assemble_elas(mesh, pat, lam, mu, v, out), flush)
+        feasm.profile_reset()
+        feasm.profile_enable(True)
+        _time_calls(torch, lambda: feasm.tet_assemble_elas(mesh, pat, lam, mu, v, out), flush)
+        feasm.profile_enable(False)
+        kern[vn] = {k: round(t / c, 4) for k, (t, c) in feasm.profile_read().items()}
+    nnz3 = pat.elas_nnz
+    # compulsory bytes: me, the vertex records, the scalar map and row_ptr read once, K written once
+    b_atomic = 16 * m.nme + 32 * m.nq + 64 * m.nme + 4 * (m.nq + 1) + 8 * nnz3
+    # the ordered variant: me and the vertex records read, the 1152-byte element matrices written
+    # and read back once, the incidence lists (12 bytes per incidence) read, K written once
+    b_gather = 16 * m.nme + 32 * m.nq + 2 * 1152 * m.nme + 48 * m.nme + 8 * nnz3
+    k_at = kern["atomic"]["k_tet_elas_atomic"]
+    k_g = sum(kern["gather"].values())
+
+    def roof(name, nbytes, t_ms, limit):
+        return {"kernel": name, "bound": "hbm", "algorithmic_bytes": int(nbytes), "achieved": round(nbytes / t_ms / 1e6, 1),
+                "peak": hbm, "unit": "GB/s", "frac": round(nbytes / t_ms / 1e6 / hbm, 4),
+                "peak_source": f"{peak_kind} HBM copy bandwidth", "limit": limit}
+    return {"workload": f"3-D elasticity K of the {cells}^3-cell cube (nq={m.nq}, nme={m.nme} tetrahedra, "
+                        f"{3 * m.nq} dofs, nnz={nnz3})",
+            "pattern_ms": round(ms_pat, 4), "pattern_gather_ms": round(ms_pat_g, 4),
+            "atomic_ms": round(ms["atomic"], 4), "gather_ms": round(ms["gather"], 4),
+            "atomic_melem_s": round(m.nme / ms["atomic"] / 1e3, 1), "gather_melem_s": round(m.nme / ms["gather"] / 1e3, 1),
+            "kernels_ms": kern,
+            "roofline": roof("k_tet_elas_atomic", b_atomic, k_at,
+                             "144 FP64 atomics per tetrahedron into values zeroed first, and FP64 element arithmetic"),
+            "roofline_gather": roof("k_tet_elas_stage + k_tet_elas_rowsum", b_gather, k_g,
+                                    "FP64 element arithmetic in the stage; random 96-byte element rows in the row sums")}
 
 
 def p2(feasm, meshgen, torch, flush, hbm, peak_kind, cells: int = 1024) -> dict:

@@ -272,8 +272,9 @@ void fe_tet_mesh_destroy(fe_tet_mesh mesh);
 
 /* CSR structure (columns ascending in each row) and the element-to-nnz map of a tetrahedral mesh.
  * flags: FE_PATTERN_GATHER adds what FE_VARIANT_GATHER needs: each row's incidences in ascending
- * element order with the in-row positions of their columns, and the staging buffer (other bits
- * are ignored; the map is always built). Synchronises once (nnz). */
+ * element order with the in-row positions of their columns, and the staging buffer;
+ * FE_TET_PATTERN_ELAS (below) adds the structure of the 3-D elasticity matrix. Other bits are
+ * ignored; the map is always built. Synchronises once (nnz). */
 fe_status fe_tet_pattern_build(fe_tet_mesh mesh, int flags, fe_stream stream, fe_tet_pattern* out);
 fe_status fe_tet_pattern_info(fe_tet_pattern pattern, int64_t* n_rows, int64_t* nnz, const int32_t** row_ptr,
                               const int32_t** col_idx);
@@ -290,6 +291,41 @@ void fe_tet_pattern_destroy(fe_tet_pattern pattern);
  * arithmetic in FP64. */
 fe_status fe_tet_assemble(fe_tet_mesh mesh, fe_tet_pattern pattern, int kind, const double* w, int variant,
                           double* values, int64_t cap, fe_stream stream);
+
+/* 3-D linear elasticity on tetrahedra: the plane elasticity of Section 7 carried to three
+ * dimensions (the paper announces the 3-D extension without formulas). Small strains, an
+ * isotropic material with constant Lame parameters lambda and mu; its material matrix must be
+ * positive definite: mu > 0 and 3 lambda + 2 mu > 0, both finite (else FE_ERR_INVALID_ARG; the
+ * plane case's condition lambda + mu > 0 is the 2-D form of the second). Dofs are interleaved:
+ * vertex v owns rows 3v (x), 3v + 1 (y) and 3v + 2 (z). With g_a = grad(phi_a) and |K| as above,
+ * and the Voigt strain vector (e_xx, e_yy, e_zz, 2 e_xy, 2 e_yz, 2 e_zx), the element matrix is
+ * K^e = |K| B^T C B, that is
+ *   K^e[3a + s][3b + t] = |K| (lambda g_a,s g_b,t + mu g_a,t g_b,s + mu [s = t] g_a . g_b).
+ * Structure: each entry (i, j) of the scalar tetrahedral pattern becomes the 3 x 3 block of rows
+ * 3i .. 3i + 2 and columns 3j .. 3j + 2. Row 3i + s starts at 9 row_ptr[i] + 3 s len_i, where
+ * len_i = row_ptr[i + 1] - row_ptr[i], and its columns ascend (3j, 3j + 1, 3j + 2 for each scalar
+ * column j). fe_tet_pattern_build makes it when its flags include FE_TET_PATTERN_ELAS; 9 nnz must
+ * be < 2^31 (FE_ERR_LIMIT). */
+#define FE_TET_PATTERN_ELAS 4
+
+/* The structure above: n_rows = 3 nq, nnz = 9 times the scalar nnz, row_ptr [3 nq + 1] and
+ * col_idx [nnz] (device memory owned by the pattern). FE_ERR_INVALID_ARG if the pattern was built
+ * without FE_TET_PATTERN_ELAS. */
+fe_status fe_tet_pattern_elas_info(fe_tet_pattern pattern, int64_t* n_rows, int64_t* nnz, const int32_t** row_ptr,
+                                   const int32_t** col_idx);
+
+/* Values of the 3-D elasticity matrix on that structure, into values[0 .. nnz) (device, capacity
+ * cap >= nnz, else FE_ERR_BUFFER_TOO_SMALL), in the order of its col_idx. The pattern needs
+ * FE_TET_PATTERN_ELAS (FE_ERR_INVALID_ARG otherwise). variant:
+ *   FE_VARIANT_ATOMIC: values zeroed, then each tetrahedron adds its 144 entries by FP64 atomicAdd
+ *                      (positions from the scalar map and row_ptr).
+ *   FE_VARIANT_GATHER: the element matrices are staged (1152 bytes per tetrahedron, allocated for
+ *                      the call), then each row sums its incidences' element rows in ascending
+ *                      element order, so every value is bit-identical from run to run. Needs a
+ *                      pattern built with FE_PATTERN_GATHER as well.
+ * Element arithmetic in FP64. */
+fe_status fe_tet_assemble_elas(fe_tet_mesh mesh, fe_tet_pattern pattern, double lambda, double mu, int variant,
+                               double* values, int64_t cap, fe_stream stream);
 
 /* ------------------------------------------------------- P2 triangles (quadratic) ---- */
 

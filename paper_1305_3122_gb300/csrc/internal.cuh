@@ -91,8 +91,20 @@ struct fe_tet_pattern_s {
     int32_t* n_long = nullptr;            // [2] their number, and 1 if a row is longer than 16 (device)
     int32_t n_long_host[2] = {0, 0};
     double* kg = nullptr;                 // [16 nme] staged element values
+    // FE_TET_PATTERN_ELAS: the 3-D elasticity structure (3 x 3 blocks of the scalar one)
+    int32_t* row_ptr3 = nullptr;          // [3 nq + 1]
+    int32_t* col_idx3 = nullptr;          // [9 nnz]
     cudaStream_t last_stream = nullptr;
 };
+
+// Row sums of the tetrahedral ordered variants: the longest row (in scalar columns) summed by one
+// thread, and the smaller accumulator count used when no row is longer. The pattern build lists
+// the rows above the first and flags any row above the second.
+constexpr int FE_TET_RS_MAX = 32;
+constexpr int FE_TET_RS_SHORT = 16;
+
+// Expands a built scalar tetrahedral pattern into the 3-D elasticity structure (tetelas.cu).
+fe_status fe_tet_elas_structure(fe_tet_pattern p, cudaStream_t s);
 
 // P2 (quadratic) triangle patterns (p2.cu).
 struct fe_p2_pattern_s {

@@ -35,8 +35,8 @@ constexpr int FAST_EMAX = 42;                // fast rows: at most 42 tetrahedra
 constexpr int BIG_TS = 4096;                 // one warp per block for rows up to FE_TET_MAX_VALENCE
 constexpr int BIG_EMAX = FE_TET_MAX_VALENCE;
 constexpr int RS_BLOCK = 128;                // row sums: threads per block, one row each
-constexpr int RS_MAX = 32;                   // row sums: longest row summed by one thread (longer: one warp)
-constexpr int RS_SHORT = 16;                 // row sums: smaller accumulators when no row is longer (twice
+constexpr int RS_MAX = FE_TET_RS_MAX;        // row sums: longest row summed by one thread (longer: one warp)
+constexpr int RS_SHORT = FE_TET_RS_SHORT;    // row sums: smaller accumulators when no row is longer (twice
                                              // the resident blocks and more L1: 1.30 against 2.80 ms at 128^3)
 static_assert(3 * BIG_EMAX + 1 < BIG_TS, "the big-row table must hold every distinct id");
 static_assert(3 * FAST_EMAX + 1 < FAST_TS, "the fast-row table must hold every distinct id");
@@ -618,6 +618,7 @@ extern "C" void fe_tet_pattern_destroy(fe_tet_pattern p) {
     FeStreamScope scope(p->last_stream);
     fe_free(p->row_ptr); fe_free(p->col_idx); fe_free(p->map);
     fe_free(p->vptr); fe_free(p->inc); fe_free(p->islot); fe_free(p->long_rows); fe_free(p->n_long); fe_free(p->kg);
+    fe_free(p->row_ptr3); fe_free(p->col_idx3);
     delete p;
 }
 
@@ -660,7 +661,7 @@ extern "C" fe_status fe_tet_pattern_build(fe_tet_mesh m, int flags, fe_stream st
     cudaStream_t s = (cudaStream_t)stream;
     FeStreamScope scope(s);
     fe_tet_pattern p = new fe_tet_pattern_s();
-    p->flags = gather ? FE_PATTERN_GATHER : 0;
+    p->flags = (gather ? FE_PATTERN_GATHER : 0) | (flags & FE_TET_PATTERN_ELAS);
     p->nq = nq;
     p->nme = nme;
     p->topology_id = m->topology_id;
@@ -729,6 +730,7 @@ extern "C" fe_status fe_tet_pattern_build(fe_tet_mesh m, int flags, fe_stream st
         p->vptr = t.vptr;
         t.vptr = nullptr;
     }
+    if ((flags & FE_TET_PATTERN_ELAS) && (st = fe_tet_elas_structure(p, s))) return fail(st);
     *out = p;
     return FE_OK;
 }

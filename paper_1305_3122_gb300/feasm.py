@@ -58,6 +58,8 @@ SIGNATURES = {
     "fe_tet_pattern_map": (_INT, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
     "fe_tet_pattern_destroy": (None, [_P]),
     "fe_tet_assemble": (_INT, [_P, _P, _INT, _P, _INT, _P, _I64, _P]),
+    "fe_tet_pattern_elas_info": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "fe_tet_assemble_elas": (_INT, [_P, _P, _D, _D, _INT, _P, _I64, _P]),
     "fe_p2_pattern_build": (_INT, [_P, _P, _INT, _P, ctypes.POINTER(_P)]),
     "fe_p2_pattern_info": (_INT, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "fe_p2_pattern_dofs": (_INT, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
@@ -330,6 +332,7 @@ def _values(pattern: Pattern, out: torch.Tensor | None) -> torch.Tensor:
 
 
 TET_MASS, TET_WMASS, TET_STIFF = 0, 1, 2
+TET_PATTERN_ELAS = 4
 
 
 class TetMesh:
@@ -374,15 +377,24 @@ class TetMesh:
 
 
 class TetPattern:
-    """CSR structure and element-to-nnz map (map[16k + 4 il + jl]) of a tetrahedral mesh."""
+    """CSR structure and element-to-nnz map (map[16k + 4 il + jl]) of a tetrahedral mesh; with
+    elas=True also the 3-D elasticity structure (rows 3i + s): elas_row_ptr, elas_col_idx."""
 
-    def __init__(self, mesh: TetMesh, gather: bool = False, stream=None):
+    def __init__(self, mesh: TetMesh, gather: bool = False, stream=None, elas: bool = False):
         h = _P()
-        _check(lib().fe_tet_pattern_build(mesh.handle, PATTERN_GATHER if gather else 0, _stream(stream), ctypes.byref(h)),
-               "fe_tet_pattern_build")
+        flags = (PATTERN_GATHER if gather else 0) | (TET_PATTERN_ELAS if elas else 0)
+        _check(lib().fe_tet_pattern_build(mesh.handle, flags, _stream(stream), ctypes.byref(h)), "fe_tet_pattern_build")
         self._h = h
         self.mesh = mesh
         self.gather = gather
+        self.elas = elas
+        if elas:
+            n3, z3, rp3, ci3 = _I64(), _I64(), _P(), _P()
+            _check(lib().fe_tet_pattern_elas_info(h, ctypes.byref(n3), ctypes.byref(z3), ctypes.byref(rp3), ctypes.byref(ci3)),
+                   "fe_tet_pattern_elas_info")
+            self.elas_n_rows, self.elas_nnz = n3.value, z3.value
+            self.elas_row_ptr = _view_i32(rp3.value, self.elas_n_rows + 1, self)
+            self.elas_col_idx = _view_i32(ci3.value, self.elas_nnz, self)
         n_rows, nnz, rp, ci = _I64(), _I64(), _P(), _P()
         _check(lib().fe_tet_pattern_info(h, ctypes.byref(n_rows), ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci)),
                "fe_tet_pattern_info")
@@ -418,6 +430,20 @@ def tet_assemble(mesh: TetMesh, pattern: TetPattern, kind: int, w: torch.Tensor 
         raise ValueError("out must be a contiguous float64 CUDA tensor")
     _check(lib().fe_tet_assemble(mesh.handle, pattern.handle, kind, _dptr(w, torch.float64, "w"), variant,
                                  out.data_ptr(), out.numel(), _stream(stream)), "fe_tet_assemble")
+    return out
+
+
+def tet_assemble_elas(mesh: TetMesh, pattern: TetPattern, lam: float, mu: float, variant: int = ATOMIC, out=None,
+                      stream=None) -> torch.Tensor:
+    """Values of the 3-D elasticity matrix (dofs 3v + s) on the pattern's elasticity structure
+    (fe_tet_assemble_elas; the pattern needs elas=True, and gather=True for GATHER)."""
+    if not getattr(pattern, "elas", False):
+        raise ValueError("the pattern was built without elas=True")
+    out = torch.empty(pattern.elas_nnz, dtype=torch.float64, device="cuda") if out is None else out
+    if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 CUDA tensor")
+    _check(lib().fe_tet_assemble_elas(mesh.handle, pattern.handle, float(lam), float(mu), variant, out.data_ptr(),
+                                      out.numel(), _stream(stream)), "fe_tet_assemble_elas")
     return out
 
 

@@ -48,6 +48,7 @@ class _Fixtures:
         self.part = feasm.Mesh.part(m.q, m.me, 20, 90)
         self.part_pat = feasm.Pattern(self.part, rows=(20, 90))
         self.p3 = feasm.P3Pattern(self.mesh, self.pat, gather=True)
+        self.tpat_e = feasm.TetPattern(self.tmesh, gather=True, elas=True)
 
 
 def _scenarios(fx: _Fixtures) -> dict:
@@ -84,6 +85,9 @@ def _scenarios(fx: _Fixtures) -> dict:
         "p3_pattern": lambda: feasm.P3Pattern(fx.mesh, fx.pat, gather=True),
         "p3_gather": lambda: feasm.p3_assemble(fx.mesh, fx.p3, feasm.P3_STIFF, variant=feasm.GATHER),
         "p3_atomic": lambda: feasm.p3_assemble(fx.mesh, fx.p3, feasm.P3_MASS, variant=feasm.ATOMIC),
+        "tet_pattern_elas": lambda: feasm.TetPattern(fx.tmesh, gather=True, elas=True),
+        "tet_elas_gather": lambda: feasm.tet_assemble_elas(fx.tmesh, fx.tpat_e, 1.25, 0.4, feasm.GATHER),
+        "tet_elas_atomic": lambda: feasm.tet_assemble_elas(fx.tmesh, fx.tpat_e, 1.25, 0.4, feasm.ATOMIC),
     }
 
 
@@ -121,10 +125,11 @@ def _fx() -> _Fixtures:
 NAMES = ["mesh", "pattern", "pattern_gather", "pattern_dofs2", "assemble_row", "assemble_atomic", "assemble_gather",
          "elasticity", "adjoint_gather", "adjoint_atomic", "drop_zeros", "tet_mesh", "tet_pattern", "tet_gather",
          "p2_pattern", "p2_gather", "host_call", "batch", "mesh_part", "pattern_part", "assemble_part", "p3_pattern",
-         "p3_gather", "p3_atomic"]
+         "p3_gather", "p3_atomic", "tet_pattern_elas", "tet_elas_gather", "tet_elas_atomic"]
 # calls that certainly allocate device memory (assembly calls may work in the pattern's buffers)
 ALLOCATING = {"mesh", "pattern", "pattern_gather", "pattern_dofs2", "drop_zeros", "tet_mesh", "tet_pattern",
-              "p2_pattern", "host_call", "batch", "mesh_part", "pattern_part", "p3_pattern"}
+              "p2_pattern", "host_call", "batch", "mesh_part", "pattern_part", "p3_pattern", "tet_pattern_elas",
+              "tet_elas_gather"}
 
 
 @pytest.mark.parametrize("name", NAMES)

@@ -65,6 +65,13 @@ tp = feasm.TetPattern(tm, gather=True)
 rpt, _, vt = oracle.tet_assemble(oracle.STIFF, t.q, t.me)
 for v in (feasm.ATOMIC, feasm.GATHER):
     assert_values_close(rpt, feasm.tet_assemble(tm, tp, feasm.TET_STIFF, None, v).cpu().numpy(), vt)
+from tests.test_gpu_tet import star_mesh
+for tq, tme in ((t.q, t.me), star_mesh(20), star_mesh(40)):
+    em = feasm.TetMesh(tq, tme)
+    ep = feasm.TetPattern(em, gather=True, elas=True)
+    rpe, _, ve = oracle.tet_elas_assemble(tq, tme, 1.25, 0.4)
+    for v in (feasm.ATOMIC, feasm.GATHER):
+        assert_values_close(rpe, feasm.tet_assemble_elas(em, ep, 1.25, 0.4, v).cpu().numpy(), ve)
 ms = [meshgen.square_mesh(n, 60 + n, random_diagonals=True) for n in (5, 12, 30)]
 fm = [feasm.Mesh(x.q, x.me) for x in ms]
 fp = [feasm.Pattern(x) for x in fm]
