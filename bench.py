@@ -621,16 +621,26 @@ def kernel_source_hash(name: str) -> str | None:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(name: str, cells: int, traffic_path: str | None):
-    """DRAM bytes per launch from an ncu capture of this kernel on this mesh size, or None when
-    none was recorded or the kernel's source changed since."""
+def recorded_counters(name: str, cells: int, traffic_path: str | None) -> dict:
+    """ncu counters of one launch of this kernel on this mesh size (DRAM bytes, and warp
+    instructions where recorded), or {} when none were recorded or the kernel's source changed
+    since."""
     if not traffic_path or not os.path.exists(traffic_path):
-        return None
+        return {}
     with open(traffic_path) as f:
         rec = json.load(f).get(name)
     if not isinstance(rec, dict) or rec.get("cells") != cells or rec.get("source") != kernel_source_hash(name):
-        return None
-    return rec.get("bytes")
+        return {}
+    return rec
+
+
+def recorded_traffic(name: str, cells: int, traffic_path: str | None):
+    """DRAM bytes per launch from an ncu capture of this kernel on this mesh size, or None."""
+    return recorded_counters(name, cells, traffic_path).get("bytes")
+
+
+# Issue roof: 4 warp instructions per SM per clock (one per scheduler), 152 SMs, 2.07 GHz.
+ISSUE_PEAK = 4 * 152 * 2.07e9
 
 
 # What limits a kernel below its HBM roof, from its ncu captures (profiles/).
@@ -653,6 +663,14 @@ def _roofline(name, nbytes, ms, hbm, peak_kind, traffic_path, cells=N_CELLS):
            "peak_source": f"{peak_kind} HBM copy bandwidth"}
     if name in LIMITS:
         out["limit"] = LIMITS[name]
+    inst = recorded_counters(name, cells, traffic_path).get("inst_executed")
+    if inst:
+        # the kernel's own bound: warp instructions per launch (ncu, same source and mesh size)
+        # over the launch time measured here, against the issue roof
+        rate = inst / (ms / 1e3)
+        out["issue"] = {"inst_per_launch": int(inst), "achieved": round(rate / 1e9, 1), "peak": round(ISSUE_PEAK / 1e9, 1),
+                        "unit": "G warp instr/s", "frac": round(rate / ISSUE_PEAK, 4),
+                        "peak_source": "4 warp instructions per SM per clock x 152 SMs x 2.07 GHz (maximum SM clock)"}
     return out
 
 
