@@ -16,7 +16,8 @@ the timed steps. Also reported:
     double-float on the FP32 pipes), and fp64_variants: the same step by the two variants whose
     element arithmetic is plain FP64 (staged gather, FP64 atomics);
   - per-kernel shares of the step, each with its algorithmic bytes and HBM fraction;
-  - unstructured: the same step on the random-diagonal 2048 x 2048 square (valences 4 to 8);
+  - unstructured: the same step on the random-diagonal 2048 x 2048 square (valences 4 to 8), and
+    disk: on a Delaunay mesh of the unit disk from 2^20 random points (valences 3 to about 20);
   - roofline of the dominant kernel, timed live with the library's own CUDA events;
   - the other legs: plane elasticity, the adjoint, zero dropping, tetrahedra, 3-D elasticity on
     tetrahedra, P2 and P3 triangles, each with both scatter variants where it has them;
@@ -498,6 +499,7 @@ def run_ours(args) -> int:
         line["fp64_variants"] = fp64_variants(feasm, torch, q_d, me_d, w_d, flush, stream, m)
     if not args.no_other and args.variant == "row" and args.cells == N_CELLS:
         line["unstructured"] = unstructured(feasm, meshgen, torch, flush, stream)
+        line["disk"] = disk(feasm, meshgen, torch, flush, stream)
     if not args.no_batched:
         line["batched"] = batched(feasm, meshgen, torch, args, hbm, peak_kind)
     if not args.no_other:
@@ -528,11 +530,9 @@ ARITH = {"row": "double-float (pairs of FP32, about 48-bit significands) element
          "gather": "fp64", "atomic": "fp64"}
 
 
-def unstructured(feasm, meshgen, torch, flush, stream, reps: int = 20) -> dict:
-    """The headline step (mesh, pattern, S + M^[w] by row owners) on the 2048 x 2048-cell square with
-    random cell diagonals: interior vertices in 4 to 8 triangles, as in unstructured meshes."""
-    m = meshgen.square_mesh(N_CELLS, SEED, random_diagonals=True)
-    w = meshgen.vertex_weights(m, SEED)
+def mesh_step(feasm, torch, flush, stream, m, w, reps: int = 20) -> dict:
+    """The headline step (mesh, pattern, S + M^[w] by row owners) on another mesh: its time (first
+    half of the steps, without the per-kernel events) and its kernels' times (second half)."""
     q_d, me_d, w_d = (torch.tensor(a, device="cuda") for a in (m.q, m.me, w))
     pat0 = feasm.Pattern(feasm.Mesh(q_d, me_d, borrow=True), map=False)
     S, M = pat0.new_values(), pat0.new_values()
@@ -565,9 +565,30 @@ def unstructured(feasm, meshgen, torch, flush, stream, reps: int = 20) -> dict:
     feasm.profile_enable(False)
     prof = feasm.profile_read()
     ms = sum(ts) / len(ts)
+    val = np.bincount(m.me.ravel(), minlength=m.nq)
+    return {"nnz": nnz, "ms_per_step": round(ms, 4), "value": round(m.nme / ms / 1e3, 3), "unit": UNIT,
+            "rows_over_8_triangles": round(float(np.mean(val > 8)), 5),
+            "kernels_ms": {k: round(v[0] / v[1], 4) for k, v in sorted(prof.items())}}
+
+
+def unstructured(feasm, meshgen, torch, flush, stream, reps: int = 20) -> dict:
+    """The headline step on the 2048 x 2048-cell square with random cell diagonals: interior
+    vertices in 4 to 8 triangles, as in unstructured meshes."""
+    m = meshgen.square_mesh(N_CELLS, SEED, random_diagonals=True)
+    r = mesh_step(feasm, torch, flush, stream, m, meshgen.vertex_weights(m, SEED), reps)
     return {"workload": f"S + M^[w], random-diagonal {N_CELLS}x{N_CELLS}-cell square (nq={m.nq}, nme={m.nme}, "
-                        f"nnz={nnz} per matrix)", "ms_per_step": round(ms, 4), "value": round(m.nme / ms / 1e3, 3),
-            "unit": UNIT, "kernels_ms": {k: round(v[0] / v[1], 4) for k, v in sorted(prof.items())}}
+                        f"nnz={r.pop('nnz')} per matrix)", **r}
+
+
+def disk(feasm, meshgen, torch, flush, stream, n: int = 1 << 20, reps: int = 20) -> dict:
+    """The headline step on a Delaunay mesh of the unit disk, the paper's domain, from random
+    points (valences 3 to about 20; about 4% of the rows are longer than 8 triangles and go to the
+    general-row kernel; thin slivers take the FP64 fan terms)."""
+    seed = SEED + 20
+    m = meshgen.disk_mesh(n, seed, points="poisson")
+    r = mesh_step(feasm, torch, flush, stream, m, meshgen.vertex_weights(m, seed), reps)
+    return {"workload": f"S + M^[w], Delaunay mesh of the unit disk from random points (nq={m.nq}, nme={m.nme}, "
+                        f"nnz={r.pop('nnz')} per matrix)", **r}
 
 
 def fp64_variants(feasm, torch, q_d, me_d, w_d, flush, stream, m, reps: int = 10) -> dict:

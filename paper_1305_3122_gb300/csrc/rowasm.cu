@@ -17,9 +17,12 @@
 // two contributions meet in a register carry and leave as one store. One thread per row, no
 // shared memory, each neighbour's coordinates loaded once. The arithmetic is double-float on
 // the FP32 pipes (ff.cuh) after an exact FP64 difference per coordinate and neighbour.
-// General rows (several chains, long fans, non-manifold) use one block per row: thread t owns
-// column t and adds, in the row's stored (sorted) triangle order, every contribution to its
-// column, converting each to FP64 and summing with Neumaier's compensated summation.
+// General rows (several chains, long fans, non-manifold) use one block per row. Each triangle's
+// contributions to its three columns are computed once (for rows of up to 256 triangles) and
+// converted to FP64. Thread t owns column t: an off-diagonal column adds its few contributions (at
+// most four, else by Neumaier's compensated summation) in the row's stored (sorted) triangle
+// order, and the diagonal's d contributions are added by a fixed-shape pairwise tree over the
+// block.
 // Both paths fix the order of every sum, so the result is bit-identical from run to run.
 #include "ff.cuh"
 #include "internal.cuh"
@@ -32,7 +35,6 @@ struct Consts {
     ff c60, c12, c24, c120;     // 1/60, 1/12, 1/24, 1/120 as double-floats
     ff l2m, lam, mu;            // lambda + 2 mu, lambda, mu (elasticity)
     double d60, d12, d24;       // the same in FP64 (general rows)
-    double dl2m, dlam, dmu;     // elasticity constants in FP64 (badly shaped triangles)
 };
 
 // A neighbour of the row's vertex: relative coordinates r = p - p_i and weight as double-floats,
@@ -54,35 +56,21 @@ struct RowTerms {
     ff w[3];       // unscaled M^w entries: D (s + 2 w_i), D (s - w_l / 2), D (s - w_j / 2)
 };
 
-// FP64 version of row_terms for badly shaped triangles (an angle below about 14.5 degrees),
-// where the double-float path would lose too many bits to cancellation. Rare, so the FP64
-// pipe's low rate does not matter; the results are split back into double-floats.
-template <int KIND>
-__device__ __noinline__ RowTerms row_terms_fp64(const double2* __restrict__ q, const double* __restrict__ w, int32_t i,
-                                                int32_t j, int32_t l, int& bad) {
-    RowTerms t;
-    double2 pi = q[i], pj = q[j], pl = q[l];
-    double eax = pj.x - pl.x, eay = pj.y - pl.y;      // e_a
-    double e1x = pl.x - pi.x, e1y = pl.y - pi.y;      // e_{a+1} = r_l
-    double e2x = pi.x - pj.x, e2y = pi.y - pj.y;      // e_{a+2} = -r_j
-    double D = e1x * e2y - e2x * e1y;
-    t.d = ff_from_value(D, bad);
-    if (KIND & W_S) {
-        double inv = 1.0 / (2.0 * D);
-        t.s[0] = ff_from_value((eax * eax + eay * eay) * inv, bad);
-        t.s[1] = ff_from_value((eax * e1x + eay * e1y) * inv, bad);
-        t.s[2] = ff_from_value((eax * e2x + eay * e2y) * inv, bad);
-    }
-    if (KIND & W_W) {
-        double wi = w[i], wj = w[j], wl = w[l];
-        double s = wi + wj + wl;
-        t.w[0] = ff_from_value(D * (s + 2.0 * wi), bad);
-        t.w[1] = ff_from_value(D * (s - 0.5 * wl), bad);
-        t.w[2] = ff_from_value(D * (s - 0.5 * wj), bad);
-    }
-    return t;
+// A badly shaped triangle (i, c, n) (an angle below about 14.5 degrees): the two quantities that
+// double-float arithmetic on the split relative coordinates would get wrong by too much, D =
+// r_c x r_n (a cancelling difference of products) and the edge e_a = p_c - p_n (a difference of
+// nearly equal vectors when the angle at i is small), come from FP64 coordinate differences (each
+// correctly rounded) and are then split; the dot products and 1/2D that use them stay in
+// double-float, where they lose nothing to the triangle's shape. 8 FP64 instructions, against about
+// 40 (with a division) for the same terms entirely in FP64.
+__device__ __noinline__ void thin_terms(const double2* __restrict__ q, int32_t i, int32_t c, int32_t n, ff& D, ff& ax,
+                                        ff& ay, int& bad) {
+    const double2 pi = q[i], pc = q[c], pn = q[n];
+    const double cx = pc.x - pi.x, cy = pc.y - pi.y, nx = pn.x - pi.x, ny = pn.y - pi.y;
+    D = ff_from_value(fma(cx, ny, -(cy * nx)), bad);
+    ax = ff_from_double(pc.x - pn.x, bad);
+    ay = ff_from_double(pc.y - pn.y, bad);
 }
-
 
 // Shape test: sin^2 of each angle is D^2 over the product of the two adjacent squared edges;
 // all three must be at least 1/16 (angles of at least about 14.5 degrees) for the fast path.
@@ -98,10 +86,10 @@ __device__ __forceinline__ RowTerms row_terms(const double2* __restrict__ q, con
                                               const Nb& j, const Nb& l, ff wi, int& bad) {
     RowTerms t;
     t.d = ff_dot2(j.x, l.x, l.y, ff_neg(j.y));                  // r_j x r_l
-    if (!well_shaped(j, l, t.d.h)) return row_terms_fp64<KIND>(q, w, i, j.id, l.id, bad);
+    ff ax = ff_sub(j.x, l.x), ay = ff_sub(j.y, l.y);            // e_a = r_j - r_l
+    if (!well_shaped(j, l, t.d.h)) thin_terms(q, i, j.id, l.id, t.d, ax, ay, bad);
     if (KIND & W_S) {
         ff inv = ff_mulf(ff_rcp_fast(t.d), 0.5f);              // 1 / 2D
-        ff ax = ff_sub(j.x, l.x), ay = ff_sub(j.y, l.y);        // e_a = r_j - r_l
         t.s[1] = ff_mul(ff_dot2(ax, ay, l.x, l.y), inv);        // e_a . r_l
         t.s[2] = ff_neg(ff_mul(ff_dot2(ax, ay, j.x, j.y), inv)); // e_a . (-r_j)
     }
@@ -262,19 +250,6 @@ __device__ __forceinline__ bool fan_well_shaped(const FanNb& c, const FanNb& n, 
     return d2 >= c.n * n.n && d2 >= eaa * n.n && d2 >= eaa * c.n;
 }
 
-// FP64 stiffness terms of a badly shaped triangle (i, c, n): D and the two half-cotangent terms.
-__device__ __noinline__ void fan_terms_fp64(const double2* __restrict__ q, int32_t i, int32_t c, int32_t n, ff& D,
-                                            ff& sc, ff& sn, int& bad) {
-    double2 pi = q[i], pc = q[c], pn = q[n];
-    double cx = pc.x - pi.x, cy = pc.y - pi.y, nx = pn.x - pi.x, ny = pn.y - pi.y;
-    double ax = pc.x - pn.x, ay = pc.y - pn.y;           // e_a
-    double d = cx * ny - cy * nx;
-    double inv = 0.5 / d;
-    D = ff_from_value(d, bad);
-    sc = ff_from_value((ax * nx + ay * ny) * inv, bad);
-    sn = ff_from_value(-(ax * cx + ay * cy) * inv, bad);
-}
-
 // FP64 value of a row entry.
 __device__ __forceinline__ void put(double* __restrict__ out, int32_t at, ff v) { out[at] = ff_to_double(v); }
 
@@ -338,16 +313,13 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
         FanNb nxt = fan_nb<KIND>(rn, pi, bad);
         ff D = ff_dot2(cur.x, nxt.x, nxt.y, ff_neg(cur.y));          // r_c x r_n
         ff ax = ff_sub(cur.x, nxt.x), ay = ff_sub(cur.y, nxt.y);      // e_a
+        if (!fan_well_shaped(cur, nxt, ax.h, ay.h, D.h)) thin_terms(q, i, cur.id, nxt.id, D, ax, ay, bad);
         ff sc = z_ff(), sn = z_ff();
-        if (fan_well_shaped(cur, nxt, ax.h, ay.h, D.h)) {
-            if (DS) {
-                ff inv = ff_rcp_fast(D);
-                inv = ff{0.5f * inv.h, 0.5f * inv.l};               // 1 / 2D
-                sc = ff_mul(ff_dot2(ax, ay, nxt.x, nxt.y), inv);
-                sn = ff_neg(ff_mul(ff_dot2(ax, ay, cur.x, cur.y), inv));
-            }
-        } else {
-            fan_terms_fp64(q, i, cur.id, nxt.id, D, sc, sn, bad);
+        if (DS) {
+            ff inv = ff_rcp_fast(D);
+            inv = ff{0.5f * inv.h, 0.5f * inv.l};                   // 1 / 2D
+            sc = ff_mul(ff_dot2(ax, ay, nxt.x, nxt.y), inv);
+            sn = ff_neg(ff_mul(ff_dot2(ax, ay, cur.x, cur.y), inv));
         }
         orient |= !(D.h > 0.f);
         ff A = z_ff(), B = z_ff();
@@ -433,6 +405,12 @@ __device__ __forceinline__ void neumaier(double& sum, double& c, double v) {
 }
 
 // One general row, by one block: thread t owns column t of the row.
+// Triangles of a general row whose terms are computed once into shared memory (longer rows
+// recompute each triangle's terms in every thread that needs them), and the general-row block
+// size (a power of two, for the diagonal's tree sum).
+constexpr int GEN_SMEM_TRIS = 256;
+constexpr int GEN_BLOCK_MAX = 64;
+
 template <int KIND>
 __device__ __forceinline__ void general_row(int32_t i, const int32_t* __restrict__ row_ptr,
                                             const int32_t* __restrict__ col_idx, const int32_t* __restrict__ vptr,
@@ -444,6 +422,99 @@ __device__ __forceinline__ void general_row(int32_t i, const int32_t* __restrict
     int32_t b0 = vptr[i], d = vptr[i + 1] - b0;
     double2 pi = q[i];
     ff wi = (KIND & W_W) ? ff_from_double(w[i], bad) : ff_make(0.f);
+    if (d <= GEN_SMEM_TRIS) {
+        // each triangle's contributions to its three columns (self, j, l), as the FP64 values the
+        // sums below take, computed once by one thread; then thread t adds those of its column
+        // in the stored triangle order, exactly as the loop further down does
+        __shared__ int2 sp[GEN_SMEM_TRIS];
+        __shared__ double sv[TWO ? 2 : 1][3][GEN_SMEM_TRIS];
+        for (int e = threadIdx.x; e < d; e += blockDim.x) {
+            int2 p = fan[b0 + e];
+            sp[e] = p;
+            Nb j = load_nb<KIND>(q, w, pi, p.x, 0, bad), l = load_nb<KIND>(q, w, pi, p.y, 0, bad);
+            RowTerms rt = row_terms<KIND>(q, w, i, j, l, wi, bad);
+            orient |= !(rt.d.h > 0.f);
+            if (KIND & W_S) rt.s[0] = ff_neg(ff_add(rt.s[1], rt.s[2]));
+#pragma unroll
+            for (int which = 0; which < 3; which++) {
+                ff v0, v1;
+                pick<KIND>(rt, which, v0, v1);
+                sv[0][which][e] = ff_to_double(v0);
+                if (TWO) sv[TWO ? 1 : 0][which][e] = ff_to_double(v1);
+            }
+        }
+        __syncthreads();
+        // the diagonal's d terms: each thread adds its strided terms in order, then a pairwise
+        // tree over the threads (a fixed shape, so the same bits every run; FP64 error at most
+        // about log2(d) 2^-53 of the sum of |terms|)
+        __shared__ double red[TWO ? 2 : 1][GEN_BLOCK_MAX];
+        {
+            double a0 = 0.0, a1 = 0.0;
+            for (int e = threadIdx.x; e < d; e += blockDim.x) {
+                a0 += sv[0][0][e];
+                if (TWO) a1 += sv[TWO ? 1 : 0][0][e];
+            }
+            red[0][threadIdx.x] = a0;
+            if (TWO) red[TWO ? 1 : 0][threadIdx.x] = a1;
+            __syncthreads();
+            for (int h = blockDim.x / 2; h > 0; h /= 2) {
+                if (threadIdx.x < h) {
+                    red[0][threadIdx.x] += red[0][threadIdx.x + h];
+                    if (TWO) red[TWO ? 1 : 0][threadIdx.x] += red[TWO ? 1 : 0][threadIdx.x + h];
+                }
+                __syncthreads();
+            }
+        }
+        for (int t = threadIdx.x; t < u; t += blockDim.x) {
+            int32_t col = col_idx[rb + t];
+            bool self = col == i;
+            double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
+            if (self) {
+                s0 = red[0][0];
+                if (TWO) s1 = red[TWO ? 1 : 0][0];
+            } else {
+                // an off-diagonal column takes one term from each triangle on its edge: two for an
+                // interior edge of a manifold mesh. Up to four are found by integer compares and
+                // added in stored order by the same plain FP64 additions in every thread (absent
+                // terms are zeros), so the FP64 instructions do not diverge; error at most
+                // 3 * 2^-53 of the sum of |terms|. More (an edge of more than four triangles)
+                // take the compensated sum over all of them.
+                int p0 = -1, p1 = -1, p2 = -1, p3 = -1, n = 0;
+                for (int32_t e = 0; e < d; e++) {
+                    int2 p = sp[e];
+                    int which = p.x == col ? 1 : (p.y == col ? 2 : -1);
+                    if (which < 0) continue;
+                    int code = 3 * e + which;
+                    p0 = n == 0 ? code : p0;
+                    p1 = n == 1 ? code : p1;
+                    p2 = n == 2 ? code : p2;
+                    p3 = n == 3 ? code : p3;
+                    n++;
+                }
+                if (n <= 4) {
+                    auto term = [&](int code, int m) { return code < 0 ? 0.0 : sv[m][code % 3][code / 3]; };
+                    s0 = ((term(p0, 0) + term(p1, 0)) + term(p2, 0)) + term(p3, 0);
+                    if (TWO) s1 = ((term(p0, TWO ? 1 : 0) + term(p1, TWO ? 1 : 0)) + term(p2, TWO ? 1 : 0)) + term(p3, TWO ? 1 : 0);
+                } else {
+                    for (int32_t e = 0; e < d; e++) {
+                        int2 p = sp[e];
+                        int which = p.x == col ? 1 : (p.y == col ? 2 : -1);
+                        if (which < 0) continue;
+                        neumaier(s0, c0, sv[0][which][e]);
+                        if (TWO) neumaier(s1, c1, sv[TWO ? 1 : 0][which][e]);
+                    }
+                }
+            }
+            double v = s0 + c0;
+            if (KIND == W_M) v *= self ? cs.d12 : cs.d24;
+            if (KIND == W_W) v *= cs.d60;
+            const double scale1 = (KIND & W_W) ? cs.d60 : (self ? cs.d12 : cs.d24);
+            out0[rb + t] = v;
+            if (TWO) out1[rb + t] = (s1 + c1) * scale1;
+        }
+        __syncthreads();
+        return;
+    }
     for (int t = threadIdx.x; t < u; t += blockDim.x) {
         int32_t col = col_idx[rb + t];
         bool self = col == i;
@@ -548,26 +619,6 @@ __device__ __forceinline__ Block2 elas_block(ff ax, ff ay, ff bx, ff by, const C
     return k;
 }
 
-__device__ __noinline__ ff elas_terms_fp64(const double2* __restrict__ q, int32_t i, int32_t j, int32_t l,
-                                           const Consts& cs, Block2 out[3], int& bad) {
-    double2 pi = q[i], pj = q[j], pl = q[l];
-    double eax = pj.x - pl.x, eay = pj.y - pl.y;
-    double e1x = pl.x - pi.x, e1y = pl.y - pi.y;      // e_{a+1} = r_l
-    double e2x = pi.x - pj.x, e2y = pi.y - pj.y;      // e_{a+2} = -r_j
-    double D = e1x * e2y - e2x * e1y;
-    double r = 1.0 / (2.0 * D);
-    double ax = r * eax, ay = r * eay;
-    double bx[3] = {eax, e1x, e2x}, by[3] = {eay, e1y, e2y};
-    double l2m = cs.dl2m, lam = cs.dlam, mu = cs.dmu;
-    for (int b = 0; b < 3; b++) {
-        out[b].k00 = ff_from_value(l2m * ay * by[b] + mu * ax * bx[b], bad);
-        out[b].k01 = ff_from_value(-(lam * ay * bx[b] + mu * ax * by[b]), bad);
-        out[b].k10 = ff_from_value(-(lam * ax * by[b] + mu * ay * bx[b]), bad);
-        out[b].k11 = ff_from_value(l2m * ax * bx[b] + mu * ay * by[b], bad);
-    }
-    return ff_from_value(D, bad);
-}
-
 // The three 2 x 2 blocks of triangle (i, j, l) in row i: out[0] (column i), out[1] (column j),
 // out[2] (column l). (Row owners of simple rows compute only the last two: K annihilates the
 // translations, since the gradients of a triangle's basis functions sum to zero, so each 2 x 2
@@ -575,9 +626,9 @@ __device__ __noinline__ ff elas_terms_fp64(const double2* __restrict__ q, int32_
 __device__ __forceinline__ ff elas_terms(const double2* __restrict__ q, int32_t i, const Nb& j, const Nb& l,
                                          const Consts& cs, Block2 out[3], int& bad) {
     ff D = ff_dot2(j.x, l.x, l.y, ff_neg(j.y));
-    if (!well_shaped(j, l, D.h)) return elas_terms_fp64(q, i, j.id, l.id, cs, out, bad);
-    ff r = ff_mulf(ff_rcp_fast(D), 0.5f);
     ff eax = ff_sub(j.x, l.x), eay = ff_sub(j.y, l.y);
+    if (!well_shaped(j, l, D.h)) thin_terms(q, i, j.id, l.id, D, eax, eay, bad);
+    ff r = ff_mulf(ff_rcp_fast(D), 0.5f);
     ff sax = ff_mul(eax, r), say = ff_mul(eay, r);
     out[0] = elas_block(sax, say, eax, eay, cs);
     out[1] = elas_block(sax, say, l.x, l.y, cs);
@@ -632,22 +683,14 @@ __global__ void __launch_bounds__(256, 2) k_fan_elas(const int32_t* __restrict__
                 recn = e + 3 < d ? fan_rec(fan, b0 + e + 3, lim) : last;
             }
             Nb nxt = make_nb<0>(rn, pi, bad);
-            // the blocks of columns n_e and n_{e+1}; the FP64 path (badly shaped triangles) fills a
-            // stack array, the fast path stays in registers
-            Block2 kc, kn;
+            // the blocks of columns n_e and n_{e+1} (D and e_a from FP64 for badly shaped triangles)
             ff D = ff_dot2(cur.x, nxt.x, nxt.y, ff_neg(cur.y));
-            if (well_shaped(cur, nxt, D.h)) {
-                ff rr = ff_mulf(ff_rcp_fast(D), 0.5f);
-                ff eax = ff_sub(cur.x, nxt.x), eay = ff_sub(cur.y, nxt.y);
-                ff sax = ff_mul(eax, rr), say = ff_mul(eay, rr);
-                kc = elas_block(sax, say, nxt.x, nxt.y, cs);
-                kn = elas_block(sax, say, ff_neg(cur.x), ff_neg(cur.y), cs);
-            } else {
-                Block2 k[3];
-                D = elas_terms_fp64(q, i, cur.id, nxt.id, cs, k, bad);
-                kc = k[1];
-                kn = k[2];
-            }
+            ff eax = ff_sub(cur.x, nxt.x), eay = ff_sub(cur.y, nxt.y);
+            if (!well_shaped(cur, nxt, D.h)) thin_terms(q, i, cur.id, nxt.id, D, eax, eay, bad);
+            ff rr = ff_mulf(ff_rcp_fast(D), 0.5f);
+            ff sax = ff_mul(eax, rr), say = ff_mul(eay, rr);
+            Block2 kc = elas_block(sax, say, nxt.x, nxt.y, cs);
+            Block2 kn = elas_block(sax, say, ff_neg(cur.x), ff_neg(cur.y), cs);
             orient |= !(D.h > 0.f);
             if (e == 0) {
                 fs = kc;
@@ -731,15 +774,12 @@ static Consts make_consts(double lam, double mu) {
     c.d60 = 1.0 / 60.0;
     c.d12 = 1.0 / 12.0;
     c.d24 = 1.0 / 24.0;
-    c.dl2m = lam + 2.0 * mu;
-    c.dlam = lam;
-    c.dmu = mu;
     return c;
 }
 
 static constexpr int FAN_BLOCK = 256;
 static constexpr int FAN_SCALAR_BLOCK = 128;
-static constexpr int GEN_BLOCK = 64;
+static constexpr int GEN_BLOCK = GEN_BLOCK_MAX;
 
 template <int KIND>
 static fe_status launch_scalar(fe_mesh m, fe_pattern p, const double* w, double* out0, double* out1, cudaStream_t s) {

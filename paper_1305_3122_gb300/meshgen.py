@@ -29,6 +29,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 
 # stream ids (one per purpose, so that changing one draw never shifts another)
 S_JITTER_X, S_JITTER_Y, S_PERM, S_WNOISE, S_SIZES, S_GRAD_S, S_GRAD_M, S_SAMPLE, S_JITTER_Z, S_DIAG = range(1, 11)
+S_DISK_A, S_DISK_B = range(11, 13)
 
 # seeds of the standard workloads: SEED_BASE + 1 mass on 64 x 64 cells, + 2 stiffness and weighted
 # mass on 2048 x 2048, + 3 elasticity on 1024 x 1024, + 4 the batch of 256 meshes, + 5 the
@@ -218,6 +219,72 @@ def cube_mesh(N: int, seed: int, jitter: float = 0.05, permute: bool = True) -> 
         q = qp
         me = newid[me]
     return Mesh(q=np.ascontiguousarray(q), me=np.ascontiguousarray(me.astype(np.int32)), N=N)
+
+
+def disk_mesh(n: int, seed: int, points: str = "poisson", permute: bool = True) -> Mesh:
+    """The unit disk, the paper's test domain (its meshes come from FreeFEM++'s Delaunay mesher),
+    triangulated by Delaunay with about ``n`` vertices.
+
+    Points: ``nb = round(2 pi / h)`` on the unit circle at equal angles, where
+    ``h = sqrt(2 pi / (sqrt(3) n))`` is the spacing of a hexagonal lattice of ``n`` points in the
+    disk, and interior points:
+      - ``points="poisson"``: ``n - nb`` points uniform in the disk of radius ``1 - h/2``
+        (valences 3 to about 20, about 4% of the vertices in more than 8 triangles);
+      - ``points="lattice"``: the hexagonal lattice of spacing ``h`` inside radius ``1 - h/2``,
+        each point moved by up to ``0.15 h`` per coordinate (valence 6 almost everywhere, like a
+        quality mesher's output).
+    Triangulation by ``scipy.spatial.Delaunay`` (Qhull), every triangle made counter-clockwise.
+    Triangles are put in scanline order of their centroids (rows of height h, then x), since a
+    mesher's output has that kind of locality, and the node ids are randomly permuted unless
+    ``permute=False``. ``N`` of the result is 0 (no cell grid)."""
+    from scipy.spatial import Delaunay
+
+    if n < 8:
+        raise ValueError("n must be >= 8")
+    h = math.sqrt(2.0 * math.pi / (math.sqrt(3.0) * n))
+    nb = max(8, int(round(2.0 * math.pi / h)))
+    t = 2.0 * math.pi * np.arange(nb) / nb
+    bnd = np.stack([np.cos(t), np.sin(t)], axis=1)
+    rmax = 1.0 - 0.5 * h
+    if points == "poisson":
+        k = max(n - nb, 1)
+        r = rmax * np.sqrt(stream_uniform(seed, S_DISK_A, k))
+        a = 2.0 * math.pi * stream_uniform(seed, S_DISK_B, k)
+        inner = np.stack([r * np.cos(a), r * np.sin(a)], axis=1)
+    elif points == "lattice":
+        dy = h * math.sqrt(3.0) / 2.0
+        rows = []
+        for j in range(-int(1.0 / dy) - 1, int(1.0 / dy) + 2):
+            xs = np.arange(-int(1.0 / h) - 1, int(1.0 / h) + 2) * h + (0.5 * h if j % 2 else 0.0)
+            rows.append(np.stack([xs, np.full_like(xs, j * dy)], axis=1))
+        inner = np.concatenate(rows)
+        inner = inner[(inner ** 2).sum(axis=1) < rmax * rmax]
+        k = inner.shape[0]
+        inner = inner + (2.0 * np.stack([stream_uniform(seed, S_DISK_A, k), stream_uniform(seed, S_DISK_B, k)], axis=1)
+                         - 1.0) * (0.15 * h)
+    else:
+        raise ValueError("points must be 'poisson' or 'lattice'")
+    P = np.concatenate([bnd, inner])
+    tri = np.asarray(Delaunay(P).simplices, dtype=np.int64)
+    a, b, c = P[tri[:, 0]], P[tri[:, 1]], P[tri[:, 2]]
+    d = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (c[:, 0] - a[:, 0]) * (b[:, 1] - a[:, 1])
+    if not (np.abs(d) > 1e-12 * h * h).all():
+        raise RuntimeError("degenerate triangle in the Delaunay triangulation")
+    flip = d < 0
+    tri[flip, 1], tri[flip, 2] = tri[flip, 2].copy(), tri[flip, 1].copy()
+    cen = (a + b + c) / 3.0
+    order = np.lexsort((cen[:, 0], np.floor((cen[:, 1] + 1.0) / h)))
+    tri = tri[order]
+    nq = P.shape[0]
+    if permute:
+        perm = random_permutation(seed, S_PERM, nq)
+        q = np.empty((2, nq))
+        q[:, perm] = P.T
+        me = perm[tri.T]
+    else:
+        q = P.T.copy()
+        me = tri.T
+    return Mesh(q=np.ascontiguousarray(q), me=np.ascontiguousarray(me.astype(np.int32)), N=0)
 
 
 def vertex_weights3(mesh: Mesh, seed: int) -> np.ndarray:

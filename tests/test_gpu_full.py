@@ -127,6 +127,46 @@ def test_stiff_wmass_2048_unstructured(mesh_2048_unstructured, variant):
     assert vm.sum() == pytest.approx(np.sum(D / 2 * (w[me[0]] + w[me[1]] + w[me[2]]) / 3), rel=1e-12)
 
 
+@pytest.fixture(scope="module")
+def disk_1m():
+    seed = meshgen.SEED_BASE + 20
+    m = meshgen.disk_mesh(1 << 20, seed, points="poisson")
+    return m, meshgen.vertex_weights(m, seed)
+
+
+@pytest.mark.parametrize("variant", [feasm.ATOMIC, feasm.GATHER, feasm.ROW])
+def test_stiff_wmass_disk_1m(disk_1m, variant):
+    """The Delaunay disk of 2^20 random points, as the benchmark's disk leg times it: sampled rows
+    (random ones, and rows of every valence from 3 to the largest, so the general-row kernel's
+    rows too) against the oracle; S 1 = 0 on every row; the M^[w] total."""
+    m, w = disk_1m
+    mesh = feasm.Mesh(m.q, m.me)
+    pat = feasm.Pattern(mesh, gather=(variant == feasm.GATHER), map=(variant == feasm.ATOMIC))
+    S, Mw = feasm.assemble_stiff_wmass(mesh, pat, torch.tensor(w, device="cuda"), variant)
+    torch.cuda.synchronize()
+    rp = pat.row_ptr.cpu().numpy()
+    ci = pat.col_idx.cpu().numpy()
+    val = np.bincount(m.me.ravel(), minlength=m.nq)
+    rows = set(int(r) for r in meshgen.sample_indices(8, 32, m.nq))
+    for v in range(3, int(val.max()) + 1):
+        rows |= set(int(r) for r in np.nonzero(val == v)[0][:2])
+    rows = sorted(rows)
+    vs, vm = S.cpu().numpy(), Mw.cpu().numpy()
+    for kind, va in ((oracle.STIFF, vs), (oracle.WMASS, vm)):
+        for r, (cols, vals) in zip(rows, oracle.csr_row_values(kind, m.q, m.me, rows, w)):
+            np.testing.assert_array_equal(ci[rp[r]:rp[r + 1]], cols)
+            assert np.abs(va[rp[r]:rp[r + 1]] - vals).max() <= ROW_TOL * np.abs(vals).max()
+    rows_t = torch.repeat_interleave(torch.arange(m.nq, device="cuda"), torch.diff(pat.row_ptr.long()))
+    rs = torch.zeros(m.nq, dtype=torch.float64, device="cuda").index_add_(0, rows_t, S)
+    rmax = torch.zeros(m.nq, dtype=torch.float64, device="cuda").index_reduce_(0, rows_t, S.abs(), "amax")
+    assert bool((rs.abs() <= 16 * ROW_TOL * rmax).all())
+    x, y = m.q
+    me = m.me
+    D = (x[me[2]] - x[me[0]]) * (y[me[0]] - y[me[1]]) - (x[me[0]] - x[me[1]]) * (y[me[2]] - y[me[0]])
+    assert vm.sum() == pytest.approx(np.sum(D / 2 * (w[me[0]] + w[me[1]] + w[me[2]]) / 3), rel=1e-12)
+    mesh.check()
+
+
 def test_mass_64_full_oracle():
     m = meshgen.square_mesh(64, meshgen.SEED_BASE + 1)
     mesh = feasm.Mesh(m.q, m.me)

@@ -72,8 +72,8 @@ def bowtie_mesh():
 def unstructured_cases():
     """Meshes beyond the valence-6 grid: random cell diagonals (closed fans of 4 to 8 triangles,
     open fans of 1 to 4), a hole (open fans around it, unused vertices, and a vertex where two
-    fans touch), and a stretched square (angles of about 4 to 168 degrees, so rows mix the
-    double-float and FP64 fan terms)."""
+    fans touch), a stretched square (angles of about 4 to 168 degrees, so rows mix the
+    double-float and FP64 fan terms), the bow-tie, and Delaunay meshes of the unit disk."""
     out = {}
     m = meshgen.square_mesh(40, 31, random_diagonals=True)
     out["rdiag40"] = (m.q, m.me)
@@ -84,6 +84,13 @@ def unstructured_cases():
     m = meshgen.square_mesh(64, 34, random_diagonals=True, hole=True, stretch=2.5)
     out["rdiag_hole_stretch64"] = (m.q, m.me)
     out["bowtie"] = bowtie_mesh()
+    # Delaunay meshes of the unit disk (the paper's domain): random points (valences 3 to about
+    # 13, rows of more than 8 triangles for the general-row kernel, thin slivers for the FP64 fan
+    # terms) and a jittered hexagonal lattice
+    m = meshgen.disk_mesh(3000, 35, points="poisson")
+    out["disk_poisson3000"] = (m.q, m.me)
+    m = meshgen.disk_mesh(900, 36, points="lattice")
+    out["disk_lattice900"] = (m.q, m.me)
     return out
 
 

@@ -159,3 +159,77 @@ def test_oracle_identities_on_random_diagonals(s):
     assert u @ _quad(rp, ci, va, u) == pytest.approx((b * b + c * c) * s, rel=1e-12)
     want = a * a * s + b * b * s ** 3 / 3 + c * c * s / 3 + a * b * s * s + a * c * s + b * c * s * s / 2
     assert u @ _quad(rpm, cim, vam, u) == pytest.approx(want, rel=1e-12)
+
+
+@pytest.mark.parametrize("points", ["poisson", "lattice"])
+def test_disk_meshes_are_valid_delaunay_triangulations(points):
+    """The unit-disk recipe: counter-clockwise triangles, a manifold mesh whose boundary edges are
+    exactly the nb chords of the circle, every vertex used, the empty-circumcircle property, and
+    the valences each point set promises."""
+    m = meshgen.disk_mesh(3000, 5, points=points, permute=False)
+    assert np.all(_signed_double_areas(m) > 0)
+    e = np.sort(np.concatenate([m.me[[0, 1]], m.me[[1, 2]], m.me[[2, 0]]], axis=1), axis=0)
+    ue, counts = np.unique(e, axis=1, return_counts=True)
+    assert set(counts.tolist()) <= {1, 2}
+    r = np.hypot(*m.q)
+    bnd = ue[:, counts == 1]
+    nb = int(np.sum(np.isclose(r, 1.0, rtol=0, atol=1e-15)))
+    assert bnd.shape[1] == nb and np.allclose(r[bnd], 1.0, rtol=0, atol=1e-15)
+    assert np.all(np.bincount(m.me.ravel(), minlength=m.nq) > 0)
+    # empty circumcircles (Delaunay): no vertex strictly inside any triangle's circumcircle
+    x, y = m.q
+    P = m.q[:, m.me]                                        # [2, 3, nme]
+    ax, ay, bx, by, cx, cy = P[0, 0], P[1, 0], P[0, 1], P[1, 1], P[0, 2], P[1, 2]
+    d = 2 * (ax * (by - cy) + bx * (cy - ay) + cx * (ay - by))
+    ux = ((ax * ax + ay * ay) * (by - cy) + (bx * bx + by * by) * (cy - ay) + (cx * cx + cy * cy) * (ay - by)) / d
+    uy = ((ax * ax + ay * ay) * (cx - bx) + (bx * bx + by * by) * (ax - cx) + (cx * cx + cy * cy) * (bx - ax)) / d
+    R2 = (ax - ux) ** 2 + (ay - uy) ** 2
+    for k in range(0, m.nme, 7):                            # a sample of the triangles
+        dist2 = (x - ux[k]) ** 2 + (y - uy[k]) ** 2
+        assert np.all(dist2 >= R2[k] * (1 - 1e-9))
+    val = np.bincount(m.me.ravel(), minlength=m.nq)
+    inner = r < 1 - 1e-12
+    if points == "lattice":
+        assert np.mean(val[inner] == 6) > 0.9
+    else:
+        assert 0.01 < np.mean(val > 8) < 0.1 and val.max() >= 10
+
+
+def test_oracle_identities_on_the_disk():
+    """On the disk recipe (a polygon with nb vertices on the unit circle): sum of M = its area
+    (nb/2) sin(2 pi/nb); S 1 = 0; u'Su = (b^2 + c^2) area for u = a + bx + cy; and x'Mx = the
+    integral of x^2 over the polygon, summed over its nb triangles from the centre."""
+    m = meshgen.disk_mesh(2000, 6, points="poisson")
+    nb = int(np.sum(np.isclose(np.hypot(*m.q), 1.0, rtol=0, atol=1e-15)))
+    area = nb / 2 * np.sin(2 * np.pi / nb)
+    rpm, cim, vam = oracle.assemble(oracle.MASS, m.q, m.me)
+    assert vam.sum() == pytest.approx(area, rel=1e-13)
+    rp, ci, va = oracle.assemble(oracle.STIFF, m.q, m.me)
+    rm = np.maximum.reduceat(np.abs(va), rp[:-1])
+    assert np.all(np.abs(_quad(rp, ci, va, np.ones(m.nq))) <= 1e-13 * rm)
+    a, b, c = 0.3, -1.7, 0.6
+    u = a + b * m.q[0] + c * m.q[1]
+    assert u @ _quad(rp, ci, va, u) == pytest.approx((b * b + c * c) * area, rel=1e-12)
+    # int x^2 over the polygon: the sum over its nb triangles (0, p_k, p_k+1) of |T|/6 (x_k^2 +
+    # x_k x_k+1 + x_k+1^2), the exact integral of a quadratic over a triangle with a vertex at 0
+    t = 2 * np.pi * np.arange(nb) / nb
+    xk, xk1 = np.cos(t), np.cos(t + 2 * np.pi / nb)
+    ix2 = np.sum(0.5 * np.sin(2 * np.pi / nb) / 6 * (xk * xk + xk * xk1 + xk1 * xk1))
+    x = m.q[0]
+    assert x @ _quad(rpm, cim, vam, x) == pytest.approx(ix2, rel=1e-12)
+
+
+def test_oracle_brute_force_on_a_small_disk():
+    """A Poisson disk of about 60 vertices (valences 3 to 9) against exact dense accumulation."""
+    m = meshgen.disk_mesh(60, 12, points="poisson")
+    w = meshgen.vertex_weights(m, 12)
+    pts = [(Fraction(float(m.q[0, i])), Fraction(float(m.q[1, i]))) for i in range(m.nq)]
+    tris = [tuple(int(v) for v in m.me[:, k]) for k in range(m.nme)]
+    wf = [Fraction(float(v)) for v in w]
+    for kind, name in ((oracle.MASS, "mass"), (oracle.WMASS, "wmass"), (oracle.STIFF, "stiff")):
+        rp, ci, va = oracle.assemble(kind, m.q, m.me, w)
+        G = exact_fe.assemble_dense(name, pts, tris, wf)
+        dense = oracle.csr_to_dense(rp, ci, va, m.nq)
+        want = np.array([[float(v) for v in row] for row in G])
+        for i in range(m.nq):
+            assert np.abs(dense[i] - want[i]).max() <= 1e-13 * np.abs(want[i]).max()
