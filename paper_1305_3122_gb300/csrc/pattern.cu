@@ -72,23 +72,6 @@ __device__ __forceinline__ void isort64(long long* x, int n) {
     }
 }
 
-// Sorted unique columns of row i into cols; returns their number.
-__device__ __forceinline__ int row_columns(int32_t i, int32_t beg, int32_t d, const int2* __restrict__ adj,
-                                           int32_t* cols) {
-    if (d == 0) return 0;   // a vertex in no triangle has an empty row
-    int n = 0;
-    cols[n++] = i;
-    for (int32_t s = 0; s < d; s++) {
-        int2 p = adj[beg + s];
-        cols[n++] = p.x;
-        cols[n++] = p.y;
-    }
-    isort32(cols, n);
-    int u = 0;
-    for (int t = 0; t < n; t++)
-        if (t == 0 || cols[t] != cols[t - 1]) cols[u++] = cols[t];
-    return u;
-}
 
 // ------------------------------------------------------------------ fans (simple rows)
 
@@ -216,14 +199,12 @@ __device__ __forceinline__ int32_t simple_row(int32_t i, int32_t beg, int n, con
 
 // Row analysis, once per row: the column count, and everything of the row that does not depend
 // on its CSR offset. Simple rows (one fan of at most FAN_MAX triangles): d + 1 entries (closed) or
-// d + 2 (open), fan records and header. General rows with at most FAST_DEG triangles: the count
-// of their sorted unique columns, their (j, l) pairs sorted lexicographically (a deterministic
-// order) and a place in the general-row list. Rows with more triangles are listed for the block
-// kernels. bucket: start of each vertex's bucket in adj (the same offsets as vptr).
+// d + 2 (open), fan records and header. Other rows are general: those of at most FAST_DEG
+// triangles are listed for one warp each, longer ones for one block each (k_row_big).
 __global__ void k_row_analyse(const int32_t* __restrict__ vptr, const int2* __restrict__ adj, int32_t nq,
                               int32_t* __restrict__ row_nnz, int2* __restrict__ fan, int2* __restrict__ hdr,
                               int32_t* __restrict__ big_list, int32_t* __restrict__ big_count,
-                              int32_t* __restrict__ gen_list, int32_t* __restrict__ gen_count, int* __restrict__ too_big) {
+                              int32_t* __restrict__ mid_list, int32_t* __restrict__ mid_count, int* __restrict__ too_big) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nq; r += (int64_t)gridDim.x * blockDim.x) {
         int32_t i = (int32_t)r;
         int32_t beg = vptr[i], d = vptr[i + 1] - beg;
@@ -259,27 +240,20 @@ __global__ void k_row_analyse(const int32_t* __restrict__ vptr, const int2* __re
             big_list[atomicAdd(big_count, 1)] = i;
             continue;
         }
-        int32_t cols[2 * FAST_DEG + 1];
-        row_nnz[i] = row_columns(i, beg, d, adj, cols);
-        long long key[FAST_DEG];
-        for (int32_t s = 0; s < d; s++) {
-            int2 p = adj[beg + s];
-            key[s] = ((long long)p.x << 32) | (unsigned)p.y;
-        }
-        isort64(key, d);
-        for (int32_t s = 0; s < d; s++) fan[beg + s] = make_int2((int32_t)(key[s] >> 32), (int32_t)(key[s] & 0xffffffffLL));
-        gen_list[atomicAdd(gen_count, 1)] = i;
+        // a medium general row: one warp of k_row_big does it (a lane sorting it here would hold
+        // up the other 31 rows of its warp)
+        mid_list[atomicAdd(mid_count, 1)] = i;
     }
 }
 
-// col_idx of the rows with at most FAST_DEG triangles, once the offsets are known: simple rows
-// from their fan records and header, general rows by sorting their columns again (they are
-// rare). The 32 rows of a warp own one contiguous range of col_idx: a warp of simple rows places
-// its entries in shared memory first and writes the range with coalesced stores (scattered
-// 4-byte stores made this pass L1-bound); a warp with a general row, or a range too long for
-// the staging area, writes directly.
+// col_idx of the simple rows, once the offsets are known, from their fan records and header
+// (general rows are placed by k_row_big). The 32 rows of a warp own one contiguous range of
+// col_idx: the warp places its entries in shared memory first and writes the range with coalesced
+// stores, leaving out the ranges of its general rows (scattered 4-byte stores made this pass
+// L1-bound); a range too long for the staging area is written directly.
 constexpr int CF_BLOCK = 256;
 constexpr int CF_STAGE = 32 * (FAN_MAX + 2);                    // entries per warp (simple rows)
+constexpr int32_t CF_SKIP = -1;                                  // a staged entry placed by another kernel
 
 __global__ void __launch_bounds__(CF_BLOCK) k_col_fill(const int32_t* __restrict__ vptr, const int2* __restrict__ adj,
                                                        int32_t nq, const int32_t* __restrict__ row_ptr,
@@ -305,14 +279,13 @@ __global__ void __launch_bounds__(CF_BLOCK) k_col_fill(const int32_t* __restrict
             d = vptr[i + 1] - beg;
         }
         const bool general = act && kind == KIND_GENERAL;
-        const unsigned any_general = __ballot_sync(0xffffffffu, general);
         // the warp's range [lo, hi): rows are consecutive, so it starts at lane 0's offset and ends
         // at the last active lane's end
         const unsigned active = __ballot_sync(0xffffffffu, act);
         const int last = active ? 31 - __clz(active) : 0;
         const int32_t lo = __shfl_sync(0xffffffffu, o, 0);
         const int32_t hi = __shfl_sync(0xffffffffu, e, last);
-        const bool staged = active && !any_general && hi - lo <= CF_STAGE;   // warp-uniform
+        const bool staged = active && hi - lo <= CF_STAGE;                   // warp-uniform
         auto put = [&](int32_t at, int32_t v) {
             at = o + FE_IDX(at - o, e - o);                  // a column position inside its row
             if (staged) st[at - lo] = v;
@@ -325,14 +298,17 @@ __global__ void __launch_bounds__(CF_BLOCK) k_col_fill(const int32_t* __restrict
                 int2 f = fan[beg + s];
                 put(o + f.y, f.x);
             }
-        } else if (general && d > 0 && d <= FAST_DEG) {
-            int32_t cols[2 * FAST_DEG + 1];
-            int u = row_columns(i, beg, d, adj, cols);
-            for (int t = 0; t < u; t++) col_idx[o + t] = cols[t];
+        } else if (general && staged) {
+            // a general row: k_row_big places its columns later, so its range is marked to be
+            // left out of the warp's copy
+            for (int32_t t = o; t < e; t++) st[t - lo] = CF_SKIP;
         }
         if (staged) {
             __syncwarp();
-            for (int32_t p = lane; p < hi - lo; p += 32) col_idx[lo + p] = st[p];
+            for (int32_t p = lane; p < hi - lo; p += 32) {
+                const int32_t v = st[p];
+                if (v != CF_SKIP) col_idx[lo + p] = v;
+            }
             __syncwarp();
         }
     }
@@ -340,12 +316,88 @@ __global__ void __launch_bounds__(CF_BLOCK) k_col_fill(const int32_t* __restrict
 
 // ------------------------------------------------------------------ high-valence rows
 
-// One block per row: the 2d+1 columns go to shared memory; pass 1 flags the first occurrence
-// of each value, pass 2 places each first occurrence at its rank among the distinct values.
+// A medium general row (not one fan of at most FAN_MAX triangles, at most FAST_DEG triangles),
+// one warp: its 2d + 1 column candidates (i, then each triangle's two other vertices) sit three
+// to a lane (d <= 32). A candidate is a column if no earlier candidate equals it; a column's place
+// is the number of columns below it. Count pass (row_ptr null): the column count, the (j, l) pairs
+// in lexicographic order (ties by bucket position, so a repeated triangle keeps both copies) and
+// the row's place in the general-row list. Fill pass: the columns.
+static_assert(2 * FAST_DEG + 1 <= 96, "a medium row's candidates must fit three to a lane");
+__device__ __forceinline__ void mid_row(int lane, int32_t i, int32_t beg, int32_t d, const int2* __restrict__ adj,
+                                        const int32_t* __restrict__ row_ptr, int32_t* __restrict__ row_nnz,
+                                        int32_t* __restrict__ col_idx, int2* __restrict__ fan,
+                                        int32_t* __restrict__ gen_list, int32_t* __restrict__ gen_count) {
+    const int n = 2 * d + 1;
+    int32_t v[3];
+#pragma unroll
+    for (int s = 0; s < 3; s++) {
+        const int idx = lane + 32 * s;
+        int32_t x = INT32_MAX;
+        if (idx == 0) {
+            x = i;
+        } else if (idx < n) {
+            const int2 p = adj[beg + (idx - 1) / 2];
+            x = ((idx - 1) & 1) ? p.y : p.x;
+        }
+        v[s] = x;
+    }
+    bool first[3];
+#pragma unroll
+    for (int s = 0; s < 3; s++) first[s] = lane + 32 * s < n;
+#pragma unroll
+    for (int s2 = 0; s2 < 3; s2++)
+        for (int l = 0; l < 32 && 32 * s2 + l < n; l++) {          // n is the same in every lane
+            const int32_t x = __shfl_sync(0xffffffffu, v[s2], l);
+            const int kk = 32 * s2 + l;
+#pragma unroll
+            for (int s = 0; s < 3; s++)
+                if (kk < lane + 32 * s && x == v[s]) first[s] = false;
+        }
+    if (!row_ptr) {
+        int cnt = 0;
+#pragma unroll
+        for (int s = 0; s < 3; s++) cnt += __popc(__ballot_sync(0xffffffffu, first[s]));
+        if (lane == 0) {
+            row_nnz[i] = cnt;
+            gen_list[atomicAdd(gen_count, 1)] = i;
+        }
+        const int2 p = lane < d ? adj[beg + lane] : make_int2(INT32_MAX, INT32_MAX);
+        const long long key = ((long long)p.x << 32) | (unsigned)p.y;
+        int rank = 0;
+        for (int t = 0; t < d; t++) {
+            const long long k2 = __shfl_sync(0xffffffffu, key, t);
+            rank += (k2 < key) || (k2 == key && t < lane);
+        }
+        if (lane < d) fan[beg + FE_IDX(rank, d)] = p;
+        return;
+    }
+    int rank[3] = {0, 0, 0};
+#pragma unroll
+    for (int s2 = 0; s2 < 3; s2++)
+        for (int l = 0; l < 32 && 32 * s2 + l < n; l++) {
+            const int32_t x = __shfl_sync(0xffffffffu, v[s2], l);
+            const bool f = __shfl_sync(0xffffffffu, first[s2], l);
+#pragma unroll
+            for (int s = 0; s < 3; s++) rank[s] += f && x < v[s];
+        }
+    const int32_t o = row_ptr[i], u = row_ptr[i + 1] - o;
+    (void)u;                                                     // bounds of the checked build
+#pragma unroll
+    for (int s = 0; s < 3; s++)
+        if (first[s]) col_idx[o + FE_IDX(rank[s], u)] = v[s];
+}
+
+// General rows by k_row_big: those of more than FAST_DEG triangles one block each (the 2d+1
+// columns go to shared memory; pass 1 flags the first occurrence of each value, pass 2 places
+// each first occurrence at its rank among the distinct values), then the medium ones one warp
+// each (mid_row). Count pass (row_ptr null): the column counts, and for the medium rows their
+// sorted pairs and general-row list places; fill pass: the columns.
 __global__ void k_row_big(const int32_t* __restrict__ big_list, const int32_t* __restrict__ nbig,
                           const int32_t* __restrict__ vptr, const int32_t* __restrict__ abase, const int2* __restrict__ adj,
                           const int32_t* __restrict__ row_ptr, int32_t* __restrict__ row_nnz,
-                          int32_t* __restrict__ col_idx) {
+                          int32_t* __restrict__ col_idx, const int32_t* __restrict__ mid_list,
+                          const int32_t* __restrict__ nmid, int2* __restrict__ fan, int32_t* __restrict__ gen_list,
+                          int32_t* __restrict__ gen_count) {
     extern __shared__ int32_t sm[];
     __shared__ int cnt;
   for (int32_t b = blockIdx.x; b < *nbig; b += gridDim.x) {
@@ -379,6 +431,13 @@ __global__ void k_row_big(const int32_t* __restrict__ big_list, const int32_t* _
     }
     __syncthreads();
     if (threadIdx.x == 0 && row_nnz) row_nnz[i] = cnt;
+  }
+  const int lane = threadIdx.x & 31;
+  const int32_t warp = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int32_t nwarps = (int32_t)(((int64_t)gridDim.x * blockDim.x) >> 5);
+  for (int32_t b = warp; b < *nmid; b += nwarps) {
+    const int32_t i = mid_list[b];
+    mid_row(lane, i, abase[i], vptr[i + 1] - vptr[i], adj, row_ptr, row_nnz, col_idx, fan, gen_list, gen_count);
   }
 }
 
@@ -444,6 +503,7 @@ __global__ void k_row_perm(const int32_t* __restrict__ vptr, const int32_t* __re
         }
         isort64(keys, n);
         int32_t o = row_ptr[i], u = row_ptr[i + 1] - o;
+        (void)u;                                                 // bounds of the checked build
         int32_t cbase = 3 * beg;   // this row's contributions occupy perm[3*vptr[i] .. 3*vptr[i+1])
         int t = 0;
         for (int s = 0; s < n; s++) {
@@ -582,17 +642,18 @@ extern "C" void fe_pattern_destroy(fe_pattern p) {
 
 namespace {
 struct Temps {
-    int32_t *row_nnz = nullptr, *big_list = nullptr, *counters = nullptr, *cur = nullptr;
-    int* flag = nullptr;                 // points into counters (counters[0..1], flags[2..3])
+    int32_t *row_nnz = nullptr, *big_list = nullptr, *mid_list = nullptr, *counters = nullptr, *cur = nullptr;
+    int* flag = nullptr;                 // points into counters (counters[0..1], flags[2..3], [4] medium rows)
     int2* adj = nullptr;
     ~Temps() {
-        fe_free(row_nnz); fe_free(big_list); fe_free(counters); fe_free(adj);
+        fe_free(row_nnz); fe_free(big_list); fe_free(mid_list); fe_free(counters); fe_free(adj);
         fe_free(cur);
     }
 };
 }  // namespace
 
 static constexpr int BIG_GRID = 152;   // blocks of the high-valence kernels (they loop over the list)
+static constexpr int ROW_BIG_GRID = 4 * 152;   // k_row_big: its medium rows take one warp each
 
 // One host synchronisation: after the last kernel that can raise a flag, to read nnz and the
 // flags. The row counts, the high-valence list and nnz stay on the device until then; col_idx is
@@ -622,8 +683,9 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     // column digit inside each row, unique, and the CSR offsets
     if ((st = fe_alloc_n(&t.row_nnz, (size_t)nq + 1, "row counts"))) return st;
     if ((st = fe_alloc_n(&t.big_list, (size_t)nq + 1, "high-valence rows"))) return st;
+    if ((st = fe_alloc_n(&t.mid_list, (size_t)nq + 1, "medium general rows"))) return st;
     // counters: [0] high-valence rows, [1] general rows, [2] a valence over the limit, [3] a key
-    // missing from the pattern
+    // missing from the pattern, [4] medium general rows
     if ((st = fe_alloc_n(&t.counters, 8, "counters and flags"))) return st;
     t.flag = t.counters + 2;
     if ((st = fe_alloc_n(&p->row_ptr, (size_t)nq + 1, "row_ptr"))) return st;
@@ -644,9 +706,10 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
         fe_status sa;
         if (nq > 0) {
             { FE_PROF("k_row_analyse", s); k_row_analyse<<<fe_grid(nq, 128, 16), 128, 0, s>>>(p->vptr, t.adj, nq, t.row_nnz, p->fan, p->hdr, t.big_list,
-                                                                                             t.counters, p->gen_rows, t.counters + 1, t.flag); }
+                                                                                             t.counters, t.mid_list, t.counters + 4, t.flag); }
             FE_LAUNCHED("k_row_analyse");
-            { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, nullptr, t.row_nnz, nullptr); }
+            { FE_PROF("k_row_big", s); k_row_big<<<ROW_BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, nullptr, t.row_nnz, nullptr,
+                                                                                   t.mid_list, t.counters + 4, p->fan, p->gen_rows, t.counters + 1); }
             FE_LAUNCHED("k_row_big (count)");
         }
         if ((sa = fe_exclusive_scan(t.row_nnz, p->row_ptr, nq, s, nullptr))) return sa;
@@ -659,7 +722,8 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     // high-valence rows, staged-gather lists, map (all need the offsets)
     auto rows_rest = [&]() -> fe_status {
         if (nq > 0) {
-            { FE_PROF("k_row_big", s); k_row_big<<<BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->row_ptr, nullptr, p->col_idx); }
+            { FE_PROF("k_row_big", s); k_row_big<<<ROW_BIG_GRID, BIG_BLOCK, big_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->row_ptr, nullptr, p->col_idx,
+                                                                                   t.mid_list, t.counters + 4, nullptr, nullptr, nullptr); }
             FE_LAUNCHED("k_row_big (fill)");
             size_t pair_smem = (size_t)FE_MAX_VALENCE * sizeof(long long);
             { FE_PROF("k_row_big_pairs", s); k_row_big_pairs<<<BIG_GRID, BIG_BLOCK, pair_smem, s>>>(t.big_list, t.counters, p->vptr, p->vptr, t.adj, p->fan, p->hdr,
