@@ -18,11 +18,11 @@
 // shared memory, each neighbour's coordinates loaded once. The arithmetic is double-float on
 // the FP32 pipes (ff.cuh) after an exact FP64 difference per coordinate and neighbour.
 // General rows (several chains, long fans, non-manifold) use one block per row. Each triangle's
-// contributions to its three columns are computed once (for rows of up to 256 triangles) and
-// converted to FP64. Thread t owns column t: an off-diagonal column adds its few contributions (at
-// most four, else by Neumaier's compensated summation) in the row's stored (sorted) triangle
-// order, and the diagonal's d contributions are added by a fixed-shape pairwise tree over the
-// block.
+// contributions to its three columns are computed once (for rows of up to 256 triangles) and kept
+// as double-floats. Thread t owns column t: an off-diagonal column adds its few contributions in
+// the row's stored (sorted) triangle order, and the diagonal's d contributions are added by a
+// fixed-shape pairwise tree over the block, all in double-float. (Longer rows: each column's
+// contributions, recomputed, converted to FP64 and added by Neumaier's compensated summation.)
 // Both paths fix the order of every sum, so the result is bit-identical from run to run.
 #include "ff.cuh"
 #include "internal.cuh"
@@ -405,11 +405,23 @@ __device__ __forceinline__ void neumaier(double& sum, double& c, double v) {
 }
 
 // One general row, by one block: thread t owns column t of the row.
-// Triangles of a general row whose terms are computed once into shared memory (longer rows
-// recompute each triangle's terms in every thread that needs them), and the general-row block
-// size (a power of two, for the diagonal's tree sum).
-constexpr int GEN_SMEM_TRIS = 256;
-constexpr int GEN_BLOCK_MAX = 64;
+// General rows: one warp each, GEN_WARPS warps per block. A row of at most GEN_SMEM_TRIS
+// triangles keeps its triangles' terms in the warp's part of shared memory; longer rows recompute
+// each triangle's terms in every lane that needs them.
+constexpr int GEN_WARPS = 4;
+constexpr int GEN_SMEM_TRIS = 64;
+
+// Sum of one double-float per lane over the warp, by a fixed-shape tree (the same bits every run;
+// for non-negative terms an error of about 7 units of 2^-48 of the sum). Every lane gets it.
+__device__ __forceinline__ ff warp_sum_ff(ff a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ff b{__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+        // both lanes of a pair add the same two values in the same order (lower lane first)
+        a = (threadIdx.x & o) ? ff_add(b, a) : ff_add(a, b);
+    }
+    return a;
+}
 
 template <int KIND>
 __device__ __forceinline__ void general_row(int32_t i, const int32_t* __restrict__ row_ptr,
@@ -418,17 +430,23 @@ __device__ __forceinline__ void general_row(int32_t i, const int32_t* __restrict
                                             const double* __restrict__ w, const Consts& cs, double* __restrict__ out0,
                                             double* __restrict__ out1, int& bad, int& orient) {
     constexpr bool TWO = (KIND & W_S) && (KIND & (W_W | W_M));   // a second matrix in out1
+    constexpr int M1 = TWO ? 1 : 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int32_t rb = row_ptr[i], u = row_ptr[i + 1] - rb;
     int32_t b0 = vptr[i], d = vptr[i + 1] - b0;
     double2 pi = q[i];
     ff wi = (KIND & W_W) ? ff_from_double(w[i], bad) : ff_make(0.f);
     if (d <= GEN_SMEM_TRIS) {
-        // each triangle's contributions to its three columns (self, j, l), as the FP64 values the
-        // sums below take, computed once by one thread; then thread t adds those of its column
-        // in the stored triangle order, exactly as the loop further down does
-        __shared__ int2 sp[GEN_SMEM_TRIS];
-        __shared__ double sv[TWO ? 2 : 1][3][GEN_SMEM_TRIS];
-        for (int e = threadIdx.x; e < d; e += blockDim.x) {
+        // each triangle's contributions to its three columns (self, j, l) computed once by one
+        // lane and kept as double-floats; the sums run in double-float too, as on the fast path,
+        // and only each entry's value is converted to FP64 (GB300's FP64 rate made FP64 sums the
+        // bound of this kernel)
+        __shared__ int2 sp_all[GEN_WARPS][GEN_SMEM_TRIS];
+        __shared__ ff sv_all[GEN_WARPS][TWO ? 2 : 1][3][GEN_SMEM_TRIS];
+        int2* sp = sp_all[wid];
+        auto sv = sv_all[wid];
+        ff a0 = z_ff(), a1 = z_ff();                                 // this lane's diagonal terms
+        for (int e = lane; e < d; e += 32) {
             int2 p = fan[b0 + e];
             sp[e] = p;
             Nb j = load_nb<KIND>(q, w, pi, p.x, 0, bad), l = load_nb<KIND>(q, w, pi, p.y, 0, bad);
@@ -439,46 +457,31 @@ __device__ __forceinline__ void general_row(int32_t i, const int32_t* __restrict
             for (int which = 0; which < 3; which++) {
                 ff v0, v1;
                 pick<KIND>(rt, which, v0, v1);
-                sv[0][which][e] = ff_to_double(v0);
-                if (TWO) sv[TWO ? 1 : 0][which][e] = ff_to_double(v1);
-            }
-        }
-        __syncthreads();
-        // the diagonal's d terms: each thread adds its strided terms in order, then a pairwise
-        // tree over the threads (a fixed shape, so the same bits every run; FP64 error at most
-        // about log2(d) 2^-53 of the sum of |terms|)
-        __shared__ double red[TWO ? 2 : 1][GEN_BLOCK_MAX];
-        {
-            double a0 = 0.0, a1 = 0.0;
-            for (int e = threadIdx.x; e < d; e += blockDim.x) {
-                a0 += sv[0][0][e];
-                if (TWO) a1 += sv[TWO ? 1 : 0][0][e];
-            }
-            red[0][threadIdx.x] = a0;
-            if (TWO) red[TWO ? 1 : 0][threadIdx.x] = a1;
-            __syncthreads();
-            for (int h = blockDim.x / 2; h > 0; h /= 2) {
-                if (threadIdx.x < h) {
-                    red[0][threadIdx.x] += red[0][threadIdx.x + h];
-                    if (TWO) red[TWO ? 1 : 0][threadIdx.x] += red[TWO ? 1 : 0][threadIdx.x + h];
+                sv[0][which][e] = v0;
+                if (TWO) sv[M1][which][e] = v1;
+                if (which == 0) {
+                    a0 = ff_add(a0, v0);
+                    if (TWO) a1 = ff_add(a1, v1);
                 }
-                __syncthreads();
             }
         }
-        for (int t = threadIdx.x; t < u; t += blockDim.x) {
+        // the diagonal's d terms (all positive for S, M^w and M): each lane's in order, then the
+        // warp's tree
+        const ff dg0 = warp_sum_ff(a0);
+        const ff dg1 = TWO ? warp_sum_ff(a1) : z_ff();
+        __syncwarp();
+        for (int t = lane; t < u; t += 32) {
             int32_t col = col_idx[rb + t];
             bool self = col == i;
-            double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
+            ff v0 = z_ff(), v1 = z_ff();
             if (self) {
-                s0 = red[0][0];
-                if (TWO) s1 = red[TWO ? 1 : 0][0];
+                v0 = dg0;
+                v1 = dg1;
             } else {
                 // an off-diagonal column takes one term from each triangle on its edge: two for an
                 // interior edge of a manifold mesh. Up to four are found by integer compares and
-                // added in stored order by the same plain FP64 additions in every thread (absent
-                // terms are zeros), so the FP64 instructions do not diverge; error at most
-                // 3 * 2^-53 of the sum of |terms|. More (an edge of more than four triangles)
-                // take the compensated sum over all of them.
+                // added in stored order by the same additions in every lane (absent terms are
+                // zeros); more (an edge of more than four triangles) in a loop over them.
                 int p0 = -1, p1 = -1, p2 = -1, p3 = -1, n = 0;
                 for (int32_t e = 0; e < d; e++) {
                     int2 p = sp[e];
@@ -492,30 +495,28 @@ __device__ __forceinline__ void general_row(int32_t i, const int32_t* __restrict
                     n++;
                 }
                 if (n <= 4) {
-                    auto term = [&](int code, int m) { return code < 0 ? 0.0 : sv[m][code % 3][code / 3]; };
-                    s0 = ((term(p0, 0) + term(p1, 0)) + term(p2, 0)) + term(p3, 0);
-                    if (TWO) s1 = ((term(p0, TWO ? 1 : 0) + term(p1, TWO ? 1 : 0)) + term(p2, TWO ? 1 : 0)) + term(p3, TWO ? 1 : 0);
+                    auto term = [&](int code, int m) { return code < 0 ? z_ff() : sv[m][code % 3][code / 3]; };
+                    v0 = ff_add(ff_add(ff_add(term(p0, 0), term(p1, 0)), term(p2, 0)), term(p3, 0));
+                    if (TWO) v1 = ff_add(ff_add(ff_add(term(p0, M1), term(p1, M1)), term(p2, M1)), term(p3, M1));
                 } else {
                     for (int32_t e = 0; e < d; e++) {
                         int2 p = sp[e];
                         int which = p.x == col ? 1 : (p.y == col ? 2 : -1);
                         if (which < 0) continue;
-                        neumaier(s0, c0, sv[0][which][e]);
-                        if (TWO) neumaier(s1, c1, sv[TWO ? 1 : 0][which][e]);
+                        v0 = ff_add(v0, sv[0][which][e]);
+                        if (TWO) v1 = ff_add(v1, sv[M1][which][e]);
                     }
                 }
             }
-            double v = s0 + c0;
-            if (KIND == W_M) v *= self ? cs.d12 : cs.d24;
-            if (KIND == W_W) v *= cs.d60;
-            const double scale1 = (KIND & W_W) ? cs.d60 : (self ? cs.d12 : cs.d24);
-            out0[rb + t] = v;
-            if (TWO) out1[rb + t] = (s1 + c1) * scale1;
+            if (KIND == W_M) v0 = ff_mul(v0, self ? cs.c12 : cs.c24);
+            if (KIND == W_W) v0 = ff_mul(v0, cs.c60);
+            out0[rb + t] = ff_to_double(v0);
+            if (TWO) out1[rb + t] = ff_to_double(ff_mul(v1, (KIND & W_W) ? cs.c60 : (self ? cs.c12 : cs.c24)));
         }
-        __syncthreads();
+        __syncwarp();
         return;
     }
-    for (int t = threadIdx.x; t < u; t += blockDim.x) {
+    for (int t = lane; t < u; t += 32) {
         int32_t col = col_idx[rb + t];
         bool self = col == i;
         double s0 = 0.0, c0 = 0.0, s1 = 0.0, c1 = 0.0;
@@ -542,14 +543,17 @@ __device__ __forceinline__ void general_row(int32_t i, const int32_t* __restrict
     }
 }
 
-// General rows of the list that lie in [r0, r1) (a row window), one block each.
+// General rows of the list (n of them) that lie in [r0, r1) (a row window), one warp each.
 template <int KIND>
-__global__ void k_general_scalar(const int32_t* __restrict__ gen, const int32_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(32 * GEN_WARPS) k_general_scalar(const int32_t* __restrict__ gen, int32_t n,
+                                 const int32_t* __restrict__ row_ptr,
                                  const int32_t* __restrict__ col_idx, const int32_t* __restrict__ vptr,
                                  const int2* __restrict__ fan, const double2* __restrict__ q,
                                  const double* __restrict__ w, Consts cs, double* __restrict__ out0,
                                  double* __restrict__ out1, int* __restrict__ err, int32_t r0, int32_t r1) {
-    const int32_t i = gen[blockIdx.x];
+    const int32_t g = blockIdx.x * GEN_WARPS + (threadIdx.x >> 5);
+    if (g >= n) return;
+    const int32_t i = gen[g];
     if (i < r0 || i >= r1) return;
     int bad = 0, orient = 0;
     general_row<KIND>(i, row_ptr, col_idx, vptr, fan, q, w, cs, out0, out1, bad, orient);
@@ -581,9 +585,12 @@ __global__ void __launch_bounds__(256) k_batch_rows(const fe_row_mesh* __restric
     }
 }
 
-__global__ void k_batch_general(const fe_row_mesh* __restrict__ desc, const int2* __restrict__ list,
-                                double* const* __restrict__ S, double* const* __restrict__ M, Consts cs) {
-    int2 e = list[blockIdx.x];                                   // (mesh, row)
+__global__ void __launch_bounds__(32 * GEN_WARPS) k_batch_general(const fe_row_mesh* __restrict__ desc, const int2* __restrict__ list,
+                                                                   int32_t n, double* const* __restrict__ S,
+                                                                   double* const* __restrict__ M, Consts cs) {
+    const int32_t g = blockIdx.x * GEN_WARPS + (threadIdx.x >> 5);
+    if (g >= n) return;
+    int2 e = list[g];                                            // (mesh, row), one warp
     fe_row_mesh d = desc[e.x];
     int bad = 0, orient = 0;
     general_row<W_S | W_M>(e.y, d.row_ptr, d.col_idx, d.vptr, d.fan, d.q, nullptr, cs, S[e.x], M[e.x], bad, orient);
@@ -717,37 +724,119 @@ __global__ void __launch_bounds__(256, 2) k_fan_elas(const int32_t* __restrict__
     if (orient) atomicOr(err, 1);
 }
 
-__global__ void k_general_elas(const int32_t* __restrict__ gen, const int32_t* __restrict__ row_ptr,
-                               const int32_t* __restrict__ col_idx, const int32_t* __restrict__ vptr,
-                               const int2* __restrict__ fan, const double2* __restrict__ q, Consts cs,
-                               double* __restrict__ out, int* __restrict__ err) {
-    int32_t i = gen[blockIdx.x];
+// General rows of K, one warp each (as k_general_scalar).
+__global__ void __launch_bounds__(32 * GEN_WARPS) k_general_elas(const int32_t* __restrict__ gen, int32_t ngen,
+                                                                 const int32_t* __restrict__ row_ptr,
+                                                                 const int32_t* __restrict__ col_idx, const int32_t* __restrict__ vptr,
+                                                                 const int2* __restrict__ fan, const double2* __restrict__ q, Consts cs,
+                                                                 double* __restrict__ out, int* __restrict__ err) {
+    const int32_t g = blockIdx.x * GEN_WARPS + (threadIdx.x >> 5);
+    if (g >= ngen) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t i = gen[g];
     int32_t rb = row_ptr[i], u = row_ptr[i + 1] - rb;
     int32_t b0 = vptr[i], d = vptr[i + 1] - b0;
     double2 pi = q[i];
     int bad = 0, orient = 0;
-    for (int t = threadIdx.x; t < u; t += blockDim.x) {
-        int32_t col = col_idx[rb + t];
-        bool self = col == i;
-        double s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
-        for (int32_t e = 0; e < d; e++) {
+    if (d <= GEN_SMEM_TRIS) {
+        // as general_row: each triangle's three 2 x 2 blocks once, as double-floats (block b of
+        // triangle e at sk[4 b + entry][e]); the diagonal block by the warp's tree, each
+        // off-diagonal block from at most four terms by the same additions in every lane, more in
+        // a loop; all sums in double-float, each entry converted to FP64 once
+        __shared__ int2 sp_all[GEN_WARPS][GEN_SMEM_TRIS];
+        __shared__ ff sk_all[GEN_WARPS][12][GEN_SMEM_TRIS];
+        int2* sp = sp_all[wid];
+        auto sk = sk_all[wid];
+        ff a[4] = {z_ff(), z_ff(), z_ff(), z_ff()};
+        for (int e = lane; e < d; e += 32) {
             int2 p = fan[b0 + e];
-            int which = self ? 0 : (p.x == col ? 1 : (p.y == col ? 2 : -1));
-            if (which < 0) continue;
+            sp[e] = p;
             Nb j = load_nb<0>(q, nullptr, pi, p.x, 0, bad), l = load_nb<0>(q, nullptr, pi, p.y, 0, bad);
             Block2 k[3];
             ff D = elas_terms(q, i, j, l, cs, k, bad);
             orient |= !(D.h > 0.f);
-            neumaier(s[0], c[0], ff_to_double(k[which].k00));
-            neumaier(s[1], c[1], ff_to_double(k[which].k01));
-            neumaier(s[2], c[2], ff_to_double(k[which].k10));
-            neumaier(s[3], c[3], ff_to_double(k[which].k11));
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                sk[4 * b][e] = k[b].k00;
+                sk[4 * b + 1][e] = k[b].k01;
+                sk[4 * b + 2][e] = k[b].k10;
+                sk[4 * b + 3][e] = k[b].k11;
+            }
+            a[0] = ff_add(a[0], k[0].k00);
+            a[1] = ff_add(a[1], k[0].k01);
+            a[2] = ff_add(a[2], k[0].k10);
+            a[3] = ff_add(a[3], k[0].k11);
         }
-        int32_t o0 = 4 * rb + 2 * t, o1 = 4 * rb + 2 * u + 2 * t;
-        out[o0] = s[0] + c[0];
-        out[o0 + 1] = s[1] + c[1];
-        out[o1] = s[2] + c[2];
-        out[o1 + 1] = s[3] + c[3];
+        ff dg[4];
+#pragma unroll
+        for (int x = 0; x < 4; x++) dg[x] = warp_sum_ff(a[x]);
+        __syncwarp();
+        for (int t = lane; t < u; t += 32) {
+            int32_t col = col_idx[rb + t];
+            ff v[4] = {z_ff(), z_ff(), z_ff(), z_ff()};
+            if (col == i) {
+#pragma unroll
+                for (int x = 0; x < 4; x++) v[x] = dg[x];
+            } else {
+                int p0 = -1, p1 = -1, p2 = -1, p3 = -1, n = 0;
+                for (int32_t e = 0; e < d; e++) {
+                    int2 p = sp[e];
+                    int which = p.x == col ? 1 : (p.y == col ? 2 : -1);
+                    if (which < 0) continue;
+                    int code = 3 * e + which;
+                    p0 = n == 0 ? code : p0;
+                    p1 = n == 1 ? code : p1;
+                    p2 = n == 2 ? code : p2;
+                    p3 = n == 3 ? code : p3;
+                    n++;
+                }
+                if (n <= 4) {
+                    auto term = [&](int code, int x) { return code < 0 ? z_ff() : sk[4 * (code % 3) + x][code / 3]; };
+#pragma unroll
+                    for (int x = 0; x < 4; x++) v[x] = ff_add(ff_add(ff_add(term(p0, x), term(p1, x)), term(p2, x)), term(p3, x));
+                } else {
+                    for (int32_t e = 0; e < d; e++) {
+                        int2 p = sp[e];
+                        int which = p.x == col ? 1 : (p.y == col ? 2 : -1);
+                        if (which < 0) continue;
+#pragma unroll
+                        for (int x = 0; x < 4; x++) v[x] = ff_add(v[x], sk[4 * which + x][e]);
+                    }
+                }
+            }
+            int32_t o0 = 4 * rb + 2 * t, o1 = 4 * rb + 2 * u + 2 * t;
+            out[o0] = ff_to_double(v[0]);
+            out[o0 + 1] = ff_to_double(v[1]);
+            out[o1] = ff_to_double(v[2]);
+            out[o1 + 1] = ff_to_double(v[3]);
+        }
+        __syncwarp();
+    } else {
+        // a long row: each lane's columns, their contributions recomputed and added by
+        // compensated FP64 sums
+        for (int t = lane; t < u; t += 32) {
+            int32_t col = col_idx[rb + t];
+            bool self = col == i;
+            double sx[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+            for (int32_t e = 0; e < d; e++) {
+                int2 p = fan[b0 + e];
+                int which = self ? 0 : (p.x == col ? 1 : (p.y == col ? 2 : -1));
+                if (which < 0) continue;
+                Nb j = load_nb<0>(q, nullptr, pi, p.x, 0, bad), l = load_nb<0>(q, nullptr, pi, p.y, 0, bad);
+                Block2 k[3];
+                ff D = elas_terms(q, i, j, l, cs, k, bad);
+                orient |= !(D.h > 0.f);
+                neumaier(sx[0], c[0], ff_to_double(k[which].k00));
+                neumaier(sx[1], c[1], ff_to_double(k[which].k01));
+                neumaier(sx[2], c[2], ff_to_double(k[which].k10));
+                neumaier(sx[3], c[3], ff_to_double(k[which].k11));
+            }
+            int32_t o0 = 4 * rb + 2 * t, o1 = 4 * rb + 2 * u + 2 * t;
+            out[o0] = sx[0] + c[0];
+            out[o0 + 1] = sx[1] + c[1];
+            out[o1] = sx[2] + c[2];
+            out[o1 + 1] = sx[3] + c[3];
+        }
     }
     if (bad) atomicOr(err, 2);
     if (orient) atomicOr(err, 1);
@@ -779,7 +868,8 @@ static Consts make_consts(double lam, double mu) {
 
 static constexpr int FAN_BLOCK = 256;
 static constexpr int FAN_SCALAR_BLOCK = 128;
-static constexpr int GEN_BLOCK = GEN_BLOCK_MAX;
+static constexpr int GEN_BLOCK = 32 * GEN_WARPS;
+static unsigned gen_grid(int32_t n) { return (unsigned)((n + GEN_WARPS - 1) / GEN_WARPS); }
 
 template <int KIND>
 static fe_status launch_scalar(fe_mesh m, fe_pattern p, const double* w, double* out0, double* out1, cudaStream_t s) {
@@ -810,7 +900,7 @@ static fe_status launch_scalar(fe_mesh m, fe_pattern p, const double* w, double*
     fe_free(vr);
     if (e != cudaSuccess) return fe_cuda_fail(e, "k_fan_scalar");
     if (p->n_gen > 0) {
-        { FE_PROF("k_general_scalar", s); k_general_scalar<KIND><<<p->n_gen, GEN_BLOCK, 0, s>>>(p->gen_rows, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q, w, cs, out0, out1, m->err, r0, r1); }
+        { FE_PROF("k_general_scalar", s); k_general_scalar<KIND><<<gen_grid(p->n_gen), GEN_BLOCK, 0, s>>>(p->gen_rows, p->n_gen, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q, w, cs, out0, out1, m->err, r0, r1); }
         FE_LAUNCHED("k_general_scalar");
     }
     return FE_OK;
@@ -836,7 +926,7 @@ fe_status fe_row_elas(fe_mesh m, fe_pattern p, double lam, double mu, double* ou
                                                                                            Lim{m->nq, 3 * (int64_t)m->nme, p->nnz_scalar}); }
     FE_LAUNCHED("k_fan_elas");
     if (p->n_gen > 0) {
-        { FE_PROF("k_general_elas", s); k_general_elas<<<p->n_gen, GEN_BLOCK, 0, s>>>(p->gen_rows, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q, cs, out, m->err); }
+        { FE_PROF("k_general_elas", s); k_general_elas<<<gen_grid(p->n_gen), GEN_BLOCK, 0, s>>>(p->gen_rows, p->n_gen, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q, cs, out, m->err); }
         FE_LAUNCHED("k_general_elas");
     }
     return FE_OK;
@@ -857,7 +947,7 @@ void fe_row_batch_launch(const fe_row_mesh* desc, const fe_row_tile* tiles, int3
         { FE_PROF("k_batch_rows", s); k_batch_rows<<<grid, block, 0, s>>>(desc, tiles, ntiles, S, M, cs); }
     }
     if (ngeneral > 0) {
-        { FE_PROF("k_batch_general", s); k_batch_general<<<ngeneral, GEN_BLOCK, 0, s>>>(desc, general, S, M, cs); }
+        { FE_PROF("k_batch_general", s); k_batch_general<<<gen_grid(ngeneral), GEN_BLOCK, 0, s>>>(desc, general, ngeneral, S, M, cs); }
     }
 }
 
@@ -981,7 +1071,7 @@ extern "C" fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const
     { FE_PROF("k_pack_vrec", s); k_pack_vrec<<<fe_grid(nq, 256), 256, 0, s>>>(m->q, wd, nq, vr, m->err); }
     if (p->n_gen > 0) {
         FE_PROF("k_general_scalar", s);
-        k_general_scalar<W_S | W_W><<<p->n_gen, GEN_BLOCK, 0, s>>>(p->gen_rows, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q,
+        k_general_scalar<W_S | W_W><<<gen_grid(p->n_gen), GEN_BLOCK, 0, s>>>(p->gen_rows, p->n_gen, p->row_ptr, p->col_idx, p->vptr, p->fan, m->q,
                                                                    wd, cs, Sd, Md, m->err, 0, nq);
     }
     for (int k = 0; k < E2E_BLOCKS; k++) {
