@@ -56,20 +56,27 @@ struct RowTerms {
     ff w[3];       // unscaled M^w entries: D (s + 2 w_i), D (s - w_l / 2), D (s - w_j / 2)
 };
 
-// A badly shaped triangle (i, c, n) (an angle below about 14.5 degrees): the two quantities that
-// double-float arithmetic on the split relative coordinates would get wrong by too much, D =
-// r_c x r_n (a cancelling difference of products) and the edge e_a = p_c - p_n (a difference of
-// nearly equal vectors when the angle at i is small), come from FP64 coordinate differences (each
-// correctly rounded) and are then split; the dot products and 1/2D that use them stay in
-// double-float, where they lose nothing to the triangle's shape. 8 FP64 instructions, against about
-// 40 (with a division) for the same terms entirely in FP64.
+// A badly shaped triangle (i, c, n) (an angle below about 14.5 degrees): the quantities that
+// double-float arithmetic on the split relative coordinates would get wrong by too much come from
+// FP64 coordinate differences (each correctly rounded) and are then split: D = r_c x r_n (a
+// cancelling difference of products), the edge e_a = p_c - p_n (a difference of nearly equal
+// vectors when the angle at i is small), and the stiffness's two dot products e_a . r_n and
+// e_a . r_c (which cancel when the angles at n and c are near 90 degrees, as they are when the
+// angle at i is small; a row whose only triangle is such a sliver has only such small entries).
+// 1/2D and the products by it stay in double-float. 12 FP64 instructions, against about 40 (with
+// a division) for the same terms entirely in FP64. The elasticity blocks take D and e_a from here
+// and form their products in double-float: each of their rows keeps entries of the size of
+// |e_a| |r| / 2D that do not cancel, so those products' rounding stays small against the row.
 __device__ __noinline__ void thin_terms(const double2* __restrict__ q, int32_t i, int32_t c, int32_t n, ff& D, ff& ax,
-                                        ff& ay, int& bad) {
+                                        ff& ay, ff* dn, ff* dc, int& bad) {
     const double2 pi = q[i], pc = q[c], pn = q[n];
     const double cx = pc.x - pi.x, cy = pc.y - pi.y, nx = pn.x - pi.x, ny = pn.y - pi.y;
+    const double ex = pc.x - pn.x, ey = pc.y - pn.y;
     D = ff_from_value(fma(cx, ny, -(cy * nx)), bad);
-    ax = ff_from_double(pc.x - pn.x, bad);
-    ay = ff_from_double(pc.y - pn.y, bad);
+    ax = ff_from_double(ex, bad);
+    ay = ff_from_double(ey, bad);
+    if (dn) *dn = ff_from_value(fma(ex, nx, ey * ny), bad);     // e_a . r_n
+    if (dc) *dc = ff_from_value(fma(ex, cx, ey * cy), bad);     // e_a . r_c
 }
 
 // Shape test: sin^2 of each angle is D^2 over the product of the two adjacent squared edges;
@@ -87,11 +94,19 @@ __device__ __forceinline__ RowTerms row_terms(const double2* __restrict__ q, con
     RowTerms t;
     t.d = ff_dot2(j.x, l.x, l.y, ff_neg(j.y));                  // r_j x r_l
     ff ax = ff_sub(j.x, l.x), ay = ff_sub(j.y, l.y);            // e_a = r_j - r_l
-    if (!well_shaped(j, l, t.d.h)) thin_terms(q, i, j.id, l.id, t.d, ax, ay, bad);
+    ff dl, dj;                                                  // e_a . r_l, e_a . r_j
+    if (well_shaped(j, l, t.d.h)) {
+        if (KIND & W_S) {
+            dl = ff_dot2(ax, ay, l.x, l.y);
+            dj = ff_dot2(ax, ay, j.x, j.y);
+        }
+    } else {
+        thin_terms(q, i, j.id, l.id, t.d, ax, ay, (KIND & W_S) ? &dl : nullptr, (KIND & W_S) ? &dj : nullptr, bad);
+    }
     if (KIND & W_S) {
         ff inv = ff_mulf(ff_rcp_fast(t.d), 0.5f);              // 1 / 2D
-        t.s[1] = ff_mul(ff_dot2(ax, ay, l.x, l.y), inv);        // e_a . r_l
-        t.s[2] = ff_neg(ff_mul(ff_dot2(ax, ay, j.x, j.y), inv)); // e_a . (-r_j)
+        t.s[1] = ff_mul(dl, inv);                               // e_a . r_l / 2D
+        t.s[2] = ff_neg(ff_mul(dj, inv));                       // e_a . (-r_j) / 2D
     }
     if (KIND & W_W) {
         ff s = ff_add(ff_add(wi, j.w), l.w);
@@ -313,13 +328,21 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
         FanNb nxt = fan_nb<KIND>(rn, pi, bad);
         ff D = ff_dot2(cur.x, nxt.x, nxt.y, ff_neg(cur.y));          // r_c x r_n
         ff ax = ff_sub(cur.x, nxt.x), ay = ff_sub(cur.y, nxt.y);      // e_a
-        if (!fan_well_shaped(cur, nxt, ax.h, ay.h, D.h)) thin_terms(q, i, cur.id, nxt.id, D, ax, ay, bad);
+        ff dn, dc;                                                    // e_a . r_n, e_a . r_c
+        if (fan_well_shaped(cur, nxt, ax.h, ay.h, D.h)) {
+            if (DS) {
+                dn = ff_dot2(ax, ay, nxt.x, nxt.y);
+                dc = ff_dot2(ax, ay, cur.x, cur.y);
+            }
+        } else {
+            thin_terms(q, i, cur.id, nxt.id, D, ax, ay, DS ? &dn : nullptr, DS ? &dc : nullptr, bad);
+        }
         ff sc = z_ff(), sn = z_ff();
         if (DS) {
             ff inv = ff_rcp_fast(D);
             inv = ff{0.5f * inv.h, 0.5f * inv.l};                   // 1 / 2D
-            sc = ff_mul(ff_dot2(ax, ay, nxt.x, nxt.y), inv);
-            sn = ff_neg(ff_mul(ff_dot2(ax, ay, cur.x, cur.y), inv));
+            sc = ff_mul(dn, inv);
+            sn = ff_neg(ff_mul(dc, inv));
         }
         orient |= !(D.h > 0.f);
         ff A = z_ff(), B = z_ff();
@@ -634,7 +657,7 @@ __device__ __forceinline__ ff elas_terms(const double2* __restrict__ q, int32_t 
                                          const Consts& cs, Block2 out[3], int& bad) {
     ff D = ff_dot2(j.x, l.x, l.y, ff_neg(j.y));
     ff eax = ff_sub(j.x, l.x), eay = ff_sub(j.y, l.y);
-    if (!well_shaped(j, l, D.h)) thin_terms(q, i, j.id, l.id, D, eax, eay, bad);
+    if (!well_shaped(j, l, D.h)) thin_terms(q, i, j.id, l.id, D, eax, eay, nullptr, nullptr, bad);
     ff r = ff_mulf(ff_rcp_fast(D), 0.5f);
     ff sax = ff_mul(eax, r), say = ff_mul(eay, r);
     out[0] = elas_block(sax, say, eax, eay, cs);
@@ -693,7 +716,7 @@ __global__ void __launch_bounds__(256, 2) k_fan_elas(const int32_t* __restrict__
             // the blocks of columns n_e and n_{e+1} (D and e_a from FP64 for badly shaped triangles)
             ff D = ff_dot2(cur.x, nxt.x, nxt.y, ff_neg(cur.y));
             ff eax = ff_sub(cur.x, nxt.x), eay = ff_sub(cur.y, nxt.y);
-            if (!well_shaped(cur, nxt, D.h)) thin_terms(q, i, cur.id, nxt.id, D, eax, eay, bad);
+            if (!well_shaped(cur, nxt, D.h)) thin_terms(q, i, cur.id, nxt.id, D, eax, eay, nullptr, nullptr, bad);
             ff rr = ff_mulf(ff_rcp_fast(D), 0.5f);
             ff sax = ff_mul(eax, rr), say = ff_mul(eay, rr);
             Block2 kc = elas_block(sax, say, nxt.x, nxt.y, cs);
