@@ -419,3 +419,32 @@ def test_end_to_end_host_call_errors():
     st = L.fe_assemble_stiff_wmass_host(m.nq, m.nme, q.ctypes.data, bad.ctypes.data, w.ctypes.data, rp.ctypes.data,
                                         ci.ctypes.data, S.ctypes.data, M.ctypes.data, 8, ctypes.byref(nnz), None)
     assert st == 4 and b"triangle 3" in L.fe_last_error()
+
+
+# The double-float row owners' error budget: each double-float operation errs by a few units of
+# 2^-48 of its operands and a row sums at most about 14 terms (fans of up to 8 triangles; longer
+# rows and thin triangles take the paths built for them), so the assembled values agree with FP64
+# to about 2^-44 of each row's maximum (the parity tolerance, 1e-13, leaves room above it).
+ROW_BUDGET = 2.0 ** -44
+
+
+@pytest.mark.parametrize("case", sorted(c for c in CASES if c != "fans5x4000"))
+def test_row_owner_error_budget(case):
+    """The row-owner variant's S, M^[w], M and K on every parity mesh stay within the error budget
+    of the double-float arithmetic, which is tighter than the parity tolerance: a change that
+    loses bits (in the thin-triangle or general-row paths, say) shows here first. (fans5x4000 is
+    left out: its rows sum 4000 contributions, beyond the budget's premise; there even the FP64
+    variants differ from the oracle by 3.2e-14 through the order of the sums.)"""
+    q, me = CASES[case]
+    w = _weights(q)
+    mesh = feasm.Mesh(q, me)
+    pat = feasm.Pattern(mesh, map=False)
+    wd = torch.tensor(w, device="cuda")
+    S, Mw = feasm.assemble_stiff_wmass(mesh, pat, wd, feasm.ROW)
+    M = feasm.assemble_mass(mesh, pat, feasm.ROW)
+    for kind, got in ((oracle.STIFF, S), (oracle.WMASS, Mw), (oracle.MASS, M)):
+        rp, _, va = oracle.assemble(kind, q, me, w)
+        assert_values_close(rp, got.cpu().numpy(), va, tol=ROW_BUDGET)
+    pat2 = feasm.Pattern(mesh, dofs=2, map=False)
+    rpk, _, vk = oracle.assemble(oracle.ELAS, q, me, lam=1.0, mu=0.5)
+    assert_values_close(rpk, feasm.assemble_elas(mesh, pat2, 1.0, 0.5, feasm.ROW).cpu().numpy(), vk, tol=ROW_BUDGET)
