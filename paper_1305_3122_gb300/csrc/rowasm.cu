@@ -64,10 +64,11 @@ struct RowTerms {
 // e_a . r_c (which cancel when the angles at n and c are near 90 degrees, as they are when the
 // angle at i is small; a row whose only triangle is such a sliver has only such small entries).
 // 1/2D and the products by it stay in double-float. 12 FP64 instructions, against about 40 (with
-// a division) for the same terms entirely in FP64. The elasticity blocks take D and e_a from here
+// a division) for the same terms entirely in FP64. Inlined: a call's register and stack handling
+// cost the fan kernel 10 registers and 5% of its time. The elasticity blocks take D and e_a from here
 // and form their products in double-float: each of their rows keeps entries of the size of
 // |e_a| |r| / 2D that do not cancel, so those products' rounding stays small against the row.
-__device__ __noinline__ void thin_terms(const double2* __restrict__ q, int32_t i, int32_t c, int32_t n, ff& D, ff& ax,
+__device__ __forceinline__ void thin_terms(const double2* __restrict__ q, int32_t i, int32_t c, int32_t n, ff& D, ff& ax,
                                         ff& ay, ff* dn, ff* dc, int& bad) {
     const double2 pi = q[i], pc = q[c], pn = q[n];
     const double cx = pc.x - pi.x, cy = pc.y - pi.y, nx = pn.x - pi.x, ny = pn.y - pi.y;
