@@ -666,10 +666,10 @@ ISSUE_PEAK = 4 * 152 * 2.07e9
 
 # What limits a kernel below its HBM roof, from its ncu captures (profiles/).
 LIMITS = {
-    "k_fan_scalar": "instruction issue and load latency: 85.3 M warp instructions at 1024^2 issued on 60.5% of cycles "
-                    "(FP32 FMA pipe 38%, integer ALU 33%, FP64 pipe 42%: double-float arithmetic in place of FP64, "
+    "k_fan_scalar": "instruction issue and load latency: 80.6 M warp instructions at 1024^2 issued on 65.8% of cycles "
+                    "(FP32 FMA pipe 42%, integer ALU 38%, FP64 pipe 48%: double-float arithmetic in place of FP64, "
                     "with FP64 for the coordinate differences and the output sums), the rest waiting on the dependent "
-                    "fan-record and vertex-record loads (3.9 long-scoreboard stalls per issue, 20 warps per SM at 95 "
+                    "fan-record and vertex-record loads (2.9 long-scoreboard stalls per issue, 20 warps per SM at 86 "
                     "registers; ncu at 1024^2); at 2048^2 the random vertex-record gathers also miss "
                     "L2 (traffic above). Locality orders, shared-memory staging and cp.async gathers measured slower",
 }
