@@ -317,51 +317,54 @@ __global__ void __launch_bounds__(CF_BLOCK) k_col_fill(const int32_t* __restrict
 // ------------------------------------------------------------------ high-valence rows
 
 // A medium general row (not one fan of at most FAN_MAX triangles, at most FAST_DEG triangles),
-// one warp: its 2d + 1 column candidates (i, then each triangle's two other vertices) sit three
-// to a lane (d <= 32). A candidate is a column if no earlier candidate equals it; a column's place
-// is the number of columns below it. Count pass (row_ptr null): the column count, the (j, l) pairs
-// in lexicographic order (ties by bucket position, so a repeated triangle keeps both copies) and
-// the row's place in the general-row list. Fill pass: the columns.
-static_assert(2 * FAST_DEG + 1 <= 96, "a medium row's candidates must fit three to a lane");
+// one warp. Its columns are i and the distinct vertices among the 2d others of its triangles (none
+// of which is i). Those 2d ids, two to a lane (element lane + 32 s), are sorted by a bitonic
+// network over 64 elements (padded with INT32_MAX); an element is a column if it differs from the
+// one before it, and its place is the number of such elements before it, plus one if i is
+// smaller. Count pass (row_ptr null): the column count, the (j, l) pairs in lexicographic order
+// (ties by bucket position, so a repeated triangle keeps both copies) and the row's place in the
+// general-row list. Fill pass: the columns.
+static_assert(2 * FAST_DEG <= 64, "a medium row's ids must fit two to a lane");
 __device__ __forceinline__ void mid_row(int lane, int32_t i, int32_t beg, int32_t d, const int2* __restrict__ adj,
                                         const int32_t* __restrict__ row_ptr, int32_t* __restrict__ row_nnz,
                                         int32_t* __restrict__ col_idx, int2* __restrict__ fan,
                                         int32_t* __restrict__ gen_list, int32_t* __restrict__ gen_count) {
-    const int n = 2 * d + 1;
-    int32_t v[3];
+    const int2 p = lane < d ? adj[beg + lane] : make_int2(INT32_MAX, INT32_MAX);
+    int32_t a0 = p.x, a1 = p.y;            // elements lane (slot 0) and lane + 32 (slot 1)
+    // (element 2t and 2t + 1 of the row are triangle t's two vertices; the network sorts any order)
 #pragma unroll
-    for (int s = 0; s < 3; s++) {
-        const int idx = lane + 32 * s;
-        int32_t x = INT32_MAX;
-        if (idx == 0) {
-            x = i;
-        } else if (idx < n) {
-            const int2 p = adj[beg + (idx - 1) / 2];
-            x = ((idx - 1) & 1) ? p.y : p.x;
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 32) {
+                // the partner is the same lane's other slot; for k = 64 every pair ascends
+                const int32_t lo = min(a0, a1), hi = max(a0, a1);
+                a0 = lo;
+                a1 = hi;
+            } else {
+                const int32_t o0 = __shfl_xor_sync(0xffffffffu, a0, j);
+                const int32_t o1 = __shfl_xor_sync(0xffffffffu, a1, j);
+                const bool lower = (lane & j) == 0;
+                const bool up0 = (lane & k) == 0, up1 = ((lane + 32) & k) == 0;
+                a0 = (up0 == lower) ? min(a0, o0) : max(a0, o0);
+                a1 = (up1 == lower) ? min(a1, o1) : max(a1, o1);
+            }
         }
-        v[s] = x;
     }
-    bool first[3];
-#pragma unroll
-    for (int s = 0; s < 3; s++) first[s] = lane + 32 * s < n;
-#pragma unroll
-    for (int s2 = 0; s2 < 3; s2++)
-        for (int l = 0; l < 32 && 32 * s2 + l < n; l++) {          // n is the same in every lane
-            const int32_t x = __shfl_sync(0xffffffffu, v[s2], l);
-            const int kk = 32 * s2 + l;
-#pragma unroll
-            for (int s = 0; s < 3; s++)
-                if (kk < lane + 32 * s && x == v[s]) first[s] = false;
-        }
+    // the element before each: lane - 1 of the same slot, or lane 31 of slot 0 for slot 1's lane 0
+    const int32_t prev0 = __shfl_up_sync(0xffffffffu, a0, 1);
+    int32_t prev1 = __shfl_up_sync(0xffffffffu, a1, 1);
+    const int32_t last0 = __shfl_sync(0xffffffffu, a0, 31);
+    if (lane == 0) prev1 = last0;
+    const bool new0 = a0 != INT32_MAX && (lane == 0 || a0 != prev0);
+    const bool new1 = a1 != INT32_MAX && a1 != prev1;
+    const unsigned b0 = __ballot_sync(0xffffffffu, new0), b1 = __ballot_sync(0xffffffffu, new1);
+    const int ndist = __popc(b0) + __popc(b1);
     if (!row_ptr) {
-        int cnt = 0;
-#pragma unroll
-        for (int s = 0; s < 3; s++) cnt += __popc(__ballot_sync(0xffffffffu, first[s]));
         if (lane == 0) {
-            row_nnz[i] = cnt;
+            row_nnz[i] = ndist + 1;
             gen_list[atomicAdd(gen_count, 1)] = i;
         }
-        const int2 p = lane < d ? adj[beg + lane] : make_int2(INT32_MAX, INT32_MAX);
         const long long key = ((long long)p.x << 32) | (unsigned)p.y;
         int rank = 0;
         for (int t = 0; t < d; t++) {
@@ -371,20 +374,15 @@ __device__ __forceinline__ void mid_row(int lane, int32_t i, int32_t beg, int32_
         if (lane < d) fan[beg + FE_IDX(rank, d)] = p;
         return;
     }
-    int rank[3] = {0, 0, 0};
-#pragma unroll
-    for (int s2 = 0; s2 < 3; s2++)
-        for (int l = 0; l < 32 && 32 * s2 + l < n; l++) {
-            const int32_t x = __shfl_sync(0xffffffffu, v[s2], l);
-            const bool f = __shfl_sync(0xffffffffu, first[s2], l);
-#pragma unroll
-            for (int s = 0; s < 3; s++) rank[s] += f && x < v[s];
-        }
+    const unsigned below = (1u << lane) - 1u;
+    const int r0 = __popc(b0 & below), r1 = __popc(b0) + __popc(b1 & below);
+    // i's place: the distinct neighbours below it
+    const int ri = __popc(__ballot_sync(0xffffffffu, new0 && a0 < i)) + __popc(__ballot_sync(0xffffffffu, new1 && a1 < i));
     const int32_t o = row_ptr[i], u = row_ptr[i + 1] - o;
     (void)u;                                                     // bounds of the checked build
-#pragma unroll
-    for (int s = 0; s < 3; s++)
-        if (first[s]) col_idx[o + FE_IDX(rank[s], u)] = v[s];
+    if (new0) col_idx[o + FE_IDX(r0 + (i < a0), u)] = a0;
+    if (new1) col_idx[o + FE_IDX(r1 + (i < a1), u)] = a1;
+    if (lane == 0) col_idx[o + FE_IDX(ri, u)] = i;
 }
 
 // General rows by k_row_big: those of more than FAST_DEG triangles one block each (the 2d+1
