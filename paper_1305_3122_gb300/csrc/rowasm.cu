@@ -56,7 +56,7 @@ struct RowTerms {
     ff w[3];       // unscaled M^w entries: D (s + 2 w_i), D (s - w_l / 2), D (s - w_j / 2)
 };
 
-// A badly shaped triangle (i, c, n) (an angle below about 14.5 degrees): the quantities that
+// A badly shaped triangle (i, c, n) (a small angle, see the shape tests): the quantities that
 // double-float arithmetic on the split relative coordinates would get wrong by too much come from
 // FP64 coordinate differences (each correctly rounded) and are then split: D = r_c x r_n (a
 // cancelling difference of products), the edge e_a = p_c - p_n (a difference of nearly equal
@@ -80,8 +80,19 @@ __device__ __forceinline__ void thin_terms(const double2* __restrict__ q, int32_
     if (dc) *dc = ff_from_value(fma(ex, cx, ey * cy), bad);     // e_a . r_c
 }
 
-// Shape test: sin^2 of each angle is D^2 over the product of the two adjacent squared edges;
-// all three must be at least 1/16 (angles of at least about 14.5 degrees) for the fast path.
+// Shape tests. sin^2 of an angle is D^2 over the product of its two squared edges.
+// For the scalar kinds only the angle at the row's own vertex i matters. D, the edge e_a and the
+// stiffness's dot products lose bits, relative to the row's largest entry, only when that angle is
+// small: D by 1/sin(angle at i); e_a when it is short against r; the dot products when the
+// other two angles are near 90 degrees, so that the row's entries are small. A small angle at c
+// or n makes the dot products' terms large, but the row's diagonal then grows as 1/sin of that
+// angle too. So the fast path needs sin^2(angle at i) >= 1/16 (about 14.5 degrees; scalar_shaped).
+// The elasticity blocks' mixed products are not covered by that argument, so they keep the test of
+// all three angles (well_shaped).
+__device__ __forceinline__ bool scalar_shaped(const Nb& j, const Nb& l, float dh) {
+    return 16.0f * dh * dh >= j.n * l.n;
+}
+
 __device__ __forceinline__ bool well_shaped(const Nb& j, const Nb& l, float dh) {
     float ex = j.x.h - l.x.h, ey = j.y.h - l.y.h;
     float eaa = ex * ex + ey * ey;
@@ -96,7 +107,7 @@ __device__ __forceinline__ RowTerms row_terms(const double2* __restrict__ q, con
     t.d = ff_dot2(j.x, l.x, l.y, ff_neg(j.y));                  // r_j x r_l
     ff ax = ff_sub(j.x, l.x), ay = ff_sub(j.y, l.y);            // e_a = r_j - r_l
     ff dl, dj;                                                  // e_a . r_l, e_a . r_j
-    if (well_shaped(j, l, t.d.h)) {
+    if (scalar_shaped(j, l, t.d.h)) {
         if (KIND & W_S) {
             dl = ff_dot2(ax, ay, l.x, l.y);
             dj = ff_dot2(ax, ay, j.x, j.y);
@@ -258,12 +269,9 @@ __device__ __forceinline__ FanNb fan_nb(const FanRaw& r, double2 pi, int& bad) {
     return b;
 }
 
-// Shape test on the float parts (sin^2 of every angle at least 1/16), as for row_terms; ex, ey
-// are the high words of e_a.
-__device__ __forceinline__ bool fan_well_shaped(const FanNb& c, const FanNb& n, float ex, float ey, float dh) {
-    float eaa = ex * ex + ey * ey;
-    float d2 = 16.0f * dh * dh;
-    return d2 >= c.n * n.n && d2 >= eaa * n.n && d2 >= eaa * c.n;
+// The scalar shape test (the angle at the row's vertex, as scalar_shaped) on the float parts.
+__device__ __forceinline__ bool fan_well_shaped(const FanNb& c, const FanNb& n, float dh) {
+    return 16.0f * dh * dh >= c.n * n.n;
 }
 
 // FP64 value of a row entry.
@@ -330,7 +338,7 @@ __device__ __forceinline__ void fan_row(int32_t i, const int32_t* __restrict__ r
         ff D = ff_dot2(cur.x, nxt.x, nxt.y, ff_neg(cur.y));          // r_c x r_n
         ff ax = ff_sub(cur.x, nxt.x), ay = ff_sub(cur.y, nxt.y);      // e_a
         ff dn, dc;                                                    // e_a . r_n, e_a . r_c
-        if (fan_well_shaped(cur, nxt, ax.h, ay.h, D.h)) {
+        if (fan_well_shaped(cur, nxt, D.h)) {
             if (DS) {
                 dn = ff_dot2(ax, ay, nxt.x, nxt.y);
                 dc = ff_dot2(ax, ay, cur.x, cur.y);
