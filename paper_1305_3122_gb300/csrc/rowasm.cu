@@ -1007,6 +1007,26 @@ cudaStream_t side_stream() {
     }
     return st;
 }
+
+// The call's events, created once per thread and device (creating and destroying nine events per
+// call put host-side driver work into every call).
+cudaEvent_t* host_call_events() {
+    static thread_local int dev = -1;
+    static thread_local cudaEvent_t ev[E2E_BLOCKS + 1] = {};
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d != dev) {
+        for (auto& e : ev) {
+            e = nullptr;                                 // the previous device's events are kept
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                dev = -1;
+                return nullptr;
+            }
+        }
+        dev = d;
+    }
+    return ev;
+}
 }  // namespace
 
 extern "C" fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const double* q, const int32_t* me,
@@ -1028,13 +1048,12 @@ extern "C" fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const
     int32_t* med = nullptr;
     double *qd = nullptr, *wd = nullptr, *Sd = nullptr, *Md = nullptr;
     VRec* vr = nullptr;
-    cudaEvent_t ev[E2E_BLOCKS + 1] = {};
+    cudaEvent_t* ev = host_call_events();
+    if (!ev) return fe_fail(FE_ERR_CUDA, "event creation");
     fe_status st = FE_OK;
     auto done = [&](fe_status ret) {
         cudaStreamSynchronize(s2);
         cudaStreamSynchronize(s);
-        for (auto& e : ev)
-            if (e) cudaEventDestroy(e);
         fe_free(vr);
         fe_free(Sd);
         fe_free(Md);
@@ -1045,8 +1064,6 @@ extern "C" fe_status fe_assemble_stiff_wmass_host(int32_t nq, int32_t nme, const
         if (m) fe_mesh_destroy(m);
         return ret;
     };
-    for (auto& e : ev)
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return done(fe_fail(FE_ERR_CUDA, "event creation"));
     // 1. the connectivity goes up first on the main stream; the coordinates and the weights follow
     //    on the side stream and arrive while the pattern is built (the pattern needs only me)
     if ((st = fe_alloc_n(&med, 3 * (size_t)nme, "mesh connectivity"))) return done(st);
