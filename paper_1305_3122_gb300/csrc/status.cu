@@ -237,44 +237,26 @@ __global__ void k_tile_sums(const int32_t* __restrict__ in, int64_t n, long long
     }
 }
 
-// One block of 1024 threads scans the tile sums in chunks of 1024 (exclusive), in place;
-// sums[ntiles] receives the total.
-__global__ void k_scan_sums(long long* sums, int64_t ntiles) {
-    __shared__ long long warp_tot[32];
-    __shared__ long long carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < ntiles; base += 1024) {
-        int64_t i = base + threadIdx.x;
-        long long v = i < ntiles ? sums[i] : 0;
-        long long x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if ((threadIdx.x & 31) >= o) x += y;
-        }
-        if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = x;
+// The tile's offset is the sum of the tile sums before it, which each block adds up itself (a few
+// KB, in L2; a separate one-block scan of the sums was a launch of pure latency). The last block
+// writes the total to sums[ntiles] and to out[n].
+__global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict__ out, int32_t* __restrict__ out2,
+                            int64_t n, long long* __restrict__ sums, int* __restrict__ overflow, int round, bool vec) {
+    __shared__ long long warp_tot[SCAN_BLOCK / 32];
+    __shared__ long long boff;
+    {
+        long long a = 0;
+        for (int64_t t = threadIdx.x; t < blockIdx.x; t += SCAN_BLOCK) a += sums[t];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = a;
         __syncthreads();
         if (threadIdx.x < 32) {
-            long long t = warp_tot[threadIdx.x];
-            for (int o = 1; o < 32; o <<= 1) {
-                long long y = __shfl_up_sync(0xffffffffu, t, o);
-                if (threadIdx.x >= o) t += y;
-            }
-            warp_tot[threadIdx.x] = t;   // inclusive over warps
+            a = threadIdx.x < SCAN_BLOCK / 32 ? warp_tot[threadIdx.x] : 0;
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (threadIdx.x == 0) boff = a;
         }
         __syncthreads();
-        long long warp_off = (threadIdx.x >> 5) ? warp_tot[(threadIdx.x >> 5) - 1] : 0;
-        if (i < ntiles) sums[i] = carry + warp_off + x - v;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += warp_tot[31];
-        __syncthreads();
     }
-    if (threadIdx.x == 0) sums[ntiles] = carry;
-}
-
-__global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict__ out, int32_t* __restrict__ out2,
-                            int64_t n, const long long* __restrict__ offs, int* __restrict__ overflow, int round, bool vec) {
-    __shared__ long long warp_tot[SCAN_BLOCK / 32];
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     long long v[SCAN_ITEMS];
     scan_load8(in, base, n, vec, round, v);
@@ -297,7 +279,7 @@ __global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict_
         if (threadIdx.x < SCAN_BLOCK / 32) warp_tot[threadIdx.x] = t;
     }
     __syncthreads();
-    long long run = offs[blockIdx.x] + ((threadIdx.x >> 5) ? warp_tot[(threadIdx.x >> 5) - 1] : 0) + x - local;
+    long long run = boff + ((threadIdx.x >> 5) ? warp_tot[(threadIdx.x >> 5) - 1] : 0) + x - local;
     if (vec && base + SCAN_ITEMS <= n) {
         int32_t r[SCAN_ITEMS];
 #pragma unroll
@@ -326,7 +308,8 @@ __global__ void k_tile_scan(const int32_t* __restrict__ in, int32_t* __restrict_
         }
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        long long tot = offs[gridDim.x];
+        long long tot = boff + warp_tot[SCAN_BLOCK / 32 - 1];
+        sums[gridDim.x] = tot;
         if (tot > INT32_MAX) *overflow = 1;
         out[n] = (int32_t)tot;
         if (out2) out2[n] = (int32_t)tot;
@@ -347,7 +330,6 @@ fe_status fe_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, cudaStre
     const bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) |
                        reinterpret_cast<uintptr_t>(out2)) & 15u) == 0;
     { FE_PROF("k_tile_sums", s); k_tile_sums<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, sums, round, vec); }
-    { FE_PROF("k_scan_sums", s); k_scan_sums<<<1, 1024, 0, s>>>(sums, ntiles); }
     { FE_PROF("k_tile_scan", s); k_tile_scan<<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, out2, n, sums, ovf, round, vec); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { fe_free(sums); fe_free(ovf); return fe_cuda_fail(e, "scan kernels"); }
