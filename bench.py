@@ -18,6 +18,8 @@ the timed steps. Also reported:
   - per-kernel shares of the step, each with its algorithmic bytes and HBM fraction;
   - unstructured: the same step on the random-diagonal 2048 x 2048 square (valences 4 to 8), and
     disk: on a Delaunay mesh of the unit disk from 2^20 random points (valences 3 to about 20);
+  - partition: the same mesh split into 2, 4 and 8 row ranges (halo triangles, no exchange of
+    values), each rank's step timed in turn on this GPU;
   - roofline of the dominant kernel, timed live with the library's own CUDA events;
   - the other legs: plane elasticity, the adjoint, zero dropping, tetrahedra, 3-D elasticity on
     tetrahedra, P2 and P3 triangles, each with both scatter variants where it has them;
@@ -500,6 +502,7 @@ def run_ours(args) -> int:
     if not args.no_other and args.variant == "row" and args.cells == N_CELLS:
         line["unstructured"] = unstructured(feasm, meshgen, torch, flush, stream)
         line["disk"] = disk(feasm, meshgen, torch, flush, stream)
+        line["partition"] = partition(feasm, meshgen, torch, flush)
     if not args.no_batched:
         line["batched"] = batched(feasm, meshgen, torch, args, hbm, peak_kind)
     if not args.no_other:
@@ -748,6 +751,56 @@ def _time_calls(torch, fn, flush, reps=20):
         ts.append(e0.elapsed_time(e1))
     ts.sort()
     return ts[len(ts) // 2]
+
+
+def partition(feasm, meshgen, torch, flush, worlds=(2, 4, 8), reps: int = 5) -> dict:
+    """The row partition of the headline mesh over `world` ranks (fe_mesh_create_part,
+    fe_pattern_build_part, the row owners on the rank's window): each rank's whole step (its halo
+    mesh from the global arrays, its rows' pattern, S + M^[w] of its rows, release) timed in turn on
+    this GPU, L2 flushed before each. The ranks exchange no values, so each rank's step on its
+    own GPU is this step; projected = all triangles / the slowest rank's step.
+    The mesh is the headline recipe with its nodes numbered row by row (permute=False), as a
+    partitioner would number them: an owned id range is then a band of the square and the halo is
+    one row of cells per cut. (With the headline's random numbering an id range is scattered over
+    the whole square, and each of two ranks holds about 87% of the triangles.)"""
+    from paper_1305_3122_gb300 import partition as part_rows
+    m = meshgen.square_mesh(N_CELLS, SEED, permute=False)
+    w = meshgen.vertex_weights(m, SEED)
+    q_d, me_d, w_d = (torch.tensor(a, device="cuda") for a in (m.q, m.me, w))
+    nq, nme = m.nq, m.nme
+    whole = _time_calls(torch, lambda: _whole_step(feasm, q_d, me_d, w_d), flush, reps=reps)
+    out = {}
+    for world in worlds:
+        ranks = []
+        halo = 0
+        for r0, r1 in part_rows.row_ranges(nq, world):
+            def step():
+                mesh = feasm.Mesh.part(q_d, me_d, r0, r1)
+                pat = feasm.Pattern(mesh, rows=(r0, r1), map=False)
+                feasm.assemble_stiff_wmass(mesh, pat, w_d, feasm.ROW)
+                pat.close()
+                mesh.close()
+            ranks.append(_time_calls(torch, step, flush, reps=reps))
+            probe = feasm.Mesh.part(q_d, me_d, r0, r1)
+            halo += probe.nme
+            probe.close()
+        worst = max(ranks)
+        out[str(world)] = {"rank_ms": [round(t, 4) for t in ranks], "rank_ms_max": round(worst, 4),
+                           "triangles_held_over_nme": round(halo / nme, 4),
+                           "projected_value": round(nme / worst / 1e3, 1), "unit": UNIT}
+    return {"workload": f"row partition of the {N_CELLS}x{N_CELLS}-cell headline mesh, nodes numbered row by row, "
+                        "S + M^[w] by row owners",
+            "how": "each rank's step timed in turn on one GPU (median of 5 between L2 flushes); the ranks exchange "
+                   "no values, so the projection for `world` GPUs is nme / the slowest rank's step",
+            "whole_ms": round(whole, 4), "worlds": out}
+
+
+def _whole_step(feasm, q_d, me_d, w_d):
+    mesh = feasm.Mesh(q_d, me_d, borrow=True)
+    pat = feasm.Pattern(mesh, map=False)
+    feasm.assemble_stiff_wmass(mesh, pat, w_d, feasm.ROW)
+    pat.close()
+    mesh.close()
 
 
 def elasticity(feasm, meshgen, torch, flush, hbm, peak_kind) -> dict:
