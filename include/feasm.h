@@ -110,9 +110,10 @@ enum {
 fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, const int32_t* me,
                          int ptr_kind, fe_stream stream, fe_mesh* out);
 
-/* Replaces the coordinates (same topology), e.g. for finite differences or moving meshes.
- * Asynchronous; does not re-validate orientation (assembly calls report it, see
- * fe_mesh_check). */
+/* Replaces the coordinates (same topology), e.g. for finite differences or moving meshes: q
+ * [2][nq] (for a part, the global mesh's q, from which it takes its vertices' points).
+ * Asynchronous for device arrays; does not re-validate orientation (assembly calls report it,
+ * see fe_mesh_check). */
 fe_status fe_mesh_set_coords(fe_mesh mesh, const double* q, int ptr_kind, fe_stream stream);
 /* (ptr_kind: FE_PTR_HOST or FE_PTR_DEVICE; FE_PTR_DEVICE_BORROW is taken as FE_PTR_DEVICE.) */
 
@@ -122,6 +123,7 @@ fe_status fe_mesh_set_coords(fe_mesh mesh, const double* q, int ptr_kind, fe_str
  * [2^-74, 2^128) (FE_ERR_LIMIT; such values are then taken as zero). Synchronises the stream. */
 fe_status fe_mesh_check(fe_mesh mesh, fe_stream stream);
 
+/* The mesh's vertex and triangle counts (a part: the global nq and the triangles it keeps). */
 fe_status fe_mesh_info(fe_mesh mesh, int32_t* nq, int32_t* nme);
 void fe_mesh_destroy(fe_mesh mesh);
 
@@ -227,11 +229,17 @@ fe_status fe_assemble_stiff_wmass_noalloc(fe_mesh mesh, fe_pattern pattern, cons
  * communicate nothing, the caller launches the ranks and collects their blocks.
  *
  * fe_mesh_create_part: from the global mesh (q [2][nq], me [3][nme], host or device as for
- * fe_mesh_create), keeps the triangles touching [row_begin, row_end) in ascending order with
- * their global vertex ids (the selection and compaction run on the device) and all nq
- * coordinates. Checks the kept triangles as fe_mesh_create does, reporting global triangle
+ * fe_mesh_create), keeps the triangles touching [row_begin, row_end) in ascending order (the
+ * selection and compaction run on the device) and the coordinates of their vertices. Inside the
+ * library the part numbers its vertices locally, so its memory and the work of every later call
+ * scale with the part, not with the global mesh; every id the calls take or return stays global:
+ * fe_mesh_info reports the global nq and the kept triangle count, fe_mesh_set_coords takes the
+ * global q [2][nq], weights w are indexed by global vertex id (nq entries), and row windows list
+ * global column ids. Checks the kept triangles as fe_mesh_create does, reporting global triangle
  * indices, and any vertex id outside [0, nq) (FE_ERR_INDEX_RANGE); 0 <= row_begin <= row_end
- * <= nq (FE_ERR_INVALID_ARG). Synchronises. Destroy with fe_mesh_destroy. */
+ * <= nq (FE_ERR_INVALID_ARG). A part builds row windows of its owned rows only
+ * (fe_pattern_build_part; fe_pattern_build on a part is FE_ERR_INVALID_ARG). Synchronises once.
+ * Destroy with fe_mesh_destroy. */
 fe_status fe_mesh_create_part(int32_t nq, int32_t nme, const double* q, const int32_t* me, int ptr_kind,
                               int32_t row_begin, int32_t row_end, fe_stream stream, fe_mesh* out);
 

@@ -197,6 +197,13 @@ __device__ __forceinline__ int32_t pos2(int32_t p, int32_t rb, int32_t g, int al
     return 4 * rb + 2 * alpha * g + 2 * (p - rb) + beta;
 }
 
+// A part's weights, given by global vertex id, in its local numbering: wl[i] = w[l2g[i]].
+__global__ void k_part_weights(const double* __restrict__ w, const int32_t* __restrict__ l2g, int32_t n,
+                               double* __restrict__ wl) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        wl[i] = w[l2g[i]];
+}
+
 __global__ void k_elas_atomic(const double2* __restrict__ q, const int32_t* __restrict__ me, int32_t nme,
                               const int32_t* __restrict__ map, const int32_t* __restrict__ row_ptr,
                               double lam, double mu, double* __restrict__ out, int* __restrict__ err, int64_t nnz4) {
@@ -314,7 +321,16 @@ static fe_status scalar(int kind, fe_mesh m, fe_pattern p, const double* w, int 
     m->last_stream = p->last_stream = s;
     if (variant == FE_VARIANT_ROW) {
         static const int bits[4] = {4, 2, 1, 3};   // K_MASS, K_WMASS, K_STIFF, K_STIFF_WMASS
-        return fe_row_scalar(bits[kind], m, p, w, out0, out1, s);
+        if (m->part1 < 0 || !(kind == K_WMASS || kind == K_STIFF_WMASS) || m->nq == 0)
+            return fe_row_scalar(bits[kind], m, p, w, out0, out1, s);
+        FeStreamScope scope(s);
+        double* wl = nullptr;
+        if ((st = fe_alloc_n(&wl, (size_t)m->nq, "part weights"))) return st;
+        { FE_PROF("k_part_weights", s); k_part_weights<<<fe_grid(m->nq, 256), 256, 0, s>>>(w, m->l2g, m->nq, wl); }
+        cudaError_t e = cudaGetLastError();
+        st = e != cudaSuccess ? fe_cuda_fail(e, "k_part_weights") : fe_row_scalar(bits[kind], m, p, wl, out0, out1, s);
+        fe_free(wl);
+        return st;
     }
     if (variant == FE_VARIANT_ATOMIC) {
         if (p->nnz > 0) FE_CUDA(cudaMemsetAsync(out0, 0, sizeof(double) * p->nnz, s));

@@ -22,7 +22,14 @@ struct fe_mesh_s {
                                 // bit 1 = a value outside the double-float range (see ff.cuh)
     uint64_t topology_id = 0;   // identifies the connectivity (patterns remember it)
     int32_t part0 = 0, part1 = -1;        // a rank's share of a row partition: owned rows [part0, part1)
-                                          // (part1 < 0: a whole mesh)
+                                          // of the global numbering (part1 < 0: a whole mesh)
+    // A part numbers its vertices locally: local id = rank of the global id among the part's
+    // vertices (those of its triangles and its owned rows), so the order of ids is kept and the
+    // owned rows are the contiguous local ids [loc0, loc0 + part1 - part0). nq, q, me and deg
+    // are local; every id the calls take or return is global.
+    int32_t* l2g = nullptr;               // [nq] global id of each local vertex (parts only)
+    int32_t nq_global = 0;                // the global mesh's nq (parts only)
+    int32_t loc0 = 0;                     // local id of the first owned row (parts only)
     cudaStream_t last_stream = nullptr;   // frees are ordered on the last stream that used the handle
 };
 
@@ -57,6 +64,7 @@ struct fe_pattern_s {
     int32_t row0 = 0, row1 = -1;
     int32_t* row_ptr_w = nullptr;         // [row1 - row0 + 1] the window's offsets, from 0
     int64_t base_w = 0;                   // row_ptr[row0]: the window's first entry in the full arrays
+    int32_t* col_idx_w = nullptr;         // a part's window: its column ids in the global numbering
     cudaStream_t last_stream = nullptr;
 };
 
@@ -155,12 +163,18 @@ uint64_t fe_next_topology_id();
 
 // Staged mesh creation for the one-shot host call (mesh.cu): the connectivity (device array,
 // owned by the mesh afterwards) is checked for range, repeats and valences with one
-// synchronisation; fe_mesh_attach_coords packs device coordinates [2][nq] and queues the
+// synchronisation (checked = false: valences only, for connectivity built by the library itself,
+// with no synchronisation); fe_mesh_attach_coords packs device coordinates [2][nq] and queues the
 // orientation check (no synchronisation); fe_mesh_orientation_status interprets the error word
 // read back afterwards (4 ints).
-fe_status fe_mesh_create_topology(int32_t nq, int32_t nme, int32_t* me_dev, cudaStream_t s, fe_mesh* out);
+fe_status fe_mesh_create_topology(int32_t nq, int32_t nme, int32_t* me_dev, cudaStream_t s, fe_mesh* out,
+                                 bool checked = true);
 fe_status fe_mesh_attach_coords(fe_mesh m, const double* q_dev, cudaStream_t s);
 fe_status fe_mesh_orientation_status(const int word[4]);
+
+// The scalar pattern of any mesh, a part included, without the map or gather lists (pattern.cu);
+// fe_pattern_build_part cuts its row window out of it.
+fe_status fe_pattern_build_rows(fe_mesh m, fe_stream stream, fe_pattern* out);
 
 // High float (top 24 significant bits, truncated) of a double, by bit operations: no FP64
 // instruction. |result - x| < 2^-23 |x|; zero and subnormals give zero, magnitudes above the

@@ -17,6 +17,15 @@ __global__ void k_pack_coords(const double* __restrict__ q, int32_t nq, double2*
         q2[i] = make_double2(q[i], q[nq + i]);
 }
 
+// A part's coordinates from the global array: q [2][nq_global] -> q2 [nq], q2[i] = point l2g[i]
+__global__ void k_pack_coords_part(const double* __restrict__ q, int32_t nq_global, const int32_t* __restrict__ l2g,
+                                   int32_t nq, double2* __restrict__ q2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = l2g[i];
+        q2[i] = make_double2(q[g], q[nq_global + g]);
+    }
+}
+
 // Validation word layout: [0] = OR of error bits, [1] = first bad triangle (min), per kind.
 enum { BAD_RANGE = 1, BAD_REPEAT = 2, BAD_ORIENT = 4 };
 
@@ -128,18 +137,22 @@ static fe_status copy_in(void* dst, const void* src, size_t bytes, int ptr_kind,
     return FE_OK;
 }
 
+// q [2][n] with n = nq, or for a part the global nq (the part gathers its vertices' points)
 static fe_status set_coords(fe_mesh m, const double* q, int ptr_kind, cudaStream_t s) {
     if (m->nq == 0) return FE_OK;
+    const bool part = m->part1 >= 0;
+    const int32_t n = part ? m->nq_global : m->nq;
     const double* qd = q;
     double* tmp = nullptr;
     if (ptr_kind == FE_PTR_HOST) {
-        fe_status st = fe_alloc_n(&tmp, 2 * (size_t)m->nq, "coordinate staging");
+        fe_status st = fe_alloc_n(&tmp, 2 * (size_t)n, "coordinate staging");
         if (st) return st;
-        st = copy_in(tmp, q, 2 * (size_t)m->nq * sizeof(double), ptr_kind, s);
+        st = copy_in(tmp, q, 2 * (size_t)n * sizeof(double), ptr_kind, s);
         if (st) { fe_free(tmp); return st; }
         qd = tmp;
     }
-    { FE_PROF("k_pack_coords", s); k_pack_coords<<<fe_grid(m->nq, 256), 256, 0, s>>>(qd, m->nq, m->q); }
+    if (part) { FE_PROF("k_pack_coords_part", s); k_pack_coords_part<<<fe_grid(m->nq, 256), 256, 0, s>>>(qd, n, m->l2g, m->nq, m->q); }
+    else { FE_PROF("k_pack_coords", s); k_pack_coords<<<fe_grid(m->nq, 256), 256, 0, s>>>(qd, m->nq, m->q); }
     cudaError_t e = cudaGetLastError();
     if (tmp) {
         cudaError_t e2 = cudaStreamSynchronize(s);
@@ -157,6 +170,7 @@ extern "C" void fe_mesh_destroy(fe_mesh m) {
     if (m->me_owned) fe_free(m->me);
     fe_free(m->err);
     fe_free(m->deg);
+    fe_free(m->l2g);
     delete m;
 }
 
@@ -230,7 +244,8 @@ extern "C" fe_status fe_mesh_create(int32_t nq, int32_t nme, const double* q, co
 // is all the pattern build needs; fe_mesh_attach_coords then packs the coordinates and queues the
 // orientation check, whose result fe_mesh_orientation_status reads from the validation word.
 
-fe_status fe_mesh_create_topology(int32_t nq, int32_t nme, int32_t* me_dev, cudaStream_t s, fe_mesh* out) {
+fe_status fe_mesh_create_topology(int32_t nq, int32_t nme, int32_t* me_dev, cudaStream_t s, fe_mesh* out,
+                                 bool checked) {
     *out = nullptr;
     fe_mesh m = new fe_mesh_s();
     m->last_stream = s;
@@ -250,6 +265,12 @@ fe_status fe_mesh_create_topology(int32_t nq, int32_t nme, int32_t* me_dev, cuda
     if (e == cudaSuccess && nme > 0) {
         { FE_PROF("k_validate", s); k_validate<<<fe_grid(((int64_t)nme + 1) / 2, 256, 16), 256, 0, s>>>(m->q, nq, m->me, nme, m->err, m->deg, VAL_TOPOLOGY); }
         e = cudaGetLastError();
+    }
+    if (!checked) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->err, 0, sizeof(int) * 4, s);
+        if (e != cudaSuccess) { fe_mesh_destroy(m); return fe_cuda_fail(e, "valence count"); }
+        *out = m;
+        return FE_OK;
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(word, m->err, sizeof word, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -315,7 +336,7 @@ extern "C" fe_status fe_mesh_check(fe_mesh m, fe_stream stream) {
 
 extern "C" fe_status fe_mesh_info(fe_mesh m, int32_t* nq, int32_t* nme) {
     if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");
-    if (nq) *nq = m->nq;
+    if (nq) *nq = m->part1 >= 0 ? m->nq_global : m->nq;     // a part: the global id space
     if (nme) *nme = m->nme;
     return FE_OK;
 }

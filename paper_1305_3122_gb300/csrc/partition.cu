@@ -9,10 +9,17 @@
 // and how their row blocks are collected is up to the caller.
 //
 //   fe_mesh_create_part    keeps the triangles of a global mesh that touch the owned rows
-//                          (selected and compacted on the device, in ascending triangle order,
-//                          with global vertex ids), checks every triangle of the global mesh that
-//                          it keeps, and counts valences for the pattern build.
-//   fe_pattern_build_part  the CSR rows [row_begin, row_end) of a mesh (a part, or a whole mesh).
+//                          (selected and compacted on the device, in ascending triangle order),
+//                          checks every triangle that it keeps, and numbers the part's vertices
+//                          locally (the rank of each global id among them), so that everything
+//                          after it -- valences, the pattern, the vertex records -- is sized by
+//                          the part, not by the global mesh.
+//   fe_pattern_build_part  the CSR rows [row_begin, row_end) of a part or of a whole mesh; a
+//                          part's window maps its columns back to global ids.
+//
+// The local numbering keeps the order of the global ids, so each row's columns and its triangle
+// fan come out in the same order as in the whole mesh, and the row-owner assembly gives each row
+// the same bits.
 #include <string>
 
 #include "internal.cuh"
@@ -21,13 +28,18 @@ namespace {
 
 enum { PART_RANGE = 1, PART_REPEAT = 2, PART_ORIENT = 4 };
 
-// keep[k] = 1 if triangle k has a vertex in [r0, r1). Every kept triangle is checked as in the
-// mesh validation (ids in range, distinct, counter-clockwise: D > 0 in FP64 from coordinate
-// differences); word: [0] OR of the problems, [1..3] the first bad triangle of each kind (global
-// index). A triangle with an id out of range anywhere is reported, kept or not.
+// keep[k] = 1 if triangle k has a vertex in [r0, r1); used[v] = 1 for every vertex of a kept
+// triangle and every owned vertex (used is zero on entry; threads that mark the same vertex write
+// the same value). Every kept triangle is checked as in the mesh validation (ids in range,
+// distinct, counter-clockwise: D > 0 in FP64 from coordinate differences); word: [0] OR of the
+// problems, [1..3] the first bad triangle of each kind (global index). A triangle with an id out
+// of range anywhere is reported, kept or not.
 __global__ void k_part_select(const int32_t* __restrict__ me, int32_t nme, int32_t nq, const double* __restrict__ q,
-                              int32_t r0, int32_t r1, int32_t* __restrict__ keep, int* __restrict__ word) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
+                              int32_t r0, int32_t r1, int32_t* __restrict__ keep, int32_t* __restrict__ used,
+                              int* __restrict__ word) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < r1; v += stride) used[v] = 1;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += stride) {
         const int32_t v0 = me[k], v1 = me[nme + k], v2 = me[2 * (int64_t)nme + k];
         const bool in = v0 >= 0 && v0 < nq && v1 >= 0 && v1 < nq && v2 >= 0 && v2 < nq;
         const bool mine = (v0 >= r0 && v0 < r1) || (v1 >= r0 && v1 < r1) || (v2 >= r0 && v2 < r1);
@@ -41,6 +53,11 @@ __global__ void k_part_select(const int32_t* __restrict__ me, int32_t nme, int32
             const double wx = x0 - q[v1], wy = y0 - q[nq + v1];          // p0 - p1
             if (!(vx * wy - wx * vy > 0.0)) bad = PART_ORIENT;
         }
+        if (in && mine) {
+            used[v0] = 1;
+            used[v1] = 1;
+            used[v2] = 1;
+        }
         if (bad) {
             atomicOr(&word[0], bad);
             atomicMin(&word[bad == PART_RANGE ? 1 : bad == PART_REPEAT ? 2 : 3], (int)k);
@@ -48,15 +65,28 @@ __global__ void k_part_select(const int32_t* __restrict__ me, int32_t nme, int32
     }
 }
 
-// The kept triangles, in ascending order, into me_part [3][n_part] (pos = exclusive scan of keep).
+// The kept triangles, in ascending order, into me_part [3][n_part] (pos = exclusive scan of
+// keep), their vertices renumbered by loc (exclusive scan of used).
 __global__ void k_part_compact(const int32_t* __restrict__ me, int32_t nme, const int32_t* __restrict__ keep,
-                               const int32_t* __restrict__ pos, int32_t n_part, int32_t* __restrict__ me_part) {
+                               const int32_t* __restrict__ pos, const int32_t* __restrict__ loc, int32_t n_part,
+                               int32_t* __restrict__ me_part) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
         if (!keep[k]) continue;
         const int64_t at = pos[k];
-        me_part[at] = me[k];
-        me_part[n_part + at] = me[nme + k];
-        me_part[2 * (int64_t)n_part + at] = me[2 * (int64_t)nme + k];
+        me_part[at] = loc[me[k]];
+        me_part[n_part + at] = loc[me[nme + k]];
+        me_part[2 * (int64_t)n_part + at] = loc[me[2 * (int64_t)nme + k]];
+    }
+}
+
+// The part's vertices: l2g[loc[v]] = v and their points q2[loc[v]] = (x, y) for every used v.
+__global__ void k_part_vertices(const double* __restrict__ q, int32_t nq, const int32_t* __restrict__ used,
+                                const int32_t* __restrict__ loc, int32_t* __restrict__ l2g, double2* __restrict__ q2) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nq; v += (int64_t)gridDim.x * blockDim.x) {
+        if (!used[v]) continue;
+        const int32_t l = loc[v];
+        l2g[l] = (int32_t)v;
+        q2[l] = make_double2(q[v], q[nq + v]);
     }
 }
 
@@ -65,6 +95,13 @@ __global__ void k_window_offsets(const int32_t* __restrict__ row_ptr, int32_t r0
     const int32_t base = row_ptr[r0];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= n; t += (int64_t)gridDim.x * blockDim.x)
         out[t] = row_ptr[r0 + t] - base;
+}
+
+// A part's window columns in the global numbering: out[e] = l2g[col[e]].
+__global__ void k_window_columns(const int32_t* __restrict__ col, int64_t nnz, const int32_t* __restrict__ l2g,
+                                 int32_t* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = l2g[col[e]];
 }
 
 }  // namespace
@@ -85,11 +122,11 @@ extern "C" fe_status fe_mesh_create_part(int32_t nq, int32_t nme, const double* 
     FeStreamScope scope(s);
     const bool host = ptr_kind == FE_PTR_HOST;
     double* q_tmp = nullptr;
-    int32_t *me_tmp = nullptr, *keep = nullptr, *pos = nullptr, *me_part = nullptr;
+    int32_t *me_tmp = nullptr, *keep = nullptr, *pos = nullptr, *used = nullptr, *loc = nullptr, *me_part = nullptr;
     int* word = nullptr;
+    // frees are ordered on the stream after the kernels that read these arrays
     auto cleanup = [&]() {
-        cudaStreamSynchronize(s);
-        fe_free(q_tmp); fe_free(me_tmp); fe_free(keep); fe_free(pos); fe_free(word);
+        fe_free(q_tmp); fe_free(me_tmp); fe_free(keep); fe_free(pos); fe_free(used); fe_free(loc); fe_free(word);
     };
     fe_status st = FE_OK;
     const double* qd = q;
@@ -107,19 +144,31 @@ extern "C" fe_status fe_mesh_create_part(int32_t nq, int32_t nme, const double* 
     }
     if (!st) st = fe_alloc_n(&keep, (size_t)nme + 1, "halo flags");
     if (!st) st = fe_alloc_n(&pos, (size_t)nme + 1, "halo positions");
+    if (!st) st = fe_alloc_n(&used, (size_t)nq + 1, "part vertex flags");
+    if (!st) st = fe_alloc_n(&loc, (size_t)nq + 1, "local vertex ids");
     if (!st) st = fe_alloc_n(&word, 4, "selection word");
     if (st) { cleanup(); return st; }
-    int host_word[4] = {0, 0, 0, 0};
-    int64_t n_part = 0;
+    // 1. select the triangles and the vertices; 2. number both by exclusive scans (the totals land
+    // in pos[nme] and loc[nq]); one read-back of the word, the two totals and loc[row_begin]
     cudaError_t e = cudaMemsetAsync(word, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(word + 1, 0x7F, 3 * sizeof(int), s);
-    if (e == cudaSuccess && nme > 0) {
-        { FE_PROF("k_part_select", s); k_part_select<<<fe_grid(nme, 256), 256, 0, s>>>(med, nme, nq, qd, row_begin, row_end, keep, word); }
+    if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, sizeof(int32_t) * ((size_t)nq + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pos, 0, sizeof(int32_t), s);      // the totals when nme or nq is 0
+    if (e == cudaSuccess) e = cudaMemsetAsync(loc, 0, sizeof(int32_t), s);
+    const int64_t sel_n = nme > row_end - row_begin ? (int64_t)nme : (int64_t)row_end - row_begin;
+    if (e == cudaSuccess && sel_n > 0) {
+        { FE_PROF("k_part_select", s); k_part_select<<<fe_grid(sel_n, 256), 256, 0, s>>>(med, nme, nq, qd, row_begin, row_end, keep, used, word); }
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) { cleanup(); return fe_cuda_fail(e, "halo selection"); }
-    if (nme > 0 && (st = fe_exclusive_scan(keep, pos, nme, s, &n_part))) { cleanup(); return st; }   // synchronises
+    if (nme > 0 && (st = fe_exclusive_scan(keep, pos, nme, s, nullptr))) { cleanup(); return st; }
+    if (nq > 0 && (st = fe_exclusive_scan(used, loc, nq, s, nullptr))) { cleanup(); return st; }
+    int host_word[4] = {0, 0, 0, 0};
+    int32_t n_part = 0, n_loc = 0, loc0 = 0;
     e = cudaMemcpyAsync(host_word, word, sizeof host_word, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n_part, pos + nme, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n_loc, loc + nq, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&loc0, loc + row_begin, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { cleanup(); return fe_cuda_fail(e, "halo selection"); }
     if (host_word[0] & PART_RANGE) {
@@ -135,26 +184,28 @@ extern "C" fe_status fe_mesh_create_part(int32_t nq, int32_t nme, const double* 
         return fe_fail(FE_ERR_ORIENTATION, "triangle " + std::to_string(host_word[3]) +
                                                " has signed area <= 0 (must be counter-clockwise)");
     }
+    // 3. the kept triangles with local ids; the part as a mesh of its own (its connectivity passes
+    // to the mesh, whose creation counts the valences the pattern build needs: every id was
+    // checked above, so without a second check or read-back); its vertices' points and global ids
     if ((st = fe_alloc_n(&me_part, 3 * (size_t)n_part, "halo connectivity"))) { cleanup(); return st; }
     if (n_part > 0) {
-        { FE_PROF("k_part_compact", s); k_part_compact<<<fe_grid(nme, 256), 256, 0, s>>>(med, nme, keep, pos, (int32_t)n_part, me_part); }
+        { FE_PROF("k_part_compact", s); k_part_compact<<<fe_grid(nme, 256), 256, 0, s>>>(med, nme, keep, pos, loc, n_part, me_part); }
         e = cudaGetLastError();
         if (e != cudaSuccess) { fe_free(me_part); cleanup(); return fe_cuda_fail(e, "halo compaction"); }
     }
-    // the part as a mesh of its own (global vertex ids, all nq coordinates): the connectivity
-    // passes to the mesh, whose creation counts the valences the pattern build needs
     fe_mesh m = nullptr;
-    if ((st = fe_mesh_create_topology(nq, (int32_t)n_part, me_part, s, &m))) { cleanup(); return st; }
-    if ((st = fe_mesh_attach_coords(m, qd, s))) { cleanup(); fe_mesh_destroy(m); return st; }
-    int mword[4] = {0, 0, 0, 0};
-    e = cudaMemcpyAsync(mword, m->err, sizeof mword, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m->err, 0, sizeof(int), s);
+    if ((st = fe_mesh_create_topology(n_loc, n_part, me_part, s, &m, false))) { cleanup(); return st; }
+    if ((st = fe_alloc_n(&m->l2g, (size_t)n_loc, "local-to-global vertex ids"))) { cleanup(); fe_mesh_destroy(m); return st; }
+    if (n_loc > 0) {
+        { FE_PROF("k_part_vertices", s); k_part_vertices<<<fe_grid(nq, 256), 256, 0, s>>>(qd, nq, used, loc, m->l2g, m->q); }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { cleanup(); fe_mesh_destroy(m); return fe_cuda_fail(e, "part vertices"); }
+    }
     cleanup();
-    if (e != cudaSuccess) { fe_mesh_destroy(m); return fe_cuda_fail(e, "part validation"); }
-    if ((st = fe_mesh_orientation_status(mword))) { fe_mesh_destroy(m); return st; }
     m->part0 = row_begin;
     m->part1 = row_end;
+    m->nq_global = nq;
+    m->loc0 = loc0;
     *out = m;
     return FE_OK;
 }
@@ -165,31 +216,43 @@ extern "C" fe_status fe_pattern_build_part(fe_mesh m, int32_t row_begin, int32_t
     if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
     if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");
-    const int32_t lo = m->part1 >= 0 ? m->part0 : 0, hi = m->part1 >= 0 ? m->part1 : m->nq;
+    const bool part = m->part1 >= 0;
+    const int32_t lo = part ? m->part0 : 0, hi = part ? m->part1 : m->nq;
     if (row_begin < lo || row_end < row_begin || row_end > hi)
         return fe_fail(FE_ERR_INVALID_ARG, "the row window must lie in [0, nq) and, for a part, in its owned rows");
     fe_pattern p = nullptr;
-    fe_status st = fe_pattern_build(m, 1, FE_PATTERN_DEFAULT, stream, &p);
+    fe_status st = fe_pattern_build_rows(m, stream, &p);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     FeStreamScope scope(s);
     const int32_t n = row_end - row_begin;
+    const int32_t r0 = part ? row_begin - m->part0 + m->loc0 : row_begin;      // the window in the mesh's ids
     st = fe_alloc_n(&p->row_ptr_w, (size_t)n + 1, "window offsets");
     int32_t ends[2] = {0, 0};
     if (!st) {
-        { FE_PROF("k_window_offsets", s); k_window_offsets<<<fe_grid((int64_t)n + 1, 256), 256, 0, s>>>(p->row_ptr, row_begin, n, p->row_ptr_w); }
+        { FE_PROF("k_window_offsets", s); k_window_offsets<<<fe_grid((int64_t)n + 1, 256), 256, 0, s>>>(p->row_ptr, r0, n, p->row_ptr_w); }
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[0], p->row_ptr + row_begin, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], p->row_ptr + row_end, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[0], p->row_ptr + r0, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], p->row_ptr + r0 + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = fe_cuda_fail(e, "row window");
     }
+    const int64_t nnz = (int64_t)ends[1] - ends[0];
+    if (!st && part) {
+        // the columns the caller sees carry global ids; the kernels keep reading the local ones
+        st = fe_alloc_n(&p->col_idx_w, (size_t)nnz, "window columns");
+        if (!st && nnz > 0) {
+            { FE_PROF("k_window_columns", s); k_window_columns<<<fe_grid(nnz, 256), 256, 0, s>>>(p->col_idx + ends[0], nnz, m->l2g, p->col_idx_w); }
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) st = fe_cuda_fail(e, "window columns");
+        }
+    }
     if (st) { fe_pattern_destroy(p); return st; }
-    p->row0 = row_begin;
-    p->row1 = row_end;
+    p->row0 = r0;
+    p->row1 = r0 + n;
     p->base_w = ends[0];
     p->n_rows = n;
-    p->nnz = (int64_t)ends[1] - ends[0];
+    p->nnz = nnz;
     *out = p;
     return FE_OK;
 }

@@ -635,6 +635,7 @@ extern "C" void fe_pattern_destroy(fe_pattern p) {
     fe_free(p->row_ptr2); fe_free(p->col_idx2);
     fe_free(p->seg_ptr); fe_free(p->perm); fe_free(p->vptr); fe_free(p->vel); fe_free(p->kg);
     fe_free(p->fan); fe_free(p->hdr); fe_free(p->gen_rows); fe_free(p->row_ptr_w);
+    fe_free(p->col_idx_w);
     delete p;
 }
 
@@ -789,15 +790,7 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     return FE_OK;
 }
 
-extern "C" fe_status fe_pattern_build(fe_mesh m, int dofs, int flags, fe_stream stream, fe_pattern* out) {
-    FE_RANGE(__func__);
-    if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
-    *out = nullptr;
-    if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");
-    if (dofs != 1 && dofs != 2) return fe_fail(FE_ERR_INVALID_ARG, "dofs_per_vertex must be 1 or 2");
-    if (flags & ~(FE_PATTERN_GATHER | FE_PATTERN_MAP)) return fe_fail(FE_ERR_INVALID_ARG, "unknown pattern flag");
-    if (dofs == 2 && 36 * (int64_t)m->nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "36*nme must be < 2^31");
-    if (9 * (int64_t)m->nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "9*nme must be < 2^31");
+static fe_status pattern_new(fe_mesh m, int dofs, int flags, fe_stream stream, fe_pattern* out) {
     fe_pattern p = new fe_pattern_s();
     p->dofs = dofs;
     p->flags = flags;
@@ -816,6 +809,27 @@ extern "C" fe_status fe_pattern_build(fe_mesh m, int dofs, int flags, fe_stream 
     return FE_OK;
 }
 
+extern "C" fe_status fe_pattern_build(fe_mesh m, int dofs, int flags, fe_stream stream, fe_pattern* out) {
+    FE_RANGE(__func__);
+    if (!out) return fe_fail(FE_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (!m) return fe_fail(FE_ERR_INVALID_ARG, "null mesh");
+    if (m->part1 >= 0)
+        return fe_fail(FE_ERR_INVALID_ARG, "a part (fe_mesh_create_part) builds row windows of its owned rows only "
+                                           "(fe_pattern_build_part)");
+    if (dofs != 1 && dofs != 2) return fe_fail(FE_ERR_INVALID_ARG, "dofs_per_vertex must be 1 or 2");
+    if (flags & ~(FE_PATTERN_GATHER | FE_PATTERN_MAP)) return fe_fail(FE_ERR_INVALID_ARG, "unknown pattern flag");
+    if (dofs == 2 && 36 * (int64_t)m->nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "36*nme must be < 2^31");
+    if (9 * (int64_t)m->nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "9*nme must be < 2^31");
+    return pattern_new(m, dofs, flags, stream, out);
+}
+
+fe_status fe_pattern_build_rows(fe_mesh m, fe_stream stream, fe_pattern* out) {
+    *out = nullptr;
+    if (9 * (int64_t)m->nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "9*nme must be < 2^31");
+    return pattern_new(m, 1, FE_PATTERN_DEFAULT, stream, out);
+}
+
 extern "C" fe_status fe_pattern_info(fe_pattern p, int64_t* n_rows, int64_t* nnz, const int32_t** row_ptr,
                                      const int32_t** col_idx) {
     if (!p) return fe_fail(FE_ERR_INVALID_ARG, "null pattern");
@@ -823,7 +837,7 @@ extern "C" fe_status fe_pattern_info(fe_pattern p, int64_t* n_rows, int64_t* nnz
     if (nnz) *nnz = p->nnz;
     if (p->row1 >= 0) {                                   // a row window: its rows only
         if (row_ptr) *row_ptr = p->row_ptr_w;
-        if (col_idx) *col_idx = p->col_idx + p->base_w;
+        if (col_idx) *col_idx = p->col_idx_w ? p->col_idx_w : p->col_idx + p->base_w;
         return FE_OK;
     }
     if (row_ptr) *row_ptr = p->dofs == 2 ? p->row_ptr2 : p->row_ptr;

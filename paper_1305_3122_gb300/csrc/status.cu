@@ -185,8 +185,9 @@ fe_status fe_check_pair(fe_mesh mesh, fe_pattern pat, int dofs) {
 
 // ------------------------------------------------------------------------ scan
 //
-// Three passes: per-tile sums, an exclusive scan of the tile sums by one block, and a
-// per-tile scan that adds the tile's offset. Tiles are SCAN_TILE consecutive elements.
+// Two passes: per-tile sums, then a per-tile scan whose block first adds up the sums of the
+// tiles before its own (its offset). Tiles are SCAN_TILE consecutive elements; the total lands in
+// out[n].
 
 static constexpr int SCAN_BLOCK = 512;
 static constexpr int SCAN_ITEMS = 8;

@@ -199,7 +199,9 @@ class Mesh:
     def part(cls, q, me, row_begin: int, row_end: int, stream=None) -> "Mesh":
         """A rank's share of a row partition (fe_mesh_create_part): the triangles of the global
         mesh (q [2, nq], me [3, nme], host or CUDA) that touch the owned vertices
-        [row_begin, row_end), with global vertex ids."""
+        [row_begin, row_end). The library numbers the part's vertices locally; every id it takes
+        or returns is global (nq is the global count, weights have nq entries, set_coords takes
+        the global q, windows list global columns)."""
         self = cls.__new__(cls)
         self._h = None
         self._me_ref = None

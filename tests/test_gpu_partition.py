@@ -110,6 +110,55 @@ def test_partition_errors_and_edge_cases():
     assert 0 < others.nme < m.nme
 
 
+def test_part_speaks_global_ids():
+    """A part numbers its vertices locally inside the library; what the caller sees stays global:
+    the vertex count, the weights, the coordinates of set_coords and the window's columns."""
+    m = _mesh()
+    wh = meshgen.vertex_weights(m, 91)
+    w = torch.tensor(wh, device="cuda")
+    r0, r1 = 700, 1300
+    part = feasm.Mesh.part(m.q, m.me, r0, r1)
+    assert part.nq == m.nq and 0 < part.nme < m.nme
+    with pytest.raises(feasm.FeasmError) as e:          # a part builds row windows only
+        feasm.Pattern(part)
+    assert e.value.status == 1
+    # moved points (a shear and a scaling keep every triangle counter-clockwise), global array
+    q2 = m.q.copy()
+    q2[0] = 1.5 * m.q[0] + 0.25 * m.q[1]
+    q2[1] = 0.75 * m.q[1] - 0.1
+    part.set_coords(torch.tensor(q2))
+    pat = feasm.Pattern(part, rows=(r0, r1))
+    S, Mw = feasm.assemble_stiff_wmass(part, pat, w, feasm.ROW)
+    part.check()
+    full = feasm.Mesh(q2, m.me)
+    fp = feasm.Pattern(full)
+    Sf, Mwf = feasm.assemble_stiff_wmass(full, fp, w, feasm.ROW)
+    rp, ci = fp.row_ptr.cpu().numpy(), fp.col_idx.cpu().numpy()
+    lo, hi = rp[r0], rp[r1]
+    np.testing.assert_array_equal(pat.row_ptr.cpu().numpy(), rp[r0:r1 + 1] - lo)
+    np.testing.assert_array_equal(pat.col_idx.cpu().numpy(), ci[lo:hi])
+    np.testing.assert_array_equal(S.cpu().numpy().view(np.int64), Sf.cpu().numpy()[lo:hi].view(np.int64))
+    np.testing.assert_array_equal(Mw.cpu().numpy().view(np.int64), Mwf.cpu().numpy()[lo:hi].view(np.int64))
+    rpo, cio, vso = oracle.assemble(oracle.STIFF, q2, m.me)
+    assert_values_close(rp, Sf.cpu().numpy(), vso)
+
+
+@pytest.mark.parametrize("rows", [(0, 0), (17, 17), (None, None)])
+def test_empty_parts(rows):
+    """An empty owned range keeps no triangle and gives an empty window; so does a range at the
+    end of the numbering."""
+    m = _mesh()
+    r0, r1 = (m.nq, m.nq) if rows[0] is None else rows
+    part = feasm.Mesh.part(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"), r0, r1)
+    assert part.nme == 0 and part.nq == m.nq
+    pat = feasm.Pattern(part, rows=(r0, r1))
+    assert pat.n_rows == 0 and pat.nnz == 0 and pat.row_ptr.cpu().tolist() == [0]
+    w = torch.ones(m.nq, dtype=torch.float64, device="cuda")
+    S, Mw = feasm.assemble_stiff_wmass(part, pat, w, feasm.ROW)
+    assert S.numel() == 0 and Mw.numel() == 0
+    part.check()
+
+
 def _rank(rank, world, port, out):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
