@@ -172,9 +172,11 @@ fe_status fe_mesh_create_topology(int32_t nq, int32_t nme, int32_t* me_dev, cuda
 fe_status fe_mesh_attach_coords(fe_mesh m, const double* q_dev, cudaStream_t s);
 fe_status fe_mesh_orientation_status(const int word[4]);
 
-// The scalar pattern of any mesh, a part included, without the map or gather lists (pattern.cu);
-// fe_pattern_build_part cuts its row window out of it.
-fe_status fe_pattern_build_rows(fe_mesh m, fe_stream stream, fe_pattern* out);
+// The scalar pattern of any mesh, a part included, without the map or gather lists, exposed as
+// the row window [row0, row1) of the mesh's own ids (pattern.cu): n_rows, nnz and base_w are set
+// from the same read-back as the rest of the build; fe_pattern_build_part adds the window's
+// offsets (and, for a part, its global column ids).
+fe_status fe_pattern_build_rows(fe_mesh m, int32_t row0, int32_t row1, fe_stream stream, fe_pattern* out);
 
 // High float (top 24 significant bits, truncated) of a double, by bit operations: no FP64
 // instruction. |result - x| < 2^-23 |x|; zero and subnormals give zero, magnitudes above the

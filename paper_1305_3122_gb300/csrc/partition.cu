@@ -28,22 +28,55 @@ namespace {
 
 enum { PART_RANGE = 1, PART_REPEAT = 2, PART_ORIENT = 4 };
 
-// keep[k] = 1 if triangle k has a vertex in [r0, r1); used[v] = 1 for every vertex of a kept
-// triangle and every owned vertex (used is zero on entry; threads that mark the same vertex write
-// the same value). Every kept triangle is checked as in the mesh validation (ids in range,
-// distinct, counter-clockwise: D > 0 in FP64 from coordinate differences); word: [0] OR of the
-// problems, [1..3] the first bad triangle of each kind (global index). A triangle with an id out
-// of range anywhere is reported, kept or not.
-__global__ void k_part_select(const int32_t* __restrict__ me, int32_t nme, int32_t nq, const double* __restrict__ q,
-                              int32_t r0, int32_t r1, int32_t* __restrict__ keep, int32_t* __restrict__ used,
-                              int* __restrict__ word) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < r1; v += stride) used[v] = 1;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += stride) {
-        const int32_t v0 = me[k], v1 = me[nme + k], v2 = me[2 * (int64_t)nme + k];
-        const bool in = v0 >= 0 && v0 < nq && v1 >= 0 && v1 < nq && v2 >= 0 && v2 < nq;
-        const bool mine = (v0 >= r0 && v0 < r1) || (v1 >= r0 && v1 < r1) || (v2 >= r0 && v2 < r1);
-        keep[k] = in && mine;
+// Selection word: [0] OR of the problems, [1] the kept triangles, [2..4] the first bad triangle
+// of each kind (global index).
+enum { W_BITS = 0, W_KEPT = 1, W_FIRST = 2 };
+
+// Triangles are taken in tiles of PT_TILE: thread t of tile b holds triangles
+// b * PT_TILE + j * PT_BLOCK + t, j < PT_ITEMS (coalesced loads for each j).
+constexpr int PT_BLOCK = 256, PT_ITEMS = 8, PT_TILE = PT_BLOCK * PT_ITEMS, PT_WARPS = PT_BLOCK / 32;
+
+__device__ __forceinline__ bool ids_in(int32_t v0, int32_t v1, int32_t v2, int32_t nq) {
+    return v0 >= 0 && v0 < nq && v1 >= 0 && v1 < nq && v2 >= 0 && v2 < nq;
+}
+
+__device__ __forceinline__ bool touches(int32_t v0, int32_t v1, int32_t v2, int32_t r0, int32_t r1) {
+    return (v0 >= r0 && v0 < r1) || (v1 >= r0 && v1 < r1) || (v2 >= r0 && v2 < r1);
+}
+
+// A triangle is kept when its ids are in range and one of its vertices is owned. Per tile: the
+// number of kept triangles (tile_cnt, and their total in word[W_KEPT]); used[v] = 1 for every
+// vertex of a kept triangle and every owned vertex (used is zero on entry; threads that mark the
+// same vertex write the same value). Every kept triangle is checked as in the mesh validation
+// (distinct ids, counter-clockwise: D > 0 in FP64 from coordinate differences); a triangle with
+// an id out of range anywhere is reported, kept or not.
+__global__ void __launch_bounds__(PT_BLOCK) k_part_count(const int32_t* __restrict__ me, int32_t nme, int32_t nq,
+                                                         const double* __restrict__ q, int32_t r0, int32_t r1,
+                                                         int32_t* __restrict__ used, int32_t* __restrict__ tile_cnt,
+                                                         int* __restrict__ word) {
+    __shared__ int red[PT_WARPS];
+    for (int64_t v = r0 + blockIdx.x * (int64_t)PT_BLOCK + threadIdx.x; v < r1; v += (int64_t)gridDim.x * PT_BLOCK)
+        used[v] = 1;
+    const int64_t base = (int64_t)blockIdx.x * PT_TILE;
+    int32_t tri[PT_ITEMS][3];                         // all loads issued before any is used
+#pragma unroll
+    for (int j = 0; j < PT_ITEMS; j++) {
+        const int64_t k = base + j * PT_BLOCK + threadIdx.x;
+        tri[j][0] = tri[j][1] = tri[j][2] = 0;
+        if (k < nme) {
+            tri[j][0] = me[k];
+            tri[j][1] = me[nme + k];
+            tri[j][2] = me[2 * (int64_t)nme + k];
+        }
+    }
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < PT_ITEMS; j++) {
+        const int64_t k = base + j * PT_BLOCK + threadIdx.x;
+        if (k >= nme) break;
+        const int32_t v0 = tri[j][0], v1 = tri[j][1], v2 = tri[j][2];
+        const bool in = ids_in(v0, v1, v2, nq);
+        const bool mine = touches(v0, v1, v2, r0, r1);
         int bad = 0;
         if (!in) bad = PART_RANGE;
         else if (mine && (v0 == v1 || v1 == v2 || v0 == v2)) bad = PART_REPEAT;
@@ -54,28 +87,85 @@ __global__ void k_part_select(const int32_t* __restrict__ me, int32_t nme, int32
             if (!(vx * wy - wx * vy > 0.0)) bad = PART_ORIENT;
         }
         if (in && mine) {
+            cnt++;
             used[v0] = 1;
             used[v1] = 1;
             used[v2] = 1;
         }
         if (bad) {
-            atomicOr(&word[0], bad);
-            atomicMin(&word[bad == PART_RANGE ? 1 : bad == PART_REPEAT ? 2 : 3], (int)k);
+            atomicOr(&word[W_BITS], bad);
+            atomicMin(&word[W_FIRST + (bad == PART_RANGE ? 0 : bad == PART_REPEAT ? 1 : 2)], (int)k);
         }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0 && base < nme) {
+        int t = 0;
+        for (int w = 0; w < PT_WARPS; w++) t += red[w];
+        tile_cnt[blockIdx.x] = t;
+        if (t) atomicAdd(&word[W_KEPT], t);
     }
 }
 
-// The kept triangles, in ascending order, into me_part [3][n_part] (pos = exclusive scan of
-// keep), their vertices renumbered by loc (exclusive scan of used).
-__global__ void k_part_compact(const int32_t* __restrict__ me, int32_t nme, const int32_t* __restrict__ keep,
-                               const int32_t* __restrict__ pos, const int32_t* __restrict__ loc, int32_t n_part,
-                               int32_t* __restrict__ me_part) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nme; k += (int64_t)gridDim.x * blockDim.x) {
-        if (!keep[k]) continue;
-        const int64_t at = pos[k];
-        me_part[at] = loc[me[k]];
-        me_part[n_part + at] = loc[me[nme + k]];
-        me_part[2 * (int64_t)n_part + at] = loc[me[2 * (int64_t)nme + k]];
+// The kept triangles, in ascending order, into me_part [3][n_part], their vertices renumbered by
+// loc (exclusive scan of used). A tile's first place is the sum of the counts of the tiles before
+// it; inside the tile, kept triangles are ranked by ballots in the order (j, warp, lane), which is
+// the order of their indices.
+__global__ void __launch_bounds__(PT_BLOCK) k_part_place(const int32_t* __restrict__ me, int32_t nme, int32_t nq,
+                                                         int32_t r0, int32_t r1, const int32_t* __restrict__ tile_cnt,
+                                                         const int32_t* __restrict__ loc, int32_t n_part,
+                                                         int32_t* __restrict__ me_part) {
+    __shared__ int red[PT_WARPS];
+    __shared__ int at0[PT_ITEMS * PT_WARPS];
+    if (tile_cnt[blockIdx.x] == 0) return;            // most tiles of a spatially compact part
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int a = 0;
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += PT_BLOCK) a += tile_cnt[t];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) red[wid] = a;
+    const int64_t base = (int64_t)blockIdx.x * PT_TILE;
+    int32_t v[PT_ITEMS][3];
+    int pre[PT_ITEMS];
+    bool kp[PT_ITEMS];
+#pragma unroll
+    for (int j = 0; j < PT_ITEMS; j++) {
+        const int64_t k = base + j * PT_BLOCK + threadIdx.x;
+        kp[j] = false;
+        v[j][0] = v[j][1] = v[j][2] = 0;
+        if (k < nme) {
+            v[j][0] = me[k];
+            v[j][1] = me[nme + k];
+            v[j][2] = me[2 * (int64_t)nme + k];
+            kp[j] = ids_in(v[j][0], v[j][1], v[j][2], nq) && touches(v[j][0], v[j][1], v[j][2], r0, r1);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, kp[j]);
+        pre[j] = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) at0[j * PT_WARPS + wid] = __popc(bal);
+    }
+    __syncthreads();
+    if (wid == 0) {                                   // exclusive scan of the 64 counts, two per lane
+        static_assert(PT_ITEMS * PT_WARPS == 64, "two counts per lane");
+        int off = lane < PT_WARPS ? red[lane] : 0;
+        for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+        const int c0 = at0[2 * lane], c1 = at0[2 * lane + 1];
+        int x = c0 + c1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const int ex = off + x - c0 - c1;
+        at0[2 * lane] = ex;
+        at0[2 * lane + 1] = ex + c0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < PT_ITEMS; j++) {
+        if (!kp[j]) continue;
+        const int64_t at = at0[j * PT_WARPS + wid] + pre[j];
+        me_part[at] = loc[v[j][0]];
+        me_part[n_part + at] = loc[v[j][1]];
+        me_part[2 * (int64_t)n_part + at] = loc[v[j][2]];
     }
 }
 
@@ -122,11 +212,11 @@ extern "C" fe_status fe_mesh_create_part(int32_t nq, int32_t nme, const double* 
     FeStreamScope scope(s);
     const bool host = ptr_kind == FE_PTR_HOST;
     double* q_tmp = nullptr;
-    int32_t *me_tmp = nullptr, *keep = nullptr, *pos = nullptr, *used = nullptr, *loc = nullptr, *me_part = nullptr;
+    int32_t *me_tmp = nullptr, *tile_cnt = nullptr, *used = nullptr, *loc = nullptr, *me_part = nullptr;
     int* word = nullptr;
     // frees are ordered on the stream after the kernels that read these arrays
     auto cleanup = [&]() {
-        fe_free(q_tmp); fe_free(me_tmp); fe_free(keep); fe_free(pos); fe_free(used); fe_free(loc); fe_free(word);
+        fe_free(q_tmp); fe_free(me_tmp); fe_free(tile_cnt); fe_free(used); fe_free(loc); fe_free(word);
     };
     fe_status st = FE_OK;
     const double* qd = q;
@@ -142,54 +232,53 @@ extern "C" fe_status fe_mesh_create_part(int32_t nq, int32_t nme, const double* 
         qd = q_tmp;
         med = me_tmp;
     }
-    if (!st) st = fe_alloc_n(&keep, (size_t)nme + 1, "halo flags");
-    if (!st) st = fe_alloc_n(&pos, (size_t)nme + 1, "halo positions");
+    const int64_t ntiles = ((int64_t)nme + PT_TILE - 1) / PT_TILE;
+    if (!st) st = fe_alloc_n(&tile_cnt, (size_t)ntiles + 1, "halo tile counts");
     if (!st) st = fe_alloc_n(&used, (size_t)nq + 1, "part vertex flags");
     if (!st) st = fe_alloc_n(&loc, (size_t)nq + 1, "local vertex ids");
-    if (!st) st = fe_alloc_n(&word, 4, "selection word");
+    if (!st) st = fe_alloc_n(&word, 8, "selection word");
     if (st) { cleanup(); return st; }
-    // 1. select the triangles and the vertices; 2. number both by exclusive scans (the totals land
-    // in pos[nme] and loc[nq]); one read-back of the word, the two totals and loc[row_begin]
-    cudaError_t e = cudaMemsetAsync(word, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(word + 1, 0x7F, 3 * sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, sizeof(int32_t) * ((size_t)nq + 1), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(pos, 0, sizeof(int32_t), s);      // the totals when nme or nq is 0
-    if (e == cudaSuccess) e = cudaMemsetAsync(loc, 0, sizeof(int32_t), s);
-    const int64_t sel_n = nme > row_end - row_begin ? (int64_t)nme : (int64_t)row_end - row_begin;
-    if (e == cudaSuccess && sel_n > 0) {
-        { FE_PROF("k_part_select", s); k_part_select<<<fe_grid(sel_n, 256), 256, 0, s>>>(med, nme, nq, qd, row_begin, row_end, keep, used, word); }
+    // 1. count the kept triangles per tile and mark the part's vertices; 2. number the vertices by
+    // an exclusive scan (its total lands in loc[nq]); one read-back of the word, the vertex total
+    // and loc[row_begin]; 3. place the kept triangles
+    cudaError_t e = cudaMemsetAsync(word, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(word + W_FIRST, 0x7F, 3 * sizeof(int), s);
+    if (e == cudaSuccess && nq > 0) e = cudaMemsetAsync(used, 0, sizeof(int32_t) * (size_t)nq, s);
+    const int64_t owned = (int64_t)row_end - row_begin;
+    const int64_t grid = ntiles > 0 ? ntiles : (owned > 0 ? 1 : 0);
+    if (e == cudaSuccess && grid > 0) {
+        { FE_PROF("k_part_count", s); k_part_count<<<(unsigned)grid, PT_BLOCK, 0, s>>>(med, nme, nq, qd, row_begin, row_end, used, tile_cnt, word); }
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) { cleanup(); return fe_cuda_fail(e, "halo selection"); }
-    if (nme > 0 && (st = fe_exclusive_scan(keep, pos, nme, s, nullptr))) { cleanup(); return st; }
     if (nq > 0 && (st = fe_exclusive_scan(used, loc, nq, s, nullptr))) { cleanup(); return st; }
-    int host_word[4] = {0, 0, 0, 0};
-    int32_t n_part = 0, n_loc = 0, loc0 = 0;
+    int host_word[5] = {0, 0, 0, 0, 0};
+    int32_t n_loc = 0, loc0 = 0;
     e = cudaMemcpyAsync(host_word, word, sizeof host_word, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&n_part, pos + nme, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&n_loc, loc + nq, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&loc0, loc + row_begin, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nq > 0) e = cudaMemcpyAsync(&n_loc, loc + nq, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nq > 0) e = cudaMemcpyAsync(&loc0, loc + row_begin, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { cleanup(); return fe_cuda_fail(e, "halo selection"); }
-    if (host_word[0] & PART_RANGE) {
+    if (host_word[W_BITS] & PART_RANGE) {
         cleanup();
-        return fe_fail(FE_ERR_INDEX_RANGE, "triangle " + std::to_string(host_word[1]) + " has a vertex id outside [0, nq)");
+        return fe_fail(FE_ERR_INDEX_RANGE, "triangle " + std::to_string(host_word[W_FIRST]) + " has a vertex id outside [0, nq)");
     }
-    if (host_word[0] & PART_REPEAT) {
+    if (host_word[W_BITS] & PART_REPEAT) {
         cleanup();
-        return fe_fail(FE_ERR_DEGENERATE, "triangle " + std::to_string(host_word[2]) + " repeats a vertex");
+        return fe_fail(FE_ERR_DEGENERATE, "triangle " + std::to_string(host_word[W_FIRST + 1]) + " repeats a vertex");
     }
-    if (host_word[0] & PART_ORIENT) {
+    if (host_word[W_BITS] & PART_ORIENT) {
         cleanup();
-        return fe_fail(FE_ERR_ORIENTATION, "triangle " + std::to_string(host_word[3]) +
+        return fe_fail(FE_ERR_ORIENTATION, "triangle " + std::to_string(host_word[W_FIRST + 2]) +
                                                " has signed area <= 0 (must be counter-clockwise)");
     }
-    // 3. the kept triangles with local ids; the part as a mesh of its own (its connectivity passes
-    // to the mesh, whose creation counts the valences the pattern build needs: every id was
-    // checked above, so without a second check or read-back); its vertices' points and global ids
+    const int32_t n_part = host_word[W_KEPT];
+    // the part as a mesh of its own: its connectivity passes to the mesh, whose creation counts the
+    // valences the pattern build needs (every id was checked above, so without a second check or
+    // read-back); then its vertices' points and global ids
     if ((st = fe_alloc_n(&me_part, 3 * (size_t)n_part, "halo connectivity"))) { cleanup(); return st; }
     if (n_part > 0) {
-        { FE_PROF("k_part_compact", s); k_part_compact<<<fe_grid(nme, 256), 256, 0, s>>>(med, nme, keep, pos, loc, n_part, me_part); }
+        { FE_PROF("k_part_place", s); k_part_place<<<(unsigned)ntiles, PT_BLOCK, 0, s>>>(med, nme, nq, row_begin, row_end, tile_cnt, loc, n_part, me_part); }
         e = cudaGetLastError();
         if (e != cudaSuccess) { fe_free(me_part); cleanup(); return fe_cuda_fail(e, "halo compaction"); }
     }
@@ -220,39 +309,33 @@ extern "C" fe_status fe_pattern_build_part(fe_mesh m, int32_t row_begin, int32_t
     const int32_t lo = part ? m->part0 : 0, hi = part ? m->part1 : m->nq;
     if (row_begin < lo || row_end < row_begin || row_end > hi)
         return fe_fail(FE_ERR_INVALID_ARG, "the row window must lie in [0, nq) and, for a part, in its owned rows");
+    const int32_t n = row_end - row_begin;
+    const int32_t r0 = part ? row_begin - m->part0 + m->loc0 : row_begin;      // the window in the mesh's ids
     fe_pattern p = nullptr;
-    fe_status st = fe_pattern_build_rows(m, stream, &p);
+    fe_status st = fe_pattern_build_rows(m, r0, r0 + n, stream, &p);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     FeStreamScope scope(s);
-    const int32_t n = row_end - row_begin;
-    const int32_t r0 = part ? row_begin - m->part0 + m->loc0 : row_begin;      // the window in the mesh's ids
     st = fe_alloc_n(&p->row_ptr_w, (size_t)n + 1, "window offsets");
-    int32_t ends[2] = {0, 0};
     if (!st) {
         { FE_PROF("k_window_offsets", s); k_window_offsets<<<fe_grid((int64_t)n + 1, 256), 256, 0, s>>>(p->row_ptr, r0, n, p->row_ptr_w); }
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[0], p->row_ptr + r0, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], p->row_ptr + r0 + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = fe_cuda_fail(e, "row window");
     }
-    const int64_t nnz = (int64_t)ends[1] - ends[0];
     if (!st && part) {
         // the columns the caller sees carry global ids; the kernels keep reading the local ones
-        st = fe_alloc_n(&p->col_idx_w, (size_t)nnz, "window columns");
-        if (!st && nnz > 0) {
-            { FE_PROF("k_window_columns", s); k_window_columns<<<fe_grid(nnz, 256), 256, 0, s>>>(p->col_idx + ends[0], nnz, m->l2g, p->col_idx_w); }
+        st = fe_alloc_n(&p->col_idx_w, (size_t)p->nnz, "window columns");
+        if (!st && p->nnz > 0) {
+            { FE_PROF("k_window_columns", s); k_window_columns<<<fe_grid(p->nnz, 256), 256, 0, s>>>(p->col_idx + p->base_w, p->nnz, m->l2g, p->col_idx_w); }
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) st = fe_cuda_fail(e, "window columns");
         }
     }
-    if (st) { fe_pattern_destroy(p); return st; }
-    p->row0 = r0;
-    p->row1 = r0 + n;
-    p->base_w = ends[0];
-    p->n_rows = n;
-    p->nnz = nnz;
+    if (st) {
+        cudaStreamSynchronize(s);
+        fe_pattern_destroy(p);
+        return st;
+    }
     *out = p;
     return FE_OK;
 }

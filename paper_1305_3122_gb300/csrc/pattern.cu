@@ -751,9 +751,14 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     // one host synchronisation: flags, the counts of the lists, nnz
     int host_c[4] = {0, 0, 0, 0};
     int32_t tot32 = 0;
+    int32_t wends[2] = {0, 0};
     auto read_back = [&]() -> fe_status {
         FE_CUDA(cudaMemcpyAsync(host_c, t.counters, sizeof host_c, cudaMemcpyDeviceToHost, s));
         FE_CUDA(cudaMemcpyAsync(&tot32, p->row_ptr + nq, sizeof tot32, cudaMemcpyDeviceToHost, s));
+        if (p->row1 >= 0) {                               // a row window's ends (fe_pattern_build_rows)
+            FE_CUDA(cudaMemcpyAsync(&wends[0], p->row_ptr + p->row0, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            FE_CUDA(cudaMemcpyAsync(&wends[1], p->row_ptr + p->row1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        }
         FE_CUDA(cudaStreamSynchronize(s));
         return FE_OK;
     };
@@ -770,6 +775,11 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     p->n_gen = host_counts[1];
     p->n_rows = nq;
     p->nnz = tot;
+    if (p->row1 >= 0) {
+        p->base_w = wends[0];
+        p->n_rows = p->row1 - p->row0;
+        p->nnz = (int64_t)wends[1] - wends[0];
+    }
     if (dofs == 2) {
         if (4 * tot >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "elasticity nnz exceeds int32");
         if ((st = fe_alloc_n(&p->row_ptr2, 2 * (size_t)nq + 1, "row_ptr (dofs=2)"))) return st;
@@ -790,8 +800,11 @@ static fe_status build(fe_mesh m, int dofs, int flags, cudaStream_t s, fe_patter
     return FE_OK;
 }
 
-static fe_status pattern_new(fe_mesh m, int dofs, int flags, fe_stream stream, fe_pattern* out) {
+static fe_status pattern_new(fe_mesh m, int dofs, int flags, fe_stream stream, fe_pattern* out, int32_t row0 = 0,
+                             int32_t row1 = -1) {
     fe_pattern p = new fe_pattern_s();
+    p->row0 = row0;
+    p->row1 = row1;
     p->dofs = dofs;
     p->flags = flags;
     p->nq = m->nq;
@@ -824,10 +837,10 @@ extern "C" fe_status fe_pattern_build(fe_mesh m, int dofs, int flags, fe_stream 
     return pattern_new(m, dofs, flags, stream, out);
 }
 
-fe_status fe_pattern_build_rows(fe_mesh m, fe_stream stream, fe_pattern* out) {
+fe_status fe_pattern_build_rows(fe_mesh m, int32_t row0, int32_t row1, fe_stream stream, fe_pattern* out) {
     *out = nullptr;
     if (9 * (int64_t)m->nme >= INT32_MAX) return fe_fail(FE_ERR_LIMIT, "9*nme must be < 2^31");
-    return pattern_new(m, 1, FE_PATTERN_DEFAULT, stream, out);
+    return pattern_new(m, 1, FE_PATTERN_DEFAULT, stream, out, row0, row1);
 }
 
 extern "C" fe_status fe_pattern_info(fe_pattern p, int64_t* n_rows, int64_t* nnz, const int32_t** row_ptr,
