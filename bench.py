@@ -788,11 +788,29 @@ def partition(feasm, meshgen, torch, flush, worlds=(2, 4, 8), reps: int = 5) -> 
         out[str(world)] = {"rank_ms": [round(t, 4) for t in ranks], "rank_ms_max": round(worst, 4),
                            "triangles_held_over_nme": round(halo / nme, 4),
                            "projected_value": round(nme / worst / 1e3, 1), "unit": UNIT}
+    # where the time of rank 0's step goes at the largest world: the library's kernel events
+    world = max(worlds)
+    r0, r1 = part_rows.row_ranges(nq, world)[0]
+    feasm.profile_reset()
+    feasm.profile_enable(True)
+    for _ in range(reps):
+        mesh = feasm.Mesh.part(q_d, me_d, r0, r1)
+        pat = feasm.Pattern(mesh, rows=(r0, r1), map=False)
+        feasm.assemble_stiff_wmass(mesh, pat, w_d, feasm.ROW)
+        pat.close()
+        mesh.close()
+    torch.cuda.synchronize()
+    feasm.profile_enable(False)
+    prof = feasm.profile_read()
+    kernels = {k: round(v[0] / reps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
     return {"workload": f"row partition of the {N_CELLS}x{N_CELLS}-cell headline mesh, nodes numbered row by row, "
                         "S + M^[w] by row owners",
-            "how": "each rank's step timed in turn on one GPU (median of 5 between L2 flushes); the ranks exchange "
-                   "no values, so the projection for `world` GPUs is nme / the slowest rank's step",
-            "whole_ms": round(whole, 4), "worlds": out}
+            "how": f"each rank's step timed in turn on one GPU (median of {reps} between L2 flushes); the ranks "
+                   "exchange no values, so the projection for `world` GPUs is nme / the slowest rank's step",
+            "whole_ms": round(whole, 4), "worlds": out,
+            "rank0_kernels_ms": {"world": world, "kernel_sum_ms": round(sum(kernels.values()), 4),
+                                 "what": "rank 0's step with the library's kernel events (ms per step, L2 not flushed)",
+                                 "kernels": kernels}}
 
 
 def _whole_step(feasm, q_d, me_d, w_d):
@@ -1135,10 +1153,12 @@ def main() -> int:
     ap.add_argument("--no-other", action="store_true", help="skip the elasticity, adjoint, zero-dropping, tetrahedra and P2 legs")
     ap.add_argument("--traffic", default=os.path.join(ROOT, "profiles", "traffic.json"),
                     help="per-kernel DRAM bytes per launch from an ncu capture (JSON)")
-    ap.add_argument("--only", choices=["elasticity", "adjoint", "drop_zeros", "tetrahedra", "p2", "p3"],
+    ap.add_argument("--only", choices=["elasticity", "adjoint", "drop_zeros", "tetrahedra", "p2", "p3", "partition"],
                     help="run this one leg alone and print its object (for profiling; no headline step)")
     ap.add_argument("--tet-cells", type=int, default=128, help="cells per side of the tetrahedra leg's cube")
     ap.add_argument("--p2-cells", type=int, default=1024, help="cells per side of the P2 leg's square")
+    ap.add_argument("--part-worlds", default="2,4,8", help="rank counts of the partition leg (comma-separated)")
+    ap.add_argument("--part-reps", type=int, default=5, help="timed repetitions of each rank's step in the partition leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)    # at least 3 untimed warm-up steps
     if args.impl == "reference":
@@ -1164,6 +1184,9 @@ def run_leg(args) -> int:
         out = p2(feasm, meshgen, torch, flush, hbm, peak_kind, cells=args.p2_cells)
     elif args.only == "p3":
         out = p3(feasm, meshgen, torch, flush, hbm, peak_kind, cells=args.p2_cells)
+    elif args.only == "partition":
+        worlds = tuple(int(x) for x in args.part_worlds.split(","))
+        out = partition(feasm, meshgen, torch, flush, worlds=worlds, reps=max(args.part_reps, 1))
     else:
         m = meshgen.square_mesh(args.cells, 13053122 + 2)
         mesh = feasm.Mesh(torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda"))
