@@ -60,6 +60,36 @@ def test_parts_join_to_whole_matrix(world, source):
     assert_values_close(rpo, vmw, vmo)
 
 
+def test_band_numbered_parts_join_to_whole_matrix():
+    """Nodes numbered row by row, as a partitioner would number them: each of 8 ranks' triangles
+    lie in a few of the 40 tiles of 2048 triangles, so most tiles keep nothing (the placement
+    skips them), and the parts' local numberings are nearly contiguous ranges."""
+    m = meshgen.square_mesh(200, 93, permute=False)
+    wh = meshgen.vertex_weights(m, 93)
+    w = torch.tensor(wh, device="cuda")
+    q, me = torch.tensor(m.q, device="cuda"), torch.tensor(m.me, device="cuda")
+    blocks, held = [], 0
+    for r0, r1 in partition.row_ranges(m.nq, 8):
+        part = feasm.Mesh.part(q, me, r0, r1)
+        held += part.nme
+        blocks.append(_block(part, (r0, r1), w))
+        part.check()
+    assert held < 1.05 * m.nme                        # each cut duplicates one or two rows of cells
+    rp, ci, vs, vmw, vm = partition.concat_rows(blocks)
+    full = feasm.Mesh(m.q, m.me)
+    fp = feasm.Pattern(full)
+    Sf, Mwf = feasm.assemble_stiff_wmass(full, fp, w, feasm.ROW)
+    Mf = feasm.assemble_mass(full, fp, feasm.ROW)
+    assert_csr_equal(rp, ci, fp.row_ptr.cpu(), fp.col_idx.cpu())
+    for got, ref in ((vs, Sf), (vmw, Mwf), (vm, Mf)):
+        np.testing.assert_array_equal(got.view(np.int64), ref.cpu().numpy().view(np.int64))
+    rpo, cio, vso = oracle.assemble(oracle.STIFF, m.q, m.me)
+    _, _, vmo = oracle.assemble(oracle.WMASS, m.q, m.me, wh)
+    assert_csr_equal(rp, ci, rpo, cio)
+    assert_values_close(rpo, vs, vso)
+    assert_values_close(rpo, vmw, vmo)
+
+
 def test_windows_of_a_whole_mesh():
     m = _mesh()
     w = torch.tensor(meshgen.vertex_weights(m, 91), device="cuda")
